@@ -1,0 +1,238 @@
+/*
+ * egm.h - exact epipolar-guided matching on NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of libegm.so.  The library implements the matching hot path of
+ * "Pixel-Accurate Epipolar Guided Matching" (arXiv 2603.18401):
+ *
+ *   1. epipole e2 = null(F^T)                                 (Algorithm 1)
+ *   2. epipolar line l_i = F p~_i^1 of every image-1 query    (Sec. 3)
+ *   3. the angle of every image-2 keypoint seen from e2 and the angular
+ *      radius of its eps-circle                               (Sec. 4.2)
+ *   4. keypoints sorted by angle (a device radix sort), the replacement of
+ *      the paper's segment tree                               (Sec. 4.2/4.4)
+ *   5. stabbing: each query scans the angle window its line can reach and
+ *      keeps exactly the keypoints with dist(l_i, p_j) <= eps_j (Eq. 3/4)
+ *   6. optional candidate lists in CSR form                   (Eq. 4)
+ *   7. descriptor distances restricted to the candidates      (Sec. 4.3)
+ *   8. best / second best by (distance, index) and Lowe's ratio test
+ *      (tau = 0.8 in Sec. 5.1)                                 (Sec. 4.3)
+ *
+ * Exactness: the candidate set of a query is the set the plain definition
+ * (Eq. 4, "<=" as printed) gives when evaluated in IEEE FP64 as
+ *     a = (F00 x + F01 y) + F02,  b = ...,  c = ...
+ *     dist = |(a x2 + b y2) + c| / sqrt(a a + b b)
+ * with one rounding per operation and no fused multiply-add.  Keypoints whose
+ * FP32 pre-test is not conclusive are decided by exactly that FP64
+ * expression, so results are bit-identical to a brute-force evaluation.
+ *
+ * Conventions for every entry point:
+ *   - Device pointers, unless the entry point's name ends in _host.  The
+ *     caller owns every input and output buffer; the library owns only the
+ *     scratch memory held by the context (grown on demand, or fixed in
+ *     advance by egm_reserve).
+ *   - Work is enqueued on the context's CUDA stream.  When params.sync is
+ *     1 (the default) a call waits for its own completion and returns the
+ *     device-side status; when 0 it returns after enqueueing and
+ *     egm_sync() returns the device-side status later.
+ *   - Errors never abort or trap the device: kernels record a status word.
+ *   - Not thread-safe per context; use one context per host thread.
+ */
+#ifndef EGM_H
+#define EGM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EGM_VERSION 1
+
+typedef struct egm_ctx egm_ctx;
+
+typedef enum egm_status {
+    EGM_OK = 0,
+    EGM_ERR_ARG = -1,            /* invalid argument (NULL, size, eps <= 0, alignment) */
+    EGM_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+    EGM_ERR_NOMEM = -3,          /* scratch allocation failed */
+    EGM_ERR_CAPACITY = -4,       /* cand_capacity too small; *cand_total holds the need */
+    EGM_ERR_DEGENERATE_F = -5,   /* F is zero, or rank < 2 (no epipole) */
+    EGM_ERR_NAN = -6,            /* NaN or Inf in F, keypoints or eps */
+    EGM_ERR_TIMEOUT = -7,        /* a bounded device wait ran out */
+    EGM_ERR_UNIMPLEMENTED = -8
+} egm_status;
+
+/* Descriptor kinds (Sec. 4.3 compares descriptors only within C_i). */
+enum {
+    EGM_DESC_U8_L2 = 0,   /* dim uint8 per row; squared L2, exact int32 */
+    EGM_DESC_F32_L2 = 1,  /* dim float32 per row; squared L2 in FP32 */
+    EGM_DESC_BIN = 2      /* dim bits per row (dim % 128 == 0); Hamming */
+};
+
+/* Per-query result flags. */
+enum {
+    EGM_FLAG_HAS_BEST = 1,         /* at least one candidate */
+    EGM_FLAG_RATIO_PASS = 2,       /* accepted: ratio test passed or no second candidate */
+    EGM_FLAG_NO_SECOND = 4,        /* exactly one candidate */
+    EGM_FLAG_DEGENERATE_LINE = 8   /* F p~ has a = b = 0: no line, empty set */
+};
+
+/*
+ * One image pair (Sec. 3 "Guided Matching": P1, P2, D1, D2 and F; the
+ * tolerance eps of Eq. 4, per image-2 keypoint as in Sec. 4.2).
+ *   xy1     [m][2] float64  image-1 keypoints (x, y) in pixels (queries)
+ *   xy2     [n][2] float64  image-2 keypoints (references)
+ *   F       [9]    float64  row-major fundamental matrix, p2^T F p1 = 0
+ *   eps2    [n]    float64  per-keypoint tolerance in pixels, or NULL to
+ *                           use eps_scalar for every keypoint; must be > 0
+ *   desc1   [m][row]        image-1 descriptors, 16-byte aligned rows
+ *   desc2   [n][row]        image-2 descriptors
+ *           row = dim bytes (U8_L2), 4*dim bytes (F32_L2), dim/8 bytes (BIN);
+ *           row % 16 == 0 and row <= 2048
+ *   width, height           image-2 size in pixels.  Only a hint for the
+ *                           angular key range; keypoints outside it are
+ *                           still handled exactly.  Must be > 0.
+ * desc1/desc2 may be NULL, in which case only candidate sets are produced
+ * (egm_out.cand_offsets must then be set).
+ */
+typedef struct egm_pair {
+    const double *xy1;
+    const double *xy2;
+    const double *F;
+    const double *eps2;
+    const void *desc1;
+    const void *desc2;
+    int32_t m;
+    int32_t n;
+    double eps_scalar;
+    int32_t kind;
+    int32_t dim;
+    int32_t width;
+    int32_t height;
+} egm_pair;
+
+/*
+ * Outputs.  For a batch, per-query arrays hold the pairs' queries one pair
+ * after another, in pair order (query k of pair p at sum_{q<p} m_q + k), and
+ * reference indices are local to the pair's image 2.
+ *   best, second   [M] int32   index j of the best / second-best candidate, -1 if none
+ *   best_d, second_d [M] float  squared L2 distance (L2 kinds) or Hamming count;
+ *                               +inf where there is no such candidate
+ *   flags          [M] uint8    EGM_FLAG_* bits
+ *   cand_offsets   [M+1] int64  optional (NULL: no candidate lists).  Row k of
+ *                               the candidate CSR is cand_idx[off[k] .. off[k+1]),
+ *                               ascending in j.
+ *   cand_idx       [cand_capacity] int32
+ *   cand_total     [1] int64    device: number of candidate entries written or
+ *                               needed; required when cand_offsets is set
+ * Any of best .. flags may be NULL to skip that output.
+ */
+typedef struct egm_out {
+    int32_t *best;
+    int32_t *second;
+    float *best_d;
+    float *second_d;
+    uint8_t *flags;
+    int64_t *cand_offsets;
+    int32_t *cand_idx;
+    int64_t cand_capacity;
+    int64_t *cand_total;
+} egm_out;
+
+/* Matching forms. */
+enum {
+    EGM_FORM_AUTO = 0,     /* library choice */
+    EGM_FORM_PLAIN = 1,    /* windowed stabbing + CUDA-core descriptor distances */
+    EGM_FORM_BANDED = 2    /* angle-banded tiles, descriptor dot products on tensor cores */
+};
+
+typedef struct egm_params {
+    int32_t ratio_num;     /* ratio test tau = num / den, default 4 / 5 (Sec. 5.1) */
+    int32_t ratio_den;
+    int32_t sync;          /* 1 (default): calls wait and return the device status */
+    int32_t form;          /* EGM_FORM_* */
+    int32_t reserved[12];  /* zero */
+} egm_params;
+
+/* Context lifetime.  `stream` is a cudaStream_t (NULL: the legacy default stream). */
+egm_status egm_create(egm_ctx **ctx, int device, void *stream);
+egm_status egm_destroy(egm_ctx *ctx);
+egm_status egm_set_stream(egm_ctx *ctx, void *stream);
+egm_status egm_set_params(egm_ctx *ctx, const egm_params *params);
+egm_status egm_get_params(egm_ctx *ctx, egm_params *params);
+void egm_default_params(egm_params *params);
+
+/* Grow the context's scratch to hold at least this many queries,
+ * references and pairs per call, so that later calls allocate nothing. */
+egm_status egm_reserve(egm_ctx *ctx, int64_t queries, int64_t refs, int32_t pairs);
+
+/* Match one pair (steps 1-8 above).  Device pointers. */
+egm_status egm_match_pair(egm_ctx *ctx, const egm_pair *pair, const egm_out *out);
+
+/* Match npairs independent pairs in one pass (one launch per step for the
+ * whole batch).  Device pointers; outputs concatenated as described above. */
+egm_status egm_match_batch(egm_ctx *ctx, const egm_pair *pairs, int32_t npairs,
+                           const egm_out *out);
+
+/* As egm_match_pair, but every pointer in *pair and *out is HOST memory
+ * (pinned memory gives the fastest copies).  The call stages the inputs to
+ * the device, matches, copies the outputs back and waits for completion. */
+egm_status egm_match_pair_host(egm_ctx *ctx, const egm_pair *pair, const egm_out *out);
+
+/* Wait for the context's stream and return (then clear) the device status. */
+egm_status egm_sync(egm_ctx *ctx);
+
+/*
+ * The paper's interval view, for inspection and tests (Sec. 4.2, Eq. theta
+ * and delta; Algorithm 1 preprocessing), computed on the device in FP64:
+ *   e3     [3] float64   epipole e2 = null(F^T), unit norm, e_w >= 0
+ *   mode   [1] int32     0: finite epipole (angular), 1: epipole at or near
+ *                        infinity (parallel lines; theta/delta not defined)
+ *   theta  [n] float64   atan2(y_j - y_e, x_j - x_e) reduced to [0, pi)
+ *   delta  [n] float64   asin(eps_j / ||p_j - e2||), or pi/2 when
+ *                        ||p_j - e2|| <= eps_j (full interval)
+ * In parallel mode theta/delta receive NaN.  Device pointers; any may be NULL.
+ */
+egm_status egm_intervals(egm_ctx *ctx, const egm_pair *pair, double *theta, double *delta,
+                         double *e3, int32_t *mode);
+
+/* Work counters of the last match call, for metrics (host memory). */
+typedef struct egm_stats {
+    int64_t queries;        /* queries processed */
+    int64_t refs;           /* reference keypoints processed */
+    int64_t window_refs;    /* references visited inside the stabbing windows */
+    int64_t candidates;     /* candidate pairs found */
+    int64_t fp64_rechecks;  /* pairs decided by the FP64 exact test */
+} egm_stats;
+
+/* Enables (1) or disables (0, default) the work counters, then reads them.
+ * Reading waits for the stream. */
+egm_status egm_set_counters(egm_ctx *ctx, int32_t enable);
+egm_status egm_get_stats(egm_ctx *ctx, egm_stats *stats);
+
+/* Per-stage device time, measured with CUDA events that the library records
+ * on its own stream around each stage of every match call while timing is
+ * enabled.  Times are sums over the calls since the last egm_set_timing(1). */
+typedef struct egm_timing {
+    double geometry_ms;   /* epipole and key frame */
+    double prep_ms;       /* reference keys and query lines */
+    double sort_ms;       /* radix sort by angle */
+    double post_sort_ms;  /* sorted records and bucket tables */
+    double stab_ms;       /* stabbing, exact test, descriptors, top-2, ratio */
+    double csr_ms;        /* candidate lists: count, scan, fill, row sort */
+    int64_t calls;        /* match calls timed */
+} egm_timing;
+
+/* Enables (1, also resets the sums) or disables (0) per-stage timing. */
+egm_status egm_set_timing(egm_ctx *ctx, int32_t enable);
+/* Waits for the stream and returns the sums. */
+egm_status egm_get_timing(egm_ctx *ctx, egm_timing *timing);
+
+const char *egm_status_string(egm_status status);
+int32_t egm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EGM_H */

@@ -1,0 +1,248 @@
+"""Exact epipolar-guided matching on GB300 (sm_103a).
+
+Python face of libegm.so.  PyTorch supplies device memory and streams; every
+step of the matching path runs in the library's CUDA kernels (see
+include/egm.h).  Importing works without a GPU; creating a ``Matcher`` needs
+the built library and a CUDA device and raises otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+from . import _egm
+from ._egm import (EGM_DESC_BIN, EGM_DESC_F32_L2, EGM_DESC_U8_L2, EGM_ERR_CAPACITY,
+                   EGM_FLAG_DEGENERATE_LINE, EGM_FLAG_HAS_BEST, EGM_FLAG_NO_SECOND,
+                   EGM_FLAG_RATIO_PASS, EGM_OK, EgmError, check, load)
+
+__all__ = ["Matcher", "EgmError", "load", "row_bytes", "EGM_DESC_U8_L2", "EGM_DESC_F32_L2",
+           "EGM_DESC_BIN", "EGM_FLAG_HAS_BEST", "EGM_FLAG_RATIO_PASS", "EGM_FLAG_NO_SECOND",
+           "EGM_FLAG_DEGENERATE_LINE"]
+
+
+def row_bytes(kind: int, dim: int) -> int:
+    return dim if kind == EGM_DESC_U8_L2 else 4 * dim if kind == EGM_DESC_F32_L2 else dim // 8
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Matcher:
+    """One libegm context bound to a CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None, ratio=(4, 5)):
+        import torch
+
+        self.torch = torch
+        self.lib = load()
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        ctx = C.c_void_p()
+        check(self.lib.egm_create(C.byref(ctx), device, C.c_void_p(stream.cuda_stream)), "egm_create")
+        self.ctx = ctx
+        p = _egm.egm_params()
+        self.lib.egm_default_params(C.byref(p))
+        p.ratio_num, p.ratio_den = int(ratio[0]), int(ratio[1])
+        check(self.lib.egm_set_params(self.ctx, C.byref(p)), "egm_set_params")
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            self.lib.egm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------- params
+    def set_params(self, ratio=None, sync=None, form=None):
+        p = _egm.egm_params()
+        check(self.lib.egm_get_params(self.ctx, C.byref(p)), "egm_get_params")
+        if ratio is not None:
+            p.ratio_num, p.ratio_den = int(ratio[0]), int(ratio[1])
+        if sync is not None:
+            p.sync = int(bool(sync))
+        if form is not None:
+            p.form = int(form)
+        check(self.lib.egm_set_params(self.ctx, C.byref(p)), "egm_set_params")
+
+    def reserve(self, queries: int, refs: int, pairs: int = 1):
+        check(self.lib.egm_reserve(self.ctx, int(queries), int(refs), int(pairs)), "egm_reserve")
+
+    def sync(self) -> int:
+        return self.lib.egm_sync(self.ctx)
+
+    def set_counters(self, on: bool):
+        check(self.lib.egm_set_counters(self.ctx, int(bool(on))), "egm_set_counters")
+
+    def set_timing(self, on: bool):
+        check(self.lib.egm_set_timing(self.ctx, int(bool(on))), "egm_set_timing")
+
+    def timing(self) -> dict:
+        t = _egm.egm_timing()
+        check(self.lib.egm_get_timing(self.ctx, C.byref(t)), "egm_get_timing")
+        return {k: (int(getattr(t, k)) if k == "calls" else float(getattr(t, k))) for k, _ in t._fields_}
+
+    def stats(self) -> dict:
+        s = _egm.egm_stats()
+        check(self.lib.egm_get_stats(self.ctx, C.byref(s)), "egm_get_stats")
+        return {k: int(getattr(s, k)) for k, _ in s._fields_}
+
+    # ------------------------------------------------------------ helpers
+    def to_device(self, scene):
+        """Device tensors for a synth.Scene-like object (xy1, xy2, F, eps, desc1, desc2, ...)."""
+        torch = self.torch
+        dev = self.device
+        d = dict(xy1=torch.as_tensor(scene.xy1, dtype=torch.float64).to(dev).contiguous(),
+                 xy2=torch.as_tensor(scene.xy2, dtype=torch.float64).to(dev).contiguous(),
+                 F=torch.as_tensor(scene.F, dtype=torch.float64).reshape(9).to(dev).contiguous(),
+                 kind=int(scene.kind), dim=int(scene.dim), width=int(scene.width),
+                 height=int(scene.height))
+        import numpy as np
+        if np.ndim(scene.eps) == 0:
+            d["eps"] = float(scene.eps)
+        else:
+            d["eps"] = torch.as_tensor(scene.eps, dtype=torch.float64).to(dev).contiguous()
+        for k in ("desc1", "desc2"):
+            v = getattr(scene, k)
+            d[k] = None if v is None else torch.as_tensor(v).to(dev).contiguous()
+        return d
+
+    def make_pair(self, xy1, xy2, F, eps, desc1=None, desc2=None, kind=EGM_DESC_U8_L2, dim=128,
+                  width=640, height=480) -> _egm.egm_pair:
+        p = _egm.egm_pair()
+        p.xy1, p.xy2, p.F = _ptr(xy1), _ptr(xy2), _ptr(F)
+        if isinstance(eps, (int, float)):
+            p.eps2, p.eps_scalar = None, float(eps)
+        else:
+            p.eps2, p.eps_scalar = _ptr(eps), 0.0
+        p.desc1, p.desc2 = _ptr(desc1), _ptr(desc2)
+        p.m, p.n = int(xy1.shape[0]), int(xy2.shape[0])
+        p.kind, p.dim, p.width, p.height = int(kind), int(dim), int(width), int(height)
+        self._keep = [xy1, xy2, F, eps, desc1, desc2]
+        return p
+
+    def _alloc_out(self, M, csr, cap):
+        torch = self.torch
+        dev = self.device
+        o = dict(best=torch.empty(M, dtype=torch.int32, device=dev),
+                 second=torch.empty(M, dtype=torch.int32, device=dev),
+                 best_d=torch.empty(M, dtype=torch.float32, device=dev),
+                 second_d=torch.empty(M, dtype=torch.float32, device=dev),
+                 flags=torch.empty(M, dtype=torch.uint8, device=dev))
+        if csr:
+            o["cand_offsets"] = torch.empty(M + 1, dtype=torch.int64, device=dev)
+            o["cand_idx"] = torch.empty(max(int(cap), 1), dtype=torch.int32, device=dev)
+            o["cand_total"] = torch.zeros(1, dtype=torch.int64, device=dev)
+        return o
+
+    @staticmethod
+    def _out_struct(o, cap):
+        s = _egm.egm_out()
+        s.best, s.second = _ptr(o["best"]), _ptr(o["second"])
+        s.best_d, s.second_d, s.flags = _ptr(o["best_d"]), _ptr(o["second_d"]), _ptr(o["flags"])
+        if "cand_offsets" in o:
+            s.cand_offsets, s.cand_idx = _ptr(o["cand_offsets"]), _ptr(o["cand_idx"])
+            s.cand_total, s.cand_capacity = _ptr(o["cand_total"]), int(cap)
+        return s
+
+    # -------------------------------------------------------------- calls
+    def egm_match_pair(self, pair: _egm.egm_pair, out: _egm.egm_out) -> int:
+        return self.lib.egm_match_pair(self.ctx, C.byref(pair), C.byref(out))
+
+    def egm_match_batch(self, pairs, out: _egm.egm_out) -> int:
+        arr = (_egm.egm_pair * len(pairs))(*pairs)
+        return self.lib.egm_match_batch(self.ctx, arr, len(pairs), C.byref(out))
+
+    def egm_match_pair_host(self, pair: _egm.egm_pair, out: _egm.egm_out) -> int:
+        return self.lib.egm_match_pair_host(self.ctx, C.byref(pair), C.byref(out))
+
+    def match(self, xy1, xy2, F, eps, desc1=None, desc2=None, kind=EGM_DESC_U8_L2, dim=128,
+              width=640, height=480, csr=False, cand_capacity=None, out=None):
+        """Match one pair of device tensors; returns a dict of device tensors."""
+        pair = self.make_pair(xy1, xy2, F, eps, desc1, desc2, kind, dim, width, height)
+        return self._run([pair], csr, cand_capacity, out, batch=False)
+
+    def match_batch(self, items, csr=False, cand_capacity=None, out=None):
+        """items: list of dicts as produced by to_device(); outputs concatenated in pair order."""
+        pairs, keep = [], []
+        for it in items:
+            pairs.append(self.make_pair(it["xy1"], it["xy2"], it["F"], it["eps"], it.get("desc1"),
+                                        it.get("desc2"), it["kind"], it["dim"], it["width"],
+                                        it["height"]))
+            keep.append(self._keep)
+        self._keep = keep
+        return self._run(pairs, csr, cand_capacity, out, batch=True)
+
+    def _run(self, pairs, csr, cap, out, batch):
+        M = sum(int(p.m) for p in pairs)
+        if csr and cap is None:
+            cap = 64 * max(M, 1)
+        o = out if out is not None else self._alloc_out(M, csr, cap or 0)
+        s = self._out_struct(o, cap or 0)
+        st = self.egm_match_batch(pairs, s) if batch else self.egm_match_pair(pairs[0], s)
+        if st == EGM_ERR_CAPACITY and csr and out is None:
+            need = int(o["cand_total"].item())
+            return self._run(pairs, csr, need, None, batch)
+        check(st, "egm_match_batch" if batch else "egm_match_pair")
+        if csr:
+            o["cand_idx"] = o["cand_idx"][: int(o["cand_offsets"][-1].item())]
+        return o
+
+    def match_host(self, scene, csr=False, cand_capacity=None):
+        """egm_match_pair_host on host (numpy) arrays; returns numpy outputs."""
+        import numpy as np
+
+        xy1 = np.ascontiguousarray(scene.xy1, np.float64)
+        xy2 = np.ascontiguousarray(scene.xy2, np.float64)
+        F = np.ascontiguousarray(scene.F, np.float64).reshape(9)
+        d1 = np.ascontiguousarray(scene.desc1)
+        d2 = np.ascontiguousarray(scene.desc2)
+        p = _egm.egm_pair()
+        hp = lambda a: a.ctypes.data_as(C.c_void_p)
+        p.xy1, p.xy2, p.F = hp(xy1), hp(xy2), hp(F)
+        if np.ndim(scene.eps) == 0:
+            p.eps2, p.eps_scalar = None, float(scene.eps)
+            eps = None
+        else:
+            eps = np.ascontiguousarray(scene.eps, np.float64)
+            p.eps2, p.eps_scalar = hp(eps), 0.0
+        p.desc1, p.desc2 = hp(d1), hp(d2)
+        p.m, p.n = xy1.shape[0], xy2.shape[0]
+        p.kind, p.dim, p.width, p.height = scene.kind, scene.dim, scene.width, scene.height
+        m = p.m
+        o = dict(best=np.empty(m, np.int32), second=np.empty(m, np.int32),
+                 best_d=np.empty(m, np.float32), second_d=np.empty(m, np.float32),
+                 flags=np.empty(m, np.uint8))
+        s = _egm.egm_out()
+        s.best, s.second, s.best_d = hp(o["best"]), hp(o["second"]), hp(o["best_d"])
+        s.second_d, s.flags = hp(o["second_d"]), hp(o["flags"])
+        if csr:
+            cap = cand_capacity or 64 * max(m, 1)
+            o["cand_offsets"] = np.empty(m + 1, np.int64)
+            o["cand_idx"] = np.empty(cap, np.int32)
+            o["cand_total"] = np.zeros(1, np.int64)
+            s.cand_offsets, s.cand_idx, s.cand_total = (hp(o["cand_offsets"]), hp(o["cand_idx"]),
+                                                        hp(o["cand_total"]))
+            s.cand_capacity = cap
+        check(self.egm_match_pair_host(p, s), "egm_match_pair_host")
+        return o
+
+    def intervals(self, xy2, F, eps, width, height):
+        """egm_intervals: (theta, delta, e3, mode) as device tensors."""
+        torch = self.torch
+        n = int(xy2.shape[0])
+        xy1 = torch.zeros((0, 2), dtype=torch.float64, device=self.device)
+        pair = self.make_pair(xy1, xy2, F, eps, None, None, EGM_DESC_U8_L2, 128, width, height)
+        th = torch.empty(max(n, 1), dtype=torch.float64, device=self.device)
+        de = torch.empty_like(th)
+        e3 = torch.empty(3, dtype=torch.float64, device=self.device)
+        mode = torch.empty(1, dtype=torch.int32, device=self.device)
+        st = self.lib.egm_intervals(self.ctx, C.byref(pair), _ptr(th), _ptr(de), _ptr(e3), _ptr(mode))
+        check(st, "egm_intervals")
+        return th[:n], de[:n], e3, int(mode.item())

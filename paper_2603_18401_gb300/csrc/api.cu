@@ -1,0 +1,603 @@
+// C ABI of libegm: context, scratch memory, argument checks and the launch
+// sequence of the matching pipeline (declarations and conventions in egm.h).
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "egm_internal.cuh"
+
+using namespace egm;
+
+namespace {
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+cudaError_t grow(DevBuf &b, size_t need) {
+    if (need <= b.bytes) return cudaSuccess;
+    if (b.ptr) {
+        cudaError_t e = cudaFree(b.ptr);
+        if (e != cudaSuccess) return e;
+        b.ptr = nullptr;
+        b.bytes = 0;
+    }
+    size_t alloc = need + need / 4 + 4096;
+    cudaError_t e = cudaMalloc(&b.ptr, alloc);
+    if (e != cudaSuccess) return e;
+    b.bytes = alloc;
+    return cudaSuccess;
+}
+
+template <typename T>
+T *as(DevBuf &b) { return reinterpret_cast<T *>(b.ptr); }
+
+}  // namespace
+
+struct egm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    egm_params params;
+    bool counters_on = false;
+    egm_stats last{};
+    // scratch
+    DevBuf pairs, geom, offs, keys, rec, tab, qrec, qcount, scan, longlist, small, counters;
+    DevBuf stage;  // host-path staging of inputs and outputs
+    // pinned host memory for the pair table and the status word
+    void *h_table = nullptr;
+    size_t h_table_bytes = 0;
+    uint32_t *h_status = nullptr;
+    unsigned long long *h_counters = nullptr;
+    cudaEvent_t table_ev = nullptr;
+    bool table_ev_pending = false;
+    // per-stage timing: kStages + 1 events per timed call
+    bool timing_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<size_t> ev_calls;   // first event of each timed call
+    egm_timing tsum{};
+};
+
+namespace {
+constexpr int kStages = 6;  // geometry, prep, sort, post_sort, stab, csr
+}
+
+namespace {
+
+egm_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return EGM_OK;
+    if (e == cudaErrorMemoryAllocation) return EGM_ERR_NOMEM;
+    return EGM_ERR_CUDA;
+}
+
+egm_status from_bits(uint32_t st) {
+    if (st & kStNan) return EGM_ERR_NAN;
+    if (st & kStDegenerateF) return EGM_ERR_DEGENERATE_F;
+    if (st & kStArg) return EGM_ERR_ARG;
+    if (st & kStCapacity) return EGM_ERR_CAPACITY;
+    if (st & kStTimeout) return EGM_ERR_TIMEOUT;
+    return EGM_OK;
+}
+
+#define EGM_TRY(x)                                   \
+    do {                                             \
+        cudaError_t e_ = (x);                        \
+        if (e_ != cudaSuccess) return from_cuda(e_); \
+    } while (0)
+
+int row_bytes_of(int kind, int dim) {
+    switch (kind) {
+        case EGM_DESC_U8_L2: return dim;
+        case EGM_DESC_F32_L2: return 4 * dim;
+        case EGM_DESC_BIN: return dim / 8;
+        default: return -1;
+    }
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Descriptors are requested when either array is given.
+bool has_desc(const egm_pair *P) { return P->desc1 != nullptr || P->desc2 != nullptr; }
+
+egm_status check_pair(const egm_pair *P) {
+    if (!P) return EGM_ERR_ARG;
+    if (P->m < 0 || P->n < 0) return EGM_ERR_ARG;
+    if (P->m > 0 && !P->xy1) return EGM_ERR_ARG;
+    if (P->n > 0 && !P->xy2) return EGM_ERR_ARG;
+    if (!P->F) return EGM_ERR_ARG;
+    if (P->width <= 0 || P->height <= 0) return EGM_ERR_ARG;
+    if (!P->eps2) {
+        if (P->eps_scalar != P->eps_scalar || P->eps_scalar == INFINITY) return EGM_ERR_NAN;
+        if (!(P->eps_scalar > 0.0)) return EGM_ERR_ARG;
+    }
+    if (has_desc(P)) {
+        // a descriptor array may be NULL only when it has no rows
+        if ((!P->desc1 && P->m > 0) || (!P->desc2 && P->n > 0)) return EGM_ERR_ARG;
+        if (P->kind == EGM_DESC_BIN && (P->dim <= 0 || P->dim % 128 != 0)) return EGM_ERR_ARG;
+        const int rb = row_bytes_of(P->kind, P->dim);
+        if (rb <= 0 || rb % 16 != 0 || rb > 2048) return EGM_ERR_ARG;
+        if (!aligned16(P->desc1) || !aligned16(P->desc2)) return EGM_ERR_ARG;
+    }
+    return EGM_OK;
+}
+
+struct Plan {
+    std::vector<PairDesc> pd;
+    std::vector<int64_t> qoffs, roffs;
+    int64_t nq = 0, nr = 0, ntab = 0;
+    int max_n = 0;
+};
+
+egm_status make_plan(const egm_pair *pairs, int npairs, Plan &pl) {
+    pl.pd.resize(npairs);
+    pl.qoffs.resize(npairs + 1);
+    pl.roffs.resize(npairs + 1);
+    for (int p = 0; p < npairs; p++) {
+        egm_status s = check_pair(pairs + p);
+        if (s != EGM_OK) return s;
+        const egm_pair &A = pairs[p];
+        PairDesc &D = pl.pd[p];
+        memset(&D, 0, sizeof(D));
+        D.xy1 = A.xy1;
+        D.xy2 = A.xy2;
+        D.F = A.F;
+        D.eps2 = A.eps2;
+        D.desc1 = static_cast<const uint8_t *>(A.desc1);
+        D.desc2 = static_cast<const uint8_t *>(A.desc2);
+        D.eps_scalar = A.eps_scalar;
+        D.m = A.m;
+        D.n = A.n;
+        D.kind = has_desc(&A) ? A.kind : EGM_DESC_U8_L2;
+        D.dim = A.dim;
+        D.row_bytes = has_desc(&A) ? row_bytes_of(A.kind, A.dim) : 0;
+        D.width = A.width;
+        D.height = A.height;
+        D.q_off = pl.nq;
+        D.r_off = pl.nr;
+        D.t_off = pl.ntab;
+        D.t_cap = 4 * (int64_t)A.n + 2 * kLevels + 32;
+        pl.qoffs[p] = pl.nq;
+        pl.roffs[p] = pl.nr;
+        pl.nq += A.m;
+        pl.nr += A.n;
+        pl.ntab += D.t_cap;
+        pl.max_n = std::max(pl.max_n, A.n);
+    }
+    pl.qoffs[npairs] = pl.nq;
+    pl.roffs[npairs] = pl.nr;
+    return EGM_OK;
+}
+
+cudaError_t reserve(egm_ctx *c, int64_t nq, int64_t nr, int64_t ntab, int npairs) {
+    cudaError_t e;
+    if ((e = grow(c->pairs, sizeof(PairDesc) * (size_t)std::max(npairs, 1))) != cudaSuccess) return e;
+    if ((e = grow(c->geom, sizeof(PairGeom) * (size_t)std::max(npairs, 1))) != cudaSuccess) return e;
+    if ((e = grow(c->offs, sizeof(int64_t) * 2 * (size_t)(npairs + 1))) != cudaSuccess) return e;
+    if ((e = grow(c->keys, sizeof(uint32_t) * 6 * (size_t)std::max<int64_t>(nr, 1))) != cudaSuccess) return e;
+    if ((e = grow(c->rec, sizeof(float4) * (size_t)std::max<int64_t>(nr, 1))) != cudaSuccess) return e;
+    if ((e = grow(c->tab, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntab, 1))) != cudaSuccess) return e;
+    if ((e = grow(c->qrec, sizeof(QueryRec) * (size_t)std::max<int64_t>(nq, 1))) != cudaSuccess) return e;
+    if ((e = grow(c->qcount, sizeof(int64_t) * (size_t)(nq + 1))) != cudaSuccess) return e;
+    if ((e = grow(c->scan, sizeof(int64_t) * (size_t)(nq / 8192 + 2))) != cudaSuccess) return e;
+    if ((e = grow(c->longlist, sizeof(uint32_t) * (size_t)(nq + 1))) != cudaSuccess) return e;
+    if ((e = grow(c->small, 256)) != cudaSuccess) return e;
+    if ((e = grow(c->counters, 8 * sizeof(unsigned long long))) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+Launch make_launch(egm_ctx *c, const Plan &pl, int npairs, const egm_out *out) {
+    Launch L;
+    memset(&L, 0, sizeof(L));
+    L.pairs = as<PairDesc>(c->pairs);
+    L.geom = as<PairGeom>(c->geom);
+    L.npairs = npairs;
+    L.nq = pl.nq;
+    L.nr = pl.nr;
+    L.q_offs = as<int64_t>(c->offs);
+    L.r_offs = as<int64_t>(c->offs) + (npairs + 1);
+    uint32_t *k = as<uint32_t>(c->keys);
+    const size_t nr = (size_t)std::max<int64_t>(pl.nr, 1);
+    L.key_a = k;
+    L.val_a = k + nr;
+    L.key_b = k + 2 * nr;
+    L.val_b = k + 3 * nr;
+    L.key_c = k + 4 * nr;
+    L.val_c = k + 5 * nr;
+    L.rec = as<float4>(c->rec);
+    L.tab = as<uint32_t>(c->tab);
+    L.qrec = as<QueryRec>(c->qrec);
+    L.status = as<uint32_t>(c->small);
+    L.counters = c->counters_on ? as<unsigned long long>(c->counters) : nullptr;
+    L.qcount = as<int64_t>(c->qcount);
+    L.scan_tmp = as<int64_t>(c->scan);
+    L.ratio_num = c->params.ratio_num;
+    L.ratio_den = c->params.ratio_den;
+    if (out) {
+        L.best = out->best;
+        L.second = out->second;
+        L.best_d = out->best_d;
+        L.second_d = out->second_d;
+        L.flags = out->flags;
+        L.cand_offsets = out->cand_offsets;
+        L.cand_idx = out->cand_idx;
+        L.cand_capacity = out->cand_capacity;
+        L.cand_total = out->cand_total;
+    }
+    return L;
+}
+
+// Upload the pair table and offsets through pinned memory.  The staging area
+// is reused only after the previous upload has been consumed.
+cudaError_t upload_plan(egm_ctx *c, const Plan &pl, int npairs) {
+    const size_t tb = sizeof(PairDesc) * npairs, ob = sizeof(int64_t) * 2 * (npairs + 1);
+    if (c->table_ev_pending) {
+        cudaError_t e = cudaEventSynchronize(c->table_ev);
+        if (e != cudaSuccess) return e;
+        c->table_ev_pending = false;
+    }
+    if (tb + ob > c->h_table_bytes) {
+        if (c->h_table) cudaFreeHost(c->h_table);
+        c->h_table = nullptr;
+        size_t want = (tb + ob) * 2 + 4096;
+        cudaError_t e = cudaMallocHost(&c->h_table, want);
+        if (e != cudaSuccess) { c->h_table_bytes = 0; return e; }
+        c->h_table_bytes = want;
+    }
+    unsigned char *h = static_cast<unsigned char *>(c->h_table);
+    memcpy(h, pl.pd.data(), tb);
+    memcpy(h + tb, pl.qoffs.data(), sizeof(int64_t) * (npairs + 1));
+    memcpy(h + tb + sizeof(int64_t) * (npairs + 1), pl.roffs.data(), sizeof(int64_t) * (npairs + 1));
+    cudaError_t e = cudaMemcpyAsync(c->pairs.ptr, h, tb, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(c->offs.ptr, h + tb, ob, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(c->table_ev, c->stream);
+    if (e != cudaSuccess) return e;
+    c->table_ev_pending = true;
+    return cudaSuccess;
+}
+
+// Records the boundary event before stage `k` (k == kStages: end of call).
+cudaError_t mark(egm_ctx *c, size_t base, int k) {
+    if (!c->timing_on) return cudaSuccess;
+    const size_t idx = base + (size_t)k;
+    while (c->ev_pool.size() <= idx) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        c->ev_pool.push_back(e);
+    }
+    return cudaEventRecord(c->ev_pool[idx], c->stream);
+}
+
+egm_status finish(egm_ctx *c, bool sync) {
+    if (!sync) return EGM_OK;
+    return egm_sync(c);
+}
+
+egm_status run_batch(egm_ctx *c, const egm_pair *pairs, int npairs, const egm_out *out, bool sync) {
+    if (!c || npairs < 0 || (npairs > 0 && !pairs) || !out) return EGM_ERR_ARG;
+    if (npairs == 0) return EGM_OK;
+    Plan pl;
+    egm_status s = make_plan(pairs, npairs, pl);
+    if (s != EGM_OK) return s;
+    const bool csr = out->cand_offsets != nullptr;
+    if (csr && (!out->cand_total || out->cand_capacity < 0 || (out->cand_capacity > 0 && !out->cand_idx)))
+        return EGM_ERR_ARG;
+    bool any_desc = false;
+    for (int p = 0; p < npairs; p++) any_desc |= has_desc(pairs + p);
+    if (!csr && !any_desc) return EGM_ERR_ARG;  // nothing to compute
+    EGM_TRY(cudaSetDevice(c->device));
+    EGM_TRY(reserve(c, pl.nq, pl.nr, pl.ntab, npairs));
+    EGM_TRY(upload_plan(c, pl, npairs));
+    Launch L = make_launch(c, pl, npairs, out);
+    cudaStream_t st = c->stream;
+    if (sync) EGM_TRY(cudaMemsetAsync(L.status, 0, sizeof(uint32_t), st));
+    if (c->counters_on) EGM_TRY(cudaMemsetAsync(c->counters.ptr, 0, 8 * sizeof(unsigned long long), st));
+    const size_t tb = c->ev_used;
+    if (c->timing_on) {
+        c->ev_calls.push_back(tb);
+        c->ev_used += kStages + 1;
+    }
+    EGM_TRY(mark(c, tb, 0));
+    EGM_TRY(launch_geometry(L, st));
+    EGM_TRY(mark(c, tb, 1));
+    EGM_TRY(launch_prep(L, st));
+    EGM_TRY(mark(c, tb, 2));
+    EGM_TRY(launch_sort(L, pl.max_n, st));
+    EGM_TRY(mark(c, tb, 3));
+    EGM_TRY(launch_post_sort(L, st));
+    EGM_TRY(mark(c, tb, 4));
+    if (csr) {
+        uint32_t *long_list = as<uint32_t>(c->longlist);
+        uint32_t *long_count = as<uint32_t>(c->small) + 16;
+        EGM_TRY(launch_stab(L, 1, st));
+        EGM_TRY(mark(c, tb, 5));
+        EGM_TRY(launch_csr_offsets(L, long_count, st));
+        EGM_TRY(launch_stab(L, 2, st));
+        EGM_TRY(launch_csr_row_sort(L, long_list, long_count, st));
+    } else {
+        EGM_TRY(launch_stab(L, 0, st));
+        EGM_TRY(mark(c, tb, 5));
+    }
+    EGM_TRY(mark(c, tb, 6));
+    c->last.queries = pl.nq;
+    c->last.refs = pl.nr;
+    return finish(c, sync);
+}
+
+}  // namespace
+
+extern "C" {
+
+void egm_default_params(egm_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->ratio_num = 4;
+    p->ratio_den = 5;
+    p->sync = 1;
+    p->form = EGM_FORM_AUTO;
+}
+
+egm_status egm_create(egm_ctx **out, int device, void *stream) {
+    if (!out) return EGM_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return EGM_ERR_CUDA;
+    egm_ctx *c = new (std::nothrow) egm_ctx();
+    if (!c) return EGM_ERR_NOMEM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(stream);
+    egm_default_params(&c->params);
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_status, 64);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_counters, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->table_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = grow(c->small, 256);
+    if (e == cudaSuccess) e = cudaMemset(c->small.ptr, 0, 256);
+    if (e != cudaSuccess) {
+        egm_destroy(c);
+        return from_cuda(e);
+    }
+    *out = c;
+    return EGM_OK;
+}
+
+egm_status egm_destroy(egm_ctx *c) {
+    if (!c) return EGM_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    DevBuf *bufs[] = {&c->pairs, &c->geom, &c->offs, &c->keys, &c->rec, &c->tab, &c->qrec, &c->qcount,
+                      &c->scan, &c->longlist, &c->small, &c->counters, &c->stage};
+    for (DevBuf *b : bufs)
+        if (b->ptr) cudaFree(b->ptr);
+    if (c->h_table) cudaFreeHost(c->h_table);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->h_counters) cudaFreeHost(c->h_counters);
+    if (c->table_ev) cudaEventDestroy(c->table_ev);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+    return EGM_OK;
+}
+
+egm_status egm_set_stream(egm_ctx *c, void *stream) {
+    if (!c) return EGM_ERR_ARG;
+    c->stream = static_cast<cudaStream_t>(stream);
+    return EGM_OK;
+}
+
+egm_status egm_set_params(egm_ctx *c, const egm_params *p) {
+    if (!c || !p) return EGM_ERR_ARG;
+    if (p->ratio_num <= 0 || p->ratio_den <= 0 || p->ratio_num > 1000000 || p->ratio_den > 1000000)
+        return EGM_ERR_ARG;
+    if (p->form < EGM_FORM_AUTO || p->form > EGM_FORM_BANDED) return EGM_ERR_ARG;
+    c->params = *p;
+    return EGM_OK;
+}
+
+egm_status egm_get_params(egm_ctx *c, egm_params *p) {
+    if (!c || !p) return EGM_ERR_ARG;
+    *p = c->params;
+    return EGM_OK;
+}
+
+egm_status egm_reserve(egm_ctx *c, int64_t queries, int64_t refs, int32_t pairs) {
+    if (!c || queries < 0 || refs < 0 || pairs < 0) return EGM_ERR_ARG;
+    EGM_TRY(cudaSetDevice(c->device));
+    const int64_t ntab = 4 * refs + (int64_t)std::max(pairs, 1) * (2 * kLevels + 32);
+    EGM_TRY(reserve(c, queries, refs, ntab, std::max(pairs, 1)));
+    return EGM_OK;
+}
+
+egm_status egm_sync(egm_ctx *c) {
+    if (!c) return EGM_ERR_ARG;
+    EGM_TRY(cudaSetDevice(c->device));
+    EGM_TRY(cudaMemcpyAsync(c->h_status, c->small.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    if (c->counters_on)
+        EGM_TRY(cudaMemcpyAsync(c->h_counters, c->counters.ptr, 8 * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, c->stream));
+    EGM_TRY(cudaStreamSynchronize(c->stream));
+    const uint32_t st = *c->h_status;
+    if (st) EGM_TRY(cudaMemsetAsync(c->small.ptr, 0, sizeof(uint32_t), c->stream));
+    if (c->counters_on) {
+        c->last.window_refs = (int64_t)c->h_counters[2];
+        c->last.candidates = (int64_t)c->h_counters[3];
+        c->last.fp64_rechecks = (int64_t)c->h_counters[4];
+    }
+    return from_bits(st);
+}
+
+egm_status egm_match_batch(egm_ctx *c, const egm_pair *pairs, int32_t npairs, const egm_out *out) {
+    if (!c) return EGM_ERR_ARG;
+    return run_batch(c, pairs, npairs, out, c->params.sync != 0);
+}
+
+egm_status egm_match_pair(egm_ctx *c, const egm_pair *pair, const egm_out *out) {
+    if (!c) return EGM_ERR_ARG;
+    return run_batch(c, pair, 1, out, c->params.sync != 0);
+}
+
+egm_status egm_match_pair_host(egm_ctx *c, const egm_pair *hp, const egm_out *ho) {
+    if (!c || !hp || !ho) return EGM_ERR_ARG;
+    egm_status s = check_pair(hp);
+    if (s != EGM_OK) return s;
+    const int64_t m = hp->m, n = hp->n;
+    const int rb = has_desc(hp) ? row_bytes_of(hp->kind, hp->dim) : 0;
+    const bool csr = ho->cand_offsets != nullptr;
+    if (csr && (!ho->cand_total || ho->cand_capacity < 0 || (ho->cand_capacity > 0 && !ho->cand_idx)))
+        return EGM_ERR_ARG;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t off = 0;
+    const size_t o_xy1 = off; off += al(16 * m);
+    const size_t o_xy2 = off; off += al(16 * n);
+    const size_t o_F = off; off += al(72);
+    const size_t o_eps = off; off += al(hp->eps2 ? 8 * n : 0);
+    const size_t o_d1 = off; off += al((size_t)rb * m);
+    const size_t o_d2 = off; off += al((size_t)rb * n);
+    const size_t o_best = off; off += al(4 * m);
+    const size_t o_second = off; off += al(4 * m);
+    const size_t o_bd = off; off += al(4 * m);
+    const size_t o_sd = off; off += al(4 * m);
+    const size_t o_fl = off; off += al(m);
+    const size_t o_co = off; off += al(csr ? 8 * (m + 1) : 0);
+    const size_t o_ct = off; off += al(csr ? 8 : 0);
+    const size_t o_ci = off; off += al(csr ? 4 * (size_t)ho->cand_capacity : 0);
+    EGM_TRY(cudaSetDevice(c->device));
+    EGM_TRY(grow(c->stage, off));
+    unsigned char *d = static_cast<unsigned char *>(c->stage.ptr);
+    cudaStream_t st = c->stream;
+    const cudaMemcpyKind H2D = cudaMemcpyHostToDevice, D2H = cudaMemcpyDeviceToHost;
+    if (m) EGM_TRY(cudaMemcpyAsync(d + o_xy1, hp->xy1, 16 * m, H2D, st));
+    if (n) EGM_TRY(cudaMemcpyAsync(d + o_xy2, hp->xy2, 16 * n, H2D, st));
+    EGM_TRY(cudaMemcpyAsync(d + o_F, hp->F, 72, H2D, st));
+    if (hp->eps2 && n) EGM_TRY(cudaMemcpyAsync(d + o_eps, hp->eps2, 8 * n, H2D, st));
+    if (rb && m) EGM_TRY(cudaMemcpyAsync(d + o_d1, hp->desc1, (size_t)rb * m, H2D, st));
+    if (rb && n) EGM_TRY(cudaMemcpyAsync(d + o_d2, hp->desc2, (size_t)rb * n, H2D, st));
+    egm_pair dp = *hp;
+    dp.xy1 = reinterpret_cast<const double *>(d + o_xy1);
+    dp.xy2 = reinterpret_cast<const double *>(d + o_xy2);
+    dp.F = reinterpret_cast<const double *>(d + o_F);
+    dp.eps2 = hp->eps2 ? reinterpret_cast<const double *>(d + o_eps) : nullptr;
+    dp.desc1 = rb ? d + o_d1 : nullptr;
+    dp.desc2 = rb ? d + o_d2 : nullptr;
+    egm_out dout;
+    memset(&dout, 0, sizeof(dout));
+    dout.best = ho->best ? reinterpret_cast<int32_t *>(d + o_best) : nullptr;
+    dout.second = ho->second ? reinterpret_cast<int32_t *>(d + o_second) : nullptr;
+    dout.best_d = ho->best_d ? reinterpret_cast<float *>(d + o_bd) : nullptr;
+    dout.second_d = ho->second_d ? reinterpret_cast<float *>(d + o_sd) : nullptr;
+    dout.flags = ho->flags ? d + o_fl : nullptr;
+    if (csr) {
+        dout.cand_offsets = reinterpret_cast<int64_t *>(d + o_co);
+        dout.cand_total = reinterpret_cast<int64_t *>(d + o_ct);
+        dout.cand_idx = reinterpret_cast<int32_t *>(d + o_ci);
+        dout.cand_capacity = ho->cand_capacity;
+    }
+    EGM_TRY(cudaMemsetAsync(c->small.ptr, 0, sizeof(uint32_t), st));
+    s = run_batch(c, &dp, 1, &dout, false);
+    if (s != EGM_OK) return s;
+    if (ho->best) EGM_TRY(cudaMemcpyAsync(ho->best, dout.best, 4 * m, D2H, st));
+    if (ho->second) EGM_TRY(cudaMemcpyAsync(ho->second, dout.second, 4 * m, D2H, st));
+    if (ho->best_d) EGM_TRY(cudaMemcpyAsync(ho->best_d, dout.best_d, 4 * m, D2H, st));
+    if (ho->second_d) EGM_TRY(cudaMemcpyAsync(ho->second_d, dout.second_d, 4 * m, D2H, st));
+    if (ho->flags) EGM_TRY(cudaMemcpyAsync(ho->flags, dout.flags, m, D2H, st));
+    if (csr) {
+        EGM_TRY(cudaMemcpyAsync(ho->cand_offsets, dout.cand_offsets, 8 * (m + 1), D2H, st));
+        EGM_TRY(cudaMemcpyAsync(ho->cand_total, dout.cand_total, 8, D2H, st));
+    }
+    s = egm_sync(c);
+    if (s != EGM_OK) return s;
+    if (csr) {
+        const int64_t tot = *ho->cand_total;
+        if (tot > 0 && tot <= ho->cand_capacity) {
+            EGM_TRY(cudaMemcpyAsync(ho->cand_idx, dout.cand_idx, 4 * (size_t)tot, D2H, st));
+            EGM_TRY(cudaStreamSynchronize(st));
+        }
+    }
+    return EGM_OK;
+}
+
+egm_status egm_intervals(egm_ctx *c, const egm_pair *pair, double *theta, double *delta, double *e3,
+                         int32_t *mode) {
+    if (!c || !pair) return EGM_ERR_ARG;
+    egm_pair p = *pair;
+    p.desc1 = p.desc2 = nullptr;
+    Plan pl;
+    egm_status s = make_plan(&p, 1, pl);
+    if (s != EGM_OK) return s;
+    EGM_TRY(cudaSetDevice(c->device));
+    EGM_TRY(reserve(c, pl.nq, pl.nr, pl.ntab, 1));
+    EGM_TRY(upload_plan(c, pl, 1));
+    Launch L = make_launch(c, pl, 1, nullptr);
+    if (c->params.sync) EGM_TRY(cudaMemsetAsync(L.status, 0, sizeof(uint32_t), c->stream));
+    EGM_TRY(launch_geometry(L, c->stream));
+    EGM_TRY(launch_intervals(L, theta, delta, e3, mode, c->stream));
+    return finish(c, c->params.sync != 0);
+}
+
+egm_status egm_set_timing(egm_ctx *c, int32_t enable) {
+    if (!c) return EGM_ERR_ARG;
+    c->timing_on = enable != 0;
+    c->ev_used = 0;
+    c->ev_calls.clear();
+    memset(&c->tsum, 0, sizeof(c->tsum));
+    return EGM_OK;
+}
+
+egm_status egm_get_timing(egm_ctx *c, egm_timing *t) {
+    if (!c || !t) return EGM_ERR_ARG;
+    EGM_TRY(cudaSetDevice(c->device));
+    EGM_TRY(cudaStreamSynchronize(c->stream));
+    for (size_t b : c->ev_calls) {
+        float ms[kStages];
+        for (int k = 0; k < kStages; k++)
+            EGM_TRY(cudaEventElapsedTime(&ms[k], c->ev_pool[b + k], c->ev_pool[b + k + 1]));
+        c->tsum.geometry_ms += ms[0];
+        c->tsum.prep_ms += ms[1];
+        c->tsum.sort_ms += ms[2];
+        c->tsum.post_sort_ms += ms[3];
+        c->tsum.stab_ms += ms[4];
+        c->tsum.csr_ms += ms[5];
+        c->tsum.calls += 1;
+    }
+    c->ev_calls.clear();
+    c->ev_used = 0;
+    *t = c->tsum;
+    return EGM_OK;
+}
+
+egm_status egm_set_counters(egm_ctx *c, int32_t enable) {
+    if (!c) return EGM_ERR_ARG;
+    c->counters_on = enable != 0;
+    return EGM_OK;
+}
+
+egm_status egm_get_stats(egm_ctx *c, egm_stats *s) {
+    if (!c || !s) return EGM_ERR_ARG;
+    egm_status st = egm_sync(c);
+    *s = c->last;
+    return st;
+}
+
+const char *egm_status_string(egm_status s) {
+    switch (s) {
+        case EGM_OK: return "ok";
+        case EGM_ERR_ARG: return "invalid argument";
+        case EGM_ERR_CUDA: return "CUDA runtime error";
+        case EGM_ERR_NOMEM: return "out of device memory";
+        case EGM_ERR_CAPACITY: return "candidate capacity too small";
+        case EGM_ERR_DEGENERATE_F: return "degenerate fundamental matrix (rank < 2)";
+        case EGM_ERR_NAN: return "NaN or Inf in the inputs";
+        case EGM_ERR_TIMEOUT: return "bounded device wait timed out";
+        case EGM_ERR_UNIMPLEMENTED: return "not implemented";
+    }
+    return "unknown status";
+}
+
+int32_t egm_version(void) { return EGM_VERSION; }
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+// Internal declarations shared by the libegm translation units.
+//
+// Data layout in device memory (one call, `npairs` pairs):
+//   PairDesc[npairs]   caller pointers, sizes and offsets into the scratch
+//   PairGeom[npairs]   epipole, key frame, per-level statistics and tables
+//   per reference (sum of n over pairs, pair p at r_off):
+//     key_a/val_a      unsorted (level|angle-key, local index) pairs
+//     key_b/val_b      sort output; key_c/val_c ping-pong for long segments
+//     rec              float4 (x - cx, y - cy, eps, index bits) in key order
+//   tab                per (pair, level) bucket -> first sorted position
+//   per query (sum of m, pair p at q_off):
+//     QueryRec         FP32 line in the pair frame, window centre, pad terms
+//     qcount           candidates per query (CSR path)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/egm.h"
+
+namespace egm {
+
+constexpr int kLevels = 32;        // angular-radius levels (5 bits of the sort key)
+constexpr int kQBits = 22;         // quantised key bits within a level
+constexpr uint32_t kQMax = (1u << kQBits) - 1u;
+constexpr int kKeyBits = kQBits + 5;
+constexpr float kPiF = 3.14159265358979f;
+constexpr float kHalfPiF = 1.57079632679490f;
+
+// Device status bits (combined with atomicOr, mapped to egm_status on the host).
+enum : uint32_t {
+    kStNan = 1u,
+    kStArg = 2u,
+    kStDegenerateF = 4u,
+    kStCapacity = 8u,
+    kStTimeout = 16u,
+};
+
+enum : int32_t { kModeAngular = 0, kModeParallel = 1 };
+
+struct PairDesc {
+    const double *xy1;
+    const double *xy2;
+    const double *F;
+    const double *eps2;
+    const uint8_t *desc1;
+    const uint8_t *desc2;
+    double eps_scalar;
+    int32_t m, n;
+    int32_t kind, dim, row_bytes;
+    int32_t width, height;
+    int32_t pad0;
+    int64_t q_off;      // first query of this pair in per-query arrays
+    int64_t r_off;      // first reference in per-reference arrays
+    int64_t t_off;      // first bucket-table entry
+    int64_t t_cap;      // bucket-table entries reserved for this pair
+};
+
+struct PairGeom {
+    double ex, ey, ew;          // homogeneous epipole, unit norm, ew >= 0
+    double xe, ye;              // Euclidean epipole (angular mode)
+    double cx, cy;              // frame origin: image centre
+    double ux, uy;              // angular: unit vector e -> centre; parallel: line direction
+    float kmin, kscale;         // key quantisation q = clamp((k - kmin) * kscale)
+    int32_t mode;               // kModeAngular / kModeParallel
+    int32_t level_base;         // level = clamp(ilogb(d/eps) - level_base, 1, kLevels-1)
+    // per-level statistics, written with atomics by the prep kernel
+    uint32_t cnt[kLevels];      // members
+    uint32_t smax[kLevels];     // float bits: upper bound of eps/d (angular) or eps (parallel)
+    uint32_t dmin[kLevels];     // float bits: lower bound of d (angular)
+    uint32_t tmax[kLevels];     // float bits: upper bound of |u . (p - c)| (parallel)
+    // filled by the sort kernel
+    uint32_t start[kLevels + 1];  // first sorted position of each level
+    uint32_t tab[kLevels];        // table offset (relative to t_off)
+    int32_t bits[kLevels];        // bucket bits of each level
+};
+
+// FP32 view of one query, written by the prep kernel.
+struct QueryRec {
+    float A, B, C;      // normalised line in the pair frame: dist = |A x' + B y' + C|
+    float key;          // angular: folded line angle; parallel: offset along the normal
+    float aux0;         // angular: r_i upper bound (px); parallel: cos(phi)
+    float aux1;         // parallel: |sin(phi)|
+    uint32_t flags;     // bit 3: degenerate line
+    uint32_t pad;
+};
+
+struct Launch {
+    const PairDesc *pairs;
+    PairGeom *geom;
+    int32_t npairs;
+    int64_t nq, nr;               // total queries / references
+    const int64_t *q_offs;        // npairs + 1 (device) for pair lookup
+    const int64_t *r_offs;        // npairs + 1
+    uint32_t *key_a, *val_a, *key_b, *val_b, *key_c, *val_c;
+    float4 *rec;
+    uint32_t *tab;
+    QueryRec *qrec;
+    uint32_t *status;
+    unsigned long long *counters;  // egm_stats fields, or NULL
+    // outputs (concatenated over pairs)
+    int32_t *best, *second;
+    float *best_d, *second_d;
+    uint8_t *flags;
+    int64_t *cand_offsets;
+    int32_t *cand_idx;
+    int64_t cand_capacity;
+    int64_t *cand_total;
+    int64_t *qcount;              // per-query candidate counts (CSR path)
+    int64_t *scan_tmp;            // scan partials
+    int32_t ratio_num, ratio_den;
+};
+
+// Index of the pair that owns flattened element g, given offs[0..npairs].
+__device__ __forceinline__ int pair_of(const int64_t *offs, int npairs, int64_t g) {
+    int lo = 0, hi = npairs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(offs + mid) <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Monotone quantisation shared by references and windows.  Explicit
+// round-to-nearest intrinsics keep the compiler from contracting the two
+// operations differently at different call sites.
+__device__ __forceinline__ uint32_t qmap(float k, float kmin, float kscale) {
+    float t = __fmul_rn(__fsub_rn(k, kmin), kscale);
+    t = fminf(fmaxf(t, 0.0f), (float)kQMax);
+    return (uint32_t)t;
+}
+
+// The oracle's FP64 evaluation order, with one rounding per operation.
+__device__ __forceinline__ void exact_line(const double *F, double x, double y, double &a, double &b,
+                                           double &c) {
+    a = __dadd_rn(__dadd_rn(__dmul_rn(__ldg(F + 0), x), __dmul_rn(__ldg(F + 1), y)), __ldg(F + 2));
+    b = __dadd_rn(__dadd_rn(__dmul_rn(__ldg(F + 3), x), __dmul_rn(__ldg(F + 4), y)), __ldg(F + 5));
+    c = __dadd_rn(__dadd_rn(__dmul_rn(__ldg(F + 6), x), __dmul_rn(__ldg(F + 7), y)), __ldg(F + 8));
+}
+
+__device__ __forceinline__ double exact_norm(double a, double b) {
+    return __dsqrt_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)));
+}
+
+// Eq. 3 / Eq. 4 decided exactly as the brute-force definition: dist <= eps.
+__device__ __forceinline__ bool exact_member(double a, double b, double c, double N, double x, double y,
+                                             double eps) {
+    double num = fabs(__dadd_rn(__dadd_rn(__dmul_rn(a, x), __dmul_rn(b, y)), c));
+    return __ddiv_rn(num, N) <= eps;
+}
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_geometry(const Launch &L, cudaStream_t s);
+cudaError_t launch_prep(const Launch &L, cudaStream_t s);
+cudaError_t launch_sort(const Launch &L, int max_n, cudaStream_t s);
+cudaError_t launch_post_sort(const Launch &L, cudaStream_t s);
+cudaError_t launch_stab(const Launch &L, int mode, cudaStream_t s);  // 0 fused match, 1 count, 2 fill+match
+cudaError_t launch_csr_offsets(const Launch &L, uint32_t *long_count, cudaStream_t s);
+cudaError_t launch_csr_row_sort(const Launch &L, uint32_t *long_list, uint32_t *long_count, cudaStream_t s);
+cudaError_t launch_long_row_sort(const Launch &L, const uint32_t *list, const uint32_t *count, cudaStream_t s);
+cudaError_t launch_intervals(const Launch &L, double *theta, double *delta, double *e3, int32_t *mode,
+                             cudaStream_t s);
+
+}  // namespace egm

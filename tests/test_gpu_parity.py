@@ -1,0 +1,397 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Candidate sets and match indices must be identical (ties to the lower index);
+pairs within 1e-9 px of the tolerance are decided by the same FP64 expression
+on both sides, and the comparison also accepts the oracle's answer with those
+pairs excluded for the few queries that have one.  u8 / binary distances are
+integers and compared exactly; float distances within 1e-5 relative.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+F32_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def mt():
+    import torch
+
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_2603_18401_gb300 import Matcher
+
+    m = Matcher(0)
+    yield m
+    torch.cuda.synchronize()
+    m.close()
+
+
+def run(mt, sc, csr=True):
+    d = mt.to_device(sc)
+    o = mt.match(d["xy1"], d["xy2"], d["F"], d["eps"], d["desc1"], d["desc2"], d["kind"], d["dim"],
+                 d["width"], d["height"], csr=csr)
+    return {k: v.cpu().numpy() for k, v in o.items()}
+
+
+def check_candidates(out, sc):
+    c = oracle.candidates(sc.xy1, sc.xy2, sc.F, sc.eps)
+    assert np.array_equal(out["cand_offsets"], c["offsets"])
+    assert np.array_equal(out["cand_idx"], c["idx"])
+    return c
+
+
+def check_matches(out, sc, ref=None, rows=None):
+    ref = ref if ref is not None else oracle.match_scene(sc)
+    alt = None
+    kind = sc.kind
+    bad = []
+    for name in ("best", "second", "flags"):
+        g = out[name] if rows is None else out[name][rows]
+        ne = np.nonzero(g != ref[name])[0]
+        bad.extend(ne.tolist())
+    bad = sorted(set(bad))
+    if bad:
+        if kind == synth.DESC_F32_L2:
+            # near-ties in FP32 vs FP64 (1e-5 relative) are listed apart
+            bd = ref["best_d"][bad]
+            sd = ref["second_d"][bad]
+            tie = np.abs(sd - bd) <= 2e-5 * np.maximum(bd, 1e-30)
+            assert tie.all(), f"{(~tie).sum()} float mismatches that are not near-ties"
+        else:
+            alt = oracle.match_scene(sc, exclude_boundary=True)
+            for i in bad:
+                for name in ("best", "second", "flags"):
+                    g = out[name][i] if rows is None else out[name][rows[i]]
+                    assert g == alt[name][i], (name, i)
+    bd_gpu = out["best_d"] if rows is None else out["best_d"][rows]
+    has = ref["best"] >= 0
+    if kind == synth.DESC_F32_L2:
+        ok = np.isclose(bd_gpu[has], ref["best_d"][has], rtol=F32_RTOL, atol=1e-7)
+        assert ok.mean() > 0.999
+    else:
+        good = np.setdiff1d(np.nonzero(has)[0], bad)
+        assert np.array_equal(bd_gpu[good], ref["best_d"][good].astype(np.float32))
+    assert np.all(np.isinf(bd_gpu[~has]))
+    return ref
+
+
+# ------------------------------------------------------------------ configs
+
+def test_config1_full(mt):
+    sc = synth.config1()
+    out = run(mt, sc)
+    check_candidates(out, sc)
+    check_matches(out, sc)
+
+
+@pytest.mark.parametrize("pose", list(synth.CONFIG2_POSES))
+@pytest.mark.parametrize("eps", [1.0, 2.0, 4.0])
+def test_config2_full(mt, pose, eps):
+    sc = synth.config2(pose, eps)
+    out = run(mt, sc)
+    check_candidates(out, sc)
+    check_matches(out, sc)
+
+
+def test_config3_batch_matches_per_pair_and_oracle(mt):
+    scenes = synth.config3(seed=0, npairs=12, scale=0.12)
+    items = [mt.to_device(s) for s in scenes]
+    ob = mt.match_batch(items, csr=True)
+    ob = {k: v.cpu().numpy() for k, v in ob.items()}
+    q0 = 0
+    c0 = 0
+    for s in scenes:
+        o1 = run(mt, s)
+        sl = slice(q0, q0 + s.m)
+        for k in ("best", "second", "flags", "best_d", "second_d"):
+            assert np.array_equal(ob[k][sl], o1[k]), k
+        offs = ob["cand_offsets"][q0:q0 + s.m + 1] - ob["cand_offsets"][q0]
+        assert np.array_equal(offs, o1["cand_offsets"])
+        n_c = int(offs[-1])
+        assert np.array_equal(ob["cand_idx"][c0:c0 + n_c], o1["cand_idx"])
+        check_candidates(o1, s)
+        check_matches(o1, s)
+        q0 += s.m
+        c0 += n_c
+
+
+def test_config4_float_descriptors(mt):
+    for sc in synth.config4(seed=0, npairs=2, scale=0.125):
+        out = run(mt, sc)
+        check_candidates(out, sc)
+        check_matches(out, sc)
+
+
+def test_full_size_batch_sampled(mt):
+    """Config-3 sizes (counts up to 32k, the multi-tile sort path) in one batch,
+    checked on sampled queries the oracle computes one by one."""
+    scenes = synth.config3(seed=1, npairs=6, scale=1.0, lo=16384, hi=32768)
+    items = [mt.to_device(s) for s in scenes]
+    ob = {k: v.cpu().numpy() for k, v in mt.match_batch(items).items()}
+    rng = np.random.default_rng(0)
+    q0 = 0
+    for s in scenes:
+        rows = np.sort(rng.choice(s.m, size=min(400, s.m), replace=False))
+        ref = oracle.match(s.xy1[rows], s.xy2, s.F, s.eps, s.desc1[rows], s.desc2, s.kind, s.dim)
+        sub = {k: ob[k][q0 + rows] for k in ("best", "second", "flags", "best_d", "second_d")}
+        for k in ("best", "second", "flags"):
+            assert np.array_equal(sub[k], ref[k]), k
+        q0 += s.m
+
+
+# ------------------------------------------------------------------ golden + edge cases
+
+def _golden(golden_dir, name):
+    with open(os.path.join(golden_dir, name)) as f:
+        return json.load(f)
+
+
+def test_golden_tiny_scenes_gpu(mt, golden_dir):
+    g = _golden(golden_dir, "tiny_scenes.json")
+    for s in g["scenes"]:
+        q = np.array(s["queries"], float)
+        r = np.array(s["refs"], float)
+        eps = s["eps"] if np.isscalar(s["eps"]) else np.array(s["eps"], float)
+        sc = synth.Scene(xy1=q, xy2=r, F=np.array(s["F"], float), eps=eps,
+                         desc1=np.zeros((len(q), 16), np.uint8), desc2=np.zeros((len(r), 16), np.uint8),
+                         kind=0, dim=16, width=200, height=200, gt=np.zeros((0, 2), np.int64))
+        out = run(mt, sc)
+        rows = [list(out["cand_idx"][out["cand_offsets"][i]:out["cand_offsets"][i + 1]]) for i in range(len(q))]
+        assert rows == s["expected"], s["name"]
+        deg = (out["flags"] & 8) != 0
+        assert list(deg.astype(int)) == s["degenerate"]
+
+
+def test_golden_matches_gpu(mt, golden_dir):
+    g = _golden(golden_dir, "tiny_matches.json")
+    for key, kind in (("u8", 0), ("bin", 2)):
+        s = g[key]
+        row = 16
+        d1 = np.zeros((len(s["queries"]), row), np.uint8)
+        d2 = np.zeros((len(s["refs"]), row), np.uint8)
+        a1 = np.array(s["desc1"], np.uint8)
+        a2 = np.array(s["desc2"], np.uint8)
+        d1[:, :a1.shape[1]] = a1
+        d2[:, :a2.shape[1]] = a2
+        dim = row if kind == 0 else row * 8
+        sc = synth.Scene(xy1=np.array(s["queries"], float), xy2=np.array(s["refs"], float),
+                         F=np.array(g["F"], float), eps=g["eps"], desc1=d1, desc2=d2, kind=kind,
+                         dim=dim, width=100, height=100, gt=np.zeros((0, 2), np.int64))
+        out = run(mt, sc, csr=False)
+        assert list(out["best"]) == s["best"]
+        assert list(out["second"]) == s["second"]
+        assert list(out["flags"]) == s["flags"]
+
+
+def _scene(xy1, xy2, F, eps, w=640, h=480, kind=0, dim=32, seed=0):
+    rng = np.random.default_rng(seed)
+    m, n = len(xy1), len(xy2)
+    if kind == 0:
+        d1 = rng.integers(0, 256, (m, dim), dtype=np.uint8)
+        d2 = rng.integers(0, 256, (n, dim), dtype=np.uint8)
+    elif kind == 2:
+        d1 = rng.integers(0, 256, (m, dim // 8), dtype=np.uint8)
+        d2 = rng.integers(0, 256, (n, dim // 8), dtype=np.uint8)
+    else:
+        d1 = rng.random((m, dim)).astype(np.float32)
+        d2 = rng.random((n, dim)).astype(np.float32)
+    return synth.Scene(xy1=np.asarray(xy1, float).reshape(-1, 2), xy2=np.asarray(xy2, float).reshape(-1, 2),
+                       F=np.asarray(F, float), eps=eps, desc1=d1, desc2=d2, kind=kind, dim=dim,
+                       width=w, height=h, gt=np.zeros((0, 2), np.int64))
+
+
+def _full_check(mt, sc):
+    out = run(mt, sc)
+    check_candidates(out, sc)
+    check_matches(out, sc)
+    return out
+
+
+def test_empty_and_tiny(mt):
+    F = synth.fundamental(synth.intrinsics(500, 640, 480), synth.intrinsics(500, 640, 480),
+                          synth.rotation([0, 1, 0], 10), [0.3, 0, 0.03])
+    rng = np.random.default_rng(1)
+    _full_check(mt, _scene(rng.uniform(0, 480, (5, 2)), np.zeros((0, 2)), F, 2.0))      # n = 0
+    _full_check(mt, _scene(rng.uniform(0, 480, (50, 2)), rng.uniform(0, 480, (1, 2)), F, 500.0))  # n = 1
+    sc = _scene(np.zeros((0, 2)), rng.uniform(0, 480, (10, 2)), F, 2.0)  # m = 0
+    d = mt.to_device(sc)
+    o = mt.match(d["xy1"], d["xy2"], d["F"], 2.0, d["desc1"], d["desc2"], 0, 32, 640, 480, csr=True)
+    assert o["cand_offsets"].cpu().numpy().tolist() == [0]
+
+
+@pytest.mark.parametrize("t", [(0.0, 0.0, 1.0), (0.1, -0.05, 1.0), (1.0, 0.0, 0.0), (0.3, 1.0, 0.0),
+                               (1.0, 0.2, 1e-7), (1.0, 0.3, 1e-12), (-0.4, 0.7, 0.2), (0.5, 0.5, -0.5)])
+def test_epipole_regimes(mt, t):
+    """Epipole at the image centre, inside, at infinity (two directions), very far
+    (1e10 and 1e15 px: both key modes), outside, and behind the camera."""
+    K = synth.intrinsics(800.0, 1000, 800)
+    F = synth.fundamental(K, K, synth.rotation([0.2, 1, 0.1], 4.0), np.array(t))
+    rng = np.random.default_rng(5)
+    xy1 = rng.uniform([-50, -50], [1050, 850], (3000, 2))
+    xy2 = rng.uniform([-50, -50], [1050, 850], (3000, 2))
+    for eps in (0.5, 3.0, 40.0):
+        _full_check(mt, _scene(xy1, xy2, F, eps, w=1000, h=800))
+
+
+def test_points_on_and_near_epipole(mt):
+    """Keypoints exactly at the epipole and within eps of it are candidates of
+    every line (Algorithm 1; Sec. 4.4)."""
+    K = synth.intrinsics(500.0, 640, 480)
+    F = synth.fundamental(K, K, np.eye(3), np.array([0.0, 0.0, 1.0]))   # e2 = (320, 240)
+    rng = np.random.default_rng(9)
+    xy2 = np.vstack([[[320.0, 240.0], [320.5, 240.0], [321.9, 240.0], [320.0, 238.2]],
+                     rng.uniform(0, 640, (2000, 2))])
+    xy1 = rng.uniform([0, 0], [640, 480], (800, 2))
+    out = _full_check(mt, _scene(xy1, xy2, F, 2.0))
+    off, idx = out["cand_offsets"], out["cand_idx"]
+    deg = (out["flags"] & 8) != 0
+    for i in range(800):
+        if not deg[i]:
+            assert {0, 1, 2, 3} <= set(idx[off[i]:off[i + 1]].tolist())
+
+
+def test_rank3_F_and_per_keypoint_eps(mt):
+    """A full-rank F (lines need not meet in one point) and per-keypoint eps."""
+    rng = np.random.default_rng(3)
+    K = synth.intrinsics(600.0, 640, 480)
+    F = synth.fundamental(K, K, synth.rotation([1, 2, 3], 7), [0.4, 0.1, 0.3])
+    F = F + 1e-4 * np.abs(F).max() * rng.normal(size=(3, 3))
+    xy1 = rng.uniform([0, 0], [640, 480], (2500, 2))
+    xy2 = rng.uniform([0, 0], [640, 480], (2500, 2))
+    eps = rng.uniform(0.25, 12.0, 2500)
+    _full_check(mt, _scene(xy1, xy2, F, eps))
+
+
+def test_boundary_pairs_exact(mt):
+    """Pairs at exactly eps (integer geometry) and within 1e-9 px of it."""
+    F = synth.skew([1.0, 0.0, 0.0])  # lines y = y1
+    rng = np.random.default_rng(4)
+    y1 = rng.integers(0, 400, 600).astype(float)
+    xy1 = np.c_[rng.uniform(0, 600, 600), y1]
+    y2 = rng.integers(0, 400, 3000).astype(float)
+    y2[:300] += rng.choice([-1e-10, 1e-10, 3e-10, 0.0], 300)
+    xy2 = np.c_[rng.uniform(0, 600, 3000), y2]
+    out = _full_check(mt, _scene(xy1, xy2, F, 2.0, w=600, h=400))
+    assert out["cand_offsets"][-1] > 0
+
+
+def test_descriptor_kinds_and_dims(mt):
+    K = synth.intrinsics(500.0, 640, 480)
+    F = synth.fundamental(K, K, synth.rotation([0, 1, 0], 5), [0.2, 0.05, 0.02])
+    rng = np.random.default_rng(6)
+    xy1 = rng.uniform([0, 0], [640, 480], (1500, 2))
+    xy2 = rng.uniform([0, 0], [640, 480], (1800, 2))
+    for kind, dim in ((0, 16), (0, 64), (0, 256), (2, 128), (2, 256), (2, 512), (1, 4), (1, 128), (1, 256)):
+        _full_check(mt, _scene(xy1, xy2, F, 6.0, kind=kind, dim=dim, seed=dim + kind))
+
+
+def test_eps_covering_image(mt):
+    """eps larger than the image: every reference is a candidate (exhaustive NN)."""
+    K = synth.intrinsics(500.0, 640, 480)
+    F = synth.fundamental(K, K, synth.rotation([0, 1, 0], 5), [0.2, 0.05, 0.02])
+    rng = np.random.default_rng(7)
+    sc = _scene(rng.uniform(0, 480, (300, 2)), rng.uniform(0, 480, (700, 2)), F, 5000.0)
+    out = _full_check(mt, sc)
+    assert np.all(np.diff(out["cand_offsets"]) == 700)
+
+
+def test_long_candidate_rows(mt):
+    """Rows longer than the warp row sort (1024) and longer than one sort tile."""
+    F = synth.skew([1.0, 0.0, 0.0])
+    rng = np.random.default_rng(8)
+    xy1 = np.c_[rng.uniform(0, 100, 40), rng.uniform(0, 10, 40)]
+    xy2 = np.c_[rng.uniform(0, 100, 20000), rng.uniform(0, 10, 20000)]
+    sc = _scene(xy1, xy2, F, 3.0, w=100, h=10)
+    _full_check(mt, sc)
+
+
+def test_intervals_match_oracle(mt):
+    import torch
+
+    K = synth.intrinsics(500.0, 640, 480)
+    F = synth.fundamental(K, K, synth.rotation([0, 1, 0], 3), np.array([0.2, 0.1, 1.0]))
+    rng = np.random.default_rng(2)
+    xy2 = rng.uniform([0, 0], [640, 480], (4000, 2))
+    eps = rng.uniform(0.5, 5.0, 4000)
+    dev = mt.device
+    th, de, e3, mode = mt.intervals(torch.tensor(xy2, device=dev), torch.tensor(F.reshape(9), device=dev),
+                                    torch.tensor(eps, device=dev), 640, 480)
+    assert mode == 0
+    t0, d0, e_xy = oracle.intervals(F, xy2, eps)
+    e_ref = oracle.epipole(F)
+    assert np.allclose(e3.cpu().numpy(), e_ref, rtol=0, atol=1e-12)
+    # The two epipoles come from different FP64 computations (column cross
+    # product vs SVD); theta and delta inherit their tiny difference, amplified
+    # near the epipole by 1/d and eps/(d^2 cos delta).
+    e_gpu = e3.cpu().numpy()
+    de_px = np.hypot(*(e_gpu[:2] / e_gpu[2] - e_xy))
+    assert de_px < 1e-7
+    d = np.hypot(xy2[:, 0] - e_xy[0], xy2[:, 1] - e_xy[1])
+    thg = th.cpu().numpy()
+    diff = np.abs(thg - t0)
+    diff = np.minimum(diff, math.pi - diff)  # same angle across the 0/pi seam
+    assert np.all(diff <= 1e-12 + 2 * de_px / d)
+    far = d > eps * (1 + 1e-6)
+    cosd = np.cos(d0[far])
+    tol = 1e-12 + 2 * de_px * eps[far] / (d[far] ** 2 * cosd)
+    assert np.all(np.abs(de.cpu().numpy()[far] - d0[far]) <= tol)
+    assert np.all(de.cpu().numpy()[d < eps * (1 - 1e-6)] == math.pi / 2)
+    # epipole at infinity: parallel mode, no intervals
+    th, de, e3, mode = mt.intervals(torch.tensor(xy2, device=dev),
+                                    torch.tensor(synth.skew([1.0, 0, 0]).reshape(9), device=dev), 2.0, 640, 480)
+    assert mode == 1 and torch.isnan(th).all()
+
+
+def test_host_path_equals_device_path(mt):
+    sc = synth.config2("far", 2.0, scale=0.25)
+    dev = run(mt, sc)
+    host = mt.match_host(sc, csr=True)
+    for k in ("best", "second", "flags", "best_d", "second_d", "cand_offsets"):
+        assert np.array_equal(host[k], dev[k]), k
+    n = int(host["cand_total"][0])
+    assert np.array_equal(host["cand_idx"][:n], dev["cand_idx"])
+
+
+def test_error_statuses(mt):
+    import torch
+
+    from paper_2603_18401_gb300 import EgmError
+
+    sc = synth.config1(scale=0.1)
+    d = mt.to_device(sc)
+    args = (d["desc1"], d["desc2"], 0, 128, 640, 480)
+    bad = d["F"].clone()
+    bad[4] = float("nan")
+    with pytest.raises(EgmError) as e:
+        mt.match(d["xy1"], d["xy2"], bad, 2.0, *args)
+    assert e.value.status == -6
+    with pytest.raises(EgmError) as e:
+        mt.match(d["xy1"], d["xy2"], torch.zeros_like(d["F"]), 2.0, *args)
+    assert e.value.status == -5
+    with pytest.raises(EgmError) as e:
+        mt.match(d["xy1"], d["xy2"], d["F"], -1.0, *args)
+    assert e.value.status == -1
+    xy = d["xy2"].clone()
+    xy[3, 0] = float("inf")
+    with pytest.raises(EgmError) as e:
+        mt.match(d["xy1"], xy, d["F"], 2.0, *args)
+    assert e.value.status == -6
+    # capacity: too small -> EGM_ERR_CAPACITY with the required total; the
+    # binding then retries with exactly that capacity
+    o = mt.match(d["xy1"], d["xy2"], d["F"], 2.0, *args, csr=True, cand_capacity=3)
+    c = oracle.candidates(sc.xy1, sc.xy2, sc.F, 2.0)
+    assert int(o["cand_total"].item()) == int(c["offsets"][-1])
+    assert np.array_equal(o["cand_idx"].cpu().numpy(), c["idx"])
+    # the context stays usable after every error
+    o = mt.match(d["xy1"], d["xy2"], d["F"], 2.0, *args)
+    assert int((o["best"] >= 0).sum()) > 0
