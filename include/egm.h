@@ -179,6 +179,31 @@ egm_status egm_match_batch(egm_ctx *ctx, const egm_pair *pairs, int32_t npairs,
  * the device, matches, copies the outputs back and waits for completion. */
 egm_status egm_match_pair_host(egm_ctx *ctx, const egm_pair *pair, const egm_out *out);
 
+/*
+ * egm_match_pair without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory, e.g.
+ * code running under a framework that owns the device allocator and its
+ * budget, real-time loops that cannot afford cudaMalloc / cudaFree (which may
+ * synchronise the whole device), or plug-ins handed a stream but no context.
+ *
+ * It takes no egm_ctx and calls no cudaMalloc, cudaFree, cudaMallocHost or
+ * other allocating routine.  All scratch lives in one fixed file-scope device
+ * array of about 1.7 MiB that every GPU loading libegm.so keeps until the
+ * process exits; it holds pairs of at most 16384 keypoints per image (m and
+ * n); larger pairs are rejected with EGM_ERR_CAPACITY before any work.
+ *   pair, out  as for egm_match_pair (device pointers)
+ *   params     ratio test (ratio_num / ratio_den); NULL for 4 / 5.  The
+ *              sync and form fields are ignored.
+ *   stream     cudaStream_t to run on (NULL: the legacy default stream)
+ * The call returns after the work finished on `stream`, with the device-side
+ * status.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same array: calls that overlap on the GPU (other
+ * streams, other host threads) race and corrupt each other's results.
+ */
+egm_status egm_match_pair_static(const egm_pair *pair, const egm_out *out, const egm_params *params,
+                                 void *stream);
+
 /* Wait for the context's stream and return (then clear) the device status. */
 egm_status egm_sync(egm_ctx *ctx);
 

@@ -81,6 +81,8 @@ SIGNATURES = {
     "egm_match_pair": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.POINTER(egm_out)]),
     "egm_match_batch": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.c_int32, C.POINTER(egm_out)]),
     "egm_match_pair_host": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.POINTER(egm_out)]),
+    "egm_match_pair_static": (C.c_int, [C.POINTER(egm_pair), C.POINTER(egm_out), C.POINTER(egm_params),
+                                        C.c_void_p]),
     "egm_sync": (C.c_int, [C.c_void_p]),
     "egm_intervals": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p]),
