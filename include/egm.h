@@ -188,7 +188,7 @@ egm_status egm_match_pair_host(egm_ctx *ctx, const egm_pair *pair, const egm_out
  *
  * It takes no egm_ctx and calls no cudaMalloc, cudaFree, cudaMallocHost or
  * other allocating routine.  All scratch lives in one fixed file-scope device
- * array of about 1.7 MiB that every GPU loading libegm.so keeps until the
+ * array of about 1.9 MB that every GPU loading libegm.so keeps until the
  * process exits; it holds pairs of at most 16384 keypoints per image (m and
  * n); larger pairs are rejected with EGM_ERR_CAPACITY before any work.
  *   pair, out  as for egm_match_pair (device pointers)

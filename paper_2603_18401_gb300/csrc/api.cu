@@ -215,6 +215,7 @@ Launch make_launch(egm_ctx *c, const Plan &pl, int npairs, const egm_out *out) {
     L.scan_tmp = as<int64_t>(c->scan);
     L.ratio_num = c->params.ratio_num;
     L.ratio_den = c->params.ratio_den;
+    L.max_n = pl.max_n;
     if (out) {
         L.best = out->best;
         L.second = out->second;

@@ -60,29 +60,37 @@ struct PairGeom {
     double ex, ey, ew;          // homogeneous epipole, unit norm, ew >= 0
     double xe, ye;              // Euclidean epipole (angular mode)
     double cx, cy;              // frame origin: image centre
-    double ux, uy;              // angular: unit vector e -> centre; parallel: line direction
+    float ux, uy;               // angular: unit vector from the epipole to the centre; parallel: line direction
+    float de;                   // angular: |centre - epipole|
+    float kappa;                // angular: -u x (epipole - centre), the rounding residue of the frame
     float kmin, kscale;         // key quantisation q = clamp((k - kmin) * kscale)
     int32_t mode;               // kModeAngular / kModeParallel
     int32_t level_base;         // level = clamp(ilogb(d/eps) - level_base, 1, kLevels-1)
+    float Ff[9];                // F rounded to FP32 (magnitudes for error terms)
+    int32_t pad0;
     // per-level statistics, written with atomics by the prep kernel
     uint32_t cnt[kLevels];      // members
     uint32_t smax[kLevels];     // float bits: upper bound of eps/d (angular) or eps (parallel)
     uint32_t dmin[kLevels];     // float bits: lower bound of d (angular)
-    uint32_t tmax[kLevels];     // float bits: upper bound of |u . (p - c)| (parallel)
+    uint32_t tmax[kLevels];     // float bits: upper bound of |p - c|
     // filled by the sort kernel
     uint32_t start[kLevels + 1];  // first sorted position of each level
     uint32_t tab[kLevels];        // table offset (relative to t_off)
     int32_t bits[kLevels];        // bucket bits of each level
 };
 
+// Query flags beyond the public EGM_FLAG_* bits.
+enum : uint32_t { kQExactOnly = 0x100u };  // FP32 view unusable: whole levels, FP64 decides every pair
+
 // FP32 view of one query, written by the prep kernel.
-struct QueryRec {
+struct __align__(16) QueryRec {
     float A, B, C;      // normalised line in the pair frame: dist = |A x' + B y' + C|
     float key;          // angular: folded line angle; parallel: offset along the normal
     float aux0;         // angular: r_i upper bound (px); parallel: cos(phi)
     float aux1;         // parallel: |sin(phi)|
-    uint32_t flags;     // bit 3: degenerate line
-    uint32_t pad;
+    float E0, E1;       // line error terms of the pre-test: E0 + E1 (|x'| + |y'| + 2 eps)
+    uint32_t flags;     // EGM_FLAG_DEGENERATE_LINE, kQExactOnly
+    uint32_t pad[3];
 };
 
 struct Launch {
@@ -109,7 +117,37 @@ struct Launch {
     int64_t *qcount;              // per-query candidate counts (CSR path)
     int64_t *scan_tmp;            // scan partials
     int32_t ratio_num, ratio_den;
+    int32_t max_n;                // largest reference count of the batch
 };
+
+// Pairs with at most this many references are sorted by one thread-block
+// cluster, which also writes the sorted records and bucket tables; larger
+// pairs take the single-block sort and the separate post-sort pass.
+constexpr int kClusterCtas = 8;
+constexpr int kClusterThreads = 512;
+constexpr int kClusterItems = 8;
+constexpr int kClusterMaxN = kClusterCtas * kClusterThreads * kClusterItems;  // 32768
+
+// Level layout (first sorted position, bucket bits, table offset) from the
+// level counts; every block that needs it computes the same values.
+__device__ __forceinline__ void level_layout(const uint32_t *cnt, uint32_t *start, int32_t *bits, uint32_t *tab,
+                                             int max_bits) {
+    uint32_t pos = 0, toff = 0;
+    for (int l = 0; l < kLevels; l++) {
+        const uint32_t c = cnt[l];
+        start[l] = pos;
+        int b = 0;
+        if (c > 1) {
+            b = 32 - __clz(c - 1) + 1;  // ~2 buckets per member
+            if (b > max_bits) b = max_bits;
+        }
+        bits[l] = b;
+        tab[l] = toff;
+        toff += (1u << b) + 1u;
+        pos += c;
+    }
+    start[kLevels] = pos;
+}
 
 // Index of the pair that owns flattened element g, given offs[0..npairs].
 __device__ __forceinline__ int pair_of(const int64_t *offs, int npairs, int64_t g) {

@@ -1,20 +1,26 @@
 // Geometry and per-keypoint preparation.
 //
-//   geometry_kernel   one block per pair: epipole e2 = null(F^T) (Algorithm 1)
+//   geometry_kernel   one warp per pair: epipole e2 = null(F^T) (Algorithm 1)
 //                     as the cross product of two columns of F, the key frame
 //                     (angular or parallel) and zeroed level statistics.
 //   prep_kernel       every reference keypoint: its angle seen from e2
 //                     (Sec. 4.2, Eq. theta), its level (the octave of
-//                     eps_j / ||p_j - e2||, i.e. of sin delta_j, Eq. delta), a
-//                     27-bit sort key; every query: its epipolar line
-//                     l_i = F p~_i^1 (Sec. 3) in FP64, the line's angle alpha_i
-//                     (Sec. 4.2, reduced mod pi) and the FP32 line used by the
-//                     pre-test.
+//                     eps_j / ||p_j - e2||, i.e. of sin delta_j, Eq. delta) and
+//                     a 27-bit sort key; every query: its epipolar line
+//                     l_i = F p~_i^1 (Sec. 3), the line's angle alpha_i
+//                     (Sec. 4.2, reduced mod pi) and the FP32 line of the
+//                     pre-test, with bounds on every rounding error.
 //   intervals_kernel  the paper's (theta_j, delta_j) in FP64 for inspection.
 //
-// Angles are measured in a frame turned so that the image centre lies at
-// angle 0 as seen from the epipole, and reduced to [-pi/2, pi/2) by flipping
-// the direction vector (exact) rather than by adding pi (rounded).
+// FP64 is scarce on GB300 (about 1/64 of the FP32 rate), so only what needs
+// it runs in FP64: the epipole, the query line (FMA form) and two dot
+// products per query.  The angular frame is turned so that the image centre
+// c lies at angle 0 seen from the epipole e; with E = e - c and u the unit
+// vector towards c, the exact decomposition
+//     p - e  =  (|E| + u.(p - c),  u x (p - c) + kappa),   kappa = -u x E,
+// lets every reference be keyed in FP32 even when e is 1e10 px away: kappa
+// (computed once in FP64) absorbs the rounding of u.  A direction is reduced
+// mod pi by flipping the vector (exact), never by adding pi (rounded).
 #include <math.h>
 
 #include "egm_internal.cuh"
@@ -25,138 +31,144 @@ namespace {
 
 __device__ __forceinline__ void set_status(uint32_t *st, uint32_t bit) { atomicOr(st, bit); }
 
-__device__ __forceinline__ void cross3(const double *a, const double *b, double *o) {
-    o[0] = a[1] * b[2] - a[2] * b[1];
-    o[1] = a[2] * b[0] - a[0] * b[2];
-    o[2] = a[0] * b[1] - a[1] * b[0];
+__device__ __forceinline__ float fold_atan2(float px, float py) {
+    if (px < 0.0f || (px == 0.0f && py > 0.0f)) { px = -px; py = -py; }
+    return atan2f(py, px);
 }
 
-__global__ void geometry_kernel(Launch L) {
+__global__ void __launch_bounds__(32) geometry_kernel(Launch L) {
     const int p = blockIdx.x;
+    const int lane = threadIdx.x;
     const PairDesc &P = L.pairs[p];
     PairGeom &G = L.geom[p];
-    const int t = threadIdx.x;
-    if (t < kLevels) {
-        G.cnt[t] = 0u;
-        G.smax[t] = 0u;
-        G.dmin[t] = 0x7f800000u;  // +inf
-        G.tmax[t] = 0u;
-    }
-    if (t != 0) return;
+    G.cnt[lane] = 0u;
+    G.smax[lane] = 0u;
+    G.dmin[lane] = 0x7f800000u;  // +inf
+    G.tmax[lane] = 0u;
 
+    // F^T e2 = 0: e2 is orthogonal to every column of F.  Lanes 0..2 form the
+    // three column cross products; the largest one is the epipole.
+    const double fv = lane < 9 ? P.F[lane] : 0.0;
     double F[9];
-    bool finite = true;
+#pragma unroll
+    for (int k = 0; k < 9; k++) F[k] = __shfl_sync(0xffffffffu, fv, k);
+    const bool finite = __all_sync(0xffffffffu, isfinite(fv));
     double fn2 = 0.0;
-    for (int k = 0; k < 9; k++) {
-        F[k] = P.F[k];
-        finite &= isfinite(F[k]);
-        fn2 += F[k] * F[k];
+#pragma unroll
+    for (int k = 0; k < 9; k++) fn2 = fma(F[k], F[k], fn2);
+    const int c0 = lane == 2 ? 1 : 0, c1 = lane == 0 ? 1 : 2;  // column pairs (0,1) (0,2) (1,2)
+    const double ax = F[c0], ay = F[3 + c0], az = F[6 + c0];
+    const double bx = F[c1], by = F[3 + c1], bz = F[6 + c1];
+    double crx = fma(ay, bz, -az * by), cry = fma(az, bx, -ax * bz), crz = fma(ax, by, -ay * bx);
+    double nk = lane < 3 ? fma(crx, crx, fma(cry, cry, crz * crz)) : -1.0;
+    int best = lane;
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        const double on = __shfl_xor_sync(0xffffffffu, nk, o);
+        const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+        if (on > nk || (on == nk && ob < best)) { nk = on; best = ob; }
     }
+    crx = __shfl_sync(0xffffffffu, crx, best);
+    cry = __shfl_sync(0xffffffffu, cry, best);
+    crz = __shfl_sync(0xffffffffu, crz, best);
+    const bool degenerate = !finite || !(fn2 > 0.0) || !(nk > 1e-26 * fn2 * fn2);
+
     const double W = (double)P.width, H = (double)P.height;
     const double cx = 0.5 * W, cy = 0.5 * H;
-    // FP64 is scarce on this GPU: the range / mode decisions below only steer
-    // efficiency (keys are clamped into any range), so they use FP32 maths on
-    // FP64-computed offsets.
-    const double diag = (double)hypotf((float)W, (float)H);
-    G.cx = cx;
-    G.cy = cy;
-
-    // e2 is orthogonal to every column of F (F^T e2 = 0): take the cross
-    // product of the two columns with the largest cross-product norm.
-    double col[3][3] = {{F[0], F[3], F[6]}, {F[1], F[4], F[7]}, {F[2], F[5], F[8]}};
-    double cr[3][3];
-    cross3(col[0], col[1], cr[0]);
-    cross3(col[0], col[2], cr[1]);
-    cross3(col[1], col[2], cr[2]);
-    int kb = 0;
-    double nb = -1.0;
-    for (int k = 0; k < 3; k++) {
-        double nk = cr[k][0] * cr[k][0] + cr[k][1] * cr[k][1] + cr[k][2] * cr[k][2];
-        if (nk > nb) { nb = nk; kb = k; }
-    }
-    bool degenerate = !finite || !(fn2 > 0.0) || !(nb > 1e-26 * fn2 * fn2);
-    if (!finite) set_status(L.status, kStNan);
-    else if (degenerate) set_status(L.status, kStDegenerateF);
-
+    const float diag = hypotf((float)W, (float)H);
     double ex = 1.0, ey = 0.0, ew = 0.0;
     if (!degenerate) {
-        double s = 1.0 / sqrt(nb);
-        ex = cr[kb][0] * s;
-        ey = cr[kb][1] * s;
-        ew = cr[kb][2] * s;
+        const double s = 1.0 / sqrt(nk);
+        ex = crx * s;
+        ey = cry * s;
+        ew = crz * s;
         if (ew < 0.0 || (ew == 0.0 && (ex < 0.0 || (ex == 0.0 && ey < 0.0)))) {
             ex = -ex; ey = -ey; ew = -ew;
         }
     }
+    bool parallel = true;
+    double xe = 0.0, ye = 0.0;
+    double Ex = 0.0, Ey = 0.0;
+    if (!degenerate && ew != 0.0) {
+        const double iw = 1.0 / ew;
+        xe = ex * iw;
+        ye = ey * iw;
+        Ex = xe - cx;
+        Ey = ye - cy;
+        parallel = !(hypotf((float)Ex, (float)Ey) <= 1e6f * diag);
+    }
+    // frame: FP32 unit vector u and, in angular mode, |E| and kappa
+    float ux = 1.0f, uy = 0.0f, de = 0.0f, kappa = 0.0f;
+    if (parallel) {
+        if (!degenerate) {
+            const double vx = ex - cx * ew, vy = ey - cy * ew;
+            const float nv = hypotf((float)vx, (float)vy);
+            if (nv > 0.0f) { ux = (float)vx / nv; uy = (float)vy / nv; }
+        }
+    } else {
+        const double dE = sqrt(fma(Ex, Ex, Ey * Ey));
+        if (dE > 1e-9 * (double)diag) {
+            ux = (float)(-Ex / dE);
+            uy = (float)(-Ey / dE);
+        }
+        de = (float)dE;
+        // kappa = -(u x E) with the rounded u, in FP64
+        kappa = (float)(-fma((double)ux, Ey, -(double)uy * Ex));
+    }
+    // key range from the image corners (lane k < 4), FP32
+    const float qx = (lane & 1) ? (float)(W - cx) : (float)(-cx);
+    const float qy = (lane & 2) ? (float)(H - cy) : (float)(-cy);
+    float kv;
+    if (parallel) kv = -uy * qx + ux * qy;
+    else kv = fold_atan2(de + (ux * qx + uy * qy), (ux * qy - uy * qx) + kappa);
+    float lo = lane < 4 ? kv : INFINITY, hi = lane < 4 ? kv : -INFINITY;
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane < 9) G.Ff[lane] = (float)fv;
+    if (lane != 0) return;
+    if (!finite) set_status(L.status, kStNan);
+    else if (degenerate) set_status(L.status, kStDegenerateF);
     G.ex = ex;
     G.ey = ey;
     G.ew = ew;
-
-    bool parallel = true;
-    double xe = 0.0, ye = 0.0, D = INFINITY;
-    if (!degenerate && ew != 0.0) {
-        xe = ex / ew;
-        ye = ey / ew;
-        D = (double)hypotf((float)(xe - cx), (float)(ye - cy));
-        parallel = !(D <= 1e6 * diag);
-    }
     G.xe = xe;
     G.ye = ye;
-    const double corners[4][2] = {{0.0, 0.0}, {W, 0.0}, {0.0, H}, {W, H}};
-    const double eps_ref = P.eps2 ? 1.0 : (P.eps_scalar > 0.0 ? P.eps_scalar : 1.0);
-
+    G.cx = cx;
+    G.cy = cy;
+    G.ux = ux;
+    G.uy = uy;
+    G.de = de;
+    G.kappa = kappa;
+    const float eps_ref = P.eps2 ? 1.0f : (P.eps_scalar > 0.0 ? (float)P.eps_scalar : 1.0f);
     if (parallel) {
-        // All lines (nearly) parallel to u, the direction of the epipole.
-        double ux = 1.0, uy = 0.0;
-        if (!degenerate) {
-            double vx = ex - cx * ew, vy = ey - cy * ew;
-            double nv = sqrt(vx * vx + vy * vy);
-            if (nv > 0.0) { ux = vx / nv; uy = vy / nv; }
-        }
         G.mode = kModeParallel;
-        G.ux = ux;
-        G.uy = uy;
-        double nx = -uy, ny = ux, lo = INFINITY, hi = -INFINITY;
-        for (int k = 0; k < 4; k++) {
-            double s = nx * (corners[k][0] - cx) + ny * (corners[k][1] - cy);
-            lo = fmin(lo, s);
-            hi = fmax(hi, s);
-        }
-        double margin = 0.01 * (hi - lo) + 1.0;
-        G.kmin = (float)(lo - margin);
-        G.kscale = (float)((double)kQMax / (hi - lo + 2.0 * margin));
-        G.level_base = ilogb(eps_ref) - 8;
+        const float margin = 0.01f * (hi - lo) + 1.0f;
+        G.kmin = lo - margin;
+        G.kscale = (float)kQMax / (hi - lo + 2.0f * margin);
+        G.level_base = ilogbf(eps_ref) - 8;
     } else {
-        double vx = cx - xe, vy = cy - ye, nv = sqrt(vx * vx + vy * vy);
-        double ux = 1.0, uy = 0.0;
-        if (nv > 1e-9 * diag) { ux = vx / nv; uy = vy / nv; }
         G.mode = kModeAngular;
-        G.ux = ux;
-        G.uy = uy;
-        double lo = INFINITY, hi = -INFINITY;
-        for (int k = 0; k < 4; k++) {
-            double wx = corners[k][0] - xe, wy = corners[k][1] - ye;
-            double px = wx * ux + wy * uy, py = ux * wy - uy * wx;
-            double a = (double)atan2f((float)py, (float)px);
-            lo = fmin(lo, a);
-            hi = fmax(hi, a);
-        }
-        double mx = 0.02 * diag;
-        bool inside = xe >= -mx && xe <= W + mx && ye >= -mx && ye <= H + mx;
-        if (inside || hi > 1.3 || lo < -1.3) {
+        const float mx = 0.02f * diag;
+        const float fxe = (float)xe, fye = (float)ye;
+        const bool inside = fxe >= -mx && fxe <= (float)W + mx && fye >= -mx && fye <= (float)H + mx;
+        if (inside || hi > 1.3f || lo < -1.3f) {
             G.kmin = -kHalfPiF;
-            G.kscale = (float)((double)kQMax / M_PI);
+            G.kscale = (float)kQMax / kPiF;
         } else {
-            double margin = 0.02 * (hi - lo);
-            G.kmin = (float)(lo - margin);
-            G.kscale = (float)((double)kQMax / (hi - lo + 2.0 * margin));
+            const float margin = 0.02f * (hi - lo);
+            G.kmin = lo - margin;
+            G.kscale = (float)kQMax / (hi - lo + 2.0f * margin);
         }
         // distance from e2 to the image rectangle
-        double dx = fmax(fmax(-xe, xe - W), 0.0), dy = fmax(fmax(-ye, ye - H), 0.0);
-        double dr = (double)hypotf((float)dx, (float)dy);
-        G.level_base = ilogb(fmax(dr, 2.0 * eps_ref) / eps_ref) - 1;
+        const float dx = fmaxf(fmaxf(-fxe, fxe - (float)W), 0.0f), dy = fmaxf(fmaxf(-fye, fye - (float)H), 0.0f);
+        const float dr = hypotf(dx, dy);
+        G.level_base = ilogbf(fmaxf(dr, 2.0f * eps_ref) / eps_ref) - 1;
     }
 }
+
 
 __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
     const int64_t total = L.nr + L.nq;
@@ -167,9 +179,8 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
         const bool is_ref = g < L.nr;
         uint32_t group = 0xffffffffu;
         uint32_t s_bits = 0, d_bits = 0x7f800000u, t_bits = 0;
-        int p = 0;
         if (valid && is_ref) {
-            p = pair_of(L.r_offs, L.npairs, g);
+            const int p = pair_of(L.r_offs, L.npairs, g);
             const PairDesc &P = L.pairs[p];
             const PairGeom &G = L.geom[p];
             const int64_t j = g - P.r_off;
@@ -178,15 +189,15 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
             if (!(isfinite(x) && isfinite(y) && isfinite(eps))) set_status(L.status, kStNan);
             else if (!(eps > 0.0)) set_status(L.status, kStArg);
             const float epsf = (float)eps;
+            const float xf = (float)(x - G.cx), yf = (float)(y - G.cy);
+            const float rr = hypotf(xf, yf);
             int level;
             float key;
             if (G.mode == kModeAngular) {
-                const double vx = x - G.xe, vy = y - G.ye;
-                double px = vx * G.ux + vy * G.uy;
-                double py = G.ux * vy - G.uy * vx;
-                if (px < 0.0 || (px == 0.0 && py > 0.0)) { px = -px; py = -py; }
-                key = atan2f((float)py, (float)px);
-                const float d = hypotf((float)vx, (float)vy);
+                const float px = G.de + (G.ux * xf + G.uy * yf);
+                const float py = (G.ux * yf - G.uy * xf) + G.kappa;
+                key = fold_atan2(px, py);
+                const float d = hypotf(px, py);
                 const float ratio = d / epsf;
                 if (!(ratio >= 2.0f)) {
                     level = 0;
@@ -194,19 +205,16 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
                     level = ilogbf(ratio) - G.level_base;
                     level = level < 1 ? 1 : (level > kLevels - 1 ? kLevels - 1 : level);
                 }
-                float s = d > 0.0f ? epsf / d : INFINITY;
+                const float s = d > 0.0f ? epsf / d : INFINITY;
                 s_bits = __float_as_uint(s * 1.000001f);
                 d_bits = __float_as_uint(d * 0.999999f);
             } else {
-                const double px = x - G.cx, py = y - G.cy;
-                const double sN = -G.uy * px + G.ux * py;
-                const double tU = G.ux * px + G.uy * py;
-                key = (float)sN;
+                key = -G.uy * xf + G.ux * yf;
                 level = ilogbf(epsf) - G.level_base;
                 level = level < 1 ? 1 : (level > kLevels - 1 ? kLevels - 1 : level);
                 s_bits = __float_as_uint(epsf * 1.000001f);
-                t_bits = __float_as_uint((float)fabs(tU) * 1.000001f + 1e-3f);
             }
+            t_bits = __float_as_uint(rr * 1.000001f);
             if (!isfinite(key)) key = 0.0f;
             const uint32_t q = qmap(key, G.kmin, G.kscale);
             L.key_a[g] = ((uint32_t)level << kQBits) | q;
@@ -214,49 +222,63 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
             group = (uint32_t)p * kLevels + (uint32_t)level;
         } else if (valid) {
             const int64_t gq = g - L.nr;
-            p = pair_of(L.q_offs, L.npairs, gq);
+            const int p = pair_of(L.q_offs, L.npairs, gq);
             const PairDesc &P = L.pairs[p];
             const PairGeom &G = L.geom[p];
             const int64_t i = gq - P.q_off;
             const double x1 = P.xy1[2 * i], y1 = P.xy1[2 * i + 1];
             QueryRec r;
             r.flags = 0;
-            r.pad = 0;
-            r.A = r.B = r.C = r.key = r.aux0 = r.aux1 = 0.0f;
+            r.pad[0] = r.pad[1] = r.pad[2] = 0;
+            r.A = r.B = r.C = r.key = r.aux0 = r.aux1 = r.E0 = r.E1 = 0.0f;
             if (!(isfinite(x1) && isfinite(y1))) set_status(L.status, kStNan);
-            double a, b, c;
-            exact_line(P.F, x1, y1, a, b, c);
-            const double N = exact_norm(a, b);
-            if (!(N > 0.0) || !isfinite(N) || !isfinite(c)) {
-                r.flags = EGM_FLAG_DEGENERATE_LINE;
+            const double *F = P.F;
+            // the line with FMAs: within a few ulps of its terms of the exact line
+            const double a = fma(F[0], x1, fma(F[1], y1, F[2]));
+            const double b = fma(F[3], x1, fma(F[4], y1, F[5]));
+            const double c = fma(F[6], x1, fma(F[7], y1, F[8]));
+            const float x1f = fabsf((float)x1), y1f = fabsf((float)y1);
+            const float ta = fabsf(G.Ff[0]) * x1f + fabsf(G.Ff[1]) * y1f + fabsf(G.Ff[2]);
+            const float tb = fabsf(G.Ff[3]) * x1f + fabsf(G.Ff[4]) * y1f + fabsf(G.Ff[5]);
+            const float tc = fabsf(G.Ff[6]) * x1f + fabsf(G.Ff[7]) * y1f + fabsf(G.Ff[8]);
+            const float af = (float)a, bf = (float)b;
+            const float N = sqrtf(af * af + bf * bf);
+            const bool usable = isfinite(N) && isfinite(c) && N > 1e-6f * (ta + tb) && N > 1e-30f;
+            if (!usable) {
+                // tiny or overflowing line: decide degeneracy exactly as the
+                // brute force (a^2 + b^2 == 0 in its evaluation order)
+                double ea, eb, ec;
+                exact_line(P.F, x1, y1, ea, eb, ec);
+                if (exact_norm(ea, eb) == 0.0) r.flags = EGM_FLAG_DEGENERATE_LINE;
+                else r.flags = kQExactOnly;
             } else {
-                const double inv = 1.0 / N;
-                double A = a * inv, B = b * inv, C = (a * G.cx + b * G.cy + c) * inv;
+                const float invN = 1.0f / N;
+                const double Cn = fma(a, G.cx, fma(b, G.cy, c));
+                float A = af * invN, B = bf * invN, C = (float)Cn * invN;
+                // the oracle's line differs from (a, b, c) by at most ~2 ulps of the terms
+                const float da = 8.9e-16f * ta, db = 8.9e-16f * tb, dc = 8.9e-16f * tc;
+                r.E0 = (da * (float)G.cx + db * (float)G.cy + dc) * invN * 1.001f;
+                r.E1 = (da + db) * invN * 1.001f;
                 if (G.mode == kModeAngular) {
-                    const double tx = B, ty = -A;  // line direction
-                    double px = tx * G.ux + ty * G.uy;
-                    double py = G.ux * ty - G.uy * tx;
-                    if (px < 0.0 || (px == 0.0 && py > 0.0)) { px = -px; py = -py; }
-                    r.key = atan2f((float)py, (float)px);
-                    // distance of the computed epipole from the line, plus a
-                    // bound on its FP64 rounding error
-                    const double ta = a * G.xe, tb = b * G.ye;
-                    const double rr = fabs(ta + tb + c) * inv;
-                    const double err = 4.5e-16 * (fabs(ta) + fabs(tb) + fabs(c)) * inv;
-                    r.aux0 = __double2float_ru((rr + err) * (1.0 + 1e-12) + 1e-9);
+                    // distance of the computed epipole from the line, rounded up
+                    const double rn = fma(a, G.xe, fma(b, G.ye, c));
+                    const float xe = fabsf((float)G.xe), ye = fabsf((float)G.ye);
+                    const float rerr = 2.0e-15f * (ta * xe + tb * ye + tc);
+                    r.aux0 = (fabsf((float)rn) + rerr) * invN * 1.00001f + 1e-12f;
+                    // line direction (B, -A) in the frame of u, reduced mod pi
+                    r.key = fold_atan2(B * G.ux - A * G.uy, -(G.ux * A + G.uy * B));
                 } else {
-                    const double nx = -G.uy, ny = G.ux;
-                    double cphi = A * nx + B * ny;
-                    if (cphi < 0.0) { A = -A; B = -B; C = -C; cphi = -cphi; }
-                    const double sphi = fabs(A * G.ux + B * G.uy);
-                    r.aux0 = __double2float_rd(cphi);
-                    r.aux1 = __double2float_ru(sphi);
-                    r.key = cphi > 0.5 ? (float)(-C / cphi) : 0.0f;
+                    float cphi = -A * G.uy + B * G.ux;
+                    if (cphi < 0.0f) { A = -A; B = -B; C = -C; cphi = -cphi; }
+                    const float sphi = fabsf(A * G.ux + B * G.uy);
+                    r.aux0 = cphi * (1.0f - 1e-6f);
+                    r.aux1 = sphi * (1.0f + 1e-6f) + 1e-12f;
+                    r.key = cphi > 0.5f ? -C / cphi : 0.0f;
                 }
-                r.A = (float)A;
-                r.B = (float)B;
-                r.C = (float)C;
-                if (!isfinite(r.C) || !isfinite(r.key)) r.flags = EGM_FLAG_DEGENERATE_LINE;
+                r.A = A;
+                r.B = B;
+                r.C = C;
+                if (!isfinite(r.C) || !isfinite(r.key)) r.flags = kQExactOnly;
             }
             L.qrec[gq] = r;
         }

@@ -17,7 +17,11 @@
 //
 // The block also derives, from the level counts of the prep kernel, each
 // level's first sorted position, bucket-table size and table offset.
+#include <cooperative_groups.h>
+
 #include "egm_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace egm {
 
@@ -218,27 +222,193 @@ __global__ void __launch_bounds__(kSortThreads, 1) sort_kernel(Launch L) {
     const PairDesc &P = L.pairs[p];
     PairGeom &G = L.geom[p];
 
-    // Level layout: first sorted position, bucket bits and table offset.
-    if (threadIdx.x == 0) {
-        uint32_t pos = 0, toff = 0;
-        for (int l = 0; l < kLevels; l++) {
-            const uint32_t c = G.cnt[l];
-            G.start[l] = pos;
-            int bits = 0;
-            if (c > 1) {
-                bits = 32 - __clz(c - 1) + 1;  // ~2 buckets per member
-                if (bits > kQBits - kFirstShift) bits = kQBits - kFirstShift;  // the sorted bits
-            }
-            G.bits[l] = bits;
-            G.tab[l] = toff;
-            toff += (1u << bits) + 1u;
-            pos += c;
-        }
-        G.start[kLevels] = pos;
-    }
+    if (P.n <= kClusterMaxN) return;  // sorted by the cluster kernel
+    if (threadIdx.x == 0) level_layout(G.cnt, G.start, G.bits, G.tab, kQBits - kFirstShift);
     const int64_t b = P.r_off;
     block_radix_sort(S, L.key_a + b, L.val_a + b, L.key_c + b, L.val_c + b, L.key_b + b, L.val_b + b, P.n,
                      kFirstShift, kPasses);
+}
+
+// ---------------------------------------------------------------------------
+// Cluster sort: the eight blocks of a thread-block cluster sort one pair.
+// Block r owns sorted positions [r*chunk, (r+1)*chunk).  Per pass every block
+// ranks its elements (ballot multi-split per warp), publishes its 128 digit
+// totals in shared memory, reads all blocks' totals through distributed
+// shared memory to place its elements, and stores each element straight into
+// the shared memory of the block that owns its new position.  After the last
+// pass the blocks write the sorted keys, the FP32 records and the bucket
+// tables (the work of post_sort_kernel) for their positions.
+constexpr int kCWarps = kClusterThreads / 32;
+constexpr int kCChunk = kClusterThreads * kClusterItems;
+
+struct ClusterSmem {
+    uint32_t rkey[kCChunk];
+    uint32_t rval[kCChunk];
+    uint32_t whist[kCWarps * kBins];
+    uint32_t hist[kBins];      // this block's digit totals, read by the whole cluster
+    uint32_t tot[kBins];
+    uint32_t base[kBins];
+    uint32_t start[kLevels + 1];
+    int32_t bits[kLevels];
+    uint32_t tab[kLevels];
+};
+
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads)
+    cluster_sort_kernel(Launch L) {
+    __shared__ __align__(16) ClusterSmem S;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int p = blockIdx.x / kClusterCtas;
+    const PairDesc &P = L.pairs[p];
+    PairGeom &G = L.geom[p];
+    const int n = P.n;
+    if (n <= 0 || n > kClusterMaxN) return;  // the same for every block of the cluster
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int items = (n + kClusterCtas * kClusterThreads - 1) / (kClusterCtas * kClusterThreads);
+    const int chunk = items * kClusterThreads;
+    const int wspan = items * 32;
+    const uint32_t lt = lanemask_lt();
+    if (threadIdx.x == 0) {
+        level_layout(G.cnt, S.start, S.bits, S.tab, kQBits - kFirstShift);
+        if (rank == 0) {
+            for (int l = 0; l < kLevels; l++) {
+                G.start[l] = S.start[l];
+                G.bits[l] = S.bits[l];
+                G.tab[l] = S.tab[l];
+            }
+            G.start[kLevels] = S.start[kLevels];
+        }
+    }
+    const int64_t b = P.r_off;
+    uint32_t key[kClusterItems], val[kClusterItems], rk[kClusterItems / 2];
+#pragma unroll
+    for (int k = 0; k < kClusterItems; k++) {
+        key[k] = 0xffffffffu;
+        val[k] = 0u;
+        if (k < items) {
+            const int e = rank * chunk + warp * wspan + k * 32 + lane;
+            if (e < n) {
+                key[k] = L.key_a[b + e];
+                val[k] = L.val_a[b + e];
+            }
+        }
+    }
+    for (int pass = 0; pass < kPasses; pass++) {
+        const int shift = kFirstShift + pass * kRBits;
+        if (pass > 0) {
+#pragma unroll
+            for (int k = 0; k < kClusterItems; k++)
+                if (k < items) {
+                    const int e = warp * wspan + k * 32 + lane;
+                    key[k] = S.rkey[e];
+                    val[k] = S.rval[e];
+                }
+        }
+        uint32_t *wh = S.whist + warp * kBins;
+        for (int d = lane; d < kBins; d += 32) wh[d] = 0u;
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < kClusterItems; k++) {
+            if (k < items) {
+                const uint32_t dg = digit_of(key[k], shift);
+                uint32_t peers = 0xffffffffu;
+#pragma unroll
+                for (int bit = 0; bit < kRBits; bit++) {
+                    const uint32_t bal = __ballot_sync(0xffffffffu, (dg >> bit) & 1u);
+                    peers &= ((dg >> bit) & 1u) ? bal : ~bal;
+                }
+                const uint32_t before = wh[dg];
+                const uint32_t r = before + __popc(peers & lt);
+                if (k & 1) rk[k >> 1] |= r << 16; else rk[k >> 1] = r;
+                __syncwarp();
+                if ((peers & lt) == 0u) wh[dg] = before + __popc(peers);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < kBins) {
+            uint32_t acc = 0;
+#pragma unroll
+            for (int w = 0; w < kCWarps; w++) {
+                uint32_t *c = S.whist + w * kBins + threadIdx.x;
+                const uint32_t v = *c;
+                *c = acc;
+                acc += v;
+            }
+            S.hist[threadIdx.x] = acc;
+        }
+        cluster.sync();  // all totals published; every block has read its receive buffer
+        if (threadIdx.x < kBins) {
+            uint32_t tot = 0, pre = 0;
+            for (int c = 0; c < kClusterCtas; c++) {
+                const uint32_t v = cluster.map_shared_rank(S.hist, c)[threadIdx.x];
+                tot += v;
+                if (c < rank) pre += v;
+            }
+            S.tot[threadIdx.x] = tot;
+            S.base[threadIdx.x] = pre;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t v[4], sum = 0;
+#pragma unroll
+            for (int q = 0; q < 4; q++) { v[q] = S.tot[lane * 4 + q]; sum += v[q]; }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            uint32_t acc = incl - sum;
+#pragma unroll
+            for (int q = 0; q < 4; q++) { S.base[lane * 4 + q] += acc; acc += v[q]; }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kClusterItems; k++) {
+            if (k < items) {
+                const uint32_t dg = digit_of(key[k], shift);
+                const uint32_t r = (rk[k >> 1] >> ((k & 1) * 16)) & 0xffffu;
+                const uint32_t pos = S.base[dg] + wh[dg] + r;
+                const int dest = (int)(pos / (uint32_t)chunk);
+                const uint32_t off = pos - (uint32_t)dest * (uint32_t)chunk;
+                cluster.map_shared_rank(S.rkey, dest)[off] = key[k];
+                cluster.map_shared_rank(S.rval, dest)[off] = val[k];
+            }
+        }
+        cluster.sync();  // every element has landed in its owner's buffer
+    }
+
+    // sorted keys, FP32 records and bucket tables for this block's positions
+    const PairGeom &Gc = G;
+    const double cx = Gc.cx, cy = Gc.cy;
+    for (int i = threadIdx.x; i < chunk; i += kClusterThreads) {
+        const int pos = rank * chunk + i;
+        if (pos >= n) break;
+        const uint32_t kk = S.rkey[i];
+        const uint32_t j = S.rval[i];
+        L.key_b[b + pos] = kk;
+        L.val_b[b + pos] = j;
+        const double x = P.xy2[2 * (int64_t)j], y = P.xy2[2 * (int64_t)j + 1];
+        const double eps = P.eps2 ? P.eps2[j] : P.eps_scalar;
+        L.rec[b + pos] = make_float4((float)(x - cx), (float)(y - cy), (float)eps, __uint_as_float(j));
+        const int lv = (int)(kk >> kQBits);
+        const uint32_t s0 = S.start[lv], e0 = S.start[lv + 1];
+        const int sh = kQBits - S.bits[lv];
+        uint32_t *T = L.tab + P.t_off + S.tab[lv];
+        const int64_t bk = (int64_t)((kk & kQMax) >> sh);
+        int64_t bp = -1;
+        if ((uint32_t)pos != s0) {
+            const uint32_t prev = i > 0 ? S.rkey[i - 1] : cluster.map_shared_rank(S.rkey, rank - 1)[chunk - 1];
+            bp = (int64_t)((prev & kQMax) >> sh);
+        }
+        for (int64_t bb = bp + 1; bb <= bk; bb++) T[bb] = (uint32_t)pos;
+        if ((uint32_t)pos == e0 - 1) {
+            const int64_t nb = (int64_t)1 << S.bits[lv];
+            for (int64_t bb = bk + 1; bb <= nb; bb++) T[bb] = e0;
+        }
+    }
+    cluster.sync();  // keep this block's shared memory alive for its neighbour's reads
 }
 
 // Candidate rows longer than a warp sorts: one block sorts them one after the
@@ -262,9 +432,11 @@ __global__ void __launch_bounds__(kSortThreads, 1) long_row_sort_kernel(Launch L
 }  // namespace
 
 cudaError_t launch_sort(const Launch &L, int max_n, cudaStream_t s) {
-    (void)max_n;
+    cluster_sort_kernel<<<L.npairs * kClusterCtas, kClusterThreads, 0, s>>>(L);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || max_n <= kClusterMaxN) return e;
     const int smem = (int)sizeof(SortSmem);
-    cudaError_t e = cudaFuncSetAttribute(sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     sort_kernel<<<L.npairs, kSortThreads, smem, s>>>(L);
     return cudaGetLastError();

@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(256) post_sort_kernel(Launch L) {
          g += (int64_t)gridDim.x * blockDim.x) {
         const int p = pair_of(L.r_offs, L.npairs, g);
         const PairDesc &P = L.pairs[p];
+        if (P.n <= kClusterMaxN) continue;  // done by the cluster sort
         const PairGeom &G = L.geom[p];
         const uint32_t pos = (uint32_t)(g - P.r_off);
         const uint32_t key = L.key_b[g];
@@ -101,25 +102,28 @@ constexpr int kStabWarps = 8;
 constexpr int kMaxRowBytes = 2048;
 
 struct Window {
-    uint32_t b0, len0, b1, len1;  // two ranges of sorted positions (pair-relative)
-    uint32_t qlo0, qhi0, qlo1, qhi1;
+    uint32_t b0, len0, b1, len1;  // up to two disjoint ranges of sorted positions (pair-relative)
 };
 
 __device__ __forceinline__ void level_window(const Launch &L, const PairDesc &P, const PairGeom &G,
                                              const QueryRec &r, int lv, Window &w) {
     w.b0 = w.len0 = w.b1 = w.len1 = 0;
-    w.qlo0 = w.qlo1 = 0;
-    w.qhi0 = w.qhi1 = kQMax;
     if (lv >= kLevels) return;
     const uint32_t cnt = G.cnt[lv];
     if (cnt == 0) return;
     const uint32_t s = G.start[lv], e = G.start[lv + 1];
     const float smax = __uint_as_float(G.smax[lv]);
-    bool full;
+    // R: largest |p - c| of the level; the FP32 keys of its members are the
+    // exact keys of points moved by at most `dpos` pixels.
+    const float R = __uint_as_float(G.tmax[lv]);
+    const float u = 5.9604645e-8f;
+    bool full = (r.flags & kQExactOnly) != 0;
     float lo = 0.0f, hi = 0.0f;
-    if (G.mode == kModeAngular) {
+    if (full) {
+    } else if (G.mode == kModeAngular) {
+        const float dpos = 8.0f * u * R + 4.0f * u * fminf(G.de, R) + 2.0f * u * fabsf(G.kappa) + 1e-9f;
         const float dmin = __uint_as_float(G.dmin[lv]);
-        const float sigma = (dmin > 0.0f) ? (smax + r.aux0 / dmin) * 1.000001f : INFINITY;
+        const float sigma = (dmin > 0.0f) ? (smax + (r.aux0 + dpos) / dmin) * 1.000001f : INFINITY;
         full = !(sigma < 1.0f);
         if (!full) {
             const float wv = asinf(sigma) * 1.000001f + 1e-37f;
@@ -129,10 +133,9 @@ __device__ __forceinline__ void level_window(const Launch &L, const PairDesc &P,
             hi = r.key + hw;
         }
     } else {
-        const float tmax = __uint_as_float(G.tmax[lv]);
         full = !(r.aux0 >= 0.5f);
         if (!full) {
-            const float wv = (smax + tmax * r.aux1) / r.aux0 * 1.000001f;
+            const float wv = (smax + R * r.aux1 + 8.0f * u * R + 1e-9f) / r.aux0 * 1.000001f;
             const float hw = wv + (1e-6f * (fabsf(r.key) + wv) + 1e-6f);
             full = !isfinite(hw);
             lo = r.key - hw;
@@ -144,36 +147,40 @@ __device__ __forceinline__ void level_window(const Launch &L, const PairDesc &P,
         w.len0 = e - s;
         return;
     }
+    // Whole buckets around the window: a superset of the keypoints whose key
+    // lies in it (the exact test decides membership).
     const int sh = kQBits - G.bits[lv];
     const uint32_t *T = L.tab + P.t_off + G.tab[lv];
-    auto range = [&](uint32_t qlo, uint32_t qhi, uint32_t &b, uint32_t &len) {
-        const uint32_t pb = __ldg(T + (qlo >> sh));
-        const uint32_t pe = __ldg(T + (qhi >> sh) + 1);
-        b = pb;
-        len = pe > pb ? pe - pb : 0;
-    };
     if (G.mode == kModeAngular && (lo < -kHalfPiF || hi >= kHalfPiF)) {
         // the window crosses the seam of the [-pi/2, pi/2) domain (Sec. 4.4,
-        // "Discontinuity at 0/pi"): split it in two disjoint key ranges
+        // "Discontinuity at 0/pi"): the high part [qa, end) of the level and
+        // the low part [start, qb]
         const bool low = lo < -kHalfPiF;
-        w.qlo0 = qmap(low ? lo + kPiF : lo, G.kmin, G.kscale);
-        w.qhi0 = kQMax;
-        w.qlo1 = 0;
-        w.qhi1 = qmap(low ? hi : hi - kPiF, G.kmin, G.kscale);
-        if (w.qhi1 >= w.qlo0) {  // the two parts meet: scan the whole level once
-            w.qlo0 = 0;
-            w.qhi1 = kQMax;
-            w.b0 = s;
-            w.len0 = e - s;
-            return;
-        }
-        range(w.qlo0, w.qhi0, w.b0, w.len0);
-        range(w.qlo1, w.qhi1, w.b1, w.len1);
+        const uint32_t qa = qmap(low ? lo + kPiF : lo, G.kmin, G.kscale);
+        const uint32_t qb = qmap(low ? hi : hi - kPiF, G.kmin, G.kscale);
+        const uint32_t pa = __ldg(T + (qa >> sh));
+        uint32_t pb = __ldg(T + (qb >> sh) + 1);
+        if (pb > pa) pb = pa;  // a shared edge bucket is visited once
+        w.b0 = pa;
+        w.len0 = e - pa;
+        w.b1 = s;
+        w.len1 = pb > s ? pb - s : 0;
     } else {
-        w.qlo0 = qmap(lo, G.kmin, G.kscale);
-        w.qhi0 = qmap(hi, G.kmin, G.kscale);
-        range(w.qlo0, w.qhi0, w.b0, w.len0);
+        const uint32_t pa = __ldg(T + (qmap(lo, G.kmin, G.kscale) >> sh));
+        const uint32_t pb = __ldg(T + (qmap(hi, G.kmin, G.kscale) >> sh) + 1);
+        w.b0 = pa;
+        w.len0 = pb > pa ? pb - pa : 0;
     }
+}
+
+// The brute-force FP64 decision for one (query, reference) pair, kept out of
+// line: it runs only when the FP32 test is inconclusive.
+__device__ __noinline__ bool exact_pair(const PairDesc &P, int64_t i, uint32_t j) {
+    double a, b, c;
+    exact_line(P.F, P.xy1[2 * i], P.xy1[2 * i + 1], a, b, c);
+    const double N = exact_norm(a, b);
+    const double eps = P.eps2 ? P.eps2[j] : P.eps_scalar;
+    return exact_member(a, b, c, N, P.xy2[2 * (int64_t)j], P.xy2[2 * (int64_t)j + 1], eps);
 }
 
 // mode 0: fused matching; 1: count candidates; 2: write candidate rows and match.
@@ -184,6 +191,7 @@ __device__ void stab_query(const Launch &L, int mode, int64_t gq, uint4 *qbuf, i
     const PairGeom &G = L.geom[p];
     const int64_t i = gq - P.q_off;
     const QueryRec r = L.qrec[gq];
+    const bool exact_only = (r.flags & kQExactOnly) != 0;
     const bool match = mode != 1 && P.row_bytes > 0;
     const int chunks = P.row_bytes >> 4;
 
@@ -209,10 +217,7 @@ __device__ void stab_query(const Launch &L, int mode, int64_t gq, uint4 *qbuf, i
             if (lane >= o) incl += t;
         }
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        const uint32_t *skey = L.key_b + P.r_off;
         const float4 *srec = L.rec + P.r_off;
-        bool have_exact = false;
-        double ea = 0.0, eb = 0.0, ec = 0.0, eN = 1.0;
         for (uint32_t base = 0; base < total; base += 32) {
             const uint32_t f = base + lane;
             // owner lane: number of lanes whose inclusive prefix is <= f
@@ -226,37 +231,29 @@ __device__ void stab_query(const Launch &L, int mode, int64_t gq, uint4 *qbuf, i
             const uint32_t ob0 = __shfl_sync(0xffffffffu, w.b0, o);
             const uint32_t ol0 = __shfl_sync(0xffffffffu, w.len0, o);
             const uint32_t ob1 = __shfl_sync(0xffffffffu, w.b1, o);
-            const uint32_t oql0 = __shfl_sync(0xffffffffu, w.qlo0, o);
-            const uint32_t oqh0 = __shfl_sync(0xffffffffu, w.qhi0, o);
-            const uint32_t oql1 = __shfl_sync(0xffffffffu, w.qlo1, o);
-            const uint32_t oqh1 = __shfl_sync(0xffffffffu, w.qhi1, o);
             bool cand = false;
             uint32_t jc = 0;
             if (f < total) {
                 const uint32_t off = f - excl;
-                const bool first = off < ol0;
-                const uint32_t pos = first ? ob0 + off : ob1 + (off - ol0);
-                const uint32_t q = __ldg(skey + pos) & kQMax;
-                const bool inwin = first ? (q >= oql0 && q <= oqh0) : (q >= oql1 && q <= oqh1);
-                if (inwin) {
+                const uint32_t pos = off < ol0 ? ob0 + off : ob1 + (off - ol0);
+                {
                     nwin++;
                     const float4 rc = __ldg(srec + pos);
                     const float t = fmaf(r.A, rc.x, fmaf(r.B, rc.y, r.C));
                     const float d = fabsf(t);
                     const float S = fmaf(fabsf(r.A), fabsf(rc.x), fmaf(fabsf(r.B), fabsf(rc.y), fabsf(r.C)));
-                    const float bound = fmaf(4.8e-7f, S, fmaf(1.2e-7f, rc.z, 1e-9f));
-                    if (d <= rc.z - bound) {
+                    // FP32 rounding (16u S), the FP32 tolerance (2u eps) and the
+                    // distance between this line and the brute force's FP64 line
+                    const float lerr = fmaf(r.E1, fabsf(rc.x) + fabsf(rc.y) + 2.0f * rc.z, r.E0);
+                    const float bound = fmaf(9.6e-7f, S, fmaf(1.2e-7f, rc.z, lerr + 1e-9f));
+                    if (exact_only) {
+                        cand = exact_pair(P, i, __float_as_uint(rc.w));
+                        nexact++;
+                    } else if (d <= rc.z - bound) {
                         cand = true;
                     } else if (!(d > rc.z + bound)) {
                         // FP32 inconclusive: the brute-force FP64 expression decides.
-                        if (!have_exact) {
-                            exact_line(P.F, P.xy1[2 * i], P.xy1[2 * i + 1], ea, eb, ec);
-                            eN = exact_norm(ea, eb);
-                            have_exact = true;
-                        }
-                        const uint32_t j = __float_as_uint(rc.w);
-                        const double eps = P.eps2 ? P.eps2[j] : P.eps_scalar;
-                        cand = exact_member(ea, eb, ec, eN, P.xy2[2 * (int64_t)j], P.xy2[2 * (int64_t)j + 1], eps);
+                        cand = exact_pair(P, i, __float_as_uint(rc.w));
                         nexact++;
                     }
                     if (cand) {
@@ -339,7 +336,7 @@ __device__ void stab_query(const Launch &L, int mode, int64_t gq, uint4 *qbuf, i
     }
 }
 
-__global__ void __launch_bounds__(kStabWarps * 32) stab_kernel(Launch L, int mode) {
+__global__ void __launch_bounds__(kStabWarps * 32, 4) stab_kernel(Launch L, int mode) {
     __shared__ __align__(16) uint4 qbuf_all[kStabWarps][kMaxRowBytes / 16];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint4 *qbuf = qbuf_all[warp];
@@ -356,7 +353,7 @@ __global__ void __launch_bounds__(kStabWarps * 32) stab_kernel(Launch L, int mod
 }  // namespace
 
 cudaError_t launch_post_sort(const Launch &L, cudaStream_t s) {
-    if (L.nr == 0) return cudaSuccess;
+    if (L.nr == 0 || L.max_n <= kClusterMaxN) return cudaSuccess;
     int64_t blocks = (L.nr + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     post_sort_kernel<<<(int)blocks, 256, 0, s>>>(L);

@@ -181,6 +181,7 @@ extern "C" egm_status egm_match_pair_static(const egm_pair *P, const egm_out *ou
     L.scan_tmp = reinterpret_cast<int64_t *>(base + kOffScan);
     L.ratio_num = rn;
     L.ratio_den = rd;
+    L.max_n = P->n;
     L.best = out->best;
     L.second = out->second;
     L.best_d = out->best_d;
