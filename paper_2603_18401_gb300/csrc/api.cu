@@ -44,7 +44,7 @@ struct egm_ctx {
     bool counters_on = false;
     egm_stats last{};
     // scratch
-    DevBuf pairs, geom, offs, keys, rec, tab, qrec, qcount, scan, longlist, small, counters;
+    DevBuf pairs, geom, offs, keys, rec, tab, qrec, qcount, scan, longlist, small, counters, blkpair;
     DevBuf stage;  // host-path staging of inputs and outputs
     // pinned host memory for the pair table and the status word
     void *h_table = nullptr;
@@ -183,6 +183,7 @@ cudaError_t reserve(egm_ctx *c, int64_t nq, int64_t nr, int64_t ntab, int npairs
     if ((e = grow(c->qcount, sizeof(int64_t) * (size_t)(nq + 1))) != cudaSuccess) return e;
     if ((e = grow(c->scan, sizeof(int64_t) * (size_t)(nq / 8192 + 2))) != cudaSuccess) return e;
     if ((e = grow(c->longlist, sizeof(uint32_t) * (size_t)(nq + 1))) != cudaSuccess) return e;
+    if ((e = grow(c->blkpair, sizeof(int32_t) * (size_t)(nq / kStabQB + 2))) != cudaSuccess) return e;
     if ((e = grow(c->small, 256)) != cudaSuccess) return e;
     if ((e = grow(c->counters, 8 * sizeof(unsigned long long))) != cudaSuccess) return e;
     return cudaSuccess;
@@ -213,9 +214,13 @@ Launch make_launch(egm_ctx *c, const Plan &pl, int npairs, const egm_out *out) {
     L.counters = c->counters_on ? as<unsigned long long>(c->counters) : nullptr;
     L.qcount = as<int64_t>(c->qcount);
     L.scan_tmp = as<int64_t>(c->scan);
+    L.blkpair = as<int32_t>(c->blkpair);
     L.ratio_num = c->params.ratio_num;
     L.ratio_den = c->params.ratio_den;
     L.max_n = pl.max_n;
+    L.kind = pl.pd.empty() ? -1 : pl.pd[0].kind;
+    for (const PairDesc &d : pl.pd)
+        if (d.kind != L.kind) L.kind = -1;
     if (out) {
         L.best = out->best;
         L.second = out->second;
@@ -373,7 +378,7 @@ egm_status egm_destroy(egm_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     DevBuf *bufs[] = {&c->pairs, &c->geom, &c->offs, &c->keys, &c->rec, &c->tab, &c->qrec, &c->qcount,
-                      &c->scan, &c->longlist, &c->small, &c->counters, &c->stage};
+                      &c->scan, &c->longlist, &c->small, &c->counters, &c->stage, &c->blkpair};
     for (DevBuf *b : bufs)
         if (b->ptr) cudaFree(b->ptr);
     if (c->h_table) cudaFreeHost(c->h_table);

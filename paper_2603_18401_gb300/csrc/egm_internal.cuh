@@ -38,7 +38,7 @@ enum : uint32_t {
 
 enum : int32_t { kModeAngular = 0, kModeParallel = 1 };
 
-struct PairDesc {
+struct __align__(16) PairDesc {
     const double *xy1;
     const double *xy2;
     const double *F;
@@ -56,7 +56,7 @@ struct PairDesc {
     int64_t t_cap;      // bucket-table entries reserved for this pair
 };
 
-struct PairGeom {
+struct __align__(16) PairGeom {
     double ex, ey, ew;          // homogeneous epipole, unit norm, ew >= 0
     double xe, ye;              // Euclidean epipole (angular mode)
     double cx, cy;              // frame origin: image centre
@@ -79,6 +79,9 @@ struct PairGeom {
     int32_t bits[kLevels];        // bucket bits of each level
 };
 
+static_assert(sizeof(PairGeom) % 16 == 0, "PairGeom is copied in 16-byte units");
+static_assert(sizeof(PairDesc) % 16 == 0, "PairDesc is copied in 16-byte units");
+
 // Query flags beyond the public EGM_FLAG_* bits.
 enum : uint32_t { kQExactOnly = 0x100u };  // FP32 view unusable: whole levels, FP64 decides every pair
 
@@ -90,8 +93,12 @@ struct __align__(16) QueryRec {
     float aux1;         // parallel: |sin(phi)|
     float E0, E1;       // line error terms of the pre-test: E0 + E1 (|x'| + |y'| + 2 eps)
     uint32_t flags;     // EGM_FLAG_DEGENERATE_LINE, kQExactOnly
-    uint32_t pad[3];
+    int32_t pair;       // pair of this query
+    uint32_t pad[2];
 };
+
+// Queries per block of the stabbing kernel.
+constexpr int kStabQB = 32;
 
 struct Launch {
     const PairDesc *pairs;
@@ -116,8 +123,10 @@ struct Launch {
     int64_t *cand_total;
     int64_t *qcount;              // per-query candidate counts (CSR path)
     int64_t *scan_tmp;            // scan partials
+    int32_t *blkpair;             // pair of query kStabQB * b, written by the prep kernel
     int32_t ratio_num, ratio_den;
     int32_t max_n;                // largest reference count of the batch
+    int32_t kind;                 // descriptor kind shared by every pair, or -1 when mixed
 };
 
 // Pairs with at most this many references are sorted by one thread-block

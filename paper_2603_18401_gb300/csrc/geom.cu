@@ -229,7 +229,9 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
             const double x1 = P.xy1[2 * i], y1 = P.xy1[2 * i + 1];
             QueryRec r;
             r.flags = 0;
-            r.pad[0] = r.pad[1] = r.pad[2] = 0;
+            r.pair = p;
+            r.pad[0] = r.pad[1] = 0;
+            if (gq % kStabQB == 0) L.blkpair[gq / kStabQB] = p;
             r.A = r.B = r.C = r.key = r.aux0 = r.aux1 = r.E0 = r.E1 = 0.0f;
             if (!(isfinite(x1) && isfinite(y1))) set_status(L.status, kStNan);
             const double *F = P.F;

@@ -55,63 +55,25 @@ __global__ void __launch_bounds__(256) post_sort_kernel(Launch L) {
 
 // ------------------------------------------------------------ descriptors
 
-template <int KIND>
-__device__ __forceinline__ uint32_t desc_dist(const uint4 *__restrict__ q, const uint4 *__restrict__ r,
-                                              int chunks) {
-    if (KIND == EGM_DESC_U8_L2) {
-        uint32_t acc = 0;
-        for (int c = 0; c < chunks; c++) {
-            const uint4 a = q[c];
-            const uint4 b = __ldg(r + c);
-            uint32_t d;
-            d = __vabsdiffu4(a.x, b.x); acc = __dp4a(d, d, acc);
-            d = __vabsdiffu4(a.y, b.y); acc = __dp4a(d, d, acc);
-            d = __vabsdiffu4(a.z, b.z); acc = __dp4a(d, d, acc);
-            d = __vabsdiffu4(a.w, b.w); acc = __dp4a(d, d, acc);
-        }
-        return acc;
-    } else if (KIND == EGM_DESC_BIN) {
-        uint32_t acc = 0;
-        for (int c = 0; c < chunks; c++) {
-            const uint4 a = q[c];
-            const uint4 b = __ldg(r + c);
-            acc += __popc(a.x ^ b.x) + __popc(a.y ^ b.y) + __popc(a.z ^ b.z) + __popc(a.w ^ b.w);
-        }
-        return acc;
-    } else {
-        float acc = 0.0f;
-        for (int c = 0; c < chunks; c++) {
-            const float4 a = reinterpret_cast<const float4 *>(q)[c];
-            const float4 b = __ldg(reinterpret_cast<const float4 *>(r) + c);
-            float d;
-            d = a.x - b.x; acc = fmaf(d, d, acc);
-            d = a.y - b.y; acc = fmaf(d, d, acc);
-            d = a.z - b.z; acc = fmaf(d, d, acc);
-            d = a.w - b.w; acc = fmaf(d, d, acc);
-        }
-        return __float_as_uint(acc);  // non-negative: bit order = value order
-    }
-}
-
-__device__ __forceinline__ void top2_insert(unsigned long long &b1, unsigned long long &b2, unsigned long long k) {
-    if (k < b1) { b2 = b1; b1 = k; }
-    else if (k < b2) { b2 = k; }
-}
-
-constexpr int kStabWarps = 8;
-constexpr int kMaxRowBytes = 2048;
-
 struct Window {
     uint32_t b0, len0, b1, len1;  // up to two disjoint ranges of sorted positions (pair-relative)
 };
 
-__device__ __forceinline__ void level_window(const Launch &L, const PairDesc &P, const PairGeom &G,
-                                             const QueryRec &r, int lv, Window &w) {
-    w.b0 = w.len0 = w.b1 = w.len1 = 0;
-    if (lv >= kLevels) return;
-    const uint32_t cnt = G.cnt[lv];
-    if (cnt == 0) return;
-    const uint32_t s = G.start[lv], e = G.start[lv + 1];
+// Window of level `lv` for query r, first without the bucket-table loads so
+// that a warp can issue the loads of several queries together.
+struct WinKeys {
+    uint32_t s, e;     // the level's sorted positions [s, e)
+    uint32_t ta, tb;   // bucket-table indices
+    int kind;          // 0 empty, 1 whole level, 2 [T[ta], T[tb]), 3 seam: [T[ta], e) and [s, T[tb])
+};
+
+__device__ __forceinline__ WinKeys window_keys(const PairGeom &G, const QueryRec &r, int lv) {
+    WinKeys k;
+    k.kind = 0;
+    k.s = k.e = k.ta = k.tb = 0;
+    if (lv >= kLevels || (r.flags & EGM_FLAG_DEGENERATE_LINE) || G.cnt[lv] == 0) return k;
+    k.s = G.start[lv];
+    k.e = G.start[lv + 1];
     const float smax = __uint_as_float(G.smax[lv]);
     // R: largest |p - c| of the level; the FP32 keys of its members are the
     // exact keys of points moved by at most `dpos` pixels.
@@ -143,34 +105,45 @@ __device__ __forceinline__ void level_window(const Launch &L, const PairDesc &P,
         }
     }
     if (full) {
-        w.b0 = s;
-        w.len0 = e - s;
-        return;
+        k.kind = 1;
+        return k;
     }
     // Whole buckets around the window: a superset of the keypoints whose key
     // lies in it (the exact test decides membership).
     const int sh = kQBits - G.bits[lv];
-    const uint32_t *T = L.tab + P.t_off + G.tab[lv];
     if (G.mode == kModeAngular && (lo < -kHalfPiF || hi >= kHalfPiF)) {
         // the window crosses the seam of the [-pi/2, pi/2) domain (Sec. 4.4,
         // "Discontinuity at 0/pi"): the high part [qa, end) of the level and
         // the low part [start, qb]
         const bool low = lo < -kHalfPiF;
-        const uint32_t qa = qmap(low ? lo + kPiF : lo, G.kmin, G.kscale);
-        const uint32_t qb = qmap(low ? hi : hi - kPiF, G.kmin, G.kscale);
-        const uint32_t pa = __ldg(T + (qa >> sh));
-        uint32_t pb = __ldg(T + (qb >> sh) + 1);
-        if (pb > pa) pb = pa;  // a shared edge bucket is visited once
-        w.b0 = pa;
-        w.len0 = e - pa;
-        w.b1 = s;
-        w.len1 = pb > s ? pb - s : 0;
+        k.ta = qmap(low ? lo + kPiF : lo, G.kmin, G.kscale) >> sh;
+        k.tb = (qmap(low ? hi : hi - kPiF, G.kmin, G.kscale) >> sh) + 1;
+        k.kind = 3;
     } else {
-        const uint32_t pa = __ldg(T + (qmap(lo, G.kmin, G.kscale) >> sh));
-        const uint32_t pb = __ldg(T + (qmap(hi, G.kmin, G.kscale) >> sh) + 1);
+        k.ta = qmap(lo, G.kmin, G.kscale) >> sh;
+        k.tb = (qmap(hi, G.kmin, G.kscale) >> sh) + 1;
+        k.kind = 2;
+    }
+    return k;
+}
+
+__device__ __forceinline__ Window window_ranges(const WinKeys &k, uint32_t pa, uint32_t pb) {
+    Window w;
+    w.b0 = w.len0 = w.b1 = w.len1 = 0;
+    if (k.kind == 1) {
+        w.b0 = k.s;
+        w.len0 = k.e - k.s;
+    } else if (k.kind == 2) {
         w.b0 = pa;
         w.len0 = pb > pa ? pb - pa : 0;
+    } else if (k.kind == 3) {
+        if (pb > pa) pb = pa;  // a shared edge bucket is visited once
+        w.b0 = pa;
+        w.len0 = k.e - pa;
+        w.b1 = k.s;
+        w.len1 = pb > k.s ? pb - k.s : 0;
     }
+    return w;
 }
 
 // The brute-force FP64 decision for one (query, reference) pair, kept out of
@@ -183,170 +156,570 @@ __device__ __noinline__ bool exact_pair(const PairDesc &P, int64_t i, uint32_t j
     return exact_member(a, b, c, N, P.xy2[2 * (int64_t)j], P.xy2[2 * (int64_t)j + 1], eps);
 }
 
+// ------------------------------------------------------------ stabbing
+//
+// One block takes kQB consecutive queries.  On GB300 a dependent global
+// access costs about a microsecond, so the kernel is organised around the
+// number of serial memory round trips per block:
+//   phase 1  (2 trips)  query records and the block's pair geometry; then
+//            the bucket-table loads of every window and the query
+//            descriptors together.  Warp w handles queries 4w .. 4w+3,
+//            lane = level; non-empty ranges are compacted into shared memory.
+//   2a (1 trip)  the concatenated window elements, a contiguous chunk per
+//            thread, record loads issued together; each passes the Eq. 3/4
+//            test (FP32 with a rigorous bound, FP64 brute-force expression
+//            when inconclusive); candidates are appended to a list with one
+//            warp-aggregated atomic.
+//   2a'      the list is counting-sorted by query into segments.
+//   2b (1 trip per 128 candidates)  a group of G lanes per candidate
+//            (G 16-byte chunks of its descriptor), four candidates per group
+//            with all loads issued first; distances go to the segment.
+//   2c       one warp per query reduces its segment into the query's best
+//            two (distance, index) keys - a single writer, no atomics.
+// Rounds of kRound elements repeat 2a-2c; the outputs follow the last round.
+constexpr int kQB = kStabQB;
+constexpr int kStabThreads = 256;
+constexpr int kRangesPerQuery = 2 * kLevels;
+constexpr int kDescCache = 256;  // query descriptors up to this many bytes are staged in shared memory
+constexpr int kBatch = 4;
+constexpr int kRound = 1024;     // window elements tested per round
+constexpr int kQPerWarp = kQB / (kStabThreads / 32);
+
+struct StabSmem {
+    uint2 rng[kQB][kRangesPerQuery];  // (first sorted position, length) of each non-empty range
+    QueryRec qr[kQB];
+    PairGeom g;                       // geometry of the block's first pair
+    PairDesc pd;                      //   and its descriptor
+    unsigned long long b1[kQB], b2[kQB];
+    uint32_t nrng[kQB];
+    uint32_t tq[kQB];
+    uint32_t eoff[kQB + 1];
+    uint32_t cnt[kQB];                // candidates per query (all rounds)
+    uint32_t rcnt[kQB];               // candidates per query in this round
+    uint32_t roff[kQB + 1];           //   their segment offsets
+    uint32_t rfill[kQB];
+    uint32_t fill[kQB];               // CSR fill counters
+    uint32_t nwin, nexact, ncand;
+    int32_t gpair;
+    uint32_t lj[kRound];              // append list: reference index
+    uint8_t lq[kRound];               //   and query slot
+    uint32_t sj[kRound];              // per-query segments: reference index
+    uint8_t sq[kRound];               //   and query slot
+    uint32_t sd[kRound];              //   and descriptor distance
+    uint32_t rmask[kQB][2];           // non-empty ranges of each query (bit k: range k)
+    int32_t lv[kLevels];              // non-empty levels of the block's pair
+    int32_t nlev;
+    uint4 qdesc[kQB][kDescCache / 16];
+};
+
+constexpr int kKindAny = -1;  // a launch that mixes descriptor kinds
+
+// Contribution of one 16-byte chunk to a descriptor distance.
+template <int KIND>
+__device__ __forceinline__ void chunk_dist(int kind, uint4 a, uint4 b, uint32_t &acc, float &facc) {
+    const int k = KIND == kKindAny ? kind : KIND;
+    if (k == EGM_DESC_U8_L2) {
+        uint32_t d;
+        d = __vabsdiffu4(a.x, b.x); acc = __dp4a(d, d, acc);
+        d = __vabsdiffu4(a.y, b.y); acc = __dp4a(d, d, acc);
+        d = __vabsdiffu4(a.z, b.z); acc = __dp4a(d, d, acc);
+        d = __vabsdiffu4(a.w, b.w); acc = __dp4a(d, d, acc);
+    } else if (k == EGM_DESC_BIN) {
+        acc += __popc(a.x ^ b.x) + __popc(a.y ^ b.y) + __popc(a.z ^ b.z) + __popc(a.w ^ b.w);
+    } else {
+        float d;
+        d = __uint_as_float(a.x) - __uint_as_float(b.x); facc = fmaf(d, d, facc);
+        d = __uint_as_float(a.y) - __uint_as_float(b.y); facc = fmaf(d, d, facc);
+        d = __uint_as_float(a.z) - __uint_as_float(b.z); facc = fmaf(d, d, facc);
+        d = __uint_as_float(a.w) - __uint_as_float(b.w); facc = fmaf(d, d, facc);
+    }
+}
+
+__device__ __forceinline__ void copy16(void *dst, const void *src, int bytes, int lane) {
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    for (int k = lane; k < bytes / 16; k += 32) d4[k] = __ldg(s4 + k);
+}
+
 // mode 0: fused matching; 1: count candidates; 2: write candidate rows and match.
 template <int KIND>
-__device__ void stab_query(const Launch &L, int mode, int64_t gq, uint4 *qbuf, int lane) {
-    const int p = pair_of(L.q_offs, L.npairs, gq);
-    const PairDesc &P = L.pairs[p];
-    const PairGeom &G = L.geom[p];
-    const int64_t i = gq - P.q_off;
-    const QueryRec r = L.qrec[gq];
-    const bool exact_only = (r.flags & kQExactOnly) != 0;
-    const bool match = mode != 1 && P.row_bytes > 0;
-    const int chunks = P.row_bytes >> 4;
-
-    unsigned long long b1 = ~0ull, b2 = ~0ull;
-    uint32_t ncand = 0, nwin = 0, nexact = 0;
-    int64_t row_off = 0;
-    if (mode == 2) row_off = L.cand_offsets[gq];
+__global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mode) {
+    __shared__ __align__(16) StabSmem S;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t lt = (1u << lane) - 1u;
     const bool write_rows = mode == 2 && L.cand_offsets[L.nq] <= L.cand_capacity;
-
-    if (!(r.flags & EGM_FLAG_DEGENERATE_LINE)) {
-        if (match) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(P.desc1 + i * (int64_t)P.row_bytes);
-            for (int c = lane; c < chunks; c += 32) qbuf[c] = __ldg(src + c);
-            __syncwarp();
+    uint32_t nwin = 0, nexact = 0;
+    if (tid == 0) { S.nwin = 0; S.nexact = 0; S.ncand = 0; }
+    for (int64_t q0 = (int64_t)blockIdx.x * kQB; q0 < L.nq; q0 += (int64_t)gridDim.x * kQB) {
+        const int nqb = (int)min((int64_t)kQB, L.nq - q0);
+        // ---- phase 1, trip 1: query records, and the first pair's geometry and descriptor
+        const int qbase = warp * kQPerWarp;
+        if (lane < 3 * kQPerWarp) {
+            const int ql = qbase + lane / 3;
+            if (ql < nqb)
+                reinterpret_cast<uint4 *>(&S.qr[ql])[lane % 3] =
+                    __ldg(reinterpret_cast<const uint4 *>(L.qrec + q0 + ql) + lane % 3);
         }
-        Window w;
-        level_window(L, P, G, r, lane, w);
-        const uint32_t len = w.len0 + w.len1;
-        uint32_t incl = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
+        if (warp == kStabThreads / 32 - 1) {
+            const int p0 = L.npairs == 1 ? 0 : L.blkpair[q0 / kQB];
+            copy16(&S.g, L.geom + p0, (int)sizeof(PairGeom), lane);
+            copy16(&S.pd, L.pairs + p0, (int)sizeof(PairDesc), lane);
+            if (lane == 0) S.gpair = p0;
         }
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        const float4 *srec = L.rec + P.r_off;
-        for (uint32_t base = 0; base < total; base += 32) {
-            const uint32_t f = base + lane;
-            // owner lane: number of lanes whose inclusive prefix is <= f
-            int o = 0;
+        __syncthreads();
+        // ---- phase 1, trip 2: windows, their bucket-table loads and the query
+        // descriptors issued together.  Lanes take (query, non-empty level)
+        // slots of the block's pair, so a pair with two populated levels costs
+        // two lanes per query, not 32; ranges go to fixed slots 2 i, 2 i + 1 of
+        // level index i (empty ones have length 0).
+        if (warp == 0) {
+            const uint32_t nz = __ballot_sync(0xffffffffu, S.g.cnt[lane] > 0);
+            if (nz & (1u << lane)) S.lv[__popc(nz & lt)] = lane;
+            if (lane == 0) S.nlev = __popc(nz);
+        }
+        if (tid < kQB) {
+            S.tq[tid] = 0;
+            S.nrng[tid] = 0;
+            S.b1[tid] = ~0ull;
+            S.b2[tid] = ~0ull;
+            S.cnt[tid] = 0;
+            S.fill[tid] = 0;
+            S.rmask[tid][0] = S.rmask[tid][1] = 0u;
+        }
+        __syncthreads();
+        constexpr int kStage = kQPerWarp * kDescCache / 16 / 32;
+        uint4 dv[kStage];
+        int dslot[kStage];
 #pragma unroll
-            for (int st = 16; st > 0; st >>= 1) {
-                const uint32_t v = __shfl_sync(0xffffffffu, incl, o + st - 1);
-                if (v <= f) o += st;
+        for (int k = 0; k < kStage; k++) {
+            const int idx = lane + 32 * k;
+            const int ql = qbase + idx / (kDescCache / 16);
+            const int c = idx % (kDescCache / 16);
+            dslot[k] = -1;
+            if (mode != 1 && ql < nqb) {
+                const int p = S.qr[ql].pair;
+                const PairDesc &P = p == S.gpair ? S.pd : L.pairs[p];
+                if (P.row_bytes > 0 && P.row_bytes <= kDescCache && c < (P.row_bytes >> 4)) {
+                    dv[k] = __ldg(reinterpret_cast<const uint4 *>(P.desc1 + (q0 + ql - P.q_off) *
+                                                                            (int64_t)P.row_bytes) + c);
+                    dslot[k] = ql * (kDescCache / 16) + c;
+                }
             }
-            const uint32_t excl = __shfl_sync(0xffffffffu, incl - len, o);
-            const uint32_t ob0 = __shfl_sync(0xffffffffu, w.b0, o);
-            const uint32_t ol0 = __shfl_sync(0xffffffffu, w.len0, o);
-            const uint32_t ob1 = __shfl_sync(0xffffffffu, w.b1, o);
-            bool cand = false;
-            uint32_t jc = 0;
-            if (f < total) {
-                const uint32_t off = f - excl;
-                const uint32_t pos = off < ol0 ? ob0 + off : ob1 + (off - ol0);
-                {
-                    nwin++;
-                    const float4 rc = __ldg(srec + pos);
-                    const float t = fmaf(r.A, rc.x, fmaf(r.B, rc.y, r.C));
-                    const float d = fabsf(t);
-                    const float S = fmaf(fabsf(r.A), fabsf(rc.x), fmaf(fabsf(r.B), fabsf(rc.y), fabsf(r.C)));
-                    // FP32 rounding (16u S), the FP32 tolerance (2u eps) and the
-                    // distance between this line and the brute force's FP64 line
-                    const float lerr = fmaf(r.E1, fabsf(rc.x) + fabsf(rc.y) + 2.0f * rc.z, r.E0);
-                    const float bound = fmaf(9.6e-7f, S, fmaf(1.2e-7f, rc.z, lerr + 1e-9f));
-                    if (exact_only) {
-                        cand = exact_pair(P, i, __float_as_uint(rc.w));
-                        nexact++;
-                    } else if (d <= rc.z - bound) {
-                        cand = true;
-                    } else if (!(d > rc.z + bound)) {
-                        // FP32 inconclusive: the brute-force FP64 expression decides.
-                        cand = exact_pair(P, i, __float_as_uint(rc.w));
-                        nexact++;
+        }
+        {
+            const int nlev = S.nlev;
+            const int nslot = nqb * nlev;
+            for (int g0 = warp * 32; g0 < nslot; g0 += kStabThreads) {
+                const int sl = g0 + lane;
+                WinKeys wk;
+                wk.kind = 0;
+                int ql = 0, li = 0;
+                if (sl < nslot) {
+                    ql = sl / nlev;
+                    li = sl - ql * nlev;
+                    if (S.qr[ql].pair == S.gpair) wk = window_keys(S.g, S.qr[ql], S.lv[li]);
+                    else ql = -1;  // another pair: handled below
+                }
+                uint32_t a = 0, b = 0;
+                if (wk.kind >= 2) {
+                    const uint32_t *T = L.tab + S.pd.t_off + S.g.tab[S.lv[li]];
+                    a = __ldg(T + wk.ta);
+                    b = __ldg(T + wk.tb);
+                }
+                if (sl < nslot && ql >= 0) {
+                    const Window w = window_ranges(wk, a, b);
+                    S.rng[ql][2 * li] = make_uint2(w.b0, w.len0);
+                    S.rng[ql][2 * li + 1] = make_uint2(w.b1, w.len1);
+                    if (w.len0 + w.len1) {
+                        atomicAdd(&S.tq[ql], w.len0 + w.len1);
+                        const uint32_t bits = (w.len0 ? 1u : 0u) | (w.len1 ? 2u : 0u);
+                        atomicOr(&S.rmask[ql][li >> 4], bits << (2 * (li & 15)));
                     }
-                    if (cand) {
-                        const uint32_t j = __float_as_uint(rc.w);
-                        jc = j;
-                        ncand++;
-                        if (match) {
-                            const uint4 *rr = reinterpret_cast<const uint4 *>(P.desc2 + (int64_t)j * P.row_bytes);
-                            const uint32_t dd = desc_dist<KIND>(qbuf, rr, chunks);
-                            top2_insert(b1, b2, ((unsigned long long)dd << 32) | j);
+                    if (li == 0) S.nrng[ql] = 2 * nlev;
+                }
+            }
+            // queries of another pair than the block's first: one warp per query, lane = level
+#pragma unroll 1
+            for (int t = 0; t < kQPerWarp; t++) {
+                const int ql = qbase + t;
+                if (ql >= nqb || S.qr[ql].pair == S.gpair) continue;
+                const int p = S.qr[ql].pair;
+                const PairGeom &G = L.geom[p];
+                const WinKeys wk = window_keys(G, S.qr[ql], lane);
+                uint32_t a = 0, b = 0;
+                if (wk.kind >= 2) {
+                    const uint32_t *T = L.tab + L.pairs[p].t_off + G.tab[lane];
+                    a = __ldg(T + wk.ta);
+                    b = __ldg(T + wk.tb);
+                }
+                const Window w = window_ranges(wk, a, b);
+                S.rng[ql][2 * lane] = make_uint2(w.b0, w.len0);
+                S.rng[ql][2 * lane + 1] = make_uint2(w.b1, w.len1);
+                const uint32_t bits = (w.len0 ? 1u : 0u) | (w.len1 ? 2u : 0u);
+                const uint32_t lo16 = __reduce_or_sync(0xffffffffu, lane < 16 ? bits << (2 * lane) : 0u);
+                const uint32_t hi16 = __reduce_or_sync(0xffffffffu, lane >= 16 ? bits << (2 * (lane - 16)) : 0u);
+                if (lane == 0) { S.rmask[ql][0] = lo16; S.rmask[ql][1] = hi16; }
+                uint32_t tot = w.len0 + w.len1;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+                if (lane == 0) {
+                    S.tq[ql] = tot;
+                    S.nrng[ql] = 2 * kLevels;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kStage; k++)
+            if (dslot[k] >= 0) (&S.qdesc[0][0])[dslot[k]] = dv[k];
+        // every query of the block in the cached pair, descriptors of one kind
+        // and staged: the pair's fields are block constants (the common case)
+        const bool uni = __syncthreads_and(tid >= nqb || S.qr[tid].pair == S.gpair) && KIND != kKindAny &&
+                         S.pd.row_bytes <= kDescCache;
+        const float4 *recb = L.rec + S.pd.r_off;
+        if (warp == 0) {
+            uint32_t incl = S.tq[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            S.eoff[lane + 1] = incl;
+            if (lane == 0) S.eoff[0] = 0;
+        }
+        __syncthreads();
+
+        // ---- phase 2, in rounds of kRound window elements
+        const uint32_t T = S.eoff[kQB];
+        for (uint32_t base = 0; base < T; base += kRound) {
+            // 2a: tests, candidates appended to the list
+            if (tid < kQB) S.rcnt[tid] = 0;
+            __syncthreads();
+            const uint32_t Tr = min(T - base, (uint32_t)kRound);
+            const uint32_t K = (Tr + kStabThreads - 1) / kStabThreads;  // the same for every thread
+            uint32_t f = base + (uint32_t)tid * K;
+            const uint32_t fend = min(f + K, base + Tr);
+            int q = 0, k = 0;
+            uint32_t rem = 0;
+            // move (q, k, rem) forward to a real element: past exhausted or empty
+            // ranges and past queries without elements
+            auto settle = [&]() {
+                while (q < kQB) {
+                    // next non-empty range at or after k
+                    const uint32_t m0 = k < 32 ? S.rmask[q][0] & (~0u << k) : 0u;
+                    const uint32_t m1 = k >= 64 ? 0u : k <= 32 ? S.rmask[q][1] : S.rmask[q][1] & (~0u << (k - 32));
+                    if (m0) k = __ffs(m0) - 1;
+                    else if (m1) k = 32 + __ffs(m1) - 1;
+                    else { q++; k = 0; continue; }
+                    const uint32_t len = S.rng[q][k].y;
+                    if (rem < len) break;
+                    rem -= len;
+                    k++;
+                }
+            };
+            if (f < fend) {
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1)
+                    if (S.eoff[q + st] <= f) q += st;
+                rem = f - S.eoff[q];
+                settle();
+            }
+            for (uint32_t kb = 0; kb < K; kb += kBatch) {
+                int bq[kBatch];
+                uint32_t bpos[kBatch];
+                bool bv[kBatch];
+#pragma unroll
+                for (int t = 0; t < kBatch; t++) {
+                    bv[t] = f < fend;
+                    bq[t] = q;
+                    bpos[t] = 0;
+                    if (bv[t]) {
+                        bpos[t] = S.rng[q][k].x + rem;
+                        f++;
+                        rem++;
+                        if (f < fend) settle();
+                    }
+                }
+                float4 rc[kBatch];
+#pragma unroll
+                for (int t = 0; t < kBatch; t++) {
+                    if (bv[t]) {
+                        if (uni) {
+                            rc[t] = __ldg(recb + bpos[t]);
+                        } else {
+                            const int p = S.qr[bq[t]].pair;
+                            const int64_t ro = p == S.gpair ? S.pd.r_off : L.pairs[p].r_off;
+                            rc[t] = __ldg(L.rec + ro + bpos[t]);
+                        }
+                    }
+                }
+#pragma unroll 1
+                for (int t = 0; t < kBatch; t++) {
+                    const int qq = bq[t];
+                    uint32_t j = 0;
+                    bool cand = false;
+                    if (bv[t]) {
+                        const QueryRec &r = S.qr[qq];
+                        j = __float_as_uint(rc[t].w);
+                        nwin++;
+                        bool exact = (r.flags & kQExactOnly) != 0;
+                        if (!exact) {
+                            const float x = rc[t].x, y = rc[t].y, e = rc[t].z;
+                            const float d = fabsf(fmaf(r.A, x, fmaf(r.B, y, r.C)));
+                            const float Sm = fmaf(fabsf(r.A), fabsf(x), fmaf(fabsf(r.B), fabsf(y), fabsf(r.C)));
+                            // FP32 rounding (16u S), the FP32 tolerance (2u eps) and the
+                            // distance between this line and the brute force's FP64 line
+                            const float lerr = fmaf(r.E1, fabsf(x) + fabsf(y) + 2.0f * e, r.E0);
+                            const float bound = fmaf(9.6e-7f, Sm, fmaf(1.2e-7f, e, lerr + 1e-9f));
+                            cand = d <= e - bound;
+                            exact = !cand && !(d > e + bound);
+                        }
+                        if (exact) {
+                            // FP32 inconclusive: the brute-force FP64 expression decides.
+                            const PairDesc &P = L.pairs[r.pair];
+                            cand = exact_pair(P, q0 + qq - P.q_off, j);
+                            nexact++;
+                        }
+                    }
+                    if (cand) atomicAdd(&S.cnt[qq], 1u);
+                    if (cand && mode == 2) {
+                        const uint32_t slot = atomicAdd(&S.fill[qq], 1u);
+                        if (write_rows) L.cand_idx[L.cand_offsets[q0 + qq] + slot] = (int32_t)j;
+                    }
+                    if (mode != 1) {
+                        // warp-aggregated append to the round's candidate list
+                        const uint32_t m = __ballot_sync(0xffffffffu, cand);
+                        if (m) {
+                            const int leader = __ffs(m) - 1;
+                            uint32_t c0 = 0;
+                            if (lane == leader) c0 = atomicAdd(&S.ncand, (uint32_t)__popc(m));
+                            c0 = __shfl_sync(0xffffffffu, c0, leader);
+                            if (cand) {
+                                const uint32_t c = c0 + __popc(m & lt);
+                                S.lj[c] = j;
+                                S.lq[c] = (uint8_t)qq;
+                                atomicAdd(&S.rcnt[qq], 1u);
+                            }
                         }
                     }
                 }
             }
-            if (mode == 2) {
-                const uint32_t bal = __ballot_sync(0xffffffffu, cand);
-                if (cand && write_rows) {
-                    const uint32_t slot = __popc(bal & ((1u << lane) - 1u));
-                    L.cand_idx[row_off + slot] = (int32_t)jc;
-                }
-                row_off += __popc(bal);
-            }
-        }
-    }
-    // warp reduction of the two best keys and the counters
+            __syncthreads();
+            const uint32_t nc = S.ncand;
+            if (mode != 1 && nc > 0) {
+                // 2a': segments by query
+                if (warp == 0) {
+                    const uint32_t v = S.rcnt[lane];
+                    uint32_t incl = v;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, b1, o);
-        const unsigned long long o2 = __shfl_xor_sync(0xffffffffu, b2, o);
-        const unsigned long long n1 = b1 < o1 ? b1 : o1;
-        const unsigned long long mx = b1 < o1 ? o1 : b1;
-        const unsigned long long mn2 = b2 < o2 ? b2 : o2;
-        b2 = mx < mn2 ? mx : mn2;
-        b1 = n1;
-        ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
-        nwin += __shfl_xor_sync(0xffffffffu, nwin, o);
-        nexact += __shfl_xor_sync(0xffffffffu, nexact, o);
-    }
-    if (lane == 0) {
-        if (mode == 1) {
-            L.qcount[gq] = ncand;
-        } else {
-            uint8_t fl = (uint8_t)(r.flags & EGM_FLAG_DEGENERATE_LINE);
-            int32_t jb = -1, js = -1;
-            float db = INFINITY, ds = INFINITY;
-            if (match && b1 != ~0ull) {
-                jb = (int32_t)(b1 & 0xffffffffu);
-                const uint32_t d1 = (uint32_t)(b1 >> 32);
-                db = KIND == EGM_DESC_F32_L2 ? __uint_as_float(d1) : (float)d1;
-                fl |= EGM_FLAG_HAS_BEST;
-                bool pass;
-                if (b2 == ~0ull) {
-                    fl |= EGM_FLAG_NO_SECOND;
-                    pass = true;
-                } else {
-                    js = (int32_t)(b2 & 0xffffffffu);
-                    const uint32_t d2 = (uint32_t)(b2 >> 32);
-                    ds = KIND == EGM_DESC_F32_L2 ? __uint_as_float(d2) : (float)d2;
-                    const long long nn = L.ratio_num, dn = L.ratio_den;
-                    if (KIND == EGM_DESC_U8_L2)
-                        pass = (long long)d1 * dn * dn < (long long)d2 * nn * nn;
-                    else if (KIND == EGM_DESC_BIN)
-                        pass = (long long)d1 * dn < (long long)d2 * nn;
-                    else
-                        pass = db * (float)(dn * dn) < ds * (float)(nn * nn);
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += t;
+                    }
+                    S.roff[lane] = incl - v;
+                    S.rfill[lane] = incl - v;
+                    if (lane == 31) S.roff[kQB] = incl;
                 }
-                if (pass) fl |= EGM_FLAG_RATIO_PASS;
+                __syncthreads();
+                for (uint32_t c = tid; c < nc; c += kStabThreads) {
+                    const int qq = S.lq[c];
+                    const uint32_t pos = atomicAdd(&S.rfill[qq], 1u);
+                    S.sj[pos] = S.lj[c];
+                    S.sq[pos] = (uint8_t)qq;
+                }
+                __syncthreads();
+                // 2b: G lanes per candidate read its descriptor row together (one
+                // cache line per group of eight 16-byte chunks), four candidates per
+                // group with the loads issued first; distances go to shared memory.
+                const int rb0 = KIND != kKindAny ? S.pd.row_bytes : kDescCache;
+                const int chunks0 = rb0 >> 4;
+                const int G = chunks0 >= 32 ? 32 : chunks0 >= 16 ? 16 : chunks0 >= 8 ? 8 : chunks0 >= 4 ? 4
+                            : chunks0 >= 2 ? 2 : 1;
+                const int groups = kStabThreads / G;
+                const int gl = tid % G;
+                constexpr int U = 4;
+                if (uni && chunks0 <= G) {
+                    // block constants; one chunk per lane of each candidate
+                    const uint4 *d2 = reinterpret_cast<const uint4 *>(S.pd.desc2);
+                    const int rb16 = chunks0;
+                    for (uint32_t cb = 0; cb < nc; cb += (uint32_t)(groups * U)) {
+                        uint32_t cc[U];
+                        uint4 rv[U];
+#pragma unroll
+                        for (int u = 0; u < U; u++) {
+                            cc[u] = cb + (uint32_t)(tid / G) + (uint32_t)(u * groups);
+                            if (cc[u] < nc && gl < rb16) rv[u] = __ldg(d2 + (int64_t)S.sj[cc[u]] * rb16 + gl);
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; u++) {
+                            uint32_t acc = 0;
+                            float facc = 0.0f;
+                            if (cc[u] < nc && gl < rb16) chunk_dist<KIND>(KIND, S.qdesc[S.sq[cc[u]]][gl], rv[u], acc, facc);
+                            if (KIND == EGM_DESC_F32_L2) {
+                                for (int o = G >> 1; o > 0; o >>= 1) facc += __shfl_xor_sync(0xffffffffu, facc, o, G);
+                                acc = __float_as_uint(facc);
+                            } else {
+                                for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+                            }
+                            if (gl == 0 && cc[u] < nc) S.sd[cc[u]] = acc;
+                        }
+                    }
+                } else
+                for (uint32_t cb = 0; cb < nc; cb += (uint32_t)(groups * U)) {
+                    uint32_t cc[U];
+                    const uint4 *rrow[U];
+                    const uint4 *qrow[U];
+                    int chunks[U], kinds[U];
+                    bool qsm[U];
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        cc[u] = cb + (uint32_t)(tid / G) + (uint32_t)(u * groups);
+                        chunks[u] = 0;
+                        kinds[u] = KIND;
+                        rrow[u] = qrow[u] = nullptr;
+                        qsm[u] = true;
+                        if (cc[u] < nc) {
+                            const int qq = S.sq[cc[u]];
+                            const int p = S.qr[qq].pair;
+                            const PairDesc &P = p == S.gpair ? S.pd : L.pairs[p];
+                            chunks[u] = P.row_bytes >> 4;
+                            if (KIND == kKindAny) kinds[u] = P.kind;
+                            rrow[u] = reinterpret_cast<const uint4 *>(P.desc2 + (int64_t)S.sj[cc[u]] * P.row_bytes);
+                            qsm[u] = P.row_bytes <= kDescCache;
+                            qrow[u] = qsm[u] ? S.qdesc[qq]
+                                             : reinterpret_cast<const uint4 *>(P.desc1 + (q0 + qq - P.q_off) *
+                                                                                         (int64_t)P.row_bytes);
+                        }
+                    }
+                    uint32_t acc[U];
+                    float facc[U];
+#pragma unroll
+                    for (int u = 0; u < U; u++) { acc[u] = 0; facc[u] = 0.0f; }
+                    int maxch = 0;
+#pragma unroll
+                    for (int u = 0; u < U; u++) maxch = max(maxch, chunks[u]);
+                    for (int ch0 = 0; ch0 < maxch; ch0 += G) {
+                        const int ch = ch0 + gl;
+                        uint4 rv[U];
+#pragma unroll
+                        for (int u = 0; u < U; u++)
+                            if (ch < chunks[u]) rv[u] = __ldg(rrow[u] + ch);
+#pragma unroll
+                        for (int u = 0; u < U; u++)
+                            if (ch < chunks[u])
+                                chunk_dist<KIND>(kinds[u], qsm[u] ? qrow[u][ch] : __ldg(qrow[u] + ch), rv[u], acc[u],
+                                                 facc[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        const bool isf = (KIND == kKindAny ? kinds[u] : KIND) == EGM_DESC_F32_L2;
+                        uint32_t v = isf ? __float_as_uint(facc[u]) : acc[u];
+                        for (int o = G >> 1; o > 0; o >>= 1) {
+                            if (isf) {
+                                facc[u] += __shfl_xor_sync(0xffffffffu, facc[u], o, G);
+                                v = __float_as_uint(facc[u]);
+                            } else {
+                                acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o, G);
+                                v = acc[u];
+                            }
+                        }
+                        if (gl == 0 && cc[u] < nc) S.sd[cc[u]] = v;
+                    }
+                }
+                __syncthreads();
+                // 2c: a thread per candidate, segmented best two per query within
+                // the warp (a query's candidates are contiguous), merged by the
+                // segment's first lane.  The merge keeps the minimum with one
+                // atomicMin and offers min(the larger of the displaced and the
+                // offered first, the offered second) to the second slot: every
+                // value offered there is an element other than the minimum and
+                // the true second is always offered, so the pair is exact under
+                // any interleaving.
+                for (uint32_t cb = 0; cb < nc; cb += kStabThreads) {
+                    const uint32_t c = cb + (uint32_t)tid;
+                    const bool valid = c < nc;
+                    const int qq = valid ? (int)S.sq[c] : -1 - lane;
+                    unsigned long long k1 = valid ? ((unsigned long long)S.sd[c] << 32) | S.sj[c] : ~0ull;
+                    unsigned long long k2 = ~0ull;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const unsigned long long o1 = __shfl_down_sync(0xffffffffu, k1, o);
+                        const unsigned long long o2 = __shfl_down_sync(0xffffffffu, k2, o);
+                        const int oq = __shfl_down_sync(0xffffffffu, qq, o);
+                        if (lane + o < 32 && oq == qq) {
+                            const unsigned long long mx = k1 < o1 ? o1 : k1;
+                            const unsigned long long mn2 = k2 < o2 ? k2 : o2;
+                            k1 = k1 < o1 ? k1 : o1;
+                            k2 = mx < mn2 ? mx : mn2;
+                        }
+                    }
+                    const int pq = __shfl_up_sync(0xffffffffu, qq, 1);
+                    if (valid && (lane == 0 || pq != qq)) {
+                        const unsigned long long old = atomicMin(&S.b1[qq], k1);
+                        const unsigned long long lose = old > k1 ? old : k1;
+                        const unsigned long long offer = lose < k2 ? lose : k2;
+                        if (offer != ~0ull) atomicMin(&S.b2[qq], offer);
+                    }
+                }
             }
-            if (L.best) L.best[gq] = jb;
-            if (L.second) L.second[gq] = js;
-            if (L.best_d) L.best_d[gq] = db;
-            if (L.second_d) L.second_d[gq] = ds;
-            if (L.flags) L.flags[gq] = fl;
+            __syncthreads();
+            if (tid == 0) S.ncand = 0;
         }
         if (L.counters) {
-            atomicAdd(L.counters + 2, (unsigned long long)nwin);
-            atomicAdd(L.counters + 3, (unsigned long long)ncand);
-            atomicAdd(L.counters + 4, (unsigned long long)nexact);
+            atomicAdd(&S.nwin, nwin);
+            atomicAdd(&S.nexact, nexact);
+            nwin = nexact = 0;
         }
-    }
-}
+        __syncthreads();
 
-__global__ void __launch_bounds__(kStabWarps * 32, 4) stab_kernel(Launch L, int mode) {
-    __shared__ __align__(16) uint4 qbuf_all[kStabWarps][kMaxRowBytes / 16];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint4 *qbuf = qbuf_all[warp];
-    for (int64_t gq = (int64_t)blockIdx.x * kStabWarps + warp; gq < L.nq; gq += (int64_t)gridDim.x * kStabWarps) {
-        const int p = pair_of(L.q_offs, L.npairs, gq);
-        const int kind = L.pairs[p].kind;
-        if (kind == EGM_DESC_U8_L2) stab_query<EGM_DESC_U8_L2>(L, mode, gq, qbuf, lane);
-        else if (kind == EGM_DESC_BIN) stab_query<EGM_DESC_BIN>(L, mode, gq, qbuf, lane);
-        else stab_query<EGM_DESC_F32_L2>(L, mode, gq, qbuf, lane);
-        __syncwarp();
+        // ---- results
+        if (tid < nqb) {
+            const int64_t gq = q0 + tid;
+            if (mode == 1) {
+                L.qcount[gq] = S.cnt[tid];
+            } else {
+                const int p = S.qr[tid].pair;
+                const PairDesc &P = p == S.gpair ? S.pd : L.pairs[p];
+                const unsigned long long b1 = S.b1[tid], b2 = S.b2[tid];
+                uint8_t fl = (uint8_t)(S.qr[tid].flags & EGM_FLAG_DEGENERATE_LINE);
+                int32_t jb = -1, js = -1;
+                float db = INFINITY, ds = INFINITY;
+                if (P.row_bytes > 0 && b1 != ~0ull) {
+                    const bool isf = P.kind == EGM_DESC_F32_L2;
+                    jb = (int32_t)(b1 & 0xffffffffu);
+                    const uint32_t d1 = (uint32_t)(b1 >> 32);
+                    db = isf ? __uint_as_float(d1) : (float)d1;
+                    fl |= EGM_FLAG_HAS_BEST;
+                    bool pass;
+                    if (b2 == ~0ull) {
+                        fl |= EGM_FLAG_NO_SECOND;
+                        pass = true;
+                    } else {
+                        js = (int32_t)(b2 & 0xffffffffu);
+                        const uint32_t d2 = (uint32_t)(b2 >> 32);
+                        ds = isf ? __uint_as_float(d2) : (float)d2;
+                        const long long nn = L.ratio_num, dn = L.ratio_den;
+                        if (P.kind == EGM_DESC_U8_L2)
+                            pass = (long long)d1 * dn * dn < (long long)d2 * nn * nn;
+                        else if (P.kind == EGM_DESC_BIN)
+                            pass = (long long)d1 * dn < (long long)d2 * nn;
+                        else
+                            pass = db * (float)(dn * dn) < ds * (float)(nn * nn);
+                    }
+                    if (pass) fl |= EGM_FLAG_RATIO_PASS;
+                }
+                if (L.best) L.best[gq] = jb;
+                if (L.second) L.second[gq] = js;
+                if (L.best_d) L.best_d[gq] = db;
+                if (L.second_d) L.second_d[gq] = ds;
+                if (L.flags) L.flags[gq] = fl;
+            }
+            if (L.counters) atomicAdd(L.counters + 3, (unsigned long long)S.cnt[tid]);
+        }
+        __syncthreads();
+    }
+    if (L.counters && tid == 0) {
+        atomicAdd(L.counters + 2, (unsigned long long)S.nwin);
+        atomicAdd(L.counters + 4, (unsigned long long)S.nexact);
     }
 }
 
@@ -362,9 +735,14 @@ cudaError_t launch_post_sort(const Launch &L, cudaStream_t s) {
 
 cudaError_t launch_stab(const Launch &L, int mode, cudaStream_t s) {
     if (L.nq == 0) return cudaSuccess;
-    int64_t blocks = (L.nq + kStabWarps - 1) / kStabWarps;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    stab_kernel<<<(int)blocks, kStabWarps * 32, 0, s>>>(L, mode);
+    int64_t blocks = (L.nq + kQB - 1) / kQB;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    switch (L.kind) {
+        case EGM_DESC_U8_L2: stab_kernel<EGM_DESC_U8_L2><<<(int)blocks, kStabThreads, 0, s>>>(L, mode); break;
+        case EGM_DESC_BIN: stab_kernel<EGM_DESC_BIN><<<(int)blocks, kStabThreads, 0, s>>>(L, mode); break;
+        case EGM_DESC_F32_L2: stab_kernel<EGM_DESC_F32_L2><<<(int)blocks, kStabThreads, 0, s>>>(L, mode); break;
+        default: stab_kernel<kKindAny><<<(int)blocks, kStabThreads, 0, s>>>(L, mode); break;
+    }
     return cudaGetLastError();
 }
 

@@ -40,7 +40,8 @@ constexpr size_t kOffQrec = align256(kOffTab + sizeof(uint32_t) * kTabCap);
 constexpr size_t kOffQcount = align256(kOffQrec + sizeof(QueryRec) * M);
 constexpr size_t kOffScan = align256(kOffQcount + sizeof(int64_t) * (M + 1));
 constexpr size_t kOffLong = align256(kOffScan + sizeof(int64_t) * (M / 8192 + 2));
-constexpr size_t kOffSmall = align256(kOffLong + sizeof(uint32_t) * (M + 1));
+constexpr size_t kOffBlk = align256(kOffLong + sizeof(uint32_t) * (M + 1));
+constexpr size_t kOffSmall = align256(kOffBlk + sizeof(int32_t) * (M / kStabQB + 2));
 constexpr size_t kScratchBytes = align256(kOffSmall + 256);
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -179,9 +180,11 @@ extern "C" egm_status egm_match_pair_static(const egm_pair *P, const egm_out *ou
     L.counters = nullptr;
     L.qcount = reinterpret_cast<int64_t *>(base + kOffQcount);
     L.scan_tmp = reinterpret_cast<int64_t *>(base + kOffScan);
+    L.blkpair = reinterpret_cast<int32_t *>(base + kOffBlk);
     L.ratio_num = rn;
     L.ratio_den = rd;
     L.max_n = P->n;
+    L.kind = up.pd.kind;
     L.best = out->best;
     L.second = out->second;
     L.best_d = out->best_d;
