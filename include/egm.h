@@ -174,6 +174,21 @@ egm_status egm_match_pair(egm_ctx *ctx, const egm_pair *pair, const egm_out *out
 egm_status egm_match_batch(egm_ctx *ctx, const egm_pair *pairs, int32_t npairs,
                            const egm_out *out);
 
+/*
+ * A batch captured once as a CUDA graph and replayed many times (the same
+ * pointers and sizes every time; the data behind the pointers may change).
+ * The graph owns its own scratch, sized for this batch, and its own copy of
+ * the pair table, so ordinary calls on the context in between do not
+ * disturb it.  egm_graph_launch enqueues the whole pipeline with one graph
+ * launch on the context's stream and, when params.sync is 1, waits and
+ * returns the device status.  Device pointers.
+ */
+typedef struct egm_graph egm_graph;
+egm_status egm_graph_create(egm_ctx *ctx, const egm_pair *pairs, int32_t npairs, const egm_out *out,
+                            egm_graph **graph);
+egm_status egm_graph_launch(egm_graph *graph);
+egm_status egm_graph_destroy(egm_graph *graph);
+
 /* As egm_match_pair, but every pointer in *pair and *out is HOST memory
  * (pinned memory gives the fastest copies).  The call stages the inputs to
  * the device, matches, copies the outputs back and waits for completion. */

@@ -194,6 +194,19 @@ class Matcher:
             o["cand_idx"] = o["cand_idx"][: int(o["cand_offsets"][-1].item())]
         return o
 
+    def graph_create(self, items, out, cand_capacity=0):
+        """egm_graph_create over device items (as from to_device) and output tensors."""
+        pairs, keep = [], []
+        for it in items:
+            pairs.append(self.make_pair(it["xy1"], it["xy2"], it["F"], it["eps"], it.get("desc1"),
+                                        it.get("desc2"), it["kind"], it["dim"], it["width"], it["height"]))
+            keep.append(self._keep)
+        arr = (_egm.egm_pair * len(pairs))(*pairs)
+        s = self._out_struct(out, cand_capacity)
+        g = C.c_void_p()
+        check(self.lib.egm_graph_create(self.ctx, arr, len(pairs), C.byref(s), C.byref(g)), "egm_graph_create")
+        return _Graph(self, g, keep, out)
+
     def match_host(self, scene, csr=False, cand_capacity=None):
         """egm_match_pair_host on host (numpy) arrays; returns numpy outputs."""
         import numpy as np
@@ -246,3 +259,24 @@ class Matcher:
         st = self.lib.egm_intervals(self.ctx, C.byref(pair), _ptr(th), _ptr(de), _ptr(e3), _ptr(mode))
         check(st, "egm_intervals")
         return th[:n], de[:n], e3, int(mode.item())
+
+
+class _Graph:
+    """A captured batch (egm_graph); launch() replays it on the matcher's stream."""
+
+    def __init__(self, mt, handle, keep, out):
+        self.mt, self.handle, self._keep, self.out = mt, handle, keep, out
+
+    def launch(self) -> int:
+        return self.mt.lib.egm_graph_launch(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            self.mt.lib.egm_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -83,6 +83,10 @@ SIGNATURES = {
     "egm_match_pair_host": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.POINTER(egm_out)]),
     "egm_match_pair_static": (C.c_int, [C.POINTER(egm_pair), C.POINTER(egm_out), C.POINTER(egm_params),
                                         C.c_void_p]),
+    "egm_graph_create": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.c_int32, C.POINTER(egm_out),
+                                   C.POINTER(C.c_void_p)]),
+    "egm_graph_launch": (C.c_int, [C.c_void_p]),
+    "egm_graph_destroy": (C.c_int, [C.c_void_p]),
     "egm_sync": (C.c_int, [C.c_void_p]),
     "egm_intervals": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p]),

@@ -35,6 +35,20 @@ cudaError_t grow(DevBuf &b, size_t need) {
 template <typename T>
 T *as(DevBuf &b) { return reinterpret_cast<T *>(b.ptr); }
 
+// Device scratch of one pipeline instance (a context, or a captured graph).
+struct Scratch {
+    DevBuf pairs, geom, offs, keys, rec, tab, qrec, qcount, scan, longlist, small, counters, blkpair;
+    void release() {
+        DevBuf *b[] = {&pairs, &geom, &offs, &keys, &rec, &tab, &qrec, &qcount, &scan, &longlist, &small,
+                       &counters, &blkpair};
+        for (DevBuf *x : b) {
+            if (x->ptr) cudaFree(x->ptr);
+            x->ptr = nullptr;
+            x->bytes = 0;
+        }
+    }
+};
+
 }  // namespace
 
 struct egm_ctx {
@@ -43,8 +57,7 @@ struct egm_ctx {
     egm_params params;
     bool counters_on = false;
     egm_stats last{};
-    // scratch
-    DevBuf pairs, geom, offs, keys, rec, tab, qrec, qcount, scan, longlist, small, counters, blkpair;
+    Scratch sc;
     DevBuf stage;  // host-path staging of inputs and outputs
     // pinned host memory for the pair table and the status word
     void *h_table = nullptr;
@@ -171,7 +184,8 @@ egm_status make_plan(const egm_pair *pairs, int npairs, Plan &pl) {
     return EGM_OK;
 }
 
-cudaError_t reserve(egm_ctx *c, int64_t nq, int64_t nr, int64_t ntab, int npairs) {
+cudaError_t reserve(Scratch &c_, int64_t nq, int64_t nr, int64_t ntab, int npairs) {
+    Scratch *c = &c_;
     cudaError_t e;
     if ((e = grow(c->pairs, sizeof(PairDesc) * (size_t)std::max(npairs, 1))) != cudaSuccess) return e;
     if ((e = grow(c->geom, sizeof(PairGeom) * (size_t)std::max(npairs, 1))) != cudaSuccess) return e;
@@ -189,7 +203,9 @@ cudaError_t reserve(egm_ctx *c, int64_t nq, int64_t nr, int64_t ntab, int npairs
     return cudaSuccess;
 }
 
-Launch make_launch(egm_ctx *c, const Plan &pl, int npairs, const egm_out *out) {
+Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const Plan &pl, int npairs,
+                   const egm_out *out) {
+    Scratch *c = &sc;
     Launch L;
     memset(&L, 0, sizeof(L));
     L.pairs = as<PairDesc>(c->pairs);
@@ -211,12 +227,12 @@ Launch make_launch(egm_ctx *c, const Plan &pl, int npairs, const egm_out *out) {
     L.tab = as<uint32_t>(c->tab);
     L.qrec = as<QueryRec>(c->qrec);
     L.status = as<uint32_t>(c->small);
-    L.counters = c->counters_on ? as<unsigned long long>(c->counters) : nullptr;
+    L.counters = counters_on ? as<unsigned long long>(c->counters) : nullptr;
     L.qcount = as<int64_t>(c->qcount);
     L.scan_tmp = as<int64_t>(c->scan);
     L.blkpair = as<int32_t>(c->blkpair);
-    L.ratio_num = c->params.ratio_num;
-    L.ratio_den = c->params.ratio_den;
+    L.ratio_num = prm.ratio_num;
+    L.ratio_den = prm.ratio_den;
     L.max_n = pl.max_n;
     L.kind = pl.pd.empty() ? -1 : pl.pd[0].kind;
     for (const PairDesc &d : pl.pd)
@@ -256,9 +272,9 @@ cudaError_t upload_plan(egm_ctx *c, const Plan &pl, int npairs) {
     memcpy(h, pl.pd.data(), tb);
     memcpy(h + tb, pl.qoffs.data(), sizeof(int64_t) * (npairs + 1));
     memcpy(h + tb + sizeof(int64_t) * (npairs + 1), pl.roffs.data(), sizeof(int64_t) * (npairs + 1));
-    cudaError_t e = cudaMemcpyAsync(c->pairs.ptr, h, tb, cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e = cudaMemcpyAsync(c->sc.pairs.ptr, h, tb, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(c->offs.ptr, h + tb, ob, cudaMemcpyHostToDevice, c->stream);
+    e = cudaMemcpyAsync(c->sc.offs.ptr, h + tb, ob, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return e;
     e = cudaEventRecord(c->table_ev, c->stream);
     if (e != cudaSuccess) return e;
@@ -284,52 +300,74 @@ egm_status finish(egm_ctx *c, bool sync) {
     return egm_sync(c);
 }
 
-egm_status run_batch(egm_ctx *c, const egm_pair *pairs, int npairs, const egm_out *out, bool sync) {
-    if (!c || npairs < 0 || (npairs > 0 && !pairs) || !out) return EGM_ERR_ARG;
-    if (npairs == 0) return EGM_OK;
-    Plan pl;
-    egm_status s = make_plan(pairs, npairs, pl);
-    if (s != EGM_OK) return s;
+// The kernel sequence of one match call.  `tc` receives stage events when
+// per-stage timing is on (NULL: no events, e.g. while capturing a graph).
+cudaError_t enqueue_pipeline(const Launch &L, Scratch &sc, bool csr, int max_n, cudaStream_t st, egm_ctx *tc) {
+    size_t tb = 0;
+    if (tc && tc->timing_on) {
+        tb = tc->ev_used;
+        tc->ev_calls.push_back(tb);
+        tc->ev_used += kStages + 1;
+    } else {
+        tc = nullptr;
+    }
+    cudaError_t e;
+#define EGM_Q(x)                           \
+    do {                                   \
+        if ((e = (x)) != cudaSuccess) return e; \
+    } while (0)
+    if (tc) EGM_Q(mark(tc, tb, 0));
+    EGM_Q(launch_geometry(L, st));
+    if (tc) EGM_Q(mark(tc, tb, 1));
+    EGM_Q(launch_prep(L, st));
+    if (tc) EGM_Q(mark(tc, tb, 2));
+    EGM_Q(launch_sort(L, max_n, st));
+    if (tc) EGM_Q(mark(tc, tb, 3));
+    EGM_Q(launch_post_sort(L, st));
+    if (tc) EGM_Q(mark(tc, tb, 4));
+    if (csr) {
+        uint32_t *long_list = as<uint32_t>(sc.longlist);
+        uint32_t *long_count = as<uint32_t>(sc.small) + 16;
+        EGM_Q(launch_stab(L, 1, st));
+        if (tc) EGM_Q(mark(tc, tb, 5));
+        EGM_Q(launch_csr_offsets(L, long_count, st));
+        EGM_Q(launch_stab(L, 2, st));
+        EGM_Q(launch_csr_row_sort(L, long_list, long_count, st));
+    } else {
+        EGM_Q(launch_stab(L, 0, st));
+        if (tc) EGM_Q(mark(tc, tb, 5));
+    }
+    if (tc) EGM_Q(mark(tc, tb, 6));
+#undef EGM_Q
+    return cudaSuccess;
+}
+
+egm_status check_out(const egm_pair *pairs, int npairs, const egm_out *out) {
     const bool csr = out->cand_offsets != nullptr;
     if (csr && (!out->cand_total || out->cand_capacity < 0 || (out->cand_capacity > 0 && !out->cand_idx)))
         return EGM_ERR_ARG;
     bool any_desc = false;
     for (int p = 0; p < npairs; p++) any_desc |= has_desc(pairs + p);
     if (!csr && !any_desc) return EGM_ERR_ARG;  // nothing to compute
+    return EGM_OK;
+}
+
+egm_status run_batch(egm_ctx *c, const egm_pair *pairs, int npairs, const egm_out *out, bool sync) {
+    if (!c || npairs < 0 || (npairs > 0 && !pairs) || !out) return EGM_ERR_ARG;
+    if (npairs == 0) return EGM_OK;
+    Plan pl;
+    egm_status s = make_plan(pairs, npairs, pl);
+    if (s != EGM_OK) return s;
+    if ((s = check_out(pairs, npairs, out)) != EGM_OK) return s;
+    const bool csr = out->cand_offsets != nullptr;
     EGM_TRY(cudaSetDevice(c->device));
-    EGM_TRY(reserve(c, pl.nq, pl.nr, pl.ntab, npairs));
+    EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, npairs));
     EGM_TRY(upload_plan(c, pl, npairs));
-    Launch L = make_launch(c, pl, npairs, out);
+    Launch L = make_launch(c->sc, c->counters_on, c->params, pl, npairs, out);
     cudaStream_t st = c->stream;
     if (sync) EGM_TRY(cudaMemsetAsync(L.status, 0, sizeof(uint32_t), st));
-    if (c->counters_on) EGM_TRY(cudaMemsetAsync(c->counters.ptr, 0, 8 * sizeof(unsigned long long), st));
-    const size_t tb = c->ev_used;
-    if (c->timing_on) {
-        c->ev_calls.push_back(tb);
-        c->ev_used += kStages + 1;
-    }
-    EGM_TRY(mark(c, tb, 0));
-    EGM_TRY(launch_geometry(L, st));
-    EGM_TRY(mark(c, tb, 1));
-    EGM_TRY(launch_prep(L, st));
-    EGM_TRY(mark(c, tb, 2));
-    EGM_TRY(launch_sort(L, pl.max_n, st));
-    EGM_TRY(mark(c, tb, 3));
-    EGM_TRY(launch_post_sort(L, st));
-    EGM_TRY(mark(c, tb, 4));
-    if (csr) {
-        uint32_t *long_list = as<uint32_t>(c->longlist);
-        uint32_t *long_count = as<uint32_t>(c->small) + 16;
-        EGM_TRY(launch_stab(L, 1, st));
-        EGM_TRY(mark(c, tb, 5));
-        EGM_TRY(launch_csr_offsets(L, long_count, st));
-        EGM_TRY(launch_stab(L, 2, st));
-        EGM_TRY(launch_csr_row_sort(L, long_list, long_count, st));
-    } else {
-        EGM_TRY(launch_stab(L, 0, st));
-        EGM_TRY(mark(c, tb, 5));
-    }
-    EGM_TRY(mark(c, tb, 6));
+    if (c->counters_on) EGM_TRY(cudaMemsetAsync(c->sc.counters.ptr, 0, 8 * sizeof(unsigned long long), st));
+    EGM_TRY(enqueue_pipeline(L, c->sc, csr, pl.max_n, st, c));
     c->last.queries = pl.nq;
     c->last.refs = pl.nr;
     return finish(c, sync);
@@ -362,8 +400,8 @@ egm_status egm_create(egm_ctx **out, int device, void *stream) {
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_status, 64);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_counters, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->table_ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = grow(c->small, 256);
-    if (e == cudaSuccess) e = cudaMemset(c->small.ptr, 0, 256);
+    if (e == cudaSuccess) e = grow(c->sc.small, 256);
+    if (e == cudaSuccess) e = cudaMemset(c->sc.small.ptr, 0, 256);
     if (e != cudaSuccess) {
         egm_destroy(c);
         return from_cuda(e);
@@ -377,10 +415,8 @@ egm_status egm_destroy(egm_ctx *c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
-    DevBuf *bufs[] = {&c->pairs, &c->geom, &c->offs, &c->keys, &c->rec, &c->tab, &c->qrec, &c->qcount,
-                      &c->scan, &c->longlist, &c->small, &c->counters, &c->stage, &c->blkpair};
-    for (DevBuf *b : bufs)
-        if (b->ptr) cudaFree(b->ptr);
+    c->sc.release();
+    if (c->stage.ptr) cudaFree(c->stage.ptr);
     if (c->h_table) cudaFreeHost(c->h_table);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->h_counters) cudaFreeHost(c->h_counters);
@@ -415,20 +451,20 @@ egm_status egm_reserve(egm_ctx *c, int64_t queries, int64_t refs, int32_t pairs)
     if (!c || queries < 0 || refs < 0 || pairs < 0) return EGM_ERR_ARG;
     EGM_TRY(cudaSetDevice(c->device));
     const int64_t ntab = 4 * refs + (int64_t)std::max(pairs, 1) * (2 * kLevels + 32);
-    EGM_TRY(reserve(c, queries, refs, ntab, std::max(pairs, 1)));
+    EGM_TRY(reserve(c->sc, queries, refs, ntab, std::max(pairs, 1)));
     return EGM_OK;
 }
 
 egm_status egm_sync(egm_ctx *c) {
     if (!c) return EGM_ERR_ARG;
     EGM_TRY(cudaSetDevice(c->device));
-    EGM_TRY(cudaMemcpyAsync(c->h_status, c->small.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    EGM_TRY(cudaMemcpyAsync(c->h_status, c->sc.small.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
     if (c->counters_on)
-        EGM_TRY(cudaMemcpyAsync(c->h_counters, c->counters.ptr, 8 * sizeof(unsigned long long),
+        EGM_TRY(cudaMemcpyAsync(c->h_counters, c->sc.counters.ptr, 8 * sizeof(unsigned long long),
                                 cudaMemcpyDeviceToHost, c->stream));
     EGM_TRY(cudaStreamSynchronize(c->stream));
     const uint32_t st = *c->h_status;
-    if (st) EGM_TRY(cudaMemsetAsync(c->small.ptr, 0, sizeof(uint32_t), c->stream));
+    if (st) EGM_TRY(cudaMemsetAsync(c->sc.small.ptr, 0, sizeof(uint32_t), c->stream));
     if (c->counters_on) {
         c->last.window_refs = (int64_t)c->h_counters[2];
         c->last.candidates = (int64_t)c->h_counters[3];
@@ -503,7 +539,7 @@ egm_status egm_match_pair_host(egm_ctx *c, const egm_pair *hp, const egm_out *ho
         dout.cand_idx = reinterpret_cast<int32_t *>(d + o_ci);
         dout.cand_capacity = ho->cand_capacity;
     }
-    EGM_TRY(cudaMemsetAsync(c->small.ptr, 0, sizeof(uint32_t), st));
+    EGM_TRY(cudaMemsetAsync(c->sc.small.ptr, 0, sizeof(uint32_t), st));
     s = run_batch(c, &dp, 1, &dout, false);
     if (s != EGM_OK) return s;
     if (ho->best) EGM_TRY(cudaMemcpyAsync(ho->best, dout.best, 4 * m, D2H, st));
@@ -536,13 +572,93 @@ egm_status egm_intervals(egm_ctx *c, const egm_pair *pair, double *theta, double
     egm_status s = make_plan(&p, 1, pl);
     if (s != EGM_OK) return s;
     EGM_TRY(cudaSetDevice(c->device));
-    EGM_TRY(reserve(c, pl.nq, pl.nr, pl.ntab, 1));
+    EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, 1));
     EGM_TRY(upload_plan(c, pl, 1));
-    Launch L = make_launch(c, pl, 1, nullptr);
+    Launch L = make_launch(c->sc, false, c->params, pl, 1, nullptr);
     if (c->params.sync) EGM_TRY(cudaMemsetAsync(L.status, 0, sizeof(uint32_t), c->stream));
     EGM_TRY(launch_geometry(L, c->stream));
     EGM_TRY(launch_intervals(L, theta, delta, e3, mode, c->stream));
     return finish(c, c->params.sync != 0);
+}
+
+}  // extern "C"
+
+struct egm_graph {
+    egm_ctx *ctx = nullptr;
+    Scratch sc;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+egm_status egm_graph_create(egm_ctx *c, const egm_pair *pairs, int32_t npairs, const egm_out *out,
+                            egm_graph **graph) {
+    if (!c || !graph || !out || npairs <= 0 || !pairs) return EGM_ERR_ARG;
+    *graph = nullptr;
+    Plan pl;
+    egm_status s = make_plan(pairs, npairs, pl);
+    if (s != EGM_OK) return s;
+    if ((s = check_out(pairs, npairs, out)) != EGM_OK) return s;
+    const bool csr = out->cand_offsets != nullptr;
+    EGM_TRY(cudaSetDevice(c->device));
+    egm_graph *g = new (std::nothrow) egm_graph();
+    if (!g) return EGM_ERR_NOMEM;
+    g->ctx = c;
+    cudaError_t e = reserve(g->sc, pl.nq, pl.nr, pl.ntab, npairs);
+    std::vector<unsigned char> h(sizeof(PairDesc) * npairs + sizeof(int64_t) * 2 * (npairs + 1));
+    memcpy(h.data(), pl.pd.data(), sizeof(PairDesc) * npairs);
+    memcpy(h.data() + sizeof(PairDesc) * npairs, pl.qoffs.data(), sizeof(int64_t) * (npairs + 1));
+    memcpy(h.data() + sizeof(PairDesc) * npairs + sizeof(int64_t) * (npairs + 1), pl.roffs.data(),
+           sizeof(int64_t) * (npairs + 1));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(g->sc.pairs.ptr, h.data(), sizeof(PairDesc) * npairs, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->sc.offs.ptr, h.data() + sizeof(PairDesc) * npairs, sizeof(int64_t) * 2 * (npairs + 1),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(g->sc.small.ptr, 0, 256);
+    cudaStream_t cs = nullptr;
+    cudaGraph_t gr = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        const Launch L = make_launch(g->sc, false, c->params, pl, npairs, out);
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = cudaMemsetAsync(L.status, 0, sizeof(uint32_t), cs);
+            if (e2 == cudaSuccess) e2 = enqueue_pipeline(L, g->sc, csr, pl.max_n, cs, nullptr);
+            e = cudaStreamEndCapture(cs, &gr);
+            if (e == cudaSuccess) e = e2;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        egm_graph_destroy(g);
+        return from_cuda(e);
+    }
+    *graph = g;
+    return EGM_OK;
+}
+
+egm_status egm_graph_launch(egm_graph *g) {
+    if (!g || !g->exec) return EGM_ERR_ARG;
+    egm_ctx *c = g->ctx;
+    EGM_TRY(cudaSetDevice(c->device));
+    EGM_TRY(cudaGraphLaunch(g->exec, c->stream));
+    if (!c->params.sync) return EGM_OK;
+    EGM_TRY(cudaMemcpyAsync(c->h_status, g->sc.small.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    EGM_TRY(cudaStreamSynchronize(c->stream));
+    return from_bits(*c->h_status);
+}
+
+egm_status egm_graph_destroy(egm_graph *g) {
+    if (!g) return EGM_OK;
+    cudaSetDevice(g->ctx->device);
+    cudaStreamSynchronize(g->ctx->stream);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    g->sc.release();
+    delete g;
+    return EGM_OK;
 }
 
 egm_status egm_set_timing(egm_ctx *c, int32_t enable) {

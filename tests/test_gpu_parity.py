@@ -395,3 +395,29 @@ def test_error_statuses(mt):
     # the context stays usable after every error
     o = mt.match(d["xy1"], d["xy2"], d["F"], 2.0, *args)
     assert int((o["best"] >= 0).sum()) > 0
+
+
+def test_graph_replay_equals_batch(mt):
+    """egm_graph_create / egm_graph_launch replay the batch pipeline; the graph
+    sees new data behind the same pointers."""
+    import torch
+
+    scenes = synth.config3(seed=3, npairs=8, scale=0.1)
+    items = [mt.to_device(s) for s in scenes]
+    M = sum(s.m for s in scenes)
+    out = mt._alloc_out(M, False, 0)
+    g = mt.graph_create(items, out)
+    for _ in range(2):
+        assert g.launch() == 0
+    ref = mt.match_batch(items)
+    for k in ("best", "second", "flags", "best_d", "second_d"):
+        assert torch.equal(out[k], ref[k]), k
+    # new descriptors in place: the replay must follow them
+    for it in items:
+        it["desc2"].copy_(torch.flip(it["desc2"], dims=[0]))
+    assert g.launch() == 0
+    ref2 = mt.match_batch(items)
+    for k in ("best", "second", "flags"):
+        assert torch.equal(out[k], ref2[k]), k
+    assert not torch.equal(ref["best"], ref2["best"])
+    g.close()
