@@ -324,3 +324,26 @@ def uniform_pair(rng, m, n, F, *, w=640, h=480, eps=2.0, kind=DESC_U8_L2, dim=12
     return Scene(xy1=xy1, xy2=xy2, F=np.asarray(F, dtype=np.float64), eps=eps, desc1=d1,
                  desc2=d2, kind=kind, dim=dim, width=w, height=h,
                  gt=np.zeros((0, 2), np.int64))
+
+
+# --------------------------------------------------------------------------
+# Initial weights of the tolerance network (random numbers only).
+# Flat layout: W1 (64,5), b1 (64), W2 (64,64), b2 (64), W3 (64,64), b3 (64),
+# W4 (1,64), b4 (1); rows are output units.
+# --------------------------------------------------------------------------
+MLP_SIZES = ((64, 5), (64, 64), (64, 64), (1, 64))
+
+
+def mlp_param_count() -> int:
+    return sum(o * i + o for o, i in MLP_SIZES)
+
+
+def mlp_init(seed: int = 0) -> np.ndarray:
+    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and zero biases, float32."""
+    rng = np.random.default_rng([seed, 77])
+    parts = []
+    for o, i in MLP_SIZES:
+        bound = 1.0 / math.sqrt(i)
+        parts.append(rng.uniform(-bound, bound, size=o * i))
+        parts.append(np.zeros(o))
+    return np.concatenate(parts).astype(np.float32)
