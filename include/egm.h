@@ -236,6 +236,48 @@ egm_status egm_sync(egm_ctx *ctx);
 egm_status egm_intervals(egm_ctx *ctx, const egm_pair *pair, double *theta, double *delta,
                          double *e3, int32_t *mode);
 
+/*
+ * Learned per-keypoint tolerance.  The paper names per-point tolerances as a
+ * promising direction (Sec. 6) without a model; this network, its features
+ * and its loss are the library's reading:
+ *   features  (ln s, orientation / 2 pi, ln response, x / W, y / H) computed
+ *             on the device from raw [n][5] float32 rows
+ *             (scale s > 0, orientation in radians, response > 0, x / W, y / H)
+ *   network   5 -> 64 -> 64 -> 64 -> 1, GELU, eps = softplus(z) + 0.25 px;
+ *             FP32 master weights rounded to BF16 for every product, FP32 sums
+ *   training  pinball (quantile) loss of the residual r - eps at quantile q,
+ *             Adam (0.9, 0.999, 1e-8); r = distance of a true match from its
+ *             epipolar line (Eq. 3), see egm_pair_residuals
+ * Parameters are a flat float32 vector of EGM_MLP_PARAMS values:
+ * W1 (64x5), b1, W2 (64x64), b2, W3 (64x64), b3, W4 (1x64), b4, rows = outputs.
+ * The object holds the parameters, the Adam moments and the step count on
+ * the context's device; calls run on the context's stream and wait for it.
+ */
+#define EGM_MLP_PARAMS 8769
+typedef struct egm_mlp egm_mlp;
+egm_status egm_mlp_create(egm_ctx *ctx, const float *params, egm_mlp **mlp);   /* params: host */
+egm_status egm_mlp_destroy(egm_mlp *mlp);
+/* Checkpoint (host pointers, any may be NULL). */
+egm_status egm_mlp_get_state(egm_mlp *mlp, float *params, float *adam_m, float *adam_v, int64_t *step);
+egm_status egm_mlp_set_state(egm_mlp *mlp, const float *params, const float *adam_m, const float *adam_v,
+                             int64_t step);
+/* eps [n] float64 (device) for features [n][5] float32 (device); the output
+ * can be passed as egm_pair.eps2. */
+egm_status egm_mlp_infer(egm_mlp *mlp, const float *feat, int64_t n, double *eps);
+/* Gradient of the mean pinball loss (device outputs: grad [EGM_MLP_PARAMS], loss [1]). */
+egm_status egm_mlp_grad(egm_mlp *mlp, const float *feat, const float *resid, int64_t n, float quantile, float *grad,
+                        float *loss);
+/* One Adam step on a batch; loss [1] (device, may be NULL) receives the batch loss. */
+egm_status egm_mlp_train_step(egm_mlp *mlp, const float *feat, const float *resid, int64_t n, float lr,
+                              float quantile, float *loss);
+
+/* Exact distances (Eq. 3, the brute force's FP64 evaluation) of the pairs
+ * (qi[t], rj[t]) of one image pair: dist [k] float64.  Device pointers; only
+ * xy1, xy2, F, m and n of the pair are read.  An index outside [0, m) or
+ * [0, n) gives NaN; a degenerate line (a = b = 0) gives +inf. */
+egm_status egm_pair_residuals(egm_ctx *ctx, const egm_pair *pair, const int32_t *qi, const int32_t *rj, int64_t k,
+                              double *dist);
+
 /* Work counters of the last match call, for metrics (host memory). */
 typedef struct egm_stats {
     int64_t queries;        /* queries processed */

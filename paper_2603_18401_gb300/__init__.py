@@ -14,7 +14,7 @@ from ._egm import (EGM_DESC_BIN, EGM_DESC_F32_L2, EGM_DESC_U8_L2, EGM_ERR_CAPACI
                    EGM_FLAG_DEGENERATE_LINE, EGM_FLAG_HAS_BEST, EGM_FLAG_NO_SECOND,
                    EGM_FLAG_RATIO_PASS, EGM_OK, EgmError, check, load)
 
-__all__ = ["Matcher", "EgmError", "load", "row_bytes", "EGM_DESC_U8_L2", "EGM_DESC_F32_L2",
+__all__ = ["Matcher", "TolNet", "EgmError", "load", "row_bytes", "EGM_DESC_U8_L2", "EGM_DESC_F32_L2",
            "EGM_DESC_BIN", "EGM_FLAG_HAS_BEST", "EGM_FLAG_RATIO_PASS", "EGM_FLAG_NO_SECOND",
            "EGM_FLAG_DEGENERATE_LINE"]
 
@@ -246,6 +246,22 @@ class Matcher:
         check(self.egm_match_pair_host(p, s), "egm_match_pair_host")
         return o
 
+    def tolnet(self, params) -> "TolNet":
+        """A learned-tolerance network on this context (egm_mlp_create)."""
+        return TolNet(self, params)
+
+    def residuals(self, xy1, xy2, F, qi, rj):
+        """Exact distances [k] float64 of the pairs (qi[t], rj[t]) from their epipolar lines."""
+        torch = self.torch
+        pair = self.make_pair(xy1, xy2, F, 0.0)
+        qi = torch.as_tensor(qi, dtype=torch.int32).to(self.device).contiguous()
+        rj = torch.as_tensor(rj, dtype=torch.int32).to(self.device).contiguous()
+        out = torch.empty(qi.shape[0], dtype=torch.float64, device=self.device)
+        check(self.lib.egm_pair_residuals(self.ctx, C.byref(pair), _ptr(qi), _ptr(rj), qi.shape[0], _ptr(out)),
+              "egm_pair_residuals")
+        self.sync()
+        return out
+
     def intervals(self, xy2, F, eps, width, height):
         """egm_intervals: (theta, delta, e3, mode) as device tensors."""
         torch = self.torch
@@ -259,6 +275,82 @@ class Matcher:
         st = self.lib.egm_intervals(self.ctx, C.byref(pair), _ptr(th), _ptr(de), _ptr(e3), _ptr(mode))
         check(st, "egm_intervals")
         return th[:n], de[:n], e3, int(mode.item())
+
+
+class TolNet:
+    """Learned per-keypoint tolerance (egm_mlp): eps = softplus(MLP(features)) + 0.25 px.
+
+    Features are [n, 5] float32 device rows (scale, orientation, response,
+    x / W, y / H); parameters a flat float32 vector of EGM_MLP_PARAMS values.
+    """
+
+    def __init__(self, mt: Matcher, params):
+        import numpy as np
+
+        self.mt, self.lib, self.torch = mt, mt.lib, mt.torch
+        p = np.ascontiguousarray(np.asarray(params, np.float32))
+        if p.size != _egm.EGM_MLP_PARAMS:
+            raise ValueError(f"expected {_egm.EGM_MLP_PARAMS} parameters, got {p.size}")
+        h = C.c_void_p()
+        check(self.lib.egm_mlp_create(mt.ctx, p.ctypes.data_as(C.c_void_p), C.byref(h)), "egm_mlp_create")
+        self.handle = h
+
+    def _feat(self, feat):
+        t = self.torch.as_tensor(feat, dtype=self.torch.float32).to(self.mt.device).contiguous()
+        if t.ndim != 2 or t.shape[1] != 5:
+            raise ValueError("features must be [n, 5]")
+        return t
+
+    def infer(self, feat):
+        """eps [n] float64 on the device."""
+        f = self._feat(feat)
+        eps = self.torch.empty(f.shape[0], dtype=self.torch.float64, device=self.mt.device)
+        check(self.lib.egm_mlp_infer(self.handle, _ptr(f), f.shape[0], _ptr(eps)), "egm_mlp_infer")
+        return eps
+
+    def grad(self, feat, resid, quantile):
+        """(gradient [EGM_MLP_PARAMS] float32, mean pinball loss) on the device."""
+        torch = self.torch
+        f = self._feat(feat)
+        r = torch.as_tensor(resid, dtype=torch.float32).to(self.mt.device).contiguous()
+        g = torch.empty(_egm.EGM_MLP_PARAMS, dtype=torch.float32, device=self.mt.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.mt.device)
+        check(self.lib.egm_mlp_grad(self.handle, _ptr(f), _ptr(r), f.shape[0], float(quantile), _ptr(g),
+                                    _ptr(loss)), "egm_mlp_grad")
+        return g, loss
+
+    def train_step(self, feat, resid, lr, quantile, loss=None):
+        """One Adam step; loss (a [1] float32 device tensor, optional) receives the batch loss."""
+        check(self.lib.egm_mlp_train_step(self.handle, _ptr(feat), _ptr(resid), feat.shape[0], float(lr),
+                                          float(quantile), _ptr(loss)), "egm_mlp_train_step")
+
+    def state(self):
+        import numpy as np
+
+        n = _egm.EGM_MLP_PARAMS
+        p, m, v = (np.empty(n, np.float32) for _ in range(3))
+        step = C.c_int64()
+        check(self.lib.egm_mlp_get_state(self.handle, p.ctypes.data_as(C.c_void_p), m.ctypes.data_as(C.c_void_p),
+                                         v.ctypes.data_as(C.c_void_p), C.byref(step)), "egm_mlp_get_state")
+        return dict(params=p, adam_m=m, adam_v=v, step=int(step.value))
+
+    def load_state(self, st):
+        import numpy as np
+
+        a = [np.ascontiguousarray(np.asarray(st[k], np.float32)) for k in ("params", "adam_m", "adam_v")]
+        check(self.lib.egm_mlp_set_state(self.handle, *(x.ctypes.data_as(C.c_void_p) for x in a),
+                                         int(st["step"])), "egm_mlp_set_state")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            self.lib.egm_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class _Graph:

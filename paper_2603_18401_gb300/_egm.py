@@ -35,6 +35,8 @@ EGM_FORM_AUTO = 0
 EGM_FORM_PLAIN = 1
 EGM_FORM_BANDED = 2
 
+EGM_MLP_PARAMS = 8769
+
 
 class egm_pair(C.Structure):
     _fields_ = [
@@ -87,6 +89,17 @@ SIGNATURES = {
                                    C.POINTER(C.c_void_p)]),
     "egm_graph_launch": (C.c_int, [C.c_void_p]),
     "egm_graph_destroy": (C.c_int, [C.c_void_p]),
+    "egm_mlp_create": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "egm_mlp_destroy": (C.c_int, [C.c_void_p]),
+    "egm_mlp_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]),
+    "egm_mlp_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
+    "egm_mlp_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "egm_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_void_p,
+                               C.c_void_p]),
+    "egm_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_float,
+                                     C.c_void_p]),
+    "egm_pair_residuals": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.c_void_p, C.c_void_p, C.c_int64,
+                                     C.c_void_p]),
     "egm_sync": (C.c_int, [C.c_void_p]),
     "egm_intervals": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p]),

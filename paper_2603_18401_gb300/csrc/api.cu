@@ -661,6 +661,135 @@ egm_status egm_graph_destroy(egm_graph *g) {
     return EGM_OK;
 }
 
+}  // extern "C"
+
+struct egm_mlp {
+    egm_ctx *ctx = nullptr;
+    DevBuf params, m, v, grad, pre, z, loss;
+    int64_t step = 0;
+};
+
+extern "C" {
+
+egm_status egm_mlp_create(egm_ctx *c, const float *params, egm_mlp **out) {
+    if (!c || !params || !out) return EGM_ERR_ARG;
+    *out = nullptr;
+    if (mlp_param_count() != EGM_MLP_PARAMS) return EGM_ERR_UNIMPLEMENTED;
+    EGM_TRY(cudaSetDevice(c->device));
+    egm_mlp *m = new (std::nothrow) egm_mlp();
+    if (!m) return EGM_ERR_NOMEM;
+    m->ctx = c;
+    const size_t pb = sizeof(float) * EGM_MLP_PARAMS;
+    cudaError_t e = grow(m->params, pb);
+    if (e == cudaSuccess) e = grow(m->m, pb);
+    if (e == cudaSuccess) e = grow(m->v, pb);
+    if (e == cudaSuccess) e = grow(m->grad, pb);
+    if (e == cudaSuccess) e = grow(m->loss, 64);
+    if (e == cudaSuccess) e = cudaMemcpy(m->params.ptr, params, pb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m->m.ptr, 0, pb);
+    if (e == cudaSuccess) e = cudaMemset(m->v.ptr, 0, pb);
+    if (e == cudaSuccess) e = cudaMemset(m->grad.ptr, 0, pb);
+    if (e != cudaSuccess) {
+        egm_mlp_destroy(m);
+        return from_cuda(e);
+    }
+    *out = m;
+    return EGM_OK;
+}
+
+egm_status egm_mlp_destroy(egm_mlp *m) {
+    if (!m) return EGM_OK;
+    cudaSetDevice(m->ctx->device);
+    cudaStreamSynchronize(m->ctx->stream);
+    DevBuf *b[] = {&m->params, &m->m, &m->v, &m->grad, &m->pre, &m->z, &m->loss};
+    for (DevBuf *x : b)
+        if (x->ptr) cudaFree(x->ptr);
+    delete m;
+    return EGM_OK;
+}
+
+egm_status egm_mlp_get_state(egm_mlp *m, float *params, float *am, float *av, int64_t *step) {
+    if (!m) return EGM_ERR_ARG;
+    EGM_TRY(cudaSetDevice(m->ctx->device));
+    EGM_TRY(cudaStreamSynchronize(m->ctx->stream));
+    const size_t pb = sizeof(float) * EGM_MLP_PARAMS;
+    if (params) EGM_TRY(cudaMemcpy(params, m->params.ptr, pb, cudaMemcpyDeviceToHost));
+    if (am) EGM_TRY(cudaMemcpy(am, m->m.ptr, pb, cudaMemcpyDeviceToHost));
+    if (av) EGM_TRY(cudaMemcpy(av, m->v.ptr, pb, cudaMemcpyDeviceToHost));
+    if (step) *step = m->step;
+    return EGM_OK;
+}
+
+egm_status egm_mlp_set_state(egm_mlp *m, const float *params, const float *am, const float *av, int64_t step) {
+    if (!m || step < 0) return EGM_ERR_ARG;
+    EGM_TRY(cudaSetDevice(m->ctx->device));
+    EGM_TRY(cudaStreamSynchronize(m->ctx->stream));
+    const size_t pb = sizeof(float) * EGM_MLP_PARAMS;
+    if (params) EGM_TRY(cudaMemcpy(m->params.ptr, params, pb, cudaMemcpyHostToDevice));
+    if (am) EGM_TRY(cudaMemcpy(m->m.ptr, am, pb, cudaMemcpyHostToDevice));
+    if (av) EGM_TRY(cudaMemcpy(m->v.ptr, av, pb, cudaMemcpyHostToDevice));
+    m->step = step;
+    return EGM_OK;
+}
+
+egm_status egm_mlp_infer(egm_mlp *m, const float *feat, int64_t n, double *eps) {
+    if (!m || n < 0 || (n > 0 && (!feat || !eps))) return EGM_ERR_ARG;
+    EGM_TRY(cudaSetDevice(m->ctx->device));
+    EGM_TRY(launch_mlp_forward(as<float>(m->params), feat, n, eps, nullptr, nullptr, m->ctx->stream));
+    EGM_TRY(cudaStreamSynchronize(m->ctx->stream));
+    return EGM_OK;
+}
+
+namespace {
+egm_status mlp_backprop(egm_mlp *m, const float *feat, const float *resid, int64_t n, float q) {
+    cudaStream_t st = m->ctx->stream;
+    EGM_TRY(grow(m->pre, sizeof(float) * 3 * 64 * (size_t)n));
+    EGM_TRY(grow(m->z, sizeof(float) * (size_t)n));
+    EGM_TRY(cudaMemsetAsync(m->grad.ptr, 0, sizeof(float) * EGM_MLP_PARAMS, st));
+    EGM_TRY(cudaMemsetAsync(m->loss.ptr, 0, sizeof(float), st));
+    EGM_TRY(launch_mlp_forward(as<float>(m->params), feat, n, nullptr, as<float>(m->pre), as<float>(m->z), st));
+    EGM_TRY(launch_mlp_backward(as<float>(m->params), feat, resid, n, q, as<float>(m->pre), as<float>(m->z),
+                                as<float>(m->grad), as<float>(m->loss), st));
+    return EGM_OK;
+}
+}  // namespace
+
+egm_status egm_mlp_grad(egm_mlp *m, const float *feat, const float *resid, int64_t n, float q, float *grad,
+                        float *loss) {
+    if (!m || n <= 0 || !feat || !resid || !(q > 0.0f && q < 1.0f)) return EGM_ERR_ARG;
+    EGM_TRY(cudaSetDevice(m->ctx->device));
+    egm_status s = mlp_backprop(m, feat, resid, n, q);
+    if (s != EGM_OK) return s;
+    cudaStream_t st = m->ctx->stream;
+    if (grad) EGM_TRY(cudaMemcpyAsync(grad, m->grad.ptr, sizeof(float) * EGM_MLP_PARAMS, cudaMemcpyDeviceToDevice, st));
+    if (loss) EGM_TRY(cudaMemcpyAsync(loss, m->loss.ptr, sizeof(float), cudaMemcpyDeviceToDevice, st));
+    EGM_TRY(cudaStreamSynchronize(st));
+    return EGM_OK;
+}
+
+egm_status egm_mlp_train_step(egm_mlp *m, const float *feat, const float *resid, int64_t n, float lr, float q,
+                              float *loss) {
+    if (!m || n <= 0 || !feat || !resid || !(q > 0.0f && q < 1.0f) || !(lr > 0.0f)) return EGM_ERR_ARG;
+    EGM_TRY(cudaSetDevice(m->ctx->device));
+    egm_status s = mlp_backprop(m, feat, resid, n, q);
+    if (s != EGM_OK) return s;
+    cudaStream_t st = m->ctx->stream;
+    if (loss) EGM_TRY(cudaMemcpyAsync(loss, m->loss.ptr, sizeof(float), cudaMemcpyDeviceToDevice, st));
+    m->step += 1;
+    EGM_TRY(launch_adam(as<float>(m->params), as<float>(m->grad), as<float>(m->m), as<float>(m->v), lr, m->step, st));
+    return EGM_OK;
+}
+
+egm_status egm_pair_residuals(egm_ctx *c, const egm_pair *pair, const int32_t *qi, const int32_t *rj, int64_t k,
+                              double *dist) {
+    if (!c || !pair || k < 0 || (k > 0 && (!qi || !rj || !dist || !pair->xy1 || !pair->xy2 || !pair->F)))
+        return EGM_ERR_ARG;
+    EGM_TRY(cudaSetDevice(c->device));
+    EGM_TRY(launch_residuals(pair->xy1, pair->xy2, pair->F, pair->m, pair->n, qi, rj, k, dist, c->stream));
+    if (c->params.sync) EGM_TRY(cudaStreamSynchronize(c->stream));
+    return EGM_OK;
+}
+
 egm_status egm_set_timing(egm_ctx *c, int32_t enable) {
     if (!c) return EGM_ERR_ARG;
     c->timing_on = enable != 0;

@@ -98,3 +98,19 @@ def test_matcher_requires_library_and_gpu():
 
     with pytest.raises(Exception):
         Matcher(0)
+
+
+def test_header_constants_match_binding():
+    """Every #define and enum value of the header has the same value in the binding."""
+    from paper_2603_18401_gb300 import _egm
+
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = {k: int(v, 0) for k, v in re.findall(r"#define\s+(EGM_\w+)\s+(-?(?:0x[0-9a-fA-F]+|\d+))\b", text)}
+    consts.update({k: int(v) for k, v in re.findall(r"\b(EGM_\w+)\s*=\s*(-?\d+)", text)})
+    assert "EGM_MLP_PARAMS" in consts
+    for k, v in consts.items():
+        if hasattr(_egm, k):
+            assert getattr(_egm, k) == v, k
+    import synth
+
+    assert consts["EGM_MLP_PARAMS"] == synth.mlp_param_count()

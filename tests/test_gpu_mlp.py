@@ -1,0 +1,249 @@
+"""Learned per-keypoint tolerance on the GPU (egm_mlp_*, egm_pair_residuals)
+against the FP64 oracle in oracle/mlp.py and oracle.point_line_distance.
+
+The kernels round the FP32 master weights to BF16 and compute in FP32, so the
+oracle is evaluated at the BF16-rounded weights (the library's gradient is the
+gradient at the rounded weights) and the tolerances below are FP32 ones:
+a 64-wide FP32 dot product of O(1) terms carries ~1e-6 relative error, three
+layers and the transcendental functions keep it below 1e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16(x):
+    """Round float32 to the nearest BF16 value (ties to even), kept as float32."""
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+@pytest.fixture(scope="module")
+def mt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_18401_gb300 import Matcher
+
+    m = Matcher(0)
+    yield m
+    m.close()
+
+
+def params(seed):
+    th = synth.mlp_init(seed).astype(np.float64)
+    rng = np.random.default_rng([seed, 3])
+    k = 0
+    for o, i in synth.MLP_SIZES:   # non-zero biases so that every term is exercised
+        k += o * i
+        th[k:k + o] = rng.normal(0.0, 0.2, o)
+        k += o
+    return th.astype(np.float32)
+
+
+def feats(n, seed):
+    rng = np.random.default_rng([seed, 4])
+    s = np.exp(rng.uniform(0.0, math.log(16.0), n))
+    return np.stack([s, rng.uniform(0, 2 * math.pi, n), np.exp(rng.normal(0, 0.5, n)) / s,
+                     rng.uniform(0, 1, n), rng.uniform(0, 1, n)], axis=1).astype(np.float32)
+
+
+def oracle_u(f):
+    f = f.astype(np.float64)
+    return omlp.features(f[:, 0], f[:, 1], f[:, 2], f[:, 3], f[:, 4])
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 1000, 4133])
+def test_forward_matches_oracle(mt, n):
+    th = params(1)
+    f = feats(n, n)
+    net = mt.tolnet(th)
+    eps = net.infer(f).cpu().numpy()
+    ref, _ = omlp.forward(bf16(th), oracle_u(f))
+    np.testing.assert_allclose(eps, ref, rtol=1e-4, atol=1e-5)
+    assert np.all(eps >= 0.25)
+    net.close()
+
+
+def residuals_away_from(eps_ref, rng, gap=1e-3):
+    r = eps_ref * np.exp(rng.normal(0.0, 0.6, eps_ref.size))
+    close = np.abs(r - eps_ref) < gap
+    r[close] += 2 * gap        # no sample sits at the pinball loss's kink
+    return r
+
+
+@pytest.mark.parametrize("n,q", [(1, 0.9), (64, 0.5), (65, 0.95), (3000, 0.99)])
+def test_gradient_matches_oracle(mt, n, q):
+    th = params(2)
+    f = feats(n, 10 + n)
+    U = oracle_u(f)
+    thr = bf16(th).astype(np.float64)
+    eps_ref, _ = omlp.forward(thr, U)
+    r = residuals_away_from(eps_ref, np.random.default_rng(n))
+    net = mt.tolnet(th)
+    g, loss = net.grad(f, r.astype(np.float32), q)
+    g = g.cpu().numpy().astype(np.float64)
+    gref = omlp.grad(thr, U, r.astype(np.float32).astype(np.float64), q)
+    lref = omlp.loss(thr, U, r.astype(np.float32).astype(np.float64), q)
+    scale = np.abs(gref).max()
+    assert np.all(np.abs(g - gref) <= 2e-4 * scale + 1e-4 * np.abs(gref)), np.abs(g - gref).max() / scale
+    assert abs(float(loss.item()) - lref) <= 1e-4 * abs(lref) + 1e-7
+    net.close()
+
+
+def test_adam_matches_oracle_and_state_round_trips(mt):
+    torch = mt.torch
+    th = params(3)
+    n = 2048
+    f = feats(n, 33)
+    thr = bf16(th).astype(np.float64)
+    eps_ref, _ = omlp.forward(thr, oracle_u(f))
+    r = residuals_away_from(eps_ref, np.random.default_rng(5)).astype(np.float32)
+    rng = np.random.default_rng(6)
+    m0 = rng.normal(0, 1e-3, th.size).astype(np.float32)
+    v0 = rng.uniform(0, 1e-6, th.size).astype(np.float32)
+    net = mt.tolnet(th)
+    net.load_state(dict(params=th, adam_m=m0, adam_v=v0, step=4))
+    st = net.state()
+    assert st["step"] == 4 and np.array_equal(st["params"], th) and np.array_equal(st["adam_m"], m0)
+    g, _ = net.grad(f, r, 0.9)
+    g = g.cpu().numpy().astype(np.float64)
+    fd = torch.as_tensor(f).cuda()
+    rd = torch.as_tensor(r).cuda()
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    net.train_step(fd, rd, 1e-3, 0.9, loss)
+    st = net.state()
+    assert st["step"] == 5
+    p_ref, m_ref, v_ref = omlp.adam_step(th.astype(np.float64), m0.astype(np.float64), v0.astype(np.float64), g,
+                                         5, 1e-3)
+    # the step's own gradient differs from g only in the order of the atomic sums
+    np.testing.assert_allclose(st["adam_m"], m_ref, rtol=1e-5, atol=1e-9)
+    np.testing.assert_allclose(st["adam_v"], v_ref, rtol=1e-4, atol=1e-12)
+    np.testing.assert_allclose(st["params"], p_ref, rtol=0, atol=1e-6)
+    assert float(loss.item()) > 0
+    net.close()
+
+
+def test_checkpoint_resume_reproduces_training(mt):
+    torch = mt.torch
+    th = params(4)
+    f = torch.as_tensor(feats(4096, 44)).cuda()
+    r = torch.as_tensor(np.random.default_rng(7).gamma(2.0, 1.0, 4096).astype(np.float32)).cuda()
+    net = mt.tolnet(th)
+    for _ in range(3):
+        net.train_step(f, r, 3e-3, 0.9)
+    saved = net.state()
+    for _ in range(2):
+        net.train_step(f, r, 3e-3, 0.9)
+    a = net.state()
+    net2 = mt.tolnet(synth.mlp_init(99))
+    net2.load_state(saved)
+    for _ in range(2):
+        net2.train_step(f, r, 3e-3, 0.9)
+    b = net2.state()
+    assert a["step"] == b["step"] == 5
+    np.testing.assert_allclose(a["params"], b["params"], rtol=0, atol=1e-5)
+    net.close()
+    net2.close()
+
+
+def test_errors(mt):
+    from paper_2603_18401_gb300 import EgmError
+
+    with pytest.raises(ValueError):
+        mt.tolnet(np.zeros(10, np.float32))
+    net = mt.tolnet(params(0))
+    f = feats(16, 0)
+    with pytest.raises(EgmError):
+        net.grad(f, np.ones(16, np.float32), 1.5)
+    with pytest.raises(EgmError):
+        net.grad(f, np.ones(16, np.float32), 0.0)
+    assert net.infer(np.zeros((0, 5), np.float32)).numel() == 0
+    net.close()
+
+
+def test_residuals_bit_exact(mt):
+    import oracle
+
+    torch = mt.torch
+    sc = synth.config5(seed=3, npairs=1, scale=0.1)[0]
+    d = mt.to_device(sc)
+    rng = np.random.default_rng(8)
+    qi = np.concatenate([sc.gt[:, 0], rng.integers(0, sc.m, 500)]).astype(np.int32)
+    rj = np.concatenate([sc.gt[:, 1], rng.integers(0, sc.n, 500)]).astype(np.int32)
+    got = mt.residuals(d["xy1"], d["xy2"], d["F"], qi, rj).cpu().numpy()
+    ref = np.array([oracle.point_line_distance(sc.F, *sc.xy1[i], *sc.xy2[j]) for i, j in zip(qi, rj)])
+    assert np.array_equal(got, ref)
+    assert mt.residuals(d["xy1"], d["xy2"], d["F"], np.zeros(0, np.int32), np.zeros(0, np.int32)).numel() == 0
+    del torch
+
+
+def train_tolerance(mt, train, q, epochs, lr, batch, seed):
+    """Fit the network to the true matches' residuals of the training scenes."""
+    torch = mt.torch
+    F, R = [], []
+    for sc in train:
+        d = mt.to_device(sc)
+        F.append(sc.feat2[sc.gt[:, 1]])
+        R.append(mt.residuals(d["xy1"], d["xy2"], d["F"], sc.gt[:, 0], sc.gt[:, 1]))
+    f = torch.as_tensor(np.concatenate(F).astype(np.float32)).cuda()
+    r = torch.cat(R).float()
+    net = mt.tolnet(synth.mlp_init(seed))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    for _ in range(epochs):
+        perm = torch.randperm(f.shape[0], device="cuda", generator=g)
+        for b in range(0, f.shape[0] - batch + 1, batch):
+            idx = perm[b:b + batch]
+            net.train_step(f[idx].contiguous(), r[idx].contiguous(), lr, q)
+    return net
+
+
+def test_learned_tolerance_beats_fixed_at_equal_budget(mt):
+    """On scenes whose localisation noise grows with keypoint scale, the learned
+    per-keypoint eps finds more true matches than one fixed eps with the same
+    total band width (the same expected number of candidates)."""
+    import oracle
+
+    scenes = synth.config5(seed=11, npairs=40, scale=0.15)
+    train, test = scenes[:30], scenes[30:]
+    net = train_tolerance(mt, train, q=0.95, epochs=30, lr=3e-3, batch=1024, seed=0)
+    hit_l = hit_f = tot = 0
+    cand_l = cand_f = 0
+    for sc in test:
+        eps_l = net.infer(sc.feat2).cpu().numpy()
+        eps_f = float(eps_l.mean())
+        dist = np.array([oracle.point_line_distance(sc.F, *sc.xy1[i], *sc.xy2[j]) for i, j in sc.gt])
+        hit_l += int(np.sum(dist <= eps_l[sc.gt[:, 1]]))
+        hit_f += int(np.sum(dist <= eps_f))
+        tot += len(sc.gt)
+        d = mt.to_device(sc)
+        for e, acc in ((eps_l, "l"), (eps_f, "f")):
+            ev = e if np.ndim(e) == 0 else mt.torch.as_tensor(e).cuda()
+            o = mt.match(d["xy1"], d["xy2"], d["F"], ev, d["desc1"], d["desc2"], sc.kind, sc.dim,
+                         sc.width, sc.height, csr=True)
+            c = int(o["cand_offsets"][-1].item())
+            if acc == "l":
+                cand_l += c
+            else:
+                cand_f += c
+    rec_l, rec_f = hit_l / tot, hit_f / tot
+    assert rec_l > 0.93, rec_l
+    assert rec_l > rec_f + 0.03, (rec_l, rec_f)
+    assert cand_l < 1.15 * cand_f, (cand_l, cand_f)
+    net.close()
+
+
+def test_residuals_out_of_range_index_is_nan(mt):
+    sc = synth.config1(seed=1, scale=0.05)
+    d = mt.to_device(sc)
+    got = mt.residuals(d["xy1"], d["xy2"], d["F"], np.array([0, sc.m, -1, 0], np.int32),
+                       np.array([0, 0, 0, sc.n], np.int32)).cpu().numpy()
+    assert np.isfinite(got[0]) and np.all(np.isnan(got[1:]))
