@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-pairs", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--form", choices=["auto", "plain", "banded"], default="auto")
     return ap.parse_args()
 
 
@@ -237,7 +238,7 @@ def run_ours(args):
 
     torch.cuda.set_device(local)
     mt = Matcher(local)
-    mt.set_params(sync=False)
+    mt.set_params(sync=False, form={"auto": 0, "plain": 1, "banded": 2}[args.form])
     dev = [mt.to_device(s) for s in scs]
     outs = [mt._alloc_out(s.m, False, 0) for s in scs]
     pairs, ostr, keep = [], [], []

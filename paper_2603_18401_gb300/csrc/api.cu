@@ -37,10 +37,10 @@ T *as(DevBuf &b) { return reinterpret_cast<T *>(b.ptr); }
 
 // Device scratch of one pipeline instance (a context, or a captured graph).
 struct Scratch {
-    DevBuf pairs, geom, offs, keys, rec, tab, qrec, qcount, scan, longlist, small, counters, blkpair;
+    DevBuf pairs, geom, offs, keys, rec, tab, qrec, qcount, scan, longlist, small, counters, blkpair, band;
     void release() {
         DevBuf *b[] = {&pairs, &geom, &offs, &keys, &rec, &tab, &qrec, &qcount, &scan, &longlist, &small,
-                       &counters, &blkpair};
+                       &counters, &blkpair, &band};
         for (DevBuf *x : b) {
             if (x->ptr) cudaFree(x->ptr);
             x->ptr = nullptr;
@@ -53,6 +53,7 @@ struct Scratch {
 
 struct egm_ctx {
     int device = 0;
+    int sms = 1;       // streaming multiprocessors of the device
     cudaStream_t stream = nullptr;
     egm_params params;
     bool counters_on = false;
@@ -72,6 +73,9 @@ struct egm_ctx {
     size_t ev_used = 0;
     std::vector<size_t> ev_calls;   // first event of each timed call
     egm_timing tsum{};
+    // the banded form sorts the queries on a second stream, beside the reference sort
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
 
 namespace {
@@ -139,9 +143,11 @@ egm_status check_pair(const egm_pair *P) {
 
 struct Plan {
     std::vector<PairDesc> pd;
+    std::vector<int64_t> offs;      // query, reference and tile offsets: 3 x (npairs + 1)
     std::vector<int64_t> qoffs, roffs;
-    int64_t nq = 0, nr = 0, ntab = 0;
+    int64_t nq = 0, nr = 0, ntab = 0, ntiles = 0;
     int max_n = 0;
+    bool band_ok = false;           // every pair fits the banded form
 };
 
 egm_status make_plan(const egm_pair *pairs, int npairs, Plan &pl) {
@@ -181,17 +187,57 @@ egm_status make_plan(const egm_pair *pairs, int npairs, Plan &pl) {
     }
     pl.qoffs[npairs] = pl.nq;
     pl.roffs[npairs] = pl.nr;
+    pl.offs.resize(3 * (size_t)(npairs + 1));
+    const int tm = band_tile_queries();
+    pl.band_ok = true;
+    for (int p = 0; p <= npairs; p++) {
+        pl.offs[p] = pl.qoffs[p];
+        pl.offs[(npairs + 1) + p] = pl.roffs[p];
+        pl.offs[2 * (npairs + 1) + p] = pl.ntiles;
+        if (p < npairs) {
+            pl.ntiles += (pairs[p].m + tm - 1) / tm;
+            pl.band_ok = pl.band_ok && has_desc(pairs + p) && band_supported(pairs[p].kind, pairs[p].dim);
+        }
+    }
     return EGM_OK;
 }
 
-cudaError_t reserve(Scratch &c_, int64_t nq, int64_t nr, int64_t ntab, int npairs) {
+// The banded form runs when it is requested or left to the library, every
+// pair fits it, and no candidate lists are asked for.
+egm_status choose_band(const Plan &pl, const egm_params &prm, bool csr, bool &band) {
+    band = prm.form != EGM_FORM_PLAIN && pl.band_ok && !csr;
+    if (prm.form == EGM_FORM_BANDED && !band) return EGM_ERR_UNIMPLEMENTED;
+    return EGM_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Banded-form scratch: query permutation, packed operand rows, norms (padded
+// for the aligned 16-byte bulk copies that read past a pair's last row).
+struct BandLayout {
+    size_t qperm, descA, descB, qbkt, qsrt, rnorm, total;
+    BandLayout(int64_t nq, int64_t nr) {
+        const size_t rb = (size_t)band_row_bytes();
+        qperm = 0;
+        descA = qperm + align256(sizeof(uint32_t) * (size_t)std::max<int64_t>(nq, 1));
+        descB = descA + align256(rb * (size_t)std::max<int64_t>(nq, 1));
+        qbkt = descB + align256(rb * (size_t)std::max<int64_t>(nr, 1));
+        qsrt = qbkt + align256(sizeof(uint16_t) * (size_t)std::max<int64_t>(nq, 1));
+        rnorm = qsrt + align256(sizeof(QueryRec) * (size_t)std::max<int64_t>(nq, 1));
+        total = rnorm + align256(sizeof(float) * (size_t)(nr + 64));
+    }
+};
+
+cudaError_t reserve(Scratch &c_, int64_t nq, int64_t nr, int64_t ntab, int npairs, bool band) {
     Scratch *c = &c_;
     cudaError_t e;
+    if (band && (e = grow(c->band, BandLayout(nq, nr).total)) != cudaSuccess) return e;
     if ((e = grow(c->pairs, sizeof(PairDesc) * (size_t)std::max(npairs, 1))) != cudaSuccess) return e;
     if ((e = grow(c->geom, sizeof(PairGeom) * (size_t)std::max(npairs, 1))) != cudaSuccess) return e;
-    if ((e = grow(c->offs, sizeof(int64_t) * 2 * (size_t)(npairs + 1))) != cudaSuccess) return e;
+    if ((e = grow(c->offs, sizeof(int64_t) * 3 * (size_t)(npairs + 1))) != cudaSuccess) return e;
     if ((e = grow(c->keys, sizeof(uint32_t) * 6 * (size_t)std::max<int64_t>(nr, 1))) != cudaSuccess) return e;
-    if ((e = grow(c->rec, sizeof(float4) * (size_t)std::max<int64_t>(nr, 1))) != cudaSuccess) return e;
+    // 32 records of padding: bulk copies of a 32-row box may run past the last row
+    if ((e = grow(c->rec, sizeof(float4) * (size_t)(nr + 32))) != cudaSuccess) return e;
     if ((e = grow(c->tab, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntab, 1))) != cudaSuccess) return e;
     if ((e = grow(c->qrec, sizeof(QueryRec) * (size_t)std::max<int64_t>(nq, 1))) != cudaSuccess) return e;
     if ((e = grow(c->qcount, sizeof(int64_t) * (size_t)(nq + 1))) != cudaSuccess) return e;
@@ -204,7 +250,7 @@ cudaError_t reserve(Scratch &c_, int64_t nq, int64_t nr, int64_t ntab, int npair
 }
 
 Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const Plan &pl, int npairs,
-                   const egm_out *out) {
+                   const egm_out *out, bool band = false) {
     Scratch *c = &sc;
     Launch L;
     memset(&L, 0, sizeof(L));
@@ -234,6 +280,18 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
     L.ratio_num = prm.ratio_num;
     L.ratio_den = prm.ratio_den;
     L.max_n = pl.max_n;
+    if (band) {
+        const BandLayout bl(pl.nq, pl.nr);
+        unsigned char *b = static_cast<unsigned char *>(c->band.ptr);
+        L.qperm = reinterpret_cast<uint32_t *>(b + bl.qperm);
+        L.descA = b + bl.descA;
+        L.descB = b + bl.descB;
+        L.qbkt = reinterpret_cast<uint16_t *>(b + bl.qbkt);
+        L.qsrt = reinterpret_cast<QueryRec *>(b + bl.qsrt);
+        L.rnorm = reinterpret_cast<float *>(b + bl.rnorm);
+        L.tile_offs = as<int64_t>(c->offs) + 2 * (npairs + 1);
+        L.ntiles = pl.ntiles;
+    }
     L.kind = pl.pd.empty() ? -1 : pl.pd[0].kind;
     for (const PairDesc &d : pl.pd)
         if (d.kind != L.kind) L.kind = -1;
@@ -254,7 +312,7 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
 // Upload the pair table and offsets through pinned memory.  The staging area
 // is reused only after the previous upload has been consumed.
 cudaError_t upload_plan(egm_ctx *c, const Plan &pl, int npairs) {
-    const size_t tb = sizeof(PairDesc) * npairs, ob = sizeof(int64_t) * 2 * (npairs + 1);
+    const size_t tb = sizeof(PairDesc) * npairs, ob = sizeof(int64_t) * 3 * (npairs + 1);
     if (c->table_ev_pending) {
         cudaError_t e = cudaEventSynchronize(c->table_ev);
         if (e != cudaSuccess) return e;
@@ -270,8 +328,7 @@ cudaError_t upload_plan(egm_ctx *c, const Plan &pl, int npairs) {
     }
     unsigned char *h = static_cast<unsigned char *>(c->h_table);
     memcpy(h, pl.pd.data(), tb);
-    memcpy(h + tb, pl.qoffs.data(), sizeof(int64_t) * (npairs + 1));
-    memcpy(h + tb + sizeof(int64_t) * (npairs + 1), pl.roffs.data(), sizeof(int64_t) * (npairs + 1));
+    memcpy(h + tb, pl.offs.data(), ob);
     cudaError_t e = cudaMemcpyAsync(c->sc.pairs.ptr, h, tb, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(c->sc.offs.ptr, h + tb, ob, cudaMemcpyHostToDevice, c->stream);
@@ -302,7 +359,17 @@ egm_status finish(egm_ctx *c, bool sync) {
 
 // The kernel sequence of one match call.  `tc` receives stage events when
 // per-stage timing is on (NULL: no events, e.g. while capturing a graph).
-cudaError_t enqueue_pipeline(const Launch &L, Scratch &sc, bool csr, int max_n, cudaStream_t st, egm_ctx *tc) {
+// A second stream and its fork / join events (created on first use).
+cudaError_t ensure_side(egm_ctx *c) {
+    cudaError_t e = cudaSuccess;
+    if (!c->side) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !c->fork_ev) e = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess && !c->join_ev) e = cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming);
+    return e;
+}
+
+cudaError_t enqueue_pipeline(const Launch &L, Scratch &sc, bool csr, int max_n, cudaStream_t st, egm_ctx *tc,
+                             bool band, int sms, egm_ctx *sidec) {
     size_t tb = 0;
     if (tc && tc->timing_on) {
         tb = tc->ev_used;
@@ -321,11 +388,23 @@ cudaError_t enqueue_pipeline(const Launch &L, Scratch &sc, bool csr, int max_n, 
     if (tc) EGM_Q(mark(tc, tb, 1));
     EGM_Q(launch_prep(L, st));
     if (tc) EGM_Q(mark(tc, tb, 2));
+    if (band) {
+        // the query order runs beside the reference sort
+        EGM_Q(cudaEventRecord(sidec->fork_ev, st));
+        EGM_Q(cudaStreamWaitEvent(sidec->side, sidec->fork_ev, 0));
+        EGM_Q(launch_query_sort(L, sidec->side));
+        EGM_Q(cudaEventRecord(sidec->join_ev, sidec->side));
+    }
     EGM_Q(launch_sort(L, max_n, st));
+    if (band) EGM_Q(cudaStreamWaitEvent(st, sidec->join_ev, 0));
     if (tc) EGM_Q(mark(tc, tb, 3));
     EGM_Q(launch_post_sort(L, st));
+    if (band) EGM_Q(launch_pack(L, st));
     if (tc) EGM_Q(mark(tc, tb, 4));
-    if (csr) {
+    if (band) {
+        EGM_Q(launch_band(L, sms, st));
+        if (tc) EGM_Q(mark(tc, tb, 5));
+    } else if (csr) {
         uint32_t *long_list = as<uint32_t>(sc.longlist);
         uint32_t *long_count = as<uint32_t>(sc.small) + 16;
         EGM_Q(launch_stab(L, 1, st));
@@ -360,14 +439,17 @@ egm_status run_batch(egm_ctx *c, const egm_pair *pairs, int npairs, const egm_ou
     if (s != EGM_OK) return s;
     if ((s = check_out(pairs, npairs, out)) != EGM_OK) return s;
     const bool csr = out->cand_offsets != nullptr;
+    bool band = false;
+    if ((s = choose_band(pl, c->params, csr, band)) != EGM_OK) return s;
     EGM_TRY(cudaSetDevice(c->device));
-    EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, npairs));
+    if (band) EGM_TRY(ensure_side(c));
+    EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, npairs, band));
     EGM_TRY(upload_plan(c, pl, npairs));
-    Launch L = make_launch(c->sc, c->counters_on, c->params, pl, npairs, out);
+    Launch L = make_launch(c->sc, c->counters_on, c->params, pl, npairs, out, band);
     cudaStream_t st = c->stream;
     if (sync) EGM_TRY(cudaMemsetAsync(L.status, 0, sizeof(uint32_t), st));
     if (c->counters_on) EGM_TRY(cudaMemsetAsync(c->sc.counters.ptr, 0, 8 * sizeof(unsigned long long), st));
-    EGM_TRY(enqueue_pipeline(L, c->sc, csr, pl.max_n, st, c));
+    EGM_TRY(enqueue_pipeline(L, c->sc, csr, pl.max_n, st, c, band, c->sms, c));
     c->last.queries = pl.nq;
     c->last.refs = pl.nr;
     return finish(c, sync);
@@ -397,6 +479,7 @@ egm_status egm_create(egm_ctx **out, int device, void *stream) {
     c->stream = static_cast<cudaStream_t>(stream);
     egm_default_params(&c->params);
     cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_status, 64);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_counters, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->table_ev, cudaEventDisableTiming);
@@ -415,6 +498,12 @@ egm_status egm_destroy(egm_ctx *c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
     c->sc.release();
     if (c->stage.ptr) cudaFree(c->stage.ptr);
     if (c->h_table) cudaFreeHost(c->h_table);
@@ -451,7 +540,7 @@ egm_status egm_reserve(egm_ctx *c, int64_t queries, int64_t refs, int32_t pairs)
     if (!c || queries < 0 || refs < 0 || pairs < 0) return EGM_ERR_ARG;
     EGM_TRY(cudaSetDevice(c->device));
     const int64_t ntab = 4 * refs + (int64_t)std::max(pairs, 1) * (2 * kLevels + 32);
-    EGM_TRY(reserve(c->sc, queries, refs, ntab, std::max(pairs, 1)));
+    EGM_TRY(reserve(c->sc, queries, refs, ntab, std::max(pairs, 1), true));
     return EGM_OK;
 }
 
@@ -572,7 +661,7 @@ egm_status egm_intervals(egm_ctx *c, const egm_pair *pair, double *theta, double
     egm_status s = make_plan(&p, 1, pl);
     if (s != EGM_OK) return s;
     EGM_TRY(cudaSetDevice(c->device));
-    EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, 1));
+    EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, 1, false));
     EGM_TRY(upload_plan(c, pl, 1));
     Launch L = make_launch(c->sc, false, c->params, pl, 1, nullptr);
     if (c->params.sync) EGM_TRY(cudaMemsetAsync(L.status, 0, sizeof(uint32_t), c->stream));
@@ -600,31 +689,32 @@ egm_status egm_graph_create(egm_ctx *c, const egm_pair *pairs, int32_t npairs, c
     if (s != EGM_OK) return s;
     if ((s = check_out(pairs, npairs, out)) != EGM_OK) return s;
     const bool csr = out->cand_offsets != nullptr;
+    bool band = false;
+    if ((s = choose_band(pl, c->params, csr, band)) != EGM_OK) return s;
     EGM_TRY(cudaSetDevice(c->device));
     egm_graph *g = new (std::nothrow) egm_graph();
     if (!g) return EGM_ERR_NOMEM;
     g->ctx = c;
-    cudaError_t e = reserve(g->sc, pl.nq, pl.nr, pl.ntab, npairs);
-    std::vector<unsigned char> h(sizeof(PairDesc) * npairs + sizeof(int64_t) * 2 * (npairs + 1));
+    cudaError_t e = band ? ensure_side(c) : cudaSuccess;
+    if (e == cudaSuccess) e = reserve(g->sc, pl.nq, pl.nr, pl.ntab, npairs, band);
+    const size_t ob = sizeof(int64_t) * pl.offs.size();
+    std::vector<unsigned char> h(sizeof(PairDesc) * npairs + ob);
     memcpy(h.data(), pl.pd.data(), sizeof(PairDesc) * npairs);
-    memcpy(h.data() + sizeof(PairDesc) * npairs, pl.qoffs.data(), sizeof(int64_t) * (npairs + 1));
-    memcpy(h.data() + sizeof(PairDesc) * npairs + sizeof(int64_t) * (npairs + 1), pl.roffs.data(),
-           sizeof(int64_t) * (npairs + 1));
+    memcpy(h.data() + sizeof(PairDesc) * npairs, pl.offs.data(), ob);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) e = cudaMemcpy(g->sc.pairs.ptr, h.data(), sizeof(PairDesc) * npairs, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(g->sc.offs.ptr, h.data() + sizeof(PairDesc) * npairs, sizeof(int64_t) * 2 * (npairs + 1),
-                       cudaMemcpyHostToDevice);
+        e = cudaMemcpy(g->sc.offs.ptr, h.data() + sizeof(PairDesc) * npairs, ob, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(g->sc.small.ptr, 0, 256);
     cudaStream_t cs = nullptr;
     cudaGraph_t gr = nullptr;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
-        const Launch L = make_launch(g->sc, false, c->params, pl, npairs, out);
+        const Launch L = make_launch(g->sc, false, c->params, pl, npairs, out, band);
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaError_t e2 = cudaMemsetAsync(L.status, 0, sizeof(uint32_t), cs);
-            if (e2 == cudaSuccess) e2 = enqueue_pipeline(L, g->sc, csr, pl.max_n, cs, nullptr);
+            if (e2 == cudaSuccess) e2 = enqueue_pipeline(L, g->sc, csr, pl.max_n, cs, nullptr, band, c->sms, c);
             e = cudaStreamEndCapture(cs, &gr);
             if (e == cudaSuccess) e = e2;
         }

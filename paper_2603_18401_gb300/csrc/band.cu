@@ -1,0 +1,703 @@
+// Banded matching on the tensor cores.
+//
+// Queries sorted by the angle of their epipolar line (Sec. 4.2, alpha_i) and
+// references sorted by the angle of their tolerance interval (theta_j) make
+// the candidate blocks of a tile of consecutive queries dense: the union of
+// the tile's stabbing windows is a few contiguous runs of sorted references
+// (one or two per level).  All descriptor dot products of the tile against
+// those runs are one dense product on the tensor cores; the exact membership
+// test of Eq. 3 / Eq. 4 then selects, per query, the entries that count.
+//
+//   query_sort_kernel  one block per pair: counting sort of the queries by
+//                      the top bits of their quantised line angle; lines
+//                      without an FP32 view (FP64-only, degenerate) last.
+//   pack_kernel        descriptor rows of the sorted references and queries
+//                      as 256-byte tensor-core operands, with their norms:
+//                        u8 (128 values)  -> BF16, exact (integers < 2^8)
+//                        binary (256 bit) -> E4M3 0 / 1 per bit, exact
+//   band_kernel        persistent; one tile of 128 sorted queries at a time.
+//                      Warps 0-3 (one thread per query) build the tile's band
+//                      from the hull of their windows; warp 4 issues TMA loads
+//                      (128-byte swizzle) of the query tile and of 32-row
+//                      boxes of the band, and the tcgen05.mma chain
+//                      (M = 128, N = 32 per box, K = 128 BF16 or 256 E4M3)
+//                      into a double-buffered TMEM accumulator; warps 0-3 read
+//                      their lanes back, run the exact test on the columns in
+//                      their own windows, and keep the best two by
+//                      (distance, index):
+//                        L2^2    = |q|^2 + |r|^2 - 2 q.r   (integers < 2^24: exact in FP32)
+//                        Hamming = |q| + |r| - 2 q.r
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <math.h>
+
+#include "egm_internal.cuh"
+#include "tc.cuh"
+
+namespace egm {
+
+namespace {
+
+// ------------------------------------------------------------ query order
+constexpr int kQSortThreads = 1024;
+constexpr int kQSortPer = 16;  // bucket loads a thread issues before its atomics
+
+__global__ void __launch_bounds__(kQSortThreads) query_sort_kernel(Launch L) {
+    __shared__ uint32_t hist[kQBuckets];
+    __shared__ uint32_t wsum[kQSortThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const PairDesc &P = L.pairs[blockIdx.x];
+    const int m = P.m;
+    if (m == 0) return;
+    const uint16_t *bk = L.qbkt + P.q_off;
+    for (int b = tid; b < kQBuckets; b += kQSortThreads) hist[b] = 0;
+    __syncthreads();
+    for (int i0 = 0; i0 < m; i0 += kQSortThreads * kQSortPer) {
+        uint32_t v[kQSortPer];
+#pragma unroll
+        for (int k = 0; k < kQSortPer; k++) {
+            const int i = i0 + k * kQSortThreads + tid;
+            v[k] = i < m ? __ldg(bk + i) : 0xffffu;
+        }
+#pragma unroll
+        for (int k = 0; k < kQSortPer; k++)
+            if (v[k] != 0xffffu) atomicAdd(&hist[v[k]], 1u);
+    }
+    __syncthreads();
+    // exclusive scan: thread t owns buckets [kPer t, kPer t + kPer)
+    constexpr int kPer = (kQBuckets + kQSortThreads - 1) / kQSortThreads;
+    uint32_t c[kPer], tot = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+        const int b = tid * kPer + k;
+        c[k] = b < kQBuckets ? hist[b] : 0u;
+        tot += c[k];
+    }
+    uint32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = wsum[lane];
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += x;
+        }
+        wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    uint32_t run = wsum[warp] + incl - tot;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+        const int b = tid * kPer + k;
+        if (b < kQBuckets) hist[b] = run;
+        run += c[k];
+    }
+    __syncthreads();
+    for (int i0 = 0; i0 < m; i0 += kQSortThreads * kQSortPer) {
+        uint32_t v[kQSortPer];
+#pragma unroll
+        for (int k = 0; k < kQSortPer; k++) {
+            const int i = i0 + k * kQSortThreads + tid;
+            v[k] = i < m ? __ldg(bk + i) : 0xffffu;
+        }
+#pragma unroll
+        for (int k = 0; k < kQSortPer; k++) {
+            const int i = i0 + k * kQSortThreads + tid;
+            if (v[k] != 0xffffu) L.qperm[P.q_off + atomicAdd(&hist[v[k]], 1u)] = (uint32_t)i;
+        }
+    }
+}
+
+// ------------------------------------------------------------ packing
+constexpr int kRowB = 256;  // packed operand row: 128 BF16 or 256 E4M3 values
+
+__device__ __forceinline__ uint32_t bf16_pair(uint32_t lo, uint32_t hi) {
+    // bytes 0..255 are exact in FP32 and their BF16 is the top half of the FP32 word
+    return (__float_as_uint((float)lo) >> 16) | (__float_as_uint((float)hi) & 0xffff0000u);
+}
+
+__device__ __forceinline__ uint32_t e4m3_nibble(uint32_t n) {
+    // four bits -> four bytes of E4M3 1.0 (0x38) or 0
+    const uint32_t spread = (n & 1u) | ((n & 2u) << 7) | ((n & 4u) << 14) | ((n & 8u) << 21);
+    return spread * 0x38u;
+}
+
+// 8 threads per row; thread part t writes output bytes [32 t, 32 t + 32).
+__global__ void __launch_bounds__(256) pack_kernel(Launch L) {
+    const int64_t rows = L.nr + L.nq;
+    const int part = threadIdx.x & 7;
+    for (int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; g0 < ((rows + 3) / 4) * 4;
+         g0 += ((int64_t)gridDim.x * blockDim.x) >> 3) {
+        const bool valid = g0 < rows;
+        const bool is_ref = g0 < L.nr;
+        uint32_t nrm = 0, qi = 0;
+        uint4 o0 = make_uint4(0, 0, 0, 0), o1 = o0, qr = o0;
+        uint8_t *dst = nullptr;
+        if (valid) {
+            const int64_t g = is_ref ? g0 : g0 - L.nr;
+            const int p = pair_of(is_ref ? L.r_offs : L.q_offs, L.npairs, g);
+            const PairDesc &P = L.pairs[p];
+            const uint8_t *src;
+            if (is_ref) {
+                const uint32_t j = __float_as_uint(L.rec[g].w);
+                src = P.desc2 + (int64_t)j * P.row_bytes;
+                dst = L.descB + g * kRowB;
+            } else {
+                qi = L.qperm[g];
+                src = P.desc1 + (int64_t)qi * P.row_bytes;
+                dst = L.descA + g * kRowB;
+                if (part < 3) qr = __ldg(reinterpret_cast<const uint4 *>(L.qrec + P.q_off + qi) + part);
+            }
+            if (P.kind == EGM_DESC_U8_L2) {
+                const uint4 w = __ldg(reinterpret_cast<const uint4 *>(src) + part);
+                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+                uint32_t out[8];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t b0 = ws[k] & 0xffu, b1 = (ws[k] >> 8) & 0xffu, b2 = (ws[k] >> 16) & 0xffu,
+                                   b3 = ws[k] >> 24;
+                    out[2 * k] = bf16_pair(b0, b1);
+                    out[2 * k + 1] = bf16_pair(b2, b3);
+                    nrm += b0 * b0 + b1 * b1 + b2 * b2 + b3 * b3;
+                }
+                o0 = make_uint4(out[0], out[1], out[2], out[3]);
+                o1 = make_uint4(out[4], out[5], out[6], out[7]);
+            } else {
+                const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(src) + part);
+                nrm = __popc(w);
+                o0 = make_uint4(e4m3_nibble(w & 15u), e4m3_nibble((w >> 4) & 15u), e4m3_nibble((w >> 8) & 15u),
+                                e4m3_nibble((w >> 12) & 15u));
+                o1 = make_uint4(e4m3_nibble((w >> 16) & 15u), e4m3_nibble((w >> 20) & 15u),
+                                e4m3_nibble((w >> 24) & 15u), e4m3_nibble(w >> 28));
+            }
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o, 8);
+        if (valid) {
+            reinterpret_cast<uint4 *>(dst)[2 * part] = o0;
+            reinterpret_cast<uint4 *>(dst)[2 * part + 1] = o1;
+            if (is_ref) {
+                if (part == 0) L.rnorm[g0] = (float)nrm;
+            } else if (part < 3) {
+                // sorted query record; the padding carries the query index and norm
+                if (part == 2) {
+                    qr.z = qi;
+                    qr.w = __float_as_uint((float)nrm);
+                }
+                reinterpret_cast<uint4 *>(L.qsrt + (g0 - L.nr))[part] = qr;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ band kernel
+constexpr int kTM = 128;                 // queries per tile (MMA M, TMEM lanes)
+constexpr int kBoxR = 32;                // reference rows per TMA box (N per box)
+constexpr int kCB = 4;                   // boxes per MMA chunk
+constexpr int kCN = kBoxR * kCB;         // columns per chunk
+constexpr int kBandThreads = kTM + 32;   // four epilogue warps and the control warp
+constexpr uint32_t kTmemCols = 2 * kCN;  // double-buffered accumulator
+constexpr int kRnRow = kBoxR + 4;        // norms copied from a 16-byte aligned start
+constexpr int kGroup = 8;                // columns per TMEM load in the epilogue
+
+struct __align__(16) Piece {
+    uint32_t start, len, box0;
+    int32_t li;
+};
+
+struct BandSmem {
+    uint8_t A[2][kTM * 128];      // query tile, K halves (1024-byte aligned)
+    uint8_t B[2][2][kCN * 128];   // band chunk: stage, K half
+    float4 rec[2][kCN];           // (x - cx, y - cy, eps, index) of each column
+    float rn[2][kCB][kRnRow];     // norms of each box's rows
+    // fullB: a stage's operand rows landed; sfree: the MMA that read them is
+    // done; fullR: a stage's records and norms landed; done: an accumulator is
+    // ready; tfree: the epilogue has read it and the stage's records
+    uint64_t fullB[2], sfree[2], fullR[2], done[2], tfree[2], afull;
+    PairGeom g;
+    PairDesc pd;
+    Piece pc[2 * kLevels];
+    uint2 wr[4][kLevels][2];      // each epilogue warp's window ranges per level index
+    float wlo[4][kLevels], whi[4][kLevels];
+    int32_t wkind[4][kLevels];
+    int32_t lv[kLevels];
+    int32_t nlev, npc, nbox, gpair;
+    uint32_t tmem;
+    volatile uint32_t err;
+};
+
+static_assert(offsetof(BandSmem, B) % 1024 == 0, "operand tiles need 1024-byte alignment");
+static_assert(offsetof(BandSmem, rn) % 16 == 0, "bulk copy destinations need 16-byte alignment");
+// Two CTAs per SM hold the 2 x 256 TMEM columns; shared memory keeps a third
+// from becoming resident (its allocation would wait for one of them to end).
+constexpr size_t kSmPerSm = 228 * 1024, kSmPerCta = sizeof(BandSmem) + 1024 + 1024;
+static_assert(2 * kSmPerCta <= kSmPerSm && 3 * kSmPerCta > kSmPerSm, "exactly two CTAs per SM");
+
+__device__ __forceinline__ int sortable(float f) {
+    const int b = __float_as_int(f);
+    return b >= 0 ? b : b ^ 0x7fffffff;
+}
+__device__ __forceinline__ float unsortable(int b) { return __int_as_float(b >= 0 ? b : b ^ 0x7fffffff); }
+
+// Walks the tile's boxes in order: piece k, box b within the piece.
+struct BoxCursor {
+    int k = 0;
+    uint32_t b = 0;
+    __device__ __forceinline__ void next(const BandSmem &S, uint32_t &pos, uint32_t &len, int &li) {
+        const Piece &pc = S.pc[k];
+        pos = pc.start + b * kBoxR;
+        len = min((uint32_t)kBoxR, pc.len - b * kBoxR);
+        li = pc.li;
+        if (++b * kBoxR >= pc.len) {
+            k++;
+            b = 0;
+        }
+    }
+};
+
+__device__ __forceinline__ void copy16(void *dst, const void *src, int bytes, int lane) {
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    for (int k = lane; k < bytes / 16; k += 32) d4[k] = __ldg(s4 + k);
+}
+
+__device__ __forceinline__ void top2(unsigned long long key, unsigned long long &b1, unsigned long long &b2) {
+    if (key < b1) {
+        b2 = b1;
+        b1 = key;
+    } else if (key < b2) {
+        b2 = key;
+    }
+}
+
+__global__ void __launch_bounds__(kBandThreads, 2)
+    band_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Launch L) {
+    extern __shared__ uint8_t smraw[];
+    // 1024-byte alignment by pointer arithmetic on the shared array, so that
+    // accesses through S stay shared-memory accesses
+    BandSmem &S = *reinterpret_cast<BandSmem *>(smraw + ((1024u - (tc::smem_addr(smraw) & 1023u)) & 1023u));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const bool ctl = tid == kTM;
+    if (ctl) {
+        for (int s = 0; s < 2; s++) {
+            tc::mbar_init(&S.fullB[s], 1);
+            tc::mbar_init(&S.sfree[s], 1);
+            tc::mbar_init(&S.fullR[s], 1);
+            tc::mbar_init(&S.done[s], 1);
+            tc::mbar_init(&S.tfree[s], 4);
+        }
+        tc::mbar_init(&S.afull, 1);
+        tc::fence_mbar_init();
+        S.err = 0;
+        S.gpair = -1;
+        tc::prefetch_tmap(&tmA);
+        tc::prefetch_tmap(&tmB);
+    }
+    if (warp == 4) {
+        tc::tmem_alloc(&S.tmem, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    // a bounded wait; after any failure every later wait returns at once
+    auto wait = [&](uint64_t *bar, uint32_t parity) {
+        if (S.err) return false;
+        if (tc::mbar_wait(bar, parity)) return true;
+        S.err = 1;
+        atomicOr(L.status, kStTimeout);
+        return false;
+    };
+    uint32_t seq = 0, aload = 0;
+    unsigned long long nwin = 0, ncand = 0, nexact = 0;
+
+    for (int64_t tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
+        if (S.err) break;
+        const int p = pair_of(L.tile_offs, L.npairs, tile);
+        const int64_t q_off = L.q_offs[p];
+        const int64_t t0 = (tile - L.tile_offs[p]) * kTM;  // first sorted slot of the tile
+        const int mt = (int)min((int64_t)kTM, L.q_offs[p + 1] - q_off - t0);
+        // ---- the tile's queries (sorted records: index and norm in the padding)
+        QueryRec r;
+        const bool qv = warp < 4 && tid < mt;
+        if (qv) {
+            r = L.qsrt[q_off + t0 + tid];
+        } else {
+            r.A = r.B = r.C = r.key = r.aux0 = r.aux1 = r.E0 = r.E1 = 0.0f;
+            r.flags = EGM_FLAG_DEGENERATE_LINE;
+            r.pair = p;
+            r.pad[0] = r.pad[1] = 0;
+        }
+        const uint32_t qi = r.pad[0];
+        const float qn = __uint_as_float(r.pad[1]);
+        if (ctl) {
+            tc::mbar_arrive_expect_tx(&S.afull, 2 * kTM * 128);
+            tc::tma_load_2d(S.A[0], &tmA, 0, (int32_t)(q_off + t0), &S.afull);
+            tc::tma_load_2d(S.A[1], &tmA, 128, (int32_t)(q_off + t0), &S.afull);
+        }
+        const bool newpair = p != S.gpair;
+        __syncthreads();
+        if (warp == 4 && newpair) {
+            copy16(&S.g, L.geom + p, (int)sizeof(PairGeom), lane);
+            copy16(&S.pd, L.pairs + p, (int)sizeof(PairDesc), lane);
+            if (lane == 0) S.gpair = p;
+        }
+        __syncthreads();
+        const PairDesc &P = S.pd;
+        const PairGeom &G = S.g;
+        if (warp == 4) {
+            const uint32_t nz = __ballot_sync(0xffffffffu, G.cnt[lane] > 0);
+            if (nz & (1u << lane)) S.lv[__popc(nz & lt)] = lane;
+            if (lane == 0) S.nlev = __popc(nz);
+        }
+        __syncthreads();
+        const int nlev = S.nlev;
+        // ---- each warp's hull of its queries' windows, level by level
+        if (warp < 4) {
+            for (int li = 0; li < nlev; li++) {
+                const KeyWin w = key_window(G, r, S.lv[li]);
+                const uint32_t anyfull = __ballot_sync(0xffffffffu, w.kind == 1);
+                const uint32_t anyrng = __ballot_sync(0xffffffffu, w.kind == 2);
+                const int lo = __reduce_min_sync(0xffffffffu, sortable(w.kind == 2 ? w.lo : INFINITY));
+                const int hi = __reduce_max_sync(0xffffffffu, sortable(w.kind == 2 ? w.hi : -INFINITY));
+                if (lane == 0) {
+                    S.wkind[warp][li] = anyfull ? 1 : anyrng ? 2 : 0;
+                    S.wlo[warp][li] = unsortable(lo);
+                    S.whi[warp][li] = unsortable(hi);
+                }
+            }
+        }
+        __syncthreads();
+        // ---- windows as sorted positions: warps 0-3 their own, warp 4 the tile's (lane = level index)
+        {
+            const int li = lane;
+            KeyWin w;
+            w.kind = 0;
+            w.lo = w.hi = 0.0f;
+            if (li < nlev) {
+                if (warp < 4) {
+                    w.kind = S.wkind[warp][li];
+                    w.lo = S.wlo[warp][li];
+                    w.hi = S.whi[warp][li];
+                } else {
+                    float lo = INFINITY, hi = -INFINITY;
+                    for (int q = 0; q < 4; q++) {
+                        const int kq = S.wkind[q][li];
+                        if (kq == 1) w.kind = 1;
+                        if (kq == 2) {
+                            if (w.kind == 0) w.kind = 2;
+                            lo = fminf(lo, S.wlo[q][li]);
+                            hi = fmaxf(hi, S.whi[q][li]);
+                        }
+                    }
+                    w.lo = lo;
+                    w.hi = hi;
+                }
+            }
+            const int lvl = li < nlev ? S.lv[li] : kLevels;
+            const WinKeys wk = win_buckets(G, lvl, w);
+            uint32_t a = 0, b = 0;
+            if (wk.kind >= 2) {
+                const uint32_t *T = L.tab + P.t_off + G.tab[lvl];
+                a = __ldg(T + wk.ta);
+                b = __ldg(T + wk.tb);
+            }
+            const Window wn = window_ranges(wk, a, b);
+            if (warp < 4) {
+                if (li < nlev) {
+                    S.wr[warp][li][0] = make_uint2(wn.b0, wn.len0);
+                    S.wr[warp][li][1] = make_uint2(wn.b1, wn.len1);
+                }
+            } else {
+                const bool h0 = li < nlev && wn.len0 > 0, h1 = li < nlev && wn.len1 > 0;
+                const uint32_t m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
+                const int base = __popc(m0 & lt) + __popc(m1 & lt);
+                const uint32_t nb0 = h0 ? (wn.len0 + kBoxR - 1) / kBoxR : 0u;
+                const uint32_t nb1 = h1 ? (wn.len1 + kBoxR - 1) / kBoxR : 0u;
+                const uint32_t tot = nb0 + nb1;
+                uint32_t incl = tot;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += x;
+                }
+                const uint32_t excl = incl - tot;
+                if (h0) {
+                    Piece pc;
+                    pc.start = wn.b0;
+                    pc.len = wn.len0;
+                    pc.box0 = excl;
+                    pc.li = li;
+                    S.pc[base] = pc;
+                }
+                if (h1) {
+                    Piece pc;
+                    pc.start = wn.b1;
+                    pc.len = wn.len1;
+                    pc.box0 = excl + nb0;
+                    pc.li = li;
+                    S.pc[base + (h0 ? 1 : 0)] = pc;
+                }
+                if (lane == 31) {
+                    S.npc = __popc(m0) + __popc(m1);
+                    S.nbox = (int)incl;
+                }
+            }
+        }
+        __syncthreads();
+        const int nbox = S.nbox;
+        const int nchunk = (nbox + kCB - 1) / kCB;
+
+        if (ctl) {
+            // ---- control.  Operand rows of chunk c + 2 load once the MMA of
+            // chunk c has read its stage; the records and norms of chunk c load
+            // once the epilogue has finished chunk c - 2 (it reads them too).
+            // At a tile start every stage and accumulator is free.
+            BoxCursor curB, curR;
+            auto issueB = [&](int c) {
+                const uint32_t sq = seq + (uint32_t)c, st = sq & 1u, use = sq >> 1;
+                if (c >= 2 && !wait(&S.sfree[st], (use - 1) & 1u)) return;
+                const int nb = min(kCB, nbox - c * kCB);
+                tc::mbar_arrive_expect_tx(&S.fullB[st], (uint32_t)nb * (2 * kBoxR * 128));
+                for (int bb = 0; bb < nb; bb++) {
+                    uint32_t pos, len;
+                    int li;
+                    curB.next(S, pos, len, li);
+                    const int32_t row = (int32_t)(P.r_off + pos);
+                    tc::tma_load_2d(S.B[st][0] + bb * kBoxR * 128, &tmB, 0, row, &S.fullB[st]);
+                    tc::tma_load_2d(S.B[st][1] + bb * kBoxR * 128, &tmB, 128, row, &S.fullB[st]);
+                }
+            };
+            auto issueR = [&](int c) {
+                const uint32_t st = (seq + (uint32_t)c) & 1u;
+                const int nb = min(kCB, nbox - c * kCB);
+                tc::mbar_arrive_expect_tx(&S.fullR[st], (uint32_t)nb * (kBoxR * 16 + kRnRow * 4));
+                for (int bb = 0; bb < nb; bb++) {
+                    uint32_t pos, len;
+                    int li;
+                    curR.next(S, pos, len, li);
+                    const int64_t row = P.r_off + pos;
+                    tc::bulk_load(&S.rec[st][bb * kBoxR], L.rec + row, kBoxR * 16, &S.fullR[st]);
+                    tc::bulk_load(&S.rn[st][bb][0], L.rnorm + (row & ~(int64_t)3), kRnRow * 4, &S.fullR[st]);
+                }
+            };
+            for (int c = 0; c < nchunk && c < 2; c++) {
+                issueB(c);
+                issueR(c);
+            }
+            const bool bin = P.kind == EGM_DESC_BIN;
+            for (int c = 0; c < nchunk; c++) {
+                const uint32_t sq = seq + (uint32_t)c, st = sq & 1u, use = sq >> 1;
+                bool ok = true;
+                if (c >= 2) {
+                    ok = wait(&S.tfree[st], (use - 1) & 1u);
+                    if (ok) issueR(c);
+                }
+                ok = wait(&S.fullB[st], use & 1u) && ok;
+                if (c == 0) ok = wait(&S.afull, aload & 1u) && ok;
+                if (!ok) continue;
+                tc::tc_fence_after();
+                const int nb = min(kCB, nbox - c * kCB);
+                const uint32_t idesc = bin ? tc::idesc_e4m3(kTM, nb * kBoxR) : tc::idesc_bf16(kTM, nb * kBoxR);
+                const uint32_t dcol = tmem + st * kCN;
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const int h = k >> 2, kk = k & 3;
+                    const uint64_t ad = tc::sdesc_sw128(tc::smem_addr(S.A[h]) + 32 * kk);
+                    const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(S.B[st][h]) + 32 * kk);
+                    if (bin) tc::mma_e4m3(dcol, ad, bd, idesc, k > 0);
+                    else tc::mma_bf16(dcol, ad, bd, idesc, k > 0);
+                }
+                tc::mma_commit(&S.done[st]);
+                tc::mma_commit(&S.sfree[st]);
+                if (c + 2 < nchunk) issueB(c + 2);
+            }
+            // the query tile's load completes before its buffer is reused
+            if (nchunk == 0) wait(&S.afull, aload & 1u);
+        }
+        aload++;
+
+        // ---- epilogue: tests and best two over this warp's columns
+        unsigned long long b1 = ~0ull, b2 = ~0ull;
+        if (warp < 4 && nchunk > 0) {
+            BoxCursor cur;
+            const bool exact_only = (r.flags & kQExactOnly) != 0;
+            const bool live = qv && !(r.flags & EGM_FLAG_DEGENERATE_LINE);
+            const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
+            for (int c = 0; c < nchunk; c++) {
+                const uint32_t sq = seq + (uint32_t)c, st = sq & 1u;
+                const bool ok = wait(&S.done[st], (sq >> 1) & 1u) && wait(&S.fullR[st], (sq >> 1) & 1u);
+                tc::tc_fence_after();
+                const int nb = min(kCB, nbox - c * kCB);
+                for (int bb = 0; bb < nb; bb++) {
+                    uint32_t pos, len;
+                    int li;
+                    cur.next(S, pos, len, li);
+                    if (!ok) continue;
+                    // columns of this box inside the warp's own windows
+                    const uint2 w0 = S.wr[warp][li][0], w1 = S.wr[warp][li][1];
+                    const int x0 = (int)max(pos, w0.x) - (int)pos;
+                    const int x1 = (int)min(pos + len, w0.x + w0.y) - (int)pos;
+                    const int y0 = (int)max(pos, w1.x) - (int)pos;
+                    const int y1 = (int)min(pos + len, w1.x + w1.y) - (int)pos;
+                    if (x1 <= x0 && y1 <= y0) continue;
+                    const float *rnb = &S.rn[st][bb][(P.r_off + pos) & 3];
+                    const float4 *recb = &S.rec[st][bb * kBoxR];
+                    const uint32_t tb = tmem + lanebase + st * kCN + bb * kBoxR;
+#pragma unroll 1
+                    for (int g = 0; g < kBoxR; g += kGroup) {
+                        if (!((x0 < g + kGroup && x1 > g) || (y0 < g + kGroup && y1 > g))) continue;
+                        // the group's records and norms, loaded together with its accumulators
+                        float4 rcs[kGroup];
+                        float rns[kGroup];
+#pragma unroll
+                        for (int k = 0; k < kGroup; k++) {
+                            rcs[k] = recb[g + k];
+                            rns[k] = rnb[g + k];
+                        }
+                        uint32_t v[kGroup];
+                        tc::tmem_ld8(tb + g, v);
+                        tc::tmem_wait_ld();
+                        // membership of all columns first, branch-free (independent
+                        // work for the scheduler); then the few candidates
+                        uint32_t cm = 0, exm = 0;  // candidates; columns left to FP64
+#pragma unroll
+                        for (int k = 0; k < kGroup; k++) {
+                            const int col = g + k;
+                            const bool in = live && ((col >= x0 && col < x1) || (col >= y0 && col < y1));
+                            const float x = rcs[k].x, y = rcs[k].y, e = rcs[k].z;
+                            const float d = fabsf(fmaf(r.A, x, fmaf(r.B, y, r.C)));
+                            const float Sm = fmaf(fabsf(r.A), fabsf(x), fmaf(fabsf(r.B), fabsf(y), fabsf(r.C)));
+                            // FP32 rounding (16u S), the FP32 tolerance (2u eps) and the
+                            // distance between this line and the brute force's FP64 line
+                            const float lerr = fmaf(r.E1, fabsf(x) + fabsf(y) + 2.0f * e, r.E0);
+                            const float bound = fmaf(9.6e-7f, Sm, fmaf(1.2e-7f, e, lerr + 1e-9f));
+                            const bool c = !exact_only && d <= e - bound;
+                            const bool u = exact_only || (!c && !(d > e + bound));
+                            cm |= (uint32_t)(in && c) << k;
+                            exm |= (uint32_t)(in && u) << k;
+                            nwin += in ? 1u : 0u;
+                        }
+                        // FP32 inconclusive: the brute-force FP64 expression decides
+                        for (uint32_t m = exm; m; m &= m - 1u) {
+                            const int k = __ffs(m) - 1;
+                            nexact++;
+                            if (exact_pair(P, qi, __float_as_uint(recb[g + k].w))) cm |= 1u << k;
+                        }
+                        for (; cm; cm &= cm - 1u) {
+                            const int k = __ffs(cm) - 1;
+                            uint32_t vk = v[0], jk = __float_as_uint(rcs[0].w);
+                            float rk = rns[0];
+#pragma unroll
+                            for (int t = 1; t < kGroup; t++)
+                                if (k == t) {
+                                    vk = v[t];
+                                    jk = __float_as_uint(rcs[t].w);
+                                    rk = rns[t];
+                                }
+                            ncand++;
+                            const float dist = qn + rk - 2.0f * __uint_as_float(vk);
+                            top2(((unsigned long long)(uint32_t)dist << 32) | jk, b1, b2);
+                        }
+                    }
+                }
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&S.tfree[st]);
+            }
+        }
+        seq += (uint32_t)nchunk;
+        if (qv) store_match(L, q_off + qi, P, r.flags, b1, b2);
+        __syncthreads();
+    }
+    if (L.counters && warp < 4) {
+        const uint32_t a = __reduce_add_sync(0xffffffffu, (uint32_t)nwin);
+        const uint32_t b = __reduce_add_sync(0xffffffffu, (uint32_t)ncand);
+        const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)nexact);
+        if (lane == 0) {
+            atomicAdd(L.counters + 2, (unsigned long long)a);
+            atomicAdd(L.counters + 3, (unsigned long long)b);
+            atomicAdd(L.counters + 4, (unsigned long long)c);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 4) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+// Rows of 256 bytes, boxes of 128 bytes x `box_rows` rows, 128-byte swizzle.
+cudaError_t make_tmap(CUtensorMap *m, const void *base, int64_t rows, uint32_t box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {(cuuint64_t)kRowB, (cuuint64_t)(rows > 0 ? rows : 1)};
+    cuuint64_t strides[1] = {(cuuint64_t)kRowB};
+    cuuint32_t box[2] = {128u, box_rows};
+    cuuint32_t es[2] = {1u, 1u};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+bool band_supported(int kind, int dim) {
+    return (kind == EGM_DESC_U8_L2 && dim == 128) || (kind == EGM_DESC_BIN && dim == 256);
+}
+
+int band_row_bytes() { return kRowB; }
+int band_tile_queries() { return kTM; }
+
+cudaError_t launch_query_sort(const Launch &L, cudaStream_t s) {
+    if (L.nq == 0) return cudaSuccess;
+    query_sort_kernel<<<L.npairs, kQSortThreads, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const Launch &L, cudaStream_t s) {
+    const int64_t rows = L.nr + L.nq;
+    if (rows == 0) return cudaSuccess;
+    int64_t blocks = (rows * 8 + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    pack_kernel<<<(int)blocks, 256, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band(const Launch &L, int sms, cudaStream_t s) {
+    if (L.ntiles == 0) return cudaSuccess;
+    CUtensorMap tA, tB;
+    cudaError_t e = make_tmap(&tA, L.descA, L.nq, kTM);
+    if (e != cudaSuccess) return e;
+    if ((e = make_tmap(&tB, L.descB, L.nr, kBoxR)) != cudaSuccess) return e;
+    const int smem = (int)sizeof(BandSmem) + 1024;
+    int64_t grid = L.ntiles;
+    if (grid > 2 * (int64_t)sms) grid = 2 * (int64_t)sms;
+    e = cudaFuncSetAttribute(band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    band_kernel<<<(int)grid, kBandThreads, smem, s>>>(tA, tB, L);
+    return cudaGetLastError();
+}
+
+}  // namespace egm

@@ -127,6 +127,14 @@ struct Launch {
     int32_t ratio_num, ratio_den;
     int32_t max_n;                // largest reference count of the batch
     int32_t kind;                 // descriptor kind shared by every pair, or -1 when mixed
+    // banded form (tiles of 128 queries sorted by angle)
+    uint32_t *qperm;              // sorted query slot -> pair-local query index
+    uint16_t *qbkt;               // per query: its bucket of the angle order (written by the prep kernel)
+    uint8_t *descA, *descB;       // 256-byte operand rows of the sorted queries / references
+    QueryRec *qsrt;               // query records in sorted order, pad = (query index, norm bits)
+    float *rnorm;                 // sorted references' squared norms (u8) or popcounts (binary)
+    const int64_t *tile_offs;     // npairs + 1: first tile of each pair
+    int64_t ntiles;
 };
 
 // Pairs with at most this many references are sorted by one thread-block
@@ -196,8 +204,192 @@ __device__ __forceinline__ bool exact_member(double a, double b, double c, doubl
     return __ddiv_rn(num, N) <= eps;
 }
 
+// Bucket of a query in the angle order of the banded form: the top bits of
+// its quantised line angle; lines without an FP32 view, or whose windows are
+// whole levels, after every angle.
+constexpr int kQSortBits = 11;
+constexpr int kQBuckets = (1 << kQSortBits) + 2;
+
+__device__ __forceinline__ uint32_t query_bucket(const PairGeom &G, const QueryRec &r) {
+    if (r.flags & EGM_FLAG_DEGENERATE_LINE) return 1u << kQSortBits;
+    if ((r.flags & kQExactOnly) || (G.mode == kModeParallel && !(r.aux0 >= 0.5f))) return (1u << kQSortBits) + 1;
+    return qmap(r.key, G.kmin, G.kscale) >> (kQBits - kQSortBits);
+}
+
+// ---------------------------------------------------------------- windows
+//
+// The stabbing window of query r in level lv (Sec. 4.2): the keys of every
+// reference of the level whose tolerance circle can meet the query's line.
+// First in key space (KeyWin), then as bucket-table indices (WinKeys) so
+// that the table loads of many windows can be issued together, then as
+// sorted positions (Window).  A hull of several KeyWins (the windows of a
+// tile of queries) goes through the same two last steps.
+
+struct KeyWin {
+    int kind;        // 0 empty, 1 the whole level, 2 keys in [lo, hi] (angular: may cross the seam)
+    float lo, hi;
+};
+
+struct WinKeys {
+    uint32_t s, e;   // the level's sorted positions [s, e)
+    uint32_t ta, tb; // bucket-table indices
+    int kind;        // 0 empty, 1 whole level, 2 [T[ta], T[tb]), 3 seam: [T[ta], e) and [s, T[tb])
+};
+
+struct Window {
+    uint32_t b0, len0, b1, len1;  // up to two disjoint ranges of sorted positions (pair-relative)
+};
+
+__device__ __forceinline__ KeyWin key_window(const PairGeom &G, const QueryRec &r, int lv) {
+    KeyWin w;
+    w.kind = 0;
+    w.lo = w.hi = 0.0f;
+    if (lv >= kLevels || (r.flags & EGM_FLAG_DEGENERATE_LINE) || G.cnt[lv] == 0) return w;
+    const float smax = __uint_as_float(G.smax[lv]);
+    // R: largest |p - c| of the level; the FP32 keys of its members are the
+    // exact keys of points moved by at most `dpos` pixels.
+    const float R = __uint_as_float(G.tmax[lv]);
+    const float u = 5.9604645e-8f;
+    bool full = (r.flags & kQExactOnly) != 0;
+    if (full) {
+    } else if (G.mode == kModeAngular) {
+        const float dpos = 8.0f * u * R + 4.0f * u * fminf(G.de, R) + 2.0f * u * fabsf(G.kappa) + 1e-9f;
+        const float dmin = __uint_as_float(G.dmin[lv]);
+        const float sigma = (dmin > 0.0f) ? (smax + (r.aux0 + dpos) / dmin) * 1.000001f : INFINITY;
+        full = !(sigma < 1.0f);
+        if (!full) {
+            const float wv = asinf(sigma) * 1.000001f + 1e-37f;
+            const float hw = wv + (4e-6f * (fabsf(r.key) + wv) + 1e-14f);
+            full = !(hw < kHalfPiF);
+            w.lo = r.key - hw;
+            w.hi = r.key + hw;
+        }
+    } else {
+        full = !(r.aux0 >= 0.5f);
+        if (!full) {
+            const float wv = (smax + R * r.aux1 + 8.0f * u * R + 1e-9f) / r.aux0 * 1.000001f;
+            const float hw = wv + (1e-6f * (fabsf(r.key) + wv) + 1e-6f);
+            full = !isfinite(hw);
+            w.lo = r.key - hw;
+            w.hi = r.key + hw;
+        }
+    }
+    w.kind = full ? 1 : 2;
+    return w;
+}
+
+__device__ __forceinline__ WinKeys win_buckets(const PairGeom &G, int lv, const KeyWin &w) {
+    WinKeys k;
+    k.kind = 0;
+    k.s = k.e = k.ta = k.tb = 0;
+    if (w.kind == 0 || lv >= kLevels || G.cnt[lv] == 0) return k;
+    k.s = G.start[lv];
+    k.e = G.start[lv + 1];
+    const float lo = w.lo, hi = w.hi;
+    const bool low = G.mode == kModeAngular && lo < -kHalfPiF;
+    const bool high = G.mode == kModeAngular && hi >= kHalfPiF;
+    if (w.kind == 1 || (low && high)) {
+        k.kind = 1;
+        return k;
+    }
+    // Whole buckets around the window: a superset of the keypoints whose key
+    // lies in it (the exact test decides membership).
+    const int sh = kQBits - G.bits[lv];
+    if (low || high) {
+        // the window crosses the seam of the [-pi/2, pi/2) domain (Sec. 4.4,
+        // "Discontinuity at 0/pi"): the high part [qa, end) of the level and
+        // the low part [start, qb]
+        k.ta = qmap(low ? lo + kPiF : lo, G.kmin, G.kscale) >> sh;
+        k.tb = (qmap(low ? hi : hi - kPiF, G.kmin, G.kscale) >> sh) + 1;
+        k.kind = 3;
+    } else {
+        k.ta = qmap(lo, G.kmin, G.kscale) >> sh;
+        k.tb = (qmap(hi, G.kmin, G.kscale) >> sh) + 1;
+        k.kind = 2;
+    }
+    return k;
+}
+
+__device__ __forceinline__ WinKeys window_keys(const PairGeom &G, const QueryRec &r, int lv) {
+    return win_buckets(G, lv, key_window(G, r, lv));
+}
+
+__device__ __forceinline__ Window window_ranges(const WinKeys &k, uint32_t pa, uint32_t pb) {
+    Window w;
+    w.b0 = w.len0 = w.b1 = w.len1 = 0;
+    if (k.kind == 1) {
+        w.b0 = k.s;
+        w.len0 = k.e - k.s;
+    } else if (k.kind == 2) {
+        w.b0 = pa;
+        w.len0 = pb > pa ? pb - pa : 0;
+    } else if (k.kind == 3) {
+        if (pb > pa) pb = pa;  // a shared edge bucket is visited once
+        w.b0 = pa;
+        w.len0 = k.e - pa;
+        w.b1 = k.s;
+        w.len1 = pb > k.s ? pb - k.s : 0;
+    }
+    return w;
+}
+
+// The brute-force FP64 decision for one (query, reference) pair, kept out of
+// line: it runs only when the FP32 test is inconclusive.
+static __device__ __noinline__ bool exact_pair(const PairDesc &P, int64_t i, uint32_t j) {
+    double a, b, c;
+    exact_line(P.F, P.xy1[2 * i], P.xy1[2 * i + 1], a, b, c);
+    const double N = exact_norm(a, b);
+    const double eps = P.eps2 ? P.eps2[j] : P.eps_scalar;
+    return exact_member(a, b, c, N, P.xy2[2 * (int64_t)j], P.xy2[2 * (int64_t)j + 1], eps);
+}
+
+// Outputs of query gq from its best two (distance << 32 | index) keys:
+// indices, distances, flags and the ratio test (Sec. 5.1) in exact integer
+// form for integer distances.
+__device__ __forceinline__ void store_match(const Launch &L, int64_t gq, const PairDesc &P, uint32_t qflags,
+                                            unsigned long long b1, unsigned long long b2) {
+    uint8_t fl = (uint8_t)(qflags & EGM_FLAG_DEGENERATE_LINE);
+    int32_t jb = -1, js = -1;
+    float db = INFINITY, ds = INFINITY;
+    if (P.row_bytes > 0 && b1 != ~0ull) {
+        const bool isf = P.kind == EGM_DESC_F32_L2;
+        jb = (int32_t)(b1 & 0xffffffffu);
+        const uint32_t d1 = (uint32_t)(b1 >> 32);
+        db = isf ? __uint_as_float(d1) : (float)d1;
+        fl |= EGM_FLAG_HAS_BEST;
+        bool pass;
+        if (b2 == ~0ull) {
+            fl |= EGM_FLAG_NO_SECOND;
+            pass = true;
+        } else {
+            js = (int32_t)(b2 & 0xffffffffu);
+            const uint32_t d2 = (uint32_t)(b2 >> 32);
+            ds = isf ? __uint_as_float(d2) : (float)d2;
+            const long long nn = L.ratio_num, dn = L.ratio_den;
+            if (P.kind == EGM_DESC_U8_L2)
+                pass = (long long)d1 * dn * dn < (long long)d2 * nn * nn;
+            else if (P.kind == EGM_DESC_BIN)
+                pass = (long long)d1 * dn < (long long)d2 * nn;
+            else
+                pass = db * (float)(dn * dn) < ds * (float)(nn * nn);
+        }
+        if (pass) fl |= EGM_FLAG_RATIO_PASS;
+    }
+    if (L.best) L.best[gq] = jb;
+    if (L.second) L.second[gq] = js;
+    if (L.best_d) L.best_d[gq] = db;
+    if (L.second_d) L.second_d[gq] = ds;
+    if (L.flags) L.flags[gq] = fl;
+}
+
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_geometry(const Launch &L, cudaStream_t s);
+bool band_supported(int kind, int dim);
+int band_row_bytes();
+int band_tile_queries();
+cudaError_t launch_query_sort(const Launch &L, cudaStream_t s);
+cudaError_t launch_pack(const Launch &L, cudaStream_t s);
+cudaError_t launch_band(const Launch &L, int sms, cudaStream_t s);
 cudaError_t launch_prep(const Launch &L, cudaStream_t s);
 cudaError_t launch_sort(const Launch &L, int max_n, cudaStream_t s);
 cudaError_t launch_post_sort(const Launch &L, cudaStream_t s);

@@ -283,6 +283,7 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
                 if (!isfinite(r.C) || !isfinite(r.key)) r.flags = kQExactOnly;
             }
             L.qrec[gq] = r;
+            if (L.qbkt) L.qbkt[gq] = (uint16_t)query_bucket(G, r);
         }
         // warp-aggregated level statistics
         const uint32_t peers = __match_any_sync(0xffffffffu, group);

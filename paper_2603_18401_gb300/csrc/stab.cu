@@ -55,107 +55,6 @@ __global__ void __launch_bounds__(256) post_sort_kernel(Launch L) {
 
 // ------------------------------------------------------------ descriptors
 
-struct Window {
-    uint32_t b0, len0, b1, len1;  // up to two disjoint ranges of sorted positions (pair-relative)
-};
-
-// Window of level `lv` for query r, first without the bucket-table loads so
-// that a warp can issue the loads of several queries together.
-struct WinKeys {
-    uint32_t s, e;     // the level's sorted positions [s, e)
-    uint32_t ta, tb;   // bucket-table indices
-    int kind;          // 0 empty, 1 whole level, 2 [T[ta], T[tb]), 3 seam: [T[ta], e) and [s, T[tb])
-};
-
-__device__ __forceinline__ WinKeys window_keys(const PairGeom &G, const QueryRec &r, int lv) {
-    WinKeys k;
-    k.kind = 0;
-    k.s = k.e = k.ta = k.tb = 0;
-    if (lv >= kLevels || (r.flags & EGM_FLAG_DEGENERATE_LINE) || G.cnt[lv] == 0) return k;
-    k.s = G.start[lv];
-    k.e = G.start[lv + 1];
-    const float smax = __uint_as_float(G.smax[lv]);
-    // R: largest |p - c| of the level; the FP32 keys of its members are the
-    // exact keys of points moved by at most `dpos` pixels.
-    const float R = __uint_as_float(G.tmax[lv]);
-    const float u = 5.9604645e-8f;
-    bool full = (r.flags & kQExactOnly) != 0;
-    float lo = 0.0f, hi = 0.0f;
-    if (full) {
-    } else if (G.mode == kModeAngular) {
-        const float dpos = 8.0f * u * R + 4.0f * u * fminf(G.de, R) + 2.0f * u * fabsf(G.kappa) + 1e-9f;
-        const float dmin = __uint_as_float(G.dmin[lv]);
-        const float sigma = (dmin > 0.0f) ? (smax + (r.aux0 + dpos) / dmin) * 1.000001f : INFINITY;
-        full = !(sigma < 1.0f);
-        if (!full) {
-            const float wv = asinf(sigma) * 1.000001f + 1e-37f;
-            const float hw = wv + (4e-6f * (fabsf(r.key) + wv) + 1e-14f);
-            full = !(hw < kHalfPiF);
-            lo = r.key - hw;
-            hi = r.key + hw;
-        }
-    } else {
-        full = !(r.aux0 >= 0.5f);
-        if (!full) {
-            const float wv = (smax + R * r.aux1 + 8.0f * u * R + 1e-9f) / r.aux0 * 1.000001f;
-            const float hw = wv + (1e-6f * (fabsf(r.key) + wv) + 1e-6f);
-            full = !isfinite(hw);
-            lo = r.key - hw;
-            hi = r.key + hw;
-        }
-    }
-    if (full) {
-        k.kind = 1;
-        return k;
-    }
-    // Whole buckets around the window: a superset of the keypoints whose key
-    // lies in it (the exact test decides membership).
-    const int sh = kQBits - G.bits[lv];
-    if (G.mode == kModeAngular && (lo < -kHalfPiF || hi >= kHalfPiF)) {
-        // the window crosses the seam of the [-pi/2, pi/2) domain (Sec. 4.4,
-        // "Discontinuity at 0/pi"): the high part [qa, end) of the level and
-        // the low part [start, qb]
-        const bool low = lo < -kHalfPiF;
-        k.ta = qmap(low ? lo + kPiF : lo, G.kmin, G.kscale) >> sh;
-        k.tb = (qmap(low ? hi : hi - kPiF, G.kmin, G.kscale) >> sh) + 1;
-        k.kind = 3;
-    } else {
-        k.ta = qmap(lo, G.kmin, G.kscale) >> sh;
-        k.tb = (qmap(hi, G.kmin, G.kscale) >> sh) + 1;
-        k.kind = 2;
-    }
-    return k;
-}
-
-__device__ __forceinline__ Window window_ranges(const WinKeys &k, uint32_t pa, uint32_t pb) {
-    Window w;
-    w.b0 = w.len0 = w.b1 = w.len1 = 0;
-    if (k.kind == 1) {
-        w.b0 = k.s;
-        w.len0 = k.e - k.s;
-    } else if (k.kind == 2) {
-        w.b0 = pa;
-        w.len0 = pb > pa ? pb - pa : 0;
-    } else if (k.kind == 3) {
-        if (pb > pa) pb = pa;  // a shared edge bucket is visited once
-        w.b0 = pa;
-        w.len0 = k.e - pa;
-        w.b1 = k.s;
-        w.len1 = pb > k.s ? pb - k.s : 0;
-    }
-    return w;
-}
-
-// The brute-force FP64 decision for one (query, reference) pair, kept out of
-// line: it runs only when the FP32 test is inconclusive.
-__device__ __noinline__ bool exact_pair(const PairDesc &P, int64_t i, uint32_t j) {
-    double a, b, c;
-    exact_line(P.F, P.xy1[2 * i], P.xy1[2 * i + 1], a, b, c);
-    const double N = exact_norm(a, b);
-    const double eps = P.eps2 ? P.eps2[j] : P.eps_scalar;
-    return exact_member(a, b, c, N, P.xy2[2 * (int64_t)j], P.xy2[2 * (int64_t)j + 1], eps);
-}
-
 // ------------------------------------------------------------ stabbing
 //
 // One block takes kQB consecutive queries.  On GB300 a dependent global
@@ -679,39 +578,7 @@ __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mod
             } else {
                 const int p = S.qr[tid].pair;
                 const PairDesc &P = p == S.gpair ? S.pd : L.pairs[p];
-                const unsigned long long b1 = S.b1[tid], b2 = S.b2[tid];
-                uint8_t fl = (uint8_t)(S.qr[tid].flags & EGM_FLAG_DEGENERATE_LINE);
-                int32_t jb = -1, js = -1;
-                float db = INFINITY, ds = INFINITY;
-                if (P.row_bytes > 0 && b1 != ~0ull) {
-                    const bool isf = P.kind == EGM_DESC_F32_L2;
-                    jb = (int32_t)(b1 & 0xffffffffu);
-                    const uint32_t d1 = (uint32_t)(b1 >> 32);
-                    db = isf ? __uint_as_float(d1) : (float)d1;
-                    fl |= EGM_FLAG_HAS_BEST;
-                    bool pass;
-                    if (b2 == ~0ull) {
-                        fl |= EGM_FLAG_NO_SECOND;
-                        pass = true;
-                    } else {
-                        js = (int32_t)(b2 & 0xffffffffu);
-                        const uint32_t d2 = (uint32_t)(b2 >> 32);
-                        ds = isf ? __uint_as_float(d2) : (float)d2;
-                        const long long nn = L.ratio_num, dn = L.ratio_den;
-                        if (P.kind == EGM_DESC_U8_L2)
-                            pass = (long long)d1 * dn * dn < (long long)d2 * nn * nn;
-                        else if (P.kind == EGM_DESC_BIN)
-                            pass = (long long)d1 * dn < (long long)d2 * nn;
-                        else
-                            pass = db * (float)(dn * dn) < ds * (float)(nn * nn);
-                    }
-                    if (pass) fl |= EGM_FLAG_RATIO_PASS;
-                }
-                if (L.best) L.best[gq] = jb;
-                if (L.second) L.second[gq] = js;
-                if (L.best_d) L.best_d[gq] = db;
-                if (L.second_d) L.second_d[gq] = ds;
-                if (L.flags) L.flags[gq] = fl;
+                store_match(L, gq, P, S.qr[tid].flags, S.b1[tid], S.b2[tid]);
             }
             if (L.counters) atomicAdd(L.counters + 3, (unsigned long long)S.cnt[tid]);
         }

@@ -1,0 +1,235 @@
+"""The banded tensor-core form (EGM_FORM_BANDED) against the oracle and the
+plain form.
+
+Both forms decide membership with the same exact test and break ties by the
+lower index, so their outputs must be identical element by element (integer
+distances); each is also checked against the oracle's matches.  Cases cover
+ragged tiles (m not a multiple of 128), bands shorter than one 32-row box,
+whole-level windows, every epipole regime, mixed u8 / binary batches and the
+graph path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from test_gpu_parity import _scene, check_matches
+
+pytestmark = pytest.mark.gpu
+
+FORM_AUTO, FORM_PLAIN, FORM_BANDED = 0, 1, 2
+KEYS = ("best", "second", "flags", "best_d", "second_d")
+
+
+@pytest.fixture(scope="module")
+def mt():
+    import torch
+
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_2603_18401_gb300 import Matcher
+
+    m = Matcher(0)
+    yield m
+    torch.cuda.synchronize()
+    m.close()
+
+
+def run_form(mt, sc, form):
+    mt.set_params(form=form)
+    try:
+        d = mt.to_device(sc)
+        o = mt.match(d["xy1"], d["xy2"], d["F"], d["eps"], d["desc1"], d["desc2"], d["kind"], d["dim"],
+                     d["width"], d["height"], csr=False)
+        return {k: v.cpu().numpy() for k, v in o.items()}
+    finally:
+        mt.set_params(form=FORM_AUTO)
+
+
+def both(mt, sc, oracle_check=True):
+    b = run_form(mt, sc, FORM_BANDED)
+    p = run_form(mt, sc, FORM_PLAIN)
+    for k in KEYS:
+        assert np.array_equal(b[k], p[k]), k
+    if oracle_check:
+        check_matches(b, sc)
+    return b
+
+
+def test_config1(mt):
+    both(mt, synth.config1())
+
+
+@pytest.mark.parametrize("pose", list(synth.CONFIG2_POSES))
+@pytest.mark.parametrize("eps", [1.0, 2.0, 4.0])
+def test_config2_full_size(mt, pose, eps):
+    both(mt, synth.config2(pose, eps))
+
+
+def test_config3_mixed_batch(mt):
+    """u8 and binary pairs in one batch (one tile never spans two pairs)."""
+    scenes = synth.config3(seed=2, npairs=10, scale=0.1)
+    items = [mt.to_device(s) for s in scenes]
+    res = {}
+    for form in (FORM_BANDED, FORM_PLAIN):
+        mt.set_params(form=form)
+        res[form] = {k: v.cpu().numpy() for k, v in mt.match_batch(items).items()}
+    mt.set_params(form=FORM_AUTO)
+    for k in KEYS:
+        assert np.array_equal(res[FORM_BANDED][k], res[FORM_PLAIN][k]), k
+    q0 = 0
+    for s in scenes:
+        sl = slice(q0, q0 + s.m)
+        check_matches({k: res[FORM_BANDED][k][sl] for k in KEYS}, s)
+        q0 += s.m
+
+
+def test_full_size_batch_sampled(mt):
+    """The bench's batch shape (256 pairs, counts log-uniform in [1k, 32k], half
+    binary) at full size: banded equals plain everywhere, and sampled queries
+    equal the oracle."""
+    scenes = synth.config3(seed=0, npairs=256, scale=1.0)
+    items = [mt.to_device(s) for s in scenes]
+    res = {}
+    for form in (FORM_BANDED, FORM_PLAIN):
+        mt.set_params(form=form)
+        res[form] = {k: v.cpu().numpy() for k, v in mt.match_batch(items).items()}
+    mt.set_params(form=FORM_AUTO)
+    for k in KEYS:
+        assert np.array_equal(res[FORM_BANDED][k], res[FORM_PLAIN][k]), k
+    rng = np.random.default_rng(1)
+    q0 = 0
+    for p, s in enumerate(scenes):
+        if p % 16 == 0:
+            rows = np.sort(rng.choice(s.m, size=min(200, s.m), replace=False))
+            ref = oracle.match(s.xy1[rows], s.xy2, s.F, s.eps, s.desc1[rows], s.desc2, s.kind, s.dim)
+            for k in ("best", "second", "flags"):
+                assert np.array_equal(res[FORM_BANDED][k][q0 + rows], ref[k]), (p, k)
+        q0 += s.m
+
+
+def _F():
+    K = synth.intrinsics(500.0, 640, 480)
+    return synth.fundamental(K, K, synth.rotation([0, 1, 0], 8), [0.3, 0.02, 0.04])
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (1, 500), (127, 31), (128, 32), (129, 33), (300, 5), (5, 3000),
+                                 (1000, 0), (257, 1)])
+def test_ragged_tiles_and_boxes(mt, m, n):
+    rng = np.random.default_rng(m * 7 + n)
+    for kind, dim in ((0, 128), (2, 256)):
+        sc = _scene(rng.uniform([0, 0], [640, 480], (m, 2)), rng.uniform([0, 0], [640, 480], (n, 2)), _F(),
+                    6.0, kind=kind, dim=dim, seed=m + n)
+        both(mt, sc)
+
+
+def test_whole_level_windows_and_near_epipole(mt):
+    """eps covering the image (every window is a whole level) and keypoints at
+    and around an epipole inside the image."""
+    rng = np.random.default_rng(11)
+    sc = _scene(rng.uniform(0, 480, (300, 2)), rng.uniform(0, 480, (700, 2)), _F(), 5000.0, dim=128)
+    b = both(mt, sc)
+    assert np.all(b["flags"] & 1)
+    K = synth.intrinsics(500.0, 640, 480)
+    F = synth.fundamental(K, K, np.eye(3), np.array([0.0, 0.0, 1.0]))
+    xy2 = np.vstack([[[320.0, 240.0], [320.5, 240.0], [321.9, 240.0]], rng.uniform(0, 640, (3000, 2))])
+    both(mt, _scene(rng.uniform(0, 640, (900, 2)), xy2, F, 2.0, dim=128))
+
+
+@pytest.mark.parametrize("t", [(0.0, 0.0, 1.0), (1.0, 0.0, 0.0), (0.3, 1.0, 0.0), (1.0, 0.3, 1e-12),
+                               (-0.4, 0.7, 0.2), (0.5, 0.5, -0.5)])
+def test_epipole_regimes(mt, t):
+    K = synth.intrinsics(800.0, 1000, 800)
+    F = synth.fundamental(K, K, synth.rotation([0.2, 1, 0.1], 4.0), np.array(t))
+    rng = np.random.default_rng(5)
+    xy1 = rng.uniform([-50, -50], [1050, 850], (3000, 2))
+    xy2 = rng.uniform([-50, -50], [1050, 850], (3000, 2))
+    for eps in (0.5, 3.0, 40.0):
+        for kind, dim in ((0, 128), (2, 256)):
+            both(mt, _scene(xy1, xy2, F, eps, w=1000, h=800, kind=kind, dim=dim))
+
+
+def test_rank3_boundary_and_per_keypoint_eps(mt):
+    rng = np.random.default_rng(3)
+    K = synth.intrinsics(600.0, 640, 480)
+    F = synth.fundamental(K, K, synth.rotation([1, 2, 3], 7), [0.4, 0.1, 0.3])
+    F = F + 1e-4 * np.abs(F).max() * rng.normal(size=(3, 3))
+    both(mt, _scene(rng.uniform([0, 0], [640, 480], (2500, 2)), rng.uniform([0, 0], [640, 480], (2500, 2)), F,
+                    rng.uniform(0.25, 12.0, 2500), dim=128))
+    # integer geometry: pairs exactly at eps and within 1e-9 px of it
+    F = synth.skew([1.0, 0.0, 0.0])
+    y2 = rng.integers(0, 400, 3000).astype(float)
+    y2[:300] += rng.choice([-1e-10, 1e-10, 3e-10, 0.0], 300)
+    xy1 = np.c_[rng.uniform(0, 600, 600), rng.integers(0, 400, 600).astype(float)]
+    both(mt, _scene(xy1, np.c_[rng.uniform(0, 600, 3000), y2], F, 2.0, w=600, h=400, kind=2, dim=256))
+
+
+def test_degenerate_lines(mt):
+    """Queries whose line is exactly null (F = [z]x: l = (-y, x, 0), null at the
+    origin): no candidates, flagged; the other lines pass through e2 = (0, 0)."""
+    F = synth.skew([0.0, 0.0, 1.0])
+    rng = np.random.default_rng(12)
+    xy1 = np.vstack([[[0.0, 0.0]] * 5, rng.uniform(0, 640, (400, 2))])
+    b = both(mt, _scene(xy1, rng.uniform(0, 640, (800, 2)), F, 3.0, dim=128))
+    assert np.all(b["flags"][:5] == 8)
+
+
+def test_graph_replay_banded(mt):
+    import torch
+
+    scenes = synth.config3(seed=4, npairs=6, scale=0.1)
+    items = [mt.to_device(s) for s in scenes]
+    M = sum(s.m for s in scenes)
+    mt.set_params(form=FORM_BANDED)
+    try:
+        out = mt._alloc_out(M, False, 0)
+        g = mt.graph_create(items, out)
+        for _ in range(2):
+            assert g.launch() == 0
+        ref = mt.match_batch(items)
+        for k in KEYS:
+            assert torch.equal(out[k], ref[k]), k
+        g.close()
+    finally:
+        mt.set_params(form=FORM_AUTO)
+    mt.set_params(form=FORM_PLAIN)
+    try:
+        plain = mt.match_batch(items)
+    finally:
+        mt.set_params(form=FORM_AUTO)
+    for k in KEYS:
+        assert torch.equal(out[k], plain[k]), k
+
+
+def test_counters_and_unsupported_inputs(mt):
+    from paper_2603_18401_gb300 import EgmError
+
+    sc = synth.config2("inside", 2.0, scale=0.25)
+    d = mt.to_device(sc)
+    args = (d["xy1"], d["xy2"], d["F"], 2.0, d["desc1"], d["desc2"], 0, 128, sc.width, sc.height)
+    mt.set_counters(True)
+    cands = {}
+    for form in (FORM_BANDED, FORM_PLAIN):
+        mt.set_params(form=form)
+        mt.match(*args)
+        cands[form] = mt.stats()["candidates"]
+    assert cands[FORM_BANDED] == cands[FORM_PLAIN] > 0
+    mt.set_counters(False)
+    mt.set_params(form=FORM_BANDED)
+    try:
+        with pytest.raises(EgmError) as e:    # candidate lists come from the plain form only
+            mt.match(*args, csr=True)
+        assert e.value.status == -8
+        rng = np.random.default_rng(0)
+        for kind, dim in ((0, 64), (1, 128), (2, 128)):
+            s2 = _scene(rng.uniform(0, 480, (50, 2)), rng.uniform(0, 480, (60, 2)), _F(), 3.0, kind=kind, dim=dim)
+            d2 = mt.to_device(s2)
+            with pytest.raises(EgmError) as e:
+                mt.match(d2["xy1"], d2["xy2"], d2["F"], 3.0, d2["desc1"], d2["desc2"], kind, dim, 640, 480)
+            assert e.value.status == -8
+    finally:
+        mt.set_params(form=FORM_AUTO)
+    # the automatic choice falls back to the plain form for the same inputs
+    o = mt.match(*args, csr=True)
+    assert int(o["cand_total"].item()) == cands[FORM_PLAIN]
