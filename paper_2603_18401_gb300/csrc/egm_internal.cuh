@@ -258,8 +258,12 @@ __device__ __forceinline__ KeyWin key_window(const PairGeom &G, const QueryRec &
         const float sigma = (dmin > 0.0f) ? (smax + (r.aux0 + dpos) / dmin) * 1.000001f : INFINITY;
         full = !(sigma < 1.0f);
         if (!full) {
+            // pads: relative (asinf, atan2f, the 1.000001 factors) and absolute
+            // (the FP32 line direction: roundings of a, b, of the normalisation
+            // and of the turn into the frame of u, about 7 ulp of 1 in all,
+            // 4.3e-7 rad; taken as 2e-6)
             const float wv = asinf(sigma) * 1.000001f + 1e-37f;
-            const float hw = wv + (4e-6f * (fabsf(r.key) + wv) + 1e-14f);
+            const float hw = wv + (4e-6f * (fabsf(r.key) + wv) + 2e-6f);
             full = !(hw < kHalfPiF);
             w.lo = r.key - hw;
             w.hi = r.key + hw;

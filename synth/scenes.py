@@ -258,16 +258,22 @@ def _random_pose(rng, max_deg):
 
 
 def config3(seed: int = 0, npairs: int = 256, scale: float = 1.0,
-            lo: int = 1024, hi: int = 32768) -> list[Scene]:
-    """Batched: per-image counts log-uniform in [lo, hi]; u8 L2 on even pairs, 256-bit binary on odd."""
+            lo: int = 1024, hi: int = 32768, only=None) -> list[Scene]:
+    """Batched: per-image counts log-uniform in [lo, hi]; u8 L2 on even pairs, 256-bit binary on odd.
+
+    `only`: indices of the pairs to build (the others are drawn and skipped, so
+    pair p is the same scene whether or not its neighbours are built)."""
     rng = np.random.default_rng(seed)
     K = intrinsics(HIGHRES_F, HIGHRES_W, HIGHRES_H)
     out = []
+    keep = None if only is None else set(int(x) for x in only)
     for p in range(npairs):
         m = int(math.floor(math.exp(rng.uniform(math.log(lo), math.log(hi)))) * scale)
         n = int(math.floor(math.exp(rng.uniform(math.log(lo), math.log(hi)))) * scale)
         m, n = max(m, 2), max(n, 2)
         R, t = _random_pose(rng, 30.0)
+        if keep is not None and p not in keep:
+            continue
         kind = DESC_U8_L2 if p % 2 == 0 else DESC_BIN256
         dim = 128 if kind == DESC_U8_L2 else 256
         sub = np.random.default_rng([seed, p])

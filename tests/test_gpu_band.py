@@ -85,28 +85,30 @@ def test_config3_mixed_batch(mt):
         q0 += s.m
 
 
-def test_full_size_batch_sampled(mt):
-    """The bench's batch shape (256 pairs, counts log-uniform in [1k, 32k], half
-    binary) at full size: banded equals plain everywhere, and sampled queries
-    equal the oracle."""
+def test_full_size_batch_exact(mt):
+    """The bench's batch (256 pairs of 6048x4032, counts log-uniform in [1k,
+    32k], half binary) at full size, every query: banded matches equal plain
+    matches and the oracle's; the plain form's candidate lists equal the
+    brute force's, row by row."""
     scenes = synth.config3(seed=0, npairs=256, scale=1.0)
     items = [mt.to_device(s) for s in scenes]
     res = {}
     for form in (FORM_BANDED, FORM_PLAIN):
         mt.set_params(form=form)
-        res[form] = {k: v.cpu().numpy() for k, v in mt.match_batch(items).items()}
+        res[form] = {k: v.cpu().numpy() for k, v in mt.match_batch(items, csr=form == FORM_PLAIN).items()}
     mt.set_params(form=FORM_AUTO)
     for k in KEYS:
         assert np.array_equal(res[FORM_BANDED][k], res[FORM_PLAIN][k]), k
-    rng = np.random.default_rng(1)
-    q0 = 0
+    q0 = c0 = 0
+    pl = res[FORM_PLAIN]
     for p, s in enumerate(scenes):
-        if p % 16 == 0:
-            rows = np.sort(rng.choice(s.m, size=min(200, s.m), replace=False))
-            ref = oracle.match(s.xy1[rows], s.xy2, s.F, s.eps, s.desc1[rows], s.desc2, s.kind, s.dim)
-            for k in ("best", "second", "flags"):
-                assert np.array_equal(res[FORM_BANDED][k][q0 + rows], ref[k]), (p, k)
+        c = oracle.candidates(s.xy1, s.xy2, s.F, s.eps)
+        off = pl["cand_offsets"][q0:q0 + s.m + 1] - pl["cand_offsets"][q0]
+        assert np.array_equal(off, c["offsets"]), p
+        assert np.array_equal(pl["cand_idx"][c0:c0 + int(off[-1])], c["idx"]), p
+        check_matches({k: res[FORM_BANDED][k][q0:q0 + s.m] for k in KEYS}, s)
         q0 += s.m
+        c0 += int(off[-1])
 
 
 def _F():

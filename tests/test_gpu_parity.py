@@ -421,3 +421,41 @@ def test_graph_replay_equals_batch(mt):
         assert torch.equal(out[k], ref2[k]), k
     assert not torch.equal(ref["best"], ref2["best"])
     g.close()
+
+
+def test_far_epipole_window_edge_regression(mt):
+    """Angular mode with the epipole ~4e5 px away: every line angle is near 0 in
+    the turned frame, so the window must cover the absolute FP32 error of the
+    query's key, not only a relative one (a reference 0.0013 px inside eps
+    was once missed here)."""
+    sc = synth.config3(seed=0, npairs=167, only=[166])[0]
+    _full_check(mt, sc)
+
+
+@pytest.mark.parametrize("t", [(-0.8, 0.6, -0.01), (0.5, 0.85, 0.002), (1.0, 0.1, 0.05)])
+def test_references_just_inside_tolerance(mt, t):
+    """References placed 1e-4 .. 2e-2 px inside eps of query lines, with the
+    epipole far outside the image (angles near 0 in the turned frame): all are
+    candidates of the brute force and must be found."""
+    K = synth.intrinsics(4800.0, 6048, 4032)
+    F = synth.fundamental(K, K, synth.rotation([0.3, 1, 0.2], 3.0), np.array(t))
+    rng = np.random.default_rng(21)
+    xy1 = rng.uniform([0, 0], [6048, 4032], (1500, 2))
+    eps = 2.0
+    refs = []
+    for x, y in xy1:
+        a, b, c = F @ np.array([x, y, 1.0])
+        nrm = np.hypot(a, b)
+        for _ in range(3):
+            if abs(b) >= abs(a):
+                px = rng.uniform(0, 6048)
+                p = np.array([px, -(a * px + c) / b])
+            else:
+                py = rng.uniform(0, 4032)
+                p = np.array([-(b * py + c) / a, py])
+            off = rng.choice([-1.0, 1.0]) * (eps - rng.uniform(1e-4, 2e-2))
+            refs.append(p + off * np.array([a, b]) / nrm)
+    xy2 = np.vstack([np.array(refs), rng.uniform([0, 0], [6048, 4032], (2000, 2))])
+    sc = _scene(xy1, xy2, F, eps, w=6048, h=4032, dim=128)
+    out = _full_check(mt, sc)
+    assert np.all(np.diff(out["cand_offsets"]) >= 3)
