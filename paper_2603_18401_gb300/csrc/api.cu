@@ -143,7 +143,8 @@ egm_status check_pair(const egm_pair *P) {
 
 struct Plan {
     std::vector<PairDesc> pd;
-    std::vector<int64_t> offs;      // query, reference and tile offsets: 3 x (npairs + 1)
+    std::vector<int64_t> offs;      // query, reference and tile offsets: 3 x (npairs + 1), then the
+                                    // tile order (int32, packed two per entry)
     std::vector<int64_t> qoffs, roffs;
     int64_t nq = 0, nr = 0, ntab = 0, ntiles = 0;
     int max_n = 0;
@@ -199,7 +200,25 @@ egm_status make_plan(const egm_pair *pairs, int npairs, Plan &pl) {
             pl.band_ok = pl.band_ok && has_desc(pairs + p) && band_supported(pairs[p].kind, pairs[p].dim);
         }
     }
+    // Tiles are handed out costliest first (longest-processing-time order): a
+    // tile's band holds about tm * n / m references plus its windows.
+    std::vector<int> order(npairs);
+    for (int p = 0; p < npairs; p++) order[p] = p;
+    auto cost = [&](int p) { return (double)tm * pairs[p].n / std::max(pairs[p].m, 1) + 64.0; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    const size_t base = pl.offs.size();
+    pl.offs.resize(base + (size_t)(pl.ntiles + 1) / 2, 0);
+    int32_t *seq = reinterpret_cast<int32_t *>(pl.offs.data() + base);
+    int64_t k = 0;
+    for (int p : order)
+        for (int64_t t = pl.offs[2 * (npairs + 1) + p]; t < pl.offs[2 * (npairs + 1) + p + 1]; t++)
+            seq[k++] = (int32_t)t;
     return EGM_OK;
+}
+
+// int64 entries of the offsets upload for a batch of npairs pairs and nq queries.
+size_t offs_entries(int npairs, int64_t nq) {
+    return 3 * (size_t)(npairs + 1) + (size_t)(nq / band_tile_queries() + npairs + 2) / 2 + 1;
 }
 
 // The banded form runs when it is requested or left to the library, every
@@ -234,7 +253,7 @@ cudaError_t reserve(Scratch &c_, int64_t nq, int64_t nr, int64_t ntab, int npair
     if (band && (e = grow(c->band, BandLayout(nq, nr).total)) != cudaSuccess) return e;
     if ((e = grow(c->pairs, sizeof(PairDesc) * (size_t)std::max(npairs, 1))) != cudaSuccess) return e;
     if ((e = grow(c->geom, sizeof(PairGeom) * (size_t)std::max(npairs, 1))) != cudaSuccess) return e;
-    if ((e = grow(c->offs, sizeof(int64_t) * 3 * (size_t)(npairs + 1))) != cudaSuccess) return e;
+    if ((e = grow(c->offs, sizeof(int64_t) * offs_entries(npairs, nq))) != cudaSuccess) return e;
     if ((e = grow(c->keys, sizeof(uint32_t) * 6 * (size_t)std::max<int64_t>(nr, 1))) != cudaSuccess) return e;
     // 32 records of padding: bulk copies of a 32-row box may run past the last row
     if ((e = grow(c->rec, sizeof(float4) * (size_t)(nr + 32))) != cudaSuccess) return e;
@@ -290,6 +309,8 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
         L.qsrt = reinterpret_cast<QueryRec *>(b + bl.qsrt);
         L.rnorm = reinterpret_cast<float *>(b + bl.rnorm);
         L.tile_offs = as<int64_t>(c->offs) + 2 * (npairs + 1);
+        L.tile_seq = reinterpret_cast<const int32_t *>(as<int64_t>(c->offs) + 3 * (npairs + 1));
+        L.work = as<uint32_t>(c->small) + 32;
         L.ntiles = pl.ntiles;
     }
     L.kind = pl.pd.empty() ? -1 : pl.pd[0].kind;
@@ -312,7 +333,7 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
 // Upload the pair table and offsets through pinned memory.  The staging area
 // is reused only after the previous upload has been consumed.
 cudaError_t upload_plan(egm_ctx *c, const Plan &pl, int npairs) {
-    const size_t tb = sizeof(PairDesc) * npairs, ob = sizeof(int64_t) * 3 * (npairs + 1);
+    const size_t tb = sizeof(PairDesc) * npairs, ob = sizeof(int64_t) * pl.offs.size();
     if (c->table_ev_pending) {
         cudaError_t e = cudaEventSynchronize(c->table_ev);
         if (e != cudaSuccess) return e;

@@ -200,7 +200,8 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
 // ------------------------------------------------------------ band kernel
 constexpr int kTM = 128;                 // queries per tile (MMA M, TMEM lanes)
 constexpr int kBoxR = 32;                // reference rows per TMA box (N per box)
-constexpr int kCB = 4;                   // boxes per MMA chunk
+constexpr int kCB = 2;                   // boxes per MMA chunk
+constexpr int kCtasPerSm = 3;            // resident CTAs per SM (shared memory and TMEM sized for it)
 constexpr int kCN = kBoxR * kCB;         // columns per chunk
 constexpr int kBandThreads = kTM + 32;   // four epilogue warps and the control warp
 constexpr uint32_t kTmemCols = 2 * kCN;  // double-buffered accumulator
@@ -229,16 +230,20 @@ struct BandSmem {
     int32_t wkind[4][kLevels];
     int32_t lv[kLevels];
     int32_t nlev, npc, nbox, gpair;
+    int32_t tile;                 // the tile being processed, then the next one
     uint32_t tmem;
     volatile uint32_t err;
 };
 
 static_assert(offsetof(BandSmem, B) % 1024 == 0, "operand tiles need 1024-byte alignment");
 static_assert(offsetof(BandSmem, rn) % 16 == 0, "bulk copy destinations need 16-byte alignment");
-// Two CTAs per SM hold the 2 x 256 TMEM columns; shared memory keeps a third
-// from becoming resident (its allocation would wait for one of them to end).
+// kCtasPerSm CTAs per SM share the 512 TMEM columns; shared memory keeps
+// one more from becoming resident (its allocation would wait for another CTA
+// to end).
 constexpr size_t kSmPerSm = 228 * 1024, kSmPerCta = sizeof(BandSmem) + 1024 + 1024;
-static_assert(2 * kSmPerCta <= kSmPerSm && 3 * kSmPerCta > kSmPerSm, "exactly two CTAs per SM");
+static_assert(kCtasPerSm * kSmPerCta <= kSmPerSm && (kCtasPerSm + 1) * kSmPerCta > kSmPerSm,
+              "shared memory admits exactly kCtasPerSm CTAs per SM");
+static_assert(kCtasPerSm * kTmemCols <= 512, "TMEM columns of the resident CTAs");
 
 __device__ __forceinline__ int sortable(float f) {
     const int b = __float_as_int(f);
@@ -277,7 +282,7 @@ __device__ __forceinline__ void top2(unsigned long long key, unsigned long long 
     }
 }
 
-__global__ void __launch_bounds__(kBandThreads, 2)
+__global__ void __launch_bounds__(kBandThreads, kCtasPerSm)
     band_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Launch L) {
     extern __shared__ uint8_t smraw[];
     // 1024-byte alignment by pointer arithmetic on the shared array, so that
@@ -298,6 +303,8 @@ __global__ void __launch_bounds__(kBandThreads, 2)
         tc::fence_mbar_init();
         S.err = 0;
         S.gpair = -1;
+        const uint32_t k = atomicAdd(L.work, 1u);
+        S.tile = k < (uint64_t)L.ntiles ? L.tile_seq[k] : -1;
         tc::prefetch_tmap(&tmA);
         tc::prefetch_tmap(&tmB);
     }
@@ -320,8 +327,12 @@ __global__ void __launch_bounds__(kBandThreads, 2)
     uint32_t seq = 0, aload = 0;
     unsigned long long nwin = 0, ncand = 0, nexact = 0;
 
-    for (int64_t tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
-        if (S.err) break;
+    for (;;) {
+        const int64_t tile = S.tile;
+        if (tile < 0 || S.err) break;
+        // the next tile, fetched while this one is processed
+        uint32_t knext = 0;
+        if (ctl) knext = atomicAdd(L.work, 1u);
         const int p = pair_of(L.tile_offs, L.npairs, tile);
         const int64_t q_off = L.q_offs[p];
         const int64_t t0 = (tile - L.tile_offs[p]) * kTM;  // first sorted slot of the tile
@@ -617,6 +628,7 @@ __global__ void __launch_bounds__(kBandThreads, 2)
         }
         seq += (uint32_t)nchunk;
         if (qv) store_match(L, q_off + qi, P, r.flags, b1, b2);
+        if (ctl) S.tile = knext < (uint64_t)L.ntiles ? L.tile_seq[knext] : -1;
         __syncthreads();
     }
     if (L.counters && warp < 4) {
@@ -693,7 +705,8 @@ cudaError_t launch_band(const Launch &L, int sms, cudaStream_t s) {
     if ((e = make_tmap(&tB, L.descB, L.nr, kBoxR)) != cudaSuccess) return e;
     const int smem = (int)sizeof(BandSmem) + 1024;
     int64_t grid = L.ntiles;
-    if (grid > 2 * (int64_t)sms) grid = 2 * (int64_t)sms;
+    if (grid > kCtasPerSm * (int64_t)sms) grid = kCtasPerSm * (int64_t)sms;
+    if ((e = cudaMemsetAsync(L.work, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
     e = cudaFuncSetAttribute(band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     band_kernel<<<(int)grid, kBandThreads, smem, s>>>(tA, tB, L);

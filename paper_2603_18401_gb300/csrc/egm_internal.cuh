@@ -134,6 +134,8 @@ struct Launch {
     QueryRec *qsrt;               // query records in sorted order, pad = (query index, norm bits)
     float *rnorm;                 // sorted references' squared norms (u8) or popcounts (binary)
     const int64_t *tile_offs;     // npairs + 1: first tile of each pair
+    const int32_t *tile_seq;      // ntiles: tiles in the order they are handed out (costliest pairs first)
+    uint32_t *work;               // tile dispenser (zeroed before the band kernel)
     int64_t ntiles;
 };
 
