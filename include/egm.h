@@ -151,7 +151,10 @@ typedef struct egm_params {
     int32_t ratio_den;
     int32_t sync;          /* 1 (default): calls wait and return the device status */
     int32_t form;          /* EGM_FORM_* */
-    int32_t reserved[12];  /* zero */
+    int32_t band_tile;     /* banded form tile shape: 0 (default) chosen by the library's tuner,
+                              which times every shape on the first call of each batch size class
+                              (that call waits for the device); k > 0: shape k - 1 */
+    int32_t reserved[11];  /* zero */
 } egm_params;
 
 /* Context lifetime.  `stream` is a cudaStream_t (NULL: the legacy default stream). */
@@ -203,7 +206,7 @@ egm_status egm_match_pair_host(egm_ctx *ctx, const egm_pair *pair, const egm_out
  *
  * It takes no egm_ctx and calls no cudaMalloc, cudaFree, cudaMallocHost or
  * other allocating routine.  All scratch lives in one fixed file-scope device
- * array of about 1.9 MB that every GPU loading libegm.so keeps until the
+ * array of about 2.2 MB that every GPU loading libegm.so keeps until the
  * process exits; it holds pairs of at most 16384 keypoints per image (m and
  * n); larger pairs are rejected with EGM_ERR_CAPACITY before any work.
  *   pair, out  as for egm_match_pair (device pointers)

@@ -60,7 +60,8 @@ class Matcher:
             pass
 
     # ------------------------------------------------------------- params
-    def set_params(self, ratio=None, sync=None, form=None):
+    def set_params(self, ratio=None, sync=None, form=None, band_tile=None):
+        """ratio (num, den); sync; form (EGM_FORM_*); band_tile (0: tuned, k > 0: shape k - 1)."""
         p = _egm.egm_params()
         check(self.lib.egm_get_params(self.ctx, C.byref(p)), "egm_get_params")
         if ratio is not None:
@@ -69,6 +70,8 @@ class Matcher:
             p.sync = int(bool(sync))
         if form is not None:
             p.form = int(form)
+        if band_tile is not None:
+            p.band_tile = int(band_tile)
         check(self.lib.egm_set_params(self.ctx, C.byref(p)), "egm_set_params")
 
     def reserve(self, queries: int, refs: int, pairs: int = 1):

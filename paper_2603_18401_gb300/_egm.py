@@ -57,7 +57,7 @@ class egm_out(C.Structure):
 
 class egm_params(C.Structure):
     _fields_ = [("ratio_num", C.c_int32), ("ratio_den", C.c_int32), ("sync", C.c_int32),
-                ("form", C.c_int32), ("reserved", C.c_int32 * 12)]
+                ("form", C.c_int32), ("band_tile", C.c_int32), ("reserved", C.c_int32 * 11)]
 
 
 class egm_stats(C.Structure):

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <vector>
 
 #include "egm_internal.cuh"
@@ -37,9 +38,9 @@ T *as(DevBuf &b) { return reinterpret_cast<T *>(b.ptr); }
 
 // Device scratch of one pipeline instance (a context, or a captured graph).
 struct Scratch {
-    DevBuf pairs, geom, offs, keys, rec, tab, qrec, qcount, scan, longlist, small, counters, blkpair, band;
+    DevBuf pairs, geom, offs, keys, rec, tab, curs, qrec, qcount, scan, longlist, small, counters, blkpair, band;
     void release() {
-        DevBuf *b[] = {&pairs, &geom, &offs, &keys, &rec, &tab, &qrec, &qcount, &scan, &longlist, &small,
+        DevBuf *b[] = {&pairs, &geom, &offs, &keys, &rec, &tab, &curs, &qrec, &qcount, &scan, &longlist, &small,
                        &counters, &blkpair, &band};
         for (DevBuf *x : b) {
             if (x->ptr) cudaFree(x->ptr);
@@ -76,6 +77,8 @@ struct egm_ctx {
     // the banded form sorts the queries on a second stream, beside the reference sort
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // band tile shape per batch size class (log2 of the tile count), set by the tuner
+    std::map<int, int> band_shape;
 };
 
 namespace {
@@ -258,6 +261,7 @@ cudaError_t reserve(Scratch &c_, int64_t nq, int64_t nr, int64_t ntab, int npair
     // 32 records of padding: bulk copies of a 32-row box may run past the last row
     if ((e = grow(c->rec, sizeof(float4) * (size_t)(nr + 32))) != cudaSuccess) return e;
     if ((e = grow(c->tab, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntab, 1))) != cudaSuccess) return e;
+    if ((e = grow(c->curs, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntab, 1))) != cudaSuccess) return e;
     if ((e = grow(c->qrec, sizeof(QueryRec) * (size_t)std::max<int64_t>(nq, 1))) != cudaSuccess) return e;
     if ((e = grow(c->qcount, sizeof(int64_t) * (size_t)(nq + 1))) != cudaSuccess) return e;
     if ((e = grow(c->scan, sizeof(int64_t) * (size_t)(nq / 8192 + 2))) != cudaSuccess) return e;
@@ -290,6 +294,9 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
     L.val_c = k + 5 * nr;
     L.rec = as<float4>(c->rec);
     L.tab = as<uint32_t>(c->tab);
+    L.ntab = pl.ntab;
+    L.curs = as<uint32_t>(c->curs);
+    L.prep_done = as<uint32_t>(c->small) + 40;
     L.qrec = as<QueryRec>(c->qrec);
     L.status = as<uint32_t>(c->small);
     L.counters = counters_on ? as<unsigned long long>(c->counters) : nullptr;
@@ -389,8 +396,10 @@ cudaError_t ensure_side(egm_ctx *c) {
     return e;
 }
 
+// `shape`: the band kernel's tile shape; negative stops before the band
+// kernel (the tuner then runs it once per shape).
 cudaError_t enqueue_pipeline(const Launch &L, Scratch &sc, bool csr, int max_n, cudaStream_t st, egm_ctx *tc,
-                             bool band, int sms, egm_ctx *sidec) {
+                             bool band, int sms, egm_ctx *sidec, int shape) {
     size_t tb = 0;
     if (tc && tc->timing_on) {
         tb = tc->ev_used;
@@ -416,14 +425,13 @@ cudaError_t enqueue_pipeline(const Launch &L, Scratch &sc, bool csr, int max_n, 
         EGM_Q(launch_query_sort(L, sidec->side));
         EGM_Q(cudaEventRecord(sidec->join_ev, sidec->side));
     }
-    EGM_Q(launch_sort(L, max_n, st));
+    EGM_Q(launch_sort(L, st));
     if (band) EGM_Q(cudaStreamWaitEvent(st, sidec->join_ev, 0));
     if (tc) EGM_Q(mark(tc, tb, 3));
-    EGM_Q(launch_post_sort(L, st));
     if (band) EGM_Q(launch_pack(L, st));
     if (tc) EGM_Q(mark(tc, tb, 4));
     if (band) {
-        EGM_Q(launch_band(L, sms, st));
+        if (shape >= 0) EGM_Q(launch_band(L, sms, shape, st));
         if (tc) EGM_Q(mark(tc, tb, 5));
     } else if (csr) {
         uint32_t *long_list = as<uint32_t>(sc.longlist);
@@ -440,6 +448,60 @@ cudaError_t enqueue_pipeline(const Launch &L, Scratch &sc, bool csr, int max_n, 
     if (tc) EGM_Q(mark(tc, tb, 6));
 #undef EGM_Q
     return cudaSuccess;
+}
+
+int tile_class(int64_t ntiles) {
+    int k = 0;
+    while (ntiles > 1) {
+        ntiles >>= 1;
+        k++;
+    }
+    return k;
+}
+
+// Times every band tile shape on the packed inputs already enqueued (the band
+// kernel only reads them, so each run rewrites the same outputs) and returns
+// the fastest by the median of three runs.  Waits for the stream.
+cudaError_t tune_band(egm_ctx *c, const Launch &L, cudaStream_t st, int &best) {
+    constexpr int kReps = 3;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    std::vector<std::vector<float>> ms(band_shapes());
+    for (int rep = 0; rep < kReps + 1 && e == cudaSuccess; rep++)   // the first round warms up
+        for (int k = 0; k < band_shapes() && e == cudaSuccess; k++) {
+            e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = launch_band(L, c->sms, k, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e == cudaSuccess && rep > 0) ms[k].push_back(t);
+        }
+    best = 0;
+    float best_ms = 0.0f;
+    for (int k = 0; k < band_shapes() && e == cudaSuccess; k++) {
+        std::sort(ms[k].begin(), ms[k].end());
+        const float med = ms[k][kReps / 2];
+        if (k == 0 || med < best_ms) {
+            best_ms = med;
+            best = k;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return e;
+}
+
+// The shape for this batch: forced by the parameters; with at most two tiles
+// per SM (every CTA takes one tile, latency decides) the shape with the
+// fewest chunks; otherwise the tuner's choice for the size class, or -1 (to
+// be tuned).
+int band_shape_for(egm_ctx *c, int64_t ntiles) {
+    if (c->params.band_tile > 0) return c->params.band_tile - 1;
+    if (ntiles <= 2 * (int64_t)c->sms) return 0;
+    auto it = c->band_shape.find(tile_class(ntiles));
+    return it == c->band_shape.end() ? -1 : it->second;
 }
 
 egm_status check_out(const egm_pair *pairs, int npairs, const egm_out *out) {
@@ -470,7 +532,16 @@ egm_status run_batch(egm_ctx *c, const egm_pair *pairs, int npairs, const egm_ou
     cudaStream_t st = c->stream;
     if (sync) EGM_TRY(cudaMemsetAsync(L.status, 0, sizeof(uint32_t), st));
     if (c->counters_on) EGM_TRY(cudaMemsetAsync(c->sc.counters.ptr, 0, 8 * sizeof(unsigned long long), st));
-    EGM_TRY(enqueue_pipeline(L, c->sc, csr, pl.max_n, st, c, band, c->sms, c));
+    const int shape = band ? band_shape_for(c, pl.ntiles) : 0;
+    if (band && shape < 0) {
+        // first batch of this size class: everything but the band kernel, then the tuner
+        EGM_TRY(enqueue_pipeline(L, c->sc, csr, pl.max_n, st, nullptr, band, c->sms, c, -1));
+        int best = 0;
+        EGM_TRY(tune_band(c, L, st, best));
+        c->band_shape[tile_class(pl.ntiles)] = best;
+    } else {
+        EGM_TRY(enqueue_pipeline(L, c->sc, csr, pl.max_n, st, c, band, c->sms, c, shape));
+    }
     c->last.queries = pl.nq;
     c->last.refs = pl.nr;
     return finish(c, sync);
@@ -547,6 +618,7 @@ egm_status egm_set_params(egm_ctx *c, const egm_params *p) {
     if (p->ratio_num <= 0 || p->ratio_den <= 0 || p->ratio_num > 1000000 || p->ratio_den > 1000000)
         return EGM_ERR_ARG;
     if (p->form < EGM_FORM_AUTO || p->form > EGM_FORM_BANDED) return EGM_ERR_ARG;
+    if (p->band_tile < 0 || p->band_tile > band_shapes()) return EGM_ERR_ARG;
     c->params = *p;
     return EGM_OK;
 }
@@ -727,6 +799,14 @@ egm_status egm_graph_create(egm_ctx *c, const egm_pair *pairs, int32_t npairs, c
     if (e == cudaSuccess)
         e = cudaMemcpy(g->sc.offs.ptr, h.data() + sizeof(PairDesc) * npairs, ob, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(g->sc.small.ptr, 0, 256);
+    int shape = band ? band_shape_for(c, pl.ntiles) : 0;
+    if (e == cudaSuccess && band && shape < 0) {
+        // tune on the graph's own scratch before capturing
+        const Launch T = make_launch(g->sc, false, c->params, pl, npairs, out, band);
+        e = enqueue_pipeline(T, g->sc, csr, pl.max_n, c->stream, nullptr, band, c->sms, c, -1);
+        if (e == cudaSuccess) e = tune_band(c, T, c->stream, shape);
+        if (e == cudaSuccess) c->band_shape[tile_class(pl.ntiles)] = shape;
+    }
     cudaStream_t cs = nullptr;
     cudaGraph_t gr = nullptr;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
@@ -735,7 +815,7 @@ egm_status egm_graph_create(egm_ctx *c, const egm_pair *pairs, int32_t npairs, c
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaError_t e2 = cudaMemsetAsync(L.status, 0, sizeof(uint32_t), cs);
-            if (e2 == cudaSuccess) e2 = enqueue_pipeline(L, g->sc, csr, pl.max_n, cs, nullptr, band, c->sms, c);
+            if (e2 == cudaSuccess) e2 = enqueue_pipeline(L, g->sc, csr, pl.max_n, cs, nullptr, band, c->sms, c, shape);
             e = cudaStreamEndCapture(cs, &gr);
             if (e == cudaSuccess) e = e2;
         }

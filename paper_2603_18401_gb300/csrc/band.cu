@@ -200,12 +200,12 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
 // ------------------------------------------------------------ band kernel
 constexpr int kTM = 128;                 // queries per tile (MMA M, TMEM lanes)
 constexpr int kBoxR = 32;                // reference rows per TMA box (N per box)
-constexpr int kCB = 2;                   // boxes per MMA chunk
-constexpr int kCtasPerSm = 3;            // resident CTAs per SM (shared memory and TMEM sized for it)
-constexpr int kCN = kBoxR * kCB;         // columns per chunk
 constexpr int kBandThreads = kTM + 32;   // four epilogue warps and the control warp
-constexpr uint32_t kTmemCols = 2 * kCN;  // double-buffered accumulator
 constexpr int kRnRow = kBoxR + 4;        // norms copied from a 16-byte aligned start
+// Tile shapes (chosen per workload by the tuner): CB boxes per MMA chunk
+// (N = 32 CB) and CPS resident CTAs per SM, which size shared memory and TMEM.
+//   0: CB 4, CPS 2   few tiles per SM (single pairs): fewer, larger chunks
+//   1: CB 2, CPS 3   many tiles (batches): more CTAs in flight per SM
 constexpr int kGroup = 8;                // columns per TMEM load in the epilogue
 
 struct __align__(16) Piece {
@@ -213,11 +213,13 @@ struct __align__(16) Piece {
     int32_t li;
 };
 
+template <int CB>
 struct BandSmem {
+    static constexpr int kCN = kBoxR * CB;  // columns per chunk
     uint8_t A[2][kTM * 128];      // query tile, K halves (1024-byte aligned)
     uint8_t B[2][2][kCN * 128];   // band chunk: stage, K half
     float4 rec[2][kCN];           // (x - cx, y - cy, eps, index) of each column
-    float rn[2][kCB][kRnRow];     // norms of each box's rows
+    float rn[2][CB][kRnRow];      // norms of each box's rows
     // fullB: a stage's operand rows landed; sfree: the MMA that read them is
     // done; fullR: a stage's records and norms landed; done: an accumulator is
     // ready; tfree: the epilogue has read it and the stage's records
@@ -235,15 +237,20 @@ struct BandSmem {
     volatile uint32_t err;
 };
 
-static_assert(offsetof(BandSmem, B) % 1024 == 0, "operand tiles need 1024-byte alignment");
-static_assert(offsetof(BandSmem, rn) % 16 == 0, "bulk copy destinations need 16-byte alignment");
-// kCtasPerSm CTAs per SM share the 512 TMEM columns; shared memory keeps
-// one more from becoming resident (its allocation would wait for another CTA
-// to end).
-constexpr size_t kSmPerSm = 228 * 1024, kSmPerCta = sizeof(BandSmem) + 1024 + 1024;
-static_assert(kCtasPerSm * kSmPerCta <= kSmPerSm && (kCtasPerSm + 1) * kSmPerCta > kSmPerSm,
-              "shared memory admits exactly kCtasPerSm CTAs per SM");
-static_assert(kCtasPerSm * kTmemCols <= 512, "TMEM columns of the resident CTAs");
+template <int CB, int CPS>
+struct BandShape {
+    static constexpr int kCB = CB, kCN = kBoxR * CB;
+    static constexpr uint32_t kTmemCols = 2 * kCN;  // double-buffered accumulator (a power of two)
+    using Smem = BandSmem<CB>;
+    static_assert(offsetof(Smem, B) % 1024 == 0, "operand tiles need 1024-byte alignment");
+    static_assert(offsetof(Smem, rn) % 16 == 0, "bulk copy destinations need 16-byte alignment");
+    // CPS CTAs per SM share the 512 TMEM columns; shared memory keeps one more
+    // from becoming resident (its allocation would wait for another CTA to end)
+    static constexpr size_t kSmPerSm = 228 * 1024, kSmPerCta = sizeof(Smem) + 1024 + 1024;
+    static_assert(CPS * kSmPerCta <= kSmPerSm && (CPS + 1) * kSmPerCta > kSmPerSm,
+                  "shared memory admits exactly CPS CTAs per SM");
+    static_assert(CPS * kTmemCols <= 512 && (kTmemCols & (kTmemCols - 1)) == 0, "TMEM columns");
+};
 
 __device__ __forceinline__ int sortable(float f) {
     const int b = __float_as_int(f);
@@ -255,7 +262,8 @@ __device__ __forceinline__ float unsortable(int b) { return __int_as_float(b >= 
 struct BoxCursor {
     int k = 0;
     uint32_t b = 0;
-    __device__ __forceinline__ void next(const BandSmem &S, uint32_t &pos, uint32_t &len, int &li) {
+    template <class SM>
+    __device__ __forceinline__ void next(const SM &S, uint32_t &pos, uint32_t &len, int &li) {
         const Piece &pc = S.pc[k];
         pos = pc.start + b * kBoxR;
         len = min((uint32_t)kBoxR, pc.len - b * kBoxR);
@@ -282,8 +290,13 @@ __device__ __forceinline__ void top2(unsigned long long key, unsigned long long 
     }
 }
 
-__global__ void __launch_bounds__(kBandThreads, kCtasPerSm)
+template <int CB, int CPS>
+__global__ void __launch_bounds__(kBandThreads, CPS)
     band_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Launch L) {
+    using Shape = BandShape<CB, CPS>;
+    using BandSmem = typename Shape::Smem;
+    constexpr int kCB = Shape::kCB, kCN = Shape::kCN;
+    constexpr uint32_t kTmemCols = Shape::kTmemCols;
     extern __shared__ uint8_t smraw[];
     // 1024-byte alignment by pointer arithmetic on the shared array, so that
     // accesses through S stay shared-memory accesses
@@ -697,20 +710,33 @@ cudaError_t launch_pack(const Launch &L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_band(const Launch &L, int sms, cudaStream_t s) {
+template <int CB, int CPS>
+cudaError_t launch_band_shape(const Launch &L, int sms, const CUtensorMap &tA, const CUtensorMap &tB,
+                              cudaStream_t s) {
+    const int smem = (int)sizeof(BandSmem<CB>) + 1024;
+    int64_t grid = L.ntiles;
+    if (grid > CPS * (int64_t)sms) grid = CPS * (int64_t)sms;
+    cudaError_t e = cudaMemsetAsync(L.work, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(band_kernel<CB, CPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    band_kernel<CB, CPS><<<(int)grid, kBandThreads, smem, s>>>(tA, tB, L);
+    return cudaGetLastError();
+}
+
+int band_shapes() { return 2; }
+
+cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s) {
     if (L.ntiles == 0) return cudaSuccess;
     CUtensorMap tA, tB;
     cudaError_t e = make_tmap(&tA, L.descA, L.nq, kTM);
     if (e != cudaSuccess) return e;
     if ((e = make_tmap(&tB, L.descB, L.nr, kBoxR)) != cudaSuccess) return e;
-    const int smem = (int)sizeof(BandSmem) + 1024;
-    int64_t grid = L.ntiles;
-    if (grid > kCtasPerSm * (int64_t)sms) grid = kCtasPerSm * (int64_t)sms;
-    if ((e = cudaMemsetAsync(L.work, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    band_kernel<<<(int)grid, kBandThreads, smem, s>>>(tA, tB, L);
-    return cudaGetLastError();
+    switch (shape) {
+        case 0: return launch_band_shape<4, 2>(L, sms, tA, tB, s);
+        case 1: return launch_band_shape<2, 3>(L, sms, tA, tB, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace egm

@@ -5,9 +5,11 @@
 //   PairGeom[npairs]   epipole, key frame, per-level statistics and tables
 //   per reference (sum of n over pairs, pair p at r_off):
 //     key_a/val_a      unsorted (level|angle-key, local index) pairs
-//     key_b/val_b      sort output; key_c/val_c ping-pong for long segments
-//     rec              float4 (x - cx, y - cy, eps, index bits) in key order
+//     key_c            scratch of the CSR long-row sort
+//     rec              float4 (x - cx, y - cy, eps, index bits) in bucket order
 //   tab                per (pair, level) bucket -> first sorted position
+//   curs               bucket fill cursors while the records are placed
+//   banded form: query order, packed operand rows, sorted query records
 //   per query (sum of m, pair p at q_off):
 //     QueryRec         FP32 line in the pair frame, window centre, pad terms
 //     qcount           candidates per query (CSR path)
@@ -110,6 +112,9 @@ struct Launch {
     uint32_t *key_a, *val_a, *key_b, *val_b, *key_c, *val_c;
     float4 *rec;
     uint32_t *tab;
+    int64_t ntab;                 // table entries of the whole call (zeroed by the prep kernel)
+    uint32_t *curs;               // bucket fill cursors (a copy of tab while the records are placed)
+    uint32_t *prep_done;          // blocks of the prep kernel finished (the last one resets it)
     QueryRec *qrec;
     uint32_t *status;
     unsigned long long *counters;  // egm_stats fields, or NULL
@@ -148,27 +153,54 @@ constexpr int kClusterItems = 8;
 constexpr int kClusterMaxN = kClusterCtas * kClusterThreads * kClusterItems;  // 32768
 
 // Level layout (first sorted position, bucket bits, table offset) from the
-// level counts; every block that needs it computes the same values.
-__device__ __forceinline__ void level_layout(const uint32_t *cnt, uint32_t *start, int32_t *bits, uint32_t *tab,
-                                             int max_bits) {
-    uint32_t pos = 0, toff = 0;
-    for (int l = 0; l < kLevels; l++) {
-        const uint32_t c = cnt[l];
-        start[l] = pos;
-        int b = 0;
-        if (c > 1) {
-            b = 32 - __clz(c - 1) + 1;  // ~2 buckets per member
-            if (b > max_bits) b = max_bits;
-        }
-        bits[l] = b;
-        tab[l] = toff;
-        toff += (1u << b) + 1u;
-        pos += c;
+// level counts; every block that needs it computes the same values.  One warp,
+// lane = level: a level of c > 1 members gets about two buckets per member
+// (ceil(log2 c) + 1 bits, at most max_bits) and a table of 2^bits + 1
+// entries; positions and table offsets are exclusive prefix sums.
+constexpr int kMaxBucketBits = 16;  // the tables resolve at most 16 bits of a 22-bit angle key
+
+__device__ __forceinline__ void level_layout_lane(uint32_t c, uint32_t *start, int32_t *bits, uint32_t *tab,
+                                                  int max_bits, int lane) {
+    int b = 0;
+    if (c > 1) {
+        b = 32 - __clz(c - 1) + 1;
+        if (b > max_bits) b = max_bits;
     }
-    start[kLevels] = pos;
+    const uint32_t sz = (1u << b) + 1u;
+    uint32_t ic = c, is = sz;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t tc = __shfl_up_sync(0xffffffffu, ic, o);
+        const uint32_t ts = __shfl_up_sync(0xffffffffu, is, o);
+        if (lane >= o) {
+            ic += tc;
+            is += ts;
+        }
+    }
+    start[lane] = ic - c;
+    bits[lane] = b;
+    tab[lane] = is - sz;
+    if (lane == kLevels - 1) start[kLevels] = ic;
+}
+static_assert(kLevels == 32, "one lane per level");
+
+__device__ __forceinline__ void level_layout_warp(const uint32_t *cnt, uint32_t *start, int32_t *bits,
+                                                  uint32_t *tab, int max_bits, int lane) {
+    level_layout_lane(cnt[lane], start, bits, tab, max_bits, lane);
 }
 
-// Index of the pair that owns flattened element g, given offs[0..npairs].
+// The same search over offsets held in shared memory (plain loads).
+__device__ __forceinline__ int pair_of_shared(const int64_t *offs, int npairs, int64_t g) {
+    int lo = 0, hi = npairs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (offs[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Index of the pair that owns flattened element g, given offs[0..npairs] in
+// global memory.
 __device__ __forceinline__ int pair_of(const int64_t *offs, int npairs, int64_t g) {
     int lo = 0, hi = npairs - 1;
     while (lo < hi) {
@@ -395,10 +427,10 @@ int band_row_bytes();
 int band_tile_queries();
 cudaError_t launch_query_sort(const Launch &L, cudaStream_t s);
 cudaError_t launch_pack(const Launch &L, cudaStream_t s);
-cudaError_t launch_band(const Launch &L, int sms, cudaStream_t s);
+int band_shapes();  // tile shapes of the band kernel (see band.cu)
+cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s);
 cudaError_t launch_prep(const Launch &L, cudaStream_t s);
-cudaError_t launch_sort(const Launch &L, int max_n, cudaStream_t s);
-cudaError_t launch_post_sort(const Launch &L, cudaStream_t s);
+cudaError_t launch_sort(const Launch &L, cudaStream_t s);
 cudaError_t launch_stab(const Launch &L, int mode, cudaStream_t s);  // 0 fused match, 1 count, 2 fill+match
 cudaError_t launch_csr_offsets(const Launch &L, uint32_t *long_count, cudaStream_t s);
 cudaError_t launch_csr_row_sort(const Launch &L, uint32_t *long_list, uint32_t *long_count, cudaStream_t s);

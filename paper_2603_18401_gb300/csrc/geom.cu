@@ -173,6 +173,9 @@ __global__ void __launch_bounds__(32) geometry_kernel(Launch L) {
 __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
     const int64_t total = L.nr + L.nq;
     const int lane = threadIdx.x & 31;
+    // the bucket tables start from zero (the counting sort after this kernel fills them)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.ntab / 4; i += (int64_t)gridDim.x * blockDim.x)
+        reinterpret_cast<uint4 *>(L.tab)[i] = make_uint4(0, 0, 0, 0);
     for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < total; g0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t g = g0 + threadIdx.x;
         const bool valid = g < total;
@@ -298,6 +301,21 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
             atomicMin(&G.dmin[lv], dmin);
             atomicMax(&G.tmax[lv], tmax);
         }
+    }
+    // The last block to finish derives every pair's level layout (first sorted
+    // position, bucket bits, table offset) from the final level counts.
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(L.prep_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (int p = threadIdx.x >> 5; p < L.npairs; p += blockDim.x >> 5) {
+            PairGeom &G = L.geom[p];
+            level_layout_lane(__ldcg(&G.cnt[lane]), G.start, G.bits, G.tab, kMaxBucketBits, lane);
+        }
+        if (threadIdx.x == 0) *L.prep_done = 0u;  // ready for the next launch
     }
 }
 

@@ -1,22 +1,18 @@
-// Device LSD radix sort of the reference keys, one thread block per pair.
+// Ordering of the reference keypoints by (level, angle bucket).
 //
 // This replaces the paper's centred segment tree (Sec. 4.4, "Segment Tree
-// Structure"): once the keypoints of each angular-radius level are sorted by
-// angle, a query's angle window is a contiguous range of the sorted array.
+// Structure"): once the keypoints of each angular-radius level are ordered by
+// angle, a query's angle window is a contiguous run of them, found through a
+// per-level bucket table (bucket -> first position).
 //
-// Keys are 27 bits: level (5) | quantised angle (22); values are the
-// keypoints' local indices.  The bucket tables that replace the tree resolve
-// at most 16 bits of the angle, so the sort orders the keys by bits 6..26
-// (level and the top 16 angle bits) in three stable passes of 7-bit digits;
-// the full key stays in the array for the exact window filter.  Within a
-// tile of 16384 elements every warp owns 512 consecutive elements in striped
-// order (item k of lane l is element 32 k + l); ranking items in k order with
-// a ballot-based warp multi-split keeps the sort stable.
-// A segment that fits one tile stays in registers and shared memory for all
-// passes; longer segments ping-pong through global scratch tile by tile.
+// Keys are 27 bits: level (5) | quantised angle (22).  The tables resolve at
+// most 16 bits of the angle, about two buckets per member of a level, so a
+// counting sort by (level, bucket) is all the order the windows need (the
+// bucket kernels below).
 //
-// The block also derives, from the level counts of the prep kernel, each
-// level's first sorted position, bucket-table size and table offset.
+// A stable LSD block radix sort (ballot-based warp multi-split over tiles of
+// 16384 elements; 7-bit digits) orders candidate rows of the CSR output that
+// are longer than a warp sorts.
 #include <cooperative_groups.h>
 
 #include "egm_internal.cuh"
@@ -34,8 +30,6 @@ constexpr int kTile = kSortThreads * kItems;     // 16384
 constexpr int kWarpSpan = 32 * kItems;           // 512 elements per warp
 constexpr int kRBits = 7;
 constexpr int kBins = 1 << kRBits;
-constexpr int kFirstShift = 6;                                               // bits below are not needed
-constexpr int kPasses = (kKeyBits - kFirstShift + kRBits - 1) / kRBits;  // 3
 
 struct SortSmem {
     uint32_t whist[kSortWarps * kBins];  // [warp][digit]
@@ -215,200 +209,160 @@ __device__ void block_radix_sort(SortSmem &S, const uint32_t *ik, const uint32_t
     }
 }
 
-__global__ void __launch_bounds__(kSortThreads, 1) sort_kernel(Launch L) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SortSmem &S = *reinterpret_cast<SortSmem *>(smem_raw);
-    const int p = blockIdx.x;
-    const PairDesc &P = L.pairs[p];
-    PairGeom &G = L.geom[p];
+// ---------------------------------------------------------------------------
+// Bucket sort of the references: one counting pass per pair.
+//   (the prep kernel zeroes the tables and lays out every pair's levels)
+//   bucket_count_kernel   per reference: one atomic add on its bucket
+//   bucket_scan_kernel    per pair: one exclusive scan over the concatenated
+//                         per-level tables, which yields every level's table
+//                         at once (the first position of each bucket; in each
+//                         level's extra last entry, the level's end), and a
+//                         copy as fill cursors; then every reference takes
+//                         the next position of its bucket and writes its FP32
+//                         record (x - cx, y - cy, eps, index) there.
+// The order within a bucket follows the atomics and is not fixed; everything
+// downstream depends only on bucket order (ties between candidates are broken
+// by index).
+constexpr int kSmemPairs = 1024;                      // pair offsets cached in shared memory up to this
 
-    if (P.n <= kClusterMaxN) return;  // sorted by the cluster kernel
-    if (threadIdx.x == 0) level_layout(G.cnt, G.start, G.bits, G.tab, kQBits - kFirstShift);
-    const int64_t b = P.r_off;
-    block_radix_sort(S, L.key_a + b, L.val_a + b, L.key_c + b, L.val_c + b, L.key_b + b, L.val_b + b, P.n,
-                     kFirstShift, kPasses);
+__device__ __forceinline__ uint32_t bucket_slot(const PairGeom &G, uint32_t key) {
+    const int lv = (int)(key >> kQBits);
+    return G.tab[lv] + ((key & kQMax) >> (kQBits - G.bits[lv]));
 }
 
-// ---------------------------------------------------------------------------
-// Cluster sort: the eight blocks of a thread-block cluster sort one pair.
-// Block r owns sorted positions [r*chunk, (r+1)*chunk).  Per pass every block
-// ranks its elements (ballot multi-split per warp), publishes its 128 digit
-// totals in shared memory, reads all blocks' totals through distributed
-// shared memory to place its elements, and stores each element straight into
-// the shared memory of the block that owns its new position.  After the last
-// pass the blocks write the sorted keys, the FP32 records and the bucket
-// tables (the work of post_sort_kernel) for their positions.
-constexpr int kCWarps = kClusterThreads / 32;
-constexpr int kCChunk = kClusterThreads * kClusterItems;
+__global__ void __launch_bounds__(256) bucket_count_kernel(Launch L) {
+    __shared__ int64_t offs[kSmemPairs + 1];
+    const bool cached = L.npairs <= kSmemPairs;
+    if (cached)
+        for (int i = threadIdx.x; i <= L.npairs; i += blockDim.x) offs[i] = L.r_offs[i];
+    __syncthreads();
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L.nr; g += (int64_t)gridDim.x * blockDim.x) {
+        const int p = cached ? pair_of_shared(offs, L.npairs, g) : pair_of(L.r_offs, L.npairs, g);
+        atomicAdd(L.tab + L.pairs[p].t_off + bucket_slot(L.geom[p], L.key_a[g]), 1u);
+    }
+}
 
-struct ClusterSmem {
-    uint32_t rkey[kCChunk];
-    uint32_t rval[kCChunk];
-    uint32_t whist[kCWarps * kBins];
-    uint32_t hist[kBins];      // this block's digit totals, read by the whole cluster
-    uint32_t tot[kBins];
-    uint32_t base[kBins];
-    uint32_t start[kLevels + 1];
-    int32_t bits[kLevels];
-    uint32_t tab[kLevels];
-};
+// The scan and the placement of one pair run on a thread-block cluster: its
+// warps hold rows of 128 table entries (a 16-byte vector per lane) in
+// registers, so a pass over the table is one round trip to memory; the
+// blocks' totals are exchanged through distributed shared memory.
+constexpr int kScanCtas = 8;
+constexpr int kScanThreads = 256;
+constexpr int kScanWarps = kScanThreads / 32;
+constexpr int kScanRound = 8;  // rows a warp keeps in registers per round
 
-__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads)
-    cluster_sort_kernel(Launch L) {
-    __shared__ __align__(16) ClusterSmem S;
+__global__ void __cluster_dims__(kScanCtas, 1, 1) __launch_bounds__(kScanThreads) bucket_scan_kernel(Launch L) {
+    __shared__ __align__(16) PairGeom G;
+    __shared__ uint32_t wtot[kScanWarps];
+    __shared__ uint32_t ctot;     // this block's total, read by the higher-ranked blocks
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    const int p = blockIdx.x / kClusterCtas;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int p = blockIdx.x / kScanCtas;
     const PairDesc &P = L.pairs[p];
-    PairGeom &G = L.geom[p];
-    const int n = P.n;
-    if (n <= 0 || n > kClusterMaxN) return;  // the same for every block of the cluster
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int items = (n + kClusterCtas * kClusterThreads - 1) / (kClusterCtas * kClusterThreads);
-    const int chunk = items * kClusterThreads;
-    const int wspan = items * 32;
-    const uint32_t lt = lanemask_lt();
-    if (threadIdx.x == 0) {
-        level_layout(G.cnt, S.start, S.bits, S.tab, kQBits - kFirstShift);
-        if (rank == 0) {
-            for (int l = 0; l < kLevels; l++) {
-                G.start[l] = S.start[l];
-                G.bits[l] = S.bits[l];
-                G.tab[l] = S.tab[l];
-            }
-            G.start[kLevels] = S.start[kLevels];
-        }
-    }
+    if (tid < (int)(sizeof(PairGeom) / 16))
+        reinterpret_cast<uint4 *>(&G)[tid] = reinterpret_cast<const uint4 *>(L.geom + p)[tid];
+    __syncthreads();
+    const uint32_t used = G.tab[kLevels - 1] + (1u << G.bits[kLevels - 1]) + 1u;
+    const uint32_t used4 = (used + 3u) & ~3u;  // the table's capacity leaves room for the padding
+    uint4 *T4 = reinterpret_cast<uint4 *>(L.tab + P.t_off);
+    uint4 *C4 = reinterpret_cast<uint4 *>(L.curs + P.t_off);
+    // warp gw of the cluster owns rows [gw R, gw R + R) of 128 entries
+    const uint32_t rows = (used4 + 127u) / 128u;
+    const uint32_t nw = kScanCtas * kScanWarps, gw = (uint32_t)(rank * kScanWarps + warp);
+    const uint32_t R = (rows + nw - 1) / nw, r0 = gw * R, r1 = min(rows, r0 + R);
+    auto load_row = [&](uint32_t r) {
+        const uint32_t i = r * 32u + (uint32_t)lane;  // uint4 index
+        return i * 4u < used4 ? T4[i] : make_uint4(0, 0, 0, 0);
+    };
+    // this thread's first references, loaded now so that the loads overlap the scan
+    constexpr int kPre = 8;
     const int64_t b = P.r_off;
-    uint32_t key[kClusterItems], val[kClusterItems], rk[kClusterItems / 2];
+    const int stride = kScanCtas * kScanThreads;
+    uint32_t key[kPre];
+    double x[kPre], y[kPre], ep[kPre];
+    auto load_refs = [&](int e0) {
 #pragma unroll
-    for (int k = 0; k < kClusterItems; k++) {
-        key[k] = 0xffffffffu;
-        val[k] = 0u;
-        if (k < items) {
-            const int e = rank * chunk + warp * wspan + k * 32 + lane;
-            if (e < n) {
+        for (int k = 0; k < kPre; k++) {
+            const int e = e0 + k * stride;
+            key[k] = 0xffffffffu;
+            if (e < P.n) {
                 key[k] = L.key_a[b + e];
-                val[k] = L.val_a[b + e];
+                x[k] = P.xy2[2 * (int64_t)e];
+                y[k] = P.xy2[2 * (int64_t)e + 1];
+                ep[k] = P.eps2 ? P.eps2[e] : P.eps_scalar;
             }
         }
+    };
+    const int first = rank * kScanThreads + tid;
+    load_refs(first);
+    // pass 1: this warp's total (rows kept in registers when they fit one round)
+    uint4 v[kScanRound];
+    uint32_t sum = 0;
+    for (uint32_t r = r0; r < r1; r += kScanRound) {
+#pragma unroll
+        for (int k = 0; k < kScanRound; k++) v[k] = r + k < r1 ? load_row(r + k) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int k = 0; k < kScanRound; k++) sum += v[k].x + v[k].y + v[k].z + v[k].w;
     }
-    for (int pass = 0; pass < kPasses; pass++) {
-        const int shift = kFirstShift + pass * kRBits;
-        if (pass > 0) {
+    sum = __reduce_add_sync(0xffffffffu, sum);
+    if (lane == 0) wtot[warp] = sum;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < kScanWarps ? wtot[lane] : 0u;
+        uint32_t wi = w;
 #pragma unroll
-            for (int k = 0; k < kClusterItems; k++)
-                if (k < items) {
-                    const int e = warp * wspan + k * 32 + lane;
-                    key[k] = S.rkey[e];
-                    val[k] = S.rval[e];
-                }
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
         }
-        uint32_t *wh = S.whist + warp * kBins;
-        for (int d = lane; d < kBins; d += 32) wh[d] = 0u;
-        __syncwarp();
+        if (lane < kScanWarps) wtot[lane] = wi - w;
+        if (lane == 31) ctot = wi;
+    }
+    cluster.sync();  // every block total published
+    uint32_t carry = wtot[warp];
+    for (int c = 0; c < rank; c++) carry += *cluster.map_shared_rank(&ctot, c);
+    // pass 2: exclusive values: the table (first position of each bucket) and the cursors
+    const bool one_round = r1 <= r0 + kScanRound;
+    for (uint32_t r = r0; r < r1; r += kScanRound) {
+        if (!one_round) {
 #pragma unroll
-        for (int k = 0; k < kClusterItems; k++) {
-            if (k < items) {
-                const uint32_t dg = digit_of(key[k], shift);
-                uint32_t peers = 0xffffffffu;
-#pragma unroll
-                for (int bit = 0; bit < kRBits; bit++) {
-                    const uint32_t bal = __ballot_sync(0xffffffffu, (dg >> bit) & 1u);
-                    peers &= ((dg >> bit) & 1u) ? bal : ~bal;
-                }
-                const uint32_t before = wh[dg];
-                const uint32_t r = before + __popc(peers & lt);
-                if (k & 1) rk[k >> 1] |= r << 16; else rk[k >> 1] = r;
-                __syncwarp();
-                if ((peers & lt) == 0u) wh[dg] = before + __popc(peers);
-                __syncwarp();
-            }
+            for (int k = 0; k < kScanRound; k++) v[k] = r + k < r1 ? load_row(r + k) : make_uint4(0, 0, 0, 0);
         }
-        __syncthreads();
-        if (threadIdx.x < kBins) {
-            uint32_t acc = 0;
 #pragma unroll
-            for (int w = 0; w < kCWarps; w++) {
-                uint32_t *c = S.whist + w * kBins + threadIdx.x;
-                const uint32_t v = *c;
-                *c = acc;
-                acc += v;
-            }
-            S.hist[threadIdx.x] = acc;
-        }
-        cluster.sync();  // all totals published; every block has read its receive buffer
-        if (threadIdx.x < kBins) {
-            uint32_t tot = 0, pre = 0;
-            for (int c = 0; c < kClusterCtas; c++) {
-                const uint32_t v = cluster.map_shared_rank(S.hist, c)[threadIdx.x];
-                tot += v;
-                if (c < rank) pre += v;
-            }
-            S.tot[threadIdx.x] = tot;
-            S.base[threadIdx.x] = pre;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t v[4], sum = 0;
-#pragma unroll
-            for (int q = 0; q < 4; q++) { v[q] = S.tot[lane * 4 + q]; sum += v[q]; }
-            uint32_t incl = sum;
+        for (int k = 0; k < kScanRound; k++) {
+            if (r + k >= r1) break;
+            const uint32_t ls = v[k].x + v[k].y + v[k].z + v[k].w;
+            uint32_t incl = ls;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += t;
             }
-            uint32_t acc = incl - sum;
-#pragma unroll
-            for (int q = 0; q < 4; q++) { S.base[lane * 4 + q] += acc; acc += v[q]; }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < kClusterItems; k++) {
-            if (k < items) {
-                const uint32_t dg = digit_of(key[k], shift);
-                const uint32_t r = (rk[k >> 1] >> ((k & 1) * 16)) & 0xffffu;
-                const uint32_t pos = S.base[dg] + wh[dg] + r;
-                const int dest = (int)(pos / (uint32_t)chunk);
-                const uint32_t off = pos - (uint32_t)dest * (uint32_t)chunk;
-                cluster.map_shared_rank(S.rkey, dest)[off] = key[k];
-                cluster.map_shared_rank(S.rval, dest)[off] = val[k];
+            const uint32_t e0 = carry + incl - ls;
+            const uint4 out = make_uint4(e0, e0 + v[k].x, e0 + v[k].x + v[k].y, e0 + v[k].x + v[k].y + v[k].z);
+            const uint32_t i = (r + k) * 32u + (uint32_t)lane;
+            if (i * 4u < used4) {
+                T4[i] = out;
+                C4[i] = out;
             }
-        }
-        cluster.sync();  // every element has landed in its owner's buffer
-    }
-
-    // sorted keys, FP32 records and bucket tables for this block's positions
-    const PairGeom &Gc = G;
-    const double cx = Gc.cx, cy = Gc.cy;
-    for (int i = threadIdx.x; i < chunk; i += kClusterThreads) {
-        const int pos = rank * chunk + i;
-        if (pos >= n) break;
-        const uint32_t kk = S.rkey[i];
-        const uint32_t j = S.rval[i];
-        L.key_b[b + pos] = kk;
-        L.val_b[b + pos] = j;
-        const double x = P.xy2[2 * (int64_t)j], y = P.xy2[2 * (int64_t)j + 1];
-        const double eps = P.eps2 ? P.eps2[j] : P.eps_scalar;
-        L.rec[b + pos] = make_float4((float)(x - cx), (float)(y - cy), (float)eps, __uint_as_float(j));
-        const int lv = (int)(kk >> kQBits);
-        const uint32_t s0 = S.start[lv], e0 = S.start[lv + 1];
-        const int sh = kQBits - S.bits[lv];
-        uint32_t *T = L.tab + P.t_off + S.tab[lv];
-        const int64_t bk = (int64_t)((kk & kQMax) >> sh);
-        int64_t bp = -1;
-        if ((uint32_t)pos != s0) {
-            const uint32_t prev = i > 0 ? S.rkey[i - 1] : cluster.map_shared_rank(S.rkey, rank - 1)[chunk - 1];
-            bp = (int64_t)((prev & kQMax) >> sh);
-        }
-        for (int64_t bb = bp + 1; bb <= bk; bb++) T[bb] = (uint32_t)pos;
-        if ((uint32_t)pos == e0 - 1) {
-            const int64_t nb = (int64_t)1 << S.bits[lv];
-            for (int64_t bb = bk + 1; bb <= nb; bb++) T[bb] = e0;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
-    cluster.sync();  // keep this block's shared memory alive for its neighbour's reads
+    cluster.sync();  // every cursor in place (cluster-scope ordering of the global writes)
+    // placement: the pair's references into their buckets
+    for (int e0 = first; e0 < P.n; e0 += stride * kPre) {
+        if (e0 != first) load_refs(e0);
+#pragma unroll
+        for (int k = 0; k < kPre; k++) {
+            if (key[k] == 0xffffffffu) continue;
+            const int e = e0 + k * stride;
+            const uint32_t pos = atomicAdd(L.curs + P.t_off + bucket_slot(G, key[k]), 1u);
+            L.rec[b + pos] = make_float4((float)(x[k] - G.cx), (float)(y[k] - G.cy), (float)ep[k],
+                                         __uint_as_float((uint32_t)e));
+        }
+    }
+    cluster.sync();  // no block leaves while another may still read its shared memory
 }
 
 // Candidate rows longer than a warp sorts: one block sorts them one after the
@@ -431,14 +385,12 @@ __global__ void __launch_bounds__(kSortThreads, 1) long_row_sort_kernel(Launch L
 
 }  // namespace
 
-cudaError_t launch_sort(const Launch &L, int max_n, cudaStream_t s) {
-    cluster_sort_kernel<<<L.npairs * kClusterCtas, kClusterThreads, 0, s>>>(L);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || max_n <= kClusterMaxN) return e;
-    const int smem = (int)sizeof(SortSmem);
-    e = cudaFuncSetAttribute(sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    sort_kernel<<<L.npairs, kSortThreads, smem, s>>>(L);
+cudaError_t launch_sort(const Launch &L, cudaStream_t s) {
+    if (L.nr == 0) return cudaSuccess;
+    int64_t blocks = (L.nr + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    bucket_count_kernel<<<(int)blocks, 256, 0, s>>>(L);
+    bucket_scan_kernel<<<L.npairs * kScanCtas, kScanThreads, 0, s>>>(L);
     return cudaGetLastError();
 }
 

@@ -1,9 +1,5 @@
 // Candidate retrieval and candidate-restricted matching.
 //
-//   post_sort_kernel  gathers the sorted references into FP32 records
-//                     (x - cx, y - cy, eps, index) and fills, per level, a
-//                     bucket table: entry b = first sorted position whose
-//                     quantised angle has top bits >= b.
 //   stab_kernel       one warp per query (Sec. 4.2 "query"; Algorithm 1,
 //                     Match loop).  Lane l computes the angle window of level
 //                     l, the largest angular radius among that level's
@@ -24,34 +20,6 @@
 namespace egm {
 
 namespace {
-
-__global__ void __launch_bounds__(256) post_sort_kernel(Launch L) {
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L.nr;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int p = pair_of(L.r_offs, L.npairs, g);
-        const PairDesc &P = L.pairs[p];
-        if (P.n <= kClusterMaxN) continue;  // done by the cluster sort
-        const PairGeom &G = L.geom[p];
-        const uint32_t pos = (uint32_t)(g - P.r_off);
-        const uint32_t key = L.key_b[g];
-        const uint32_t j = L.val_b[g];
-        const double x = P.xy2[2 * (int64_t)j], y = P.xy2[2 * (int64_t)j + 1];
-        const double eps = P.eps2 ? P.eps2[j] : P.eps_scalar;
-        L.rec[g] = make_float4((float)(x - G.cx), (float)(y - G.cy), (float)eps, __uint_as_float(j));
-
-        const int lv = (int)(key >> kQBits);
-        const uint32_t s = G.start[lv], e = G.start[lv + 1];
-        const int sh = kQBits - G.bits[lv];
-        uint32_t *T = L.tab + P.t_off + G.tab[lv];
-        const int64_t b = (int64_t)((key & kQMax) >> sh);
-        const int64_t bp = pos == s ? -1 : (int64_t)((L.key_b[g - 1] & kQMax) >> sh);
-        for (int64_t bb = bp + 1; bb <= b; bb++) T[bb] = pos;
-        if (pos == e - 1) {
-            const int64_t nb = (int64_t)1 << G.bits[lv];
-            for (int64_t bb = b + 1; bb <= nb; bb++) T[bb] = e;
-        }
-    }
-}
 
 // ------------------------------------------------------------ descriptors
 
@@ -591,14 +559,6 @@ __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mod
 }
 
 }  // namespace
-
-cudaError_t launch_post_sort(const Launch &L, cudaStream_t s) {
-    if (L.nr == 0 || L.max_n <= kClusterMaxN) return cudaSuccess;
-    int64_t blocks = (L.nr + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    post_sort_kernel<<<(int)blocks, 256, 0, s>>>(L);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_stab(const Launch &L, int mode, cudaStream_t s) {
     if (L.nq == 0) return cudaSuccess;

@@ -36,7 +36,8 @@ constexpr size_t kOffKeys = align256(kOffOffs + 4 * sizeof(int64_t));
 constexpr size_t kOffRec = align256(kOffKeys + 6 * sizeof(uint32_t) * N);
 constexpr size_t kOffTab = align256(kOffRec + sizeof(float4) * N);
 constexpr int64_t kTabCap = 4 * N + 2 * kLevels + 32;
-constexpr size_t kOffQrec = align256(kOffTab + sizeof(uint32_t) * kTabCap);
+constexpr size_t kOffCurs = align256(kOffTab + sizeof(uint32_t) * kTabCap);
+constexpr size_t kOffQrec = align256(kOffCurs + sizeof(uint32_t) * kTabCap);
 constexpr size_t kOffQcount = align256(kOffQrec + sizeof(QueryRec) * M);
 constexpr size_t kOffScan = align256(kOffQcount + sizeof(int64_t) * (M + 1));
 constexpr size_t kOffLong = align256(kOffScan + sizeof(int64_t) * (M / 8192 + 2));
@@ -175,6 +176,9 @@ extern "C" egm_status egm_match_pair_static(const egm_pair *P, const egm_out *ou
     L.val_c = k + 5 * nr;
     L.rec = reinterpret_cast<float4 *>(base + kOffRec);
     L.tab = reinterpret_cast<uint32_t *>(base + kOffTab);
+    L.ntab = kTabCap;
+    L.curs = reinterpret_cast<uint32_t *>(base + kOffCurs);
+    L.prep_done = reinterpret_cast<uint32_t *>(base + kOffSmall) + 40;
     L.qrec = reinterpret_cast<QueryRec *>(base + kOffQrec);
     L.status = reinterpret_cast<uint32_t *>(base + kOffSmall);
     L.counters = nullptr;
@@ -197,8 +201,7 @@ extern "C" egm_status egm_match_pair_static(const egm_pair *P, const egm_out *ou
 
     EGM_STATIC_TRY(launch_geometry(L, st));
     EGM_STATIC_TRY(launch_prep(L, st));
-    EGM_STATIC_TRY(launch_sort(L, P->n, st));
-    EGM_STATIC_TRY(launch_post_sort(L, st));
+    EGM_STATIC_TRY(launch_sort(L, st));
     if (csr) {
         uint32_t *long_list = reinterpret_cast<uint32_t *>(base + kOffLong);
         uint32_t *long_count = reinterpret_cast<uint32_t *>(base + kOffSmall) + 16;

@@ -235,3 +235,23 @@ def test_counters_and_unsupported_inputs(mt):
     # the automatic choice falls back to the plain form for the same inputs
     o = mt.match(*args, csr=True)
     assert int(o["cand_total"].item()) == cands[FORM_PLAIN]
+
+
+def test_every_tile_shape_and_the_tuner(mt):
+    """Each band tile shape gives the same outputs; the tuner's pick (first
+    call of a size class) does too, and so does a call of a class already tuned."""
+    scenes = synth.config3(seed=5, npairs=12, scale=0.15)
+    items = [mt.to_device(s) for s in scenes]
+    mt.set_params(form=FORM_PLAIN)
+    ref = {k: v.cpu().numpy() for k, v in mt.match_batch(items).items()}
+    try:
+        for tile in (1, 2, 0, 0):
+            mt.set_params(form=FORM_BANDED, band_tile=tile)
+            got = {k: v.cpu().numpy() for k, v in mt.match_batch(items).items()}
+            for k in KEYS:
+                assert np.array_equal(got[k], ref[k]), (tile, k)
+        from paper_2603_18401_gb300 import EgmError
+        with pytest.raises(EgmError):
+            mt.set_params(band_tile=99)
+    finally:
+        mt.set_params(form=FORM_AUTO, band_tile=0)
