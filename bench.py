@@ -5,9 +5,15 @@ Workload (one GPU): the high-resolution single-pair configuration -- nine
 image pairs of 6048x4032 px with 16384 keypoints per image (70% true
 projections), epipole inside / far outside / at infinity, eps in {1, 2, 4} px,
 128-d uint8 descriptors.  One step matches all nine pairs, one pair per
-egm_match_pair call (the plain one-pair form).  Inputs are resident in HBM
+egm_match_pair call, in the library's automatic form (the banded tensor-core
+form for these descriptors; --form picks one).  Inputs are resident in HBM
 before the timed region; L2 is flushed (a 256 MiB write) before every step
 and the flush is outside the CUDA-event-timed interval.
+
+Beside the headline: the same single-pair step in the plain CUDA-core form,
+the batched configuration (256 pairs, one CUDA-graph launch per step) in both
+forms, the end-to-end rate through host buffers, per-stage times, and the
+roofline of the dominant kernel.
 
 --impl reference times the CPU oracle (the plain brute-force definition) on
 the host cores instead: the paper publishes no code or GPU number, so the
@@ -53,6 +59,8 @@ def parse():
     ap.add_argument("--batch-pairs", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--form", choices=["auto", "plain", "banded"], default="auto")
+    ap.add_argument("--compare-steps", type=int, default=200)
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-form comparison legs")
     return ap.parse_args()
 
 
@@ -202,23 +210,27 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ ours
-def stab_traffic(cur_hash):
-    """DRAM bytes per stab launch from the committed ncu summary, if it was
-    taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "stab_kernel_config2.json")
+KERNEL_SOURCES = {"band_kernel": ("band.cu", "tc.cuh", "egm_internal.cuh"),
+                  "stab_kernel": ("stab.cu", "egm_internal.cuh")}
+
+
+def source_hash(kernel):
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2603_18401_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def kernel_profile(kernel):
+    """Counters of the committed ncu summary of `kernel` on this workload, if
+    it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_config2.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    return d.get("dram_bytes_per_launch") if d.get("source_sha256") == cur_hash else None
-
-
-def source_hash():
-    h = hashlib.sha256()
-    for name in ("stab.cu", "egm_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2603_18401_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()
+    return d if d.get("source_sha256") == source_hash(kernel) else None
 
 
 def run_ours(args):
@@ -292,24 +304,58 @@ def run_ours(args):
     q_per_step = sum(s.m for s in scs)
     value = world * q_per_step * args.steps / (ms * 1e-3)
 
-    # dominant kernel: stabbing + exact test + descriptors + top-2 + ratio
+    # dominant kernel: the matching kernel of the form in use ("stab" stage)
     calls = max(tm["calls"], 1)
     stage_ms = {k[:-3]: tm[k] / calls for k in tm if k.endswith("_ms")}
     dom = max(stage_ms, key=stage_ms.get)
+    # the automatic form runs the plain form on single pairs (128 tiles, fewer
+    # than two per SM) and the banded form on the batch
+    banded = args.form == "banded"
+    kernel = "band_kernel" if banded else "stab_kernel"
     row = scs[0].desc1.shape[1]
-    # algorithmic bytes of one stab launch: every query's line record (32 B),
-    # descriptor and result (17 B) once; every reference's sorted record
-    # (16 B), key (4 B) and descriptor once.
-    stab_bytes = sum(s.m * (32 + row + 17) + s.n * (20 + row) for s in scs) / len(scs)
-    stab_s = stage_ms["stab"] * 1e-3
+    if banded:
+        # every query's packed operand row (256 B), sorted record (48 B) and
+        # result (17 B) once; every reference's packed row (256 B), record
+        # (16 B) and norm (4 B) once
+        kbytes = sum(s.m * (256 + 48 + 17) + s.n * (256 + 16 + 4) for s in scs) / len(scs)
+    else:
+        # every query's line record (48 B), descriptor and result (17 B) once;
+        # every reference's record (16 B) and descriptor once
+        kbytes = sum(s.m * (48 + row + 17) + s.n * (16 + row) for s in scs) / len(scs)
+    k_s = stage_ms["stab"] * 1e-3
     peak, peak_kind = measured_peaks()
-    achieved = stab_bytes / stab_s / 1e9
-    roofline = {"kernel": "stab_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+    achieved = kbytes / k_s / 1e9
+    prof = kernel_profile(kernel)
+    roofline = {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": stab_traffic(source_hash()), "avg_launch_us": stage_ms["stab"] * 1e3,
-                "algorithmic_bytes_per_launch": stab_bytes,
+                "traffic": prof.get("dram_bytes_per_launch") if prof else None,
+                "tensor_pipe_active_pct": prof.get("tensor_pipe_active_pct") if prof else None,
+                "avg_launch_us": stage_ms["stab"] * 1e3, "algorithmic_bytes_per_launch": kbytes,
                 "stage_us_per_pair": {k: round(v * 1e3, 2) for k, v in stage_ms.items()},
                 "dominant_stage": dom}
+
+    # the same step in the other form, for comparison
+    other_form = None
+    if not args.no_compare:
+        other = 2 if not banded else 1
+        mt.set_params(form=other)
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.compare_steps)]
+        for k in range(args.compare_steps):
+            flush.zero_()
+            pe[k][0].record(stream)
+            step()
+            pe[k][1].record(stream)
+        torch.cuda.synchronize()
+        pms = max_over_ranks(sum(a.elapsed_time(b) for a, b in pe), world, local)
+        other_form = {"value": world * q_per_step * args.compare_steps / (pms * 1e-3), "unit": "queries/s",
+                      "ms_per_step": pms / args.compare_steps, "steps": args.compare_steps,
+                      "form": ("banded: tcgen05 tiles of 128 queries" if other == 2
+                               else "plain: windowed stabbing, CUDA-core descriptor distances")}
+        mt.set_params(form={"auto": 0, "plain": 1, "banded": 2}[args.form])
 
     # end to end: host (pinned) buffers through egm_match_pair_host, copies inside
     host = []
@@ -373,25 +419,39 @@ def run_ours(args):
         bsc = _synth.config3(seed=0, npairs=args.batch_pairs)
         bitems = [mt.to_device(s) for s in bsc]
         bM = sum(s.m for s in bsc)
-        bout = mt._alloc_out(bM, False, 0)
-        graph = mt.graph_create(bitems, bout)
+
+        def time_graph(form):
+            mt.set_params(form=form)
+            bout = mt._alloc_out(bM, False, 0)
+            graph = mt.graph_create(bitems, bout)
+            for _ in range(3):
+                if graph.launch() != 0:
+                    raise EgmError(mt.sync(), "batched warm-up")
+            torch.cuda.synchronize()
+            bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.batch_steps)]
+            barrier(world)
+            torch.cuda.synchronize()
+            for k in range(args.batch_steps):
+                bev[k][0].record(stream)
+                graph.launch()
+                bev[k][1].record(stream)
+            torch.cuda.synchronize()
+            st = mt.sync()
+            if st != 0:
+                raise EgmError(st, "batched timed region")
+            graph.close()
+            return max_over_ranks(sum(a.elapsed_time(b) for a, b in bev), world, local) / args.batch_steps
+
+        bform = {"auto": 0, "plain": 1, "banded": 2}[args.form]
+        bms = time_graph(bform)
+        # per-stage split of one batch, outside the timed region
+        mt.set_timing(True)
         for _ in range(3):
-            if graph.launch() != 0:
-                raise EgmError(mt.sync(), "batched warm-up")
-        torch.cuda.synchronize()
-        bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.batch_steps)]
-        barrier(world)
-        torch.cuda.synchronize()
-        for k in range(args.batch_steps):
-            bev[k][0].record(stream)
-            graph.launch()
-            bev[k][1].record(stream)
-        torch.cuda.synchronize()
-        st = mt.sync()
-        if st != 0:
-            raise EgmError(st, "batched timed region")
-        bms = max_over_ranks(sum(a.elapsed_time(b) for a, b in bev), world, local) / args.batch_steps
+            mt.match_batch(bitems)
+        bt = mt.timing()
+        mt.set_timing(False)
+        bstage = {k[:-3]: round(bt[k] / max(bt["calls"], 1), 4) for k in bt if k.endswith("_ms")}
         in_bytes = sum(s.xy1.nbytes + s.xy2.nbytes + s.desc1.nbytes + s.desc2.nbytes for s in bsc)
         batched = {"workload": f"{len(bsc)} pairs 6048x4032, per-image counts log-uniform in [1024, 32768], "
                                "random poses (rotation up to 30 deg), u8 L2 on even / 256-bit binary on odd pairs",
@@ -399,22 +459,30 @@ def run_ours(args):
                    "queries_per_s": world * bM / (bms * 1e-3), "ms_per_step": bms, "steps": args.batch_steps,
                    "queries_per_step": bM, "refs_per_step": sum(s.n for s in bsc),
                    "input_bytes": int(in_bytes), "l2": "inputs larger than L2 (129 MB)",
-                   "form": "egm_graph_launch (one CUDA graph per step)"}
-        graph.close()
+                   "form": f"{args.form} (egm_graph_launch, one CUDA graph per step)",
+                   "stage_ms": bstage}
+        if bform != 1 and not args.no_compare:
+            pms = time_graph(1)
+            batched["plain_form"] = {"pairs_per_s": world * len(bsc) / (pms * 1e-3), "ms_per_step": pms}
+        mt.set_params(form=bform)
 
-    launches_per_pair = 5
+    # kernels per match call: geometry, prep, bucket count, bucket scan, and
+    # either the stab kernel or the query sort, pack and band kernels
+    launches_per_pair = 7 if banded else 5
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64/f32 geometry, u8 descriptors (int32 distances)", "data": "synthetic",
+        "dtype": ("f64/f32 geometry, u8 descriptors as bf16 on tensor cores (exact integer distances)" if banded
+                  else "f64/f32 geometry, u8 descriptors (int32 distances)"), "data": "synthetic",
         "config": {"workload": WORKLOAD, "pairs_per_step": len(scs), "queries_per_step": q_per_step,
-                   "form": "plain one-pair (egm_match_pair)", "l2": "flushed before every step (256 MiB write)",
+                   "form": f"{args.form} one-pair (egm_match_pair)", "l2": "flushed before every step (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "api": "egm_match_pair_host", "steps": args.e2e_steps},
         "roofline": roofline,
         "batched": batched,
+        "other_form_one_pair": other_form,
         "clocks": clk,
         "gpu_launches": launches_per_pair * len(scs) * args.steps,
     }

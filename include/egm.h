@@ -141,7 +141,8 @@ typedef struct egm_out {
 
 /* Matching forms. */
 enum {
-    EGM_FORM_AUTO = 0,     /* library choice */
+    EGM_FORM_AUTO = 0,     /* library choice: banded for batches with more than two
+                              128-query tiles per SM, plain otherwise */
     EGM_FORM_PLAIN = 1,    /* windowed stabbing + CUDA-core descriptor distances */
     EGM_FORM_BANDED = 2    /* angle-banded tiles, descriptor dot products on tensor cores */
 };

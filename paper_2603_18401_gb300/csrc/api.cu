@@ -224,10 +224,14 @@ size_t offs_entries(int npairs, int64_t nq) {
     return 3 * (size_t)(npairs + 1) + (size_t)(nq / band_tile_queries() + npairs + 2) / 2 + 1;
 }
 
-// The banded form runs when it is requested or left to the library, every
-// pair fits it, and no candidate lists are asked for.
-egm_status choose_band(const Plan &pl, const egm_params &prm, bool csr, bool &band) {
-    band = prm.form != EGM_FORM_PLAIN && pl.band_ok && !csr;
+// The banded form runs when every pair fits it, no candidate lists are asked
+// for, and it is requested -- or left to the library and the call has more
+// than two tiles per SM.  With fewer, every CTA of the band kernel takes one
+// latency-bound tile and the plain form (no query sort, no packing) finishes
+// first; with more, the banded form's throughput wins.
+egm_status choose_band(const Plan &pl, const egm_params &prm, bool csr, int sms, bool &band) {
+    band = pl.band_ok && !csr &&
+           (prm.form == EGM_FORM_BANDED || (prm.form == EGM_FORM_AUTO && pl.ntiles > 2 * (int64_t)sms));
     if (prm.form == EGM_FORM_BANDED && !band) return EGM_ERR_UNIMPLEMENTED;
     return EGM_OK;
 }
@@ -523,7 +527,7 @@ egm_status run_batch(egm_ctx *c, const egm_pair *pairs, int npairs, const egm_ou
     if ((s = check_out(pairs, npairs, out)) != EGM_OK) return s;
     const bool csr = out->cand_offsets != nullptr;
     bool band = false;
-    if ((s = choose_band(pl, c->params, csr, band)) != EGM_OK) return s;
+    if ((s = choose_band(pl, c->params, csr, c->sms, band)) != EGM_OK) return s;
     EGM_TRY(cudaSetDevice(c->device));
     if (band) EGM_TRY(ensure_side(c));
     EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, npairs, band));
@@ -783,7 +787,7 @@ egm_status egm_graph_create(egm_ctx *c, const egm_pair *pairs, int32_t npairs, c
     if ((s = check_out(pairs, npairs, out)) != EGM_OK) return s;
     const bool csr = out->cand_offsets != nullptr;
     bool band = false;
-    if ((s = choose_band(pl, c->params, csr, band)) != EGM_OK) return s;
+    if ((s = choose_band(pl, c->params, csr, c->sms, band)) != EGM_OK) return s;
     EGM_TRY(cudaSetDevice(c->device));
     egm_graph *g = new (std::nothrow) egm_graph();
     if (!g) return EGM_ERR_NOMEM;
