@@ -62,12 +62,16 @@ struct egm_ctx {
     Scratch sc;
     DevBuf stage;  // host-path staging of inputs and outputs
     // pinned host memory for the pair table and the status word
-    void *h_table = nullptr;
-    size_t h_table_bytes = 0;
+    // pinned staging slots of the pair-table uploads, used round-robin: the
+    // host waits only when a slot's previous upload is still in flight
+    static constexpr int kSlots = 8;
+    void *h_table[kSlots] = {};
+    size_t h_table_bytes[kSlots] = {};
+    cudaEvent_t slot_ev[kSlots] = {};
+    bool slot_pending[kSlots] = {};
+    int slot = 0;
     uint32_t *h_status = nullptr;
     unsigned long long *h_counters = nullptr;
-    cudaEvent_t table_ev = nullptr;
-    bool table_ev_pending = false;
     // per-stage timing: kStages + 1 events per timed call
     bool timing_on = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -152,6 +156,7 @@ struct Plan {
     int64_t nq = 0, nr = 0, ntab = 0, ntiles = 0;
     int max_n = 0;
     bool band_ok = false;           // every pair fits the banded form
+    bool has_float = false;         // some pair has float descriptors
 };
 
 egm_status make_plan(const egm_pair *pairs, int npairs, Plan &pl) {
@@ -201,6 +206,7 @@ egm_status make_plan(const egm_pair *pairs, int npairs, Plan &pl) {
         if (p < npairs) {
             pl.ntiles += (pairs[p].m + tm - 1) / tm;
             pl.band_ok = pl.band_ok && has_desc(pairs + p) && band_supported(pairs[p].kind, pairs[p].dim);
+            pl.has_float = pl.has_float || (has_desc(pairs + p) && pairs[p].kind == EGM_DESC_F32_L2);
         }
     }
     // Tiles are handed out costliest first (longest-processing-time order): a
@@ -250,7 +256,7 @@ struct BandLayout {
         qbkt = descB + align256(rb * (size_t)std::max<int64_t>(nr, 1));
         qsrt = qbkt + align256(sizeof(uint16_t) * (size_t)std::max<int64_t>(nq, 1));
         rnorm = qsrt + align256(sizeof(QueryRec) * (size_t)std::max<int64_t>(nq, 1));
-        total = rnorm + align256(sizeof(float) * (size_t)(nr + 64));
+        total = rnorm + align256(sizeof(float2) * (size_t)(nr + 64));
     }
 };
 
@@ -318,15 +324,17 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
         L.descB = b + bl.descB;
         L.qbkt = reinterpret_cast<uint16_t *>(b + bl.qbkt);
         L.qsrt = reinterpret_cast<QueryRec *>(b + bl.qsrt);
-        L.rnorm = reinterpret_cast<float *>(b + bl.rnorm);
+        L.rnorm = reinterpret_cast<float2 *>(b + bl.rnorm);
         L.tile_offs = as<int64_t>(c->offs) + 2 * (npairs + 1);
         L.tile_seq = reinterpret_cast<const int32_t *>(as<int64_t>(c->offs) + 3 * (npairs + 1));
         L.work = as<uint32_t>(c->small) + 32;
         L.ntiles = pl.ntiles;
     }
     L.kind = pl.pd.empty() ? -1 : pl.pd[0].kind;
-    for (const PairDesc &d : pl.pd)
+    for (const PairDesc &d : pl.pd) {
         if (d.kind != L.kind) L.kind = -1;
+        if (d.row_bytes > 0) L.kinds |= 1u << d.kind;
+    }
     if (out) {
         L.best = out->best;
         L.second = out->second;
@@ -341,33 +349,38 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
     return L;
 }
 
-// Upload the pair table and offsets through pinned memory.  The staging area
-// is reused only after the previous upload has been consumed.
+// Upload the pair table and offsets through a pinned staging slot.  The
+// device copy is ordered on the stream after the previous call's kernels; the
+// host reuses a slot only once its previous upload has been consumed.
 cudaError_t upload_plan(egm_ctx *c, const Plan &pl, int npairs) {
     const size_t tb = sizeof(PairDesc) * npairs, ob = sizeof(int64_t) * pl.offs.size();
-    if (c->table_ev_pending) {
-        cudaError_t e = cudaEventSynchronize(c->table_ev);
-        if (e != cudaSuccess) return e;
-        c->table_ev_pending = false;
+    const int k = c->slot;
+    c->slot = (k + 1) % egm_ctx::kSlots;
+    cudaError_t e;
+    if (!c->slot_ev[k] && (e = cudaEventCreateWithFlags(&c->slot_ev[k], cudaEventDisableTiming)) != cudaSuccess)
+        return e;
+    if (c->slot_pending[k]) {
+        if ((e = cudaEventSynchronize(c->slot_ev[k])) != cudaSuccess) return e;
+        c->slot_pending[k] = false;
     }
-    if (tb + ob > c->h_table_bytes) {
-        if (c->h_table) cudaFreeHost(c->h_table);
-        c->h_table = nullptr;
-        size_t want = (tb + ob) * 2 + 4096;
-        cudaError_t e = cudaMallocHost(&c->h_table, want);
-        if (e != cudaSuccess) { c->h_table_bytes = 0; return e; }
-        c->h_table_bytes = want;
+    if (tb + ob > c->h_table_bytes[k]) {
+        if (c->h_table[k]) cudaFreeHost(c->h_table[k]);
+        c->h_table[k] = nullptr;
+        const size_t want = (tb + ob) * 2 + 4096;
+        if ((e = cudaMallocHost(&c->h_table[k], want)) != cudaSuccess) {
+            c->h_table_bytes[k] = 0;
+            return e;
+        }
+        c->h_table_bytes[k] = want;
     }
-    unsigned char *h = static_cast<unsigned char *>(c->h_table);
+    unsigned char *h = static_cast<unsigned char *>(c->h_table[k]);
     memcpy(h, pl.pd.data(), tb);
     memcpy(h + tb, pl.offs.data(), ob);
-    cudaError_t e = cudaMemcpyAsync(c->sc.pairs.ptr, h, tb, cudaMemcpyHostToDevice, c->stream);
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(c->sc.offs.ptr, h + tb, ob, cudaMemcpyHostToDevice, c->stream);
-    if (e != cudaSuccess) return e;
-    e = cudaEventRecord(c->table_ev, c->stream);
-    if (e != cudaSuccess) return e;
-    c->table_ev_pending = true;
+    if ((e = cudaMemcpyAsync(c->sc.pairs.ptr, h, tb, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(c->sc.offs.ptr, h + tb, ob, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+        return e;
+    if ((e = cudaEventRecord(c->slot_ev[k], c->stream)) != cudaSuccess) return e;
+    c->slot_pending[k] = true;
     return cudaSuccess;
 }
 
@@ -501,7 +514,8 @@ cudaError_t tune_band(egm_ctx *c, const Launch &L, cudaStream_t st, int &best) {
 // per SM (every CTA takes one tile, latency decides) the shape with the
 // fewest chunks; otherwise the tuner's choice for the size class, or -1 (to
 // be tuned).
-int band_shape_for(egm_ctx *c, int64_t ntiles) {
+int band_shape_for(egm_ctx *c, int64_t ntiles, bool has_float) {
+    if (has_float) return 0;  // float pairs: one shape (see launch_band)
     if (c->params.band_tile > 0) return c->params.band_tile - 1;
     if (ntiles <= 2 * (int64_t)c->sms) return 0;
     auto it = c->band_shape.find(tile_class(ntiles));
@@ -536,7 +550,7 @@ egm_status run_batch(egm_ctx *c, const egm_pair *pairs, int npairs, const egm_ou
     cudaStream_t st = c->stream;
     if (sync) EGM_TRY(cudaMemsetAsync(L.status, 0, sizeof(uint32_t), st));
     if (c->counters_on) EGM_TRY(cudaMemsetAsync(c->sc.counters.ptr, 0, 8 * sizeof(unsigned long long), st));
-    const int shape = band ? band_shape_for(c, pl.ntiles) : 0;
+    const int shape = band ? band_shape_for(c, pl.ntiles, pl.has_float) : 0;
     if (band && shape < 0) {
         // first batch of this size class: everything but the band kernel, then the tuner
         EGM_TRY(enqueue_pipeline(L, c->sc, csr, pl.max_n, st, nullptr, band, c->sms, c, -1));
@@ -578,7 +592,6 @@ egm_status egm_create(egm_ctx **out, int device, void *stream) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_status, 64);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_counters, 8 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->table_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = grow(c->sc.small, 256);
     if (e == cudaSuccess) e = cudaMemset(c->sc.small.ptr, 0, 256);
     if (e != cudaSuccess) {
@@ -602,10 +615,12 @@ egm_status egm_destroy(egm_ctx *c) {
     if (c->join_ev) cudaEventDestroy(c->join_ev);
     c->sc.release();
     if (c->stage.ptr) cudaFree(c->stage.ptr);
-    if (c->h_table) cudaFreeHost(c->h_table);
+    for (int k = 0; k < egm_ctx::kSlots; k++) {
+        if (c->h_table[k]) cudaFreeHost(c->h_table[k]);
+        if (c->slot_ev[k]) cudaEventDestroy(c->slot_ev[k]);
+    }
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->h_counters) cudaFreeHost(c->h_counters);
-    if (c->table_ev) cudaEventDestroy(c->table_ev);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
     return EGM_OK;
@@ -803,7 +818,7 @@ egm_status egm_graph_create(egm_ctx *c, const egm_pair *pairs, int32_t npairs, c
     if (e == cudaSuccess)
         e = cudaMemcpy(g->sc.offs.ptr, h.data() + sizeof(PairDesc) * npairs, ob, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(g->sc.small.ptr, 0, 256);
-    int shape = band ? band_shape_for(c, pl.ntiles) : 0;
+    int shape = band ? band_shape_for(c, pl.ntiles, pl.has_float) : 0;
     if (e == cudaSuccess && band && shape < 0) {
         // tune on the graph's own scratch before capturing
         const Launch T = make_launch(g->sc, false, c->params, pl, npairs, out, band);

@@ -15,6 +15,8 @@
 //                      as 256-byte tensor-core operands, with their norms:
 //                        u8 (128 values)  -> BF16, exact (integers < 2^8)
 //                        binary (256 bit) -> E4M3 0 / 1 per bit, exact
+//                        float (128 FP32) -> BF16 (nearest), with the norm of
+//                          the rounded row and the rounding error |x - bf16(x)|
 //   band_kernel        persistent; one tile of 128 sorted queries at a time.
 //                      Warps 0-3 (one thread per query) build the tile's band
 //                      from the hull of their windows; warp 4 issues TMA loads
@@ -29,6 +31,7 @@
 //                        Hamming = |q| + |r| - 2 q.r
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "egm_internal.cuh"
@@ -138,6 +141,8 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
         const bool valid = g0 < rows;
         const bool is_ref = g0 < L.nr;
         uint32_t nrm = 0, qi = 0;
+        float fnrm = 0.0f, ferr = 0.0f;  // float rows: squared norm of the BF16 row, squared rounding error
+        bool isf = false;
         uint4 o0 = make_uint4(0, 0, 0, 0), o1 = o0, qr = o0;
         uint8_t *dst = nullptr;
         if (valid) {
@@ -169,6 +174,27 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
                 }
                 o0 = make_uint4(out[0], out[1], out[2], out[3]);
                 o1 = make_uint4(out[4], out[5], out[6], out[7]);
+            } else if (P.kind == EGM_DESC_F32_L2) {
+                // 16 values per thread: 64 bytes in, 32 bytes of BF16 out
+                isf = true;
+                uint32_t out[8];
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const float4 v = __ldg(reinterpret_cast<const float4 *>(src) + 4 * part + c);
+                    const float xs[4] = {v.x, v.y, v.z, v.w};
+                    float b[4];
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        b[k] = __bfloat162float(__float2bfloat16_rn(xs[k]));
+                        fnrm = fmaf(b[k], b[k], fnrm);
+                        const float d = xs[k] - b[k];  // exact: b is x rounded to 8 bits
+                        ferr = fmaf(d, d, ferr);
+                    }
+                    out[2 * c] = (__float_as_uint(b[0]) >> 16) | (__float_as_uint(b[1]) & 0xffff0000u);
+                    out[2 * c + 1] = (__float_as_uint(b[2]) >> 16) | (__float_as_uint(b[3]) & 0xffff0000u);
+                }
+                o0 = make_uint4(out[0], out[1], out[2], out[3]);
+                o1 = make_uint4(out[4], out[5], out[6], out[7]);
             } else {
                 const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(src) + part);
                 nrm = __popc(w);
@@ -179,17 +205,26 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
             }
         }
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o, 8);
+        for (int o = 4; o > 0; o >>= 1) {
+            nrm += __shfl_xor_sync(0xffffffffu, nrm, o, 8);
+            fnrm += __shfl_xor_sync(0xffffffffu, fnrm, o, 8);
+            ferr += __shfl_xor_sync(0xffffffffu, ferr, o, 8);
+        }
+        // norm of the operand row; for float rows also |x - bf16(x)|, rounded up
+        const float norm = isf ? fnrm : (float)nrm;
+        const float err = isf ? sqrtf(ferr) * 1.0001f + 1e-30f : 0.0f;
         if (valid) {
             reinterpret_cast<uint4 *>(dst)[2 * part] = o0;
             reinterpret_cast<uint4 *>(dst)[2 * part + 1] = o1;
             if (is_ref) {
-                if (part == 0) L.rnorm[g0] = (float)nrm;
+                if (part == 0) L.rnorm[g0] = make_float2(norm, err);
             } else if (part < 3) {
-                // sorted query record; the padding carries the query index and norm
+                // sorted query record; the padding carries the query index and the
+                // norm, the pair field (the tile knows its pair) the rounding error
                 if (part == 2) {
+                    qr.y = __float_as_uint(err);
                     qr.z = qi;
-                    qr.w = __float_as_uint((float)nrm);
+                    qr.w = __float_as_uint(norm);
                 }
                 reinterpret_cast<uint4 *>(L.qsrt + (g0 - L.nr))[part] = qr;
             }
@@ -201,7 +236,7 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
 constexpr int kTM = 128;                 // queries per tile (MMA M, TMEM lanes)
 constexpr int kBoxR = 32;                // reference rows per TMA box (N per box)
 constexpr int kBandThreads = kTM + 32;   // four epilogue warps and the control warp
-constexpr int kRnRow = kBoxR + 4;        // norms copied from a 16-byte aligned start
+constexpr int kRnRow = kBoxR + 2;        // norms (float2) copied from a 16-byte aligned start
 // Tile shapes (chosen per workload by the tuner): CB boxes per MMA chunk
 // (N = 32 CB) and CPS resident CTAs per SM, which size shared memory and TMEM.
 //   0: CB 4, CPS 2   few tiles per SM (single pairs): fewer, larger chunks
@@ -219,7 +254,7 @@ struct BandSmem {
     uint8_t A[2][kTM * 128];      // query tile, K halves (1024-byte aligned)
     uint8_t B[2][2][kCN * 128];   // band chunk: stage, K half
     float4 rec[2][kCN];           // (x - cx, y - cy, eps, index) of each column
-    float rn[2][CB][kRnRow];      // norms of each box's rows
+    float2 rn[2][CB][kRnRow];     // (norm, rounding error) of each box's rows
     // fullB: a stage's operand rows landed; sfree: the MMA that read them is
     // done; fullR: a stage's records and norms landed; done: an accumulator is
     // ready; tfree: the epilogue has read it and the stage's records
@@ -281,6 +316,107 @@ __device__ __forceinline__ void copy16(void *dst, const void *src, int bytes, in
     for (int k = lane; k < bytes / 16; k += 32) d4[k] = __ldg(s4 + k);
 }
 
+// ---- float descriptors: BF16 tensor-core pass, FP32 rerank
+//
+// For rows q, r with BF16 roundings q~, r~ (|q - q~| <= eq, |r - r~| <= er) the
+// squared distances d = |q - r|^2 and d~ = |q~ - r~|^2 satisfy
+// |d - d~| <= 2 sqrt(d~) D + D^2 with D = eq + er.  d~ is evaluated as
+// |q~|^2 + |r~|^2 - 2 q~.r~ in FP32 (products of BF16 values are exact; the
+// sums of 128 terms are within 3e-5 (|q~|^2 + |r~|^2), a wide allowance for the
+// tensor core's accumulation), and the rerank's FP32 evaluation of d is within
+// 1e-4 relative of d.  A candidate whose lower bound exceeds the second
+// smallest upper bound cannot be among the best two.
+constexpr int kFBuf = 8;  // candidates kept per query for the rerank
+
+__device__ __forceinline__ void float_bounds(float dt, float qn, float rn, float eq, float er, float &lo, float &hi) {
+    const float efp = 3.0e-5f * (qn + rn) + 1e-30f;
+    const float D = eq + er;
+    const float sd = sqrtf(fmaxf(dt + efp, 0.0f));
+    const float E = fmaf(2.0f * sd, D, fmaf(D, D, efp));
+    hi = (dt + E) * 1.0001f + 1e-30f;
+    lo = (dt - E) - 1.0e-4f * fabsf(dt + E) - 1e-30f;
+}
+
+// The candidates of one query that can still be among its best two: lower
+// bounds (L, +inf when free) and indices, the two smallest upper bounds seen,
+// and the smallest lower bound ever dropped for lack of room.
+struct FBuf {
+    float U1, U2, drop;
+    float L[kFBuf];
+    uint32_t J[kFBuf];
+    __device__ __forceinline__ void init() {
+        U1 = U2 = drop = INFINITY;
+#pragma unroll
+        for (int t = 0; t < kFBuf; t++) {
+            L[t] = INFINITY;
+            J[t] = 0u;
+        }
+    }
+    __device__ __forceinline__ void insert(float lo, float up, uint32_t j) {
+        if (up < U1) {
+            U2 = U1;
+            U1 = up;
+        } else if (up < U2) {
+            U2 = up;
+        }
+        if (!(lo <= U2)) return;
+        int slot = -1, mxs = 0;
+        float mx = -INFINITY;
+#pragma unroll
+        for (int t = 0; t < kFBuf; t++) {
+            if (L[t] > U2) L[t] = INFINITY;  // out for good: U2 only decreases
+            if (slot < 0 && L[t] == INFINITY) slot = t;
+            if (L[t] > mx) {
+                mx = L[t];
+                mxs = t;
+            }
+        }
+        if (slot < 0) {  // full: keep the smaller lower bounds
+            if (lo < mx) {
+                drop = fminf(drop, mx);
+                slot = mxs;
+            } else {
+                drop = fminf(drop, lo);
+                return;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kFBuf; t++)
+            if (t == slot) {
+                L[t] = lo;
+                J[t] = j;
+            }
+    }
+    // every reference that can be among the best two is in the buffer
+    __device__ __forceinline__ bool complete() const { return drop > U2; }
+};
+
+// FP32 squared distance of the query row (this lane's 16-byte chunk in qv)
+// and the reference row at r, in the plain kernel's order: four fused
+// multiply-adds per lane, then an XOR butterfly over the warp.
+__device__ __forceinline__ float coop_dist(const float4 &qv, const uint8_t *r, int lane) {
+    const float4 rv = __ldg(reinterpret_cast<const float4 *>(r) + lane);
+    float acc = 0.0f, d;
+    d = qv.x - rv.x; acc = fmaf(d, d, acc);
+    d = qv.y - rv.y; acc = fmaf(d, d, acc);
+    d = qv.z - rv.z; acc = fmaf(d, d, acc);
+    d = qv.w - rv.w; acc = fmaf(d, d, acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+// Eq. 3 / Eq. 4 in FP32 with the rigorous bound: 1 member, 0 not, 2 inconclusive.
+__device__ __forceinline__ int member32(float A, float B, float C, float E0, float E1, const float4 &rc) {
+    const float x = rc.x, y = rc.y, e = rc.z;
+    const float d = fabsf(fmaf(A, x, fmaf(B, y, C)));
+    const float Sm = fmaf(fabsf(A), fabsf(x), fmaf(fabsf(B), fabsf(y), fabsf(C)));
+    const float lerr = fmaf(E1, fabsf(x) + fabsf(y) + 2.0f * e, E0);
+    const float bound = fmaf(9.6e-7f, Sm, fmaf(1.2e-7f, e, lerr + 1e-9f));
+    if (d <= e - bound) return 1;
+    return d > e + bound ? 0 : 2;
+}
+
 __device__ __forceinline__ void top2(unsigned long long key, unsigned long long &b1, unsigned long long &b2) {
     if (key < b1) {
         b2 = b1;
@@ -290,7 +426,9 @@ __device__ __forceinline__ void top2(unsigned long long key, unsigned long long 
     }
 }
 
-template <int CB, int CPS>
+// FLT: float descriptor pairs may occur (compiled out otherwise: the rerank
+// state costs registers).
+template <int CB, int CPS, bool FLT>
 __global__ void __launch_bounds__(kBandThreads, CPS)
     band_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Launch L) {
     using Shape = BandShape<CB, CPS>;
@@ -363,6 +501,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         }
         const uint32_t qi = r.pad[0];
         const float qn = __uint_as_float(r.pad[1]);
+        const float qerr = __uint_as_float((uint32_t)r.pair);  // float rows: |q - bf16(q)|
         if (ctl) {
             tc::mbar_arrive_expect_tx(&S.afull, 2 * kTM * 128);
             tc::tma_load_2d(S.A[0], &tmA, 0, (int32_t)(q_off + t0), &S.afull);
@@ -504,14 +643,14 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             auto issueR = [&](int c) {
                 const uint32_t st = (seq + (uint32_t)c) & 1u;
                 const int nb = min(kCB, nbox - c * kCB);
-                tc::mbar_arrive_expect_tx(&S.fullR[st], (uint32_t)nb * (kBoxR * 16 + kRnRow * 4));
+                tc::mbar_arrive_expect_tx(&S.fullR[st], (uint32_t)nb * (kBoxR * 16 + kRnRow * 8));
                 for (int bb = 0; bb < nb; bb++) {
                     uint32_t pos, len;
                     int li;
                     curR.next(S, pos, len, li);
                     const int64_t row = P.r_off + pos;
                     tc::bulk_load(&S.rec[st][bb * kBoxR], L.rec + row, kBoxR * 16, &S.fullR[st]);
-                    tc::bulk_load(&S.rn[st][bb][0], L.rnorm + (row & ~(int64_t)3), kRnRow * 4, &S.fullR[st]);
+                    tc::bulk_load(&S.rn[st][bb][0], L.rnorm + (row & ~(int64_t)1), kRnRow * 8, &S.fullR[st]);
                 }
             };
             for (int c = 0; c < nchunk && c < 2; c++) {
@@ -552,6 +691,9 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
 
         // ---- epilogue: tests and best two over this warp's columns
         unsigned long long b1 = ~0ull, b2 = ~0ull;
+        const bool isf = FLT && P.kind == EGM_DESC_F32_L2;
+        FBuf fb;
+        fb.init();
         if (warp < 4 && nchunk > 0) {
             BoxCursor cur;
             const bool exact_only = (r.flags & kQExactOnly) != 0;
@@ -574,7 +716,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                     const int y0 = (int)max(pos, w1.x) - (int)pos;
                     const int y1 = (int)min(pos + len, w1.x + w1.y) - (int)pos;
                     if (x1 <= x0 && y1 <= y0) continue;
-                    const float *rnb = &S.rn[st][bb][(P.r_off + pos) & 3];
+                    const float2 *rnb = &S.rn[st][bb][(P.r_off + pos) & 1];
                     const float4 *recb = &S.rec[st][bb * kBoxR];
                     const uint32_t tb = tmem + lanebase + st * kCN + bb * kBoxR;
 #pragma unroll 1
@@ -582,7 +724,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                         if (!((x0 < g + kGroup && x1 > g) || (y0 < g + kGroup && y1 > g))) continue;
                         // the group's records and norms, loaded together with its accumulators
                         float4 rcs[kGroup];
-                        float rns[kGroup];
+                        float2 rns[kGroup];
 #pragma unroll
                         for (int k = 0; k < kGroup; k++) {
                             rcs[k] = recb[g + k];
@@ -620,7 +762,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                         for (; cm; cm &= cm - 1u) {
                             const int k = __ffs(cm) - 1;
                             uint32_t vk = v[0], jk = __float_as_uint(rcs[0].w);
-                            float rk = rns[0];
+                            float2 rk = rns[0];
 #pragma unroll
                             for (int t = 1; t < kGroup; t++)
                                 if (k == t) {
@@ -629,14 +771,78 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                                     rk = rns[t];
                                 }
                             ncand++;
-                            const float dist = qn + rk - 2.0f * __uint_as_float(vk);
-                            top2(((unsigned long long)(uint32_t)dist << 32) | jk, b1, b2);
+                            const float dist = qn + rk.x - 2.0f * __uint_as_float(vk);
+                            if (!isf) {
+                                // integer distances: exact
+                                top2(((unsigned long long)(uint32_t)dist << 32) | jk, b1, b2);
+                            } else {
+                                // distance of the BF16-rounded rows, bracketed around the FP32
+                                // distance the rerank will compute
+                                float lo, hi;
+                                float_bounds(dist, qn, rk.x, qerr, rk.y, lo, hi);
+                                fb.insert(lo, hi, jk);
+                            }
                         }
                     }
                 }
                 tc::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&S.tfree[st]);
+            }
+            if (isf) {
+                // FP32 rerank, one query of the warp at a time, the lanes over the
+                // dimensions: the candidates that can be among the best two, or
+                // (buffer overflow) every reference in the warp's windows
+                const bool live = qv && !(r.flags & EGM_FLAG_DEGENERATE_LINE);
+                const bool complete = fb.complete();
+                const bool exact_only = (r.flags & kQExactOnly) != 0;
+                for (int q = 0; q < 32; q++) {
+                    if (!__shfl_sync(0xffffffffu, (int)live, q)) continue;
+                    const uint32_t qiq = __shfl_sync(0xffffffffu, qi, q);
+                    const float4 qv4 = __ldg(reinterpret_cast<const float4 *>(P.desc1 + (int64_t)qiq * 512) + lane);
+                    unsigned long long k1 = ~0ull, k2 = ~0ull;
+                    if (__shfl_sync(0xffffffffu, (int)complete, q)) {
+                        const float U2q = __shfl_sync(0xffffffffu, fb.U2, q);
+#pragma unroll
+                        for (int t = 0; t < kFBuf; t++) {
+                            const float Lt = __shfl_sync(0xffffffffu, fb.L[t], q);
+                            const uint32_t jt = __shfl_sync(0xffffffffu, fb.J[t], q);
+                            if (Lt <= U2q) {
+                                const float d = coop_dist(qv4, P.desc2 + (int64_t)jt * 512, lane);
+                                top2(((unsigned long long)__float_as_uint(d) << 32) | jt, k1, k2);
+                            }
+                        }
+                    } else {
+                        const float qA = __shfl_sync(0xffffffffu, r.A, q), qB = __shfl_sync(0xffffffffu, r.B, q);
+                        const float qC = __shfl_sync(0xffffffffu, r.C, q);
+                        const float qE0 = __shfl_sync(0xffffffffu, r.E0, q), qE1 = __shfl_sync(0xffffffffu, r.E1, q);
+                        const bool qex = __shfl_sync(0xffffffffu, (int)exact_only, q) != 0;
+                        for (int li = 0; li < nlev; li++)
+                            for (int h = 0; h < 2; h++) {
+                                const uint2 w = S.wr[warp][li][h];
+                                for (uint32_t b0 = 0; b0 < w.y; b0 += 32) {
+                                    const bool valid = b0 + (uint32_t)lane < w.y;
+                                    uint32_t j = 0;
+                                    int m = 0;
+                                    if (valid) {
+                                        const float4 rc = L.rec[P.r_off + w.x + b0 + lane];
+                                        j = __float_as_uint(rc.w);
+                                        m = qex ? 2 : member32(qA, qB, qC, qE0, qE1, rc);
+                                        if (m == 2) m = exact_pair(P, qiq, j) ? 1 : 0;
+                                    }
+                                    for (uint32_t bal = __ballot_sync(0xffffffffu, m == 1); bal; bal &= bal - 1u) {
+                                        const uint32_t jt = __shfl_sync(0xffffffffu, j, __ffs(bal) - 1);
+                                        const float d = coop_dist(qv4, P.desc2 + (int64_t)jt * 512, lane);
+                                        top2(((unsigned long long)__float_as_uint(d) << 32) | jt, k1, k2);
+                                    }
+                                }
+                            }
+                    }
+                    if (lane == q) {
+                        b1 = k1;
+                        b2 = k2;
+                    }
+                }
             }
         }
         seq += (uint32_t)nchunk;
@@ -689,7 +895,8 @@ cudaError_t make_tmap(CUtensorMap *m, const void *base, int64_t rows, uint32_t b
 }  // namespace
 
 bool band_supported(int kind, int dim) {
-    return (kind == EGM_DESC_U8_L2 && dim == 128) || (kind == EGM_DESC_BIN && dim == 256);
+    return (kind == EGM_DESC_U8_L2 && dim == 128) || (kind == EGM_DESC_BIN && dim == 256) ||
+           (kind == EGM_DESC_F32_L2 && dim == 128);
 }
 
 int band_row_bytes() { return kRowB; }
@@ -710,7 +917,7 @@ cudaError_t launch_pack(const Launch &L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int CB, int CPS>
+template <int CB, int CPS, bool FLT>
 cudaError_t launch_band_shape(const Launch &L, int sms, const CUtensorMap &tA, const CUtensorMap &tB,
                               cudaStream_t s) {
     const int smem = (int)sizeof(BandSmem<CB>) + 1024;
@@ -718,9 +925,9 @@ cudaError_t launch_band_shape(const Launch &L, int sms, const CUtensorMap &tA, c
     if (grid > CPS * (int64_t)sms) grid = CPS * (int64_t)sms;
     cudaError_t e = cudaMemsetAsync(L.work, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(band_kernel<CB, CPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(band_kernel<CB, CPS, FLT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    band_kernel<CB, CPS><<<(int)grid, kBandThreads, smem, s>>>(tA, tB, L);
+    band_kernel<CB, CPS, FLT><<<(int)grid, kBandThreads, smem, s>>>(tA, tB, L);
     return cudaGetLastError();
 }
 
@@ -732,9 +939,10 @@ cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s) {
     cudaError_t e = make_tmap(&tA, L.descA, L.nq, kTM);
     if (e != cudaSuccess) return e;
     if ((e = make_tmap(&tB, L.descB, L.nr, kBoxR)) != cudaSuccess) return e;
+    if (L.kinds & (1u << EGM_DESC_F32_L2)) return launch_band_shape<4, 2, true>(L, sms, tA, tB, s);
     switch (shape) {
-        case 0: return launch_band_shape<4, 2>(L, sms, tA, tB, s);
-        case 1: return launch_band_shape<2, 3>(L, sms, tA, tB, s);
+        case 0: return launch_band_shape<4, 2, false>(L, sms, tA, tB, s);
+        case 1: return launch_band_shape<2, 3, false>(L, sms, tA, tB, s);
         default: return cudaErrorInvalidValue;
     }
 }

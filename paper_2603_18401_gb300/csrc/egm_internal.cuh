@@ -132,12 +132,14 @@ struct Launch {
     int32_t ratio_num, ratio_den;
     int32_t max_n;                // largest reference count of the batch
     int32_t kind;                 // descriptor kind shared by every pair, or -1 when mixed
+    uint32_t kinds;               // bit k set when some pair has descriptor kind k
     // banded form (tiles of 128 queries sorted by angle)
     uint32_t *qperm;              // sorted query slot -> pair-local query index
     uint16_t *qbkt;               // per query: its bucket of the angle order (written by the prep kernel)
     uint8_t *descA, *descB;       // 256-byte operand rows of the sorted queries / references
     QueryRec *qsrt;               // query records in sorted order, pad = (query index, norm bits)
-    float *rnorm;                 // sorted references' squared norms (u8) or popcounts (binary)
+    float2 *rnorm;                // sorted references: (squared norm of the operand row, or popcount;
+                                  //   rounding error |r - bf16(r)| of float rows, else 0)
     const int64_t *tile_offs;     // npairs + 1: first tile of each pair
     const int32_t *tile_seq;      // ntiles: tiles in the order they are handed out (costliest pairs first)
     uint32_t *work;               // tile dispenser (zeroed before the band kernel)

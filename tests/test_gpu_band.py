@@ -224,7 +224,7 @@ def test_counters_and_unsupported_inputs(mt):
             mt.match(*args, csr=True)
         assert e.value.status == -8
         rng = np.random.default_rng(0)
-        for kind, dim in ((0, 64), (1, 128), (2, 128)):
+        for kind, dim in ((0, 64), (1, 64), (2, 128)):
             s2 = _scene(rng.uniform(0, 480, (50, 2)), rng.uniform(0, 480, (60, 2)), _F(), 3.0, kind=kind, dim=dim)
             d2 = mt.to_device(s2)
             with pytest.raises(EgmError) as e:
@@ -255,3 +255,67 @@ def test_every_tile_shape_and_the_tuner(mt):
             mt.set_params(band_tile=99)
     finally:
         mt.set_params(form=FORM_AUTO, band_tile=0)
+
+
+# ------------------------------------------------------------------ float descriptors
+# BF16 tensor-core pass, then an FP32 rerank in the plain kernel's order: the
+# outputs equal the plain form's bit for bit (distances included).
+
+def test_float_config4(mt):
+    for sc in synth.config4(seed=0, npairs=2, scale=0.125):
+        both(mt, sc)
+
+
+def test_float_config4_full_size(mt):
+    both(mt, synth.config4(seed=1, npairs=1)[0])
+
+
+def test_float_mixed_with_u8_batch(mt):
+    scenes = synth.config4(seed=2, npairs=3, scale=0.1) + synth.config3(seed=6, npairs=4, scale=0.1)
+    items = [mt.to_device(s) for s in scenes]
+    res = {}
+    for form in (FORM_BANDED, FORM_PLAIN):
+        mt.set_params(form=form)
+        try:
+            res[form] = {k: v.cpu().numpy() for k, v in mt.match_batch(items).items()}
+        finally:
+            mt.set_params(form=FORM_AUTO)
+    # the plain form's kind-generic kernel (mixed batches) sums a float row over
+    # 16 lanes instead of 32: float distances agree to FP32 rounding, not bit
+    # for bit; integer kinds agree exactly
+    q0 = 0
+    for s in scenes:
+        sl = slice(q0, q0 + s.m)
+        bd, pd = res[FORM_BANDED], res[FORM_PLAIN]
+        if s.kind == synth.DESC_F32_L2:
+            for k in ("best_d", "second_d"):
+                fin = np.isfinite(pd[k][sl])
+                assert np.array_equal(np.isfinite(bd[k][sl]), fin)
+                assert np.allclose(bd[k][sl][fin], pd[k][sl][fin], rtol=1e-5, atol=1e-7)
+        else:
+            for k in KEYS:
+                assert np.array_equal(bd[k][sl], pd[k][sl]), k
+        check_matches({k: bd[k][sl] for k in KEYS}, s)
+        q0 += s.m
+
+
+def test_float_rerank_buffer_overflow(mt):
+    """Twenty references on every query's line share one descriptor: their
+    approximate distances tie, more of them than the rerank buffer holds can
+    be among the best two, and the exhaustive pass over the windows decides."""
+    K = synth.intrinsics(500.0, 640, 480)
+    F = synth.fundamental(K, K, synth.rotation([0, 1, 0], 6), [0.3, 0.05, 0.03])
+    rng = np.random.default_rng(13)
+    xy1 = rng.uniform([0, 0], [640, 480], (300, 2))
+    refs = []
+    for x, y in xy1[:60]:
+        a, b, c = F @ np.array([x, y, 1.0])
+        for px in rng.uniform(0, 640, 20):
+            refs.append([px, -(a * px + c) / b + rng.uniform(-1.0, 1.0)])
+    xy2 = np.vstack([np.array(refs), rng.uniform([0, 0], [640, 480], (1500, 2))])
+    sc = _scene(xy1, xy2, F, 2.0, kind=1, dim=128, seed=3)
+    base = rng.random(128).astype(np.float32)
+    sc.desc2[:len(refs)] = base                      # identical descriptors
+    sc.desc1[:60] = base + rng.normal(0, 1e-3, (60, 128)).astype(np.float32)
+    b = both(mt, sc)
+    assert np.all(b["flags"][:60] & 1)
