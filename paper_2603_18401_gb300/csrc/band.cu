@@ -136,6 +136,9 @@ __device__ __forceinline__ uint32_t e4m3_nibble(uint32_t n) {
 __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
     const int64_t rows = L.nr + L.nq;
     const int part = threadIdx.x & 7;
+    __shared__ int64_t s_roffs[kSmemPairs + 1], s_qoffs[kSmemPairs + 1];
+    const bool cached = load_offsets(s_roffs, L.r_offs, L.npairs) && load_offsets(s_qoffs, L.q_offs, L.npairs);
+    __syncthreads();
     for (int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; g0 < ((rows + 3) / 4) * 4;
          g0 += ((int64_t)gridDim.x * blockDim.x) >> 3) {
         const bool valid = g0 < rows;
@@ -147,7 +150,8 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
         uint8_t *dst = nullptr;
         if (valid) {
             const int64_t g = is_ref ? g0 : g0 - L.nr;
-            const int p = pair_of(is_ref ? L.r_offs : L.q_offs, L.npairs, g);
+            const int p = cached ? pair_of_shared(is_ref ? s_roffs : s_qoffs, L.npairs, g)
+                                 : pair_of(is_ref ? L.r_offs : L.q_offs, L.npairs, g);
             const PairDesc &P = L.pairs[p];
             const uint8_t *src;
             if (is_ref) {
@@ -524,19 +528,29 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         }
         __syncthreads();
         const int nlev = S.nlev;
-        // ---- each warp's hull of its queries' windows, level by level
+        // ---- each warp's hull of its queries' windows: the extremes of its
+        // queries' keys and pad arguments, then one window per level (lane = level)
         if (warp < 4) {
-            for (int li = 0; li < nlev; li++) {
-                const KeyWin w = key_window(G, r, S.lv[li]);
-                const uint32_t anyfull = __ballot_sync(0xffffffffu, w.kind == 1);
-                const uint32_t anyrng = __ballot_sync(0xffffffffu, w.kind == 2);
-                const int lo = __reduce_min_sync(0xffffffffu, sortable(w.kind == 2 ? w.lo : INFINITY));
-                const int hi = __reduce_max_sync(0xffffffffu, sortable(w.kind == 2 ? w.hi : -INFINITY));
-                if (lane == 0) {
-                    S.wkind[warp][li] = anyfull ? 1 : anyrng ? 2 : 0;
-                    S.wlo[warp][li] = unsortable(lo);
-                    S.whi[warp][li] = unsortable(hi);
-                }
+            const bool use = qv && !(r.flags & EGM_FLAG_DEGENERATE_LINE);
+            const bool ex = use && (r.flags & kQExactOnly);
+            const bool kv = use && !ex;
+            const float kmin = unsortable(__reduce_min_sync(0xffffffffu, sortable(kv ? r.key : INFINITY)));
+            const float kmax = unsortable(__reduce_max_sync(0xffffffffu, sortable(kv ? r.key : -INFINITY)));
+            const float kabs = unsortable(__reduce_max_sync(0xffffffffu, sortable(kv ? fabsf(r.key) : 0.0f)));
+            const float a0hi = unsortable(__reduce_max_sync(0xffffffffu, sortable(kv ? r.aux0 : -INFINITY)));
+            const float a0lo = unsortable(__reduce_min_sync(0xffffffffu, sortable(kv ? r.aux0 : INFINITY)));
+            const float a1hi = unsortable(__reduce_max_sync(0xffffffffu, sortable(kv ? r.aux1 : -INFINITY)));
+            const bool anyex = __any_sync(0xffffffffu, ex), anykv = __any_sync(0xffffffffu, kv);
+            if (lane < nlev) {
+                KeyWin w;
+                w.kind = 0;
+                w.lo = w.hi = 0.0f;
+                if (anyex || anykv)
+                    w = key_window_span(G, S.lv[lane], kmin, kmax, kabs, G.mode == kModeAngular ? a0hi : a0lo,
+                                        a1hi, anyex);
+                S.wkind[warp][lane] = w.kind;
+                S.wlo[warp][lane] = w.lo;
+                S.whi[warp][lane] = w.hi;
             }
         }
         __syncthreads();
@@ -699,6 +713,12 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             const bool exact_only = (r.flags & kQExactOnly) != 0;
             const bool live = qv && !(r.flags & EGM_FLAG_DEGENERATE_LINE);
             const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
+            // The pre-test bound of the plain kernel, 9.6e-7 S + 1.2e-7 eps + E1 (|x| + |y| + 2 eps)
+            // + E0 + 1e-9 with S = |A x| + |B y| + |C|, taken with |A|, |B| <= 1 (the line is
+            // normalised): bound = k1 (|x| + |y|) + ke eps + k0, never smaller.
+            const float k1 = 9.6e-7f * 1.00001f + r.E1;
+            const float ke = 1.2e-7f + 2.0f * r.E1;
+            const float k0 = fmaf(9.6e-7f, fabsf(r.C), r.E0 + 1e-9f);
             for (int c = 0; c < nchunk; c++) {
                 const uint32_t sq = seq + (uint32_t)c, st = sq & 1u;
                 const bool ok = wait(&S.done[st], (sq >> 1) & 1u) && wait(&S.fullR[st], (sq >> 1) & 1u);
@@ -719,40 +739,42 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                     const float2 *rnb = &S.rn[st][bb][(P.r_off + pos) & 1];
                     const float4 *recb = &S.rec[st][bb * kBoxR];
                     const uint32_t tb = tmem + lanebase + st * kCN + bb * kBoxR;
+                    // the box's columns inside the warp's windows, as a bit mask
+                    auto span = [](int a, int b) {
+                        a = max(a, 0);
+                        b = min(b, kBoxR);
+                        return b <= a ? 0u : (b - a >= 32 ? ~0u : ((1u << (b - a)) - 1u) << a);
+                    };
+                    const uint32_t inbox = live ? (span(x0, x1) | span(y0, y1)) : 0u;
 #pragma unroll 1
                     for (int g = 0; g < kBoxR; g += kGroup) {
-                        if (!((x0 < g + kGroup && x1 > g) || (y0 < g + kGroup && y1 > g))) continue;
-                        // the group's records and norms, loaded together with its accumulators
+                        if (!__any_sync(0xffffffffu, (inbox >> g) & 0xffu)) continue;
+                        // the group's records, loaded together with its accumulators
                         float4 rcs[kGroup];
-                        float2 rns[kGroup];
 #pragma unroll
-                        for (int k = 0; k < kGroup; k++) {
-                            rcs[k] = recb[g + k];
-                            rns[k] = rnb[g + k];
-                        }
+                        for (int k = 0; k < kGroup; k++) rcs[k] = recb[g + k];
                         uint32_t v[kGroup];
                         tc::tmem_ld8(tb + g, v);
                         tc::tmem_wait_ld();
                         // membership of all columns first, branch-free (independent
                         // work for the scheduler); then the few candidates
-                        uint32_t cm = 0, exm = 0;  // candidates; columns left to FP64
+                        const uint32_t gm = (inbox >> g) & 0xffu;
+                        uint32_t cm = 0, um = 0;  // FP32 sure members; members or inconclusive
 #pragma unroll
                         for (int k = 0; k < kGroup; k++) {
-                            const int col = g + k;
-                            const bool in = live && ((col >= x0 && col < x1) || (col >= y0 && col < y1));
                             const float x = rcs[k].x, y = rcs[k].y, e = rcs[k].z;
                             const float d = fabsf(fmaf(r.A, x, fmaf(r.B, y, r.C)));
-                            const float Sm = fmaf(fabsf(r.A), fabsf(x), fmaf(fabsf(r.B), fabsf(y), fabsf(r.C)));
-                            // FP32 rounding (16u S), the FP32 tolerance (2u eps) and the
-                            // distance between this line and the brute force's FP64 line
-                            const float lerr = fmaf(r.E1, fabsf(x) + fabsf(y) + 2.0f * e, r.E0);
-                            const float bound = fmaf(9.6e-7f, Sm, fmaf(1.2e-7f, e, lerr + 1e-9f));
-                            const bool c = !exact_only && d <= e - bound;
-                            const bool u = exact_only || (!c && !(d > e + bound));
-                            cm |= (uint32_t)(in && c) << k;
-                            exm |= (uint32_t)(in && u) << k;
-                            nwin += in ? 1u : 0u;
+                            const float bound = fmaf(k1, fabsf(x) + fabsf(y), fmaf(ke, e, k0));
+                            cm |= (uint32_t)(d <= e - bound) << k;
+                            um |= (uint32_t)(d <= e + bound) << k;
                         }
+                        if (exact_only) {
+                            cm = 0u;
+                            um = 0xffu;
+                        }
+                        cm &= gm;
+                        uint32_t exm = um & ~cm & gm;  // left to the FP64 expression
+                        nwin += __popc(gm);
                         // FP32 inconclusive: the brute-force FP64 expression decides
                         for (uint32_t m = exm; m; m &= m - 1u) {
                             const int k = __ffs(m) - 1;
@@ -762,14 +784,13 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                         for (; cm; cm &= cm - 1u) {
                             const int k = __ffs(cm) - 1;
                             uint32_t vk = v[0], jk = __float_as_uint(rcs[0].w);
-                            float2 rk = rns[0];
 #pragma unroll
                             for (int t = 1; t < kGroup; t++)
                                 if (k == t) {
                                     vk = v[t];
                                     jk = __float_as_uint(rcs[t].w);
-                                    rk = rns[t];
                                 }
+                            const float2 rk = rnb[g + k];
                             ncand++;
                             const float dist = qn + rk.x - 2.0f * __uint_as_float(vk);
                             if (!isf) {

@@ -201,6 +201,16 @@ __device__ __forceinline__ int pair_of_shared(const int64_t *offs, int npairs, i
     return lo;
 }
 
+// Pair offsets cached in a block's shared memory when the batch has at most
+// kSmemPairs pairs (every thread calls load_offsets, then the block syncs).
+constexpr int kSmemPairs = 512;
+
+__device__ __forceinline__ bool load_offsets(int64_t *s_offs, const int64_t *offs, int npairs) {
+    if (npairs > kSmemPairs) return false;
+    for (int i = threadIdx.x; i <= npairs; i += blockDim.x) s_offs[i] = offs[i];
+    return true;
+}
+
 // Index of the pair that owns flattened element g, given offs[0..npairs] in
 // global memory.
 __device__ __forceinline__ int pair_of(const int64_t *offs, int npairs, int64_t g) {
@@ -315,6 +325,50 @@ __device__ __forceinline__ KeyWin key_window(const PairGeom &G, const QueryRec &
         }
     }
     w.kind = full ? 1 : 2;
+    return w;
+}
+
+// One window containing the windows of several queries of a pair (a warp of
+// the banded form): keys in [kmin, kmax], |key| <= kabs, and the pad argument
+// a0 (angular: the largest r_i; parallel: the smallest cos phi) and a1
+// (parallel: the largest |sin phi|).  The true half-width grows with r_i
+// (angular) and with |sin phi| / cos phi (parallel), and the pads of
+// key_window cover the FP32 evaluation for any argument, so the result
+// contains every one of those queries' windows.  `exact`: some query has no
+// FP32 view (every level whole).
+__device__ __forceinline__ KeyWin key_window_span(const PairGeom &G, int lv, float kmin, float kmax, float kabs,
+                                                  float a0, float a1, bool exact) {
+    KeyWin w;
+    w.kind = 0;
+    w.lo = w.hi = 0.0f;
+    if (lv >= kLevels || G.cnt[lv] == 0) return w;
+    const float smax = __uint_as_float(G.smax[lv]);
+    const float R = __uint_as_float(G.tmax[lv]);
+    const float u = 5.9604645e-8f;
+    bool full = exact;
+    float hw = 0.0f;
+    if (full) {
+    } else if (G.mode == kModeAngular) {
+        const float dpos = 8.0f * u * R + 4.0f * u * fminf(G.de, R) + 2.0f * u * fabsf(G.kappa) + 1e-9f;
+        const float dmin = __uint_as_float(G.dmin[lv]);
+        const float sigma = (dmin > 0.0f) ? (smax + (a0 + dpos) / dmin) * 1.000001f : INFINITY;
+        full = !(sigma < 1.0f);
+        if (!full) {
+            const float wv = asinf(sigma) * 1.000001f + 1e-37f;
+            hw = wv + (4e-6f * (kabs + wv) + 2e-6f);
+            full = !(hw < kHalfPiF);
+        }
+    } else {
+        full = !(a0 >= 0.5f);
+        if (!full) {
+            const float wv = (smax + R * a1 + 8.0f * u * R + 1e-9f) / a0 * 1.000001f;
+            hw = wv + (1e-6f * (kabs + wv) + 1e-6f);
+            full = !isfinite(hw);
+        }
+    }
+    w.kind = full ? 1 : 2;
+    w.lo = kmin - hw;
+    w.hi = kmax + hw;
     return w;
 }
 

@@ -223,7 +223,6 @@ __device__ void block_radix_sort(SortSmem &S, const uint32_t *ik, const uint32_t
 // The order within a bucket follows the atomics and is not fixed; everything
 // downstream depends only on bucket order (ties between candidates are broken
 // by index).
-constexpr int kSmemPairs = 1024;                      // pair offsets cached in shared memory up to this
 
 __device__ __forceinline__ uint32_t bucket_slot(const PairGeom &G, uint32_t key) {
     const int lv = (int)(key >> kQBits);
@@ -232,9 +231,7 @@ __device__ __forceinline__ uint32_t bucket_slot(const PairGeom &G, uint32_t key)
 
 __global__ void __launch_bounds__(256) bucket_count_kernel(Launch L) {
     __shared__ int64_t offs[kSmemPairs + 1];
-    const bool cached = L.npairs <= kSmemPairs;
-    if (cached)
-        for (int i = threadIdx.x; i <= L.npairs; i += blockDim.x) offs[i] = L.r_offs[i];
+    const bool cached = load_offsets(offs, L.r_offs, L.npairs);
     __syncthreads();
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L.nr; g += (int64_t)gridDim.x * blockDim.x) {
         const int p = cached ? pair_of_shared(offs, L.npairs, g) : pair_of(L.r_offs, L.npairs, g);

@@ -319,3 +319,20 @@ def test_float_rerank_buffer_overflow(mt):
     sc.desc1[:60] = base + rng.normal(0, 1e-3, (60, 128)).astype(np.float32)
     b = both(mt, sc)
     assert np.all(b["flags"][:60] & 1)
+
+
+def test_float_distance_error_against_fp64(mt):
+    """The FP32 distances of both forms against the oracle's FP64 distances
+    (config 4, every query with a match): the largest relative error is
+    reported and must stay within 1e-5."""
+    worst = 0.0
+    for sc in synth.config4(seed=3, npairs=2, scale=0.25):
+        ref = oracle.match_scene(sc)
+        has = ref["best"] >= 0
+        for form in (FORM_BANDED, FORM_PLAIN):
+            out = run_form(mt, sc, form)
+            same = has & (out["best"] == ref["best"])
+            rel = np.abs(out["best_d"][same].astype(np.float64) - ref["best_d"][same]) / np.maximum(ref["best_d"][same], 1e-30)
+            worst = max(worst, float(rel.max()))
+    print(f"largest relative error of FP32 best distances against FP64: {worst:.3e}")
+    assert worst <= 1e-5
