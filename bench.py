@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--compare-steps", type=int, default=200)
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-form comparison legs")
     ap.add_argument("--no-mlp", action="store_true", help="skip the learned-tolerance leg")
+    ap.add_argument("--no-float", action="store_true", help="skip the float-descriptor batch")
+    ap.add_argument("--float-pairs", type=int, default=64)
+    ap.add_argument("--no-matching", action="store_true", help="skip the mutual-matching leg")
     return ap.parse_args()
 
 
@@ -232,6 +235,46 @@ def kernel_profile(kernel):
     with open(path) as f:
         d = json.load(f)
     return d if d.get("source_sha256") == source_hash(kernel) else None
+
+
+def matching_leg(mt, torch, stream, scs, dev, steps):
+    """Mutual matching (both directions, cross-check) of the single-pair scenes
+    and the compact list of ratio-passing mutual matches; recall and precision
+    against the true pairs of the synthetic scenes."""
+    RATIO_MUTUAL = 2 | 16
+
+    def one(s, d):
+        o = mt.match_mutual(d["xy1"], d["xy2"], d["F"], d["eps"], 2.0, d["desc1"], d["desc2"], d["kind"],
+                            d["dim"], d["width"], d["height"])
+        return mt.compact_matches(o["flags"][:s.m], o["best"][:s.m], RATIO_MUTUAL)
+
+    tp = n_true = n_got = 0
+    for s, d in zip(scs, dev):
+        qi, rj = one(s, d)
+        got = set(zip(qi.cpu().numpy().tolist(), rj.cpu().numpy().tolist()))
+        truth = set(map(tuple, s.gt.tolist()))
+        tp += len(got & truth)
+        n_true += len(truth)
+        n_got += len(got)
+    mt.set_params(sync=False)
+    for _ in range(3):
+        for s, d in zip(scs, dev):
+            one(s, d)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = max(steps // 10, 5)
+    for _ in range(reps):
+        for s, d in zip(scs, dev):
+            one(s, d)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    q = sum(s.m + s.n for s in scs)
+    return {"workload": "the nine single pairs, both directions (eps 2 px for image-1 keypoints)",
+            "queries_per_s": q / (ms * 1e-3), "ms_per_step": ms, "matches": n_got,
+            "recall": tp / max(n_true, 1), "precision": tp / max(n_got, 1),
+            "filter": "ratio test (4/5) and mutual"}
 
 
 def mlp_leg(mt, torch, stream):
@@ -485,10 +528,10 @@ def run_ours(args):
         bitems = [mt.to_device(s) for s in bsc]
         bM = sum(s.m for s in bsc)
 
-        def time_graph(form):
+        def time_graph(form, items=bitems, total=bM):
             mt.set_params(form=form)
-            bout = mt._alloc_out(bM, False, 0)
-            graph = mt.graph_create(bitems, bout)
+            bout = mt._alloc_out(total, False, 0)
+            graph = mt.graph_create(items, bout)
             for _ in range(3):
                 if graph.launch() != 0:
                     raise EgmError(mt.sync(), "batched warm-up")
@@ -529,7 +572,29 @@ def run_ours(args):
         if bform != 1 and not args.no_compare:
             pms = time_graph(1)
             batched["plain_form"] = {"pairs_per_s": world * len(bsc) / (pms * 1e-3), "ms_per_step": pms}
+        del bitems
+        # float descriptors: 128-d RootSIFT-like FP32, 16384 keypoints per image
+        if not args.no_float:
+            fsc = _synth.config4(seed=0, npairs=args.float_pairs)
+            fitems = [mt.to_device(s) for s in fsc]
+            fM = sum(s.m for s in fsc)
+            fms = time_graph(bform, fitems, fM)
+            fl = {"workload": f"{len(fsc)} pairs 6048x4032, 16384 keypoints per image, 128-d float L2 "
+                              "(RootSIFT-like), random poses",
+                  "pairs_per_s": world * len(fsc) / (fms * 1e-3), "queries_per_s": world * fM / (fms * 1e-3),
+                  "ms_per_step": fms, "form": args.form}
+            if bform != 1 and not args.no_compare:
+                pms = time_graph(1, fitems, fM)
+                fl["plain_form"] = {"pairs_per_s": world * len(fsc) / (pms * 1e-3), "ms_per_step": pms}
+            batched["float_descriptors"] = fl
+            del fitems
         mt.set_params(form=bform)
+
+    # mutual matching and the match list, with recall / precision on the
+    # scenes' true pairs (synthetic ground truth)
+    matching = None
+    if not args.no_matching:
+        matching = matching_leg(mt, torch, stream, scs, dev, args.compare_steps)
 
     # learned tolerance: training steps and inference of the 5-64-64-64-1 network
     mlp = None
@@ -554,6 +619,7 @@ def run_ours(args):
         "batched": batched,
         "other_form_one_pair": other_form,
         "learned_tolerance": mlp,
+        "matching": matching,
         "clocks": clk,
         "gpu_launches": launches_per_pair * len(scs) * args.steps,
     }

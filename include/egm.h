@@ -74,7 +74,8 @@ enum {
     EGM_FLAG_HAS_BEST = 1,         /* at least one candidate */
     EGM_FLAG_RATIO_PASS = 2,       /* accepted: ratio test passed or no second candidate */
     EGM_FLAG_NO_SECOND = 4,        /* exactly one candidate */
-    EGM_FLAG_DEGENERATE_LINE = 8   /* F p~ has a = b = 0: no line, empty set */
+    EGM_FLAG_DEGENERATE_LINE = 8,  /* F p~ has a = b = 0: no line, empty set */
+    EGM_FLAG_MUTUAL = 16           /* egm_match_mutual: the best match's own best is this row */
 };
 
 /*
@@ -237,6 +238,31 @@ egm_status egm_sync(egm_ctx *ctx);
  *                        ||p_j - e2|| <= eps_j (full interval)
  * In parallel mode theta/delta receive NaN.  Device pointers; any may be NULL.
  */
+/*
+ * Mutual (cross-check) matching: the matching step of Algorithm 1 run in both
+ * directions; a match i -> j is kept as mutual when j's best match in the
+ * other direction is i.  `fwd` is the pair as for egm_match_pair; `rev` the
+ * same images with the roles swapped: xy1 / desc1 of image 2, xy2 / desc2 of
+ * image 1, F transposed (p1^T F^T p2 = 0), the tolerance of the image-1
+ * keypoints, and image 1's width and height.  rev->m must equal fwd->n and
+ * rev->n fwd->m, with the same descriptor kind and dimension.  `out` has
+ * fwd->m + fwd->n rows: [0, m) the forward results, [m, m + n) the reverse
+ * ones (indices local to each direction); every row whose best match is
+ * mutual gets EGM_FLAG_MUTUAL.  No candidate lists (cand_offsets NULL).
+ */
+egm_status egm_match_mutual(egm_ctx *ctx, const egm_pair *fwd, const egm_pair *rev, const egm_out *out);
+
+/*
+ * The compact list of matches: (qi[k], rj[k]) = (i, best[i]) for every row
+ * i < m whose flags contain every bit of `require` (for example
+ * EGM_FLAG_RATIO_PASS | EGM_FLAG_MUTUAL), in ascending i; *count receives
+ * their number.  flags, best: m entries; qi, rj: room for m; count: one
+ * int64.  Device pointers.  This library extension has no counterpart in the
+ * paper beyond its output "matches" (Algorithm 1).
+ */
+egm_status egm_compact_matches(egm_ctx *ctx, const uint8_t *flags, const int32_t *best, int64_t m,
+                               uint32_t require, int32_t *qi, int32_t *rj, int64_t *count);
+
 egm_status egm_intervals(egm_ctx *ctx, const egm_pair *pair, double *theta, double *delta,
                          double *e3, int32_t *mode);
 

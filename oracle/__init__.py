@@ -12,6 +12,9 @@ the CUDA path.  Everything is FP64.
   delta_j = asin(eps_j / ||p_j - e||) (Sec. 4.2), folded into [0, pi)
   (Sec. 4.2, "reduced domain"); keypoints within eps of the epipole get the
   full interval (Algorithm 1; Sec. 4.4 "Keypoints near the epipole").
+- ``match_mutual``: matching in both directions (the reverse with F^T and the
+  roles of the images swapped, Sec. 3) and the cross-check: i -> j is mutual
+  when j's best in the reverse direction is i.
 - ``mlp``: the learned-tolerance network in FP64 (see ``oracle/mlp.py``).
 """
 from __future__ import annotations
@@ -27,6 +30,7 @@ FLAG_HAS_BEST = 1
 FLAG_RATIO_PASS = 2
 FLAG_NO_SECOND = 4
 FLAG_DEGENERATE_LINE = 8
+FLAG_MUTUAL = 16
 BOUNDARY_BAND = 1e-9
 
 _lib = None
@@ -144,6 +148,22 @@ def match(xy1, xy2, F, eps, desc1, desc2, kind, dim, ratio=(4, 5), exclude_bound
                      _p(out["best"]), _p(out["second"]), _p(out["best_d"]), _p(out["second_d"]),
                      _p(out["flags"]), _p(out["ncand"]))
     return out
+
+
+def match_mutual(xy1, xy2, F, eps2, eps1, desc1, desc2, kind, dim, ratio=(4, 5), exclude_boundary=False):
+    """Both directions and the cross-check.  Returns (forward, reverse): the
+    dicts of ``match`` for image 1 -> 2 (F, tolerance eps2 of the image-2
+    keypoints) and image 2 -> 1 (F^T, tolerance eps1 of the image-1
+    keypoints), with FLAG_MUTUAL added to every row whose best match has that
+    row as its own best."""
+    F = _f64(F, (3, 3))
+    fw = match(xy1, xy2, F, eps2, desc1, desc2, kind, dim, ratio, exclude_boundary)
+    rv = match(xy2, xy1, F.T.copy(), eps1, desc2, desc1, kind, dim, ratio, exclude_boundary)
+    for a, b in ((fw, rv), (rv, fw)):
+        for i, j in enumerate(a["best"]):
+            if j >= 0 and b["best"][j] == i:
+                a["flags"][i] |= FLAG_MUTUAL
+    return fw, rv
 
 
 def match_scene(sc, ratio=(4, 5), exclude_boundary=False, eps=None):

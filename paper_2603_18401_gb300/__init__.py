@@ -11,12 +11,12 @@ import ctypes as C
 
 from . import _egm
 from ._egm import (EGM_DESC_BIN, EGM_DESC_F32_L2, EGM_DESC_U8_L2, EGM_ERR_CAPACITY,
-                   EGM_FLAG_DEGENERATE_LINE, EGM_FLAG_HAS_BEST, EGM_FLAG_NO_SECOND,
+                   EGM_FLAG_DEGENERATE_LINE, EGM_FLAG_HAS_BEST, EGM_FLAG_MUTUAL, EGM_FLAG_NO_SECOND,
                    EGM_FLAG_RATIO_PASS, EGM_OK, EgmError, check, load)
 
 __all__ = ["Matcher", "TolNet", "EgmError", "load", "row_bytes", "EGM_DESC_U8_L2", "EGM_DESC_F32_L2",
            "EGM_DESC_BIN", "EGM_FLAG_HAS_BEST", "EGM_FLAG_RATIO_PASS", "EGM_FLAG_NO_SECOND",
-           "EGM_FLAG_DEGENERATE_LINE"]
+           "EGM_FLAG_DEGENERATE_LINE", "EGM_FLAG_MUTUAL"]
 
 
 def row_bytes(kind: int, dim: int) -> int:
@@ -248,6 +248,36 @@ class Matcher:
             s.cand_capacity = cap
         check(self.egm_match_pair_host(p, s), "egm_match_pair_host")
         return o
+
+    def match_mutual(self, xy1, xy2, F, eps2, eps1, desc1, desc2, kind=EGM_DESC_U8_L2, dim=128,
+                     width2=640, height2=480, width1=None, height1=None):
+        """egm_match_mutual: device tensors of one pair and the tolerance of each
+        image's keypoints (eps1 for the reverse direction).  Returns the outputs
+        of m + n rows: forward results, then reverse results."""
+        torch = self.torch
+        fwd = self.make_pair(xy1, xy2, F, eps2, desc1, desc2, kind, dim, width2, height2)
+        keep = self._keep
+        Ft = F.reshape(3, 3).t().contiguous().reshape(9)
+        rev = self.make_pair(xy2, xy1, Ft, eps1, desc2, desc1, kind, dim,
+                             width1 if width1 is not None else width2, height1 if height1 is not None else height2)
+        self._keep = [keep, self._keep, Ft]
+        o = self._alloc_out(int(xy1.shape[0]) + int(xy2.shape[0]), False, 0)
+        s = self._out_struct(o, 0)
+        check(self.lib.egm_match_mutual(self.ctx, C.byref(fwd), C.byref(rev), C.byref(s)), "egm_match_mutual")
+        del torch
+        return o
+
+    def compact_matches(self, flags, best, require):
+        """egm_compact_matches: (i, best[i]) of the rows whose flags contain `require`."""
+        torch = self.torch
+        m = int(flags.shape[0])
+        qi = torch.empty(max(m, 1), dtype=torch.int32, device=self.device)
+        rj = torch.empty(max(m, 1), dtype=torch.int32, device=self.device)
+        cnt = torch.empty(1, dtype=torch.int64, device=self.device)
+        check(self.lib.egm_compact_matches(self.ctx, _ptr(flags), _ptr(best), m, int(require), _ptr(qi), _ptr(rj),
+                                           _ptr(cnt)), "egm_compact_matches")
+        k = int(cnt.item())
+        return qi[:k], rj[:k]
 
     def tolnet(self, params) -> "TolNet":
         """A learned-tolerance network on this context (egm_mlp_create)."""

@@ -30,6 +30,7 @@ EGM_FLAG_HAS_BEST = 1
 EGM_FLAG_RATIO_PASS = 2
 EGM_FLAG_NO_SECOND = 4
 EGM_FLAG_DEGENERATE_LINE = 8
+EGM_FLAG_MUTUAL = 16
 
 EGM_FORM_AUTO = 0
 EGM_FORM_PLAIN = 1
@@ -100,6 +101,9 @@ SIGNATURES = {
                                      C.c_void_p]),
     "egm_pair_residuals": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.c_void_p, C.c_void_p, C.c_int64,
                                      C.c_void_p]),
+    "egm_match_mutual": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.POINTER(egm_pair), C.POINTER(egm_out)]),
+    "egm_compact_matches": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_uint32, C.c_void_p,
+                                      C.c_void_p, C.c_void_p]),
     "egm_sync": (C.c_int, [C.c_void_p]),
     "egm_intervals": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p]),

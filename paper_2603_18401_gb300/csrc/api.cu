@@ -61,6 +61,7 @@ struct egm_ctx {
     egm_stats last{};
     Scratch sc;
     DevBuf stage;  // host-path staging of inputs and outputs
+    DevBuf compact;  // tile counts of egm_compact_matches
     // pinned host memory for the pair table and the status word
     // pinned staging slots of the pair-table uploads, used round-robin: the
     // host waits only when a slot's previous upload is still in flight
@@ -615,6 +616,7 @@ egm_status egm_destroy(egm_ctx *c) {
     if (c->join_ev) cudaEventDestroy(c->join_ev);
     c->sc.release();
     if (c->stage.ptr) cudaFree(c->stage.ptr);
+    if (c->compact.ptr) cudaFree(c->compact.ptr);
     for (int k = 0; k < egm_ctx::kSlots; k++) {
         if (c->h_table[k]) cudaFreeHost(c->h_table[k]);
         if (c->slot_ev[k]) cudaEventDestroy(c->slot_ev[k]);
@@ -761,6 +763,29 @@ egm_status egm_match_pair_host(egm_ctx *c, const egm_pair *hp, const egm_out *ho
             EGM_TRY(cudaStreamSynchronize(st));
         }
     }
+    return EGM_OK;
+}
+
+egm_status egm_match_mutual(egm_ctx *c, const egm_pair *fwd, const egm_pair *rev, const egm_out *out) {
+    if (!c || !fwd || !rev || !out || !out->best || !out->flags || out->cand_offsets) return EGM_ERR_ARG;
+    if (rev->m != fwd->n || rev->n != fwd->m || rev->kind != fwd->kind || rev->dim != fwd->dim) return EGM_ERR_ARG;
+    const egm_pair both[2] = {*fwd, *rev};
+    EGM_TRY(cudaSetDevice(c->device));
+    if (c->params.sync) EGM_TRY(cudaMemsetAsync(c->sc.small.ptr, 0, sizeof(uint32_t), c->stream));
+    egm_status s = run_batch(c, both, 2, out, false);
+    if (s != EGM_OK) return s;
+    EGM_TRY(launch_mutual(out->best, out->flags, fwd->m, fwd->n, c->stream));
+    return finish(c, c->params.sync != 0);
+}
+
+egm_status egm_compact_matches(egm_ctx *c, const uint8_t *flags, const int32_t *best, int64_t m,
+                               uint32_t require, int32_t *qi, int32_t *rj, int64_t *count) {
+    if (!c || m < 0 || !count || (m > 0 && (!flags || !best || !qi || !rj))) return EGM_ERR_ARG;
+    EGM_TRY(cudaSetDevice(c->device));
+    EGM_TRY(grow(c->compact, sizeof(uint32_t) * (size_t)std::max<int64_t>(compact_tiles(m), 1)));
+    EGM_TRY(launch_compact(flags, best, m, require, static_cast<uint32_t *>(c->compact.ptr), qi, rj, count,
+                           c->stream));
+    if (c->params.sync) EGM_TRY(cudaStreamSynchronize(c->stream));
     return EGM_OK;
 }
 

@@ -484,6 +484,10 @@ int band_tile_queries();
 cudaError_t launch_query_sort(const Launch &L, cudaStream_t s);
 cudaError_t launch_pack(const Launch &L, cudaStream_t s);
 int band_shapes();  // tile shapes of the band kernel (see band.cu)
+cudaError_t launch_mutual(const int32_t *best, uint8_t *flags, int64_t m, int64_t n, cudaStream_t s);
+int64_t compact_tiles(int64_t m);
+cudaError_t launch_compact(const uint8_t *flags, const int32_t *best, int64_t m, uint32_t require,
+                           uint32_t *tile_count, int32_t *qi, int32_t *rj, int64_t *count, cudaStream_t s);
 cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s);
 cudaError_t launch_prep(const Launch &L, cudaStream_t s);
 cudaError_t launch_sort(const Launch &L, cudaStream_t s);

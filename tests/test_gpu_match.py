@@ -1,0 +1,126 @@
+"""Mutual matching (egm_match_mutual) and the compact match list
+(egm_compact_matches) against the oracle, and matching recall on the
+synthetic ground truth."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from test_gpu_parity import _scene, check_matches
+
+pytestmark = pytest.mark.gpu
+
+FORM_AUTO, FORM_PLAIN, FORM_BANDED = 0, 1, 2
+KEYS = ("best", "second", "flags", "best_d", "second_d")
+RATIO, MUTUAL = 2, 16
+
+
+@pytest.fixture(scope="module")
+def mt():
+    import torch
+
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_2603_18401_gb300 import Matcher
+
+    m = Matcher(0)
+    yield m
+    torch.cuda.synchronize()
+    m.close()
+
+
+def mutual(mt, sc, eps1, form=FORM_AUTO):
+    torch = mt.torch
+    d = mt.to_device(sc)
+    e1 = eps1 if np.ndim(eps1) == 0 else torch.as_tensor(eps1, dtype=torch.float64).to(mt.device)
+    mt.set_params(form=form)
+    try:
+        o = mt.match_mutual(d["xy1"], d["xy2"], d["F"], d["eps"], e1, d["desc1"], d["desc2"], d["kind"], d["dim"],
+                            d["width"], d["height"])
+    finally:
+        mt.set_params(form=FORM_AUTO)
+    return {k: v.cpu().numpy() for k, v in o.items()}, o
+
+
+def check_mutual(out, sc, eps1):
+    fw, rv = oracle.match_mutual(sc.xy1, sc.xy2, sc.F, sc.eps, eps1, sc.desc1, sc.desc2, sc.kind, sc.dim)
+    m = sc.m
+    check_matches({k: out[k][:m] for k in KEYS}, sc, ref=fw)
+    rev = synth.Scene(xy1=sc.xy2, xy2=sc.xy1, F=np.ascontiguousarray(sc.F.T), eps=eps1, desc1=sc.desc2,
+                      desc2=sc.desc1, kind=sc.kind, dim=sc.dim, width=sc.width, height=sc.height,
+                      gt=np.zeros((0, 2), np.int64))
+    check_matches({k: out[k][m:] for k in KEYS}, rev, ref=rv)
+    return fw, rv
+
+
+@pytest.mark.parametrize("form", [FORM_PLAIN, FORM_BANDED])
+def test_mutual_config1_and_config2(mt, form):
+    for sc in (synth.config1(), synth.config2("far", 2.0, scale=0.25), synth.config2("inside", 4.0, scale=0.25)):
+        out, _ = mutual(mt, sc, 2.0 if np.ndim(sc.eps) == 0 else sc.eps, form)
+        check_mutual(out, sc, 2.0)
+
+
+def test_mutual_binary_float_and_per_keypoint_eps(mt):
+    rng = np.random.default_rng(4)
+    for sc in (synth.config3(seed=7, npairs=2, scale=0.1)[1], synth.config4(seed=1, npairs=1, scale=0.1)[0]):
+        out, _ = mutual(mt, sc, 2.0)
+        check_mutual(out, sc, 2.0)
+    K = synth.intrinsics(500.0, 640, 480)
+    F = synth.fundamental(K, K, synth.rotation([0, 1, 0], 6), [0.3, 0.05, 0.03])
+    sc = _scene(rng.uniform([0, 0], [640, 480], (700, 2)), rng.uniform([0, 0], [640, 480], (900, 2)), F,
+                rng.uniform(0.5, 6.0, 900), dim=128)
+    eps1 = rng.uniform(0.5, 6.0, 700)
+    out, _ = mutual(mt, sc, eps1)
+    check_mutual(out, sc, eps1)
+
+
+def test_mutual_rejects_inconsistent_pairs(mt):
+    from paper_2603_18401_gb300 import EgmError, _egm
+    import ctypes as C
+
+    sc = synth.config1(scale=0.1)
+    d = mt.to_device(sc)
+    fwd = mt.make_pair(d["xy1"], d["xy2"], d["F"], 2.0, d["desc1"], d["desc2"], 0, 128)
+    rev = mt.make_pair(d["xy1"], d["xy2"], d["F"], 2.0, d["desc1"], d["desc2"], 0, 128)  # sizes not swapped
+    o = mt._alloc_out(2 * sc.m, False, 0)
+    s = mt._out_struct(o, 0)
+    if sc.m != sc.n:
+        assert mt.lib.egm_match_mutual(mt.ctx, C.byref(fwd), C.byref(rev), C.byref(s)) == _egm.EGM_ERR_ARG
+    assert mt.lib.egm_match_mutual(mt.ctx, None, C.byref(rev), C.byref(s)) == _egm.EGM_ERR_ARG
+    del EgmError
+
+
+@pytest.mark.parametrize("m", [0, 1, 777, 2048, 2049, 40000])
+def test_compact_matches(mt, m):
+    torch = mt.torch
+    rng = np.random.default_rng(m)
+    flags = rng.integers(0, 32, m).astype(np.uint8)
+    best = rng.integers(-1, 1000, m).astype(np.int32)
+    f, b = torch.as_tensor(flags).to(mt.device), torch.as_tensor(best).to(mt.device)
+    for req in (0, RATIO, RATIO | MUTUAL, 31):
+        qi, rj = mt.compact_matches(f, b, req)
+        sel = np.nonzero((flags & req) == req)[0]
+        assert np.array_equal(qi.cpu().numpy(), sel)
+        assert np.array_equal(rj.cpu().numpy(), best[sel])
+
+
+def recall_precision(qi, rj, gt):
+    truth = set(map(tuple, gt.tolist()))
+    got = set(zip(qi.tolist(), rj.tolist()))
+    tp = len(got & truth)
+    return tp / max(len(truth), 1), tp / max(len(got), 1)
+
+
+def test_matching_recall_on_synthetic_ground_truth(mt):
+    """Ratio-passing mutual matches against the scenes' true pairs: the GPU
+    list equals the oracle's, so its recall and precision do too."""
+    for sc in (synth.config1(), synth.config2("inside", 2.0), synth.config2("far", 2.0)):
+        out, dev = mutual(mt, sc, 2.0)
+        qi, rj = mt.compact_matches(dev["flags"][:sc.m], dev["best"][:sc.m], RATIO | MUTUAL)
+        qi, rj = qi.cpu().numpy(), rj.cpu().numpy()
+        fw, _ = oracle.match_mutual(sc.xy1, sc.xy2, sc.F, sc.eps, 2.0, sc.desc1, sc.desc2, sc.kind, sc.dim)
+        sel = np.nonzero((fw["flags"] & (RATIO | MUTUAL)) == (RATIO | MUTUAL))[0]
+        assert np.array_equal(qi, sel) and np.array_equal(rj, fw["best"][sel])
+        rec, prec = recall_precision(qi, rj, sc.gt)
+        assert rec > 0.85 and prec > 0.97, (rec, prec)

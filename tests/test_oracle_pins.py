@@ -264,3 +264,27 @@ def test_exclude_boundary_changes_only_boundary_queries():
     b = oracle.match(xy1, xy2, F, 2.0, d1, d2, 0, 2, exclude_boundary=True)
     assert a["best"][0] == 0 and b["best"][0] == 1
     assert a["best"][1] == b["best"][1] == 2
+
+
+def test_mutual_matching_hand_case_and_symmetry():
+    """A hand-built pair: F = [x]_x (lines y = y1 in both directions), two
+    points per image on the same rows; descriptors make 0 <-> 1 and 1 <-> 0
+    mutual, while query 2's best (reference 1) prefers query 1."""
+    F = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, -1.0], [0.0, 1.0, 0.0]])  # [e_x]_x: p2^T F p1 = y1 - y2
+    xy1 = np.array([[10.0, 5.0], [20.0, 7.0], [30.0, 7.0]])
+    xy2 = np.array([[40.0, 5.0], [50.0, 7.0]])
+    d1 = np.array([[0] * 15 + [0], [0] * 15 + [100], [0] * 15 + [110]], np.uint8)
+    d2 = np.array([[0] * 15 + [1], [0] * 15 + [101]], np.uint8)
+    fw, rv = oracle.match_mutual(xy1, xy2, F, 0.5, 0.5, d1, d2, 0, 16)
+    assert list(fw["best"]) == [0, 1, 1]
+    assert list(rv["best"]) == [0, 1]
+    mf = (fw["flags"] & oracle.FLAG_MUTUAL) != 0
+    mr = (rv["flags"] & oracle.FLAG_MUTUAL) != 0
+    assert list(mf) == [True, True, False] and list(mr) == [True, True]
+    # symmetry on a random scene: mutual rows pair up one to one
+    sc = synth.config1(seed=2, scale=0.2)
+    fw, rv = oracle.match_mutual(sc.xy1, sc.xy2, sc.F, 2.0, 2.0, sc.desc1, sc.desc2, sc.kind, sc.dim)
+    mf = np.nonzero(fw["flags"] & oracle.FLAG_MUTUAL)[0]
+    mr = np.nonzero(rv["flags"] & oracle.FLAG_MUTUAL)[0]
+    assert len(mf) == len(mr) > 0
+    assert sorted(fw["best"][mf]) == sorted(mr) and sorted(rv["best"][mr]) == sorted(mf)
