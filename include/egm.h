@@ -75,7 +75,8 @@ enum {
     EGM_FLAG_RATIO_PASS = 2,       /* accepted: ratio test passed or no second candidate */
     EGM_FLAG_NO_SECOND = 4,        /* exactly one candidate */
     EGM_FLAG_DEGENERATE_LINE = 8,  /* F p~ has a = b = 0: no line, empty set */
-    EGM_FLAG_MUTUAL = 16           /* egm_match_mutual: the best match's own best is this row */
+    EGM_FLAG_MUTUAL = 16,          /* egm_match_mutual: the best match's own best is this row */
+    EGM_FLAG_GMS = 32              /* egm_gms: the match passed the grid motion-statistics filter */
 };
 
 /*
@@ -262,6 +263,29 @@ egm_status egm_match_mutual(egm_ctx *ctx, const egm_pair *fwd, const egm_pair *r
  */
 egm_status egm_compact_matches(egm_ctx *ctx, const uint8_t *flags, const int32_t *best, int64_t m,
                                uint32_t require, int32_t *qi, int32_t *rj, int64_t *count);
+
+/*
+ * Grid-based motion statistics filter (GMS, Bian et al. 2017), the filter the
+ * paper applies to its guided matches by default with the neighbour
+ * threshold 6 (Sec. 5.1; Sec. 4.3).  The input matches are the rows i < m
+ * with 0 <= best[i] < n whose flags contain every bit of `require` (for
+ * example EGM_FLAG_HAS_BEST: every query's best candidate).  Both images are
+ * cut into grid x grid cells; a match from image-1 cell c to image-2 cell d
+ * is kept when d is the cell receiving most of c's matches (the lowest
+ * d = dy * grid + dx on ties) and the matches between the 3 x 3
+ * neighbourhoods of c and d number more than alpha * sqrt(n / 9), n the
+ * matches in c's neighbourhood; image-1 grids shifted by (0 or 1/2,
+ * 0 or 1/2) cell are tried and their keeps united.  Cells are computed as
+ * floor(x * grid / width) in FP64.
+ *   xy1 [m][2], xy2 [n][2] float64; best [m] int32; flags [m] uint8, updated
+ *   in place: EGM_FLAG_GMS set on kept input matches, cleared on every other
+ *   row.  Device pointers, asynchronous on the context stream.
+ *   width1 .. height2 > 0 (image sizes in pixels); 1 <= grid <= 48 (GMS
+ *   uses 20); alpha > 0 (6).  m <= 2^31 - 1.  EGM_ERR_ARG otherwise.
+ */
+egm_status egm_gms(egm_ctx *ctx, const double *xy1, int64_t m, const double *xy2, int64_t n, const int32_t *best,
+                   uint8_t *flags, int32_t width1, int32_t height1, int32_t width2, int32_t height2,
+                   uint32_t require, int32_t grid, double alpha);
 
 egm_status egm_intervals(egm_ctx *ctx, const egm_pair *pair, double *theta, double *delta,
                          double *e3, int32_t *mode);

@@ -16,6 +16,7 @@ the CUDA path.  Everything is FP64.
   roles of the images swapped, Sec. 3) and the cross-check: i -> j is mutual
   when j's best in the reverse direction is i.
 - ``mlp``: the learned-tolerance network in FP64 (see ``oracle/mlp.py``).
+- ``gms``: the grid motion-statistics filter of the matches (see ``oracle/gms.py``).
 """
 from __future__ import annotations
 

@@ -11,12 +11,12 @@ import ctypes as C
 
 from . import _egm
 from ._egm import (EGM_DESC_BIN, EGM_DESC_F32_L2, EGM_DESC_U8_L2, EGM_ERR_CAPACITY,
-                   EGM_FLAG_DEGENERATE_LINE, EGM_FLAG_HAS_BEST, EGM_FLAG_MUTUAL, EGM_FLAG_NO_SECOND,
+                   EGM_FLAG_DEGENERATE_LINE, EGM_FLAG_GMS, EGM_FLAG_HAS_BEST, EGM_FLAG_MUTUAL, EGM_FLAG_NO_SECOND,
                    EGM_FLAG_RATIO_PASS, EGM_OK, EgmError, check, load)
 
 __all__ = ["Matcher", "TolNet", "EgmError", "load", "row_bytes", "EGM_DESC_U8_L2", "EGM_DESC_F32_L2",
            "EGM_DESC_BIN", "EGM_FLAG_HAS_BEST", "EGM_FLAG_RATIO_PASS", "EGM_FLAG_NO_SECOND",
-           "EGM_FLAG_DEGENERATE_LINE", "EGM_FLAG_MUTUAL"]
+           "EGM_FLAG_DEGENERATE_LINE", "EGM_FLAG_MUTUAL", "EGM_FLAG_GMS"]
 
 
 def row_bytes(kind: int, dim: int) -> int:
@@ -278,6 +278,15 @@ class Matcher:
                                            _ptr(cnt)), "egm_compact_matches")
         k = int(cnt.item())
         return qi[:k], rj[:k]
+
+    def gms(self, xy1, xy2, best, flags, size1, size2, require=EGM_FLAG_HAS_BEST, grid=20, alpha=6.0):
+        """egm_gms: sets EGM_FLAG_GMS in `flags` (in place) on the input matches
+        the grid motion-statistics filter keeps; size1, size2 = (width, height)."""
+        m, n = int(xy1.shape[0]), int(xy2.shape[0])
+        check(self.lib.egm_gms(self.ctx, _ptr(xy1), m, _ptr(xy2), n, _ptr(best), _ptr(flags), int(size1[0]),
+                               int(size1[1]), int(size2[0]), int(size2[1]), int(require), int(grid), float(alpha)),
+              "egm_gms")
+        return flags
 
     def tolnet(self, params) -> "TolNet":
         """A learned-tolerance network on this context (egm_mlp_create)."""

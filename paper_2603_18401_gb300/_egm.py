@@ -31,6 +31,7 @@ EGM_FLAG_RATIO_PASS = 2
 EGM_FLAG_NO_SECOND = 4
 EGM_FLAG_DEGENERATE_LINE = 8
 EGM_FLAG_MUTUAL = 16
+EGM_FLAG_GMS = 32
 
 EGM_FORM_AUTO = 0
 EGM_FORM_PLAIN = 1
@@ -102,6 +103,8 @@ SIGNATURES = {
     "egm_pair_residuals": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.c_void_p, C.c_void_p, C.c_int64,
                                      C.c_void_p]),
     "egm_match_mutual": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.POINTER(egm_pair), C.POINTER(egm_out)]),
+    "egm_gms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                          C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, C.c_int32, C.c_double]),
     "egm_compact_matches": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_uint32, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
     "egm_sync": (C.c_int, [C.c_void_p]),

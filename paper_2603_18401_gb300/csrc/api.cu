@@ -62,6 +62,7 @@ struct egm_ctx {
     Scratch sc;
     DevBuf stage;  // host-path staging of inputs and outputs
     DevBuf compact;  // tile counts of egm_compact_matches
+    DevBuf gms;      // egm_gms: matches sorted by cell, decisions per grid shift
     // pinned host memory for the pair table and the status word
     // pinned staging slots of the pair-table uploads, used round-robin: the
     // host waits only when a slot's previous upload is still in flight
@@ -617,6 +618,7 @@ egm_status egm_destroy(egm_ctx *c) {
     c->sc.release();
     if (c->stage.ptr) cudaFree(c->stage.ptr);
     if (c->compact.ptr) cudaFree(c->compact.ptr);
+    if (c->gms.ptr) cudaFree(c->gms.ptr);
     for (int k = 0; k < egm_ctx::kSlots; k++) {
         if (c->h_table[k]) cudaFreeHost(c->h_table[k]);
         if (c->slot_ev[k]) cudaEventDestroy(c->slot_ev[k]);
@@ -785,6 +787,21 @@ egm_status egm_compact_matches(egm_ctx *c, const uint8_t *flags, const int32_t *
     EGM_TRY(grow(c->compact, sizeof(uint32_t) * (size_t)std::max<int64_t>(compact_tiles(m), 1)));
     EGM_TRY(launch_compact(flags, best, m, require, static_cast<uint32_t *>(c->compact.ptr), qi, rj, count,
                            c->stream));
+    if (c->params.sync) EGM_TRY(cudaStreamSynchronize(c->stream));
+    return EGM_OK;
+}
+
+egm_status egm_gms(egm_ctx *c, const double *xy1, int64_t m, const double *xy2, int64_t n, const int32_t *best,
+                   uint8_t *flags, int32_t width1, int32_t height1, int32_t width2, int32_t height2,
+                   uint32_t require, int32_t grid, double alpha) {
+    if (!c || m < 0 || m > INT32_MAX || n < 0 || grid < 1 || grid > 48 || !(alpha > 0.0) ||
+        !(alpha < INFINITY) || width1 <= 0 || height1 <= 0 || width2 <= 0 || height2 <= 0)
+        return EGM_ERR_ARG;
+    if (m > 0 && (!xy1 || !best || !flags || (n > 0 && !xy2))) return EGM_ERR_ARG;
+    EGM_TRY(cudaSetDevice(c->device));
+    EGM_TRY(grow(c->gms, gms_scratch_bytes(m, grid)));
+    EGM_TRY(launch_gms(xy1, m, xy2, n, best, flags, width1, height1, width2, height2, require, grid, alpha,
+                       c->gms.ptr, c->stream));
     if (c->params.sync) EGM_TRY(cudaStreamSynchronize(c->stream));
     return EGM_OK;
 }

@@ -124,3 +124,76 @@ def test_matching_recall_on_synthetic_ground_truth(mt):
         assert np.array_equal(qi, sel) and np.array_equal(rj, fw["best"][sel])
         rec, prec = recall_precision(qi, rj, sc.gt)
         assert rec > 0.85 and prec > 0.97, (rec, prec)
+
+
+# ------------------------------------------------------------------ GMS
+def gms_both(mt, xy1, xy2, best, flags, size1, size2, require=1, grid=20, alpha=6.0):
+    """egm_gms on the device and the oracle on the same inputs: identical flags."""
+    from oracle import gms as ogms
+
+    torch = mt.torch
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(mt.device)
+    f = dev(flags)
+    mt.gms(dev(xy1), dev(xy2), dev(best.astype(np.int32)), f, size1, size2, require, grid, alpha)
+    got = f.cpu().numpy()
+    want = ogms.gms(xy1, xy2, best, flags, size1, size2, require=require, grid=grid, alpha=alpha)
+    assert np.array_equal(got, want), (int((got != want).sum()), grid, alpha, require)
+    return got
+
+
+def test_gms_on_matches_of_the_configs(mt):
+    for sc in (synth.config1(), synth.config2("inside", 2.0), synth.config2("far", 4.0),
+               synth.config2("infinity", 1.0)):
+        o = run_match(mt, sc)
+        size = (sc.width, sc.height)
+        for req, grid, alpha in ((1, 20, 6.0), (RATIO, 20, 6.0), (1, 7, 4.5), (1, 48, 6.0), (1, 1, 2.0)):
+            got = gms_both(mt, sc.xy1, sc.xy2, o["best"], o["flags"], size, size, req, grid, alpha)
+        # GMS alone on the nearest neighbours (the paper's default filter):
+        # far more precise than its input, still most of the true pairs
+        got = gms_both(mt, sc.xy1, sc.xy2, o["best"], o["flags"], size, size)
+        truth = set(map(tuple, sc.gt.tolist()))
+        prec = lambda rows: np.mean([(i, o["best"][i]) in truth for i in rows])
+        kept = np.nonzero(got & 32)[0]
+        inputs = np.nonzero(o["best"] >= 0)[0]
+        assert len(kept) > 0.5 * len(truth) and prec(kept) > prec(inputs) + 0.15, (len(kept), prec(kept))
+
+
+def run_match(mt, sc):
+    d = mt.to_device(sc)
+    o = mt.match(d["xy1"], d["xy2"], d["F"], d["eps"], d["desc1"], d["desc2"], d["kind"], d["dim"], d["width"],
+                 d["height"])
+    return {k: v.cpu().numpy() for k, v in o.items()}
+
+
+@pytest.mark.parametrize("m", [0, 1, 5, 1000, 70000])
+def test_gms_edge_cases(mt, m):
+    rng = np.random.default_rng(m + 3)
+    n = max(m // 2, 1)
+    # clustered motion plus noise, points outside the image, duplicates, invalid rows
+    xy1 = rng.uniform([-50, -50], [1100, 800], (m, 2))
+    xy2 = rng.uniform([-50, -50], [900, 700], (n, 2))
+    best = rng.integers(-2, n + 2, m)
+    if m >= 1000:
+        k = m // 3
+        xy1[:k] = rng.uniform([0, 0], [1000, 700], (k, 2))
+        best[:k] = np.arange(k) % n
+        xy2[best[:k]] = xy1[:k] * 0.8 + 20.0
+        xy1[k:k + 50] = xy1[0]
+    flags = rng.integers(0, 64, m).astype(np.uint8)
+    for req in (0, 1, 3):
+        gms_both(mt, xy1, xy2, best, flags, (1024, 768), (800, 600), req)
+    gms_both(mt, xy1, xy2, best, flags, (1024, 768), (800, 600), 0, 13, 3.0)
+
+
+def test_gms_rejects_bad_arguments(mt):
+    from paper_2603_18401_gb300 import EgmError
+
+    torch = mt.torch
+    xy = torch.zeros((4, 2), dtype=torch.float64, device=mt.device)
+    best = torch.zeros(4, dtype=torch.int32, device=mt.device)
+    f = torch.zeros(4, dtype=torch.uint8, device=mt.device)
+    for kw in (dict(grid=0), dict(grid=49), dict(alpha=0.0), dict(alpha=float("inf")), dict(size1=(0, 10))):
+        args = dict(size1=(10, 10), size2=(10, 10), grid=20, alpha=6.0)
+        args.update(kw)
+        with pytest.raises(EgmError):
+            mt.gms(xy, xy, best, f, args["size1"], args["size2"], 1, args["grid"], args["alpha"])
