@@ -5,12 +5,13 @@ Workload (one GPU): the high-resolution single-pair configuration -- nine
 image pairs of 6048x4032 px with 16384 keypoints per image (70% true
 projections), epipole inside / far outside / at infinity, eps in {1, 2, 4} px,
 128-d uint8 descriptors.  One step matches all nine pairs, one pair per
-egm_match_pair call, in the library's automatic form (the banded tensor-core
-form for these descriptors; --form picks one).  Inputs are resident in HBM
+egm_match_pair call, in the library's automatic form (the plain form on
+sparse pairs, the banded tensor-core form where about 20 or more candidates
+per query are expected; --form forces one).  Inputs are resident in HBM
 before the timed region; L2 is flushed (a 256 MiB write) before every step
 and the flush is outside the CUDA-event-timed interval.
 
-Beside the headline: the same single-pair step in the plain CUDA-core form,
+Beside the headline: the same single-pair step in each forced form,
 the batched configuration (256 pairs, one CUDA-graph launch per step) in both
 forms, the end-to-end rate through host buffers, per-stage times, and the
 roofline of the dominant kernel.
@@ -65,6 +66,7 @@ def parse():
     ap.add_argument("--no-float", action="store_true", help="skip the float-descriptor batch")
     ap.add_argument("--float-pairs", type=int, default=64)
     ap.add_argument("--no-matching", action="store_true", help="skip the mutual-matching leg")
+    ap.add_argument("--no-sweeps", action="store_true", help="skip the tolerance and pose-noise sweeps")
     return ap.parse_args()
 
 
@@ -205,7 +207,7 @@ def cpu_segtree_rate(scs, seconds):
         out[name] = {"value": n_q / el, "unit": "queries/s", "pairs": k, "seconds": el,
                      "build_ms_per_pair": 1e3 * b / k, "match_ms_per_pair": 1e3 * mtime / k}
     out["cores"] = segtree.num_threads()
-    out["kind"] = "the paper's centred segment tree in C (OpenMP over queries; index built single-threaded)"
+    out["kind"] = "the paper's centred segment tree in C (OpenMP: intervals, subtree tasks, queries)"
     return out
 
 
@@ -340,6 +342,79 @@ def matching_leg(mt, torch, stream, scs, dev, steps):
     return {"mutual_ratio": mutual, "gms": gms, "timing": "CUDA events; each call reads the match count back"}
 
 
+def sweeps_leg(mt, torch, stream, reps):
+    """Analogues of the paper's tolerance sweep (Sec. 5.3: 25,000 keypoints
+    per image, tolerance up to 200 px) and pose-noise sweep (Sec. 5.5: noise
+    levels 0 to 3.3 at 200 px, against brute-force matching) on synthetic
+    6048x4032 pairs."""
+    import numpy as np
+    import synth
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def quality(sc, o):
+        best, flags = o["best"].cpu().numpy(), o["flags"].cpu().numpy()
+        ok = np.nonzero(flags & 2)[0]
+        got = set(zip(ok.tolist(), best[ok].tolist()))
+        truth = set(map(tuple, sc.gt.tolist()))
+        tp = len(got & truth)
+        return tp / max(len(truth), 1), tp / max(len(got), 1)
+
+    out = {}
+    sc = synth.config2("inside", 2.0, seed=5, scale=25000 / 16384)
+    d = mt.to_device(sc)
+    args = lambda eps, F=None: (d["xy1"], d["xy2"], d["F"] if F is None else F, eps, d["desc1"], d["desc2"],
+                                d["kind"], d["dim"], d["width"], d["height"])
+    rows = []
+    for eps in (1.0, 2.0, 5.0, 10.0, 20.0, 50.0, 100.0, 200.0):
+        o = mt.match(*args(eps), csr=True)
+        kbar = int(o["cand_offsets"][-1].item()) / sc.m
+        rec, prec = quality(sc, o)
+        row = {"eps_px": eps, "candidates_per_query": kbar, "matching_recall": rec, "matching_precision": prec}
+        for name, form in (("auto", 0), ("plain", 1), ("banded", 2)):
+            mt.set_params(form=form)
+            row[f"{name}_ms"] = timed(lambda: mt.match(*args(eps)))
+        mt.set_params(form=0)
+        row["candidates_csr_ms"] = timed(lambda: mt.match(*args(eps), csr=True))
+        rows.append(row)
+    out["tolerance"] = {"workload": "one 6048x4032 pair, 25,000 keypoints per image (17,500 true), epipole "
+                                    "inside, u8 128-d; matching time per pair (CUDA events, L2 warm)",
+                        "rows": rows}
+
+    sc = synth.config2("far", 200.0, seed=6)
+    d = mt.to_device(sc)
+    rows = []
+    qi = torch.as_tensor(sc.gt[:, 0], dtype=torch.int32).to(mt.device)
+    rj = torch.as_tensor(sc.gt[:, 1], dtype=torch.int32).to(mt.device)
+    for level in (0.0, 0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.3):
+        Fn = synth.perturb_pose(sc, level, seed=11) if level > 0 else sc.F
+        Ft = torch.as_tensor(np.ascontiguousarray(Fn).reshape(9)).to(mt.device)
+        res = mt.residuals(d["xy1"], d["xy2"], Ft, qi, rj).cpu().numpy()
+        o = mt.match(*args(200.0, Ft))
+        rec, prec = quality(sc, o)
+        mt.set_params(form=2)
+        ob = mt.match(*args(1e7, Ft))
+        mt.set_params(form=0)
+        brec, bprec = quality(sc, ob)
+        rows.append({"level": level, "candidate_recall": float(np.mean(res <= 200.0)), "matching_recall": rec,
+                     "matching_precision": prec, "bf_matching_recall": brec, "bf_matching_precision": bprec,
+                     "ms": timed(lambda: mt.match(*args(200.0, Ft)))})
+    out["pose_noise"] = {"workload": "one 6048x4032 pair, 16,384 keypoints per image, epipole far outside; F from "
+                                     "a perturbed pose (per-axis rotation U[-l, l] deg, translation U[-l/4, l/4] "
+                                     "units); eps 200 px vs brute force (eps 1e7 px)",
+                         "rows": rows}
+    return out
+
+
 def mlp_leg(mt, torch, stream):
     """Throughput of the learned-tolerance kernels on config-5-like features.
 
@@ -462,39 +537,57 @@ def run_ours(args):
     st = mt.sync()
     if st != 0:
         raise EgmError(st, "timed region")
-    # per-stage split from the library's stage events, in separate untimed steps
-    # (the events add host work to every call)
-    mt.set_timing(True)
-    for _ in range(20):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
-    tm = mt.timing()
-    mt.set_timing(False)
+    # per-stage split from the library's stage events, pair by pair, in
+    # separate untimed passes (the events add host work to every call); the
+    # library also reports which form each call ran
+    per_pair = []
+    for p, o in zip(pairs, ostr):
+        mt.set_timing(True)
+        for _ in range(20):
+            flush.zero_()
+            if mt.egm_match_pair(p, o) != 0:
+                raise EgmError(mt.sync(), "timing pass")
+        torch.cuda.synchronize()
+        t = mt.timing()
+        mt.set_timing(False)
+        c = max(t["calls"], 1)
+        per_pair.append(({k[:-3]: t[k] / c for k in t if k.endswith("_ms")}, 2 * t["banded_calls"] > t["calls"]))
     ms = sum(a.elapsed_time(b) for a, b in evs)
     ms = max_over_ranks(ms, world, local)
     q_per_step = sum(s.m for s in scs)
     value = world * q_per_step * args.steps / (ms * 1e-3)
 
-    # dominant kernel: the matching kernel of the form in use ("stab" stage)
-    calls = max(tm["calls"], 1)
-    stage_ms = {k[:-3]: tm[k] / calls for k in tm if k.endswith("_ms")}
+    # dominant kernel: the matching kernel ("stab" stage) that takes the most
+    # time over the step -- stab_kernel on the pairs run in the plain form,
+    # band_kernel on those run in the banded form
+    stage_ms = {}
+    for st_ms, _ in per_pair:
+        for k, v in st_ms.items():
+            stage_ms[k] = stage_ms.get(k, 0.0) + v / len(per_pair)
     dom = max(stage_ms, key=stage_ms.get)
-    # the automatic form runs the plain form on single pairs (128 tiles, fewer
-    # than two per SM) and the banded form on the batch
-    banded = args.form == "banded"
-    kernel = "band_kernel" if banded else "stab_kernel"
-    row = scs[0].desc1.shape[1]
-    if banded:
-        # every query's packed operand row (256 B), sorted record (48 B) and
-        # result (17 B) once; every reference's packed row (256 B), record
-        # (16 B) and norm (4 B) once
-        kbytes = sum(s.m * (256 + 48 + 17) + s.n * (256 + 16 + 4) for s in scs) / len(scs)
-    else:
+    n_banded = sum(1 for _, b in per_pair if b)
+
+    def kernel_bytes(sc, band):
+        if band:
+            # every query's packed operand row (256 B), sorted record (48 B) and
+            # result (17 B) once; every reference's packed row (256 B), record
+            # (16 B) and norm (4 B) once
+            return sc.m * (256 + 48 + 17) + sc.n * (256 + 16 + 4)
         # every query's line record (48 B), descriptor and result (17 B) once;
         # every reference's record (16 B) and descriptor once
-        kbytes = sum(s.m * (48 + row + 17) + s.n * (16 + row) for s in scs) / len(scs)
-    k_s = stage_ms["stab"] * 1e-3
+        row = sc.desc1.shape[1]
+        return sc.m * (48 + row + 17) + sc.n * (16 + row)
+
+    kt = {False: 0.0, True: 0.0}
+    kb = {False: 0.0, True: 0.0}
+    for (st_ms, b), sc in zip(per_pair, scs):
+        kt[b] += st_ms["stab"]
+        kb[b] += kernel_bytes(sc, b)
+    banded = kt[True] > kt[False]
+    kernel = "band_kernel" if banded else "stab_kernel"
+    npk = n_banded if banded else len(scs) - n_banded
+    kbytes = kb[banded] / max(npk, 1)
+    k_s = kt[banded] / max(npk, 1) * 1e-3
     peak, peak_kind = measured_peaks()
     achieved = kbytes / k_s / 1e9
     prof = kernel_profile(kernel)
@@ -502,31 +595,36 @@ def run_ours(args):
                 "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": prof.get("dram_bytes_per_launch") if prof else None,
                 "tensor_pipe_active_pct": prof.get("tensor_pipe_active_pct") if prof else None,
-                "avg_launch_us": stage_ms["stab"] * 1e3, "algorithmic_bytes_per_launch": kbytes,
+                "avg_launch_us": k_s * 1e6, "algorithmic_bytes_per_launch": kbytes,
+                "launches_averaged": f"{npk} of the {len(scs)} pairs run this kernel",
                 "stage_us_per_pair": {k: round(v * 1e3, 2) for k, v in stage_ms.items()},
-                "dominant_stage": dom}
+                "dominant_stage": dom,
+                "pairs_banded": n_banded}
 
-    # the same step in the other form, for comparison
+    # the same step in each forced form (or the other one), for comparison
     other_form = None
     if not args.no_compare:
-        other = 2 if not banded else 1
-        mt.set_params(form=other)
-        for _ in range(3):
-            step()
-        torch.cuda.synchronize()
-        pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.compare_steps)]
-        for k in range(args.compare_steps):
-            flush.zero_()
-            pe[k][0].record(stream)
-            step()
-            pe[k][1].record(stream)
-        torch.cuda.synchronize()
-        pms = max_over_ranks(sum(a.elapsed_time(b) for a, b in pe), world, local)
-        other_form = {"value": world * q_per_step * args.compare_steps / (pms * 1e-3), "unit": "queries/s",
-                      "ms_per_step": pms / args.compare_steps, "steps": args.compare_steps,
-                      "form": ("banded: tcgen05 tiles of 128 queries" if other == 2
-                               else "plain: windowed stabbing, CUDA-core descriptor distances")}
+        other_form = {}
+        forms = (1, 2) if args.form == "auto" else ((2,) if args.form == "plain" else (1,))
+        for other in forms:
+            mt.set_params(form=other)
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.compare_steps)]
+            for k in range(args.compare_steps):
+                flush.zero_()
+                pe[k][0].record(stream)
+                step()
+                pe[k][1].record(stream)
+            torch.cuda.synchronize()
+            pms = max_over_ranks(sum(a.elapsed_time(b) for a, b in pe), world, local)
+            other_form["banded" if other == 2 else "plain"] = {
+                "value": world * q_per_step * args.compare_steps / (pms * 1e-3), "unit": "queries/s",
+                "ms_per_step": pms / args.compare_steps, "steps": args.compare_steps,
+                "form": ("banded: tcgen05 tiles of 128 queries" if other == 2
+                         else "plain: windowed stabbing, CUDA-core descriptor distances")}
         mt.set_params(form={"auto": 0, "plain": 1, "banded": 2}[args.form])
 
     # end to end: host (pinned) buffers through egm_match_pair_host, copies inside
@@ -660,6 +758,11 @@ def run_ours(args):
     if not args.no_matching:
         matching = matching_leg(mt, torch, stream, scs, dev, args.compare_steps)
 
+    # tolerance and pose-noise sweeps
+    sweeps = None
+    if not args.no_sweeps:
+        sweeps = sweeps_leg(mt, torch, stream, 10)
+
     # learned tolerance: training steps and inference of the 5-64-64-64-1 network
     mlp = None
     if not args.no_mlp:
@@ -667,13 +770,13 @@ def run_ours(args):
 
     # kernels per match call: geometry, prep, bucket count, bucket scan, and
     # either the stab kernel or the query sort, pack and band kernels
-    launches_per_pair = 7 if banded else 5
+    launches = 7 * n_banded + 5 * (len(scs) - n_banded)
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": ("f64/f32 geometry, u8 descriptors as bf16 on tensor cores (exact integer distances)" if banded
-                  else "f64/f32 geometry, u8 descriptors (int32 distances)"), "data": "synthetic",
+        "dtype": ("f64/f32 geometry; u8 descriptors: int32 distances (plain form) and bf16 tensor-core "
+                  "products with f32 sums (banded form), both exact integers"), "data": "synthetic",
         "config": {"workload": WORKLOAD, "pairs_per_step": len(scs), "queries_per_step": q_per_step,
                    "form": f"{args.form} one-pair (egm_match_pair)", "l2": "flushed before every step (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
@@ -681,11 +784,12 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(d2h), "api": "egm_match_pair_host", "steps": args.e2e_steps},
         "roofline": roofline,
         "batched": batched,
-        "other_form_one_pair": other_form,
+        "forced_forms_one_pair": other_form,
         "learned_tolerance": mlp,
         "matching": matching,
+        "sweeps": sweeps,
         "clocks": clk,
-        "gpu_launches": launches_per_pair * len(scs) * args.steps,
+        "gpu_launches": launches * args.steps,
     }
     if cpu is not None:
         rate, cores, npairs, el = cpu

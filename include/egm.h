@@ -144,7 +144,10 @@ typedef struct egm_out {
 /* Matching forms. */
 enum {
     EGM_FORM_AUTO = 0,     /* library choice: banded for batches with more than two
-                              128-query tiles per SM, plain otherwise */
+                              128-query tiles per SM, or when every pair has u8
+                              descriptors, a scalar eps and an expected 20 or more
+                              candidates per query (2 eps n / (W H) x 0.8 of the
+                              image diagonal); plain otherwise */
     EGM_FORM_PLAIN = 1,    /* windowed stabbing + CUDA-core descriptor distances */
     EGM_FORM_BANDED = 2    /* angle-banded tiles, descriptor dot products on tensor cores */
 };
@@ -351,12 +354,17 @@ egm_status egm_get_stats(egm_ctx *ctx, egm_stats *stats);
  * enabled.  Times are sums over the calls since the last egm_set_timing(1). */
 typedef struct egm_timing {
     double geometry_ms;   /* epipole and key frame */
-    double prep_ms;       /* reference keys and query lines */
-    double sort_ms;       /* radix sort by angle */
-    double post_sort_ms;  /* sorted records and bucket tables */
-    double stab_ms;       /* stabbing, exact test, descriptors, top-2, ratio */
+    double prep_ms;       /* reference keys, query lines, bucket tables zeroed */
+    double sort_ms;       /* reference counting sort by (level, angle bucket):
+                             bucket counts, scan, placement of the records */
+    double post_sort_ms;  /* banded form: query order and operand packing;
+                             plain form: nothing */
+    double stab_ms;       /* the matching kernel (plain: stabbing, exact test,
+                             descriptors, top-2, ratio; banded: the same on
+                             tensor-core tiles) */
     double csr_ms;        /* candidate lists: count, scan, fill, row sort */
     int64_t calls;        /* match calls timed */
+    int64_t banded_calls; /* of which ran the banded form */
 } egm_timing;
 
 /* Enables (1, also resets the sums) or disables (0) per-stage timing. */

@@ -160,12 +160,15 @@ static void swap_iv(Interval *a, Interval *b) {
     *b = t;
 }
 
-/* Builds the subtree over items[lo, hi); returns its node index or -1. */
+/* Builds the subtree over items[lo, hi); returns its node index or -1.
+ * Subtrees of more than 2048 intervals are built as parallel tasks; each
+ * uses the scratch range [lo, hi) and takes its node index atomically. */
 static int32_t build_node(Index *ix, int64_t lo, int64_t hi, double *scratch) {
     if (lo >= hi) return -1;
     int64_t cnt = hi - lo;
-    for (int64_t k = 0; k < cnt; k++) scratch[k] = 0.5 * (ix->items[lo + k].lo + ix->items[lo + k].hi);
-    double c = nth_smallest(scratch, cnt, cnt / 2);
+    double *sc = scratch + lo;
+    for (int64_t k = 0; k < cnt; k++) sc[k] = 0.5 * (ix->items[lo + k].lo + ix->items[lo + k].hi);
+    double c = nth_smallest(sc, cnt, cnt / 2);
     /* three-way partition: [lo, a) left of c, [a, b) containing c, [b, hi) right */
     int64_t a = lo, k = lo, b = hi;
     while (k < b) {
@@ -177,7 +180,10 @@ static int32_t build_node(Index *ix, int64_t lo, int64_t hi, double *scratch) {
         else
             k++;
     }
-    int32_t id = (int32_t)ix->nnodes++;
+    int64_t id64;
+#pragma omp atomic capture
+    id64 = ix->nnodes++;
+    int32_t id = (int32_t)id64;
     Node *nd = &ix->nodes[id];
     nd->split = c;
     nd->b0 = a;
@@ -188,8 +194,16 @@ static int32_t build_node(Index *ix, int64_t lo, int64_t hi, double *scratch) {
         if (ix->items[t].lo < nd->min_lo) nd->min_lo = ix->items[t].lo;
         if (ix->items[t].hi > nd->max_hi) nd->max_hi = ix->items[t].hi;
     }
-    int32_t l = build_node(ix, lo, a, scratch);
-    int32_t r = build_node(ix, b, hi, scratch);
+    int32_t l, r;
+    if (cnt > 2048) {
+#pragma omp task shared(l)
+        l = build_node(ix, lo, a, scratch);
+        r = build_node(ix, b, hi, scratch);
+#pragma omp taskwait
+    } else {
+        l = build_node(ix, lo, a, scratch);
+        r = build_node(ix, b, hi, scratch);
+    }
     ix->nodes[id].left = l;
     ix->nodes[id].right = r;
     return id;
@@ -246,7 +260,9 @@ static int build_index(Index *ix, int64_t m, const double *xy1, int64_t n, const
     double pad = 0.0;
     if (exact) {
         double worst = 0.0, R = 0.0;
-        for (int64_t i = 0; i < m; i++) {
+        int64_t i;
+#pragma omp parallel for reduction(max : worst) schedule(static)
+        for (i = 0; i < m; i++) {
             double l[3];
             line_of(F, xy1[2 * i], xy1[2 * i + 1], l);
             double nn = hypot(l[0], l[1]);
@@ -271,37 +287,54 @@ static int build_index(Index *ix, int64_t m, const double *xy1, int64_t n, const
             pad = worst * 1.000001 + 1e-6;
         }
     }
+    /* up to two intervals per keypoint in slots 2j, 2j + 1, then compacted */
+    Interval *tmp = (Interval *)malloc(sizeof(Interval) * (size_t)(2 * n + 1));
+    uint8_t *cnt = (uint8_t *)malloc((size_t)n + 1);
     ix->items = (Interval *)malloc(sizeof(Interval) * (size_t)(2 * n + 1));
-    if (!ix->items) return -1;
-    int64_t k = 0;
-    for (int64_t j = 0; j < n; j++) {
+    if (!tmp || !cnt || !ix->items) {
+        free(tmp);
+        free(cnt);
+        return -1;
+    }
+    int64_t j;
+#pragma omp parallel for schedule(static)
+    for (j = 0; j < n; j++) {
         double x = xy2[2 * j], y = xy2[2 * j + 1], eps = eps_at(eps2, eps_scalar, j);
+        Interval *o = tmp + 2 * j;
+        cnt[j] = 1;
         if (ix->parallel) {
             double key = ix->nx * (x - ix->cx) + ix->ny * (y - ix->cy);
             double w = eps + pad + (exact ? 1e-13 * fabs(key) + 1e-9 : 0.0);
-            ix->items[k++] = (Interval){key - w, key + w, (int32_t)j};
+            o[0] = (Interval){key - w, key + w, (int32_t)j};
             continue;
         }
         double dx = x - ix->ex, dy = y - ix->ey;
         double d = hypot(dx, dy);
         double r = exact ? eps + pad + 1e-13 * d : eps;
         if (d <= r) {
-            ix->items[k++] = (Interval){0.0, M_PI, (int32_t)j};
+            o[0] = (Interval){0.0, M_PI, (int32_t)j};
             continue;
         }
         double th = fold_pi(atan2(dy, dx));
         double de = asin(r / d);
         double lo = th - de, hi = th + de;
         if (lo < 0.0) {
-            ix->items[k++] = (Interval){lo + M_PI, M_PI, (int32_t)j};
-            ix->items[k++] = (Interval){0.0, hi, (int32_t)j};
+            o[0] = (Interval){lo + M_PI, M_PI, (int32_t)j};
+            o[1] = (Interval){0.0, hi, (int32_t)j};
+            cnt[j] = 2;
         } else if (hi > M_PI) {
-            ix->items[k++] = (Interval){lo, M_PI, (int32_t)j};
-            ix->items[k++] = (Interval){0.0, hi - M_PI, (int32_t)j};
+            o[0] = (Interval){lo, M_PI, (int32_t)j};
+            o[1] = (Interval){0.0, hi - M_PI, (int32_t)j};
+            cnt[j] = 2;
         } else {
-            ix->items[k++] = (Interval){lo, hi, (int32_t)j};
+            o[0] = (Interval){lo, hi, (int32_t)j};
         }
     }
+    int64_t k = 0;
+    for (j = 0; j < n; j++)
+        for (int t = 0; t < cnt[j]; t++) ix->items[k++] = tmp[2 * j + t];
+    free(tmp);
+    free(cnt);
     ix->nitems = k;
     ix->nodes = (Node *)malloc(sizeof(Node) * (size_t)(k + 1));
     double *scratch = (double *)malloc(sizeof(double) * (size_t)(k + 1));
@@ -309,7 +342,11 @@ static int build_index(Index *ix, int64_t m, const double *xy1, int64_t n, const
         free(scratch);
         return -1;
     }
-    ix->root = build_node(ix, 0, k, scratch);
+    int32_t root = -1;
+#pragma omp parallel
+#pragma omp single
+    root = build_node(ix, 0, k, scratch);
+    ix->root = root;
     free(scratch);
     return 0;
 }

@@ -89,7 +89,8 @@ class Matcher:
     def timing(self) -> dict:
         t = _egm.egm_timing()
         check(self.lib.egm_get_timing(self.ctx, C.byref(t)), "egm_get_timing")
-        return {k: (int(getattr(t, k)) if k == "calls" else float(getattr(t, k))) for k, _ in t._fields_}
+        return {k: (int(getattr(t, k)) if k in ("calls", "banded_calls") else float(getattr(t, k)))
+                for k, _ in t._fields_}
 
     def stats(self) -> dict:
         s = _egm.egm_stats()

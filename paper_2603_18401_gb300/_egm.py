@@ -70,7 +70,7 @@ class egm_stats(C.Structure):
 class egm_timing(C.Structure):
     _fields_ = [("geometry_ms", C.c_double), ("prep_ms", C.c_double), ("sort_ms", C.c_double),
                 ("post_sort_ms", C.c_double), ("stab_ms", C.c_double), ("csr_ms", C.c_double),
-                ("calls", C.c_int64)]
+                ("calls", C.c_int64), ("banded_calls", C.c_int64)]
 
 
 # name -> (restype, argtypes); every symbol include/egm.h declares

@@ -79,6 +79,7 @@ struct egm_ctx {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<size_t> ev_calls;   // first event of each timed call
+    std::vector<bool> ev_band;      // whether that call ran the banded form
     egm_timing tsum{};
     // the banded form sorts the queries on a second stream, beside the reference sort
     cudaStream_t side = nullptr;
@@ -159,6 +160,7 @@ struct Plan {
     int max_n = 0;
     bool band_ok = false;           // every pair fits the banded form
     bool has_float = false;         // some pair has float descriptors
+    bool dense_u8 = false;          // every pair u8 with a scalar tolerance and >= 20 estimated candidates per query
 };
 
 egm_status make_plan(const egm_pair *pairs, int npairs, Plan &pl) {
@@ -201,6 +203,16 @@ egm_status make_plan(const egm_pair *pairs, int npairs, Plan &pl) {
     pl.offs.resize(3 * (size_t)(npairs + 1));
     const int tm = band_tile_queries();
     pl.band_ok = true;
+    // candidates per query of a pair, estimated as the expected count within
+    // eps of a line crossing the image: 2 eps (n / (W H)) L, with the mean
+    // chord L taken as 0.8 of the diagonal
+    pl.dense_u8 = npairs > 0;
+    for (int p = 0; p < npairs; p++) {
+        const egm_pair &A = pairs[p];
+        const double W = A.width, H = A.height;
+        const double kbar = 2.0 * A.eps_scalar * (double)A.n / (W * H) * 0.8 * std::sqrt(W * W + H * H);
+        pl.dense_u8 = pl.dense_u8 && has_desc(&A) && A.kind == EGM_DESC_U8_L2 && !A.eps2 && kbar >= 20.0;
+    }
     for (int p = 0; p <= npairs; p++) {
         pl.offs[p] = pl.qoffs[p];
         pl.offs[(npairs + 1) + p] = pl.roffs[p];
@@ -233,13 +245,17 @@ size_t offs_entries(int npairs, int64_t nq) {
 }
 
 // The banded form runs when every pair fits it, no candidate lists are asked
-// for, and it is requested -- or left to the library and the call has more
-// than two tiles per SM.  With fewer, every CTA of the band kernel takes one
-// latency-bound tile and the plain form (no query sort, no packing) finishes
-// first; with more, the banded form's throughput wins.
+// for, and it is requested -- or left to the library and either the call has
+// more than two tiles per SM or its u8 pairs are dense (about 20 or more
+// candidates per query).  With few tiles of sparse pairs every CTA of the
+// band kernel takes one latency-bound tile and the plain form (no query
+// sort, no packing) finishes first; with many tiles the banded form's
+// throughput wins, and on dense pairs its tensor-core distances beat one
+// CUDA-core distance per candidate.
 egm_status choose_band(const Plan &pl, const egm_params &prm, bool csr, int sms, bool &band) {
     band = pl.band_ok && !csr &&
-           (prm.form == EGM_FORM_BANDED || (prm.form == EGM_FORM_AUTO && pl.ntiles > 2 * (int64_t)sms));
+           (prm.form == EGM_FORM_BANDED ||
+            (prm.form == EGM_FORM_AUTO && (pl.ntiles > 2 * (int64_t)sms || pl.dense_u8)));
     if (prm.form == EGM_FORM_BANDED && !band) return EGM_ERR_UNIMPLEMENTED;
     return EGM_OK;
 }
@@ -423,6 +439,7 @@ cudaError_t enqueue_pipeline(const Launch &L, Scratch &sc, bool csr, int max_n, 
     if (tc && tc->timing_on) {
         tb = tc->ev_used;
         tc->ev_calls.push_back(tb);
+        tc->ev_band.push_back(band);
         tc->ev_used += kStages + 1;
     } else {
         tc = nullptr;
@@ -1047,6 +1064,7 @@ egm_status egm_set_timing(egm_ctx *c, int32_t enable) {
     c->timing_on = enable != 0;
     c->ev_used = 0;
     c->ev_calls.clear();
+    c->ev_band.clear();
     memset(&c->tsum, 0, sizeof(c->tsum));
     return EGM_OK;
 }
@@ -1055,7 +1073,8 @@ egm_status egm_get_timing(egm_ctx *c, egm_timing *t) {
     if (!c || !t) return EGM_ERR_ARG;
     EGM_TRY(cudaSetDevice(c->device));
     EGM_TRY(cudaStreamSynchronize(c->stream));
-    for (size_t b : c->ev_calls) {
+    for (size_t q = 0; q < c->ev_calls.size(); q++) {
+        const size_t b = c->ev_calls[q];
         float ms[kStages];
         for (int k = 0; k < kStages; k++)
             EGM_TRY(cudaEventElapsedTime(&ms[k], c->ev_pool[b + k], c->ev_pool[b + k + 1]));
@@ -1066,8 +1085,10 @@ egm_status egm_get_timing(egm_ctx *c, egm_timing *t) {
         c->tsum.stab_ms += ms[4];
         c->tsum.csr_ms += ms[5];
         c->tsum.calls += 1;
+        c->tsum.banded_calls += c->ev_band[q] ? 1 : 0;
     }
     c->ev_calls.clear();
+    c->ev_band.clear();
     c->ev_used = 0;
     *t = c->tsum;
     return EGM_OK;

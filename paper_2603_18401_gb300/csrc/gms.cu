@@ -12,6 +12,10 @@
 //   keep       d == d*(c) and S(c) > alpha * sqrt(sum_o N[c + o] / 9),
 //              the union over the four shifts
 //
+// gms_prep_kernel: one thread per row; the image-1 cell under each shift and
+// the image-2 cell, each coordinate divided once (x * G / W, then + 1/2 for
+// the shifted grids: the same operations, in the same order, as the cell
+// formula), packed as 16-bit cell numbers.
 // gms_cells_kernel: one block per shift.  Counting sort of the matches by
 // image-1 cell (shared-memory counts, the image-2 cells placed in global
 // scratch), then a warp per cell: a shared-memory histogram over image-2
@@ -28,15 +32,18 @@ constexpr int kGmsThreads = 1024;
 constexpr int kGmsWarps = kGmsThreads / 32;
 constexpr int kGmsSmemBudget = 160 * 1024;
 
-__device__ __forceinline__ int gms_cell(double v, int G, double size, double shift, int top) {
-    const double t = __dadd_rn(__ddiv_rn(__dmul_rn(v, (double)G), size), shift);
+constexpr uint16_t kNoCell = 0xFFFF;
+
+__device__ __forceinline__ int clamp_cell(double t, int top) {
     const double f = floor(t);
     if (!(f > 0.0)) return 0;  // also NaN
     return f >= (double)top ? top : (int)f;
 }
 
-__device__ __forceinline__ double shift_x(int s) { return (s & 1) ? 0.5 : 0.0; }
-__device__ __forceinline__ double shift_y(int s) { return (s & 2) ? 0.5 : 0.0; }
+// x * G / size, rounded as written
+__device__ __forceinline__ double grid_coord(double v, int G, double size) {
+    return __ddiv_rn(__dmul_rn(v, (double)G), size);
+}
 
 struct GmsArgs {
     const double *xy1, *xy2;
@@ -49,41 +56,51 @@ struct GmsArgs {
     double alpha;
 };
 
-__device__ __forceinline__ bool gms_input(const GmsArgs &a, int64_t i, int32_t &j) {
-    j = a.best[i];
-    return j >= 0 && j < a.n && (a.flags[i] & a.require) == a.require;
+// c1[i] = image-1 cell under shifts 0..3 (x shift = bit 0, y shift = bit 1),
+// c2[i] = image-2 cell, kNoCell where row i is not an input match
+__global__ void gms_prep_kernel(GmsArgs a, ushort4 *c1, uint16_t *c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.m) return;
+    const int32_t j = a.best[i];
+    const bool in = j >= 0 && j < a.n && (a.flags[i] & a.require) == a.require;
+    if (!in) {
+        c1[i] = make_ushort4(kNoCell, kNoCell, kNoCell, kNoCell);
+        c2[i] = kNoCell;
+        return;
+    }
+    const int G = a.G, G1 = G + 1;
+    const double tx = grid_coord(a.xy1[2 * i], G, a.w1), ty = grid_coord(a.xy1[2 * i + 1], G, a.h1);
+    const int x0 = clamp_cell(tx, G), x1 = clamp_cell(__dadd_rn(tx, 0.5), G);
+    const int y0 = clamp_cell(ty, G), y1 = clamp_cell(__dadd_rn(ty, 0.5), G);
+    c1[i] = make_ushort4((uint16_t)(y0 * G1 + x0), (uint16_t)(y0 * G1 + x1), (uint16_t)(y1 * G1 + x0),
+                         (uint16_t)(y1 * G1 + x1));
+    const int dx = clamp_cell(grid_coord(a.xy2[2 * (int64_t)j], G, a.w2), G - 1);
+    const int dy = clamp_cell(grid_coord(a.xy2[2 * (int64_t)j + 1], G, a.h2), G - 1);
+    c2[i] = (uint16_t)(dy * G + dx);
 }
 
-__device__ __forceinline__ int cell1(const GmsArgs &a, int64_t i, int s) {
-    const int G1 = a.G + 1;
-    const int cx = gms_cell(a.xy1[2 * i], a.G, a.w1, shift_x(s), a.G);
-    const int cy = gms_cell(a.xy1[2 * i + 1], a.G, a.h1, shift_y(s), a.G);
-    return cy * G1 + cx;
-}
-
-__device__ __forceinline__ int cell2(const GmsArgs &a, int32_t j) {
-    const int dx = gms_cell(a.xy2[2 * (int64_t)j], a.G, a.w2, 0.0, a.G - 1);
-    const int dy = gms_cell(a.xy2[2 * (int64_t)j + 1], a.G, a.h2, 0.0, a.G - 1);
-    return dy * a.G + dx;
+__device__ __forceinline__ uint16_t shift_cell(const ushort4 &v, int s) {
+    return s == 0 ? v.x : s == 1 ? v.y : s == 2 ? v.z : v.w;
 }
 
 // dynamic shared memory: count, start, cursor, dstar [(G + 1)^2] int32, then
 // the histograms of `hw` warps, G^2 uint32 each
-__global__ void __launch_bounds__(kGmsThreads) gms_cells_kernel(GmsArgs a, int hw, uint16_t *dsorted,
-                                                                 int32_t *decision) {
+__global__ void __launch_bounds__(kGmsThreads) gms_cells_kernel(int64_t m, int G, double alpha, int hw,
+                                                                 const ushort4 *c1, const uint16_t *c2,
+                                                                 uint16_t *dsorted, int32_t *decision) {
     extern __shared__ int32_t gsm[];
-    const int G = a.G, G1 = G + 1, C1 = G1 * G1, C2 = G * G;
+    const int G1 = G + 1, C1 = G1 * G1, C2 = G * G;
     const int s = blockIdx.x;
     int32_t *count = gsm, *start = gsm + C1, *cursor = gsm + 2 * C1, *dstar = gsm + 3 * C1;
     uint32_t *hist = reinterpret_cast<uint32_t *>(gsm + 4 * C1);
-    uint16_t *ds = dsorted + (int64_t)s * a.m;
+    uint16_t *ds = dsorted + (int64_t)s * m;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     for (int k = threadIdx.x; k < C1; k += kGmsThreads) count[k] = 0, cursor[k] = 0;
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < a.m; i += kGmsThreads) {
-        int32_t j;
-        if (gms_input(a, i, j)) atomicAdd(&count[cell1(a, i, s)], 1);
+    for (int64_t i = threadIdx.x; i < m; i += kGmsThreads) {
+        const uint16_t c = shift_cell(c1[i], s);
+        if (c != kNoCell) atomicAdd(&count[c], 1);
     }
     __syncthreads();
     if (warp == 0) {  // exclusive scan of the counts
@@ -101,11 +118,9 @@ __global__ void __launch_bounds__(kGmsThreads) gms_cells_kernel(GmsArgs a, int h
         }
     }
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < a.m; i += kGmsThreads) {
-        int32_t j;
-        if (!gms_input(a, i, j)) continue;
-        const int c = cell1(a, i, s);
-        ds[start[c] + atomicAdd(&cursor[c], 1)] = (uint16_t)cell2(a, j);
+    for (int64_t i = threadIdx.x; i < m; i += kGmsThreads) {
+        const uint16_t c = shift_cell(c1[i], s);
+        if (c != kNoCell) ds[start[c] + atomicAdd(&cursor[c], 1)] = c2[i];
     }
     __syncthreads();
 
@@ -163,33 +178,40 @@ __global__ void __launch_bounds__(kGmsThreads) gms_cells_kernel(GmsArgs a, int h
                 for (int k = lane; k < count[ac]; k += 32) k0 += lst[k] == target;
                 S += __reduce_add_sync(0xffffffffu, k0);
             }
-            const double thr = __dmul_rn(a.alpha, __dsqrt_rn(__ddiv_rn((double)total, 9.0)));
+            const double thr = __dmul_rn(alpha, __dsqrt_rn(__ddiv_rn((double)total, 9.0)));
             if ((double)S > thr) res = d;
         }
         if (lane == 0) decision[(int64_t)s * C1 + c] = res;
     }
 }
 
-__global__ void gms_flag_kernel(GmsArgs a, const int32_t *decision, uint8_t *flags) {
+__global__ void gms_flag_kernel(int64_t m, int G, const ushort4 *c1, const uint16_t *c2, const int32_t *decision,
+                                uint8_t *flags) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.m) return;
-    const int C1 = (a.G + 1) * (a.G + 1);
-    int32_t j;
+    if (i >= m) return;
+    const int C1 = (G + 1) * (G + 1);
+    const uint16_t d = c2[i];
     bool keep = false;
-    if (gms_input(a, i, j)) {
-        const int d = cell2(a, j);
-#pragma unroll
-        for (int s = 0; s < 4; s++) keep |= decision[s * C1 + cell1(a, i, s)] == d;
+    if (d != kNoCell) {
+        const ushort4 c = c1[i];
+        keep = decision[c.x] == d || decision[C1 + c.y] == d || decision[2 * C1 + c.z] == d ||
+               decision[3 * C1 + c.w] == d;
     }
-    const uint8_t f = a.flags[i];
+    const uint8_t f = flags[i];
     flags[i] = (uint8_t)((f & ~EGM_FLAG_GMS) | (keep ? EGM_FLAG_GMS : 0));
 }
 
 }  // namespace
 
+// scratch: sorted lists 4 m x 16 bit | decisions 4 (G + 1)^2 x 32 bit |
+// image-1 cells m x 64 bit | image-2 cells m x 16 bit
+namespace {
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+}
+
 size_t gms_scratch_bytes(int64_t m, int grid) {
-    const size_t ds = ((size_t)4 * (size_t)m * sizeof(uint16_t) + 255) & ~(size_t)255;
-    return ds + (size_t)4 * (grid + 1) * (grid + 1) * sizeof(int32_t);
+    return align256((size_t)4 * m * sizeof(uint16_t)) + align256((size_t)4 * (grid + 1) * (grid + 1) * sizeof(int32_t)) +
+           align256((size_t)m * sizeof(ushort4)) + align256((size_t)m * sizeof(uint16_t));
 }
 
 cudaError_t launch_gms(const double *xy1, int64_t m, const double *xy2, int64_t n, const int32_t *best,
@@ -201,13 +223,20 @@ cudaError_t launch_gms(const double *xy1, int64_t m, const double *xy2, int64_t 
     const size_t fixed = (size_t)4 * C1 * sizeof(int32_t);
     const int hw = (int)std::min<size_t>(kGmsWarps, (kGmsSmemBudget - fixed) / ((size_t)C2 * sizeof(uint32_t)));
     const size_t smem = fixed + (size_t)hw * C2 * sizeof(uint32_t);
-    uint16_t *ds = static_cast<uint16_t *>(scratch);
-    int32_t *decision = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) +
-                                                    (((size_t)4 * (size_t)m * sizeof(uint16_t) + 255) & ~(size_t)255));
+    char *p = static_cast<char *>(scratch);
+    uint16_t *ds = reinterpret_cast<uint16_t *>(p);
+    p += align256((size_t)4 * m * sizeof(uint16_t));
+    int32_t *decision = reinterpret_cast<int32_t *>(p);
+    p += align256((size_t)4 * C1 * sizeof(int32_t));
+    ushort4 *c1 = reinterpret_cast<ushort4 *>(p);
+    p += align256((size_t)m * sizeof(ushort4));
+    uint16_t *c2 = reinterpret_cast<uint16_t *>(p);
     cudaError_t e = cudaFuncSetAttribute(gms_cells_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    gms_cells_kernel<<<4, kGmsThreads, smem, st>>>(a, hw, ds, decision);
-    gms_flag_kernel<<<(int)((m + 255) / 256), 256, 0, st>>>(a, decision, flags);
+    const int blocks = (int)((m + 255) / 256);
+    gms_prep_kernel<<<blocks, 256, 0, st>>>(a, c1, c2);
+    gms_cells_kernel<<<4, kGmsThreads, smem, st>>>(m, grid, alpha, hw, c1, c2, ds, decision);
+    gms_flag_kernel<<<blocks, 256, 0, st>>>(m, grid, c1, c2, decision, flags);
     return cudaGetLastError();
 }
 

@@ -250,6 +250,20 @@ def config2(pose: str = "inside", eps: float = 2.0, seed: int | None = None,
                      meta=dict(config=2, pose=pose, seed=seed))
 
 
+def perturb_pose(sc: Scene, level: float, seed: int = 0) -> np.ndarray:
+    """F of the scene's true pose with pose noise of the given level: the
+    rotation perturbed about each axis by U[-level, level] degrees and each
+    translation component by U[-0.25 level, 0.25 level] scene units (the
+    paper's noise model, Sec. 5.5; a scene unit plays the metre, depths are
+    2 to 10 units)."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(-level, level, 3)
+    dR = rotation([0, 0, 1], a[2]) @ rotation([0, 1, 0], a[1]) @ rotation([1, 0, 0], a[0])
+    dt = rng.uniform(-0.25 * level, 0.25 * level, 3)
+    m = sc.meta
+    return fundamental(m["K1"], m["K2"], dR @ m["R"], np.asarray(m["t"], np.float64) + dt)
+
+
 def _random_pose(rng, max_deg):
     axis = rng.normal(size=3)
     R = rotation(axis, rng.uniform(0.0, max_deg))
