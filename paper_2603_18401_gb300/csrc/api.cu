@@ -467,7 +467,7 @@ cudaError_t enqueue_pipeline(const Launch &L, Scratch &sc, bool csr, int max_n, 
     if (band) EGM_Q(launch_pack(L, st));
     if (tc) EGM_Q(mark(tc, tb, 4));
     if (band) {
-        if (shape >= 0) EGM_Q(launch_band(L, sms, shape, st));
+        if (shape >= 0) EGM_Q(launch_band(L, sms, shape, st, false));
         if (tc) EGM_Q(mark(tc, tb, 5));
     } else if (csr) {
         uint32_t *long_list = as<uint32_t>(sc.longlist);

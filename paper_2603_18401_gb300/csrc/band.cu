@@ -46,6 +46,7 @@ constexpr int kQSortThreads = 1024;
 constexpr int kQSortPer = 16;  // bucket loads a thread issues before its atomics
 
 __global__ void __launch_bounds__(kQSortThreads) query_sort_kernel(Launch L) {
+    pdl_begin();
     __shared__ uint32_t hist[kQBuckets];
     __shared__ uint32_t wsum[kQSortThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -134,6 +135,8 @@ __device__ __forceinline__ uint32_t e4m3_nibble(uint32_t n) {
 
 // 8 threads per row; thread part t writes output bytes [32 t, 32 t + 32).
 __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
+    pdl_begin();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *L.work = 0u;  // the band kernel's tile dispenser
     const int64_t rows = L.nr + L.nq;
     const int part = threadIdx.x & 7;
     __shared__ int64_t s_roffs[kSmemPairs + 1], s_qoffs[kSmemPairs + 1];
@@ -435,6 +438,7 @@ __device__ __forceinline__ void top2(unsigned long long key, unsigned long long 
 template <int CB, int CPS, bool FLT>
 __global__ void __launch_bounds__(kBandThreads, CPS)
     band_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Launch L) {
+    pdl_begin();
     using Shape = BandShape<CB, CPS>;
     using BandSmem = typename Shape::Smem;
     constexpr int kCB = Shape::kCB, kCN = Shape::kCN;
@@ -925,6 +929,8 @@ int band_tile_queries() { return kTM; }
 
 cudaError_t launch_query_sort(const Launch &L, cudaStream_t s) {
     if (L.nq == 0) return cudaSuccess;
+    // plain launches here and for the pack kernel: both follow a cross-stream
+    // event wait, which must order them in full
     query_sort_kernel<<<L.npairs, kQSortThreads, 0, s>>>(L);
     return cudaGetLastError();
 }
@@ -940,30 +946,30 @@ cudaError_t launch_pack(const Launch &L, cudaStream_t s) {
 
 template <int CB, int CPS, bool FLT>
 cudaError_t launch_band_shape(const Launch &L, int sms, const CUtensorMap &tA, const CUtensorMap &tB,
-                              cudaStream_t s) {
+                              bool zero_work, cudaStream_t s) {
     const int smem = (int)sizeof(BandSmem<CB>) + 1024;
     int64_t grid = L.ntiles;
     if (grid > CPS * (int64_t)sms) grid = CPS * (int64_t)sms;
-    cudaError_t e = cudaMemsetAsync(L.work, 0, sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if (zero_work && (e = cudaMemsetAsync(L.work, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
     e = cudaFuncSetAttribute(band_kernel<CB, CPS, FLT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    band_kernel<CB, CPS, FLT><<<(int)grid, kBandThreads, smem, s>>>(tA, tB, L);
-    return cudaGetLastError();
+    return launch_pdl(band_kernel<CB, CPS, FLT>, dim3((unsigned)grid), dim3(kBandThreads), (size_t)smem, s, tA, tB,
+                      L);
 }
 
 int band_shapes() { return 2; }
 
-cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s) {
+cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s, bool zero_work) {
     if (L.ntiles == 0) return cudaSuccess;
     CUtensorMap tA, tB;
     cudaError_t e = make_tmap(&tA, L.descA, L.nq, kTM);
     if (e != cudaSuccess) return e;
     if ((e = make_tmap(&tB, L.descB, L.nr, kBoxR)) != cudaSuccess) return e;
-    if (L.kinds & (1u << EGM_DESC_F32_L2)) return launch_band_shape<4, 2, true>(L, sms, tA, tB, s);
+    if (L.kinds & (1u << EGM_DESC_F32_L2)) return launch_band_shape<4, 2, true>(L, sms, tA, tB, zero_work, s);
     switch (shape) {
-        case 0: return launch_band_shape<4, 2, false>(L, sms, tA, tB, s);
-        case 1: return launch_band_shape<2, 3, false>(L, sms, tA, tB, s);
+        case 0: return launch_band_shape<4, 2, false>(L, sms, tA, tB, zero_work, s);
+        case 1: return launch_band_shape<2, 3, false>(L, sms, tA, tB, zero_work, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -46,6 +46,7 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *warp_sums
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_partials_kernel(Launch L) {
+    pdl_begin();
     __shared__ int64_t ws[33];
     const int64_t t0 = (int64_t)blockIdx.x * kScanTile;
     int64_t s = 0;
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_partials_kernel(Launch L) {
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_top_kernel(Launch L, int nblocks, uint32_t *long_count) {
+    pdl_begin();
     __shared__ int64_t ws[33];
     if (threadIdx.x == 0) *long_count = 0u;
     int64_t carry = 0;
@@ -80,6 +82,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_top_kernel(Launch L, int nb
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_final_kernel(Launch L) {
+    pdl_begin();
     __shared__ int64_t ws[33];
     const int64_t t0 = (int64_t)blockIdx.x * kScanTile;
     int64_t v[kScanItems];
@@ -105,6 +108,7 @@ constexpr int kRowMax = 1024;
 
 __global__ void __launch_bounds__(kRowWarps * 32) row_sort_kernel(Launch L, uint32_t *long_list,
                                                                   uint32_t *long_count) {
+    pdl_begin();
     __shared__ uint32_t buf_all[kRowWarps][kRowMax];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *buf = buf_all[warp];

@@ -23,6 +23,35 @@
 
 namespace egm {
 
+// ------------------------------------------------------------ dependent launch
+// The pipeline's kernels are launched with programmatic stream serialization:
+// a kernel may be scheduled while its predecessor in the stream finishes.
+// pdl_begin(), the first statement of every such kernel, waits until the
+// predecessor has completed and its memory is visible (so no kernel touches
+// global memory early) and then lets the successor be scheduled.  For a
+// kernel launched without the attribute both instructions return at once.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+
 constexpr int kLevels = 32;        // angular-radius levels (5 bits of the sort key)
 constexpr int kQBits = 22;         // quantised key bits within a level
 constexpr uint32_t kQMax = (1u << kQBits) - 1u;
@@ -493,7 +522,9 @@ cudaError_t launch_gms(const double *xy1, int64_t m, const double *xy2, int64_t 
 int64_t compact_tiles(int64_t m);
 cudaError_t launch_compact(const uint8_t *flags, const int32_t *best, int64_t m, uint32_t require,
                            uint32_t *tile_count, int32_t *qi, int32_t *rj, int64_t *count, cudaStream_t s);
-cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s);
+// zero_work: reset the tile dispenser first (the pipeline's pack kernel
+// resets it otherwise, keeping the launches back to back)
+cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s, bool zero_work = true);
 cudaError_t launch_prep(const Launch &L, cudaStream_t s);
 cudaError_t launch_sort(const Launch &L, cudaStream_t s);
 cudaError_t launch_stab(const Launch &L, int mode, cudaStream_t s);  // 0 fused match, 1 count, 2 fill+match

@@ -37,6 +37,7 @@ __device__ __forceinline__ float fold_atan2(float px, float py) {
 }
 
 __global__ void __launch_bounds__(32) geometry_kernel(Launch L) {
+    pdl_begin();
     const int p = blockIdx.x;
     const int lane = threadIdx.x;
     const PairDesc &P = L.pairs[p];
@@ -171,6 +172,7 @@ __global__ void __launch_bounds__(32) geometry_kernel(Launch L) {
 
 
 __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
+    pdl_begin();
     const int64_t total = L.nr + L.nq;
     const int lane = threadIdx.x & 31;
     __shared__ int64_t s_roffs[kSmemPairs + 1], s_qoffs[kSmemPairs + 1];
@@ -348,8 +350,7 @@ __global__ void intervals_kernel(Launch L, double *theta, double *delta, double 
 }  // namespace
 
 cudaError_t launch_geometry(const Launch &L, cudaStream_t s) {
-    geometry_kernel<<<L.npairs, 32, 0, s>>>(L);
-    return cudaGetLastError();
+    return launch_pdl(geometry_kernel, dim3(L.npairs), dim3(32), 0, s, L);
 }
 
 cudaError_t launch_prep(const Launch &L, cudaStream_t s) {
@@ -357,8 +358,7 @@ cudaError_t launch_prep(const Launch &L, cudaStream_t s) {
     if (total == 0) return cudaSuccess;
     int64_t blocks = (total + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    prep_kernel<<<(int)blocks, 256, 0, s>>>(L);
-    return cudaGetLastError();
+    return launch_pdl(prep_kernel, dim3((unsigned)blocks), dim3(256), 0, s, L);
 }
 
 cudaError_t launch_intervals(const Launch &L, double *theta, double *delta, double *e3, int32_t *mode,

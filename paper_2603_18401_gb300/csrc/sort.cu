@@ -230,6 +230,7 @@ __device__ __forceinline__ uint32_t bucket_slot(const PairGeom &G, uint32_t key)
 }
 
 __global__ void __launch_bounds__(256) bucket_count_kernel(Launch L) {
+    pdl_begin();
     __shared__ int64_t offs[kSmemPairs + 1];
     const bool cached = load_offsets(offs, L.r_offs, L.npairs);
     __syncthreads();
@@ -249,6 +250,7 @@ constexpr int kScanWarps = kScanThreads / 32;
 constexpr int kScanRound = 8;  // rows a warp keeps in registers per round
 
 __global__ void __cluster_dims__(kScanCtas, 1, 1) __launch_bounds__(kScanThreads) bucket_scan_kernel(Launch L) {
+    pdl_begin();
     __shared__ __align__(16) PairGeom G;
     __shared__ uint32_t wtot[kScanWarps];
     __shared__ uint32_t ctot;     // this block's total, read by the higher-ranked blocks
@@ -386,9 +388,9 @@ cudaError_t launch_sort(const Launch &L, cudaStream_t s) {
     if (L.nr == 0) return cudaSuccess;
     int64_t blocks = (L.nr + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    bucket_count_kernel<<<(int)blocks, 256, 0, s>>>(L);
-    bucket_scan_kernel<<<L.npairs * kScanCtas, kScanThreads, 0, s>>>(L);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(bucket_count_kernel, dim3((unsigned)blocks), dim3(256), 0, s, L);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(bucket_scan_kernel, dim3(L.npairs * kScanCtas), dim3(kScanThreads), 0, s, L);
 }
 
 cudaError_t launch_long_row_sort(const Launch &L, const uint32_t *list, const uint32_t *count, cudaStream_t s) {

@@ -111,6 +111,7 @@ __device__ __forceinline__ void copy16(void *dst, const void *src, int bytes, in
 // mode 0: fused matching; 1: count candidates; 2: write candidate rows and match.
 template <int KIND>
 __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mode) {
+    pdl_begin();
     __shared__ __align__(16) StabSmem S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -564,13 +565,13 @@ cudaError_t launch_stab(const Launch &L, int mode, cudaStream_t s) {
     if (L.nq == 0) return cudaSuccess;
     int64_t blocks = (L.nq + kQB - 1) / kQB;
     if (blocks > 152 * 8) blocks = 152 * 8;
+    const dim3 g((unsigned)blocks), b(kStabThreads);
     switch (L.kind) {
-        case EGM_DESC_U8_L2: stab_kernel<EGM_DESC_U8_L2><<<(int)blocks, kStabThreads, 0, s>>>(L, mode); break;
-        case EGM_DESC_BIN: stab_kernel<EGM_DESC_BIN><<<(int)blocks, kStabThreads, 0, s>>>(L, mode); break;
-        case EGM_DESC_F32_L2: stab_kernel<EGM_DESC_F32_L2><<<(int)blocks, kStabThreads, 0, s>>>(L, mode); break;
-        default: stab_kernel<kKindAny><<<(int)blocks, kStabThreads, 0, s>>>(L, mode); break;
+        case EGM_DESC_U8_L2: return launch_pdl(stab_kernel<EGM_DESC_U8_L2>, g, b, 0, s, L, mode);
+        case EGM_DESC_BIN: return launch_pdl(stab_kernel<EGM_DESC_BIN>, g, b, 0, s, L, mode);
+        case EGM_DESC_F32_L2: return launch_pdl(stab_kernel<EGM_DESC_F32_L2>, g, b, 0, s, L, mode);
+        default: return launch_pdl(stab_kernel<kKindAny>, g, b, 0, s, L, mode);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace egm
