@@ -45,6 +45,8 @@ namespace {
 //            two (distance, index) keys - a single writer, no atomics.
 // Rounds of kRound elements repeat 2a-2c; the outputs follow the last round.
 constexpr int kQB = kStabQB;
+// the per-round segment scan gives one lane of warp 0 to each query of the block
+static_assert(kQB == 32, "one lane per query in the segment scan");
 constexpr int kStabThreads = 256;
 constexpr int kRangesPerQuery = 2 * kLevels;
 constexpr int kDescCache = 256;  // query descriptors up to this many bytes are staged in shared memory
