@@ -203,6 +203,20 @@ egm_status egm_graph_destroy(egm_graph *graph);
  * the device, matches, copies the outputs back and waits for completion. */
 egm_status egm_match_pair_host(egm_ctx *ctx, const egm_pair *pair, const egm_out *out);
 
+/* Several pairs from HOST memory, each matched on its own as by
+ * egm_match_pair (the same kernels, one pair per pipeline), with the copies
+ * overlapped: every pair's inputs are queued for upload on a copy stream of
+ * the context, and pair k is matched as soon as its inputs are on the device
+ * while later pairs are still uploading; each pair's outputs are copied back
+ * after its matching.  outs[k] holds pair k's outputs (host memory, m_k rows;
+ * no candidate lists: cand_offsets must be NULL, and every pair needs
+ * descriptors).  pairs, outs: npairs entries.  The device copies of all the
+ * inputs are staged at once (grow-only context memory).  Host buffers should
+ * be pinned for the copies to overlap.  The call returns after the last
+ * output arrived, with the status of the batch.  EGM_ERR_ARG for invalid
+ * pairs or requested candidate lists. */
+egm_status egm_match_batch_host(egm_ctx *ctx, const egm_pair *pairs, int32_t npairs, const egm_out *outs);
+
 /*
  * egm_match_pair without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate device memory, e.g.

@@ -166,6 +166,13 @@ class Matcher:
     def egm_match_pair_host(self, pair: _egm.egm_pair, out: _egm.egm_out) -> int:
         return self.lib.egm_match_pair_host(self.ctx, C.byref(pair), C.byref(out))
 
+    def egm_match_batch_host(self, pairs, outs) -> int:
+        """egm_match_batch_host over lists of egm_pair / egm_out structs holding host pointers."""
+        n = len(pairs)
+        pa = (_egm.egm_pair * n)(*pairs)
+        oa = (_egm.egm_out * n)(*outs)
+        return self.lib.egm_match_batch_host(self.ctx, pa, n, oa)
+
     def match(self, xy1, xy2, F, eps, desc1=None, desc2=None, kind=EGM_DESC_U8_L2, dim=128,
               width=640, height=480, csr=False, cand_capacity=None, out=None):
         """Match one pair of device tensors; returns a dict of device tensors."""

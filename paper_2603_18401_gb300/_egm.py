@@ -103,6 +103,7 @@ SIGNATURES = {
     "egm_pair_residuals": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.c_void_p, C.c_void_p, C.c_int64,
                                      C.c_void_p]),
     "egm_match_mutual": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.POINTER(egm_pair), C.POINTER(egm_out)]),
+    "egm_match_batch_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "egm_gms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                           C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, C.c_int32, C.c_double]),
     "egm_compact_matches": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_uint32, C.c_void_p,

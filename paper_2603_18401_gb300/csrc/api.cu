@@ -84,6 +84,10 @@ struct egm_ctx {
     // the banded form sorts the queries on a second stream, beside the reference sort
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // egm_match_batch_host: input copies run on their own stream, one event per pair
+    cudaStream_t copy = nullptr;
+    cudaEvent_t copy_start = nullptr;
+    std::vector<cudaEvent_t> in_ev;
     // band tile shape per batch size class (log2 of the tile count), set by the tuner
     std::map<int, int> band_shape;
 };
@@ -632,6 +636,12 @@ egm_status egm_destroy(egm_ctx *c) {
     }
     if (c->fork_ev) cudaEventDestroy(c->fork_ev);
     if (c->join_ev) cudaEventDestroy(c->join_ev);
+    if (c->copy) {
+        cudaStreamSynchronize(c->copy);
+        cudaStreamDestroy(c->copy);
+    }
+    if (c->copy_start) cudaEventDestroy(c->copy_start);
+    for (cudaEvent_t e : c->in_ev) cudaEventDestroy(e);
     c->sc.release();
     if (c->stage.ptr) cudaFree(c->stage.ptr);
     if (c->compact.ptr) cudaFree(c->compact.ptr);
@@ -783,6 +793,103 @@ egm_status egm_match_pair_host(egm_ctx *c, const egm_pair *hp, const egm_out *ho
         }
     }
     return EGM_OK;
+}
+
+egm_status egm_match_batch_host(egm_ctx *c, const egm_pair *hp, int32_t npairs, const egm_out *ho) {
+    if (!c || npairs < 0 || (npairs > 0 && (!hp || !ho))) return EGM_ERR_ARG;
+    if (npairs == 0) return EGM_OK;
+    struct Off {
+        size_t xy1, xy2, F, eps, d1, d2, best, second, bd, sd, fl;
+    };
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    std::vector<Off> offs((size_t)npairs);
+    size_t off = 0;
+    for (int k = 0; k < npairs; k++) {
+        egm_status s = check_pair(hp + k);
+        if (s != EGM_OK) return s;
+        if (ho[k].cand_offsets || !has_desc(hp + k)) return EGM_ERR_ARG;
+        const int64_t m = hp[k].m, n = hp[k].n;
+        const size_t rb = (size_t)row_bytes_of(hp[k].kind, hp[k].dim);
+        Off &o = offs[(size_t)k];
+        o.xy1 = off; off += al(16 * (size_t)m);
+        o.xy2 = off; off += al(16 * (size_t)n);
+        o.F = off; off += al(72);
+        o.eps = off; off += al(hp[k].eps2 ? 8 * (size_t)n : 0);
+        o.d1 = off; off += al(rb * (size_t)m);
+        o.d2 = off; off += al(rb * (size_t)n);
+        o.best = off; off += al(4 * (size_t)m);
+        o.second = off; off += al(4 * (size_t)m);
+        o.bd = off; off += al(4 * (size_t)m);
+        o.sd = off; off += al(4 * (size_t)m);
+        o.fl = off; off += al((size_t)m);
+    }
+    EGM_TRY(cudaSetDevice(c->device));
+    EGM_TRY(grow(c->stage, off));
+    if (!c->copy) EGM_TRY(cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking));
+    if (!c->copy_start) EGM_TRY(cudaEventCreateWithFlags(&c->copy_start, cudaEventDisableTiming));
+    while ((int)c->in_ev.size() < npairs) {
+        cudaEvent_t e;
+        EGM_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c->in_ev.push_back(e);
+    }
+    unsigned char *d = static_cast<unsigned char *>(c->stage.ptr);
+    cudaStream_t st = c->stream, cs = c->copy;
+    const cudaMemcpyKind H2D = cudaMemcpyHostToDevice, D2H = cudaMemcpyDeviceToHost;
+    // the copies start once the context's stream is done with the staging buffer
+    EGM_TRY(cudaEventRecord(c->copy_start, st));
+    EGM_TRY(cudaStreamWaitEvent(cs, c->copy_start, 0));
+    EGM_TRY(cudaMemsetAsync(c->sc.small.ptr, 0, sizeof(uint32_t), st));
+    // on a failure after copies were queued, wait for them: they read the caller's buffers
+    auto fail = [&](egm_status s) {
+        cudaStreamSynchronize(cs);
+        cudaStreamSynchronize(st);
+        return s;
+    };
+    for (int k = 0; k < npairs; k++) {
+        const egm_pair &P = hp[k];
+        const Off &o = offs[(size_t)k];
+        const size_t rb = (size_t)row_bytes_of(P.kind, P.dim);
+        cudaError_t e = cudaSuccess;
+        if (P.m) e = cudaMemcpyAsync(d + o.xy1, P.xy1, 16 * (size_t)P.m, H2D, cs);
+        if (e == cudaSuccess && P.n) e = cudaMemcpyAsync(d + o.xy2, P.xy2, 16 * (size_t)P.n, H2D, cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d + o.F, P.F, 72, H2D, cs);
+        if (e == cudaSuccess && P.eps2 && P.n) e = cudaMemcpyAsync(d + o.eps, P.eps2, 8 * (size_t)P.n, H2D, cs);
+        if (e == cudaSuccess && P.m) e = cudaMemcpyAsync(d + o.d1, P.desc1, rb * (size_t)P.m, H2D, cs);
+        if (e == cudaSuccess && P.n) e = cudaMemcpyAsync(d + o.d2, P.desc2, rb * (size_t)P.n, H2D, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(c->in_ev[(size_t)k], cs);
+        if (e != cudaSuccess) return fail(from_cuda(e));
+    }
+    for (int k = 0; k < npairs; k++) {
+        const egm_pair &P = hp[k];
+        const egm_out &O = ho[k];
+        const Off &o = offs[(size_t)k];
+        const size_t m = (size_t)P.m;
+        egm_pair dp = P;
+        dp.xy1 = reinterpret_cast<const double *>(d + o.xy1);
+        dp.xy2 = reinterpret_cast<const double *>(d + o.xy2);
+        dp.F = reinterpret_cast<const double *>(d + o.F);
+        dp.eps2 = P.eps2 ? reinterpret_cast<const double *>(d + o.eps) : nullptr;
+        dp.desc1 = d + o.d1;
+        dp.desc2 = d + o.d2;
+        egm_out dout;
+        memset(&dout, 0, sizeof(dout));
+        dout.best = O.best ? reinterpret_cast<int32_t *>(d + o.best) : nullptr;
+        dout.second = O.second ? reinterpret_cast<int32_t *>(d + o.second) : nullptr;
+        dout.best_d = O.best_d ? reinterpret_cast<float *>(d + o.bd) : nullptr;
+        dout.second_d = O.second_d ? reinterpret_cast<float *>(d + o.sd) : nullptr;
+        dout.flags = O.flags ? d + o.fl : nullptr;
+        cudaError_t e = cudaStreamWaitEvent(st, c->in_ev[(size_t)k], 0);
+        if (e != cudaSuccess) return fail(from_cuda(e));
+        egm_status s = run_batch(c, &dp, 1, &dout, false);
+        if (s != EGM_OK) return fail(s);
+        if (O.best) e = cudaMemcpyAsync(O.best, dout.best, 4 * m, D2H, st);
+        if (e == cudaSuccess && O.second) e = cudaMemcpyAsync(O.second, dout.second, 4 * m, D2H, st);
+        if (e == cudaSuccess && O.best_d) e = cudaMemcpyAsync(O.best_d, dout.best_d, 4 * m, D2H, st);
+        if (e == cudaSuccess && O.second_d) e = cudaMemcpyAsync(O.second_d, dout.second_d, 4 * m, D2H, st);
+        if (e == cudaSuccess && O.flags) e = cudaMemcpyAsync(O.flags, dout.flags, m, D2H, st);
+        if (e != cudaSuccess) return fail(from_cuda(e));
+    }
+    return egm_sync(c);
 }
 
 egm_status egm_match_mutual(egm_ctx *c, const egm_pair *fwd, const egm_pair *rev, const egm_out *out) {
