@@ -152,6 +152,13 @@ enum {
     EGM_FORM_BANDED = 2    /* angle-banded tiles, descriptor dot products on tensor cores */
 };
 
+/* Tensor-core pass of float descriptors in the banded form (Sec. 4.3 on the
+ * tensor cores): rows rounded to BF16, or to FP8 E4M3 with one scale per row
+ * (max |x| / 448).  Either pass bounds every distance it computes by the
+ * rows' rounding errors; the candidates that can be among the best two are
+ * then re-ranked in FP32, so both give the plain form's FP32 result. */
+enum { EGM_FLOAT_PASS_BF16 = 0, EGM_FLOAT_PASS_FP8 = 1 };
+
 typedef struct egm_params {
     int32_t ratio_num;     /* ratio test tau = num / den, default 4 / 5 (Sec. 5.1) */
     int32_t ratio_den;
@@ -160,7 +167,10 @@ typedef struct egm_params {
     int32_t band_tile;     /* banded form tile shape: 0 (default) chosen by the library's tuner,
                               which times every shape on the first call of each batch size class
                               (that call waits for the device); k > 0: shape k - 1 */
-    int32_t reserved[11];  /* zero */
+    int32_t float_pass;    /* banded form, float descriptors: the tensor-core pass that brackets
+                              the distances before the exact FP32 rerank (results are the same):
+                              EGM_FLOAT_PASS_BF16 (default) or EGM_FLOAT_PASS_FP8 */
+    int32_t reserved[10];  /* zero */
 } egm_params;
 
 /* Context lifetime.  `stream` is a cudaStream_t (NULL: the legacy default stream). */

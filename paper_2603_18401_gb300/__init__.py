@@ -60,8 +60,9 @@ class Matcher:
             pass
 
     # ------------------------------------------------------------- params
-    def set_params(self, ratio=None, sync=None, form=None, band_tile=None):
-        """ratio (num, den); sync; form (EGM_FORM_*); band_tile (0: tuned, k > 0: shape k - 1)."""
+    def set_params(self, ratio=None, sync=None, form=None, band_tile=None, float_pass=None):
+        """ratio (num, den); sync; form (EGM_FORM_*); band_tile (0: tuned, k > 0: shape k - 1);
+        float_pass (EGM_FLOAT_PASS_*)."""
         p = _egm.egm_params()
         check(self.lib.egm_get_params(self.ctx, C.byref(p)), "egm_get_params")
         if ratio is not None:
@@ -72,6 +73,8 @@ class Matcher:
             p.form = int(form)
         if band_tile is not None:
             p.band_tile = int(band_tile)
+        if float_pass is not None:
+            p.float_pass = int(float_pass)
         check(self.lib.egm_set_params(self.ctx, C.byref(p)), "egm_set_params")
 
     def reserve(self, queries: int, refs: int, pairs: int = 1):

@@ -32,6 +32,8 @@ EGM_FLAG_NO_SECOND = 4
 EGM_FLAG_DEGENERATE_LINE = 8
 EGM_FLAG_MUTUAL = 16
 EGM_FLAG_GMS = 32
+EGM_FLOAT_PASS_BF16 = 0
+EGM_FLOAT_PASS_FP8 = 1
 
 EGM_FORM_AUTO = 0
 EGM_FORM_PLAIN = 1
@@ -59,7 +61,8 @@ class egm_out(C.Structure):
 
 class egm_params(C.Structure):
     _fields_ = [("ratio_num", C.c_int32), ("ratio_den", C.c_int32), ("sync", C.c_int32),
-                ("form", C.c_int32), ("band_tile", C.c_int32), ("reserved", C.c_int32 * 11)]
+                ("form", C.c_int32), ("band_tile", C.c_int32), ("float_pass", C.c_int32),
+                ("reserved", C.c_int32 * 10)]
 
 
 class egm_stats(C.Structure):

@@ -84,10 +84,11 @@ struct egm_ctx {
     // the banded form sorts the queries on a second stream, beside the reference sort
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
-    // egm_match_batch_host: input copies run on their own stream, one event per pair
-    cudaStream_t copy = nullptr;
-    cudaEvent_t copy_start = nullptr;
-    std::vector<cudaEvent_t> in_ev;
+    // egm_match_batch_host: input and output copies run on their own streams,
+    // ordered against the matching by one event per pair and direction
+    cudaStream_t copy = nullptr, copy_out = nullptr;
+    cudaEvent_t copy_start = nullptr, out_done = nullptr;
+    std::vector<cudaEvent_t> in_ev, done_ev;
     // band tile shape per batch size class (log2 of the tile count), set by the tuner
     std::map<int, int> band_shape;
 };
@@ -269,7 +270,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 // Banded-form scratch: query permutation, packed operand rows, norms (padded
 // for the aligned 16-byte bulk copies that read past a pair's last row).
 struct BandLayout {
-    size_t qperm, descA, descB, qbkt, qsrt, rnorm, total;
+    size_t qperm, descA, descB, qbkt, qsrt, qscale, rnorm, total;
     BandLayout(int64_t nq, int64_t nr) {
         const size_t rb = (size_t)band_row_bytes();
         qperm = 0;
@@ -277,8 +278,9 @@ struct BandLayout {
         descB = descA + align256(rb * (size_t)std::max<int64_t>(nq, 1));
         qbkt = descB + align256(rb * (size_t)std::max<int64_t>(nr, 1));
         qsrt = qbkt + align256(sizeof(uint16_t) * (size_t)std::max<int64_t>(nq, 1));
-        rnorm = qsrt + align256(sizeof(QueryRec) * (size_t)std::max<int64_t>(nq, 1));
-        total = rnorm + align256(sizeof(float2) * (size_t)(nr + 64));
+        qscale = qsrt + align256(sizeof(QueryRec) * (size_t)std::max<int64_t>(nq, 1));
+        rnorm = qscale + align256(sizeof(float) * (size_t)std::max<int64_t>(nq, 1));
+        total = rnorm + align256(sizeof(float4) * (size_t)(nr + 64));
     }
 };
 
@@ -337,6 +339,10 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
     L.blkpair = as<int32_t>(c->blkpair);
     L.ratio_num = prm.ratio_num;
     L.ratio_den = prm.ratio_den;
+    if (npairs == 1) {
+        L.inl_use = 1;
+        L.inl = pl.pd[0];
+    }
     L.max_n = pl.max_n;
     if (band) {
         const BandLayout bl(pl.nq, pl.nr);
@@ -346,7 +352,9 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
         L.descB = b + bl.descB;
         L.qbkt = reinterpret_cast<uint16_t *>(b + bl.qbkt);
         L.qsrt = reinterpret_cast<QueryRec *>(b + bl.qsrt);
-        L.rnorm = reinterpret_cast<float2 *>(b + bl.rnorm);
+        L.rnorm = reinterpret_cast<float4 *>(b + bl.rnorm);
+        L.qscale = reinterpret_cast<float *>(b + bl.qscale);
+        L.fp8 = prm.float_pass == EGM_FLOAT_PASS_FP8;
         L.tile_offs = as<int64_t>(c->offs) + 2 * (npairs + 1);
         L.tile_seq = reinterpret_cast<const int32_t *>(as<int64_t>(c->offs) + 3 * (npairs + 1));
         L.work = as<uint32_t>(c->small) + 32;
@@ -568,7 +576,7 @@ egm_status run_batch(egm_ctx *c, const egm_pair *pairs, int npairs, const egm_ou
     EGM_TRY(cudaSetDevice(c->device));
     if (band) EGM_TRY(ensure_side(c));
     EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, npairs, band));
-    EGM_TRY(upload_plan(c, pl, npairs));
+    if (npairs > 1) EGM_TRY(upload_plan(c, pl, npairs));  // one pair: the plan rides in the launch
     Launch L = make_launch(c->sc, c->counters_on, c->params, pl, npairs, out, band);
     cudaStream_t st = c->stream;
     if (sync) EGM_TRY(cudaMemsetAsync(L.status, 0, sizeof(uint32_t), st));
@@ -640,8 +648,14 @@ egm_status egm_destroy(egm_ctx *c) {
         cudaStreamSynchronize(c->copy);
         cudaStreamDestroy(c->copy);
     }
+    if (c->copy_out) {
+        cudaStreamSynchronize(c->copy_out);
+        cudaStreamDestroy(c->copy_out);
+    }
     if (c->copy_start) cudaEventDestroy(c->copy_start);
+    if (c->out_done) cudaEventDestroy(c->out_done);
     for (cudaEvent_t e : c->in_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->done_ev) cudaEventDestroy(e);
     c->sc.release();
     if (c->stage.ptr) cudaFree(c->stage.ptr);
     if (c->compact.ptr) cudaFree(c->compact.ptr);
@@ -669,6 +683,7 @@ egm_status egm_set_params(egm_ctx *c, const egm_params *p) {
         return EGM_ERR_ARG;
     if (p->form < EGM_FORM_AUTO || p->form > EGM_FORM_BANDED) return EGM_ERR_ARG;
     if (p->band_tile < 0 || p->band_tile > band_shapes()) return EGM_ERR_ARG;
+    if (p->float_pass != EGM_FLOAT_PASS_BF16 && p->float_pass != EGM_FLOAT_PASS_FP8) return EGM_ERR_ARG;
     c->params = *p;
     return EGM_OK;
 }
@@ -826,14 +841,18 @@ egm_status egm_match_batch_host(egm_ctx *c, const egm_pair *hp, int32_t npairs, 
     EGM_TRY(cudaSetDevice(c->device));
     EGM_TRY(grow(c->stage, off));
     if (!c->copy) EGM_TRY(cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking));
+    if (!c->copy_out) EGM_TRY(cudaStreamCreateWithFlags(&c->copy_out, cudaStreamNonBlocking));
     if (!c->copy_start) EGM_TRY(cudaEventCreateWithFlags(&c->copy_start, cudaEventDisableTiming));
+    if (!c->out_done) EGM_TRY(cudaEventCreateWithFlags(&c->out_done, cudaEventDisableTiming));
     while ((int)c->in_ev.size() < npairs) {
-        cudaEvent_t e;
+        cudaEvent_t e, f;
         EGM_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         c->in_ev.push_back(e);
+        EGM_TRY(cudaEventCreateWithFlags(&f, cudaEventDisableTiming));
+        c->done_ev.push_back(f);
     }
     unsigned char *d = static_cast<unsigned char *>(c->stage.ptr);
-    cudaStream_t st = c->stream, cs = c->copy;
+    cudaStream_t st = c->stream, cs = c->copy, co = c->copy_out;
     const cudaMemcpyKind H2D = cudaMemcpyHostToDevice, D2H = cudaMemcpyDeviceToHost;
     // the copies start once the context's stream is done with the staging buffer
     EGM_TRY(cudaEventRecord(c->copy_start, st));
@@ -843,6 +862,7 @@ egm_status egm_match_batch_host(egm_ctx *c, const egm_pair *hp, int32_t npairs, 
     auto fail = [&](egm_status s) {
         cudaStreamSynchronize(cs);
         cudaStreamSynchronize(st);
+        cudaStreamSynchronize(co);
         return s;
     };
     for (int k = 0; k < npairs; k++) {
@@ -882,13 +902,20 @@ egm_status egm_match_batch_host(egm_ctx *c, const egm_pair *hp, int32_t npairs, 
         if (e != cudaSuccess) return fail(from_cuda(e));
         egm_status s = run_batch(c, &dp, 1, &dout, false);
         if (s != EGM_OK) return fail(s);
-        if (O.best) e = cudaMemcpyAsync(O.best, dout.best, 4 * m, D2H, st);
-        if (e == cudaSuccess && O.second) e = cudaMemcpyAsync(O.second, dout.second, 4 * m, D2H, st);
-        if (e == cudaSuccess && O.best_d) e = cudaMemcpyAsync(O.best_d, dout.best_d, 4 * m, D2H, st);
-        if (e == cudaSuccess && O.second_d) e = cudaMemcpyAsync(O.second_d, dout.second_d, 4 * m, D2H, st);
-        if (e == cudaSuccess && O.flags) e = cudaMemcpyAsync(O.flags, dout.flags, m, D2H, st);
+        // the outputs go back on the output stream, off the matching's path
+        e = cudaEventRecord(c->done_ev[(size_t)k], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(co, c->done_ev[(size_t)k], 0);
+        if (e == cudaSuccess && O.best) e = cudaMemcpyAsync(O.best, dout.best, 4 * m, D2H, co);
+        if (e == cudaSuccess && O.second) e = cudaMemcpyAsync(O.second, dout.second, 4 * m, D2H, co);
+        if (e == cudaSuccess && O.best_d) e = cudaMemcpyAsync(O.best_d, dout.best_d, 4 * m, D2H, co);
+        if (e == cudaSuccess && O.second_d) e = cudaMemcpyAsync(O.second_d, dout.second_d, 4 * m, D2H, co);
+        if (e == cudaSuccess && O.flags) e = cudaMemcpyAsync(O.flags, dout.flags, m, D2H, co);
         if (e != cudaSuccess) return fail(from_cuda(e));
     }
+    // the context's stream waits for the last output copy, then the status
+    cudaError_t e = cudaEventRecord(c->out_done, co);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->out_done, 0);
+    if (e != cudaSuccess) return fail(from_cuda(e));
     return egm_sync(c);
 }
 

@@ -32,6 +32,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <math.h>
 
 #include "egm_internal.cuh"
@@ -147,8 +149,10 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
         const bool valid = g0 < rows;
         const bool is_ref = g0 < L.nr;
         uint32_t nrm = 0, qi = 0;
-        float fnrm = 0.0f, ferr = 0.0f;  // float rows: squared norm of the BF16 row, squared rounding error
-        bool isf = false;
+        float fnrm = 0.0f, ferr = 0.0f;  // float rows: squared norm of the rounded row, squared rounding error
+        bool isf = false, isf8 = false;
+        float xs8[16];                   // FP8 pass: this thread's 16 values, kept for the second step
+        float amax = 0.0f;               //   and their largest magnitude
         uint4 o0 = make_uint4(0, 0, 0, 0), o1 = o0, qr = o0;
         uint8_t *dst = nullptr;
         if (valid) {
@@ -181,6 +185,19 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
                 }
                 o0 = make_uint4(out[0], out[1], out[2], out[3]);
                 o1 = make_uint4(out[4], out[5], out[6], out[7]);
+            } else if (P.kind == EGM_DESC_F32_L2 && L.fp8) {
+                // FP8 pass, step 1: 16 values per thread and their largest magnitude
+                // (the row's scale needs the maximum over its 8 threads)
+                isf = isf8 = true;
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const float4 v = __ldg(reinterpret_cast<const float4 *>(src) + 4 * part + c);
+                    xs8[4 * c] = v.x;
+                    xs8[4 * c + 1] = v.y;
+                    xs8[4 * c + 2] = v.z;
+                    xs8[4 * c + 3] = v.w;
+                    amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+                }
             } else if (P.kind == EGM_DESC_F32_L2) {
                 // 16 values per thread: 64 bytes in, 32 bytes of BF16 out
                 isf = true;
@@ -211,21 +228,50 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
                                 e4m3_nibble((w >> 24) & 15u), e4m3_nibble(w >> 28));
             }
         }
+        // FP8 pass, step 2: the row's scale s = max |x| / 448 (E4M3's largest
+        // value); the operand holds e4m3(x / s) in bytes 0..127 and zeros in
+        // 128..255, and the squared norm and rounding error are those of
+        // s e4m3(x / s), the row the tensor cores see
+        float scale = 1.0f;
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o, 8));
+        if (isf8) {
+            const float inv = amax > 0.0f ? 448.0f / amax : 1.0f;
+            scale = amax > 0.0f ? amax / 448.0f : 1.0f;
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                const __nv_fp8_storage_t e = __nv_cvt_float_to_fp8(xs8[k] * inv, __NV_SATFINITE, __NV_E4M3);
+                const float b = __half2float(__half(__nv_cvt_fp8_to_halfraw(e, __NV_E4M3))) * scale;
+                fnrm = fmaf(b, b, fnrm);
+                const float d = xs8[k] - b;
+                ferr = fmaf(d, d, ferr);
+                w[k >> 2] |= (uint32_t)e << (8 * (k & 3));
+            }
+            o0 = make_uint4(w[0], w[1], w[2], w[3]);
+        }
 #pragma unroll
         for (int o = 4; o > 0; o >>= 1) {
             nrm += __shfl_xor_sync(0xffffffffu, nrm, o, 8);
             fnrm += __shfl_xor_sync(0xffffffffu, fnrm, o, 8);
             ferr += __shfl_xor_sync(0xffffffffu, ferr, o, 8);
         }
-        // norm of the operand row; for float rows also |x - bf16(x)|, rounded up
+        // norm of the operand row; for float rows also |x - x~|, rounded up
         const float norm = isf ? fnrm : (float)nrm;
         const float err = isf ? sqrtf(ferr) * 1.0001f + 1e-30f : 0.0f;
         if (valid) {
-            reinterpret_cast<uint4 *>(dst)[2 * part] = o0;
-            reinterpret_cast<uint4 *>(dst)[2 * part + 1] = o1;
+            if (isf8) {
+                // 16 bytes per thread: bytes [16 part, 16 part + 16), zeros above 128
+                reinterpret_cast<uint4 *>(dst)[part] = o0;
+                reinterpret_cast<uint4 *>(dst)[8 + part] = make_uint4(0u, 0u, 0u, 0u);
+            } else {
+                reinterpret_cast<uint4 *>(dst)[2 * part] = o0;
+                reinterpret_cast<uint4 *>(dst)[2 * part + 1] = o1;
+            }
             if (is_ref) {
-                if (part == 0) L.rnorm[g0] = make_float2(norm, err);
+                if (part == 0) L.rnorm[g0] = make_float4(norm, err, scale, 0.0f);
             } else if (part < 3) {
+                if (part == 0) L.qscale[g0 - L.nr] = scale;
                 // sorted query record; the padding carries the query index and the
                 // norm, the pair field (the tile knows its pair) the rounding error
                 if (part == 2) {
@@ -243,7 +289,6 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
 constexpr int kTM = 128;                 // queries per tile (MMA M, TMEM lanes)
 constexpr int kBoxR = 32;                // reference rows per TMA box (N per box)
 constexpr int kBandThreads = kTM + 32;   // four epilogue warps and the control warp
-constexpr int kRnRow = kBoxR + 2;        // norms (float2) copied from a 16-byte aligned start
 // Tile shapes (chosen per workload by the tuner): CB boxes per MMA chunk
 // (N = 32 CB) and CPS resident CTAs per SM, which size shared memory and TMEM.
 //   0: CB 4, CPS 2   few tiles per SM (single pairs): fewer, larger chunks
@@ -261,7 +306,7 @@ struct BandSmem {
     uint8_t A[2][kTM * 128];      // query tile, K halves (1024-byte aligned)
     uint8_t B[2][2][kCN * 128];   // band chunk: stage, K half
     float4 rec[2][kCN];           // (x - cx, y - cy, eps, index) of each column
-    float2 rn[2][CB][kRnRow];     // (norm, rounding error) of each box's rows
+    float4 rn[2][CB][kBoxR];      // (norm, rounding error, row scale, 0) of each box's rows
     // fullB: a stage's operand rows landed; sfree: the MMA that read them is
     // done; fullR: a stage's records and norms landed; done: an accumulator is
     // ready; tfree: the epilogue has read it and the stage's records
@@ -509,7 +554,8 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         }
         const uint32_t qi = r.pad[0];
         const float qn = __uint_as_float(r.pad[1]);
-        const float qerr = __uint_as_float((uint32_t)r.pair);  // float rows: |q - bf16(q)|
+        const float qerr = __uint_as_float((uint32_t)r.pair);  // float rows: |q - q~|
+        const float qs = FLT && qv ? L.qscale[q_off + t0 + tid] : 1.0f;  // row scale of the FP8 pass
         if (ctl) {
             tc::mbar_arrive_expect_tx(&S.afull, 2 * kTM * 128);
             tc::tma_load_2d(S.A[0], &tmA, 0, (int32_t)(q_off + t0), &S.afull);
@@ -661,21 +707,22 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             auto issueR = [&](int c) {
                 const uint32_t st = (seq + (uint32_t)c) & 1u;
                 const int nb = min(kCB, nbox - c * kCB);
-                tc::mbar_arrive_expect_tx(&S.fullR[st], (uint32_t)nb * (kBoxR * 16 + kRnRow * 8));
+                tc::mbar_arrive_expect_tx(&S.fullR[st], (uint32_t)nb * (kBoxR * 16 + kBoxR * 16));
                 for (int bb = 0; bb < nb; bb++) {
                     uint32_t pos, len;
                     int li;
                     curR.next(S, pos, len, li);
                     const int64_t row = P.r_off + pos;
                     tc::bulk_load(&S.rec[st][bb * kBoxR], L.rec + row, kBoxR * 16, &S.fullR[st]);
-                    tc::bulk_load(&S.rn[st][bb][0], L.rnorm + (row & ~(int64_t)1), kRnRow * 8, &S.fullR[st]);
+                    tc::bulk_load(&S.rn[st][bb][0], L.rnorm + row, kBoxR * 16, &S.fullR[st]);
                 }
             };
             for (int c = 0; c < nchunk && c < 2; c++) {
                 issueB(c);
                 issueR(c);
             }
-            const bool bin = P.kind == EGM_DESC_BIN;
+            // E4M3 operands: binary rows (bits as 0 / 1) and float rows of the FP8 pass
+            const bool bin = P.kind == EGM_DESC_BIN || (FLT && L.fp8 && P.kind == EGM_DESC_F32_L2);
             for (int c = 0; c < nchunk; c++) {
                 const uint32_t sq = seq + (uint32_t)c, st = sq & 1u, use = sq >> 1;
                 bool ok = true;
@@ -740,7 +787,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                     const int y0 = (int)max(pos, w1.x) - (int)pos;
                     const int y1 = (int)min(pos + len, w1.x + w1.y) - (int)pos;
                     if (x1 <= x0 && y1 <= y0) continue;
-                    const float2 *rnb = &S.rn[st][bb][(P.r_off + pos) & 1];
+                    const float4 *rnb = &S.rn[st][bb][0];
                     const float4 *recb = &S.rec[st][bb * kBoxR];
                     const uint32_t tb = tmem + lanebase + st * kCN + bb * kBoxR;
                     // the box's columns inside the warp's windows, as a bit mask
@@ -794,9 +841,11 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                                     vk = v[t];
                                     jk = __float_as_uint(rcs[t].w);
                                 }
-                            const float2 rk = rnb[g + k];
+                            const float4 rk = rnb[g + k];
                             ncand++;
-                            const float dist = qn + rk.x - 2.0f * __uint_as_float(vk);
+                            // the accumulator holds the product of the scaled rows (scales 1
+                            // except in the FP8 pass)
+                            const float dist = qn + rk.x - 2.0f * ((qs * rk.z) * __uint_as_float(vk));
                             if (!isf) {
                                 // integer distances: exact
                                 top2(((unsigned long long)(uint32_t)dist << 32) | jk, b1, b2);

@@ -168,12 +168,20 @@ struct Launch {
     uint16_t *qbkt;               // per query: its bucket of the angle order (written by the prep kernel)
     uint8_t *descA, *descB;       // 256-byte operand rows of the sorted queries / references
     QueryRec *qsrt;               // query records in sorted order, pad = (query index, norm bits)
-    float2 *rnorm;                // sorted references: (squared norm of the operand row, or popcount;
-                                  //   rounding error |r - bf16(r)| of float rows, else 0)
+    float4 *rnorm;                // sorted references: (squared norm of the operand row, or popcount;
+                                  //   rounding error |r - r~| of float rows, else 0; row scale, 1
+                                  //   unless FP8; 0)
+    float *qscale;                // sorted queries: row scale of the operand row (1 unless FP8)
+    int32_t fp8;                  // float rows packed as FP8 E4M3 with per-row scales
     const int64_t *tile_offs;     // npairs + 1: first tile of each pair
     const int32_t *tile_seq;      // ntiles: tiles in the order they are handed out (costliest pairs first)
     uint32_t *work;               // tile dispenser (zeroed before the band kernel)
     int64_t ntiles;
+    // a single pair's plan travels in the launch parameters: the geometry
+    // kernel writes the pair table, offsets and tile order that the later
+    // kernels read, so the call needs no host-to-device copy
+    int32_t inl_use;
+    PairDesc inl;
 };
 
 // Pairs with at most this many references are sorted by one thread-block

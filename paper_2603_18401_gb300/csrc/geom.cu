@@ -40,7 +40,25 @@ __global__ void __launch_bounds__(32) geometry_kernel(Launch L) {
     pdl_begin();
     const int p = blockIdx.x;
     const int lane = threadIdx.x;
-    const PairDesc &P = L.pairs[p];
+    if (L.inl_use) {
+        // one pair: write its plan for the later kernels
+        if (lane == 0) {
+            *const_cast<PairDesc *>(L.pairs) = L.inl;
+            int64_t *qo = const_cast<int64_t *>(L.q_offs), *ro = const_cast<int64_t *>(L.r_offs);
+            qo[0] = 0;
+            qo[1] = L.inl.m;
+            ro[0] = 0;
+            ro[1] = L.inl.n;
+            if (L.tile_offs) {
+                int64_t *to = const_cast<int64_t *>(L.tile_offs);
+                to[0] = 0;
+                to[1] = L.ntiles;
+            }
+        }
+        if (L.tile_seq)
+            for (int64_t t = lane; t < L.ntiles; t += 32) const_cast<int32_t *>(L.tile_seq)[t] = (int32_t)t;
+    }
+    const PairDesc &P = L.inl_use ? L.inl : L.pairs[p];
     PairGeom &G = L.geom[p];
     G.cnt[lane] = 0u;
     G.smax[lane] = 0u;

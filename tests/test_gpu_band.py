@@ -258,19 +258,27 @@ def test_every_tile_shape_and_the_tuner(mt):
 
 
 # ------------------------------------------------------------------ float descriptors
-# BF16 tensor-core pass, then an FP32 rerank in the plain kernel's order: the
-# outputs equal the plain form's bit for bit (distances included).
+# A BF16 or FP8 (E4M3, per-row scale) tensor-core pass, then an FP32 rerank in
+# the plain kernel's order: the outputs equal the plain form's bit for bit
+# (distances included) with either pass.
 
-def test_float_config4(mt):
+@pytest.fixture(params=[0, 1], ids=["bf16", "fp8"])
+def fpass(mt, request):
+    mt.set_params(float_pass=request.param)
+    yield request.param
+    mt.set_params(float_pass=0)
+
+
+def test_float_config4(mt, fpass):
     for sc in synth.config4(seed=0, npairs=2, scale=0.125):
         both(mt, sc)
 
 
-def test_float_config4_full_size(mt):
+def test_float_config4_full_size(mt, fpass):
     both(mt, synth.config4(seed=1, npairs=1)[0])
 
 
-def test_float_mixed_with_u8_batch(mt):
+def test_float_mixed_with_u8_batch(mt, fpass):
     scenes = synth.config4(seed=2, npairs=3, scale=0.1) + synth.config3(seed=6, npairs=4, scale=0.1)
     items = [mt.to_device(s) for s in scenes]
     res = {}
@@ -299,7 +307,7 @@ def test_float_mixed_with_u8_batch(mt):
         q0 += s.m
 
 
-def test_float_rerank_buffer_overflow(mt):
+def test_float_rerank_buffer_overflow(mt, fpass):
     """Twenty references on every query's line share one descriptor: their
     approximate distances tie, more of them than the rerank buffer holds can
     be among the best two, and the exhaustive pass over the windows decides."""
@@ -321,7 +329,7 @@ def test_float_rerank_buffer_overflow(mt):
     assert np.all(b["flags"][:60] & 1)
 
 
-def test_float_distance_error_against_fp64(mt):
+def test_float_distance_error_against_fp64(mt, fpass):
     """The FP32 distances of both forms against the oracle's FP64 distances
     (config 4, every query with a match): the largest relative error is
     reported and must stay within 1e-5."""
@@ -334,5 +342,5 @@ def test_float_distance_error_against_fp64(mt):
             same = has & (out["best"] == ref["best"])
             rel = np.abs(out["best_d"][same].astype(np.float64) - ref["best_d"][same]) / np.maximum(ref["best_d"][same], 1e-30)
             worst = max(worst, float(rel.max()))
-    print(f"largest relative error of FP32 best distances against FP64: {worst:.3e}")
+    print(f"pass {fpass}: largest relative error of FP32 best distances against FP64: {worst:.3e}")
     assert worst <= 1e-5
