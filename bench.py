@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--float-pairs", type=int, default=64)
     ap.add_argument("--no-matching", action="store_true", help="skip the mutual-matching leg")
     ap.add_argument("--no-sweeps", action="store_true", help="skip the tolerance and pose-noise sweeps")
+    ap.add_argument("--batched-only", action="store_true", help="run only the batched configuration")
     return ap.parse_args()
 
 
@@ -256,10 +257,10 @@ def source_hash(kernel):
     return h.hexdigest()
 
 
-def kernel_profile(kernel):
+def kernel_profile(kernel, workload="config2"):
     """Counters of the committed ncu summary of `kernel` on this workload, if
     it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_config2.json")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
@@ -473,6 +474,103 @@ def mlp_leg(mt, torch, stream):
     return out
 
 
+def batched_leg(mt, torch, stream, args, world, local):
+    """The batched configuration: 256 pairs with uneven counts in one
+    CUDA-graph launch per step, in the requested form and the plain form,
+    with the per-stage split; the 64-pair float batch in both forms and both
+    tensor-core passes."""
+    from paper_2603_18401_gb300 import EgmError
+
+    import synth as _synth
+
+    bsc = _synth.config3(seed=0, npairs=args.batch_pairs)
+    bitems = [mt.to_device(s) for s in bsc]
+    bM = sum(s.m for s in bsc)
+
+    def time_graph(form, items=bitems, total=bM):
+        mt.set_params(form=form)
+        bout = mt._alloc_out(total, False, 0)
+        graph = mt.graph_create(items, bout)
+        for _ in range(3):
+            if graph.launch() != 0:
+                raise EgmError(mt.sync(), "batched warm-up")
+        torch.cuda.synchronize()
+        bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.batch_steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        for k in range(args.batch_steps):
+            bev[k][0].record(stream)
+            graph.launch()
+            bev[k][1].record(stream)
+        torch.cuda.synchronize()
+        st = mt.sync()
+        if st != 0:
+            raise EgmError(st, "batched timed region")
+        graph.close()
+        return max_over_ranks(sum(a.elapsed_time(b) for a, b in bev), world, local) / args.batch_steps
+
+    bform = {"auto": 0, "plain": 1, "banded": 2}[args.form]
+    bms = time_graph(bform)
+    # per-stage split of one batch, outside the timed region
+    mt.set_timing(True)
+    for _ in range(3):
+        mt.match_batch(bitems)
+    bt = mt.timing()
+    mt.set_timing(False)
+    bstage = {k[:-3]: round(bt[k] / max(bt["calls"], 1), 4) for k in bt if k.endswith("_ms")}
+    in_bytes = sum(s.xy1.nbytes + s.xy2.nbytes + s.desc1.nbytes + s.desc2.nbytes for s in bsc)
+    batched = {"workload": f"{len(bsc)} pairs 6048x4032, per-image counts log-uniform in [1024, 32768], "
+                           "random poses (rotation up to 30 deg), u8 L2 on even / 256-bit binary on odd pairs",
+               "pairs_per_s": world * len(bsc) / (bms * 1e-3),
+               "queries_per_s": world * bM / (bms * 1e-3), "ms_per_step": bms, "steps": args.batch_steps,
+               "queries_per_step": bM, "refs_per_step": sum(s.n for s in bsc),
+               "input_bytes": int(in_bytes), "l2": "inputs larger than L2 (129 MB)",
+               "form": f"{args.form} (egm_graph_launch, one CUDA graph per step)",
+               "stage_ms": bstage}
+    if bform != 1:
+        # the band kernel over the batch: every query's packed row (256 B),
+        # sorted record (48 B) and result (17 B), every reference's packed row,
+        # record (16 B) and norms (16 B), once
+        kb = bM * (256 + 48 + 17) + sum(s.n for s in bsc) * (256 + 16 + 16)
+        ks = bstage["stab"] * 1e-3
+        peak, peak_kind = measured_peaks()
+        prof = kernel_profile("band_kernel", "batch")
+        batched["roofline"] = {"kernel": "band_kernel", "bound": "hbm", "achieved": kb / ks / 1e9, "peak": peak,
+                               "peak_source": peak_kind, "unit": "GB/s", "frac": kb / ks / 1e9 / peak,
+                               "algorithmic_bytes_per_launch": kb, "avg_launch_us": ks * 1e6,
+                               "traffic": prof.get("dram_bytes_per_launch") if prof else None,
+                               "tensor_pipe_active_pct": prof.get("tensor_pipe_active_pct") if prof else None}
+    if bform != 1 and not args.no_compare:
+        pms = time_graph(1)
+        batched["plain_form"] = {"pairs_per_s": world * len(bsc) / (pms * 1e-3), "ms_per_step": pms}
+    del bitems
+    # float descriptors: 128-d RootSIFT-like FP32, 16384 keypoints per image
+    if not args.no_float:
+        fsc = _synth.config4(seed=0, npairs=args.float_pairs)
+        fitems = [mt.to_device(s) for s in fsc]
+        fM = sum(s.m for s in fsc)
+        fms = time_graph(bform, fitems, fM)
+        fl = {"workload": f"{len(fsc)} pairs 6048x4032, 16384 keypoints per image, 128-d float L2 "
+                          "(RootSIFT-like), random poses",
+              "pairs_per_s": world * len(fsc) / (fms * 1e-3), "queries_per_s": world * fM / (fms * 1e-3),
+              "ms_per_step": fms, "form": args.form}
+        if bform != 1 and not args.no_compare:
+            pms = time_graph(1, fitems, fM)
+            fl["plain_form"] = {"pairs_per_s": world * len(fsc) / (pms * 1e-3), "ms_per_step": pms}
+            # the FP8 (E4M3, per-row scale) tensor-core pass instead of BF16
+            mt.set_params(float_pass=1)
+            f8 = time_graph(2, fitems, fM)
+            mt.set_params(float_pass=0)
+            fl["fp8_pass"] = {"pairs_per_s": world * len(fsc) / (f8 * 1e-3), "ms_per_step": f8,
+                              "form": "banded, FP8 E4M3 pass with per-row scales, FP32 rerank"}
+        fl["pass"] = "BF16 tensor-core pass, FP32 rerank (outputs identical to the plain FP32 form)"
+        batched["float_descriptors"] = fl
+        del fitems
+    mt.set_params(form=bform)
+    return batched
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -503,6 +601,14 @@ def run_ours(args):
     mt.reserve(max(s.m for s in scs), max(s.n for s in scs), 1)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=mt.device)
     stream = torch.cuda.current_stream()
+    if args.batched_only:
+        # the batched configuration alone (for profiling it): its own line
+        b = batched_leg(mt, torch, stream, args, world, local)
+        if rank == 0:
+            print(json.dumps({"metric": "pairs/sec batched", "value": b["pairs_per_s"], "unit": "pairs/s",
+                              "n_gpus": world, "higher_is_better": True, "batched": b}), flush=True)
+        mt.close()
+        return
 
     def step():
         for p, o in zip(pairs, ostr):
@@ -708,82 +814,7 @@ def run_ours(args):
     e2e_per_call = time_e2e(e2e_step_per_call, max(args.e2e_steps // 2, 1))
 
     # batched: 256 pairs with uneven counts in one CUDA-graph launch per step
-    batched = None
-    if not args.no_batched:
-        import synth as _synth
-
-        bsc = _synth.config3(seed=0, npairs=args.batch_pairs)
-        bitems = [mt.to_device(s) for s in bsc]
-        bM = sum(s.m for s in bsc)
-
-        def time_graph(form, items=bitems, total=bM):
-            mt.set_params(form=form)
-            bout = mt._alloc_out(total, False, 0)
-            graph = mt.graph_create(items, bout)
-            for _ in range(3):
-                if graph.launch() != 0:
-                    raise EgmError(mt.sync(), "batched warm-up")
-            torch.cuda.synchronize()
-            bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                   for _ in range(args.batch_steps)]
-            barrier(world)
-            torch.cuda.synchronize()
-            for k in range(args.batch_steps):
-                bev[k][0].record(stream)
-                graph.launch()
-                bev[k][1].record(stream)
-            torch.cuda.synchronize()
-            st = mt.sync()
-            if st != 0:
-                raise EgmError(st, "batched timed region")
-            graph.close()
-            return max_over_ranks(sum(a.elapsed_time(b) for a, b in bev), world, local) / args.batch_steps
-
-        bform = {"auto": 0, "plain": 1, "banded": 2}[args.form]
-        bms = time_graph(bform)
-        # per-stage split of one batch, outside the timed region
-        mt.set_timing(True)
-        for _ in range(3):
-            mt.match_batch(bitems)
-        bt = mt.timing()
-        mt.set_timing(False)
-        bstage = {k[:-3]: round(bt[k] / max(bt["calls"], 1), 4) for k in bt if k.endswith("_ms")}
-        in_bytes = sum(s.xy1.nbytes + s.xy2.nbytes + s.desc1.nbytes + s.desc2.nbytes for s in bsc)
-        batched = {"workload": f"{len(bsc)} pairs 6048x4032, per-image counts log-uniform in [1024, 32768], "
-                               "random poses (rotation up to 30 deg), u8 L2 on even / 256-bit binary on odd pairs",
-                   "pairs_per_s": world * len(bsc) / (bms * 1e-3),
-                   "queries_per_s": world * bM / (bms * 1e-3), "ms_per_step": bms, "steps": args.batch_steps,
-                   "queries_per_step": bM, "refs_per_step": sum(s.n for s in bsc),
-                   "input_bytes": int(in_bytes), "l2": "inputs larger than L2 (129 MB)",
-                   "form": f"{args.form} (egm_graph_launch, one CUDA graph per step)",
-                   "stage_ms": bstage}
-        if bform != 1 and not args.no_compare:
-            pms = time_graph(1)
-            batched["plain_form"] = {"pairs_per_s": world * len(bsc) / (pms * 1e-3), "ms_per_step": pms}
-        del bitems
-        # float descriptors: 128-d RootSIFT-like FP32, 16384 keypoints per image
-        if not args.no_float:
-            fsc = _synth.config4(seed=0, npairs=args.float_pairs)
-            fitems = [mt.to_device(s) for s in fsc]
-            fM = sum(s.m for s in fsc)
-            fms = time_graph(bform, fitems, fM)
-            fl = {"workload": f"{len(fsc)} pairs 6048x4032, 16384 keypoints per image, 128-d float L2 "
-                              "(RootSIFT-like), random poses",
-                  "pairs_per_s": world * len(fsc) / (fms * 1e-3), "queries_per_s": world * fM / (fms * 1e-3),
-                  "ms_per_step": fms, "form": args.form}
-            if bform != 1 and not args.no_compare:
-                pms = time_graph(1, fitems, fM)
-                fl["plain_form"] = {"pairs_per_s": world * len(fsc) / (pms * 1e-3), "ms_per_step": pms}
-                # the FP8 (E4M3, per-row scale) tensor-core pass instead of BF16
-                mt.set_params(float_pass=1)
-                f8 = time_graph(2, fitems, fM)
-                mt.set_params(float_pass=0)
-                fl["fp8_pass"] = {"pairs_per_s": world * len(fsc) / (f8 * 1e-3), "ms_per_step": f8,
-                                  "form": "banded, FP8 E4M3 pass with per-row scales, FP32 rerank"}
-            fl["pass"] = "BF16 tensor-core pass, FP32 rerank (outputs identical to the plain FP32 form)"
-            batched["float_descriptors"] = fl
-            del fitems
-        mt.set_params(form=bform)
+    batched = None if args.no_batched else batched_leg(mt, torch, stream, args, world, local)
 
     # mutual matching and the match list, with recall / precision on the
     # scenes' true pairs (synthetic ground truth)
