@@ -111,7 +111,11 @@ __device__ __forceinline__ void copy16(void *dst, const void *src, int bytes, in
 }
 
 // mode 0: fused matching; 1: count candidates; 2: write candidate rows and match.
-template <int KIND>
+// ONE: a call of one pair whose descriptor rows (u8 or binary) are staged
+// whole: every block is uniform, and the paths for blocks that span pairs or
+// read rows piecewise are compiled out (their registers would otherwise
+// crowd the common path into local memory).
+template <int KIND, bool ONE>
 __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mode) {
     pdl_begin();
     __shared__ __align__(16) StabSmem S;
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mod
             }
             // queries of another pair than the block's first: one warp per query, lane = level
 #pragma unroll 1
-            for (int t = 0; t < kQPerWarp; t++) {
+            for (int t = 0; t < (ONE ? 0 : kQPerWarp); t++) {
                 const int ql = qbase + t;
                 if (ql >= nqb || S.qr[ql].pair == S.gpair) continue;
                 const int p = S.qr[ql].pair;
@@ -243,8 +247,10 @@ __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mod
             if (dslot[k] >= 0) (&S.qdesc[0][0])[dslot[k]] = dv[k];
         // every query of the block in the cached pair, descriptors of one kind
         // and staged: the pair's fields are block constants (the common case)
-        const bool uni = __syncthreads_and(tid >= nqb || S.qr[tid].pair == S.gpair) && KIND != kKindAny &&
-                         S.pd.row_bytes <= kDescCache;
+        bool uni = true;
+        if (ONE) __syncthreads();
+        else uni = __syncthreads_and(tid >= nqb || S.qr[tid].pair == S.gpair) && KIND != kKindAny &&
+                   S.pd.row_bytes <= kDescCache;
         const float4 *recb = L.rec + S.pd.r_off;
         if (warp == 0) {
             uint32_t incl = S.tq[lane];
@@ -324,16 +330,27 @@ __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mod
                 }
 #pragma unroll 1
                 for (int t = 0; t < kBatch; t++) {
-                    const int qq = bq[t];
+                    // element t of the batch by register selects: a dynamic index into
+                    // these arrays would place them in local memory
+                    int qq = bq[0];
+                    bool bvt = bv[0];
+                    float4 rct = rc[0];
+#pragma unroll
+                    for (int u = 1; u < kBatch; u++)
+                        if (t == u) {
+                            qq = bq[u];
+                            bvt = bv[u];
+                            rct = rc[u];
+                        }
                     uint32_t j = 0;
                     bool cand = false;
-                    if (bv[t]) {
+                    if (bvt) {
                         const QueryRec &r = S.qr[qq];
-                        j = __float_as_uint(rc[t].w);
+                        j = __float_as_uint(rct.w);
                         nwin++;
                         bool exact = (r.flags & kQExactOnly) != 0;
                         if (!exact) {
-                            const float x = rc[t].x, y = rc[t].y, e = rc[t].z;
+                            const float x = rct.x, y = rct.y, e = rct.z;
                             const float d = fabsf(fmaf(r.A, x, fmaf(r.B, y, r.C)));
                             const float Sm = fmaf(fabsf(r.A), fabsf(x), fmaf(fabsf(r.B), fabsf(y), fabsf(r.C)));
                             // FP32 rounding (16u S), the FP32 tolerance (2u eps) and the
@@ -407,7 +424,7 @@ __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mod
                 const int groups = kStabThreads / G;
                 const int gl = tid % G;
                 constexpr int U = 4;
-                if (uni && chunks0 <= G) {
+                if (ONE || (uni && chunks0 <= G)) {
                     // block constants; one chunk per lane of each candidate
                     const uint4 *d2 = reinterpret_cast<const uint4 *>(S.pd.desc2);
                     const int rb16 = chunks0;
@@ -568,11 +585,19 @@ cudaError_t launch_stab(const Launch &L, int mode, cudaStream_t s) {
     int64_t blocks = (L.nq + kQB - 1) / kQB;
     if (blocks > 152 * 8) blocks = 152 * 8;
     const dim3 g((unsigned)blocks), b(kStabThreads);
+    // one pair with rows of 16..256 bytes, a power of two (u8 128-d, binary
+    // 256-bit): the uniform variant
+    const int rb = L.inl_use ? L.inl.row_bytes : 0;
+    const bool one = L.npairs == 1 && L.inl_use && rb >= 16 && rb <= kDescCache && (rb & (rb - 1)) == 0;
     switch (L.kind) {
-        case EGM_DESC_U8_L2: return launch_pdl(stab_kernel<EGM_DESC_U8_L2>, g, b, 0, s, L, mode);
-        case EGM_DESC_BIN: return launch_pdl(stab_kernel<EGM_DESC_BIN>, g, b, 0, s, L, mode);
-        case EGM_DESC_F32_L2: return launch_pdl(stab_kernel<EGM_DESC_F32_L2>, g, b, 0, s, L, mode);
-        default: return launch_pdl(stab_kernel<kKindAny>, g, b, 0, s, L, mode);
+        case EGM_DESC_U8_L2:
+            return one ? launch_pdl(stab_kernel<EGM_DESC_U8_L2, true>, g, b, 0, s, L, mode)
+                       : launch_pdl(stab_kernel<EGM_DESC_U8_L2, false>, g, b, 0, s, L, mode);
+        case EGM_DESC_BIN:
+            return one ? launch_pdl(stab_kernel<EGM_DESC_BIN, true>, g, b, 0, s, L, mode)
+                       : launch_pdl(stab_kernel<EGM_DESC_BIN, false>, g, b, 0, s, L, mode);
+        case EGM_DESC_F32_L2: return launch_pdl(stab_kernel<EGM_DESC_F32_L2, false>, g, b, 0, s, L, mode);
+        default: return launch_pdl(stab_kernel<kKindAny, false>, g, b, 0, s, L, mode);
     }
 }
 
