@@ -6,7 +6,7 @@ image pairs of 6048x4032 px with 16384 keypoints per image (70% true
 projections), epipole inside / far outside / at infinity, eps in {1, 2, 4} px,
 128-d uint8 descriptors.  One step matches all nine pairs, one pair per
 egm_match_pair call, in the library's automatic form (the plain form on
-sparse pairs, the banded tensor-core form where about 20 or more candidates
+sparse pairs, the banded tensor-core form where about 32 or more candidates
 per query are expected; --form forces one).  Inputs are resident in HBM
 before the timed region; L2 is flushed (a 256 MiB write) before every step
 and the flush is outside the CUDA-event-timed interval.

@@ -145,7 +145,7 @@ typedef struct egm_out {
 enum {
     EGM_FORM_AUTO = 0,     /* library choice: banded for batches with more than two
                               128-query tiles per SM, or when every pair has u8
-                              descriptors, a scalar eps and an expected 20 or more
+                              descriptors, a scalar eps and an expected 32 or more
                               candidates per query (2 eps n / (W H) x 0.8 of the
                               image diagonal); plain otherwise */
     EGM_FORM_PLAIN = 1,    /* windowed stabbing + CUDA-core descriptor distances */

@@ -165,7 +165,7 @@ struct Plan {
     int max_n = 0;
     bool band_ok = false;           // every pair fits the banded form
     bool has_float = false;         // some pair has float descriptors
-    bool dense_u8 = false;          // every pair u8 with a scalar tolerance and >= 20 estimated candidates per query
+    bool dense_u8 = false;          // every pair u8 with a scalar tolerance and >= 32 estimated candidates per query
 };
 
 egm_status make_plan(const egm_pair *pairs, int npairs, Plan &pl) {
@@ -216,7 +216,7 @@ egm_status make_plan(const egm_pair *pairs, int npairs, Plan &pl) {
         const egm_pair &A = pairs[p];
         const double W = A.width, H = A.height;
         const double kbar = 2.0 * A.eps_scalar * (double)A.n / (W * H) * 0.8 * std::sqrt(W * W + H * H);
-        pl.dense_u8 = pl.dense_u8 && has_desc(&A) && A.kind == EGM_DESC_U8_L2 && !A.eps2 && kbar >= 20.0;
+        pl.dense_u8 = pl.dense_u8 && has_desc(&A) && A.kind == EGM_DESC_U8_L2 && !A.eps2 && kbar >= 32.0;
     }
     for (int p = 0; p <= npairs; p++) {
         pl.offs[p] = pl.qoffs[p];
@@ -251,7 +251,7 @@ size_t offs_entries(int npairs, int64_t nq) {
 
 // The banded form runs when every pair fits it, no candidate lists are asked
 // for, and it is requested -- or left to the library and either the call has
-// more than two tiles per SM or its u8 pairs are dense (about 20 or more
+// more than two tiles per SM or its u8 pairs are dense (about 32 or more
 // candidates per query).  With few tiles of sparse pairs every CTA of the
 // band kernel takes one latency-bound tile and the plain form (no query
 // sort, no packing) finishes first; with many tiles the banded form's

@@ -50,7 +50,11 @@ static_assert(kQB == 32, "one lane per query in the segment scan");
 constexpr int kStabThreads = 256;
 constexpr int kRangesPerQuery = 2 * kLevels;
 constexpr int kDescCache = 256;  // query descriptors up to this many bytes are staged in shared memory
-constexpr int kBatch = 4;
+// window elements a thread tests per batch of record loads, and candidates
+// per lane group in the distance pass: smaller in the single-pair variant,
+// where fewer registers keep the kernel out of local memory
+template <bool ONE> constexpr int kBatchOf = ONE ? 2 : 4;
+template <bool ONE> constexpr int kUOf = ONE ? 2 : 4;
 constexpr int kRound = 1024;     // window elements tested per round
 constexpr int kQPerWarp = kQB / (kStabThreads / 32);
 
@@ -104,6 +108,16 @@ __device__ __forceinline__ void chunk_dist(int kind, uint4 a, uint4 b, uint32_t 
     }
 }
 
+// 16-byte asynchronous copy global -> shared (no registers held while it is
+// in flight); cp_async_wait() before the data is read
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ void copy16(void *dst, const void *src, int bytes, int lane) {
     const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
     uint4 *d4 = reinterpret_cast<uint4 *>(dst);
@@ -117,6 +131,7 @@ __device__ __forceinline__ void copy16(void *dst, const void *src, int bytes, in
 // crowd the common path into local memory).
 template <int KIND, bool ONE>
 __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mode) {
+    constexpr int kBatch = kBatchOf<ONE>;
     pdl_begin();
     __shared__ __align__(16) StabSmem S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -161,23 +176,19 @@ __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mod
             S.rmask[tid][0] = S.rmask[tid][1] = 0u;
         }
         __syncthreads();
+        // the query descriptors, copied to shared memory while the windows are computed
         constexpr int kStage = kQPerWarp * kDescCache / 16 / 32;
-        uint4 dv[kStage];
-        int dslot[kStage];
 #pragma unroll
         for (int k = 0; k < kStage; k++) {
             const int idx = lane + 32 * k;
             const int ql = qbase + idx / (kDescCache / 16);
             const int c = idx % (kDescCache / 16);
-            dslot[k] = -1;
             if (mode != 1 && ql < nqb) {
                 const int p = S.qr[ql].pair;
                 const PairDesc &P = p == S.gpair ? S.pd : L.pairs[p];
-                if (P.row_bytes > 0 && P.row_bytes <= kDescCache && c < (P.row_bytes >> 4)) {
-                    dv[k] = __ldg(reinterpret_cast<const uint4 *>(P.desc1 + (q0 + ql - P.q_off) *
-                                                                            (int64_t)P.row_bytes) + c);
-                    dslot[k] = ql * (kDescCache / 16) + c;
-                }
+                if (P.row_bytes > 0 && P.row_bytes <= kDescCache && c < (P.row_bytes >> 4))
+                    cp_async16(&S.qdesc[ql][c], reinterpret_cast<const uint4 *>(P.desc1 + (q0 + ql - P.q_off) *
+                                                                                         (int64_t)P.row_bytes) + c);
             }
         }
         {
@@ -242,9 +253,7 @@ __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mod
                 }
             }
         }
-#pragma unroll
-        for (int k = 0; k < kStage; k++)
-            if (dslot[k] >= 0) (&S.qdesc[0][0])[dslot[k]] = dv[k];
+        cp_async_wait();
         // every query of the block in the cached pair, descriptors of one kind
         // and staged: the pair's fields are block constants (the common case)
         bool uni = true;
@@ -423,7 +432,7 @@ __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mod
                             : chunks0 >= 2 ? 2 : 1;
                 const int groups = kStabThreads / G;
                 const int gl = tid % G;
-                constexpr int U = 4;
+                constexpr int U = kUOf<ONE>;
                 if (ONE || (uni && chunks0 <= G)) {
                     // block constants; one chunk per lane of each candidate
                     const uint4 *d2 = reinterpret_cast<const uint4 *>(S.pd.desc2);
