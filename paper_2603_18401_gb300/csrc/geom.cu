@@ -75,9 +75,11 @@ __global__ void __launch_bounds__(32) geometry_kernel(Launch L) {
     double fn2 = 0.0;
 #pragma unroll
     for (int k = 0; k < 9; k++) fn2 = fma(F[k], F[k], fn2);
-    const int c0 = lane == 2 ? 1 : 0, c1 = lane == 0 ? 1 : 2;  // column pairs (0,1) (0,2) (1,2)
-    const double ax = F[c0], ay = F[3 + c0], az = F[6 + c0];
-    const double bx = F[c1], by = F[3 + c1], bz = F[6 + c1];
+    // column pairs (0,1) (0,2) (1,2), picked by selects (an index that depends
+    // on the lane would move F to local memory)
+    const bool a1 = lane == 2, b1 = lane == 0;
+    const double ax = a1 ? F[1] : F[0], ay = a1 ? F[4] : F[3], az = a1 ? F[7] : F[6];
+    const double bx = b1 ? F[1] : F[2], by = b1 ? F[4] : F[5], bz = b1 ? F[7] : F[8];
     double crx = fma(ay, bz, -az * by), cry = fma(az, bx, -ax * bz), crz = fma(ax, by, -ay * bx);
     double nk = lane < 3 ? fma(crx, crx, fma(cry, cry, crz * crz)) : -1.0;
     int best = lane;
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
         uint32_t s_bits = 0, d_bits = 0x7f800000u, t_bits = 0;
         if (valid && is_ref) {
             const int p = cached ? pair_of_shared(s_roffs, L.npairs, g) : pair_of(L.r_offs, L.npairs, g);
-            const PairDesc &P = L.pairs[p];
+            const PairView P = pair_view(L, p);
             const PairGeom &G = L.geom[p];
             const int64_t j = g - P.r_off;
             const double x = P.xy2[2 * j], y = P.xy2[2 * j + 1];
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
         } else if (valid) {
             const int64_t gq = g - L.nr;
             const int p = cached ? pair_of_shared(s_qoffs, L.npairs, gq) : pair_of(L.q_offs, L.npairs, gq);
-            const PairDesc &P = L.pairs[p];
+            const PairView P = pair_view(L, p);
             const PairGeom &G = L.geom[p];
             const int64_t i = gq - P.q_off;
             const double x1 = P.xy1[2 * i], y1 = P.xy1[2 * i + 1];

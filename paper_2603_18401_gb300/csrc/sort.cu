@@ -258,7 +258,7 @@ __global__ void __cluster_dims__(kScanCtas, 1, 1) __launch_bounds__(kScanThreads
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int p = blockIdx.x / kScanCtas;
-    const PairDesc &P = L.pairs[p];
+    const PairView P = pair_view(L, p);
     if (tid < (int)(sizeof(PairGeom) / 16))
         reinterpret_cast<uint4 *>(&G)[tid] = reinterpret_cast<const uint4 *>(L.geom + p)[tid];
     __syncthreads();
