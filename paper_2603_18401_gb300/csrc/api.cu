@@ -39,6 +39,10 @@ T *as(DevBuf &b) { return reinterpret_cast<T *>(b.ptr); }
 // Device scratch of one pipeline instance (a context, or a captured graph).
 struct Scratch {
     DevBuf pairs, geom, offs, keys, rec, tab, curs, qrec, qcount, scan, longlist, small, counters, blkpair, band;
+    // the pair table, offsets and geometry are double-buffered: call k uses
+    // half k mod 2, so that its geometry kernel can write while call k - 1's
+    // last kernel still reads the other half
+    int parity = 0;
     void release() {
         DevBuf *b[] = {&pairs, &geom, &offs, &keys, &rec, &tab, &curs, &qrec, &qcount, &scan, &longlist, &small,
                        &counters, &blkpair, &band};
@@ -288,9 +292,9 @@ cudaError_t reserve(Scratch &c_, int64_t nq, int64_t nr, int64_t ntab, int npair
     Scratch *c = &c_;
     cudaError_t e;
     if (band && (e = grow(c->band, BandLayout(nq, nr).total)) != cudaSuccess) return e;
-    if ((e = grow(c->pairs, sizeof(PairDesc) * (size_t)std::max(npairs, 1))) != cudaSuccess) return e;
-    if ((e = grow(c->geom, sizeof(PairGeom) * (size_t)std::max(npairs, 1))) != cudaSuccess) return e;
-    if ((e = grow(c->offs, sizeof(int64_t) * offs_entries(npairs, nq))) != cudaSuccess) return e;
+    if ((e = grow(c->pairs, 2 * sizeof(PairDesc) * (size_t)std::max(npairs, 1) + 512)) != cudaSuccess) return e;
+    if ((e = grow(c->geom, 2 * sizeof(PairGeom) * (size_t)std::max(npairs, 1) + 512)) != cudaSuccess) return e;
+    if ((e = grow(c->offs, 2 * sizeof(int64_t) * offs_entries(npairs, nq) + 512)) != cudaSuccess) return e;
     if ((e = grow(c->keys, sizeof(uint32_t) * 6 * (size_t)std::max<int64_t>(nr, 1))) != cudaSuccess) return e;
     // 32 records of padding: bulk copies of a 32-row box may run past the last row
     if ((e = grow(c->rec, sizeof(float4) * (size_t)(nr + 32))) != cudaSuccess) return e;
@@ -306,18 +310,27 @@ cudaError_t reserve(Scratch &c_, int64_t nq, int64_t nr, int64_t ntab, int npair
     return cudaSuccess;
 }
 
+// Half `parity` of a double-buffered scratch buffer (halves of half its
+// capacity, 256-byte aligned: the same split for every call while the buffer
+// does not grow).
+template <class T>
+T *half_of(DevBuf &b, int parity) {
+    return reinterpret_cast<T *>(static_cast<char *>(b.ptr) + (parity ? (b.bytes / 2) & ~(size_t)255 : 0));
+}
+
 Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const Plan &pl, int npairs,
                    const egm_out *out, bool band = false) {
     Scratch *c = &sc;
     Launch L;
     memset(&L, 0, sizeof(L));
-    L.pairs = as<PairDesc>(c->pairs);
-    L.geom = as<PairGeom>(c->geom);
+    L.pairs = half_of<PairDesc>(c->pairs, c->parity);
+    L.geom = half_of<PairGeom>(c->geom, c->parity);
     L.npairs = npairs;
     L.nq = pl.nq;
     L.nr = pl.nr;
-    L.q_offs = as<int64_t>(c->offs);
-    L.r_offs = as<int64_t>(c->offs) + (npairs + 1);
+    int64_t *offs = half_of<int64_t>(c->offs, c->parity);
+    L.q_offs = offs;
+    L.r_offs = offs + (npairs + 1);
     uint32_t *k = as<uint32_t>(c->keys);
     const size_t nr = (size_t)std::max<int64_t>(pl.nr, 1);
     L.key_a = k;
@@ -355,8 +368,8 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
         L.rnorm = reinterpret_cast<float4 *>(b + bl.rnorm);
         L.qscale = reinterpret_cast<float *>(b + bl.qscale);
         L.fp8 = prm.float_pass == EGM_FLOAT_PASS_FP8;
-        L.tile_offs = as<int64_t>(c->offs) + 2 * (npairs + 1);
-        L.tile_seq = reinterpret_cast<const int32_t *>(as<int64_t>(c->offs) + 3 * (npairs + 1));
+        L.tile_offs = offs + 2 * (npairs + 1);
+        L.tile_seq = reinterpret_cast<const int32_t *>(offs + 3 * (npairs + 1));
         L.work = as<uint32_t>(c->small) + 32;
         L.ntiles = pl.ntiles;
     }
@@ -406,8 +419,11 @@ cudaError_t upload_plan(egm_ctx *c, const Plan &pl, int npairs) {
     unsigned char *h = static_cast<unsigned char *>(c->h_table[k]);
     memcpy(h, pl.pd.data(), tb);
     memcpy(h + tb, pl.offs.data(), ob);
-    if ((e = cudaMemcpyAsync(c->sc.pairs.ptr, h, tb, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(c->sc.offs.ptr, h + tb, ob, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(half_of<PairDesc>(c->sc.pairs, c->sc.parity), h, tb, cudaMemcpyHostToDevice,
+                             c->stream)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(half_of<int64_t>(c->sc.offs, c->sc.parity), h + tb, ob, cudaMemcpyHostToDevice,
+                             c->stream)) != cudaSuccess)
         return e;
     if ((e = cudaEventRecord(c->slot_ev[k], c->stream)) != cudaSuccess) return e;
     c->slot_pending[k] = true;
@@ -576,6 +592,7 @@ egm_status run_batch(egm_ctx *c, const egm_pair *pairs, int npairs, const egm_ou
     EGM_TRY(cudaSetDevice(c->device));
     if (band) EGM_TRY(ensure_side(c));
     EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, npairs, band));
+    c->sc.parity ^= 1;
     if (npairs > 1) EGM_TRY(upload_plan(c, pl, npairs));  // one pair: the plan rides in the launch
     Launch L = make_launch(c->sc, c->counters_on, c->params, pl, npairs, out, band);
     cudaStream_t st = c->stream;
@@ -967,6 +984,7 @@ egm_status egm_intervals(egm_ctx *c, const egm_pair *pair, double *theta, double
     if (s != EGM_OK) return s;
     EGM_TRY(cudaSetDevice(c->device));
     EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, 1, false));
+    c->sc.parity ^= 1;
     EGM_TRY(upload_plan(c, pl, 1));
     Launch L = make_launch(c->sc, false, c->params, pl, 1, nullptr);
     if (c->params.sync) EGM_TRY(cudaMemsetAsync(L.status, 0, sizeof(uint32_t), c->stream));

@@ -30,9 +30,11 @@ namespace egm {
 // predecessor has completed and its memory is visible (so no kernel touches
 // global memory early) and then lets the successor be scheduled.  For a
 // kernel launched without the attribute both instructions return at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_begin() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    pdl_wait();
+    pdl_trigger();
 }
 
 template <typename... KArgs, typename... Args>

@@ -36,8 +36,13 @@ __device__ __forceinline__ float fold_atan2(float px, float py) {
     return atan2f(py, px);
 }
 
+// The geometry kernel reads only its parameters (or a pair table uploaded
+// before it) and writes this call's half of the double-buffered pair table,
+// offsets and geometry, which the previous call no longer reads: it computes
+// while the previous call's last kernel runs and waits for that kernel only
+// before it ends, so that the kernels after it see the previous call done.
 __global__ void __launch_bounds__(32) geometry_kernel(Launch L) {
-    pdl_begin();
+    pdl_trigger();
     const int p = blockIdx.x;
     const int lane = threadIdx.x;
     if (L.inl_use) {
@@ -149,7 +154,10 @@ __global__ void __launch_bounds__(32) geometry_kernel(Launch L) {
         hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
     if (lane < 9) G.Ff[lane] = (float)fv;
-    if (lane != 0) return;
+    if (lane != 0) {
+        pdl_wait();
+        return;
+    }
     if (!finite) set_status(L.status, kStNan);
     else if (degenerate) set_status(L.status, kStDegenerateF);
     G.ex = ex;
@@ -188,6 +196,7 @@ __global__ void __launch_bounds__(32) geometry_kernel(Launch L) {
         const float dr = hypotf(dx, dy);
         G.level_base = ilogbf(fmaxf(dr, 2.0f * eps_ref) / eps_ref) - 1;
     }
+    pdl_wait();
 }
 
 
