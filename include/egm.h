@@ -185,7 +185,12 @@ void egm_default_params(egm_params *params);
  * references and pairs per call, so that later calls allocate nothing. */
 egm_status egm_reserve(egm_ctx *ctx, int64_t queries, int64_t refs, int32_t pairs);
 
-/* Match one pair (steps 1-8 above).  Device pointers. */
+/* Match one pair (steps 1-8 above).  Device pointers.
+ * Calls on a context are ordered on its stream, with one relaxation: when a
+ * call directly follows another call of the context on the stream, its
+ * first kernel may read the new F (9 doubles) while the previous call's last
+ * kernel still runs; F must therefore not alias the previous call's output
+ * arrays.  Every other input is read only after the previous call ended. */
 egm_status egm_match_pair(egm_ctx *ctx, const egm_pair *pair, const egm_out *out);
 
 /* Match npairs independent pairs in one pass (one launch per step for the
