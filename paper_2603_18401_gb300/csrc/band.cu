@@ -136,6 +136,9 @@ __device__ __forceinline__ uint32_t e4m3_nibble(uint32_t n) {
 }
 
 // 8 threads per row; thread part t writes output bytes [32 t, 32 t + 32).
+// F8: float rows packed for the FP8 pass (a separate variant: its staged
+// values would cost the common variant registers and occupancy).
+template <bool F8>
 __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
     pdl_begin();
     if (blockIdx.x == 0 && threadIdx.x == 0) *L.work = 0u;  // the band kernel's tile dispenser
@@ -185,7 +188,7 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
                 }
                 o0 = make_uint4(out[0], out[1], out[2], out[3]);
                 o1 = make_uint4(out[4], out[5], out[6], out[7]);
-            } else if (P.kind == EGM_DESC_F32_L2 && L.fp8) {
+            } else if (F8 && P.kind == EGM_DESC_F32_L2) {
                 // FP8 pass, step 1: 16 values per thread and their largest magnitude
                 // (the row's scale needs the maximum over its 8 threads)
                 isf = isf8 = true;
@@ -233,9 +236,11 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
         // 128..255, and the squared norm and rounding error are those of
         // s e4m3(x / s), the row the tensor cores see
         float scale = 1.0f;
+        if (F8) {
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o, 8));
-        if (isf8) {
+            for (int o = 4; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o, 8));
+        }
+        if (F8 && isf8) {
             const float inv = amax > 0.0f ? 448.0f / amax : 1.0f;
             scale = amax > 0.0f ? amax / 448.0f : 1.0f;
             uint32_t w[4] = {0u, 0u, 0u, 0u};
@@ -260,7 +265,7 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
         const float norm = isf ? fnrm : (float)nrm;
         const float err = isf ? sqrtf(ferr) * 1.0001f + 1e-30f : 0.0f;
         if (valid) {
-            if (isf8) {
+            if (F8 && isf8) {
                 // 16 bytes per thread: bytes [16 part, 16 part + 16), zeros above 128
                 reinterpret_cast<uint4 *>(dst)[part] = o0;
                 reinterpret_cast<uint4 *>(dst)[8 + part] = make_uint4(0u, 0u, 0u, 0u);
@@ -989,7 +994,8 @@ cudaError_t launch_pack(const Launch &L, cudaStream_t s) {
     if (rows == 0) return cudaSuccess;
     int64_t blocks = (rows * 8 + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    pack_kernel<<<(int)blocks, 256, 0, s>>>(L);
+    if (L.fp8 && (L.kinds & (1u << EGM_DESC_F32_L2))) pack_kernel<true><<<(int)blocks, 256, 0, s>>>(L);
+    else pack_kernel<false><<<(int)blocks, 256, 0, s>>>(L);
     return cudaGetLastError();
 }
 
