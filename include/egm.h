@@ -319,6 +319,22 @@ egm_status egm_gms(egm_ctx *ctx, const double *xy1, int64_t m, const double *xy2
                    uint8_t *flags, int32_t width1, int32_t height1, int32_t width2, int32_t height2,
                    uint32_t require, int32_t grid, double alpha);
 
+/* egm_gms over several pairs in one call (one set of launches; pairs are
+ * filtered independently).  Each entry as the arguments of egm_gms, device
+ * pointers; m <= 2^31 - 1 in total.  EGM_ERR_ARG if any entry is invalid
+ * (nothing is launched then). */
+typedef struct egm_gms_pair {
+    const double *xy1;
+    const double *xy2;
+    const int32_t *best;
+    uint8_t *flags;
+    int64_t m, n;
+    int32_t width1, height1, width2, height2;
+} egm_gms_pair;
+
+egm_status egm_gms_batch(egm_ctx *ctx, const egm_gms_pair *pairs, int32_t npairs, uint32_t require, int32_t grid,
+                         double alpha);
+
 egm_status egm_intervals(egm_ctx *ctx, const egm_pair *pair, double *theta, double *delta,
                          double *e3, int32_t *mode);
 

@@ -299,6 +299,18 @@ class Matcher:
               "egm_gms")
         return flags
 
+    def gms_batch(self, items, require=EGM_FLAG_HAS_BEST, grid=20, alpha=6.0):
+        """egm_gms_batch: items of (xy1, xy2, best, flags, size1, size2) device
+        tensors; every flags tensor is updated in place."""
+        arr = (_egm.egm_gms_pair * len(items))()
+        for k, (xy1, xy2, best, flags, size1, size2) in enumerate(items):
+            q = arr[k]
+            q.xy1, q.xy2, q.best, q.flags = _ptr(xy1), _ptr(xy2), _ptr(best), _ptr(flags)
+            q.m, q.n = int(xy1.shape[0]), int(xy2.shape[0])
+            q.width1, q.height1, q.width2, q.height2 = int(size1[0]), int(size1[1]), int(size2[0]), int(size2[1])
+        check(self.lib.egm_gms_batch(self.ctx, arr, len(items), int(require), int(grid), float(alpha)),
+              "egm_gms_batch")
+
     def tolnet(self, params) -> "TolNet":
         """A learned-tolerance network on this context (egm_mlp_create)."""
         return TolNet(self, params)

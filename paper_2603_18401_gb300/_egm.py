@@ -76,6 +76,12 @@ class egm_timing(C.Structure):
                 ("calls", C.c_int64), ("banded_calls", C.c_int64)]
 
 
+class egm_gms_pair(C.Structure):
+    _fields_ = [("xy1", C.c_void_p), ("xy2", C.c_void_p), ("best", C.c_void_p), ("flags", C.c_void_p),
+                ("m", C.c_int64), ("n", C.c_int64), ("width1", C.c_int32), ("height1", C.c_int32),
+                ("width2", C.c_int32), ("height2", C.c_int32)]
+
+
 # name -> (restype, argtypes); every symbol include/egm.h declares
 SIGNATURES = {
     "egm_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
@@ -107,6 +113,7 @@ SIGNATURES = {
                                      C.c_void_p]),
     "egm_match_mutual": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.POINTER(egm_pair), C.POINTER(egm_out)]),
     "egm_match_batch_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "egm_gms_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_uint32, C.c_int32, C.c_double]),
     "egm_gms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                           C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, C.c_int32, C.c_double]),
     "egm_compact_matches": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_uint32, C.c_void_p,

@@ -66,7 +66,10 @@ struct egm_ctx {
     Scratch sc;
     DevBuf stage;  // host-path staging of inputs and outputs
     DevBuf compact;  // tile counts of egm_compact_matches
-    DevBuf gms;      // egm_gms: matches sorted by cell, decisions per grid shift
+    DevBuf gms;      // egm_gms: pair table, matches sorted by cell, decisions per grid shift
+    void *gms_host = nullptr;        // pinned staging of the GMS pair table
+    size_t gms_host_bytes = 0;
+    cudaEvent_t gms_host_ev = nullptr;
     // pinned host memory for the pair table and the status word
     // pinned staging slots of the pair-table uploads, used round-robin: the
     // host waits only when a slot's previous upload is still in flight
@@ -677,6 +680,8 @@ egm_status egm_destroy(egm_ctx *c) {
     if (c->stage.ptr) cudaFree(c->stage.ptr);
     if (c->compact.ptr) cudaFree(c->compact.ptr);
     if (c->gms.ptr) cudaFree(c->gms.ptr);
+    if (c->gms_host) cudaFreeHost(c->gms_host);
+    if (c->gms_host_ev) cudaEventDestroy(c->gms_host_ev);
     for (int k = 0; k < egm_ctx::kSlots; k++) {
         if (c->h_table[k]) cudaFreeHost(c->h_table[k]);
         if (c->slot_ev[k]) cudaEventDestroy(c->slot_ev[k]);
@@ -959,19 +964,67 @@ egm_status egm_compact_matches(egm_ctx *c, const uint8_t *flags, const int32_t *
     return EGM_OK;
 }
 
+namespace {
+
+// GMS over a table of pairs: validation, upload of the table and row offsets
+// (pinned staging, reused once its previous copy has finished), launch.
+egm_status run_gms(egm_ctx *c, const egm_gms_pair *pairs, int32_t npairs, uint32_t require, int32_t grid,
+                   double alpha) {
+    if (!c || npairs < 0 || (npairs > 0 && !pairs) || grid < 1 || grid > 48 || !(alpha > 0.0) ||
+        !(alpha < INFINITY))
+        return EGM_ERR_ARG;
+    std::vector<GmsPair> tab((size_t)npairs);
+    std::vector<int64_t> offs((size_t)npairs + 1, 0);
+    for (int k = 0; k < npairs; k++) {
+        const egm_gms_pair &q = pairs[k];
+        if (q.m < 0 || q.m > INT32_MAX || q.n < 0 || q.width1 <= 0 || q.height1 <= 0 || q.width2 <= 0 ||
+            q.height2 <= 0)
+            return EGM_ERR_ARG;
+        if (q.m > 0 && (!q.xy1 || !q.best || !q.flags || (q.n > 0 && !q.xy2))) return EGM_ERR_ARG;
+        tab[(size_t)k] = GmsPair{q.xy1, q.xy2, q.best, q.flags, q.m, q.n, offs[(size_t)k],
+                                 (double)q.width1, (double)q.height1, (double)q.width2, (double)q.height2};
+        offs[(size_t)k + 1] = offs[(size_t)k] + q.m;
+    }
+    const int64_t rows = offs[(size_t)npairs];
+    if (rows > INT32_MAX) return EGM_ERR_ARG;
+    if (rows == 0) return EGM_OK;
+    EGM_TRY(cudaSetDevice(c->device));
+    const GmsLayout l = gms_layout(npairs, rows, grid);
+    EGM_TRY(grow(c->gms, l.total));
+    const size_t tb = sizeof(GmsPair) * (size_t)npairs, ob = sizeof(int64_t) * offs.size();
+    if (c->gms_host_ev) EGM_TRY(cudaEventSynchronize(c->gms_host_ev));  // the staging's previous copy
+    else EGM_TRY(cudaEventCreateWithFlags(&c->gms_host_ev, cudaEventDisableTiming));
+    if (tb + ob > c->gms_host_bytes) {
+        if (c->gms_host) cudaFreeHost(c->gms_host);
+        c->gms_host = nullptr;
+        c->gms_host_bytes = 0;
+        EGM_TRY(cudaMallocHost(&c->gms_host, 2 * (tb + ob) + 4096));
+        c->gms_host_bytes = 2 * (tb + ob) + 4096;
+    }
+    unsigned char *h = static_cast<unsigned char *>(c->gms_host);
+    memcpy(h, tab.data(), tb);
+    memcpy(h + tb, offs.data(), ob);
+    unsigned char *d = static_cast<unsigned char *>(c->gms.ptr);
+    EGM_TRY(cudaMemcpyAsync(d + l.table, h, tb, cudaMemcpyHostToDevice, c->stream));
+    EGM_TRY(cudaMemcpyAsync(d + l.offs, h + tb, ob, cudaMemcpyHostToDevice, c->stream));
+    EGM_TRY(cudaEventRecord(c->gms_host_ev, c->stream));
+    EGM_TRY(launch_gms(c->gms.ptr, l, npairs, rows, require, grid, alpha, c->stream));
+    if (c->params.sync) EGM_TRY(cudaStreamSynchronize(c->stream));
+    return EGM_OK;
+}
+
+}  // namespace
+
 egm_status egm_gms(egm_ctx *c, const double *xy1, int64_t m, const double *xy2, int64_t n, const int32_t *best,
                    uint8_t *flags, int32_t width1, int32_t height1, int32_t width2, int32_t height2,
                    uint32_t require, int32_t grid, double alpha) {
-    if (!c || m < 0 || m > INT32_MAX || n < 0 || grid < 1 || grid > 48 || !(alpha > 0.0) ||
-        !(alpha < INFINITY) || width1 <= 0 || height1 <= 0 || width2 <= 0 || height2 <= 0)
-        return EGM_ERR_ARG;
-    if (m > 0 && (!xy1 || !best || !flags || (n > 0 && !xy2))) return EGM_ERR_ARG;
-    EGM_TRY(cudaSetDevice(c->device));
-    EGM_TRY(grow(c->gms, gms_scratch_bytes(m, grid)));
-    EGM_TRY(launch_gms(xy1, m, xy2, n, best, flags, width1, height1, width2, height2, require, grid, alpha,
-                       c->gms.ptr, c->stream));
-    if (c->params.sync) EGM_TRY(cudaStreamSynchronize(c->stream));
-    return EGM_OK;
+    const egm_gms_pair q{xy1, xy2, best, flags, m, n, width1, height1, width2, height2};
+    return run_gms(c, &q, 1, require, grid, alpha);
+}
+
+egm_status egm_gms_batch(egm_ctx *c, const egm_gms_pair *pairs, int32_t npairs, uint32_t require, int32_t grid,
+                         double alpha) {
+    return run_gms(c, pairs, npairs, require, grid, alpha);
 }
 
 egm_status egm_intervals(egm_ctx *c, const egm_pair *pair, double *theta, double *delta, double *e3,

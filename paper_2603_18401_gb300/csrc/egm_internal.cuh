@@ -542,10 +542,21 @@ cudaError_t launch_query_sort(const Launch &L, cudaStream_t s);
 cudaError_t launch_pack(const Launch &L, cudaStream_t s);
 int band_shapes();  // tile shapes of the band kernel (see band.cu)
 cudaError_t launch_mutual(const int32_t *best, uint8_t *flags, int64_t m, int64_t n, cudaStream_t s);
-size_t gms_scratch_bytes(int64_t m, int grid);
-cudaError_t launch_gms(const double *xy1, int64_t m, const double *xy2, int64_t n, const int32_t *best,
-                       uint8_t *flags, double w1, double h1, double w2, double h2, uint32_t require, int grid,
-                       double alpha, void *scratch, cudaStream_t st);
+// GMS (gms.cu): one pair of a batch, as the kernels read it from the table
+struct GmsPair {
+    const double *xy1, *xy2;
+    const int32_t *best;
+    uint8_t *flags;
+    int64_t m, n, row_off;   // rows, references, first row in the concatenated per-row arrays
+    double w1, h1, w2, h2;
+};
+struct GmsLayout {
+    size_t table, offs, ds, dec, c1, c2, total;
+};
+GmsLayout gms_layout(int npairs, int64_t rows, int grid);
+// the pair table and row offsets are already in the scratch at l.table, l.offs
+cudaError_t launch_gms(void *scratch, const GmsLayout &l, int npairs, int64_t rows, uint32_t require, int grid,
+                       double alpha, cudaStream_t st);
 int64_t compact_tiles(int64_t m);
 cudaError_t launch_compact(const uint8_t *flags, const int32_t *best, int64_t m, uint32_t require,
                            uint32_t *tile_count, int32_t *qi, int32_t *rj, int64_t *count, cudaStream_t s);

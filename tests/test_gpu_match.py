@@ -197,3 +197,28 @@ def test_gms_rejects_bad_arguments(mt):
         args.update(kw)
         with pytest.raises(EgmError):
             mt.gms(xy, xy, best, f, args["size1"], args["size2"], 1, args["grid"], args["alpha"])
+
+
+def test_gms_batch_equals_per_pair_oracle(mt):
+    """egm_gms_batch over pairs of different sizes (one empty) in one call:
+    every pair's flags equal the oracle's for that pair alone."""
+    from oracle import gms as ogms
+
+    torch = mt.torch
+    rng = np.random.default_rng(21)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(mt.device)
+    items, want = [], []
+    for k, m in enumerate([3000, 0, 800, 12000, 1]):
+        n = max(m, 5)
+        xy1 = rng.uniform([0, 0], [1200, 900], (m, 2))
+        xy2 = rng.uniform([0, 0], [1000, 800], (n, 2))
+        best = rng.integers(-1, n, m)
+        kk = m // 2
+        xy2[best[:kk]] = xy1[:kk] * 0.7 + 30.0   # a coherent part
+        flags = rng.integers(0, 64, m).astype(np.uint8)
+        size1, size2 = (1200, 900), (1000, 800)
+        want.append(ogms.gms(xy1, xy2, best, flags, size1, size2, require=1, grid=20, alpha=6.0))
+        items.append((dev(xy1), dev(xy2), dev(best.astype(np.int32)), dev(flags), size1, size2))
+    mt.gms_batch(items, require=1, grid=20, alpha=6.0)
+    for (_, _, _, f, _, _), w in zip(items, want):
+        assert np.array_equal(f.cpu().numpy(), w)

@@ -459,3 +459,40 @@ def test_references_just_inside_tolerance(mt, t):
     sc = _scene(xy1, xy2, F, eps, w=6048, h=4032, dim=128)
     out = _full_check(mt, sc)
     assert np.all(np.diff(out["cand_offsets"]) >= 3)
+
+
+def test_back_to_back_calls_without_sync(mt):
+    """Consecutive single-pair calls queued without waiting: the geometry
+    kernel of a call overlaps the previous call's last kernel (double-buffered
+    plan and geometry), so alternating different pairs must still give each
+    call its own pair's exact result, including calls that reuse one output
+    buffer."""
+    torch = mt.torch
+    scs = [synth.config2("inside", 2.0, scale=0.3), synth.config2("far", 4.0, scale=0.2),
+           synth.config1(seed=4), synth.config3(seed=8, npairs=2, scale=0.15)[1]]
+    dev = [mt.to_device(s) for s in scs]
+    ref = [run(mt, s, csr=False) for s in scs]
+    mt.set_params(sync=False)
+    try:
+        outs = []
+        shared = mt._alloc_out(max(s.m for s in scs), False, 0)
+        for rep in range(3):
+            for k, (s, d) in enumerate(zip(scs, dev)):
+                o = mt.match(d["xy1"], d["xy2"], d["F"], d["eps"], d["desc1"], d["desc2"], d["kind"], d["dim"],
+                             d["width"], d["height"])
+                outs.append((k, o))
+            # the same output buffer for every pair, the last call's result must remain
+            for s, d in zip(scs, dev):
+                pair = mt.make_pair(d["xy1"], d["xy2"], d["F"], d["eps"], d["desc1"], d["desc2"], d["kind"], d["dim"],
+                                    d["width"], d["height"])
+                assert mt.egm_match_pair(pair, mt._out_struct(shared, 0)) == 0
+        assert mt.sync() == 0
+        torch.cuda.synchronize()
+    finally:
+        mt.set_params(sync=True)
+    for k, o in outs:
+        for key in ("best", "second", "flags", "best_d"):
+            assert np.array_equal(o[key].cpu().numpy(), ref[k][key]), (k, key)
+    last = scs[-1]
+    for key in ("best", "second", "flags"):
+        assert np.array_equal(shared[key][:last.m].cpu().numpy(), ref[-1][key]), key
