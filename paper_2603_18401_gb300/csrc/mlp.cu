@@ -12,13 +12,11 @@
 // kernel loads them; every product and sum is FP32.
 //
 //   mlp_forward_kernel   one thread per sample, 128 samples per block, the
-//                        weights and the block's activations in shared
-//                        memory (activations column-major: no bank conflicts
-//                        while every thread reads the same weight)
-//   mlp_backward_kernel  64 samples per block: deltas layer by layer, then the
-//                        block's weight gradients with one thread per weight
-//                        element summing over the samples, added to the global
-//                        gradient with atomics
+//                        sample's activations in registers, the weights in
+//                        shared memory read as broadcast float4
+//   mlp_backward_kernel  64 samples per block: deltas layer by layer and the
+//                        block's weight gradients in 4 x 4 register tiles,
+//                        added to the global gradient with atomics
 //   adam_kernel          the Adam update, one thread per parameter
 //   residual_kernel      FP64 distances of given (query, reference) pairs,
 //                        in the brute force's exact evaluation order
@@ -62,14 +60,19 @@ __device__ __forceinline__ void features(const float *feat, int64_t s, float *u)
 }
 
 constexpr int kFB = 128;  // forward samples per block
+constexpr int kWPad = (kP + 3) & ~3;  // weights, then the activation buffer (16-byte aligned)
+static_assert(oW2 % 4 == 0 && oW3 % 4 == 0 && oW4 % 4 == 0, "float4 weight rows");
 
 // eps (double) and, for training, pre-activations a1..a3 stored [layer][unit][sample].
-__global__ void __launch_bounds__(kFB) mlp_forward_kernel(const float *params, const float *feat, int64_t n,
-                                                          double *eps, float *pre, float *zout) {
+// One thread per sample with its activations in registers; the weights are
+// read from shared memory as broadcast float4 (one load feeds four products)
+// for four output units at a time.  Every dot product runs over the inputs in
+// ascending order, one FMA at a time.
+__global__ void __launch_bounds__(kFB, 3) mlp_forward_kernel(const float *params, const float *feat, int64_t n,
+                                                             double *eps, float *pre, float *zout) {
     extern __shared__ float sm[];
     float *w = sm;                  // kP
-    float *ha = w + kP + 3;         // kH x kFB
-    float *hb = ha + kH * kFB;      // kH x kFB
+    float *hs = w + kWPad;          // kH x kFB: a layer's outputs, [unit][sample]
     load_weights(w, params);
     __syncthreads();
     const int t = threadIdx.x;
@@ -77,33 +80,52 @@ __global__ void __launch_bounds__(kFB) mlp_forward_kernel(const float *params, c
     const bool valid = s < n;
     float u[kIn] = {0, 0, 0, 0, 0};
     if (valid) features(feat, s, u);
+    float h[kH];
     // layer 1
+#pragma unroll
     for (int k = 0; k < kH; k++) {
         float a = w[ob1 + k];
 #pragma unroll
         for (int j = 0; j < kIn; j++) a = fmaf(w[oW1 + k * kIn + j], u[j], a);
         if (valid && pre) pre[(0 * kH + k) * n + s] = a;
-        ha[k * kFB + t] = gelu(a);
+        h[k] = gelu(a);
     }
     // layers 2 and 3
-    float *hin = ha, *hout = hb;
     for (int l = 0; l < 2; l++) {
-        const float *W = w + (l == 0 ? oW2 : oW3);
+        const float4 *W = reinterpret_cast<const float4 *>(w + (l == 0 ? oW2 : oW3));
         const float *b = w + (l == 0 ? ob2 : ob3);
-        for (int k = 0; k < kH; k++) {
-            float a = b[k];
-#pragma unroll 8
-            for (int j = 0; j < kH; j++) a = fmaf(W[k * kH + j], hin[j * kFB + t], a);
-            if (valid && pre) pre[((1 + l) * kH + k) * n + s] = a;
-            hout[k * kFB + t] = gelu(a);
+#pragma unroll 1
+        for (int k = 0; k < kH; k += 4) {
+            float a0 = b[k], a1 = b[k + 1], a2 = b[k + 2], a3 = b[k + 3];
+#pragma unroll
+            for (int j4 = 0; j4 < kH / 4; j4++) {
+                const float4 w0 = W[(k + 0) * (kH / 4) + j4], w1 = W[(k + 1) * (kH / 4) + j4];
+                const float4 w2 = W[(k + 2) * (kH / 4) + j4], w3 = W[(k + 3) * (kH / 4) + j4];
+                const float x0 = h[4 * j4], x1 = h[4 * j4 + 1], x2 = h[4 * j4 + 2], x3 = h[4 * j4 + 3];
+                a0 = fmaf(w0.x, x0, a0); a0 = fmaf(w0.y, x1, a0); a0 = fmaf(w0.z, x2, a0); a0 = fmaf(w0.w, x3, a0);
+                a1 = fmaf(w1.x, x0, a1); a1 = fmaf(w1.y, x1, a1); a1 = fmaf(w1.z, x2, a1); a1 = fmaf(w1.w, x3, a1);
+                a2 = fmaf(w2.x, x0, a2); a2 = fmaf(w2.y, x1, a2); a2 = fmaf(w2.z, x2, a2); a2 = fmaf(w2.w, x3, a2);
+                a3 = fmaf(w3.x, x0, a3); a3 = fmaf(w3.y, x1, a3); a3 = fmaf(w3.z, x2, a3); a3 = fmaf(w3.w, x3, a3);
+            }
+            if (valid && pre) {
+                float *pl = pre + ((1 + l) * kH + k) * n + s;
+                pl[0] = a0;
+                pl[n] = a1;
+                pl[2 * n] = a2;
+                pl[3 * n] = a3;
+            }
+            // this thread's own column: no other thread reads it
+            hs[(k + 0) * kFB + t] = gelu(a0);
+            hs[(k + 1) * kFB + t] = gelu(a1);
+            hs[(k + 2) * kFB + t] = gelu(a2);
+            hs[(k + 3) * kFB + t] = gelu(a3);
         }
-        float *tmp = hin;
-        hin = hout;
-        hout = tmp;
+#pragma unroll
+        for (int k = 0; k < kH; k++) h[k] = hs[k * kFB + t];
     }
     float z = w[ob4];
-#pragma unroll 8
-    for (int j = 0; j < kH; j++) z = fmaf(w[oW4 + j], hin[j * kFB + t], z);
+#pragma unroll
+    for (int j = 0; j < kH; j++) z = fmaf(w[oW4 + j], h[j], z);
     if (valid) {
         if (eps) eps[s] = (double)(softplus(z) + kEpsFloor);
         if (zout) zout[s] = z;
@@ -111,20 +133,31 @@ __global__ void __launch_bounds__(kFB) mlp_forward_kernel(const float *params, c
 }
 
 constexpr int kBB = 64;        // backward samples per block
-constexpr int kBS = kBB + 1;   // padded row stride of the [unit][sample] buffers
+constexpr int kRS = kH + 4;    // padded row stride of the [sample][unit] buffers (16-byte rows)
 
-__global__ void __launch_bounds__(256) mlp_backward_kernel(const float *params, const float *feat,
-                                                           const float *resid, int64_t n, float q, const float *pre,
-                                                           const float *zin, float *grad, float *loss) {
+// One block of 256 threads per kBB samples; activations, their GELU slopes
+// and deltas are stored sample-major in shared memory, so that
+//   weight gradients  dW[k][j] = sum_c D[c][k] H[c][j]: a thread accumulates a
+//                     4 x 4 tile from two float4 loads per sample;
+//   deltas below      E[c][j] = (sum_k W[k][j] D[c][k]) gelu'(a[c][j]): a
+//                     thread accumulates a 4 x 4 (sample x unit) tile from
+//                     eight float4 loads per four k.
+// Every sum runs over samples, or over k, in ascending order.  The block's
+// gradients are added to the global gradient with atomics.
+__global__ void __launch_bounds__(256, 2) mlp_backward_kernel(const float *params, const float *feat,
+                                                              const float *resid, int64_t n, float q,
+                                                              const float *pre, const float *zin, float *grad,
+                                                              float *loss) {
     extern __shared__ float sm[];
     float *w = sm;                   // kP
-    float *H = w + kP + 3;           // activations of the layer below  [unit][sample]
-    float *D = H + kH * kBS;         // deltas of the current layer     [unit][sample]
-    float *E = D + kH * kBS;         // deltas of the layer below
-    float *dz = E + kH * kBS;        // [sample]
-    float *red = dz + kBB;           // loss partials
+    float *Hs = w + kWPad;           // activations of the layer below  [sample][unit]
+    float *Gs = Hs + kBB * kRS;      // their GELU slopes               [sample][unit]
+    float *Ds = Gs + kBB * kRS;      // deltas of the current layer     [sample][unit]
+    float *Es = Ds + kBB * kRS;      // deltas of the layer below       [sample][unit]
+    float *dz = Es + kBB * kRS;      // [sample]
+    float *red = dz + kBB;           // loss partials of the warps
     load_weights(w, params);
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t s0 = (int64_t)blockIdx.x * kBB;
     const int nb = (int)min((int64_t)kBB, n - s0);
     __syncthreads();
@@ -144,7 +177,14 @@ __global__ void __launch_bounds__(256) mlp_backward_kernel(const float *params, 
         }
         dz[t] = d;
     }
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0) red[warp] = lsum;
     __syncthreads();
+    if (t == 0 && loss) {
+        float v = 0.0f;
+        for (int k = 0; k < 8; k++) v += red[k];
+        atomicAdd(loss, v / (float)n);
+    }
     // h3 and delta3 = dz W4 gelu'(a3)
     for (int i = t; i < kH * kBB; i += blockDim.x) {
         const int k = i / kBB, c = i % kBB;
@@ -154,24 +194,14 @@ __global__ void __launch_bounds__(256) mlp_backward_kernel(const float *params, 
             h = gelu(a);
             d = dz[c] * w[oW4 + k] * gelu_grad(a);
         }
-        H[k * kBS + c] = h;
-        D[k * kBS + c] = d;
-    }
-    if (t < 32) {
-        float v = lsum;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (t == 0) red[0] = v;
-    } else if (t < 64) {
-        float v = lsum;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (t == 32) red[1] = v;
+        Hs[c * kRS + k] = h;
+        Ds[c * kRS + k] = d;
     }
     __syncthreads();
-    if (t == 0 && loss) atomicAdd(loss, (red[0] + red[1]) / (float)n);
     // W4, b4
     if (t < kH) {
         float g = 0.0f;
-        for (int c = 0; c < nb; c++) g = fmaf(dz[c], H[t * kBS + c], g);
+        for (int c = 0; c < nb; c++) g = fmaf(dz[c], Hs[c * kRS + t], g);
         atomicAdd(grad + oW4 + t, g);
     } else if (t == kH) {
         float g = 0.0f;
@@ -183,53 +213,106 @@ __global__ void __launch_bounds__(256) mlp_backward_kernel(const float *params, 
     for (int L = 3; L >= 2; L--) {
         const float *W = w + (L == 3 ? oW3 : oW2);
         const int oW = L == 3 ? oW3 : oW2, ob = L == 3 ? ob3 : ob2;
-        // activations of the layer below
+        // activations of the layer below and their slopes
         for (int i = t; i < kH * kBB; i += blockDim.x) {
             const int k = i / kBB, c = i % kBB;
-            H[k * kBS + c] = c < nb ? gelu(pre[((L - 2) * kH + k) * n + s0 + c]) : 0.0f;
+            float h = 0.0f, gg = 0.0f;
+            if (c < nb) {
+                const float a = pre[((L - 2) * kH + k) * n + s0 + c];
+                h = gelu(a);
+                gg = gelu_grad(a);
+            }
+            Hs[c * kRS + k] = h;
+            Gs[c * kRS + k] = gg;
         }
         __syncthreads();
-        // weight gradients of layer L: one thread per (row, column) group
-        for (int i = t; i < kH * kH; i += blockDim.x) {
-            const int k = i / kH, j = i % kH;
-            float g = 0.0f;
-            for (int c = 0; c < nb; c++) g = fmaf(D[k * kBS + c], H[j * kBS + c], g);
-            atomicAdd(grad + oW + i, g);
+        // weight gradients of layer L: a 4 x 4 tile (rows 4 kt.., columns 4 jt..) per thread
+        {
+            const int kt = t >> 4, jt = t & 15;
+            float acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = 0.0f;
+            for (int c = 0; c < nb; c++) {
+                const float4 d4 = *reinterpret_cast<const float4 *>(Ds + c * kRS + 4 * kt);
+                const float4 h4 = *reinterpret_cast<const float4 *>(Hs + c * kRS + 4 * jt);
+                const float dv[4] = {d4.x, d4.y, d4.z, d4.w}, hv[4] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) acc[i][j] = fmaf(dv[i], hv[j], acc[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) atomicAdd(grad + oW + (4 * kt + i) * kH + 4 * jt + j, acc[i][j]);
         }
         if (t < kH) {
             float g = 0.0f;
-            for (int c = 0; c < nb; c++) g += D[t * kBS + c];
+            for (int c = 0; c < nb; c++) g += Ds[c * kRS + t];
             atomicAdd(grad + ob + t, g);
         }
-        // deltas of the layer below: E = (W^T D) * gelu'(a_{L-1})
-        for (int i = t; i < kH * kBB; i += blockDim.x) {
-            const int j = i / kBB, c = i % kBB;
-            float a = 0.0f;
-            for (int k = 0; k < kH; k++) a = fmaf(W[k * kH + j], D[k * kBS + c], a);
-            E[j * kBS + c] = c < nb ? a * gelu_grad(pre[((L - 2) * kH + j) * n + s0 + c]) : 0.0f;
+        // deltas of the layer below: E[c][j] = (sum_k W[k][j] D[c][k]) gelu'(a[c][j]),
+        // a 4 x 4 tile (samples 4 ct.., units 4 jt..) per thread and step
+        for (int tile = t; tile < (kH / 4) * (kBB / 4); tile += blockDim.x) {
+            const int jt = tile & 15, ct = tile >> 4;
+            float e[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) e[i][j] = 0.0f;
+            for (int k = 0; k < kH; k += 4) {
+                float4 wr[4], dr[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) wr[i] = *reinterpret_cast<const float4 *>(W + (k + i) * kH + 4 * jt);
+#pragma unroll
+                for (int cc = 0; cc < 4; cc++)
+                    dr[cc] = *reinterpret_cast<const float4 *>(Ds + (4 * ct + cc) * kRS + k);
+#pragma unroll
+                for (int cc = 0; cc < 4; cc++) {
+                    const float dv[4] = {dr[cc].x, dr[cc].y, dr[cc].z, dr[cc].w};
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const float wv[4] = {j == 0 ? wr[0].x : j == 1 ? wr[0].y : j == 2 ? wr[0].z : wr[0].w,
+                                             j == 0 ? wr[1].x : j == 1 ? wr[1].y : j == 2 ? wr[1].z : wr[1].w,
+                                             j == 0 ? wr[2].x : j == 1 ? wr[2].y : j == 2 ? wr[2].z : wr[2].w,
+                                             j == 0 ? wr[3].x : j == 1 ? wr[3].y : j == 2 ? wr[3].z : wr[3].w};
+#pragma unroll
+                        for (int i = 0; i < 4; i++) e[cc][j] = fmaf(wv[i], dv[i], e[cc][j]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < 4; cc++) {
+                const int c = 4 * ct + cc;
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    Es[c * kRS + 4 * jt + j] = c < nb ? e[cc][j] * Gs[c * kRS + 4 * jt + j] : 0.0f;
+            }
         }
         __syncthreads();
-        float *tmp = D;
-        D = E;
-        E = tmp;
+        float *tmp = Ds;
+        Ds = Es;
+        Es = tmp;
     }
-    // layer 1: inputs are the features
-    for (int i = t; i < kIn * kBB; i += blockDim.x) {
-        const int j = i / kBB, c = i % kBB;
+    // layer 1: inputs are the features (sample-major in Hs, kIn columns)
+    for (int c = t; c < kBB; c += blockDim.x) {
         float u[kIn] = {0, 0, 0, 0, 0};
         if (c < nb) features(feat, s0 + c, u);
-        H[j * kBS + c] = u[j];
+#pragma unroll
+        for (int j = 0; j < kIn; j++) Hs[c * kRS + j] = u[j];
     }
     __syncthreads();
     for (int i = t; i < kH * kIn; i += blockDim.x) {
         const int k = i / kIn, j = i % kIn;
         float g = 0.0f;
-        for (int c = 0; c < nb; c++) g = fmaf(D[k * kBS + c], H[j * kBS + c], g);
+        for (int c = 0; c < nb; c++) g = fmaf(Ds[c * kRS + k], Hs[c * kRS + j], g);
         atomicAdd(grad + oW1 + i, g);
     }
     if (t < kH) {
         float g = 0.0f;
-        for (int c = 0; c < nb; c++) g += D[t * kBS + c];
+        for (int c = 0; c < nb; c++) g += Ds[c * kRS + t];
         atomicAdd(grad + ob1 + t, g);
     }
 }
@@ -267,8 +350,8 @@ __global__ void residual_kernel(const double *xy1, const double *xy2, const doub
 
 int mlp_param_count() { return kP; }
 
-size_t mlp_forward_smem() { return sizeof(float) * (kP + 3 + 2 * kH * kFB); }
-size_t mlp_backward_smem() { return sizeof(float) * (kP + 3 + 3 * kH * kBS + kBB + 8); }
+size_t mlp_forward_smem() { return sizeof(float) * (kWPad + kH * kFB); }
+size_t mlp_backward_smem() { return sizeof(float) * (kWPad + 4 * kBB * kRS + kBB + 8); }
 
 cudaError_t launch_mlp_forward(const float *params, const float *feat, int64_t n, double *eps, float *pre, float *z,
                                cudaStream_t s) {
