@@ -192,15 +192,15 @@ struct Launch {
 struct PairView {
     const double *xy1, *xy2, *F, *eps2;
     double eps_scalar;
-    int64_t q_off, r_off, t_off;
+    int64_t q_off, r_off, t_off, t_cap;
     int32_t n;
 };
 __device__ __forceinline__ PairView pair_view(const Launch &L, int p) {
     if (L.inl_use)
         return PairView{L.inl.xy1, L.inl.xy2, L.inl.F, L.inl.eps2, L.inl.eps_scalar,
-                        L.inl.q_off, L.inl.r_off, L.inl.t_off, L.inl.n};
+                        L.inl.q_off, L.inl.r_off, L.inl.t_off, L.inl.t_cap, L.inl.n};
     const PairDesc &P = L.pairs[p];
-    return PairView{P.xy1, P.xy2, P.F, P.eps2, P.eps_scalar, P.q_off, P.r_off, P.t_off, P.n};
+    return PairView{P.xy1, P.xy2, P.F, P.eps2, P.eps_scalar, P.q_off, P.r_off, P.t_off, P.t_cap, P.n};
 }
 
 // Pairs with at most this many references are sorted by one thread-block

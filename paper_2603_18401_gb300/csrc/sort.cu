@@ -319,8 +319,10 @@ __global__ void __cluster_dims__(kScanCtas, 1, 1) __launch_bounds__(kScanThreads
         if (lane == 31) ctot = wi;
     }
     cluster.sync();  // every block total published
-    uint32_t carry = wtot[warp];
-    for (int c = 0; c < rank; c++) carry += *cluster.map_shared_rank(&ctot, c);
+    // the lower-ranked blocks' totals, read in parallel (lane c reads block c)
+    uint32_t lower = lane < rank ? *cluster.map_shared_rank(&ctot, lane) : 0u;
+    lower = __reduce_add_sync(0xffffffffu, lower);
+    uint32_t carry = wtot[warp] + lower;
     // pass 2: exclusive values: the table (first position of each bucket) and the cursors
     const bool one_round = r1 <= r0 + kScanRound;
     for (uint32_t r = r0; r < r1; r += kScanRound) {
