@@ -135,7 +135,11 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ distributed
-def dist_setup(gpus):
+# One process per GPU, replicas of the same workload (the pairs are
+# independent: no data-path collective).  The process group only carries the
+# barriers around the timed regions and the max over ranks of the times: NCCL
+# on GPUs, gloo where there is none (the multi-process tests on CPU).
+def dist_setup(gpus, backend=None):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -143,8 +147,11 @@ def dist_setup(gpus):
         import torch
         import torch.distributed as dist
 
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return rank, world, local
 
 
@@ -161,9 +168,16 @@ def max_over_ranks(x, world, local):
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{local}")
+    dev = f"cuda:{local}" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_rate(units_per_rank, world, seconds_max):
+    """Whole-job throughput of `world` replicas that each processed
+    `units_per_rank` units, timed by the slowest rank."""
+    return world * units_per_rank / seconds_max
 
 
 # ------------------------------------------------------------------ oracle (CPU)
@@ -661,7 +675,7 @@ def run_ours(args):
     ms = sum(a.elapsed_time(b) for a, b in evs)
     ms = max_over_ranks(ms, world, local)
     q_per_step = sum(s.m for s in scs)
-    value = world * q_per_step * args.steps / (ms * 1e-3)
+    value = replica_rate(q_per_step * args.steps, world, ms * 1e-3)
 
     # dominant kernel: the matching kernel ("stab" stage) that takes the most
     # time over the step -- stab_kernel on the pairs run in the plain form,
