@@ -901,6 +901,7 @@ egm_status egm_match_batch_host(egm_ctx *c, const egm_pair *hp, int32_t npairs, 
         if (e == cudaSuccess) e = cudaEventRecord(c->in_ev[(size_t)k], cs);
         if (e != cudaSuccess) return fail(from_cuda(e));
     }
+    int covered = -1;  // the inputs of pairs 0 .. covered are on the device for the matching stream
     for (int k = 0; k < npairs; k++) {
         const egm_pair &P = hp[k];
         const egm_out &O = ho[k];
@@ -920,7 +921,17 @@ egm_status egm_match_batch_host(egm_ctx *c, const egm_pair *hp, int32_t npairs, 
         dout.best_d = O.best_d ? reinterpret_cast<float *>(d + o.bd) : nullptr;
         dout.second_d = O.second_d ? reinterpret_cast<float *>(d + o.sd) : nullptr;
         dout.flags = O.flags ? d + o.fl : nullptr;
-        cudaError_t e = cudaStreamWaitEvent(st, c->in_ev[(size_t)k], 0);
+        // The matching of pair k needs pair k's inputs.  The copy stream runs
+        // in order, so the event of a later pair covers every earlier one:
+        // waiting at pairs 0, 1, 2, 4, 7, ... for the inputs of pairs up to
+        // about 1.5 k keeps most consecutive pairs' kernels chained (an event
+        // wait ends a chain of dependent launches) while the uploads, faster
+        // than the matching, stay ahead.
+        cudaError_t e = cudaSuccess;
+        if (k > covered) {
+            covered = std::min(npairs - 1, k + k / 2);
+            e = cudaStreamWaitEvent(st, c->in_ev[(size_t)covered], 0);
+        }
         if (e != cudaSuccess) return fail(from_cuda(e));
         egm_status s = run_batch(c, &dp, 1, &dout, false);
         if (s != EGM_OK) return fail(s);
