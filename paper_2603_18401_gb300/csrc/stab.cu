@@ -55,9 +55,13 @@ constexpr int kDescCache = 256;  // query descriptors up to this many bytes are 
 // where fewer registers keep the kernel out of local memory
 template <bool ONE> constexpr int kBatchOf = ONE ? 2 : 4;
 template <bool ONE> constexpr int kUOf = ONE ? 2 : 4;
-constexpr int kRound = 1024;     // window elements tested per round
+// window elements tested per round: more in the single-pair variant (one
+// wave of blocks, fewer rounds), fewer in the other (shared memory for
+// occupancy)
+template <bool ONE> constexpr int kRoundOf = ONE ? 1536 : 1024;
 constexpr int kQPerWarp = kQB / (kStabThreads / 32);
 
+template <int kRound>
 struct StabSmem {
     uint2 rng[kQB][kRangesPerQuery];  // (first sorted position, length) of each non-empty range
     QueryRec qr[kQB];
@@ -133,7 +137,8 @@ template <int KIND, bool ONE>
 __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mode) {
     constexpr int kBatch = kBatchOf<ONE>;
     pdl_begin();
-    __shared__ __align__(16) StabSmem S;
+    constexpr int kRound = kRoundOf<ONE>;
+    __shared__ __align__(16) StabSmem<kRound> S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt = (1u << lane) - 1u;
     const bool write_rows = mode == 2 && L.cand_offsets[L.nq] <= L.cand_capacity;
