@@ -405,6 +405,22 @@ def sweeps_leg(mt, torch, stream, reps):
                                     "inside, u8 128-d; matching time per pair (CUDA events, L2 warm)",
                         "rows": rows}
 
+    # keypoint counts (Sec. 5.4: 5,000 to 50,000 keypoints at 50 px)
+    rows = []
+    for count in (5000, 10000, 25000, 50000):
+        sc = synth.config2("far", 50.0, seed=9, scale=count / 16384)
+        d = mt.to_device(sc)
+        o = mt.match(*args(50.0), csr=True)
+        kbar = int(o["cand_offsets"][-1].item()) / sc.m
+        row = {"keypoints": count, "candidates_per_query": kbar}
+        for name, form in (("auto", 0), ("plain", 1), ("banded", 2)):
+            mt.set_params(form=form)
+            row[f"{name}_ms"] = timed(lambda: mt.match(*args(50.0)))
+        mt.set_params(form=0)
+        rows.append(row)
+    out["scalability"] = {"workload": "one 6048x4032 pair per size, epipole far outside, eps 50 px, u8 128-d",
+                          "rows": rows}
+
     sc = synth.config2("far", 200.0, seed=6)
     d = mt.to_device(sc)
     rows = []

@@ -203,14 +203,6 @@ __device__ __forceinline__ PairView pair_view(const Launch &L, int p) {
     return PairView{P.xy1, P.xy2, P.F, P.eps2, P.eps_scalar, P.q_off, P.r_off, P.t_off, P.t_cap, P.n};
 }
 
-// Pairs with at most this many references are sorted by one thread-block
-// cluster, which also writes the sorted records and bucket tables; larger
-// pairs take the single-block sort and the separate post-sort pass.
-constexpr int kClusterCtas = 8;
-constexpr int kClusterThreads = 512;
-constexpr int kClusterItems = 8;
-constexpr int kClusterMaxN = kClusterCtas * kClusterThreads * kClusterItems;  // 32768
-
 // Level layout (first sorted position, bucket bits, table offset) from the
 // level counts; every block that needs it computes the same values.  One warp,
 // lane = level: a level of c > 1 members gets about two buckets per member

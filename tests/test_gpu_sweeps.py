@@ -93,3 +93,18 @@ def test_tolerance_covering_the_image_is_brute_force(mt):
         assert np.array_equal(out["best"], order[:, 0])
         assert np.array_equal(out["second"], order[:, 1])
         assert np.array_equal(out["best_d"], d[np.arange(sc.m), order[:, 0]].astype(np.float32))
+
+
+@pytest.mark.parametrize("count", [50000])
+def test_scalability_size_sampled_rows(mt, count):
+    """50,000 keypoints per image at 50 px (the largest size of the paper's
+    scalability runs, Sec. 5.4), in both forms: every output of 500 sampled
+    queries against the oracle."""
+    sc = synth.config2("far", 50.0, seed=9, scale=count / 16384)
+    rows = np.sort(np.random.default_rng(1).choice(sc.m, 500, replace=False))
+    ref = oracle.match(sc.xy1[rows], sc.xy2, sc.F, sc.eps, sc.desc1[rows], sc.desc2, sc.kind, sc.dim)
+    sub = with_(sc)
+    sub.xy1, sub.desc1 = sc.xy1[rows], sc.desc1[rows]
+    for form in (FORM_PLAIN, FORM_BANDED):
+        out = run(mt, sc, form=form)
+        check_matches({k: v[rows] for k, v in out.items()}, sub, ref=ref)
