@@ -8,10 +8,13 @@
  *   2. epipolar line l_i = F p~_i^1 of every image-1 query    (Sec. 3)
  *   3. the angle of every image-2 keypoint seen from e2 and the angular
  *      radius of its eps-circle                               (Sec. 4.2)
- *   4. keypoints sorted by angle (a device radix sort), the replacement of
- *      the paper's segment tree                               (Sec. 4.2/4.4)
+ *   4. keypoints ordered by (angular-radius level, angle bucket) with a
+ *      device counting sort, the replacement of the paper's segment tree
+ *                                                              (Sec. 4.2/4.4)
  *   5. stabbing: each query scans the angle window its line can reach and
- *      keeps exactly the keypoints with dist(l_i, p_j) <= eps_j (Eq. 3/4)
+ *      keeps exactly the keypoints with dist(l_i, p_j) <= eps_j (Eq. 3/4);
+ *      or (the banded form) tiles of 128 angle-ordered queries against the
+ *      band of keypoints their windows reach, distances on the tensor cores
  *   6. optional candidate lists in CSR form                   (Eq. 4)
  *   7. descriptor distances restricted to the candidates      (Sec. 4.3)
  *   8. best / second best by (distance, index) and Lowe's ratio test
