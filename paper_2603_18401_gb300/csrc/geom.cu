@@ -205,7 +205,9 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
     const int64_t total = L.nr + L.nq;
     const int lane = threadIdx.x & 31;
     __shared__ int64_t s_roffs[kSmemPairs + 1], s_qoffs[kSmemPairs + 1];
-    const bool cached = load_offsets(s_roffs, L.r_offs, L.npairs) && load_offsets(s_qoffs, L.q_offs, L.npairs);
+    // one pair (plan in the parameters): every row is pair 0, no offsets to load
+    const bool one = L.inl_use != 0;
+    const bool cached = one || (load_offsets(s_roffs, L.r_offs, L.npairs) && load_offsets(s_qoffs, L.q_offs, L.npairs));
     __syncthreads();
     // the bucket tables start from zero (the counting sort after this kernel fills them)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.ntab / 4; i += (int64_t)gridDim.x * blockDim.x)
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
         uint32_t group = 0xffffffffu;
         uint32_t s_bits = 0, d_bits = 0x7f800000u, t_bits = 0;
         if (valid && is_ref) {
-            const int p = cached ? pair_of_shared(s_roffs, L.npairs, g) : pair_of(L.r_offs, L.npairs, g);
+            const int p = one ? 0 : cached ? pair_of_shared(s_roffs, L.npairs, g) : pair_of(L.r_offs, L.npairs, g);
             const PairView P = pair_view(L, p);
             const PairGeom &G = L.geom[p];
             const int64_t j = g - P.r_off;
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
             group = (uint32_t)p * kLevels + (uint32_t)level;
         } else if (valid) {
             const int64_t gq = g - L.nr;
-            const int p = cached ? pair_of_shared(s_qoffs, L.npairs, gq) : pair_of(L.q_offs, L.npairs, gq);
+            const int p = one ? 0 : cached ? pair_of_shared(s_qoffs, L.npairs, gq) : pair_of(L.q_offs, L.npairs, gq);
             const PairView P = pair_view(L, p);
             const PairGeom &G = L.geom[p];
             const int64_t i = gq - P.q_off;

@@ -232,11 +232,13 @@ __device__ __forceinline__ uint32_t bucket_slot(const PairGeom &G, uint32_t key)
 __global__ void __launch_bounds__(256) bucket_count_kernel(Launch L) {
     pdl_begin();
     __shared__ int64_t offs[kSmemPairs + 1];
-    const bool cached = load_offsets(offs, L.r_offs, L.npairs);
+    const bool one = L.inl_use != 0;  // one pair: every reference is pair 0
+    const bool cached = one || load_offsets(offs, L.r_offs, L.npairs);
     __syncthreads();
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L.nr; g += (int64_t)gridDim.x * blockDim.x) {
-        const int p = cached ? pair_of_shared(offs, L.npairs, g) : pair_of(L.r_offs, L.npairs, g);
-        atomicAdd(L.tab + L.pairs[p].t_off + bucket_slot(L.geom[p], L.key_a[g]), 1u);
+        const int p = one ? 0 : cached ? pair_of_shared(offs, L.npairs, g) : pair_of(L.r_offs, L.npairs, g);
+        const int64_t t_off = one ? L.inl.t_off : L.pairs[p].t_off;
+        atomicAdd(L.tab + t_off + bucket_slot(L.geom[p], L.key_a[g]), 1u);
     }
 }
 
