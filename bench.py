@@ -763,6 +763,49 @@ def run_ours(args):
                          else "plain: windowed stabbing, CUDA-core descriptor distances")}
         mt.set_params(form={"auto": 0, "plain": 1, "banded": 2}[args.form])
 
+    # the same nine pairs as one batch: one CUDA graph (egm_graph_launch) per
+    # step, L2 flushed before every step, in the automatic and the plain form;
+    # the outputs must equal the one-pair calls'
+    same_batch = None
+    if not args.no_compare:
+        same_batch = {"workload": "the nine pairs above in one call", "api": "egm_graph_launch (one CUDA graph per step)"}
+        single = {k: torch.cat([o[k][:s.m] for o, s in zip(outs, scs)]) for k in ("best", "second", "flags")}
+        for name, form in (("auto", 0), ("plain", 1)):
+            mt.set_params(form=form)
+            mt.match_batch(dev)  # the first batch of a size class also tunes the band tile shape
+            mt.set_timing(True)
+            mt.match_batch(dev)
+            banded_calls = mt.timing()["banded_calls"]
+            mt.set_timing(False)
+            bout = mt._alloc_out(q_per_step, False, 0)
+            graph = mt.graph_create(dev, bout)
+            for _ in range(3):
+                flush.zero_()
+                if graph.launch() != 0:
+                    raise EgmError(mt.sync(), "nine-pair batch warm-up")
+            torch.cuda.synchronize()
+            for k in single:
+                if not torch.equal(bout[k][:q_per_step], single[k]):
+                    raise RuntimeError(f"nine-pair batch ({name}): {k} differs from the one-pair calls")
+            pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.compare_steps)]
+            for k in range(args.compare_steps):
+                flush.zero_()
+                pe[k][0].record(stream)
+                graph.launch()
+                pe[k][1].record(stream)
+            torch.cuda.synchronize()
+            st = mt.sync()
+            if st != 0:
+                raise EgmError(st, "nine-pair batch")
+            graph.close()
+            pms = max_over_ranks(sum(a.elapsed_time(b) for a, b in pe), world, local)
+            same_batch[name] = {"value": world * q_per_step * args.compare_steps / (pms * 1e-3),
+                                "unit": "queries/s", "ms_per_step": pms / args.compare_steps,
+                                "steps": args.compare_steps,
+                                "form": "banded" if banded_calls else "plain"}
+        mt.set_params(form={"auto": 0, "plain": 1, "banded": 2}[args.form])
+
     # end to end: host (pinned) buffers through egm_match_pair_host, copies inside
     host = []
     h2d = d2h = 0
@@ -885,6 +928,7 @@ def run_ours(args):
         "roofline": roofline,
         "batched": batched,
         "forced_forms_one_pair": other_form,
+        "same_pairs_one_batch": same_batch,
         "learned_tolerance": mlp,
         "matching": matching,
         "sweeps": sweeps,

@@ -67,6 +67,24 @@ def test_config2_full_size(mt, pose, eps):
     both(mt, synth.config2(pose, eps))
 
 
+def test_config2_nine_pairs_as_one_batch(mt):
+    """The nine full-size config-2 pairs (three poses x eps 1, 2, 4 px) in one
+    batch: every output equals the one-pair call's in each form (each one-pair
+    call is checked against the oracle in test_config2_full_size)."""
+    scenes = [synth.config2(p, e) for p in synth.CONFIG2_POSES for e in (1.0, 2.0, 4.0)]
+    items = [mt.to_device(s) for s in scenes]
+    singles = [run_form(mt, s, FORM_PLAIN) for s in scenes]
+    for form in (FORM_AUTO, FORM_BANDED, FORM_PLAIN):
+        mt.set_params(form=form)
+        out = {k: v.cpu().numpy() for k, v in mt.match_batch(items).items()}
+        mt.set_params(form=FORM_AUTO)
+        q0 = 0
+        for s, one in zip(scenes, singles):
+            for k in KEYS:
+                assert np.array_equal(out[k][q0:q0 + s.m], one[k]), (form, k)
+            q0 += s.m
+
+
 def test_config3_mixed_batch(mt):
     """u8 and binary pairs in one batch (one tile never spans two pairs)."""
     scenes = synth.config3(seed=2, npairs=10, scale=0.1)
