@@ -169,7 +169,8 @@ typedef struct egm_params {
     int32_t form;          /* EGM_FORM_* */
     int32_t band_tile;     /* banded form tile shape: 0 (default) chosen by the library's tuner,
                               which times every shape on the first call of each batch size class
-                              (that call waits for the device); k > 0: shape k - 1 */
+                              (that call waits for the device); k = 1, 2, 3: shape k - 1 (4, 2 or 1
+                              boxes of 32 references per tensor-core chunk) */
     int32_t float_pass;    /* banded form, float descriptors: the tensor-core pass that brackets
                               the distances before the exact FP32 rerank (results are the same):
                               EGM_FLOAT_PASS_BF16 (default) or EGM_FLOAT_PASS_FP8 */

@@ -298,6 +298,7 @@ constexpr int kBandThreads = kTM + 32;   // four epilogue warps and the control 
 // (N = 32 CB) and CPS resident CTAs per SM, which size shared memory and TMEM.
 //   0: CB 4, CPS 2   few tiles per SM (single pairs): fewer, larger chunks
 //   1: CB 2, CPS 3   many tiles (batches): more CTAs in flight per SM
+//   2: CB 1, CPS 4   many tiles: more CTAs still, more synchronisation per box
 constexpr int kGroup = 8;                // columns per TMEM load in the epilogue
 
 struct __align__(16) Piece {
@@ -310,8 +311,19 @@ struct BandSmem {
     static constexpr int kCN = kBoxR * CB;  // columns per chunk
     uint8_t A[2][kTM * 128];      // query tile, K halves (1024-byte aligned)
     uint8_t B[2][2][kCN * 128];   // band chunk: stage, K half
-    float4 rec[2][kCN];           // (x - cx, y - cy, eps, index) of each column
-    float4 rn[2][CB][kBoxR];      // (norm, rounding error, row scale, 0) of each box's rows
+    // The record stages are idle while a tile's windows are computed (every
+    // load of the previous tile has landed and been read, and the next ones
+    // are issued after), so the per-warp hulls share their memory.
+    union {
+        struct {
+            float4 rec[2][kCN];       // (x - cx, y - cy, eps, index) of each column
+            float4 rn[2][CB][kBoxR];  // (norm, rounding error, row scale, 0) of each box's rows
+        } io;
+        struct {
+            float wlo[4][kLevels], whi[4][kLevels];  // each epilogue warp's hull per level index
+            int32_t wkind[4][kLevels];
+        } hull;
+    } u;
     // fullB: a stage's operand rows landed; sfree: the MMA that read them is
     // done; fullR: a stage's records and norms landed; done: an accumulator is
     // ready; tfree: the epilogue has read it and the stage's records
@@ -320,8 +332,6 @@ struct BandSmem {
     PairDesc pd;
     Piece pc[2 * kLevels];
     uint2 wr[4][kLevels][2];      // each epilogue warp's window ranges per level index
-    float wlo[4][kLevels], whi[4][kLevels];
-    int32_t wkind[4][kLevels];
     int32_t lv[kLevels];
     int32_t nlev, npc, nbox, gpair;
     int32_t tile;                 // the tile being processed, then the next one
@@ -335,7 +345,7 @@ struct BandShape {
     static constexpr uint32_t kTmemCols = 2 * kCN;  // double-buffered accumulator (a power of two)
     using Smem = BandSmem<CB>;
     static_assert(offsetof(Smem, B) % 1024 == 0, "operand tiles need 1024-byte alignment");
-    static_assert(offsetof(Smem, rn) % 16 == 0, "bulk copy destinations need 16-byte alignment");
+    static_assert(offsetof(Smem, u) % 16 == 0, "bulk copy destinations need 16-byte alignment");
     // CPS CTAs per SM share the 512 TMEM columns; shared memory keeps one more
     // from becoming resident (its allocation would wait for another CTA to end)
     static constexpr size_t kSmPerSm = 228 * 1024, kSmPerCta = sizeof(Smem) + 1024 + 1024;
@@ -603,9 +613,9 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 if (anyex || anykv)
                     w = key_window_span(G, S.lv[lane], kmin, kmax, kabs, G.mode == kModeAngular ? a0hi : a0lo,
                                         a1hi, anyex);
-                S.wkind[warp][lane] = w.kind;
-                S.wlo[warp][lane] = w.lo;
-                S.whi[warp][lane] = w.hi;
+                S.u.hull.wkind[warp][lane] = w.kind;
+                S.u.hull.wlo[warp][lane] = w.lo;
+                S.u.hull.whi[warp][lane] = w.hi;
             }
         }
         __syncthreads();
@@ -617,18 +627,18 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             w.lo = w.hi = 0.0f;
             if (li < nlev) {
                 if (warp < 4) {
-                    w.kind = S.wkind[warp][li];
-                    w.lo = S.wlo[warp][li];
-                    w.hi = S.whi[warp][li];
+                    w.kind = S.u.hull.wkind[warp][li];
+                    w.lo = S.u.hull.wlo[warp][li];
+                    w.hi = S.u.hull.whi[warp][li];
                 } else {
                     float lo = INFINITY, hi = -INFINITY;
                     for (int q = 0; q < 4; q++) {
-                        const int kq = S.wkind[q][li];
+                        const int kq = S.u.hull.wkind[q][li];
                         if (kq == 1) w.kind = 1;
                         if (kq == 2) {
                             if (w.kind == 0) w.kind = 2;
-                            lo = fminf(lo, S.wlo[q][li]);
-                            hi = fmaxf(hi, S.whi[q][li]);
+                            lo = fminf(lo, S.u.hull.wlo[q][li]);
+                            hi = fmaxf(hi, S.u.hull.whi[q][li]);
                         }
                     }
                     w.lo = lo;
@@ -685,6 +695,9 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 }
             }
         }
+        // the hull arrays' last generic accesses before the record stages they
+        // share are written by bulk copies again
+        tc::fence_proxy_async();
         __syncthreads();
         const int nbox = S.nbox;
         const int nchunk = (nbox + kCB - 1) / kCB;
@@ -718,8 +731,8 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                     int li;
                     curR.next(S, pos, len, li);
                     const int64_t row = P.r_off + pos;
-                    tc::bulk_load(&S.rec[st][bb * kBoxR], L.rec + row, kBoxR * 16, &S.fullR[st]);
-                    tc::bulk_load(&S.rn[st][bb][0], L.rnorm + row, kBoxR * 16, &S.fullR[st]);
+                    tc::bulk_load(&S.u.io.rec[st][bb * kBoxR], L.rec + row, kBoxR * 16, &S.fullR[st]);
+                    tc::bulk_load(&S.u.io.rn[st][bb][0], L.rnorm + row, kBoxR * 16, &S.fullR[st]);
                 }
             };
             for (int c = 0; c < nchunk && c < 2; c++) {
@@ -792,8 +805,8 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                     const int y0 = (int)max(pos, w1.x) - (int)pos;
                     const int y1 = (int)min(pos + len, w1.x + w1.y) - (int)pos;
                     if (x1 <= x0 && y1 <= y0) continue;
-                    const float4 *rnb = &S.rn[st][bb][0];
-                    const float4 *recb = &S.rec[st][bb * kBoxR];
+                    const float4 *rnb = &S.u.io.rn[st][bb][0];
+                    const float4 *recb = &S.u.io.rec[st][bb * kBoxR];
                     const uint32_t tb = tmem + lanebase + st * kCN + bb * kBoxR;
                     // the box's columns inside the warp's windows, as a bit mask
                     auto span = [](int a, int b) {
@@ -1013,7 +1026,7 @@ cudaError_t launch_band_shape(const Launch &L, int sms, const CUtensorMap &tA, c
                       L);
 }
 
-int band_shapes() { return 2; }
+int band_shapes() { return 3; }
 
 cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s, bool zero_work) {
     if (L.ntiles == 0) return cudaSuccess;
@@ -1025,6 +1038,7 @@ cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s, boo
     switch (shape) {
         case 0: return launch_band_shape<4, 2, false>(L, sms, tA, tB, zero_work, s);
         case 1: return launch_band_shape<2, 3, false>(L, sms, tA, tB, zero_work, s);
+        case 2: return launch_band_shape<1, 4, false>(L, sms, tA, tB, zero_work, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -263,7 +263,7 @@ def test_every_tile_shape_and_the_tuner(mt):
     mt.set_params(form=FORM_PLAIN)
     ref = {k: v.cpu().numpy() for k, v in mt.match_batch(items).items()}
     try:
-        for tile in (1, 2, 0, 0):
+        for tile in (1, 2, 3, 0, 0):
             mt.set_params(form=FORM_BANDED, band_tile=tile)
             got = {k: v.cpu().numpy() for k, v in mt.match_batch(items).items()}
             for k in KEYS:
@@ -273,6 +273,27 @@ def test_every_tile_shape_and_the_tuner(mt):
             mt.set_params(band_tile=99)
     finally:
         mt.set_params(form=FORM_AUTO, band_tile=0)
+
+
+@pytest.mark.parametrize("tile", [1, 2, 3])
+def test_each_tile_shape_on_ragged_and_full_size_pairs(mt, tile):
+    """Each forced tile shape (boxes per chunk, CTAs per SM) on ragged tiles
+    and boxes and on a full-size pair: outputs equal the plain form's."""
+    rng = np.random.default_rng(tile)
+    cases = [_scene(rng.uniform([0, 0], [640, 480], (m, 2)), rng.uniform([0, 0], [640, 480], (n, 2)), _F(), 6.0,
+                    kind=kind, dim=dim, seed=m + n)
+             for m, n in ((1, 500), (129, 33), (300, 5), (257, 1)) for kind, dim in ((0, 128), (2, 256))]
+    cases.append(synth.config2("inside", 4.0, seed=1))
+    try:
+        for sc in cases:
+            mt.set_params(band_tile=tile)
+            b = run_form(mt, sc, FORM_BANDED)
+            mt.set_params(band_tile=0)
+            p = run_form(mt, sc, FORM_PLAIN)
+            for k in KEYS:
+                assert np.array_equal(b[k], p[k]), (tile, sc.m, k)
+    finally:
+        mt.set_params(band_tile=0)
 
 
 # ------------------------------------------------------------------ float descriptors
