@@ -451,9 +451,10 @@ def mlp_leg(mt, torch, stream):
 
     FLOPs per sample: forward 2 (5*64 + 2*64*64 + 64) = 17 152 in the layer
     products plus ~25 per unit for GELU / softplus; training adds the
-    backward pass, twice the forward products.  The kernels run on the FP32
-    CUDA cores: the peak is 152 SMs x 128 FP32 lanes x 2 FLOP x the sampled
-    SM clock."""
+    backward pass, twice the forward products.  Inference runs layers 2 and 3
+    on the tensor cores (two BF16 products per layer: activations split into
+    hi and lo parts), the rest on the FP32 CUDA cores; training runs on the
+    CUDA cores, whose peak is 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz."""
     import numpy as np
     import synth
 
@@ -501,6 +502,8 @@ def mlp_leg(mt, torch, stream):
                        "achieved": out["train_step"]["tflops"], "frac": out["train_step"]["tflops"] / peak,
                        "kernel": "mlp_forward_kernel + mlp_backward_kernel + adam_kernel (one training step)"}
     out["network"] = "5-64-64-64-1 GELU, softplus + 0.25 px, BF16-rounded weights, FP32 arithmetic"
+    out["inference"]["kernel"] = ("mlp_forward_tc_kernel: layers 2 and 3 as tcgen05.mma (M 128, N 64, K 64, BF16 "
+                                  "hi + lo activations, FP32 in TMEM); layers 1 and 4, GELU on CUDA cores")
     return out
 
 

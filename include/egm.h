@@ -368,7 +368,10 @@ egm_status egm_mlp_get_state(egm_mlp *mlp, float *params, float *adam_m, float *
 egm_status egm_mlp_set_state(egm_mlp *mlp, const float *params, const float *adam_m, const float *adam_v,
                              int64_t step);
 /* eps [n] float64 (device) for features [n][5] float32 (device); the output
- * can be passed as egm_pair.eps2. */
+ * can be passed as egm_pair.eps2.  Layers 2 and 3 run on the tensor cores
+ * (tcgen05.mma, BF16 weights; each FP32 activation enters as the sum of two
+ * BF16 parts, so results agree with FP32 products to about 1e-6 relative);
+ * EGM_ERR_TIMEOUT if a tensor-core wait gave up (outputs NaN). */
 egm_status egm_mlp_infer(egm_mlp *mlp, const float *feat, int64_t n, double *eps);
 /* Gradient of the mean pinball loss (device outputs: grad [EGM_MLP_PARAMS], loss [1]). */
 egm_status egm_mlp_grad(egm_mlp *mlp, const float *feat, const float *resid, int64_t n, float quantile, float *grad,

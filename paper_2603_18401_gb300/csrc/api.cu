@@ -1150,7 +1150,7 @@ egm_status egm_graph_destroy(egm_graph *g) {
 
 struct egm_mlp {
     egm_ctx *ctx = nullptr;
-    DevBuf params, m, v, grad, pre, z, loss;
+    DevBuf params, m, v, grad, pre, z, loss, err;
     int64_t step = 0;
 };
 
@@ -1170,6 +1170,7 @@ egm_status egm_mlp_create(egm_ctx *c, const float *params, egm_mlp **out) {
     if (e == cudaSuccess) e = grow(m->v, pb);
     if (e == cudaSuccess) e = grow(m->grad, pb);
     if (e == cudaSuccess) e = grow(m->loss, 64);
+    if (e == cudaSuccess) e = grow(m->err, 16);
     if (e == cudaSuccess) e = cudaMemcpy(m->params.ptr, params, pb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->m.ptr, 0, pb);
     if (e == cudaSuccess) e = cudaMemset(m->v.ptr, 0, pb);
@@ -1186,7 +1187,7 @@ egm_status egm_mlp_destroy(egm_mlp *m) {
     if (!m) return EGM_OK;
     cudaSetDevice(m->ctx->device);
     cudaStreamSynchronize(m->ctx->stream);
-    DevBuf *b[] = {&m->params, &m->m, &m->v, &m->grad, &m->pre, &m->z, &m->loss};
+    DevBuf *b[] = {&m->params, &m->m, &m->v, &m->grad, &m->pre, &m->z, &m->loss, &m->err};
     for (DevBuf *x : b)
         if (x->ptr) cudaFree(x->ptr);
     delete m;
@@ -1220,9 +1221,14 @@ egm_status egm_mlp_set_state(egm_mlp *m, const float *params, const float *am, c
 egm_status egm_mlp_infer(egm_mlp *m, const float *feat, int64_t n, double *eps) {
     if (!m || n < 0 || (n > 0 && (!feat || !eps))) return EGM_ERR_ARG;
     EGM_TRY(cudaSetDevice(m->ctx->device));
-    EGM_TRY(launch_mlp_forward(as<float>(m->params), feat, n, eps, nullptr, nullptr, m->ctx->stream));
-    EGM_TRY(cudaStreamSynchronize(m->ctx->stream));
-    return EGM_OK;
+    if (n == 0) return EGM_OK;
+    cudaStream_t st = m->ctx->stream;
+    EGM_TRY(cudaMemsetAsync(m->err.ptr, 0, sizeof(uint32_t), st));
+    EGM_TRY(launch_mlp_forward_tc(as<float>(m->params), feat, n, eps, as<uint32_t>(m->err), m->ctx->sms, st));
+    uint32_t bits = 0;
+    EGM_TRY(cudaMemcpyAsync(&bits, m->err.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    EGM_TRY(cudaStreamSynchronize(st));
+    return from_bits(bits);
 }
 
 namespace {

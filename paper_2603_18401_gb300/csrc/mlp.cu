@@ -14,6 +14,9 @@
 //   mlp_forward_kernel   one thread per sample, 128 samples per block, the
 //                        sample's activations in registers, the weights in
 //                        shared memory read as broadcast float4
+//   mlp_forward_tc_kernel  inference: layers 2 and 3 on the tensor cores
+//                        (tcgen05.mma, M = 128 samples, N = 64 units, K = 64),
+//                        the rest as in mlp_forward_kernel
 //   mlp_backward_kernel  64 samples per block: deltas layer by layer and the
 //                        block's weight gradients in 4 x 4 register tiles,
 //                        added to the global gradient with atomics
@@ -24,6 +27,7 @@
 #include <math.h>
 
 #include "egm_internal.cuh"
+#include "tc.cuh"
 
 namespace egm {
 
@@ -130,6 +134,162 @@ __global__ void __launch_bounds__(kFB, 3) mlp_forward_kernel(const float *params
         if (eps) eps[s] = (double)(softplus(z) + kEpsFloor);
         if (zout) zout[s] = z;
     }
+}
+
+// ------------------------------------------------------------ tensor-core forward
+// Layers 2 and 3 (the two 64 x 64 products, 97 % of the network's FLOPs) as
+// tcgen05.mma with FP32 accumulators in TMEM: A = the tile's 128 activation
+// rows, B = the layer's weight rows (already BF16), both K-major rows of 64
+// BF16 values (128 bytes) in the 128-byte swizzle layout.  A layer's FP32
+// activations h are split into hi = bf16(h) and lo = bf16(h - hi); both
+// products accumulate, so the operand carries h to about 2^-17 relative and
+// the result stays within FP32-level error of the CUDA-core kernel.  Layer 1
+// (5 inputs), layer 4 (one output), the biases and GELU run on the CUDA
+// cores; one thread per sample, which is also the sample's TMEM lane.
+constexpr int kTT = 128;            // samples per tile (MMA M, TMEM lanes)
+constexpr uint32_t kTmemMlp = 64;   // accumulator columns (N)
+
+struct __align__(1024) MlpTcSmem {
+    uint8_t Ahi[kTT * 128];         // activation rows, hi part (1024-byte swizzle atoms)
+    uint8_t Alo[kTT * 128];         //   and lo part
+    uint8_t W2[kH * 128];           // weight rows [unit][input] of layers 2 and 3
+    uint8_t W3[kH * 128];
+    float w1[kH * kIn], b1[kH], b2[kH], b3[kH], w4[kH], b4;
+    uint64_t bar;                   // MMA completion
+    uint32_t tmem;
+};
+
+// Byte offset of the 16-byte chunk c (0..7) of row r in a tile of 128-byte
+// rows with the 128-byte swizzle: the chunk index is XORed with the row's
+// position in its 8-row atom, as the tensor cores read it.
+__device__ __forceinline__ uint32_t sw128_off(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
+__device__ __forceinline__ uint32_t bf16x2(float a, float b) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+}
+
+// Row r of the hi and lo activation tiles from h[0..63].
+__device__ __forceinline__ void store_split(MlpTcSmem &S, int r, const float (&h)[kH]) {
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        float hi[8], lo[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            hi[k] = bf16r(h[8 * c + k]);
+            lo[k] = h[8 * c + k] - hi[k];  // exact
+        }
+        *reinterpret_cast<uint4 *>(S.Ahi + sw128_off(r, c)) =
+            make_uint4(bf16x2(hi[0], hi[1]), bf16x2(hi[2], hi[3]), bf16x2(hi[4], hi[5]), bf16x2(hi[6], hi[7]));
+        *reinterpret_cast<uint4 *>(S.Alo + sw128_off(r, c)) =
+            make_uint4(bf16x2(lo[0], lo[1]), bf16x2(lo[2], lo[3]), bf16x2(lo[4], lo[5]), bf16x2(lo[6], lo[7]));
+    }
+}
+
+// Persistent: each block takes tiles of 128 samples in turn.  Every wait on
+// the MMA barrier is bounded; a timeout sets the timeout bit in *err, the
+// block issues no more MMAs and its remaining outputs are NaN.
+__global__ void __launch_bounds__(kTT, 4) mlp_forward_tc_kernel(const float *params, const float *feat, int64_t n,
+                                                                double *eps, uint32_t *err) {
+    extern __shared__ uint8_t smraw[];
+    MlpTcSmem &S = *reinterpret_cast<MlpTcSmem *>(smraw + ((1024u - (tc::smem_addr(smraw) & 1023u)) & 1023u));
+    const int t = threadIdx.x, warp = t >> 5;
+    // the weights: BF16 tiles of W2 and W3 (one 16-byte chunk per step), FP32 copies of the rest
+    for (int i = t; i < 2 * kH * 8; i += kTT) {
+        const int l = i / (kH * 8), r = (i / 8) % kH, c = i % 8;
+        const float *src = params + (l == 0 ? oW2 : oW3) + r * kH + 8 * c;
+        *reinterpret_cast<uint4 *>((l == 0 ? S.W2 : S.W3) + sw128_off(r, c)) =
+            make_uint4(bf16x2(src[0], src[1]), bf16x2(src[2], src[3]), bf16x2(src[4], src[5]), bf16x2(src[6], src[7]));
+    }
+    for (int i = t; i < kH * kIn; i += kTT) S.w1[i] = bf16r(params[oW1 + i]);
+    if (t < kH) {
+        S.b1[t] = bf16r(params[ob1 + t]);
+        S.b2[t] = bf16r(params[ob2 + t]);
+        S.b3[t] = bf16r(params[ob3 + t]);
+        S.w4[t] = bf16r(params[oW4 + t]);
+    }
+    if (t == 0) {
+        S.b4 = bf16r(params[ob4]);
+        tc::mbar_init(&S.bar, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&S.tmem, kTmemMlp);
+        tc::tmem_relinquish();
+    }
+    tc::fence_proxy_async();  // the weight tiles' generic writes, before the MMAs read them
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    constexpr uint32_t idesc = tc::idesc_bf16(kTT, kH);
+    const int64_t ntiles = (n + kTT - 1) / kTT;
+    // A failed wait ends the block's MMAs; every decision about it is uniform
+    // where it must be (the warp for TMEM loads, the block for barriers), and
+    // no thread leaves the loops early.
+    bool failed = false;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t s = tile * kTT + t;
+        const bool valid = s < n;
+        float u[kIn] = {0, 0, 0, 0, 0};
+        if (valid) features(feat, s, u);
+        float h[kH];
+#pragma unroll
+        for (int k = 0; k < kH; k++) {
+            float a = S.b1[k];
+#pragma unroll
+            for (int j = 0; j < kIn; j++) a = fmaf(S.w1[k * kIn + j], u[j], a);
+            h[k] = gelu(a);
+        }
+        store_split(S, t, h);
+#pragma unroll 1
+        for (int l = 0; l < 2; l++) {
+            // every row written and the previous accumulator read before the MMAs
+            tc::fence_proxy_async();
+            tc::tc_fence_before();
+            failed = __syncthreads_or(failed) != 0;
+            if (!failed) {
+                if (t == 0) {
+                    tc::tc_fence_after();
+                    const uint8_t *W = l == 0 ? S.W2 : S.W3;
+#pragma unroll
+                    for (int kk = 0; kk < 4; kk++)
+                        tc::mma_bf16(tmem, tc::sdesc_sw128(tc::smem_addr(S.Ahi) + 32 * kk),
+                                     tc::sdesc_sw128(tc::smem_addr(W) + 32 * kk), idesc, kk > 0);
+#pragma unroll
+                    for (int kk = 0; kk < 4; kk++)
+                        tc::mma_bf16(tmem, tc::sdesc_sw128(tc::smem_addr(S.Alo) + 32 * kk),
+                                     tc::sdesc_sw128(tc::smem_addr(W) + 32 * kk), idesc, 1);
+                    tc::mma_commit(&S.bar);
+                }
+                // two commits per tile: the layer's phase parity is l
+                const bool done = tc::mbar_wait(&S.bar, (uint32_t)l);
+                failed = __any_sync(0xffffffffu, !done);
+                if (failed && (t & 31) == 0) atomicOr(err, kStTimeout);
+            }
+            if (!failed) {
+                tc::tc_fence_after();
+                const float *b = l == 0 ? S.b2 : S.b3;
+#pragma unroll
+                for (int half = 0; half < 2; half++) {
+                    uint32_t v[32];
+                    tc::tmem_ld32(tmem + lane_base + 32 * half, v);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int k = 0; k < 32; k++) h[32 * half + k] = gelu(__uint_as_float(v[k]) + b[32 * half + k]);
+                }
+                if (l == 0) store_split(S, t, h);
+            }
+        }
+        float z = S.b4;
+#pragma unroll
+        for (int j = 0; j < kH; j++) z = fmaf(S.w4[j], h[j], z);
+        if (valid) eps[s] = failed ? (double)NAN : (double)(softplus(z) + kEpsFloor);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemMlp);
 }
 
 constexpr int kBB = 64;        // backward samples per block
@@ -360,6 +520,18 @@ cudaError_t launch_mlp_forward(const float *params, const float *feat, int64_t n
     cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     mlp_forward_kernel<<<(int)((n + kFB - 1) / kFB), kFB, smem, s>>>(params, feat, n, eps, pre, z);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_forward_tc(const float *params, const float *feat, int64_t n, double *eps, uint32_t *err,
+                                  int sms, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int smem = (int)sizeof(MlpTcSmem) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (n + kTT - 1) / kTT;
+    const int grid = (int)std::min<int64_t>(tiles, 4 * (int64_t)sms);
+    mlp_forward_tc_kernel<<<grid, kTT, smem, s>>>(params, feat, n, eps, err);
     return cudaGetLastError();
 }
 
