@@ -9,6 +9,13 @@
 
 #include "egm_internal.cuh"
 
+namespace egm {
+// Learned-tolerance inference with layers 2 and 3 on the tensor cores
+// (mlp.cu); a timed-out MMA wait sets kStTimeout in *err (device).
+cudaError_t launch_mlp_forward_tc(const float *params, const float *feat, int64_t n, double *eps, uint32_t *err,
+                                  int sms, cudaStream_t s);
+}  // namespace egm
+
 using namespace egm;
 
 namespace {

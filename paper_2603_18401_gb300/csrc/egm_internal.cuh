@@ -564,10 +564,6 @@ cudaError_t launch_long_row_sort(const Launch &L, const uint32_t *list, const ui
 cudaError_t launch_intervals(const Launch &L, double *theta, double *delta, double *e3, int32_t *mode,
                              cudaStream_t s);
 int mlp_param_count();
-// Inference with layers 2 and 3 on the tensor cores; a timed-out MMA wait sets
-// kStTimeout in *err (device).
-cudaError_t launch_mlp_forward_tc(const float *params, const float *feat, int64_t n, double *eps, uint32_t *err,
-                                  int sms, cudaStream_t s);
 cudaError_t launch_mlp_forward(const float *params, const float *feat, int64_t n, double *eps, float *pre, float *z,
                                cudaStream_t s);
 cudaError_t launch_mlp_backward(const float *params, const float *feat, const float *resid, int64_t n, float q,
