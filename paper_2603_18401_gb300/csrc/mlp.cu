@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kFB, 3) mlp_forward_kernel(const float *params
 }
 
 // ------------------------------------------------------------ tensor-core forward
-// Layers 2 and 3 (the two 64 x 64 products, 97 % of the network's FLOPs) as
+// Layers 2 and 3 (the two 64 x 64 products, 96 % of the network's multiply-adds) as
 // tcgen05.mma with FP32 accumulators in TMEM: A = the tile's 128 activation
 // rows, B = the layer's weight rows (already BF16), both K-major rows of 64
 // BF16 values (128 bytes) in the 128-byte swizzle layout.  A layer's FP32
