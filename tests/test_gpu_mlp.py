@@ -72,6 +72,20 @@ def test_forward_matches_oracle(mt, n):
     net.close()
 
 
+def test_forward_persistent_blocks_match_oracle(mt):
+    """More 128-sample tiles than resident blocks (each block of the
+    tensor-core forward takes several tiles in turn), with a ragged last
+    tile: every output against the FP64 oracle."""
+    th = params(3)
+    n = 200_003
+    f = feats(n, 77)
+    net = mt.tolnet(th)
+    eps = net.infer(f).cpu().numpy()
+    ref, _ = omlp.forward(bf16(th), oracle_u(f))
+    np.testing.assert_allclose(eps, ref, rtol=1e-4, atol=1e-5)
+    net.close()
+
+
 def residuals_away_from(eps_ref, rng, gap=1e-3):
     r = eps_ref * np.exp(rng.normal(0.0, 0.6, eps_ref.size))
     close = np.abs(r - eps_ref) < gap
