@@ -10,7 +10,7 @@ the CUDA path.  Everything is FP64.
 - ``intervals``: the angular interval of every reference keypoint as seen from
   the epipole, theta_j = atan2(y_j - y_e, x_j - x_e) and
   delta_j = asin(eps_j / ||p_j - e||) (Sec. 4.2), folded into [0, pi)
-  (Sec. 4.2, "reduced domain"); keypoints within eps of the epipole get the
+  (Sec. 4.2: lines are undirected, so angles are taken mod pi); keypoints within eps of the epipole get the
   full interval (Algorithm 1; Sec. 4.4 "Keypoints near the epipole").
 - ``match_mutual``: matching in both directions (the reverse with F^T and the
   roles of the images swapped, Sec. 3) and the cross-check: i -> j is mutual
