@@ -940,9 +940,10 @@ def run_ours(args):
     }
     if cpu is not None:
         rate, cores, npairs, el = cpu
+        # the CPU leg: the oracle, and beside it the paper's own data structure on the same cores
         line["cpu_baseline"] = {"value": rate, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                                "sample": f"{npairs} config pairs (16384 queries each) cycled, {el:.1f} s"}
-        line["cpu_segment_tree"] = seg
+                                "sample": f"{npairs} config pairs (16384 queries each) cycled, {el:.1f} s",
+                                "segment_tree": seg}
     if rank == 0:
         print(json.dumps(line), flush=True)
     mt.close()
