@@ -11,10 +11,13 @@ per query are expected; --form forces one).  Inputs are resident in HBM
 before the timed region; L2 is flushed (a 256 MiB write) before every step
 and the flush is outside the CUDA-event-timed interval.
 
-Beside the headline: the same single-pair step in each forced form,
-the batched configuration (256 pairs, one CUDA-graph launch per step) in both
-forms, the end-to-end rate through host buffers, per-stage times, and the
-roofline of the dominant kernel.
+Beside the headline: the same single-pair step in each forced form, the same
+nine pairs as one batched call, the batched configuration (256 pairs, one
+CUDA-graph launch per step) in both forms, the float-descriptor batch, the
+end-to-end rate through host buffers, per-stage times, the roofline of the
+dominant kernel, mutual matching and GMS, the tolerance / scalability /
+pose-noise sweeps, the learned-tolerance kernels, and the CPU leg (the oracle
+and the paper's segment tree on the host cores).
 
 --impl reference times the CPU oracle (the plain brute-force definition) on
 the host cores instead: the paper publishes no code or GPU number, so the
