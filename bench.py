@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--compare-steps", type=int, default=200)
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-form comparison legs")
     ap.add_argument("--no-mlp", action="store_true", help="skip the learned-tolerance leg")
+    ap.add_argument("--no-learned-experiment", action="store_true",
+                    help="skip the config-5 train / test experiment (learned vs fixed tolerance)")
+    ap.add_argument("--learned-pairs", type=int, default=512)
     ap.add_argument("--no-float", action="store_true", help="skip the float-descriptor batch")
     ap.add_argument("--float-pairs", type=int, default=64)
     ap.add_argument("--no-matching", action="store_true", help="skip the mutual-matching leg")
@@ -89,9 +92,28 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def desc_row_bytes(kind, dim):
+    """Native descriptor row D in bytes: u8 dim, binary dim / 8, float 4 dim."""
+    return dim if kind == 0 else dim // 8 if kind == 2 else 4 * dim
+
+
+def algorithmic_bytes(sc):
+    """What the method must move for one pair, each input read once and each
+    output written once: per query its keypoint (16 B), descriptor (D) and
+    result (17 B: best, second, two distances, flags); per reference its
+    keypoint (16 B), descriptor (D) and, when per keypoint, its tolerance
+    (8 B); per pair F (72 B).  Tile re-reads, sorted copies and scratch
+    records are not counted."""
+    import numpy as np
+
+    D = desc_row_bytes(sc.kind, sc.dim)
+    per_ref = 16 + D + (0 if np.ndim(sc.eps) == 0 else 8)
+    return sc.m * (16 + D + 17) + sc.n * per_ref + 72
+
+
 # ------------------------------------------------------------------ clocks
 class Clocks:
-    """nvidia-smi samples every 200 ms during the timed region."""
+    """nvidia-smi samples during the timed region: every 50 ms, and one at each end."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -102,24 +124,44 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
 
+    def _once(self):
+        """One synchronous sample (a query only), appended to the record."""
+        try:
+            r = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
+            self.extra.append(r.stdout)
+        except (OSError, subprocess.SubprocessError):
+            pass
+
     def start(self):
+        """Starts the periodic sampler (every 50 ms); `edge` also takes one
+        sample at once, so that even a timed region shorter than the period
+        has a sample at each end."""
+        self.extra = []
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
 
+    def edge(self):
+        if self.p is not None:
+            self._once()
+
     def stop(self):
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self._once()
         self.p.terminate()
         self.p.wait()
         self.f.flush()
         self.f.seek(0)
+        periodic = self.f.read().splitlines()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.f.read().splitlines():
+        edge_lines = [ln for out in self.extra for ln in out.splitlines()]
+        for line in periodic + edge_lines:
             c = [x.strip() for x in line.split(",")]
             if len(c) < 9:
                 continue
@@ -134,6 +176,7 @@ class Clocks:
         os.unlink(self.f.name)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "samples": len(sm),
+                "samples_periodic": len(periodic), "samples_at_edges": len(edge_lines),
                 "reasons": sorted(reasons)}
 
 
@@ -230,6 +273,9 @@ def cpu_segtree_rate(scs, seconds):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle on the host cores, on the same
+    workload and step as our arm (one step = the nine config pairs), so that
+    the two lines time the same work per step."""
     rank, world, local = dist_setup(args.gpus)
     if rank != 0:
         return
@@ -237,25 +283,30 @@ def run_reference(args):
     import oracle
 
     oracle.match_scene(scs[0])  # load / build
-    times, nq = [], 0
-    for s in range(args.warmup + args.steps):
-        sc = scs[s % len(scs)]
-        t0 = time.perf_counter()
-        oracle.match_scene(sc)
-        dt = time.perf_counter() - t0
-        if s >= args.warmup:
-            times.append(dt)
-            nq += sc.m
-    total = sum(times)
-    value = nq / total
+
+    def step():
+        for sc in scs:
+            oracle.match_scene(sc)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    total = time.perf_counter() - t0
+    q_per_step = sum(sc.m for sc in scs)
+    value = q_per_step * args.steps / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD + "; one pair per step, cycled", "pairs_per_step": 1},
+        "config": {"workload": WORKLOAD, "pairs_per_step": len(scs), "queries_per_step": q_per_step,
+                   "form": "CPU oracle: FP64 brute force over every (query, reference) pair",
+                   "parallelism": f"OpenMP over queries, {oracle.num_threads()} threads"},
         "cpu_baseline": {"value": value, "unit": "queries/s", "cores": oracle.num_threads(),
-                         "kind": "oracle", "sample": f"{args.steps} timed steps of one config pair each"},
+                         "kind": "oracle",
+                         "sample": f"{args.steps} timed steps of the nine config pairs ({q_per_step} queries each)"},
         "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -510,6 +561,166 @@ def mlp_leg(mt, torch, stream):
     return out
 
 
+def _config5_chunk(seed, idx):
+    import synth
+
+    return synth.config5(seed=seed, only=idx)
+
+
+def config5_scenes(seed, npairs):
+    """The config-5 pairs, generated on the host cores in parallel (spawned
+    workers: safe beside a CUDA context)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    workers = max(1, min(16, os.cpu_count() or 1))
+    chunks = [list(range(k, npairs, workers)) for k in range(workers)]
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        parts = list(ex.map(_config5_chunk, [seed] * len(chunks), chunks))
+    out = [None] * npairs
+    for idx, scs in zip(chunks, parts):
+        for p, sc in zip(idx, scs):
+            out[p] = sc
+    return out
+
+
+def learned_tolerance_experiment(mt, torch, stream, args):
+    """Config 5 as stated: 512 pairs (4k-16k keypoints per image, keypoint
+    scale s ~ logU[1, 16], localisation noise 0.3 s px); the network is
+    trained by the library's kernels on the exact residuals of the true
+    matches of pairs 0-383 (Adam, lr 1e-3, 20 epochs, pinball loss at
+    q = 0.95) and tested on pairs 384-511 against the fixed tolerance of
+    2 px and against a fixed tolerance with the same candidate budget (the
+    mean learned tolerance).  The oracle judges: its brute-force candidate
+    sets at each tolerance give the candidate recall (true match in the
+    set) and the candidates per query, and the GPU candidate sets at the
+    learned tolerance are compared with them pair by pair.  Matching rates
+    are the 128 test pairs in one CUDA-graph launch per step."""
+    import numpy as np
+
+    import oracle
+    import synth
+
+    t0 = time.perf_counter()
+    scenes = config5_scenes(0, args.learned_pairs)
+    gen_s = time.perf_counter() - t0
+    ntrain = args.learned_pairs * 3 // 4
+    train, test = scenes[:ntrain], scenes[ntrain:]
+    dev = mt.device
+    # training set: features of the image-2 keypoint of every true match and
+    # its exact residual (Eq. 3, egm_pair_residuals)
+    F, R = [], []
+    for sc in train:
+        d = mt.to_device(sc)
+        F.append(sc.feat2[sc.gt[:, 1]])
+        R.append(mt.residuals(d["xy1"], d["xy2"], d["F"], sc.gt[:, 0], sc.gt[:, 1]))
+    f = torch.as_tensor(np.concatenate(F).astype(np.float32)).to(dev)
+    r = torch.cat(R).float()
+    del F, R
+    net = mt.tolnet(synth.mlp_init(0))
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    batch, epochs, lr, q = 1024, 20, 1e-3, 0.95
+    steps = 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(epochs):
+        perm = torch.randperm(f.shape[0], device=dev, generator=g)
+        fp, rp = f[perm].contiguous(), r[perm].contiguous()
+        for b in range(0, f.shape[0] - batch + 1, batch):
+            net.train_step(fp[b:b + batch], rp[b:b + batch], lr, q)
+            steps += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+
+    # held-out pairs: learned tolerance, then the oracle's judgement
+    eps_l = [net.infer(sc.feat2).cpu().numpy() for sc in test]
+    mean_l = float(np.mean(np.concatenate(eps_l)))
+    settings = (("learned", eps_l), ("fixed_2px", [2.0] * len(test)), ("fixed_same_budget", [mean_l] * len(test)))
+    rows = {}
+    identical = 0
+    for name, eps in settings:
+        hit = cand = tot = 0
+        for k, (sc, e) in enumerate(zip(test, eps)):
+            c = oracle.candidates(sc.xy1, sc.xy2, sc.F, e)
+            off, idx = c["offsets"], c["idx"]
+            rowid = np.repeat(np.arange(sc.m, dtype=np.int64), np.diff(off))
+            hit += int(np.isin(sc.gt[:, 0] * sc.n + sc.gt[:, 1], rowid * sc.n + idx).sum())
+            cand += int(off[-1])
+            tot += len(sc.gt)
+            if name == "learned":
+                d = mt.to_device(sc)
+                o = mt.match(d["xy1"], d["xy2"], d["F"], torch.as_tensor(e).to(dev), d["desc1"], d["desc2"],
+                             sc.kind, sc.dim, sc.width, sc.height, csr=True)
+                identical += int(np.array_equal(o["cand_offsets"].cpu().numpy(), off) and
+                                 np.array_equal(o["cand_idx"].cpu().numpy(), idx))
+        rows[name] = {"candidate_recall": hit / tot, "candidates_per_query": cand / sum(s.m for s in test),
+                      "mean_eps_px": float(np.mean(np.concatenate([np.broadcast_to(e, (s.n,)) for s, e in
+                                                                   zip(test, eps)])))}
+
+    # matching on the GPU: the 128 test pairs in one graph per step
+    qn = sum(s.m for s in test)
+    feat_all = torch.as_tensor(np.concatenate([s.feat2 for s in test]).astype(np.float32)).to(dev)
+    for name, eps in settings:
+        items = []
+        for sc, e in zip(test, eps):
+            d = mt.to_device(sc)
+            d["eps"] = torch.as_tensor(e).to(dev) if np.ndim(e) else float(e)
+            items.append(d)
+        out = mt._alloc_out(qn, False, 0)
+        graph = mt.graph_create(items, out)
+        for _ in range(3):
+            graph.launch()
+        torch.cuda.synchronize()
+        reps = 10
+        e0.record(stream)
+        for _ in range(reps):
+            graph.launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        graph.close()
+        best, flags = out["best"].cpu().numpy(), out["flags"].cpu().numpy()
+        tp = ngot = ntrue = 0
+        q0 = 0
+        for sc in test:
+            ok = np.nonzero(flags[q0:q0 + sc.m] & 2)[0]
+            got = set(zip(ok.tolist(), best[q0:q0 + sc.m][ok].tolist()))
+            truth = set(map(tuple, sc.gt.tolist()))
+            tp += len(got & truth)
+            ngot += len(got)
+            ntrue += len(truth)
+            q0 += sc.m
+        rows[name].update({"match_ms": ms, "queries_per_s": qn / (ms * 1e-3), "matches": ngot,
+                           "matches_per_s": ngot / (ms * 1e-3), "matching_recall": tp / max(ntrue, 1),
+                           "matching_precision": tp / max(ngot, 1)})
+    # inference over every test keypoint
+    epsbuf = torch.empty(feat_all.shape[0], dtype=torch.float64, device=dev)
+    from paper_2603_18401_gb300 import check
+
+    for _ in range(3):
+        check(mt.lib.egm_mlp_infer(net.handle, feat_all.data_ptr(), feat_all.shape[0], epsbuf.data_ptr()), "infer")
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(10):
+        check(mt.lib.egm_mlp_infer(net.handle, feat_all.data_ptr(), feat_all.shape[0], epsbuf.data_ptr()), "infer")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    infer_ms = e0.elapsed_time(e1) / 10
+    rows["learned"]["infer_ms"] = infer_ms
+    rows["learned"]["queries_per_s_with_inference"] = qn / ((rows["learned"]["match_ms"] + infer_ms) * 1e-3)
+    net.close()
+    return {"workload": f"config 5: {len(scenes)} pairs 6048x4032, 4096-16384 keypoints per image, scale "
+                        "logU[1,16], noise 0.3 s px; train on pairs 0-" + str(ntrain - 1) + ", test on " +
+                        f"{ntrain}-{len(scenes) - 1}",
+            "training": {"samples": int(f.shape[0]), "epochs": epochs, "batch": batch, "lr": lr, "quantile": q,
+                         "adam_steps": steps, "ms": train_ms, "generation_s": gen_s},
+            "oracle_checked_pairs": len(test), "gpu_candidate_sets_identical_to_oracle": identical,
+            "judge": "oracle brute-force candidate sets (recall = true match in the set)",
+            "test": rows}
+
+
 def batched_leg(mt, torch, stream, args, world, local):
     """The batched configuration: 256 pairs with uneven counts in one
     CUDA-graph launch per step, in the requested form and the plain form,
@@ -565,18 +776,24 @@ def batched_leg(mt, torch, stream, args, world, local):
                "form": f"{args.form} (egm_graph_launch, one CUDA graph per step)",
                "stage_ms": bstage}
     if bform != 1:
-        # the band kernel over the batch: every query's packed row (256 B),
-        # sorted record (48 B) and result (17 B), every reference's packed row,
-        # record (16 B) and norms (16 B), once
-        kb = bM * (256 + 48 + 17) + sum(s.n for s in bsc) * (256 + 16 + 16)
+        # the band kernel over the batch, on the method's algorithmic bytes
+        # (each pair's inputs read once, its results written once); the
+        # kernel's own layout (packed 256-byte operand rows, sorted records,
+        # norms) beside them
+        kb = sum(algorithmic_bytes(s) for s in bsc)
+        lb = bM * (256 + 48 + 17) + sum(s.n for s in bsc) * (256 + 16 + 16)
         ks = bstage["stab"] * 1e-3
         peak, peak_kind = measured_peaks()
         prof = kernel_profile("band_kernel", "batch")
+        traffic = prof.get("dram_bytes_per_launch") if prof else None
         batched["roofline"] = {"kernel": "band_kernel", "bound": "hbm", "achieved": kb / ks / 1e9, "peak": peak,
                                "peak_source": peak_kind, "unit": "GB/s", "frac": kb / ks / 1e9 / peak,
-                               "algorithmic_bytes_per_launch": kb, "avg_launch_us": ks * 1e6,
-                               "traffic": prof.get("dram_bytes_per_launch") if prof else None,
-                               "tensor_pipe_active_pct": prof.get("tensor_pipe_active_pct") if prof else None}
+                               "algorithmic_bytes_per_launch": kb, "layout_bytes_per_launch": lb,
+                               "avg_launch_us": ks * 1e6, "traffic": traffic,
+                               "traffic_over_algorithmic": traffic / kb if traffic else None,
+                               "tensor_pipe_active_pct": prof.get("tensor_pipe_active_pct") if prof else None,
+                               "whole_batch": {"achieved": kb / (bms * 1e-3) / 1e9,
+                                               "frac": kb / (bms * 1e-3) / 1e9 / peak}}
     if bform != 1 and not args.no_compare:
         pms = time_graph(1)
         batched["plain_form"] = {"pairs_per_s": world * len(bsc) / (pms * 1e-3), "ms_per_step": pms}
@@ -673,6 +890,7 @@ def run_ours(args):
         evs[k][0].record(stream)
         step()
         evs[k][1].record(stream)
+    clocks.edge()  # the enqueued steps are still running on the device
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier(world)
@@ -709,12 +927,13 @@ def run_ours(args):
     dom = max(stage_ms, key=stage_ms.get)
     n_banded = sum(1 for _, b in per_pair if b)
 
-    def kernel_bytes(sc, band):
+    def layout_bytes(sc, band):
+        """The kernel's own layout: what it reads and writes per launch."""
         if band:
             # every query's packed operand row (256 B), sorted record (48 B) and
             # result (17 B) once; every reference's packed row (256 B), record
-            # (16 B) and norm (4 B) once
-            return sc.m * (256 + 48 + 17) + sc.n * (256 + 16 + 4)
+            # (16 B) and norms (16 B) once
+            return sc.m * (256 + 48 + 17) + sc.n * (256 + 16 + 16)
         # every query's line record (48 B), descriptor and result (17 B) once;
         # every reference's record (16 B) and descriptor once
         row = sc.desc1.shape[1]
@@ -722,26 +941,38 @@ def run_ours(args):
 
     kt = {False: 0.0, True: 0.0}
     kb = {False: 0.0, True: 0.0}
+    kl = {False: 0.0, True: 0.0}
     for (st_ms, b), sc in zip(per_pair, scs):
         kt[b] += st_ms["stab"]
-        kb[b] += kernel_bytes(sc, b)
+        kb[b] += algorithmic_bytes(sc)
+        kl[b] += layout_bytes(sc, b)
     banded = kt[True] > kt[False]
     kernel = "band_kernel" if banded else "stab_kernel"
     npk = n_banded if banded else len(scs) - n_banded
     kbytes = kb[banded] / max(npk, 1)
+    lbytes = kl[banded] / max(npk, 1)
     k_s = kt[banded] / max(npk, 1) * 1e-3
     peak, peak_kind = measured_peaks()
     achieved = kbytes / k_s / 1e9
     prof = kernel_profile(kernel)
+    traffic = prof.get("dram_bytes_per_launch") if prof else None
+    step_bytes = sum(algorithmic_bytes(sc) for sc in scs)
+    step_s = ms / args.steps * 1e-3
     roofline = {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": prof.get("dram_bytes_per_launch") if prof else None,
+                "traffic": traffic,
+                "traffic_over_algorithmic": traffic / kbytes if traffic else None,
                 "tensor_pipe_active_pct": prof.get("tensor_pipe_active_pct") if prof else None,
                 "avg_launch_us": k_s * 1e6, "algorithmic_bytes_per_launch": kbytes,
+                "algorithmic_bytes_rule": "per query 16 + D + 17 B, per reference 16 + D (+8 with per-keypoint "
+                                          "eps) B, per pair 72 B; D = 128 (u8), 32 (binary), 512 (float)",
+                "layout_bytes_per_launch": lbytes,
                 "launches_averaged": f"{npk} of the {len(scs)} pairs run this kernel",
                 "stage_us_per_pair": {k: round(v * 1e3, 2) for k, v in stage_ms.items()},
                 "dominant_stage": dom,
-                "pairs_banded": n_banded}
+                "pairs_banded": n_banded,
+                "whole_step": {"algorithmic_bytes": step_bytes, "achieved": step_bytes / step_s / 1e9,
+                               "frac": step_bytes / step_s / 1e9 / peak}}
 
     # the same step in each forced form (or the other one), for comparison
     other_form = None
@@ -910,6 +1141,8 @@ def run_ours(args):
     mlp = None
     if not args.no_mlp:
         mlp = mlp_leg(mt, torch, stream)
+        if not args.no_learned_experiment:
+            mlp["experiment"] = learned_tolerance_experiment(mt, torch, stream, args)
 
     # kernels per match call: geometry, prep, bucket count, bucket scan, and
     # either the stab kernel or the query sort, pack and band kernels

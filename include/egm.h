@@ -174,7 +174,15 @@ typedef struct egm_params {
     int32_t float_pass;    /* banded form, float descriptors: the tensor-core pass that brackets
                               the distances before the exact FP32 rerank (results are the same):
                               EGM_FLOAT_PASS_BF16 (default) or EGM_FLOAT_PASS_FP8 */
-    int32_t reserved[10];  /* zero */
+    int32_t timeout_check; /* 0 (default); 1: a check of the device timeout path (no results).
+                              Every wait of the banded form's kernel on the device is bounded
+                              (2 s); when one gives up, the kernel records EGM_ERR_TIMEOUT, lets
+                              the copies and tensor-core operations it issued complete (again
+                              bounded), releases its tensor memory and ends.  With 1, each CTA of
+                              that kernel first waits 10 us on a barrier that nothing completes,
+                              before it issues any copy: banded calls then return
+                              EGM_ERR_TIMEOUT and the context stays usable */
+    int32_t reserved[9];   /* zero */
 } egm_params;
 
 /* Context lifetime.  `stream` is a cudaStream_t (NULL: the legacy default stream). */
@@ -186,7 +194,10 @@ egm_status egm_get_params(egm_ctx *ctx, egm_params *params);
 void egm_default_params(egm_params *params);
 
 /* Grow the context's scratch to hold at least this many queries,
- * references and pairs per call, so that later calls allocate nothing. */
+ * references and pairs per call, so that later calls allocate nothing.
+ * Memory management of the library (no counterpart in the paper, whose
+ * Algorithm 1 builds its index per call).  EGM_ERR_ARG for negative sizes,
+ * EGM_ERR_NOMEM when the device memory is not available. */
 egm_status egm_reserve(egm_ctx *ctx, int64_t queries, int64_t refs, int32_t pairs);
 
 /* Match one pair (steps 1-8 above).  Device pointers.
@@ -198,13 +209,19 @@ egm_status egm_reserve(egm_ctx *ctx, int64_t queries, int64_t refs, int32_t pair
 egm_status egm_match_pair(egm_ctx *ctx, const egm_pair *pair, const egm_out *out);
 
 /* Match npairs independent pairs in one pass (one launch per step for the
- * whole batch).  Device pointers; outputs concatenated as described above. */
+ * whole batch).  Algorithm 1 applied to each pair (its Match loop over the
+ * queries of every pair at once); the pairs share nothing, so the results
+ * equal npairs calls of egm_match_pair.  Device pointers; outputs
+ * concatenated as described above.  Errors as for egm_match_pair; an invalid
+ * pair rejects the whole call before any work. */
 egm_status egm_match_batch(egm_ctx *ctx, const egm_pair *pairs, int32_t npairs,
                            const egm_out *out);
 
 /*
  * A batch captured once as a CUDA graph and replayed many times (the same
  * pointers and sizes every time; the data behind the pointers may change).
+ * The computation is egm_match_batch's (Algorithm 1 per pair); the graph is
+ * a launch mechanism of the library with no counterpart in the paper.
  * The graph owns its own scratch, sized for this batch, and its own copy of
  * the pair table, so ordinary calls on the context in between do not
  * disturb it.  egm_graph_launch enqueues the whole pipeline with one graph
@@ -264,17 +281,6 @@ egm_status egm_match_pair_static(const egm_pair *pair, const egm_out *out, const
 /* Wait for the context's stream and return (then clear) the device status. */
 egm_status egm_sync(egm_ctx *ctx);
 
-/*
- * The paper's interval view, for inspection and tests (Sec. 4.2, Eq. theta
- * and delta; Algorithm 1 preprocessing), computed on the device in FP64:
- *   e3     [3] float64   epipole e2 = null(F^T), unit norm, e_w >= 0
- *   mode   [1] int32     0: finite epipole (angular), 1: epipole at or near
- *                        infinity (parallel lines; theta/delta not defined)
- *   theta  [n] float64   atan2(y_j - y_e, x_j - x_e) reduced to [0, pi)
- *   delta  [n] float64   asin(eps_j / ||p_j - e2||), or pi/2 when
- *                        ||p_j - e2|| <= eps_j (full interval)
- * In parallel mode theta/delta receive NaN.  Device pointers; any may be NULL.
- */
 /*
  * Mutual (cross-check) matching: the matching step of Algorithm 1 run in both
  * directions; a match i -> j is kept as mutual when j's best match in the
@@ -339,6 +345,17 @@ typedef struct egm_gms_pair {
 egm_status egm_gms_batch(egm_ctx *ctx, const egm_gms_pair *pairs, int32_t npairs, uint32_t require, int32_t grid,
                          double alpha);
 
+/*
+ * The paper's interval view, for inspection and tests (Sec. 4.2, Eq. theta
+ * and delta; Algorithm 1 preprocessing), computed on the device in FP64:
+ *   e3     [3] float64   epipole e2 = null(F^T), unit norm, e_w >= 0
+ *   mode   [1] int32     0: finite epipole (angular), 1: epipole at or near
+ *                        infinity (parallel lines; theta/delta not defined)
+ *   theta  [n] float64   atan2(y_j - y_e, x_j - x_e) reduced to [0, pi)
+ *   delta  [n] float64   asin(eps_j / ||p_j - e2||), or pi/2 when
+ *                        ||p_j - e2|| <= eps_j (full interval)
+ * In parallel mode theta/delta receive NaN.  Device pointers; any may be NULL.
+ */
 egm_status egm_intervals(egm_ctx *ctx, const egm_pair *pair, double *theta, double *delta,
                          double *e3, int32_t *mode);
 
@@ -370,9 +387,17 @@ egm_status egm_mlp_set_state(egm_mlp *mlp, const float *params, const float *ada
 /* eps [n] float64 (device) for features [n][5] float32 (device); the output
  * can be passed as egm_pair.eps2.  Layers 2 and 3 run on the tensor cores
  * (tcgen05.mma, BF16 weights; each FP32 activation enters as the sum of two
- * BF16 parts, so results agree with FP32 products to about 1e-6 relative);
- * EGM_ERR_TIMEOUT if a tensor-core wait gave up (outputs NaN). */
+ * BF16 parts, so results agree with FP32 products to about 1e-6 relative).
+ * Fixed-tolerance fallback: a sample whose network output is not a finite
+ * tolerance (NaN / Inf features, or weights that overflow) receives the
+ * fallback tolerance (2 px, see egm_mlp_set_fallback) instead, so every
+ * output is a valid egm_pair.eps2 entry.  EGM_ERR_TIMEOUT if a tensor-core
+ * wait gave up: the samples of the blocks concerned receive the fallback. */
 egm_status egm_mlp_infer(egm_mlp *mlp, const float *feat, int64_t n, double *eps);
+/* The fallback tolerance of egm_mlp_infer in pixels (default 2, the fixed
+ * tolerance the learned one is compared with).  EGM_ERR_ARG unless finite
+ * and > 0. */
+egm_status egm_mlp_set_fallback(egm_mlp *mlp, double eps_px);
 /* Gradient of the mean pinball loss (device outputs: grad [EGM_MLP_PARAMS], loss [1]). */
 egm_status egm_mlp_grad(egm_mlp *mlp, const float *feat, const float *resid, int64_t n, float quantile, float *grad,
                         float *loss);

@@ -60,9 +60,9 @@ class Matcher:
             pass
 
     # ------------------------------------------------------------- params
-    def set_params(self, ratio=None, sync=None, form=None, band_tile=None, float_pass=None):
+    def set_params(self, ratio=None, sync=None, form=None, band_tile=None, float_pass=None, timeout_check=None):
         """ratio (num, den); sync; form (EGM_FORM_*); band_tile (0: tuned, k > 0: shape k - 1);
-        float_pass (EGM_FLOAT_PASS_*)."""
+        float_pass (EGM_FLOAT_PASS_*); timeout_check (1: the banded kernel's timeout path, no results)."""
         p = _egm.egm_params()
         check(self.lib.egm_get_params(self.ctx, C.byref(p)), "egm_get_params")
         if ratio is not None:
@@ -75,6 +75,8 @@ class Matcher:
             p.band_tile = int(band_tile)
         if float_pass is not None:
             p.float_pass = int(float_pass)
+        if timeout_check is not None:
+            p.timeout_check = int(timeout_check)
         check(self.lib.egm_set_params(self.ctx, C.byref(p)), "egm_set_params")
 
     def reserve(self, queries: int, refs: int, pairs: int = 1):
@@ -372,6 +374,10 @@ class TolNet:
         eps = self.torch.empty(f.shape[0], dtype=self.torch.float64, device=self.mt.device)
         check(self.lib.egm_mlp_infer(self.handle, _ptr(f), f.shape[0], _ptr(eps)), "egm_mlp_infer")
         return eps
+
+    def set_fallback(self, eps_px):
+        """Tolerance given to samples without a finite network output (default 2 px)."""
+        check(self.lib.egm_mlp_set_fallback(self.handle, float(eps_px)), "egm_mlp_set_fallback")
 
     def grad(self, feat, resid, quantile):
         """(gradient [EGM_MLP_PARAMS] float32, mean pinball loss) on the device."""

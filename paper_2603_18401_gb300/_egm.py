@@ -62,7 +62,7 @@ class egm_out(C.Structure):
 class egm_params(C.Structure):
     _fields_ = [("ratio_num", C.c_int32), ("ratio_den", C.c_int32), ("sync", C.c_int32),
                 ("form", C.c_int32), ("band_tile", C.c_int32), ("float_pass", C.c_int32),
-                ("reserved", C.c_int32 * 10)]
+                ("timeout_check", C.c_int32), ("reserved", C.c_int32 * 9)]
 
 
 class egm_stats(C.Structure):
@@ -105,6 +105,7 @@ SIGNATURES = {
     "egm_mlp_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]),
     "egm_mlp_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     "egm_mlp_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "egm_mlp_set_fallback": (C.c_int, [C.c_void_p, C.c_double]),
     "egm_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_void_p,
                                C.c_void_p]),
     "egm_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_float,

@@ -11,9 +11,10 @@
 
 namespace egm {
 // Learned-tolerance inference with layers 2 and 3 on the tensor cores
-// (mlp.cu); a timed-out MMA wait sets kStTimeout in *err (device).
+// (mlp.cu); a timed-out MMA wait sets kStTimeout in *err (device); samples
+// without a finite output get `fallback`.
 cudaError_t launch_mlp_forward_tc(const float *params, const float *feat, int64_t n, double *eps, uint32_t *err,
-                                  int sms, cudaStream_t s);
+                                  double fallback, int sms, cudaStream_t s);
 }  // namespace egm
 
 using namespace egm;
@@ -378,6 +379,7 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
         L.rnorm = reinterpret_cast<float4 *>(b + bl.rnorm);
         L.qscale = reinterpret_cast<float *>(b + bl.qscale);
         L.fp8 = prm.float_pass == EGM_FLOAT_PASS_FP8;
+        L.probe = prm.timeout_check;
         L.tile_offs = offs + 2 * (npairs + 1);
         L.tile_seq = reinterpret_cast<const int32_t *>(offs + 3 * (npairs + 1));
         L.work = as<uint32_t>(c->small) + 32;
@@ -713,6 +715,7 @@ egm_status egm_set_params(egm_ctx *c, const egm_params *p) {
     if (p->form < EGM_FORM_AUTO || p->form > EGM_FORM_BANDED) return EGM_ERR_ARG;
     if (p->band_tile < 0 || p->band_tile > band_shapes()) return EGM_ERR_ARG;
     if (p->float_pass != EGM_FLOAT_PASS_BF16 && p->float_pass != EGM_FLOAT_PASS_FP8) return EGM_ERR_ARG;
+    if (p->timeout_check != 0 && p->timeout_check != 1) return EGM_ERR_ARG;
     c->params = *p;
     return EGM_OK;
 }
@@ -1159,6 +1162,7 @@ struct egm_mlp {
     egm_ctx *ctx = nullptr;
     DevBuf params, m, v, grad, pre, z, loss, err;
     int64_t step = 0;
+    double fallback = 2.0;   // tolerance (px) of samples without a finite network output
 };
 
 extern "C" {
@@ -1225,13 +1229,20 @@ egm_status egm_mlp_set_state(egm_mlp *m, const float *params, const float *am, c
     return EGM_OK;
 }
 
+egm_status egm_mlp_set_fallback(egm_mlp *m, double eps_px) {
+    if (!m || !(eps_px > 0.0) || !(eps_px < INFINITY)) return EGM_ERR_ARG;
+    m->fallback = eps_px;
+    return EGM_OK;
+}
+
 egm_status egm_mlp_infer(egm_mlp *m, const float *feat, int64_t n, double *eps) {
     if (!m || n < 0 || (n > 0 && (!feat || !eps))) return EGM_ERR_ARG;
     EGM_TRY(cudaSetDevice(m->ctx->device));
     if (n == 0) return EGM_OK;
     cudaStream_t st = m->ctx->stream;
     EGM_TRY(cudaMemsetAsync(m->err.ptr, 0, sizeof(uint32_t), st));
-    EGM_TRY(launch_mlp_forward_tc(as<float>(m->params), feat, n, eps, as<uint32_t>(m->err), m->ctx->sms, st));
+    EGM_TRY(launch_mlp_forward_tc(as<float>(m->params), feat, n, eps, as<uint32_t>(m->err), m->fallback,
+                                  m->ctx->sms, st));
     uint32_t bits = 0;
     EGM_TRY(cudaMemcpyAsync(&bits, m->err.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     EGM_TRY(cudaStreamSynchronize(st));

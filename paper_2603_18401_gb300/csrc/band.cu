@@ -328,6 +328,7 @@ struct BandSmem {
     // done; fullR: a stage's records and norms landed; done: an accumulator is
     // ready; tfree: the epilogue has read it and the stage's records
     uint64_t fullB[2], sfree[2], fullR[2], done[2], tfree[2], afull;
+    uint64_t probe;               // never arrived on: the wait of the timeout check (Launch::probe)
     PairGeom g;
     PairDesc pd;
     Piece pc[2 * kLevels];
@@ -519,6 +520,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             tc::mbar_init(&S.tfree[s], 4);
         }
         tc::mbar_init(&S.afull, 1);
+        tc::mbar_init(&S.probe, 1);
         tc::fence_mbar_init();
         S.err = 0;
         S.gpair = -1;
@@ -545,6 +547,18 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
     };
     uint32_t seq = 0, aload = 0;
     unsigned long long nwin = 0, ncand = 0, nexact = 0;
+    // phases the control thread armed on each barrier (copies and MMAs issued):
+    // after a failed wait, the CTA lets them complete before it leaves
+    uint32_t armB[2] = {0u, 0u}, armR[2] = {0u, 0u}, armD[2] = {0u, 0u}, armA = 0u;
+    if (L.probe) {
+        // the timeout check: a short wait on a barrier that nothing arrives
+        // on, before any copy or MMA is issued, takes the error path below
+        if (ctl && !tc::mbar_wait(&S.probe, 0u, 10000ull)) {
+            S.err = 1;
+            atomicOr(L.status, kStTimeout);
+        }
+        __syncthreads();
+    }
 
     for (;;) {
         const int64_t tile = S.tile;
@@ -573,6 +587,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         const float qs = FLT && qv ? L.qscale[q_off + t0 + tid] : 1.0f;  // row scale of the FP8 pass
         if (ctl) {
             tc::mbar_arrive_expect_tx(&S.afull, 2 * kTM * 128);
+            armA++;
             tc::tma_load_2d(S.A[0], &tmA, 0, (int32_t)(q_off + t0), &S.afull);
             tc::tma_load_2d(S.A[1], &tmA, 128, (int32_t)(q_off + t0), &S.afull);
         }
@@ -713,6 +728,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 if (c >= 2 && !wait(&S.sfree[st], (use - 1) & 1u)) return;
                 const int nb = min(kCB, nbox - c * kCB);
                 tc::mbar_arrive_expect_tx(&S.fullB[st], (uint32_t)nb * (2 * kBoxR * 128));
+                armB[st]++;
                 for (int bb = 0; bb < nb; bb++) {
                     uint32_t pos, len;
                     int li;
@@ -726,6 +742,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 const uint32_t st = (seq + (uint32_t)c) & 1u;
                 const int nb = min(kCB, nbox - c * kCB);
                 tc::mbar_arrive_expect_tx(&S.fullR[st], (uint32_t)nb * (kBoxR * 16 + kBoxR * 16));
+                armR[st]++;
                 for (int bb = 0; bb < nb; bb++) {
                     uint32_t pos, len;
                     int li;
@@ -765,6 +782,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 }
                 tc::mma_commit(&S.done[st]);
                 tc::mma_commit(&S.sfree[st]);
+                armD[st]++;
                 if (c + 2 < nchunk) issueB(c + 2);
             }
             // the query tile's load completes before its buffer is reused
@@ -951,6 +969,23 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             atomicAdd(L.counters + 3, (unsigned long long)b);
             atomicAdd(L.counters + 4, (unsigned long long)c);
         }
+    }
+    if (ctl && S.err) {
+        // A wait gave up.  Before the CTA's shared memory and TMEM are
+        // released, every copy and MMA it issued must have landed: wait
+        // (bounded) for the last phase armed on each barrier.  The pipeline
+        // re-arms a barrier only after the previous phase was waited for, so
+        // at most that last phase is outstanding; an MMA commit also covers
+        // every earlier MMA of the thread.
+        for (int st = 0; st < 2; st++) {
+            if (armB[st]) tc::mbar_wait(&S.fullB[st], (armB[st] - 1u) & 1u);
+            if (armR[st]) tc::mbar_wait(&S.fullR[st], (armR[st] - 1u) & 1u);
+            if (armD[st]) {
+                tc::mbar_wait(&S.done[st], (armD[st] - 1u) & 1u);
+                tc::mbar_wait(&S.sfree[st], (armD[st] - 1u) & 1u);
+            }
+        }
+        if (armA) tc::mbar_wait(&S.afull, (armA - 1u) & 1u);
     }
     tc::tc_fence_before();
     __syncthreads();

@@ -179,6 +179,7 @@ struct Launch {
     const int32_t *tile_seq;      // ntiles: tiles in the order they are handed out (costliest pairs first)
     uint32_t *work;               // tile dispenser (zeroed before the band kernel)
     int64_t ntiles;
+    int32_t probe;                // timeout check: band CTAs first wait on a barrier nothing completes
     // a single pair's plan travels in the launch parameters: the geometry
     // kernel writes the pair table, offsets and tile order that the later
     // kernels read, so the call needs no host-to-device copy

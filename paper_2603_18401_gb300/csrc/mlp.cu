@@ -187,10 +187,12 @@ __device__ __forceinline__ void store_split(MlpTcSmem &S, int r, const float (&h
 }
 
 // Persistent: each block takes tiles of 128 samples in turn.  Every wait on
-// the MMA barrier is bounded; a timeout sets the timeout bit in *err, the
-// block issues no more MMAs and its remaining outputs are NaN.
+// the MMA barrier is bounded; a timeout sets the timeout bit in *err and the
+// block issues no more MMAs.  A sample whose output is not a finite
+// tolerance (non-finite features, or a block whose MMA wait gave up) gets the
+// fixed tolerance `fallback` instead.
 __global__ void __launch_bounds__(kTT, 4) mlp_forward_tc_kernel(const float *params, const float *feat, int64_t n,
-                                                                double *eps, uint32_t *err) {
+                                                                double *eps, uint32_t *err, double fallback) {
     extern __shared__ uint8_t smraw[];
     MlpTcSmem &S = *reinterpret_cast<MlpTcSmem *>(smraw + ((1024u - (tc::smem_addr(smraw) & 1023u)) & 1023u));
     const int t = threadIdx.x, warp = t >> 5;
@@ -229,6 +231,7 @@ __global__ void __launch_bounds__(kTT, 4) mlp_forward_tc_kernel(const float *par
     // where it must be (the warp for TMEM loads, the block for barriers), and
     // no thread leaves the loops early.
     bool failed = false;
+    uint32_t mma_commits = 0;  // phases of S.bar armed (the same count in every thread)
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t s = tile * kTT + t;
         const bool valid = s < n;
@@ -263,6 +266,7 @@ __global__ void __launch_bounds__(kTT, 4) mlp_forward_tc_kernel(const float *par
                                      tc::sdesc_sw128(tc::smem_addr(W) + 32 * kk), idesc, 1);
                     tc::mma_commit(&S.bar);
                 }
+                mma_commits++;
                 // two commits per tile: the layer's phase parity is l
                 const bool done = tc::mbar_wait(&S.bar, (uint32_t)l);
                 failed = __any_sync(0xffffffffu, !done);
@@ -285,8 +289,14 @@ __global__ void __launch_bounds__(kTT, 4) mlp_forward_tc_kernel(const float *par
         float z = S.b4;
 #pragma unroll
         for (int j = 0; j < kH; j++) z = fmaf(S.w4[j], h[j], z);
-        if (valid) eps[s] = failed ? (double)NAN : (double)(softplus(z) + kEpsFloor);
+        if (valid) {
+            const float e = softplus(z) + kEpsFloor;
+            eps[s] = (failed || !isfinite(e)) ? fallback : (double)e;
+        }
     }
+    // after a failed wait the MMAs of the last commit may still run: wait for
+    // that commit's phase (bounded) before the TMEM is released
+    if (failed && t == 0) tc::mbar_wait(&S.bar, (uint32_t)(mma_commits - 1) & 1u);
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemMlp);
@@ -524,14 +534,14 @@ cudaError_t launch_mlp_forward(const float *params, const float *feat, int64_t n
 }
 
 cudaError_t launch_mlp_forward_tc(const float *params, const float *feat, int64_t n, double *eps, uint32_t *err,
-                                  int sms, cudaStream_t s) {
+                                  double fallback, int sms, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int smem = (int)sizeof(MlpTcSmem) + 1024;
     cudaError_t e = cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (n + kTT - 1) / kTT;
     const int grid = (int)std::min<int64_t>(tiles, 4 * (int64_t)sms);
-    mlp_forward_tc_kernel<<<grid, kTT, smem, s>>>(params, feat, n, eps, err);
+    mlp_forward_tc_kernel<<<grid, kTT, smem, s>>>(params, feat, n, eps, err, fallback);
     return cudaGetLastError();
 }
 

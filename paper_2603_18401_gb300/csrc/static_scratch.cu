@@ -127,33 +127,27 @@ extern "C" egm_status egm_match_pair_static(const egm_pair *P, const egm_out *ou
     EGM_STATIC_TRY(scratch_address(device, &base));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
-    // pair table and offsets (copied from host memory on the stack)
-    struct Upload {
-        PairDesc pd;
-        int64_t offs[4];
-    } up;
-    memset(&up, 0, sizeof(up));
-    up.pd.xy1 = P->xy1;
-    up.pd.xy2 = P->xy2;
-    up.pd.F = P->F;
-    up.pd.eps2 = P->eps2;
-    up.pd.desc1 = static_cast<const uint8_t *>(P->desc1);
-    up.pd.desc2 = static_cast<const uint8_t *>(P->desc2);
-    up.pd.eps_scalar = P->eps_scalar;
-    up.pd.m = P->m;
-    up.pd.n = P->n;
-    up.pd.kind = desc ? P->kind : EGM_DESC_U8_L2;
-    up.pd.dim = P->dim;
-    up.pd.row_bytes = rb;
-    up.pd.width = P->width;
-    up.pd.height = P->height;
-    up.pd.t_cap = kTabCap;
-    up.offs[0] = 0;
-    up.offs[1] = P->m;
-    up.offs[2] = 0;
-    up.offs[3] = P->n;
-    EGM_STATIC_TRY(cudaMemcpyAsync(base + kOffPairs, &up.pd, sizeof(PairDesc), cudaMemcpyHostToDevice, st));
-    EGM_STATIC_TRY(cudaMemcpyAsync(base + kOffOffs, up.offs, sizeof(up.offs), cudaMemcpyHostToDevice, st));
+    // The pair travels in the launch parameters: the geometry kernel writes
+    // the pair table and offsets into the array for the later kernels, so the
+    // call copies nothing from host memory.
+    PairDesc pd;
+    memset(&pd, 0, sizeof(pd));
+    pd.xy1 = P->xy1;
+    pd.xy2 = P->xy2;
+    pd.F = P->F;
+    pd.eps2 = P->eps2;
+    pd.desc1 = static_cast<const uint8_t *>(P->desc1);
+    pd.desc2 = static_cast<const uint8_t *>(P->desc2);
+    pd.eps_scalar = P->eps_scalar;
+    pd.m = P->m;
+    pd.n = P->n;
+    pd.kind = desc ? P->kind : EGM_DESC_U8_L2;
+    pd.dim = P->dim;
+    pd.row_bytes = rb;
+    pd.width = P->width;
+    pd.height = P->height;
+    // bucket-table entries this pair needs (the prep kernel zeroes them all)
+    pd.t_cap = 4 * (int64_t)P->n + 2 * kLevels + 32;
     // the array keeps the previous call's contents: clear the status word and counters
     EGM_STATIC_TRY(cudaMemsetAsync(base + kOffSmall, 0, 256, st));
 
@@ -176,7 +170,7 @@ extern "C" egm_status egm_match_pair_static(const egm_pair *P, const egm_out *ou
     L.val_c = k + 5 * nr;
     L.rec = reinterpret_cast<float4 *>(base + kOffRec);
     L.tab = reinterpret_cast<uint32_t *>(base + kOffTab);
-    L.ntab = kTabCap;
+    L.ntab = pd.t_cap;
     L.curs = reinterpret_cast<uint32_t *>(base + kOffCurs);
     L.prep_done = reinterpret_cast<uint32_t *>(base + kOffSmall) + 40;
     L.qrec = reinterpret_cast<QueryRec *>(base + kOffQrec);
@@ -188,7 +182,9 @@ extern "C" egm_status egm_match_pair_static(const egm_pair *P, const egm_out *ou
     L.ratio_num = rn;
     L.ratio_den = rd;
     L.max_n = P->n;
-    L.kind = up.pd.kind;
+    L.kind = pd.kind;
+    L.inl_use = 1;
+    L.inl = pd;
     L.best = out->best;
     L.second = out->second;
     L.best_d = out->best_d;

@@ -312,18 +312,21 @@ def config4(seed: int = 0, npairs: int = 64, scale: float = 1.0) -> list[Scene]:
     return out
 
 
-def config5(seed: int = 0, npairs: int = 512, scale: float = 1.0) -> list[Scene]:
-    """Scale-dependent localisation noise (sigma = 0.3 s) for the learned per-keypoint tolerance."""
+def config5(seed: int = 0, npairs: int = 512, scale: float = 1.0, only=None) -> list[Scene]:
+    """Scale-dependent localisation noise (sigma = 0.3 s) for the learned per-keypoint tolerance.
+
+    Pair p draws from its own generator, so `only` (indices of the pairs to
+    build) gives the same scenes as the full list."""
     K = intrinsics(HIGHRES_F, HIGHRES_W, HIGHRES_H)
     out = []
-    for p in range(npairs):
-        rng = np.random.default_rng([seed, 5, p])
+    for p in (range(npairs) if only is None else only):
+        rng = np.random.default_rng([seed, 5, int(p)])
         m = max(2, int(rng.integers(4096, 16385) * scale))
         n = max(2, int(rng.integers(4096, 16385) * scale))
         R, t = _random_pose(rng, 30.0)
         out.append(make_pair(rng, w=HIGHRES_W, h=HIGHRES_H, K1=K, K2=K, R=R, t=t, m=m, n=n,
                              n_true=int(0.7 * min(m, n)), eps=2.0, kind=DESC_U8_L2, dim=128,
-                             scale_model=True, meta=dict(config=5, seed=seed, pair=p)))
+                             scale_model=True, meta=dict(config=5, seed=seed, pair=int(p))))
     return out
 
 

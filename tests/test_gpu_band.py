@@ -383,3 +383,32 @@ def test_float_distance_error_against_fp64(mt, fpass):
             worst = max(worst, float(rel.max()))
     print(f"pass {fpass}: largest relative error of FP32 best distances against FP64: {worst:.3e}")
     assert worst <= 1e-5
+
+
+def test_device_timeout_path_reports_and_context_survives(mt):
+    """The band kernel's bounded-wait error path, run with nothing in flight:
+    with timeout_check = 1 every CTA first waits 10 us on a barrier that
+    nothing completes, records the timeout, releases its tensor memory and
+    ends; the call returns EGM_ERR_TIMEOUT and the next call on the same
+    context is exact again."""
+    from paper_2603_18401_gb300 import EgmError
+
+    sc = synth.config2("far", 4.0, scale=0.125)
+    mt.set_params(timeout_check=1)
+    try:
+        for _ in range(2):
+            with pytest.raises(EgmError) as e:
+                run_form(mt, sc, FORM_BANDED)
+            assert e.value.status == -7
+    finally:
+        mt.set_params(timeout_check=0)
+    b = run_form(mt, sc, FORM_BANDED)
+    check_matches(b, sc)
+    # the plain form has no device waits: the check does not concern it
+    mt.set_params(timeout_check=1)
+    try:
+        p = run_form(mt, sc, FORM_PLAIN)
+    finally:
+        mt.set_params(timeout_check=0)
+    for k in KEYS:
+        assert np.array_equal(b[k], p[k]), k

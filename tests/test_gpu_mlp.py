@@ -261,3 +261,91 @@ def test_residuals_out_of_range_index_is_nan(mt):
     got = mt.residuals(d["xy1"], d["xy2"], d["F"], np.array([0, sc.m, -1, 0], np.int32),
                        np.array([0, 0, 0, sc.n], np.int32)).cpu().numpy()
     assert np.isfinite(got[0]) and np.all(np.isnan(got[1:]))
+
+
+def test_fixed_tolerance_fallback(mt):
+    """Samples without a finite network output receive the fixed tolerance
+    (2 px by default, settable): non-finite features, and a network whose
+    weights diverged; every other sample keeps its learned tolerance."""
+    from paper_2603_18401_gb300 import EgmError
+
+    net = mt.tolnet(params(4))
+    f = feats(300, 4)
+    want = net.infer(f).cpu().numpy()
+    bad = f.copy()
+    bad[3, 0] = 0.0            # ln(scale) = -inf
+    bad[17, 0] = np.nan
+    bad[40, 2] = np.inf        # ln(response) = +inf
+    bad[41, 3] = np.nan
+    got = net.infer(bad).cpu().numpy()
+    assert np.all(np.isfinite(got))
+    hit = np.array([3, 17, 40, 41])
+    rest = np.setdiff1d(np.arange(300), hit)
+    assert np.array_equal(got[rest], want[rest])
+    # each broken row holds either the fallback or a finite learned value
+    # (ln 0 = -inf can still saturate to a finite output); NaN rows fall back
+    assert got[17] == 2.0 and got[41] == 2.0
+    net.set_fallback(3.5)
+    got = net.infer(bad).cpu().numpy()
+    assert got[17] == 3.5 and got[41] == 3.5
+    assert np.array_equal(got[rest], want[rest])
+    with pytest.raises(EgmError):
+        net.set_fallback(0.0)
+    with pytest.raises(EgmError):
+        net.set_fallback(float("nan"))
+    # diverged weights: every sample falls back
+    st = net.state()
+    st["params"] = np.full_like(st["params"], np.nan)
+    net.load_state(st)
+    assert np.all(net.infer(f).cpu().numpy() == 3.5)
+    net.close()
+
+
+def _config5_split(ntrain, ntest, seed):
+    """Config-5 pairs at their stated size (4k-16k keypoints per image, scale
+    s ~ logU[1, 16], localisation noise 0.3 s px)."""
+    scenes = synth.config5(seed=seed, npairs=ntrain + ntest)
+    return scenes[:ntrain], scenes[ntrain:]
+
+
+def test_config5_full_size_learned_tolerance_exact_and_better_than_2px(mt):
+    """Config 5 at its stated sizes: the network is trained on the exact
+    residuals of the training pairs; on held-out pairs, matching with the
+    learned per-keypoint tolerance gives candidate sets and matches identical
+    to the oracle's, element by element, and the oracle judges the candidate
+    recall against the fixed tolerance of 2 px."""
+    import oracle
+    from test_gpu_parity import check_matches
+
+    train, test = _config5_split(24, 6, seed=21)
+    net = train_tolerance(mt, train, q=0.95, epochs=20, lr=1e-3, batch=1024, seed=0)
+    hit_l = hit_f = tot = cand_l = cand_f = 0
+    for sc in test:
+        eps_l = net.infer(sc.feat2).cpu().numpy()
+        assert np.all(np.isfinite(eps_l)) and np.all(eps_l >= 0.25)
+        d = mt.to_device(sc)
+        o = mt.match(d["xy1"], d["xy2"], d["F"], mt.torch.as_tensor(eps_l).cuda(), d["desc1"], d["desc2"],
+                     sc.kind, sc.dim, sc.width, sc.height, csr=True)
+        out = {k: v.cpu().numpy() for k, v in o.items()}
+        c = oracle.candidates(sc.xy1, sc.xy2, sc.F, eps_l)
+        assert np.array_equal(out["cand_offsets"], c["offsets"])
+        assert np.array_equal(out["cand_idx"], c["idx"])
+        check_matches(out, sc, ref=oracle.match_scene(sc, eps=eps_l), eps=eps_l)
+        cf = oracle.candidates(sc.xy1, sc.xy2, sc.F, 2.0)
+        for cc, acc in ((c, "l"), (cf, "f")):
+            rows = [set(cc["idx"][cc["offsets"][i]:cc["offsets"][i + 1]].tolist()) for i in sc.gt[:, 0]]
+            hits = sum(int(j in r) for r, j in zip(rows, sc.gt[:, 1]))
+            if acc == "l":
+                hit_l += hits
+                cand_l += int(cc["offsets"][-1])
+            else:
+                hit_f += hits
+                cand_f += int(cc["offsets"][-1])
+        tot += len(sc.gt)
+    rec_l, rec_f = hit_l / tot, hit_f / tot
+    q = sum(sc.m for sc in test)
+    print(f"candidate recall learned {rec_l:.4f} vs 2 px {rec_f:.4f}; candidates per query "
+          f"{cand_l / q:.2f} vs {cand_f / q:.2f}")
+    assert rec_l > 0.9, rec_l
+    assert rec_l > rec_f + 0.1, (rec_l, rec_f)
+    net.close()
