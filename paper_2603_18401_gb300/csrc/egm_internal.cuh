@@ -111,6 +111,11 @@ struct __align__(16) PairGeom {
     uint32_t start[kLevels + 1];  // first sorted position of each level
     uint32_t tab[kLevels];        // table offset (relative to t_off)
     int32_t bits[kLevels];        // bucket bits of each level
+    // extremes over the pair's queries with an FP32 view, written with atomics
+    // by the prep kernel (float bits of non-negative values): the largest
+    // aux0 (angular: r_i), the smallest aux0 and the largest aux1 (parallel:
+    // cos phi and |sin phi|), the largest |key|
+    uint32_t qa0max, qa0min, qa1max, qkabs;
 };
 
 static_assert(sizeof(PairGeom) % 16 == 0, "PairGeom is copied in 16-byte units");

@@ -69,6 +69,12 @@ __global__ void __launch_bounds__(32) geometry_kernel(Launch L) {
     G.smax[lane] = 0u;
     G.dmin[lane] = 0x7f800000u;  // +inf
     G.tmax[lane] = 0u;
+    if (lane == 0) {
+        G.qa0max = 0u;
+        G.qa0min = 0x7f800000u;
+        G.qa1max = 0u;
+        G.qkabs = 0u;
+    }
 
     // F^T e2 = 0: e2 is orthogonal to every column of F.  Lanes 0..2 form the
     // three column cross products; the largest one is the epipole.
@@ -218,6 +224,7 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
         const bool is_ref = g < L.nr;
         uint32_t group = 0xffffffffu;
         uint32_t s_bits = 0, d_bits = 0x7f800000u, t_bits = 0;
+        uint32_t qgroup = 0xffffffffu, qa0 = 0u, qa1 = 0u, qk = 0u;
         if (valid && is_ref) {
             const int p = one ? 0 : cached ? pair_of_shared(s_roffs, L.npairs, g) : pair_of(L.r_offs, L.npairs, g);
             const PairView P = pair_view(L, p);
@@ -323,6 +330,28 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
             }
             L.qrec[gq] = r;
             if (L.qbkt) L.qbkt[gq] = (uint16_t)query_bucket(G, r);
+            if (r.flags == 0u) {
+                qgroup = (uint32_t)p;
+                qa0 = __float_as_uint(r.aux0);
+                qa1 = __float_as_uint(r.aux1);
+                qk = __float_as_uint(fabsf(r.key));
+            }
+        }
+        // warp-aggregated query extremes of each pair (the single-pair
+        // stabbing kernel's per-level windows cover every query with them)
+        {
+            const uint32_t qpeers = __match_any_sync(0xffffffffu, qgroup);
+            const uint32_t a0x = __reduce_max_sync(qpeers, qa0);
+            const uint32_t a0n = __reduce_min_sync(qpeers, qgroup == 0xffffffffu ? 0x7f800000u : qa0);
+            const uint32_t a1x = __reduce_max_sync(qpeers, qa1);
+            const uint32_t kx = __reduce_max_sync(qpeers, qk);
+            if (qgroup != 0xffffffffu && lane == __ffs(qpeers) - 1) {
+                PairGeom &G = L.geom[qgroup];
+                atomicMax(&G.qa0max, a0x);
+                atomicMin(&G.qa0min, a0n);
+                atomicMax(&G.qa1max, a1x);
+                atomicMax(&G.qkabs, kx);
+            }
         }
         // warp-aggregated level statistics
         const uint32_t peers = __match_any_sync(0xffffffffu, group);

@@ -112,6 +112,15 @@ __device__ __forceinline__ void chunk_dist(int kind, uint4 a, uint4 b, uint32_t 
     }
 }
 
+__device__ __forceinline__ void top2_key(unsigned long long key, unsigned long long &b1, unsigned long long &b2) {
+    if (key < b1) {
+        b2 = b1;
+        b1 = key;
+    } else if (key < b2) {
+        b2 = key;
+    }
+}
+
 // 16-byte asynchronous copy global -> shared (no registers held while it is
 // in flight); cp_async_wait() before the data is read
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
@@ -592,6 +601,339 @@ __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mod
     }
 }
 
+// ------------------------------------------------------------ one pair, a warp per query
+//
+// The queries of one pair share nothing but the pair's tables, so in this
+// variant each warp takes one query at a time and needs no block-wide
+// phase: lane l computes the window of the pair's l-th populated level and
+// its two ranges of sorted positions (Sec. 4.2 query, split at the seam);
+// the ranges are flattened by a prefix sum over the lanes, and the warp
+// tests 32 window elements per step (each lane finds its element's range by
+// a five-step search over the lanes' prefix sums).  Candidates go to a small
+// per-warp ring in shared memory; every 32 of them are one batch of
+// descriptor distances (Sec. 4.3): G lanes read one candidate's row (16
+// bytes each, coalesced), G rounds are accumulated per lane and reduced by
+// a transposed butterfly (G - 1 shuffles for the G rounds), after which
+// each lane holds one candidate's distance.  Each lane keeps its best two
+// (distance, index) keys; four warp reductions give the query's best two.
+constexpr int kPairThreads = 128;
+constexpr int kPairWarps = kPairThreads / 32;
+constexpr int kRing = 64;  // candidate ring per warp: 32 waiting + 32 new
+
+// The window of a query in one level, from the level's half-width over all
+// of the pair's queries (key_window_span with the pair's extremes of the pad
+// arguments and of |key|, recorded by the prep kernel): a superset of each
+// query's own window, so the exact test keeps the same candidates.
+struct LevelWin {
+    float hw;      // half-width of every window in the level's key space
+    int whole;     // 1: every window covers the whole level
+    uint32_t s, e; // sorted positions of the level
+    int sh;        // key bits below the level's buckets
+};
+
+__device__ __forceinline__ LevelWin level_win(const PairGeom &G, int lv) {
+    const float a0 = G.mode == kModeAngular ? __uint_as_float(G.qa0max) : __uint_as_float(G.qa0min);
+    const KeyWin w = key_window_span(G, lv, 0.0f, 0.0f, __uint_as_float(G.qkabs), a0, __uint_as_float(G.qa1max),
+                                     false);
+    LevelWin c;
+    c.hw = w.hi;
+    c.whole = w.kind == 1 ? 1 : 0;
+    c.s = G.start[lv];
+    c.e = G.start[lv + 1];
+    c.sh = kQBits - G.bits[lv];
+    return c;
+}
+
+// The window of query r in the lane's level as bucket-table indices (the
+// kinds of WinKeys).
+__device__ __forceinline__ WinKeys level_window(const PairGeom &G, const LevelWin &c, const QueryRec &r) {
+    WinKeys k;
+    k.s = c.s;
+    k.e = c.e;
+    k.ta = k.tb = 0u;
+    k.kind = 0;
+    if (r.flags & EGM_FLAG_DEGENERATE_LINE) return k;
+    const bool full = c.whole || (r.flags & kQExactOnly) != 0;
+    const float lo = r.key - c.hw, hi = r.key + c.hw;
+    const bool low = G.mode == kModeAngular && lo < -kHalfPiF;
+    const bool high = G.mode == kModeAngular && hi >= kHalfPiF;
+    if (full || (low && high)) {
+        k.kind = 1;
+    } else if (low || high) {
+        // across the seam of the [-pi/2, pi/2) domain: [ta, end) and [start, tb)
+        k.ta = qmap(low ? lo + kPiF : lo, G.kmin, G.kscale) >> c.sh;
+        k.tb = (qmap(low ? hi : hi - kPiF, G.kmin, G.kscale) >> c.sh) + 1;
+        k.kind = 3;
+    } else {
+        k.ta = qmap(lo, G.kmin, G.kscale) >> c.sh;
+        k.tb = (qmap(hi, G.kmin, G.kscale) >> c.sh) + 1;
+        k.kind = 2;
+    }
+    return k;
+}
+
+// The brute force's FP64 decision for one (query, reference) pair of a
+// single-pair call, from plain pointers.
+static __device__ __noinline__ bool exact_pair_p(const double *F, const double *xy1, const double *xy2,
+                                                 const double *eps2, double eps_scalar, int64_t i, uint32_t j) {
+    double a, b, c;
+    exact_line(F, xy1[2 * i], xy1[2 * i + 1], a, b, c);
+    const double N = exact_norm(a, b);
+    const double eps = eps2 ? eps2[j] : eps_scalar;
+    return exact_member(a, b, c, N, xy2[2 * (int64_t)j], xy2[2 * (int64_t)j + 1], eps);
+}
+
+template <int KIND, int G, int MODE>
+__global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
+    static_assert(G >= 1 && G <= 16 && (G & (G - 1)) == 0, "lanes per descriptor row");
+    constexpr int kPerRound = 32 / G;  // candidates per round of loads
+    constexpr bool kDesc = MODE != 1;  // descriptor distances (the launcher checks that rows exist)
+    pdl_begin();
+    __shared__ __align__(16) PairGeom sg;
+    __shared__ int32_t slv[kLevels];
+    __shared__ int32_t snlev;
+    __shared__ uint32_t ring[kPairWarps][kRing];
+    __shared__ LevelWin slc[kLevels];
+    // the next query's record and descriptor row, copied ahead (double-buffered per warp)
+    __shared__ __align__(16) QueryRec qbuf[kPairWarps][2];
+    __shared__ __align__(16) uint4 dbuf[kPairWarps][2][G];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int k = tid; k < (int)(sizeof(PairGeom) / 16); k += kPairThreads)
+        reinterpret_cast<uint4 *>(&sg)[k] = __ldg(reinterpret_cast<const uint4 *>(L.geom) + k);
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t nz = __ballot_sync(0xffffffffu, sg.cnt[lane] > 0);
+        const int idx = __popc(nz & lt);
+        if (nz & (1u << lane)) {
+            slv[idx] = lane;
+            slc[idx] = level_win(sg, lane);
+        }
+        if (lane == 0) snlev = __popc(nz);
+    }
+    __syncthreads();
+    // the pair's fields, by value from the launch parameters
+    const double *Fp = L.inl.F, *xy1 = L.inl.xy1, *xy2 = L.inl.xy2, *eps2 = L.inl.eps2;
+    const double eps_scalar = L.inl.eps_scalar;
+    const int64_t q_off = L.inl.q_off;
+    const int nlev = snlev;
+    const bool haslev = lane < nlev;
+    const int lvl = haslev ? slv[lane] : 0;
+    const uint32_t *T = L.tab + L.inl.t_off + sg.tab[lvl];
+    const float4 *recb = L.rec + L.inl.r_off;
+    uint32_t *rg = ring[warp];
+    const int sub = lane % G, grp = lane / G;
+    const uint4 *d1 = reinterpret_cast<const uint4 *>(L.inl.desc1);
+    const uint4 *d2 = reinterpret_cast<const uint4 *>(L.inl.desc2);
+    const bool write_rows = MODE == 2 && L.cand_offsets[L.nq] <= L.cand_capacity;
+    // result outputs of lanes 0-3 (32-bit words) and 4 (flags)
+    void *outp = lane == 0 ? (void *)L.best : lane == 1 ? (void *)L.second : lane == 2 ? (void *)L.best_d
+               : lane == 3 ? (void *)L.second_d : lane == 4 ? (void *)L.flags : nullptr;
+    const int64_t rnum = L.ratio_num, rden = L.ratio_den;
+    uint32_t nwin = 0, ncand = 0, nexact = 0;
+    const int64_t nwarps = (int64_t)gridDim.x * kPairWarps;
+    int64_t q = (int64_t)blockIdx.x * kPairWarps + warp;
+    // copies of a query's record (3 lanes) and descriptor row (G lanes) into buffer b
+    auto fetch = [&](int64_t qq, int b) {
+        if (lane < 3)
+            cp_async16(reinterpret_cast<uint4 *>(&qbuf[warp][b]) + lane, reinterpret_cast<const uint4 *>(L.qrec + qq) + lane);
+        if (kDesc && lane >= 8 && lane < 8 + G) cp_async16(&dbuf[warp][b][lane - 8], d1 + (qq - q_off) * G + (lane - 8));
+    };
+    if (q < L.nq) fetch(q, 0);
+    for (int it = 0; q < L.nq; q += nwarps, it++) {
+        const int64_t qi = q - q_off;
+        cp_async_wait();
+        __syncwarp();
+        const QueryRec rq = qbuf[warp][it & 1];
+        uint4 qdq = make_uint4(0u, 0u, 0u, 0u);
+        if (kDesc) qdq = dbuf[warp][it & 1][sub];
+        __syncwarp();
+        if (q + nwarps < L.nq) fetch(q + nwarps, (it + 1) & 1);
+        // the window of this lane's level as (at most) two ranges of sorted positions
+        Window w;
+        w.b0 = w.len0 = w.b1 = w.len1 = 0u;
+        if (haslev) {
+            const WinKeys wk = level_window(sg, slc[lane], rq);
+            uint32_t a = 0, b = 0;
+            if (wk.kind >= 2) {
+                a = __ldg(T + wk.ta);
+                b = __ldg(T + wk.tb);
+            }
+            w = window_ranges(wk, a, b);
+        }
+        const uint32_t tl = w.len0 + w.len1;
+        uint32_t incl = tl;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += x;
+        }
+        const uint32_t p0 = incl - tl;  // first flattened element of this lane's ranges
+        const uint32_t E = __shfl_sync(0xffffffffu, incl, 31);
+        const bool exact_only = (rq.flags & kQExactOnly) != 0;
+        uint32_t count = 0, done = 0;  // candidates found / already in a distance batch (warp-uniform)
+        unsigned long long k1 = ~0ull, k2 = ~0ull;
+
+        // one batch of nb <= 32 candidates from the ring, starting at `start`
+        auto batch = [&](uint32_t start, uint32_t nb) {
+            __syncwarp();
+            uint32_t acc[G];
+#pragma unroll
+            for (int u = 0; u < G; u++) acc[u] = 0u;
+#pragma unroll
+            for (int u = 0; u < G; u++) {
+                if ((uint32_t)(u * kPerRound) >= nb) break;
+                const uint32_t c = (uint32_t)(u * kPerRound + grp);
+                if (c < nb) {
+                    const uint32_t jj = rg[(start + c) % kRing];
+                    const uint4 rv = __ldg(d2 + (int64_t)jj * G + sub);
+                    float unused = 0.0f;
+                    chunk_dist<KIND>(KIND, qdq, rv, acc[u], unused);
+                }
+            }
+            // transposed butterfly: after the step over lane bit h a lane keeps
+            // the rounds whose bit h equals its own, summed with its partner's
+#pragma unroll
+            for (int h = G / 2; h >= 1; h >>= 1) {
+                const bool up = (sub & h) != 0;
+#pragma unroll
+                for (int k = 0; k < h; k++) {
+                    const uint32_t send = up ? acc[k] : acc[k + h];
+                    const uint32_t keep = up ? acc[k + h] : acc[k];
+                    acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+                }
+            }
+            // lane (grp, sub) now holds the full distance of round sub
+            const uint32_t c = (uint32_t)(sub * kPerRound + grp);
+            if (c < nb) top2_key(((unsigned long long)acc[0] << 32) | rg[(start + c) % kRing], k1, k2);
+            __syncwarp();
+        };
+
+        for (uint32_t base = 0; base < E; base += 32) {
+            const uint32_t e = base + (uint32_t)lane;
+            // the lane whose ranges hold element e: the last one whose first
+            // element is <= e (it has elements, since the next one starts after e)
+            int o = 0;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1)
+                if (__shfl_sync(0xffffffffu, p0, o + st) <= e) o += st;
+            const uint32_t ob0 = __shfl_sync(0xffffffffu, w.b0, o), ol0 = __shfl_sync(0xffffffffu, w.len0, o);
+            const uint32_t ob1 = __shfl_sync(0xffffffffu, w.b1, o), op0 = __shfl_sync(0xffffffffu, p0, o);
+            bool cand = false;
+            uint32_t j = 0;
+            if (e < E) {
+                const uint32_t off = e - op0;
+                const float4 rc = __ldg(recb + (off < ol0 ? ob0 + off : ob1 + (off - ol0)));
+                j = __float_as_uint(rc.w);
+                nwin++;
+                bool exact = exact_only;
+                if (!exact) {
+                    const float x = rc.x, y = rc.y, ee = rc.z;
+                    const float d = fabsf(fmaf(rq.A, x, fmaf(rq.B, y, rq.C)));
+                    const float Sm = fmaf(fabsf(rq.A), fabsf(x), fmaf(fabsf(rq.B), fabsf(y), fabsf(rq.C)));
+                    // FP32 rounding (16u S), the FP32 tolerance (2u eps) and the
+                    // distance between this line and the brute force's FP64 line
+                    const float lerr = fmaf(rq.E1, fabsf(x) + fabsf(y) + 2.0f * ee, rq.E0);
+                    const float bound = fmaf(9.6e-7f, Sm, fmaf(1.2e-7f, ee, lerr + 1e-9f));
+                    cand = d <= ee - bound;
+                    exact = !cand && !(d > ee + bound);
+                }
+                if (exact) {
+                    // FP32 inconclusive: the brute-force FP64 expression decides
+                    cand = exact_pair_p(Fp, xy1, xy2, eps2, eps_scalar, qi, j);
+                    nexact++;
+                }
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, cand);
+            if (cand) {
+                const uint32_t slot = count + (uint32_t)__popc(m & lt);
+                if (MODE == 2 && write_rows) L.cand_idx[L.cand_offsets[q] + slot] = (int32_t)j;
+                if (kDesc) rg[slot % kRing] = j;
+            }
+            count += (uint32_t)__popc(m);
+            if (kDesc && count - done >= 32u) {
+                batch(done, 32u);
+                done += 32u;
+            }
+        }
+        if (kDesc && count > done) batch(done, count - done);
+        ncand += count;
+        if (MODE == 1) {
+            if (lane == 0) L.qcount[q] = count;
+            continue;
+        }
+        // the query's best two over the lanes' best two: (distance, index) minima
+        const uint32_t dk1 = (uint32_t)(k1 >> 32), jk1 = (uint32_t)k1;
+        const uint32_t md = __reduce_min_sync(0xffffffffu, dk1);
+        const uint32_t mj = __reduce_min_sync(0xffffffffu, dk1 == md ? jk1 : 0xffffffffu);
+        const unsigned long long c2 = (dk1 == md && jk1 == mj) ? k2 : k1;
+        const uint32_t dk2 = (uint32_t)(c2 >> 32), jk2 = (uint32_t)c2;
+        const uint32_t sd = __reduce_min_sync(0xffffffffu, dk2);
+        const uint32_t sj = __reduce_min_sync(0xffffffffu, dk2 == sd ? jk2 : 0xffffffffu);
+        // outputs as store_match writes them (integer distances; Sec. 5.1 ratio
+        // test in exact integer form), one field per lane 0-4
+        uint32_t fl = rq.flags & EGM_FLAG_DEGENERATE_LINE;
+        const bool has1 = md != 0xffffffffu || mj != 0xffffffffu;
+        const bool has2 = sd != 0xffffffffu || sj != 0xffffffffu;
+        if (has1) {
+            fl |= EGM_FLAG_HAS_BEST;
+            bool pass;
+            if (!has2) {
+                fl |= EGM_FLAG_NO_SECOND;
+                pass = true;
+            } else if (KIND == EGM_DESC_U8_L2) {
+                pass = (long long)md * rden * rden < (long long)sd * rnum * rnum;
+            } else {
+                pass = (long long)md * rden < (long long)sd * rnum;
+            }
+            if (pass) fl |= EGM_FLAG_RATIO_PASS;
+        }
+        const uint32_t word = lane == 0 ? (has1 ? mj : 0xffffffffu)
+                            : lane == 1 ? (has2 ? sj : 0xffffffffu)
+                            : lane == 2 ? __float_as_uint(has1 ? (float)md : INFINITY)
+                                        : __float_as_uint(has2 ? (float)sd : INFINITY);
+        if (outp) {
+            if (lane < 4) static_cast<uint32_t *>(outp)[q] = word;
+            else static_cast<uint8_t *>(outp)[q] = (uint8_t)fl;
+        }
+    }
+    if (L.counters) {
+        const uint32_t a = __reduce_add_sync(0xffffffffu, nwin);
+        const uint32_t b = __reduce_add_sync(0xffffffffu, lane == 0 ? ncand : 0u);
+        const uint32_t c = __reduce_add_sync(0xffffffffu, nexact);
+        if (lane == 0) {
+            atomicAdd(L.counters + 2, (unsigned long long)a);
+            atomicAdd(L.counters + 3, (unsigned long long)b);
+            atomicAdd(L.counters + 4, (unsigned long long)c);
+        }
+    }
+}
+
+template <int KIND, int G, int MODE>
+cudaError_t launch_pair_mode(const Launch &L, int sms, cudaStream_t s) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stab_pair_kernel<KIND, G, MODE>,
+                                                                      kPairThreads, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+    }
+    int64_t blocks = (L.nq + kPairWarps - 1) / kPairWarps;
+    blocks = std::min<int64_t>(blocks, (int64_t)per_sm * sms);
+    return launch_pdl(stab_pair_kernel<KIND, G, MODE>, dim3((unsigned)blocks), dim3(kPairThreads), 0, s, L);
+}
+
+template <int KIND, int G>
+cudaError_t launch_pair(const Launch &L, int mode, int sms, cudaStream_t s) {
+    // without descriptors only candidate lists are written (mode 2 then counts as mode 1 for
+    // the distances: the kernel's mode-2 path also needs rows)
+    switch (mode) {
+        case 0: return launch_pair_mode<KIND, G, 0>(L, sms, s);
+        case 1: return launch_pair_mode<KIND, G, 1>(L, sms, s);
+        default: return launch_pair_mode<KIND, G, 2>(L, sms, s);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_stab(const Launch &L, int mode, cudaStream_t s) {
@@ -603,6 +945,20 @@ cudaError_t launch_stab(const Launch &L, int mode, cudaStream_t s) {
     // 256-bit): the uniform variant
     const int rb = L.inl_use ? L.inl.row_bytes : 0;
     const bool one = L.npairs == 1 && L.inl_use && rb >= 16 && rb <= kDescCache && (rb & (rb - 1)) == 0;
+    if (one && (L.kind == EGM_DESC_U8_L2 || L.kind == EGM_DESC_BIN)) {
+        // one pair: a warp per query
+        int sms = 0;
+        cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+        if (e != cudaSuccess) return e;
+        const bool u8 = L.kind == EGM_DESC_U8_L2;
+        switch (rb >> 4) {
+            case 1: return u8 ? launch_pair<EGM_DESC_U8_L2, 1>(L, mode, sms, s) : launch_pair<EGM_DESC_BIN, 1>(L, mode, sms, s);
+            case 2: return u8 ? launch_pair<EGM_DESC_U8_L2, 2>(L, mode, sms, s) : launch_pair<EGM_DESC_BIN, 2>(L, mode, sms, s);
+            case 4: return u8 ? launch_pair<EGM_DESC_U8_L2, 4>(L, mode, sms, s) : launch_pair<EGM_DESC_BIN, 4>(L, mode, sms, s);
+            case 8: return u8 ? launch_pair<EGM_DESC_U8_L2, 8>(L, mode, sms, s) : launch_pair<EGM_DESC_BIN, 8>(L, mode, sms, s);
+            default: return u8 ? launch_pair<EGM_DESC_U8_L2, 16>(L, mode, sms, s) : launch_pair<EGM_DESC_BIN, 16>(L, mode, sms, s);
+        }
+    }
     switch (L.kind) {
         case EGM_DESC_U8_L2:
             return one ? launch_pdl(stab_kernel<EGM_DESC_U8_L2, true>, g, b, 0, s, L, mode)
