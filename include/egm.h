@@ -262,7 +262,7 @@ egm_status egm_match_batch_host(egm_ctx *ctx, const egm_pair *pairs, int32_t npa
  *
  * It takes no egm_ctx and calls no cudaMalloc, cudaFree, cudaMallocHost or
  * other allocating routine.  All scratch lives in one fixed file-scope device
- * array of about 2.2 MB that every GPU loading libegm.so keeps until the
+ * array of about 2.4 MB that every GPU loading libegm.so keeps until the
  * process exits; it holds pairs of at most 16384 keypoints per image (m and
  * n); larger pairs are rejected with EGM_ERR_CAPACITY before any work.
  *   pair, out  as for egm_match_pair (device pointers)

@@ -46,13 +46,13 @@ T *as(DevBuf &b) { return reinterpret_cast<T *>(b.ptr); }
 
 // Device scratch of one pipeline instance (a context, or a captured graph).
 struct Scratch {
-    DevBuf pairs, geom, offs, keys, rec, tab, curs, qrec, qcount, scan, longlist, small, counters, blkpair, band;
+    DevBuf pairs, geom, offs, keys, rec, rtmp, tab, curs, qrec, qcount, scan, longlist, small, counters, blkpair, band;
     // the pair table, offsets and geometry are double-buffered: call k uses
     // half k mod 2, so that its geometry kernel can write while call k - 1's
     // last kernel still reads the other half
     int parity = 0;
     void release() {
-        DevBuf *b[] = {&pairs, &geom, &offs, &keys, &rec, &tab, &curs, &qrec, &qcount, &scan, &longlist, &small,
+        DevBuf *b[] = {&pairs, &geom, &offs, &keys, &rec, &rtmp, &tab, &curs, &qrec, &qcount, &scan, &longlist, &small,
                        &counters, &blkpair, &band};
         for (DevBuf *x : b) {
             if (x->ptr) cudaFree(x->ptr);
@@ -309,6 +309,7 @@ cudaError_t reserve(Scratch &c_, int64_t nq, int64_t nr, int64_t ntab, int npair
     if ((e = grow(c->keys, sizeof(uint32_t) * 6 * (size_t)std::max<int64_t>(nr, 1))) != cudaSuccess) return e;
     // 32 records of padding: bulk copies of a 32-row box may run past the last row
     if ((e = grow(c->rec, sizeof(float4) * (size_t)(nr + 32))) != cudaSuccess) return e;
+    if ((e = grow(c->rtmp, sizeof(float4) * (size_t)std::max<int64_t>(nr, 1))) != cudaSuccess) return e;
     if ((e = grow(c->tab, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntab, 1))) != cudaSuccess) return e;
     if ((e = grow(c->curs, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntab, 1))) != cudaSuccess) return e;
     if ((e = grow(c->qrec, sizeof(QueryRec) * (size_t)std::max<int64_t>(nq, 1))) != cudaSuccess) return e;
@@ -351,6 +352,7 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
     L.key_c = k + 4 * nr;
     L.val_c = k + 5 * nr;
     L.rec = as<float4>(c->rec);
+    L.rtmp = as<float4>(c->rtmp);
     L.tab = as<uint32_t>(c->tab);
     L.ntab = pl.ntab;
     L.curs = as<uint32_t>(c->curs);

@@ -116,6 +116,7 @@ struct __align__(16) PairGeom {
     // aux0 (angular: r_i), the smallest aux0 and the largest aux1 (parallel:
     // cos phi and |sin phi|), the largest |key|
     uint32_t qa0max, qa0min, qa1max, qkabs;
+    float cxf, cyf, xef, yef;     // cx, cy, xe, ye rounded to FP32 (for error terms)
 };
 
 static_assert(sizeof(PairGeom) % 16 == 0, "PairGeom is copied in 16-byte units");
@@ -148,6 +149,8 @@ struct Launch {
     const int64_t *r_offs;        // npairs + 1
     uint32_t *key_a, *val_a, *key_b, *val_b, *key_c, *val_c;
     float4 *rec;
+    float4 *rtmp;                 // per reference in input order: its record (x - cx, y - cy, eps, index),
+                                  //   written by the prep kernel, moved to its bucket by the sort
     uint32_t *tab;
     int64_t ntab;                 // table entries of the whole call (zeroed by the prep kernel)
     uint32_t *curs;               // bucket fill cursors (a copy of tab while the records are placed)
@@ -285,6 +288,11 @@ __device__ __forceinline__ uint32_t qmap(float k, float kmin, float kscale) {
     t = fminf(fmaxf(t, 0.0f), (float)kQMax);
     return (uint32_t)t;
 }
+
+// FP64 classification on the integer pipes (the FP64 pipe is scarce on
+// GB300): finite (exponent not all ones) and strictly positive.
+__device__ __forceinline__ bool finite64(double v) { return (__double2hiint(v) & 0x7ff00000) != 0x7ff00000; }
+__device__ __forceinline__ bool positive64(double v) { return __double_as_longlong(v) > 0; }
 
 // The oracle's FP64 evaluation order, with one rounding per operation.
 __device__ __forceinline__ void exact_line(const double *F, double x, double y, double &a, double &b,

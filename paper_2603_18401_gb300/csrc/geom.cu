@@ -173,6 +173,10 @@ __global__ void __launch_bounds__(32) geometry_kernel(Launch L) {
     G.ye = ye;
     G.cx = cx;
     G.cy = cy;
+    G.cxf = (float)cx;
+    G.cyf = (float)cy;
+    G.xef = (float)xe;
+    G.yef = (float)ye;
     G.ux = ux;
     G.uy = uy;
     G.de = de;
@@ -232,10 +236,12 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
             const int64_t j = g - P.r_off;
             const double x = P.xy2[2 * j], y = P.xy2[2 * j + 1];
             const double eps = P.eps2 ? P.eps2[j] : P.eps_scalar;
-            if (!(isfinite(x) && isfinite(y) && isfinite(eps))) set_status(L.status, kStNan);
-            else if (!(eps > 0.0)) set_status(L.status, kStArg);
+            if (!(finite64(x) && finite64(y) && finite64(eps))) set_status(L.status, kStNan);
+            else if (!positive64(eps)) set_status(L.status, kStArg);
             const float epsf = (float)eps;
             const float xf = (float)(x - G.cx), yf = (float)(y - G.cy);
+            // the reference's FP32 record, placed in its bucket by the sort
+            L.rtmp[g] = make_float4(xf, yf, epsf, __uint_as_float((uint32_t)j));
             const float rr = hypotf(xf, yf);
             int level;
             float key;
@@ -264,7 +270,6 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
             if (!isfinite(key)) key = 0.0f;
             const uint32_t q = qmap(key, G.kmin, G.kscale);
             L.key_a[g] = ((uint32_t)level << kQBits) | q;
-            L.val_a[g] = (uint32_t)j;
             group = (uint32_t)p * kLevels + (uint32_t)level;
         } else if (valid) {
             const int64_t gq = g - L.nr;
@@ -279,7 +284,7 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
             r.pad[0] = r.pad[1] = 0;
             if (gq % kStabQB == 0) L.blkpair[gq / kStabQB] = p;
             r.A = r.B = r.C = r.key = r.aux0 = r.aux1 = r.E0 = r.E1 = 0.0f;
-            if (!(isfinite(x1) && isfinite(y1))) set_status(L.status, kStNan);
+            if (!(finite64(x1) && finite64(y1))) set_status(L.status, kStNan);
             const double *F = P.F;
             // the line with FMAs: within a few ulps of its terms of the exact line
             const double a = fma(F[0], x1, fma(F[1], y1, F[2]));
@@ -291,7 +296,7 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
             const float tc = fabsf(G.Ff[6]) * x1f + fabsf(G.Ff[7]) * y1f + fabsf(G.Ff[8]);
             const float af = (float)a, bf = (float)b;
             const float N = sqrtf(af * af + bf * bf);
-            const bool usable = isfinite(N) && isfinite(c) && N > 1e-6f * (ta + tb) && N > 1e-30f;
+            const bool usable = isfinite(N) && finite64(c) && N > 1e-6f * (ta + tb) && N > 1e-30f;
             if (!usable) {
                 // tiny or overflowing line: decide degeneracy exactly as the
                 // brute force (a^2 + b^2 == 0 in its evaluation order)
@@ -305,12 +310,12 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
                 float A = af * invN, B = bf * invN, C = (float)Cn * invN;
                 // the oracle's line differs from (a, b, c) by at most ~2 ulps of the terms
                 const float da = 8.9e-16f * ta, db = 8.9e-16f * tb, dc = 8.9e-16f * tc;
-                r.E0 = (da * (float)G.cx + db * (float)G.cy + dc) * invN * 1.001f;
+                r.E0 = (da * G.cxf + db * G.cyf + dc) * invN * 1.001f;
                 r.E1 = (da + db) * invN * 1.001f;
                 if (G.mode == kModeAngular) {
                     // distance of the computed epipole from the line, rounded up
                     const double rn = fma(a, G.xe, fma(b, G.ye, c));
-                    const float xe = fabsf((float)G.xe), ye = fabsf((float)G.ye);
+                    const float xe = fabsf(G.xef), ye = fabsf(G.yef);
                     const float rerr = 2.0e-15f * (ta * xe + tb * ye + tc);
                     r.aux0 = (fabsf((float)rn) + rerr) * invN * 1.00001f + 1e-12f;
                     // line direction (B, -A) in the frame of u, reduced mod pi

@@ -218,8 +218,9 @@ __device__ void block_radix_sort(SortSmem &S, const uint32_t *ik, const uint32_t
 //                         at once (the first position of each bucket; in each
 //                         level's extra last entry, the level's end), and a
 //                         copy as fill cursors; then every reference takes
-//                         the next position of its bucket and writes its FP32
-//                         record (x - cx, y - cy, eps, index) there.
+//                         the next position of its bucket and moves its FP32
+//                         record (x - cx, y - cy, eps, index), written by the
+//                         prep kernel, there.
 // The order within a bucket follows the atomics and is not fixed; everything
 // downstream depends only on bucket order (ties between candidates are broken
 // by index).
@@ -281,7 +282,7 @@ __global__ void __cluster_dims__(kScanCtas, 1, 1) __launch_bounds__(kScanThreads
     const int64_t b = P.r_off;
     const int stride = kScanCtas * kScanThreads;
     uint32_t key[kPre];
-    double x[kPre], y[kPre], ep[kPre];
+    float4 rv[kPre];
     auto load_refs = [&](int e0) {
 #pragma unroll
         for (int k = 0; k < kPre; k++) {
@@ -289,9 +290,7 @@ __global__ void __cluster_dims__(kScanCtas, 1, 1) __launch_bounds__(kScanThreads
             key[k] = 0xffffffffu;
             if (e < P.n) {
                 key[k] = L.key_a[b + e];
-                x[k] = P.xy2[2 * (int64_t)e];
-                y[k] = P.xy2[2 * (int64_t)e + 1];
-                ep[k] = P.eps2 ? P.eps2[e] : P.eps_scalar;
+                rv[k] = L.rtmp[b + e];
             }
         }
     };
@@ -361,8 +360,7 @@ __global__ void __cluster_dims__(kScanCtas, 1, 1) __launch_bounds__(kScanThreads
             if (key[k] == 0xffffffffu) continue;
             const int e = e0 + k * stride;
             const uint32_t pos = atomicAdd(L.curs + P.t_off + bucket_slot(G, key[k]), 1u);
-            L.rec[b + pos] = make_float4((float)(x[k] - G.cx), (float)(y[k] - G.cy), (float)ep[k],
-                                         __uint_as_float((uint32_t)e));
+            L.rec[b + pos] = rv[k];
         }
     }
     cluster.sync();  // no block leaves while another may still read its shared memory

@@ -34,7 +34,8 @@ constexpr size_t kOffGeom = align256(kOffPairs + sizeof(PairDesc));
 constexpr size_t kOffOffs = align256(kOffGeom + sizeof(PairGeom));
 constexpr size_t kOffKeys = align256(kOffOffs + 4 * sizeof(int64_t));
 constexpr size_t kOffRec = align256(kOffKeys + 6 * sizeof(uint32_t) * N);
-constexpr size_t kOffTab = align256(kOffRec + sizeof(float4) * N);
+constexpr size_t kOffRtmp = align256(kOffRec + sizeof(float4) * N);
+constexpr size_t kOffTab = align256(kOffRtmp + sizeof(float4) * N);
 constexpr int64_t kTabCap = 4 * N + 2 * kLevels + 32;
 constexpr size_t kOffCurs = align256(kOffTab + sizeof(uint32_t) * kTabCap);
 constexpr size_t kOffQrec = align256(kOffCurs + sizeof(uint32_t) * kTabCap);
@@ -169,6 +170,7 @@ extern "C" egm_status egm_match_pair_static(const egm_pair *P, const egm_out *ou
     L.key_c = k + 4 * nr;
     L.val_c = k + 5 * nr;
     L.rec = reinterpret_cast<float4 *>(base + kOffRec);
+    L.rtmp = reinterpret_cast<float4 *>(base + kOffRtmp);
     L.tab = reinterpret_cast<uint32_t *>(base + kOffTab);
     L.ntab = pd.t_cap;
     L.curs = reinterpret_cast<uint32_t *>(base + kOffCurs);
