@@ -285,7 +285,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 // Banded-form scratch: query permutation, packed operand rows, norms (padded
 // for the aligned 16-byte bulk copies that read past a pair's last row).
 struct BandLayout {
-    size_t qperm, descA, descB, qbkt, qsrt, qscale, rnorm, total;
+    size_t qperm, descA, descB, qbkt, qsrt, qscale, rnorm, rbin, total;
     BandLayout(int64_t nq, int64_t nr) {
         const size_t rb = (size_t)band_row_bytes();
         qperm = 0;
@@ -295,7 +295,9 @@ struct BandLayout {
         qsrt = qbkt + align256(sizeof(uint16_t) * (size_t)std::max<int64_t>(nq, 1));
         qscale = qsrt + align256(sizeof(QueryRec) * (size_t)std::max<int64_t>(nq, 1));
         rnorm = qscale + align256(sizeof(float) * (size_t)std::max<int64_t>(nq, 1));
-        total = rnorm + align256(sizeof(float4) * (size_t)(nr + 64));
+        rbin = rnorm + align256(sizeof(float4) * (size_t)(nr + 64));
+        // 32 rows of padding: bulk copies of a 32-row box may run past the last row
+        total = rbin + align256(32 * (size_t)(nr + 64));
     }
 };
 
@@ -379,6 +381,7 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
         L.qbkt = reinterpret_cast<uint16_t *>(b + bl.qbkt);
         L.qsrt = reinterpret_cast<QueryRec *>(b + bl.qsrt);
         L.rnorm = reinterpret_cast<float4 *>(b + bl.rnorm);
+        L.rbin = b + bl.rbin;
         L.qscale = reinterpret_cast<float *>(b + bl.qscale);
         L.fp8 = prm.float_pass == EGM_FLOAT_PASS_FP8;
         L.probe = prm.timeout_check;

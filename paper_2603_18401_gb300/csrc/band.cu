@@ -14,9 +14,11 @@
 //   pack_kernel        descriptor rows of the sorted references and queries
 //                      as 256-byte tensor-core operands, with their norms:
 //                        u8 (128 values)  -> BF16, exact (integers < 2^8)
-//                        binary (256 bit) -> E4M3 0 / 1 per bit, exact
 //                        float (128 FP32) -> BF16 (nearest), with the norm of
 //                          the rounded row and the rounding error |x - bf16(x)|
+//                      binary (256-bit) reference rows are copied in sorted
+//                      order as they are (32 bytes): their Hamming distances
+//                      are popcounts on the CUDA cores
 //   band_kernel        persistent; one tile of 128 sorted queries at a time.
 //                      Warps 0-3 (one thread per query) build the tile's band
 //                      from the hull of their windows; warp 4 issues TMA loads
@@ -123,16 +125,11 @@ __global__ void __launch_bounds__(kQSortThreads) query_sort_kernel(Launch L) {
 
 // ------------------------------------------------------------ packing
 constexpr int kRowB = 256;  // packed operand row: 128 BF16 or 256 E4M3 values
+constexpr int kBinRowB = 32;  // binary row (256 bits), kept as it is
 
 __device__ __forceinline__ uint32_t bf16_pair(uint32_t lo, uint32_t hi) {
     // bytes 0..255 are exact in FP32 and their BF16 is the top half of the FP32 word
     return (__float_as_uint((float)lo) >> 16) | (__float_as_uint((float)hi) & 0xffff0000u);
-}
-
-__device__ __forceinline__ uint32_t e4m3_nibble(uint32_t n) {
-    // four bits -> four bytes of E4M3 1.0 (0x38) or 0
-    const uint32_t spread = (n & 1u) | ((n & 2u) << 7) | ((n & 4u) << 14) | ((n & 8u) << 21);
-    return spread * 0x38u;
 }
 
 // 8 threads per row; thread part t writes output bytes [32 t, 32 t + 32).
@@ -158,6 +155,7 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
         float amax = 0.0f;               //   and their largest magnitude
         uint4 o0 = make_uint4(0, 0, 0, 0), o1 = o0, qr = o0;
         uint8_t *dst = nullptr;
+        int rowkind = 0;                 // 0: 256-byte operand row at dst; 1: binary row at dst; 2: none
         if (valid) {
             const int64_t g = is_ref ? g0 : g0 - L.nr;
             const int p = cached ? pair_of_shared(is_ref ? s_roffs : s_qoffs, L.npairs, g)
@@ -222,13 +220,14 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
                 }
                 o0 = make_uint4(out[0], out[1], out[2], out[3]);
                 o1 = make_uint4(out[4], out[5], out[6], out[7]);
+            } else if (is_ref) {
+                // binary: the row itself (32 bytes) in sorted order; Hamming
+                // distances are popcounts in the band kernel, no operand row
+                if (part < 2) o0 = __ldg(reinterpret_cast<const uint4 *>(src) + part);
+                dst = L.rbin + g * kBinRowB;
+                rowkind = 1;
             } else {
-                const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(src) + part);
-                nrm = __popc(w);
-                o0 = make_uint4(e4m3_nibble(w & 15u), e4m3_nibble((w >> 4) & 15u), e4m3_nibble((w >> 8) & 15u),
-                                e4m3_nibble((w >> 12) & 15u));
-                o1 = make_uint4(e4m3_nibble((w >> 16) & 15u), e4m3_nibble((w >> 20) & 15u),
-                                e4m3_nibble((w >> 24) & 15u), e4m3_nibble(w >> 28));
+                rowkind = 2;  // binary query: its sorted record only
             }
         }
         // FP8 pass, step 2: the row's scale s = max |x| / 448 (E4M3's largest
@@ -265,7 +264,10 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
         const float norm = isf ? fnrm : (float)nrm;
         const float err = isf ? sqrtf(ferr) * 1.0001f + 1e-30f : 0.0f;
         if (valid) {
-            if (F8 && isf8) {
+            if (rowkind == 1) {
+                if (part < 2) reinterpret_cast<uint4 *>(dst)[part] = o0;
+            } else if (rowkind == 2) {
+            } else if (F8 && isf8) {
                 // 16 bytes per thread: bytes [16 part, 16 part + 16), zeros above 128
                 reinterpret_cast<uint4 *>(dst)[part] = o0;
                 reinterpret_cast<uint4 *>(dst)[8 + part] = make_uint4(0u, 0u, 0u, 0u);
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
                 reinterpret_cast<uint4 *>(dst)[2 * part + 1] = o1;
             }
             if (is_ref) {
-                if (part == 0) L.rnorm[g0] = make_float4(norm, err, scale, 0.0f);
+                if (part == 0 && rowkind == 0) L.rnorm[g0] = make_float4(norm, err, scale, 0.0f);
             } else if (part < 3) {
                 if (part == 0) L.qscale[g0 - L.nr] = scale;
                 // sorted query record; the padding carries the query index and the
@@ -545,7 +547,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         atomicOr(L.status, kStTimeout);
         return false;
     };
-    uint32_t seq = 0, aload = 0;
+    uint32_t seq = 0;
     unsigned long long nwin = 0, ncand = 0, nexact = 0;
     // phases the control thread armed on each barrier (copies and MMAs issued):
     // after a failed wait, the CTA lets them complete before it leaves
@@ -585,11 +587,20 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         const float qn = __uint_as_float(r.pad[1]);
         const float qerr = __uint_as_float((uint32_t)r.pair);  // float rows: |q - q~|
         const float qs = FLT && qv ? L.qscale[q_off + t0 + tid] : 1.0f;  // row scale of the FP8 pass
-        if (ctl) {
+        // binary pairs: Hamming distances by popcount, no operand rows
+        const bool pop = __ldg(&L.pairs[p].kind) == EGM_DESC_BIN;
+        if (ctl && !pop) {
             tc::mbar_arrive_expect_tx(&S.afull, 2 * kTM * 128);
             armA++;
             tc::tma_load_2d(S.A[0], &tmA, 0, (int32_t)(q_off + t0), &S.afull);
             tc::tma_load_2d(S.A[1], &tmA, 128, (int32_t)(q_off + t0), &S.afull);
+        }
+        // a binary query's row, in the idle query-tile buffer (its thread's slot)
+        uint4 *qbrow = reinterpret_cast<uint4 *>(S.A[0] + tid * kBinRowB);
+        if (pop && qv) {
+            const uint4 *qrow = reinterpret_cast<const uint4 *>(L.pairs[p].desc1 + (int64_t)qi * kBinRowB);
+            qbrow[0] = __ldg(qrow);
+            qbrow[1] = __ldg(qrow + 1);
         }
         const bool newpair = p != S.gpair;
         __syncthreads();
@@ -727,6 +738,13 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 const uint32_t sq = seq + (uint32_t)c, st = sq & 1u, use = sq >> 1;
                 if (c >= 2 && !wait(&S.sfree[st], (use - 1) & 1u)) return;
                 const int nb = min(kCB, nbox - c * kCB);
+                if (pop) {
+                    // no operand rows: the phase completes at once (every barrier
+                    // keeps one phase per use of its stage)
+                    tc::mbar_arrive(&S.fullB[st]);
+                    armB[st]++;
+                    return;
+                }
                 tc::mbar_arrive_expect_tx(&S.fullB[st], (uint32_t)nb * (2 * kBoxR * 128));
                 armB[st]++;
                 for (int bb = 0; bb < nb; bb++) {
@@ -741,7 +759,10 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             auto issueR = [&](int c) {
                 const uint32_t st = (seq + (uint32_t)c) & 1u;
                 const int nb = min(kCB, nbox - c * kCB);
-                tc::mbar_arrive_expect_tx(&S.fullR[st], (uint32_t)nb * (kBoxR * 16 + kBoxR * 16));
+                // records, and the norms (operand tiles) or the binary rows, which
+                // take the idle operand stage (popcount tiles)
+                const uint32_t extra = pop ? kBoxR * kBinRowB : kBoxR * 16;
+                tc::mbar_arrive_expect_tx(&S.fullR[st], (uint32_t)nb * (kBoxR * 16 + extra));
                 armR[st]++;
                 for (int bb = 0; bb < nb; bb++) {
                     uint32_t pos, len;
@@ -749,15 +770,19 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                     curR.next(S, pos, len, li);
                     const int64_t row = P.r_off + pos;
                     tc::bulk_load(&S.u.io.rec[st][bb * kBoxR], L.rec + row, kBoxR * 16, &S.fullR[st]);
-                    tc::bulk_load(&S.u.io.rn[st][bb][0], L.rnorm + row, kBoxR * 16, &S.fullR[st]);
+                    if (pop)
+                        tc::bulk_load(S.B[st][0] + bb * kBoxR * kBinRowB, L.rbin + row * kBinRowB, kBoxR * kBinRowB,
+                                      &S.fullR[st]);
+                    else
+                        tc::bulk_load(&S.u.io.rn[st][bb][0], L.rnorm + row, kBoxR * 16, &S.fullR[st]);
                 }
             };
             for (int c = 0; c < nchunk && c < 2; c++) {
                 issueB(c);
                 issueR(c);
             }
-            // E4M3 operands: binary rows (bits as 0 / 1) and float rows of the FP8 pass
-            const bool bin = P.kind == EGM_DESC_BIN || (FLT && L.fp8 && P.kind == EGM_DESC_F32_L2);
+            // E4M3 operands: float rows of the FP8 pass
+            const bool bin = FLT && L.fp8 && P.kind == EGM_DESC_F32_L2;
             for (int c = 0; c < nchunk; c++) {
                 const uint32_t sq = seq + (uint32_t)c, st = sq & 1u, use = sq >> 1;
                 bool ok = true;
@@ -766,8 +791,16 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                     if (ok) issueR(c);
                 }
                 ok = wait(&S.fullB[st], use & 1u) && ok;
-                if (c == 0) ok = wait(&S.afull, aload & 1u) && ok;
+                if (c == 0 && !pop) ok = wait(&S.afull, (armA - 1u) & 1u) && ok;
                 if (!ok) continue;
+                if (pop) {
+                    // no product: the accumulator and the stage are free at once
+                    tc::mbar_arrive(&S.done[st]);
+                    tc::mbar_arrive(&S.sfree[st]);
+                    armD[st]++;
+                    if (c + 2 < nchunk) issueB(c + 2);
+                    continue;
+                }
                 tc::tc_fence_after();
                 const int nb = min(kCB, nbox - c * kCB);
                 const uint32_t idesc = bin ? tc::idesc_e4m3(kTM, nb * kBoxR) : tc::idesc_bf16(kTM, nb * kBoxR);
@@ -786,9 +819,8 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 if (c + 2 < nchunk) issueB(c + 2);
             }
             // the query tile's load completes before its buffer is reused
-            if (nchunk == 0) wait(&S.afull, aload & 1u);
+            if (nchunk == 0 && !pop) wait(&S.afull, (armA - 1u) & 1u);
         }
-        aload++;
 
         // ---- epilogue: tests and best two over this warp's columns
         unsigned long long b1 = ~0ull, b2 = ~0ull;
@@ -841,8 +873,10 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
 #pragma unroll
                         for (int k = 0; k < kGroup; k++) rcs[k] = recb[g + k];
                         uint32_t v[kGroup];
-                        tc::tmem_ld8(tb + g, v);
-                        tc::tmem_wait_ld();
+                        if (!pop) {
+                            tc::tmem_ld8(tb + g, v);
+                            tc::tmem_wait_ld();
+                        }
                         // membership of all columns first, branch-free (independent
                         // work for the scheduler); then the few candidates
                         const uint32_t gm = (inbox >> g) & 0xffu;
@@ -867,6 +901,20 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                             const int k = __ffs(m) - 1;
                             nexact++;
                             if (exact_pair(P, qi, __float_as_uint(recb[g + k].w))) cm |= 1u << k;
+                        }
+                        if (pop) {
+                            // Hamming distance of the binary rows by popcount
+                            for (; cm; cm &= cm - 1u) {
+                                const int k = __ffs(cm) - 1;
+                                const uint4 *rb = reinterpret_cast<const uint4 *>(
+                                    S.B[st][0] + (bb * kBoxR + g + k) * kBinRowB);
+                                const uint4 r0 = rb[0], r1 = rb[1], q0 = qbrow[0], q1 = qbrow[1];
+                                const uint32_t h = __popc(q0.x ^ r0.x) + __popc(q0.y ^ r0.y) + __popc(q0.z ^ r0.z) +
+                                                   __popc(q0.w ^ r0.w) + __popc(q1.x ^ r1.x) + __popc(q1.y ^ r1.y) +
+                                                   __popc(q1.z ^ r1.z) + __popc(q1.w ^ r1.w);
+                                ncand++;
+                                top2(((unsigned long long)h << 32) | __float_as_uint(recb[g + k].w), b1, b2);
+                            }
                         }
                         for (; cm; cm &= cm - 1u) {
                             const int k = __ffs(cm) - 1;
@@ -957,6 +1005,9 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         }
         seq += (uint32_t)nchunk;
         if (qv) store_match(L, q_off + qi, P, r.flags, b1, b2);
+        // the query-tile buffer's generic accesses (binary rows) before the
+        // next tile's copies into it
+        if (pop) tc::fence_proxy_async();
         if (ctl) S.tile = knext < (uint64_t)L.ntiles ? L.tile_seq[knext] : -1;
         __syncthreads();
     }

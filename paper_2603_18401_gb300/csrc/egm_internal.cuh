@@ -177,6 +177,7 @@ struct Launch {
     uint32_t *qperm;              // sorted query slot -> pair-local query index
     uint16_t *qbkt;               // per query: its bucket of the angle order (written by the prep kernel)
     uint8_t *descA, *descB;       // 256-byte operand rows of the sorted queries / references
+    uint8_t *rbin;                // binary pairs: 32-byte rows of the sorted references (popcount tiles)
     QueryRec *qsrt;               // query records in sorted order, pad = (query index, norm bits)
     float4 *rnorm;                // sorted references: (squared norm of the operand row, or popcount;
                                   //   rounding error |r - r~| of float rows, else 0; row scale, 1
