@@ -774,7 +774,8 @@ def batched_leg(mt, torch, stream, args, world, local):
                "queries_per_step": bM, "refs_per_step": sum(s.n for s in bsc),
                "input_bytes": int(in_bytes), "l2": "inputs larger than L2 (129 MB)",
                "form": f"{args.form} (egm_graph_launch, one CUDA graph per step)",
-               "stage_ms": bstage}
+               "stage_ms": bstage,
+               "tuned_regimes": mt.tuner_entries()}
     if bform != 1:
         # the band kernel over the batch, on the method's algorithmic bytes
         # (each pair's inputs read once, its results written once); the
@@ -1172,6 +1173,7 @@ def run_ours(args):
         "matching": matching,
         "sweeps": sweeps,
         "clocks": clk,
+        "tuned_regimes": mt.tuner_entries(),
         "gpu_launches": launches * args.steps,
     }
     if cpu is not None:

@@ -167,10 +167,9 @@ typedef struct egm_params {
     int32_t ratio_den;
     int32_t sync;          /* 1 (default): calls wait and return the device status */
     int32_t form;          /* EGM_FORM_* */
-    int32_t band_tile;     /* banded form tile shape: 0 (default) chosen by the library's tuner,
-                              which times every shape on the first call of each batch size class
-                              (that call waits for the device); k = 1, 2, 3: shape k - 1 (4, 2 or 1
-                              boxes of 32 references per tensor-core chunk) */
+    int32_t band_tile;     /* banded form tile shape: 0 (default) chosen by the tuner (see tune);
+                              k = 1, 2, 3: shape k - 1 (4, 2 or 1 boxes of 32 references per
+                              tensor-core chunk, with 2, 3 or 4 resident CTAs per SM) */
     int32_t float_pass;    /* banded form, float descriptors: the tensor-core pass that brackets
                               the distances before the exact FP32 rerank (results are the same):
                               EGM_FLOAT_PASS_BF16 (default) or EGM_FLOAT_PASS_FP8 */
@@ -182,7 +181,15 @@ typedef struct egm_params {
                               that kernel first waits 10 us on a barrier that nothing completes,
                               before it issues any copy: banded calls then return
                               EGM_ERR_TIMEOUT and the context stays usable */
-    int32_t reserved[9];   /* zero */
+    int32_t tune;          /* 1 (default): the library's tuner picks the form (EGM_FORM_AUTO) and the
+                              band tile shape (band_tile 0) per call regime -- the number of 128-query
+                              tiles (log2), one or several pairs, the descriptor kinds, the expected
+                              candidates per query (log2) -- by timing the plain form and every band
+                              tile shape on the first call of a regime (that call waits for the
+                              device and runs the pipeline 16 times; results are the same in every
+                              configuration) and caching the fastest in the context
+                              (egm_tuner_export / egm_tuner_import); 0: no timing, a fixed rule */
+    int32_t reserved[8];   /* zero */
 } egm_params;
 
 /* Context lifetime.  `stream` is a cudaStream_t (NULL: the legacy default stream). */
@@ -277,6 +284,24 @@ egm_status egm_match_batch_host(egm_ctx *ctx, const egm_pair *pairs, int32_t npa
  */
 egm_status egm_match_pair_static(const egm_pair *pair, const egm_out *out, const egm_params *params,
                                  void *stream);
+
+/*
+ * The tuner's cache (egm_params.tune): one entry per call regime with the
+ * timings of the plain form and of the fastest band tile shape, and the
+ * choice.  egm_tuner_export writes it to `buf` (host memory, `capacity`
+ * bytes) and *size receives the bytes it needs; with buf NULL only *size
+ * is set; EGM_ERR_CAPACITY when capacity < *size.  egm_tuner_import
+ * replaces the context's cache with an exported one (for example from an
+ * earlier process on the same GPU model), so that calls of those regimes
+ * are not timed again; EGM_ERR_ARG if the bytes are not an export of this
+ * format.  Layout: a 16-byte header ("EGMT", version 1, entry count, SM
+ * count of the device it was measured on, as uint32) and 24 bytes per entry
+ * (uint64 regime key, int32 form, int32 shape, float ms_plain, float
+ * ms_band).  A tuning method of the library, with no counterpart in the
+ * paper.
+ */
+egm_status egm_tuner_export(egm_ctx *ctx, void *buf, int64_t capacity, int64_t *size);
+egm_status egm_tuner_import(egm_ctx *ctx, const void *buf, int64_t size);
 
 /* Wait for the context's stream and return (then clear) the device status. */
 egm_status egm_sync(egm_ctx *ctx);

@@ -60,9 +60,11 @@ class Matcher:
             pass
 
     # ------------------------------------------------------------- params
-    def set_params(self, ratio=None, sync=None, form=None, band_tile=None, float_pass=None, timeout_check=None):
+    def set_params(self, ratio=None, sync=None, form=None, band_tile=None, float_pass=None, timeout_check=None,
+                   tune=None):
         """ratio (num, den); sync; form (EGM_FORM_*); band_tile (0: tuned, k > 0: shape k - 1);
-        float_pass (EGM_FLOAT_PASS_*); timeout_check (1: the banded kernel's timeout path, no results)."""
+        float_pass (EGM_FLOAT_PASS_*); timeout_check (1: the banded kernel's timeout path, no results);
+        tune (1: timed choice of form and shape per regime, 0: fixed rule)."""
         p = _egm.egm_params()
         check(self.lib.egm_get_params(self.ctx, C.byref(p)), "egm_get_params")
         if ratio is not None:
@@ -77,7 +79,33 @@ class Matcher:
             p.float_pass = int(float_pass)
         if timeout_check is not None:
             p.timeout_check = int(timeout_check)
+        if tune is not None:
+            p.tune = int(tune)
         check(self.lib.egm_set_params(self.ctx, C.byref(p)), "egm_set_params")
+
+    def tuner_export(self) -> bytes:
+        """The tuner's cache (egm_tuner_export) as bytes."""
+        n = C.c_int64()
+        check(self.lib.egm_tuner_export(self.ctx, None, 0, C.byref(n)), "egm_tuner_export")
+        buf = C.create_string_buffer(max(int(n.value), 1))
+        check(self.lib.egm_tuner_export(self.ctx, buf, int(n.value), C.byref(n)), "egm_tuner_export")
+        return buf.raw[:int(n.value)]
+
+    def tuner_import(self, data: bytes):
+        check(self.lib.egm_tuner_import(self.ctx, data, len(data)), "egm_tuner_import")
+
+    def tuner_entries(self) -> list:
+        """The cache as dicts: regime key fields, chosen form and shape, timings (ms)."""
+        import struct
+        raw = self.tuner_export()
+        magic, version, count, sms = struct.unpack_from("<4sIII", raw, 0)
+        out = []
+        for k in range(count):
+            key, form, shape, ms_plain, ms_band = struct.unpack_from("<Qiiff", raw, 16 + 24 * k)
+            out.append({"tiles_log2": key & 63, "one_pair": bool((key >> 6) & 1), "kinds": (key >> 8) & 7,
+                        "candidates_log2": (key >> 12) & 15, "form": "banded" if form == 2 else "plain",
+                        "band_tile": shape, "ms_plain": ms_plain, "ms_band": ms_band})
+        return out
 
     def reserve(self, queries: int, refs: int, pairs: int = 1):
         check(self.lib.egm_reserve(self.ctx, int(queries), int(refs), int(pairs)), "egm_reserve")

@@ -62,7 +62,7 @@ class egm_out(C.Structure):
 class egm_params(C.Structure):
     _fields_ = [("ratio_num", C.c_int32), ("ratio_den", C.c_int32), ("sync", C.c_int32),
                 ("form", C.c_int32), ("band_tile", C.c_int32), ("float_pass", C.c_int32),
-                ("timeout_check", C.c_int32), ("reserved", C.c_int32 * 9)]
+                ("timeout_check", C.c_int32), ("tune", C.c_int32), ("reserved", C.c_int32 * 8)]
 
 
 class egm_stats(C.Structure):
@@ -106,6 +106,8 @@ SIGNATURES = {
     "egm_mlp_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     "egm_mlp_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "egm_mlp_set_fallback": (C.c_int, [C.c_void_p, C.c_double]),
+    "egm_tuner_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "egm_tuner_import": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "egm_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_void_p,
                                C.c_void_p]),
     "egm_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_float,

@@ -64,6 +64,13 @@ struct Scratch {
 
 }  // namespace
 
+// One regime's timings and choice (the tuner's cache entry).
+struct TuneEntry {
+    int32_t form = EGM_FORM_PLAIN;  // the faster form
+    int32_t shape = 0;              // the fastest band tile shape
+    float ms_plain = 0.0f, ms_band = 0.0f;
+};
+
 struct egm_ctx {
     int device = 0;
     int sms = 1;       // streaming multiprocessors of the device
@@ -104,8 +111,8 @@ struct egm_ctx {
     cudaStream_t copy = nullptr, copy_out = nullptr;
     cudaEvent_t copy_start = nullptr, out_done = nullptr;
     std::vector<cudaEvent_t> in_ev, done_ev;
-    // band tile shape per batch size class (log2 of the tile count), set by the tuner
-    std::map<int, int> band_shape;
+    // the tuner's choice per call regime (regime_key)
+    std::map<uint64_t, TuneEntry> tuned;
 };
 
 namespace {
@@ -181,6 +188,9 @@ struct Plan {
     bool band_ok = false;           // every pair fits the banded form
     bool has_float = false;         // some pair has float descriptors
     bool dense_u8 = false;          // every pair u8 with a scalar tolerance and >= 32 estimated candidates per query
+    double kbar_q = 0.0;            // sum over pairs of (estimated candidates per query) x (queries)
+    bool eps_vec = false;           // some pair has per-keypoint tolerances (density unknown on the host)
+    uint32_t kinds = 0;             // descriptor kinds present (bit k: kind k)
 };
 
 egm_status make_plan(const egm_pair *pairs, int npairs, Plan &pl) {
@@ -232,6 +242,9 @@ egm_status make_plan(const egm_pair *pairs, int npairs, Plan &pl) {
         const double W = A.width, H = A.height;
         const double kbar = 2.0 * A.eps_scalar * (double)A.n / (W * H) * 0.8 * std::sqrt(W * W + H * H);
         pl.dense_u8 = pl.dense_u8 && has_desc(&A) && A.kind == EGM_DESC_U8_L2 && !A.eps2 && kbar >= 32.0;
+        pl.kbar_q += A.eps2 ? 0.0 : kbar * (double)A.m;
+        pl.eps_vec = pl.eps_vec || A.eps2 != nullptr;
+        if (has_desc(&A)) pl.kinds |= 1u << (A.kind & 7);
     }
     for (int p = 0; p <= npairs; p++) {
         pl.offs[p] = pl.qoffs[p];
@@ -540,50 +553,106 @@ int tile_class(int64_t ntiles) {
     return k;
 }
 
-// Times every band tile shape on the packed inputs already enqueued (the band
-// kernel only reads them, so each run rewrites the same outputs) and returns
-// the fastest by the median of three runs.  Waits for the stream.
-cudaError_t tune_band(egm_ctx *c, const Launch &L, cudaStream_t st, int &best) {
-    constexpr int kReps = 3;
+// A call's regime, what the fastest form and band tile shape depend on:
+// the number of 128-query tiles (log2), one or several pairs, the
+// descriptor kinds present, and the expected candidates per query (log2 of
+// 1 + the estimate; 15 when some tolerance is per keypoint and therefore
+// unknown on the host).
+uint64_t regime_key(const Plan &pl, int npairs) {
+    int dens = 15;
+    if (!pl.eps_vec) {
+        const double kb = pl.kbar_q / (double)std::max<int64_t>(pl.nq, 1);
+        dens = 0;
+        while (dens < 14 && (double)(2 << dens) <= kb + 1.0) dens++;
+    }
+    return (uint64_t)std::min(tile_class(pl.ntiles), 63) | ((uint64_t)(npairs == 1) << 6) |
+           ((uint64_t)(pl.kinds & 7u) << 8) | ((uint64_t)dens << 12);
+}
+
+// Times the whole pipeline of the call in one configuration (form and band
+// tile shape) on the call's own inputs and outputs: one warm-up run, then
+// the median of three, each waited for, so that the runs do not overlap.
+// Every configuration computes the same exact results.
+cudaError_t time_config(egm_ctx *c, Scratch &sc, const Plan &pl, int npairs, const egm_out *out, bool band,
+                        int shape, float &ms) {
+    const Launch L = make_launch(sc, false, c->params, pl, npairs, out, band);
+    cudaStream_t st = c->stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    std::vector<std::vector<float>> ms(band_shapes());
-    for (int rep = 0; rep < kReps + 1 && e == cudaSuccess; rep++)   // the first round warms up
-        for (int k = 0; k < band_shapes() && e == cudaSuccess; k++) {
-            e = cudaEventRecord(e0, st);
-            if (e == cudaSuccess) e = launch_band(L, c->sms, k, st);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float t = 0.0f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
-            if (e == cudaSuccess && rep > 0) ms[k].push_back(t);
-        }
-    best = 0;
-    float best_ms = 0.0f;
-    for (int k = 0; k < band_shapes() && e == cudaSuccess; k++) {
-        std::sort(ms[k].begin(), ms[k].end());
-        const float med = ms[k][kReps / 2];
-        if (k == 0 || med < best_ms) {
-            best_ms = med;
-            best = k;
-        }
+    float t[3] = {0.0f, 0.0f, 0.0f};
+    for (int rep = 0; rep < 4 && e == cudaSuccess; rep++) {
+        e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = enqueue_pipeline(L, sc, false, pl.max_n, st, nullptr, band, c->sms, c, shape);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float x = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&x, e0, e1);
+        if (rep > 0) t[rep - 1] = x;
     }
+    std::sort(t, t + 3);
+    ms = t[1];
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     return e;
 }
 
-// The shape for this batch: forced by the parameters; with at most two tiles
-// per SM (every CTA takes one tile, latency decides) the shape with the
-// fewest chunks; otherwise the tuner's choice for the size class, or -1 (to
-// be tuned).
-int band_shape_for(egm_ctx *c, int64_t ntiles, bool has_float) {
-    if (has_float) return 0;  // float pairs: one shape (see launch_band)
-    if (c->params.band_tile > 0) return c->params.band_tile - 1;
-    if (ntiles <= 2 * (int64_t)c->sms) return 0;
-    auto it = c->band_shape.find(tile_class(ntiles));
-    return it == c->band_shape.end() ? -1 : it->second;
+// The configuration of a call.  Forced choices (plain form, candidate lists,
+// a forced shape) need no timing; with params.tune == 0 the heuristic of
+// choose_band picks the form, and the shape is (4 boxes, 2 CTAs per SM) up
+// to two tiles per SM, else (1 box, 4 CTAs); otherwise the regime's entry
+// in the tuner's cache decides, and `tune` asks the caller to time the
+// candidates first (the regime has none yet).
+egm_status choose_config(const egm_ctx *c, const Plan &pl, int npairs, bool csr, bool &band, int &shape,
+                         bool &tune) {
+    const egm_params &prm = c->params;
+    band = false;
+    shape = 0;
+    tune = false;
+    const bool can_band = pl.band_ok && !csr;
+    if (prm.form == EGM_FORM_BANDED && !can_band) return EGM_ERR_UNIMPLEMENTED;
+    if (!can_band || prm.form == EGM_FORM_PLAIN) return EGM_OK;
+    const int forced = pl.has_float ? 0 : prm.band_tile > 0 ? prm.band_tile - 1 : -1;
+    if (!prm.tune) {
+        egm_status s = choose_band(pl, prm, csr, c->sms, band);
+        if (s != EGM_OK) return s;
+        shape = forced >= 0 ? forced : pl.ntiles <= 2 * (int64_t)c->sms ? 0 : 2;
+        return EGM_OK;
+    }
+    const auto it = c->tuned.find(regime_key(pl, npairs));
+    if (it == c->tuned.end()) {
+        tune = true;
+        return EGM_OK;
+    }
+    band = prm.form == EGM_FORM_BANDED || it->second.form == EGM_FORM_BANDED;
+    shape = forced >= 0 ? forced : it->second.shape;
+    return EGM_OK;
+}
+
+// Times every candidate configuration of the call (the plain form and each
+// band tile shape) and records the regime's fastest; band, shape receive
+// the configuration the call then runs (a forced form or shape is kept).
+egm_status tune_regime(egm_ctx *c, Scratch &sc, const Plan &pl, int npairs, const egm_out *out, bool &band,
+                       int &shape) {
+    TuneEntry t;
+    EGM_TRY(time_config(c, sc, pl, npairs, out, false, 0, t.ms_plain));
+    t.ms_band = INFINITY;
+    t.shape = 0;
+    const int nshape = pl.has_float ? 1 : band_shapes();
+    for (int k = 0; k < nshape; k++) {
+        float ms = 0.0f;
+        EGM_TRY(time_config(c, sc, pl, npairs, out, true, k, ms));
+        if (ms < t.ms_band) {
+            t.ms_band = ms;
+            t.shape = k;
+        }
+    }
+    t.form = t.ms_band < t.ms_plain ? EGM_FORM_BANDED : EGM_FORM_PLAIN;
+    c->tuned[regime_key(pl, npairs)] = t;
+    const egm_params &prm = c->params;
+    band = prm.form == EGM_FORM_BANDED || t.form == EGM_FORM_BANDED;
+    shape = pl.has_float ? 0 : prm.band_tile > 0 ? prm.band_tile - 1 : t.shape;
+    return EGM_OK;
 }
 
 egm_status check_out(const egm_pair *pairs, int npairs, const egm_out *out) {
@@ -604,27 +673,21 @@ egm_status run_batch(egm_ctx *c, const egm_pair *pairs, int npairs, const egm_ou
     if (s != EGM_OK) return s;
     if ((s = check_out(pairs, npairs, out)) != EGM_OK) return s;
     const bool csr = out->cand_offsets != nullptr;
-    bool band = false;
-    if ((s = choose_band(pl, c->params, csr, c->sms, band)) != EGM_OK) return s;
+    bool band = false, tune = false;
+    int shape = 0;
+    if ((s = choose_config(c, pl, npairs, csr, band, shape, tune)) != EGM_OK) return s;
     EGM_TRY(cudaSetDevice(c->device));
-    if (band) EGM_TRY(ensure_side(c));
-    EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, npairs, band));
+    if (band || tune) EGM_TRY(ensure_side(c));
+    EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, npairs, band || tune));
     c->sc.parity ^= 1;
     if (npairs > 1) EGM_TRY(upload_plan(c, pl, npairs));  // one pair: the plan rides in the launch
-    Launch L = make_launch(c->sc, c->counters_on, c->params, pl, npairs, out, band);
     cudaStream_t st = c->stream;
-    if (sync) EGM_TRY(cudaMemsetAsync(L.status, 0, sizeof(uint32_t), st));
+    if (sync) EGM_TRY(cudaMemsetAsync(as<uint32_t>(c->sc.small), 0, sizeof(uint32_t), st));
+    // a regime met for the first time: every configuration is timed on this call's data
+    if (tune && (s = tune_regime(c, c->sc, pl, npairs, out, band, shape)) != EGM_OK) return s;
+    Launch L = make_launch(c->sc, c->counters_on, c->params, pl, npairs, out, band);
     if (c->counters_on) EGM_TRY(cudaMemsetAsync(c->sc.counters.ptr, 0, 8 * sizeof(unsigned long long), st));
-    const int shape = band ? band_shape_for(c, pl.ntiles, pl.has_float) : 0;
-    if (band && shape < 0) {
-        // first batch of this size class: everything but the band kernel, then the tuner
-        EGM_TRY(enqueue_pipeline(L, c->sc, csr, pl.max_n, st, nullptr, band, c->sms, c, -1));
-        int best = 0;
-        EGM_TRY(tune_band(c, L, st, best));
-        c->band_shape[tile_class(pl.ntiles)] = best;
-    } else {
-        EGM_TRY(enqueue_pipeline(L, c->sc, csr, pl.max_n, st, c, band, c->sms, c, shape));
-    }
+    EGM_TRY(enqueue_pipeline(L, c->sc, csr, pl.max_n, st, c, band, c->sms, c, shape));
     c->last.queries = pl.nq;
     c->last.refs = pl.nr;
     return finish(c, sync);
@@ -641,6 +704,7 @@ void egm_default_params(egm_params *p) {
     p->ratio_den = 5;
     p->sync = 1;
     p->form = EGM_FORM_AUTO;
+    p->tune = 1;
 }
 
 egm_status egm_create(egm_ctx **out, int device, void *stream) {
@@ -721,6 +785,7 @@ egm_status egm_set_params(egm_ctx *c, const egm_params *p) {
     if (p->band_tile < 0 || p->band_tile > band_shapes()) return EGM_ERR_ARG;
     if (p->float_pass != EGM_FLOAT_PASS_BF16 && p->float_pass != EGM_FLOAT_PASS_FP8) return EGM_ERR_ARG;
     if (p->timeout_check != 0 && p->timeout_check != 1) return EGM_ERR_ARG;
+    if (p->tune != 0 && p->tune != 1) return EGM_ERR_ARG;
     c->params = *p;
     return EGM_OK;
 }
@@ -736,6 +801,56 @@ egm_status egm_reserve(egm_ctx *c, int64_t queries, int64_t refs, int32_t pairs)
     EGM_TRY(cudaSetDevice(c->device));
     const int64_t ntab = 4 * refs + (int64_t)std::max(pairs, 1) * (2 * kLevels + 32);
     EGM_TRY(reserve(c->sc, queries, refs, ntab, std::max(pairs, 1), true));
+    return EGM_OK;
+}
+
+egm_status egm_tuner_export(egm_ctx *c, void *buf, int64_t capacity, int64_t *size) {
+    if (!c || !size || capacity < 0) return EGM_ERR_ARG;
+    const int64_t need = 16 + 24 * (int64_t)c->tuned.size();
+    *size = need;
+    if (!buf) return EGM_OK;
+    if (capacity < need) return EGM_ERR_CAPACITY;
+    unsigned char *o = static_cast<unsigned char *>(buf);
+    const uint32_t head[4] = {0x544d4745u /* "EGMT" */, 1u, (uint32_t)c->tuned.size(), (uint32_t)c->sms};
+    memcpy(o, head, 16);
+    o += 16;
+    for (const auto &kv : c->tuned) {
+        const uint64_t key = kv.first;
+        const int32_t fs[2] = {kv.second.form, kv.second.shape};
+        const float ms[2] = {kv.second.ms_plain, kv.second.ms_band};
+        memcpy(o, &key, 8);
+        memcpy(o + 8, fs, 8);
+        memcpy(o + 16, ms, 8);
+        o += 24;
+    }
+    return EGM_OK;
+}
+
+egm_status egm_tuner_import(egm_ctx *c, const void *buf, int64_t size) {
+    if (!c || !buf || size < 16) return EGM_ERR_ARG;
+    const unsigned char *in = static_cast<const unsigned char *>(buf);
+    uint32_t head[4];
+    memcpy(head, in, 16);
+    if (head[0] != 0x544d4745u || head[1] != 1u || size != 16 + 24 * (int64_t)head[2]) return EGM_ERR_ARG;
+    std::map<uint64_t, TuneEntry> t;
+    for (uint32_t k = 0; k < head[2]; k++) {
+        const unsigned char *e = in + 16 + 24 * (size_t)k;
+        uint64_t key;
+        int32_t fs[2];
+        float ms[2];
+        memcpy(&key, e, 8);
+        memcpy(fs, e + 8, 8);
+        memcpy(ms, e + 16, 8);
+        if ((fs[0] != EGM_FORM_PLAIN && fs[0] != EGM_FORM_BANDED) || fs[1] < 0 || fs[1] >= band_shapes())
+            return EGM_ERR_ARG;
+        TuneEntry x;
+        x.form = fs[0];
+        x.shape = fs[1];
+        x.ms_plain = ms[0];
+        x.ms_band = ms[1];
+        t[key] = x;
+    }
+    c->tuned.swap(t);
     return EGM_OK;
 }
 
@@ -1091,14 +1206,15 @@ egm_status egm_graph_create(egm_ctx *c, const egm_pair *pairs, int32_t npairs, c
     if (s != EGM_OK) return s;
     if ((s = check_out(pairs, npairs, out)) != EGM_OK) return s;
     const bool csr = out->cand_offsets != nullptr;
-    bool band = false;
-    if ((s = choose_band(pl, c->params, csr, c->sms, band)) != EGM_OK) return s;
+    bool band = false, tune = false;
+    int shape = 0;
+    if ((s = choose_config(c, pl, npairs, csr, band, shape, tune)) != EGM_OK) return s;
     EGM_TRY(cudaSetDevice(c->device));
     egm_graph *g = new (std::nothrow) egm_graph();
     if (!g) return EGM_ERR_NOMEM;
     g->ctx = c;
-    cudaError_t e = band ? ensure_side(c) : cudaSuccess;
-    if (e == cudaSuccess) e = reserve(g->sc, pl.nq, pl.nr, pl.ntab, npairs, band);
+    cudaError_t e = band || tune ? ensure_side(c) : cudaSuccess;
+    if (e == cudaSuccess) e = reserve(g->sc, pl.nq, pl.nr, pl.ntab, npairs, band || tune);
     const size_t ob = sizeof(int64_t) * pl.offs.size();
     std::vector<unsigned char> h(sizeof(PairDesc) * npairs + ob);
     memcpy(h.data(), pl.pd.data(), sizeof(PairDesc) * npairs);
@@ -1108,13 +1224,14 @@ egm_status egm_graph_create(egm_ctx *c, const egm_pair *pairs, int32_t npairs, c
     if (e == cudaSuccess)
         e = cudaMemcpy(g->sc.offs.ptr, h.data() + sizeof(PairDesc) * npairs, ob, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(g->sc.small.ptr, 0, 256);
-    int shape = band ? band_shape_for(c, pl.ntiles, pl.has_float) : 0;
-    if (e == cudaSuccess && band && shape < 0) {
+    if (e == cudaSuccess && tune) {
         // tune on the graph's own scratch before capturing
-        const Launch T = make_launch(g->sc, false, c->params, pl, npairs, out, band);
-        e = enqueue_pipeline(T, g->sc, csr, pl.max_n, c->stream, nullptr, band, c->sms, c, -1);
-        if (e == cudaSuccess) e = tune_band(c, T, c->stream, shape);
-        if (e == cudaSuccess) c->band_shape[tile_class(pl.ntiles)] = shape;
+        s = tune_regime(c, g->sc, pl, npairs, out, band, shape);
+        if (s != EGM_OK) {
+            cudaStreamSynchronize(c->stream);
+            egm_graph_destroy(g);
+            return s;
+        }
     }
     cudaStream_t cs = nullptr;
     cudaGraph_t gr = nullptr;

@@ -412,3 +412,71 @@ def test_device_timeout_path_reports_and_context_survives(mt):
         mt.set_params(timeout_check=0)
     for k in KEYS:
         assert np.array_equal(b[k], p[k]), k
+
+
+def test_regime_tuner_cache_export_import(mt):
+    """The tuner times the plain form and every band tile shape on the first
+    call of a regime and keeps the fastest; the tuned call's outputs equal the
+    plain form's; a second context that imports the cache runs the same
+    regime without timing it again (its first call is as fast as a tuned
+    one) and gives the same outputs; malformed caches are rejected."""
+    import struct
+    import time
+
+    import torch
+
+    from paper_2603_18401_gb300 import EgmError, Matcher
+
+    scenes = synth.config3(seed=9, npairs=24, scale=0.2)
+    items = [mt.to_device(s) for s in scenes]
+    mt.set_params(form=FORM_PLAIN)
+    ref = {k: v.cpu().numpy() for k, v in mt.match_batch(items).items()}
+    mt.set_params(form=FORM_AUTO, tune=1)
+    got = {k: v.cpu().numpy() for k, v in mt.match_batch(items).items()}
+    for k in KEYS:
+        assert np.array_equal(got[k], ref[k]), k
+    entries = mt.tuner_entries()
+    assert len(entries) >= 1
+    e = [x for x in entries if not x["one_pair"]][0]
+    assert e["form"] in ("plain", "banded") and 0 <= e["band_tile"] < 3
+    assert e["ms_plain"] > 0 and e["ms_band"] > 0
+    assert (e["form"] == "banded") == (e["ms_band"] < e["ms_plain"])
+    blob = mt.tuner_export()
+    assert len(blob) == 16 + 24 * len(entries) and blob[:4] == b"EGMT"
+
+    other = Matcher(0)
+    try:
+        other.tuner_import(blob)
+        assert other.tuner_entries() == entries
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out2 = {k: v.cpu().numpy() for k, v in other.match_batch(items).items()}
+        first = time.perf_counter() - t0
+        for k in KEYS:
+            assert np.array_equal(out2[k], ref[k]), k
+        # no timing runs: the imported regime is not tuned again
+        assert other.tuner_entries() == entries
+        t0 = time.perf_counter()
+        other.match_batch(items)
+        second = time.perf_counter() - t0
+        assert first < 10 * second + 0.05
+        with pytest.raises(EgmError):
+            other.tuner_import(blob[:20])
+        bad = bytearray(blob)
+        struct.pack_into("<i", bad, 16 + 8, 7)     # an unknown form
+        with pytest.raises(EgmError):
+            other.tuner_import(bytes(bad))
+        other.tuner_import(struct.pack("<4sIII", b"EGMT", 1, 0, 0))
+        assert other.tuner_entries() == []
+    finally:
+        other.close()
+    # with tune = 0 no regime is timed
+    fresh = Matcher(0)
+    try:
+        fresh.set_params(tune=0)
+        out3 = {k: v.cpu().numpy() for k, v in fresh.match_batch(items).items()}
+        for k in KEYS:
+            assert np.array_equal(out3[k], ref[k]), k
+        assert fresh.tuner_entries() == []
+    finally:
+        fresh.close()
