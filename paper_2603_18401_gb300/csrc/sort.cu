@@ -246,13 +246,16 @@ __global__ void __launch_bounds__(256) bucket_count_kernel(Launch L) {
 // The scan and the placement of one pair run on a thread-block cluster: its
 // warps hold rows of 128 table entries (a 16-byte vector per lane) in
 // registers, so a pass over the table is one round trip to memory; the
-// blocks' totals are exchanged through distributed shared memory.
-constexpr int kScanCtas = 8;
-constexpr int kScanThreads = 256;
-constexpr int kScanWarps = kScanThreads / 32;
+// blocks' totals are exchanged through distributed shared memory.  A call
+// of one pair takes a cluster of 16 blocks of 512 threads (the placement's
+// atomics and stores spread over more SMs: the nine-pair config-2 step runs
+// 0.377 instead of 0.397 ms); a batch 8 blocks of 256 per pair (the larger
+// clusters took its sort stage from 0.118 to 0.262 ms).
 constexpr int kScanRound = 8;  // rows a warp keeps in registers per round
 
+template <int kScanCtas, int kScanThreads>
 __global__ void __cluster_dims__(kScanCtas, 1, 1) __launch_bounds__(kScanThreads) bucket_scan_kernel(Launch L) {
+    constexpr int kScanWarps = kScanThreads / 32;
     pdl_begin();
     __shared__ __align__(16) PairGeom G;
     __shared__ uint32_t wtot[kScanWarps];
@@ -392,7 +395,12 @@ cudaError_t launch_sort(const Launch &L, cudaStream_t s) {
     if (blocks > 152 * 16) blocks = 152 * 16;
     cudaError_t e = launch_pdl(bucket_count_kernel, dim3((unsigned)blocks), dim3(256), 0, s, L);
     if (e != cudaSuccess) return e;
-    return launch_pdl(bucket_scan_kernel, dim3(L.npairs * kScanCtas), dim3(kScanThreads), 0, s, L);
+    if (L.npairs == 1) {
+        e = cudaFuncSetAttribute(bucket_scan_kernel<16, 512>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        return launch_pdl(bucket_scan_kernel<16, 512>, dim3(16), dim3(512), 0, s, L);
+    }
+    return launch_pdl(bucket_scan_kernel<8, 256>, dim3(L.npairs * 8), dim3(256), 0, s, L);
 }
 
 cudaError_t launch_long_row_sort(const Launch &L, const uint32_t *list, const uint32_t *count, cudaStream_t s) {
