@@ -373,7 +373,11 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
         }
     }
     // The last block to finish derives every pair's level layout (first sorted
-    // position, bucket bits, table offset) from the final level counts.
+    // position, bucket bits, table offset) from the final level counts.  A
+    // single pair's layout is derived by the bucket-count kernel instead
+    // (each of its blocks from the counts), which keeps this step -- a fence
+    // and an atomic round trip -- off the single-pair chain.
+    if (one) return;
     __shared__ bool s_last;
     __threadfence();
     __syncthreads();

@@ -233,13 +233,34 @@ __device__ __forceinline__ uint32_t bucket_slot(const PairGeom &G, uint32_t key)
 __global__ void __launch_bounds__(256) bucket_count_kernel(Launch L) {
     pdl_begin();
     __shared__ int64_t offs[kSmemPairs + 1];
+    __shared__ uint32_t s_tab[kLevels], s_start[kLevels + 1];
+    __shared__ int32_t s_bits[kLevels];
     const bool one = L.inl_use != 0;  // one pair: every reference is pair 0
     const bool cached = one || load_offsets(offs, L.r_offs, L.npairs);
+    if (one && threadIdx.x < 32) {
+        // a single pair's level layout from the final level counts (the prep
+        // kernel leaves it to this kernel); block 0 publishes it for the
+        // kernels after this one
+        const int lane = threadIdx.x;
+        level_layout_lane(L.geom[0].cnt[lane], s_start, s_bits, s_tab, kMaxBucketBits, lane);
+        if (blockIdx.x == 0) {
+            PairGeom &G = L.geom[0];
+            G.start[lane] = s_start[lane];
+            G.bits[lane] = s_bits[lane];
+            G.tab[lane] = s_tab[lane];
+            if (lane == kLevels - 1) G.start[kLevels] = s_start[kLevels];
+        }
+    }
     __syncthreads();
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L.nr; g += (int64_t)gridDim.x * blockDim.x) {
-        const int p = one ? 0 : cached ? pair_of_shared(offs, L.npairs, g) : pair_of(L.r_offs, L.npairs, g);
-        const int64_t t_off = one ? L.inl.t_off : L.pairs[p].t_off;
-        atomicAdd(L.tab + t_off + bucket_slot(L.geom[p], L.key_a[g]), 1u);
+        if (one) {
+            const uint32_t key = L.key_a[g];
+            const int lv = (int)(key >> kQBits);
+            atomicAdd(L.tab + L.inl.t_off + s_tab[lv] + ((key & kQMax) >> (kQBits - s_bits[lv])), 1u);
+            continue;
+        }
+        const int p = cached ? pair_of_shared(offs, L.npairs, g) : pair_of(L.r_offs, L.npairs, g);
+        atomicAdd(L.tab + L.pairs[p].t_off + bucket_slot(L.geom[p], L.key_a[g]), 1u);
     }
 }
 
