@@ -314,7 +314,8 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ ours
 KERNEL_SOURCES = {"band_kernel": ("band.cu", "tc.cuh", "egm_internal.cuh"),
-                  "stab_kernel": ("stab.cu", "egm_internal.cuh")}
+                  "stab_kernel": ("stab.cu", "egm_internal.cuh"),
+                  "stab_pair_kernel": ("stab.cu", "egm_internal.cuh")}
 
 
 def source_hash(kernel):
@@ -948,7 +949,9 @@ def run_ours(args):
         kb[b] += algorithmic_bytes(sc)
         kl[b] += layout_bytes(sc, b)
     banded = kt[True] > kt[False]
-    kernel = "band_kernel" if banded else "stab_kernel"
+    # the plain form of a single pair with u8 or binary rows runs the warp-per-query variant
+    kernel = "band_kernel" if banded else ("stab_pair_kernel" if all(s.kind in (0, 2) for s in scs)
+                                           else "stab_kernel")
     npk = n_banded if banded else len(scs) - n_banded
     kbytes = kb[banded] / max(npk, 1)
     lbytes = kl[banded] / max(npk, 1)
