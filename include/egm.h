@@ -320,6 +320,16 @@ egm_status egm_sync(egm_ctx *ctx);
  */
 egm_status egm_match_mutual(egm_ctx *ctx, const egm_pair *fwd, const egm_pair *rev, const egm_out *out);
 
+/* egm_match_mutual from the forward pair alone: the library forms the
+ * reverse direction itself (image-2 keypoints and descriptors as queries,
+ * image 1's as references, F^T computed on the device into context scratch,
+ * Sec. 3).  eps1 [m] float64 (device): the tolerance of each image-1
+ * keypoint, or NULL to use eps1_scalar (> 0); width1, height1: image 1's
+ * size in pixels.  out as for egm_match_mutual (m + n rows).  Errors as for
+ * egm_match_mutual. */
+egm_status egm_match_mutual_pair(egm_ctx *ctx, const egm_pair *fwd, const double *eps1, double eps1_scalar,
+                                 int32_t width1, int32_t height1, const egm_out *out);
+
 /*
  * The compact list of matches: (qi[k], rj[k]) = (i, best[i]) for every row
  * i < m whose flags contain every bit of `require` (for example

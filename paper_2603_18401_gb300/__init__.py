@@ -308,6 +308,21 @@ class Matcher:
         del torch
         return o
 
+    def match_mutual_pair(self, xy1, xy2, F, eps2, eps1, desc1, desc2, kind=EGM_DESC_U8_L2, dim=128,
+                          width2=640, height2=480, width1=None, height1=None):
+        """egm_match_mutual_pair: as match_mutual, the reverse direction formed by the library."""
+        fwd = self.make_pair(xy1, xy2, F, eps2, desc1, desc2, kind, dim, width2, height2)
+        keep = self._keep
+        e1p, e1s = (None, float(eps1)) if isinstance(eps1, (int, float)) else (_ptr(eps1), 0.0)
+        o = self._alloc_out(int(xy1.shape[0]) + int(xy2.shape[0]), False, 0)
+        s = self._out_struct(o, 0)
+        check(self.lib.egm_match_mutual_pair(self.ctx, C.byref(fwd), e1p, e1s,
+                                             int(width1 if width1 is not None else width2),
+                                             int(height1 if height1 is not None else height2), C.byref(s)),
+              "egm_match_mutual_pair")
+        self._keep = [keep, eps1]
+        return o
+
     def compact_matches(self, flags, best, require):
         """egm_compact_matches: (i, best[i]) of the rows whose flags contain `require`."""
         torch = self.torch

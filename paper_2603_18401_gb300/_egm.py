@@ -106,6 +106,8 @@ SIGNATURES = {
     "egm_mlp_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     "egm_mlp_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "egm_mlp_set_fallback": (C.c_int, [C.c_void_p, C.c_double]),
+    "egm_match_mutual_pair": (C.c_int, [C.c_void_p, C.POINTER(egm_pair), C.c_void_p, C.c_double, C.c_int32, C.c_int32,
+                                        C.POINTER(egm_out)]),
     "egm_tuner_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "egm_tuner_import": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "egm_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_void_p,

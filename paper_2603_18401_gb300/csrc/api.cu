@@ -81,6 +81,7 @@ struct egm_ctx {
     Scratch sc;
     DevBuf stage;  // host-path staging of inputs and outputs
     DevBuf compact;  // tile counts of egm_compact_matches
+    DevBuf ft;       // egm_match_mutual_pair: F^T of the reverse direction
     DevBuf gms;      // egm_gms: pair table, matches sorted by cell, decisions per grid shift
     void *gms_host = nullptr;        // pinned staging of the GMS pair table
     size_t gms_host_bytes = 0;
@@ -757,6 +758,7 @@ egm_status egm_destroy(egm_ctx *c) {
     c->sc.release();
     if (c->stage.ptr) cudaFree(c->stage.ptr);
     if (c->compact.ptr) cudaFree(c->compact.ptr);
+    if (c->ft.ptr) cudaFree(c->ft.ptr);
     if (c->gms.ptr) cudaFree(c->gms.ptr);
     if (c->gms_host) cudaFreeHost(c->gms_host);
     if (c->gms_host_ev) cudaEventDestroy(c->gms_host_ev);
@@ -1092,6 +1094,30 @@ egm_status egm_match_mutual(egm_ctx *c, const egm_pair *fwd, const egm_pair *rev
     if (s != EGM_OK) return s;
     EGM_TRY(launch_mutual(out->best, out->flags, fwd->m, fwd->n, c->stream));
     return finish(c, c->params.sync != 0);
+}
+
+egm_status egm_match_mutual_pair(egm_ctx *c, const egm_pair *fwd, const double *eps1, double eps1_scalar,
+                                 int32_t width1, int32_t height1, const egm_out *out) {
+    if (!c || !fwd || !fwd->F || !out) return EGM_ERR_ARG;
+    EGM_TRY(cudaSetDevice(c->device));
+    EGM_TRY(grow(c->ft, 9 * sizeof(double)));
+    // the reverse direction: image 2's keypoints query image 1's under F^T
+    egm_pair rev = *fwd;
+    rev.xy1 = fwd->xy2;
+    rev.xy2 = fwd->xy1;
+    rev.m = fwd->n;
+    rev.n = fwd->m;
+    rev.desc1 = fwd->desc2;
+    rev.desc2 = fwd->desc1;
+    rev.eps2 = eps1;
+    rev.eps_scalar = eps1_scalar;
+    rev.width = width1;
+    rev.height = height1;
+    rev.F = as<double>(c->ft);
+    egm_status s = check_pair(&rev);
+    if (s != EGM_OK) return s;
+    EGM_TRY(launch_transpose3(fwd->F, as<double>(c->ft), c->stream));
+    return egm_match_mutual(c, fwd, &rev, out);
 }
 
 egm_status egm_compact_matches(egm_ctx *c, const uint8_t *flags, const int32_t *best, int64_t m,

@@ -549,6 +549,7 @@ cudaError_t launch_query_sort(const Launch &L, cudaStream_t s);
 cudaError_t launch_pack(const Launch &L, cudaStream_t s);
 int band_shapes();  // tile shapes of the band kernel (see band.cu)
 cudaError_t launch_mutual(const int32_t *best, uint8_t *flags, int64_t m, int64_t n, cudaStream_t s);
+cudaError_t launch_transpose3(const double *F, double *Ft, cudaStream_t s);
 // GMS (gms.cu): one pair of a batch, as the kernels read it from the table
 struct GmsPair {
     const double *xy1, *xy2;

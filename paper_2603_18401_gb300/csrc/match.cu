@@ -117,6 +117,17 @@ __global__ void __launch_bounds__(kCompactThreads) compact_write_kernel(const ui
 
 }  // namespace
 
+// F^T of a row-major 3 x 3 matrix (the reverse direction of a pair, Sec. 3).
+__global__ void transpose3_kernel(const double *F, double *Ft) {
+    const int k = threadIdx.x;
+    if (k < 9) Ft[3 * (k % 3) + k / 3] = F[k];
+}
+
+cudaError_t launch_transpose3(const double *F, double *Ft, cudaStream_t s) {
+    transpose3_kernel<<<1, 32, 0, s>>>(F, Ft);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mutual(const int32_t *best, uint8_t *flags, int64_t m, int64_t n, cudaStream_t s) {
     if (m + n == 0) return cudaSuccess;
     mutual_kernel<<<(int)((m + n + 255) / 256), 256, 0, s>>>(best, flags, m, n);

@@ -51,14 +51,11 @@ constexpr int kStabThreads = 256;
 constexpr int kRangesPerQuery = 2 * kLevels;
 constexpr int kDescCache = 256;  // query descriptors up to this many bytes are staged in shared memory
 // window elements a thread tests per batch of record loads, and candidates
-// per lane group in the distance pass: smaller in the single-pair variant,
-// where fewer registers keep the kernel out of local memory
-template <bool ONE> constexpr int kBatchOf = ONE ? 2 : 4;
-template <bool ONE> constexpr int kUOf = ONE ? 2 : 4;
-// window elements tested per round: more in the single-pair variant (one
-// wave of blocks, fewer rounds), fewer in the other (shared memory for
-// occupancy)
-template <bool ONE> constexpr int kRoundOf = ONE ? 1536 : 1024;
+// per lane group in the distance pass
+constexpr int kBatch = 4;
+constexpr int kU = 4;
+// window elements tested per round (shared memory for occupancy)
+constexpr int kRound = 1024;
 constexpr int kQPerWarp = kQB / (kStabThreads / 32);
 
 template <int kRound>
@@ -138,15 +135,10 @@ __device__ __forceinline__ void copy16(void *dst, const void *src, int bytes, in
 }
 
 // mode 0: fused matching; 1: count candidates; 2: write candidate rows and match.
-// ONE: a call of one pair whose descriptor rows (u8 or binary) are staged
-// whole: every block is uniform, and the paths for blocks that span pairs or
-// read rows piecewise are compiled out (their registers would otherwise
-// crowd the common path into local memory).
-template <int KIND, bool ONE>
+// (A single pair with u8 or binary rows runs stab_pair_kernel instead.)
+template <int KIND>
 __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mode) {
-    constexpr int kBatch = kBatchOf<ONE>;
     pdl_begin();
-    constexpr int kRound = kRoundOf<ONE>;
     __shared__ __align__(16) StabSmem<kRound> S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -239,7 +231,7 @@ __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mod
             }
             // queries of another pair than the block's first: one warp per query, lane = level
 #pragma unroll 1
-            for (int t = 0; t < (ONE ? 0 : kQPerWarp); t++) {
+            for (int t = 0; t < kQPerWarp; t++) {
                 const int ql = qbase + t;
                 if (ql >= nqb || S.qr[ql].pair == S.gpair) continue;
                 const int p = S.qr[ql].pair;
@@ -270,10 +262,8 @@ __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mod
         cp_async_wait();
         // every query of the block in the cached pair, descriptors of one kind
         // and staged: the pair's fields are block constants (the common case)
-        bool uni = true;
-        if (ONE) __syncthreads();
-        else uni = __syncthreads_and(tid >= nqb || S.qr[tid].pair == S.gpair) && KIND != kKindAny &&
-                   S.pd.row_bytes <= kDescCache;
+        const bool uni = __syncthreads_and(tid >= nqb || S.qr[tid].pair == S.gpair) && KIND != kKindAny &&
+                         S.pd.row_bytes <= kDescCache;
         const float4 *recb = L.rec + S.pd.r_off;
         if (warp == 0) {
             uint32_t incl = S.tq[lane];
@@ -446,8 +436,8 @@ __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mod
                             : chunks0 >= 2 ? 2 : 1;
                 const int groups = kStabThreads / G;
                 const int gl = tid % G;
-                constexpr int U = kUOf<ONE>;
-                if (ONE || (uni && chunks0 <= G)) {
+                constexpr int U = kU;
+                if (uni && chunks0 <= G) {
                     // block constants; one chunk per lane of each candidate
                     const uint4 *d2 = reinterpret_cast<const uint4 *>(S.pd.desc2);
                     const int rb16 = chunks0;
@@ -960,14 +950,10 @@ cudaError_t launch_stab(const Launch &L, int mode, cudaStream_t s) {
         }
     }
     switch (L.kind) {
-        case EGM_DESC_U8_L2:
-            return one ? launch_pdl(stab_kernel<EGM_DESC_U8_L2, true>, g, b, 0, s, L, mode)
-                       : launch_pdl(stab_kernel<EGM_DESC_U8_L2, false>, g, b, 0, s, L, mode);
-        case EGM_DESC_BIN:
-            return one ? launch_pdl(stab_kernel<EGM_DESC_BIN, true>, g, b, 0, s, L, mode)
-                       : launch_pdl(stab_kernel<EGM_DESC_BIN, false>, g, b, 0, s, L, mode);
-        case EGM_DESC_F32_L2: return launch_pdl(stab_kernel<EGM_DESC_F32_L2, false>, g, b, 0, s, L, mode);
-        default: return launch_pdl(stab_kernel<kKindAny, false>, g, b, 0, s, L, mode);
+        case EGM_DESC_U8_L2: return launch_pdl(stab_kernel<EGM_DESC_U8_L2>, g, b, 0, s, L, mode);
+        case EGM_DESC_BIN: return launch_pdl(stab_kernel<EGM_DESC_BIN>, g, b, 0, s, L, mode);
+        case EGM_DESC_F32_L2: return launch_pdl(stab_kernel<EGM_DESC_F32_L2>, g, b, 0, s, L, mode);
+        default: return launch_pdl(stab_kernel<kKindAny>, g, b, 0, s, L, mode);
     }
 }
 

@@ -222,3 +222,24 @@ def test_gms_batch_equals_per_pair_oracle(mt):
     mt.gms_batch(items, require=1, grid=20, alpha=6.0)
     for (_, _, _, f, _, _), w in zip(items, want):
         assert np.array_equal(f.cpu().numpy(), w)
+
+
+def test_mutual_from_one_pair_equals_two_pair_call(mt):
+    """egm_match_mutual_pair forms the reverse direction (F^T on the device,
+    image-1 tolerances) itself: its outputs equal egm_match_mutual's with the
+    caller-built reverse pair and the oracle's cross-check, with scalar and
+    per-keypoint image-1 tolerances, on consecutive calls of different pairs."""
+    torch = mt.torch
+    rng = np.random.default_rng(31)
+    for sc, eps1 in ((synth.config1(seed=6), 2.0), (synth.config2("far", 2.0, scale=0.25), None)):
+        if eps1 is None:
+            eps1 = rng.uniform(0.5, 4.0, sc.m)
+        d = mt.to_device(sc)
+        e1 = eps1 if np.ndim(eps1) == 0 else torch.as_tensor(eps1, dtype=torch.float64).to(mt.device)
+        o = mt.match_mutual_pair(d["xy1"], d["xy2"], d["F"], d["eps"], e1, d["desc1"], d["desc2"], d["kind"],
+                                 d["dim"], d["width"], d["height"])
+        got = {k: v.cpu().numpy() for k, v in o.items()}
+        ref, _ = mutual(mt, sc, eps1)
+        for k in KEYS:
+            assert np.array_equal(got[k], ref[k]), k
+        check_mutual(got, sc, eps1)
