@@ -609,6 +609,7 @@ __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mod
 constexpr int kPairThreads = 128;
 constexpr int kPairWarps = kPairThreads / 32;
 constexpr int kRing = 64;  // candidate ring per warp: 32 waiting + 32 new
+constexpr int kChunkQ = 8; // queries per warp whose windows are computed in one pass
 
 // The window of a query in one level, from the level's half-width over all
 // of the pair's queries (key_window_span with the pair's extremes of the pad
@@ -684,9 +685,10 @@ __global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
     __shared__ int32_t snlev;
     __shared__ uint32_t ring[kPairWarps][kRing];
     __shared__ LevelWin slc[kLevels];
-    // the next query's record and descriptor row, copied ahead (double-buffered per warp)
-    __shared__ __align__(16) QueryRec qbuf[kPairWarps][2];
-    __shared__ __align__(16) uint4 dbuf[kPairWarps][2][G];
+    // a warp's chunk of queries: their records, descriptor rows and window ranges
+    __shared__ __align__(16) QueryRec qchunk[kPairWarps][kChunkQ];
+    __shared__ __align__(16) uint4 dchunk[kPairWarps][kChunkQ][G];
+    __shared__ __align__(16) uint4 wrng[kPairWarps][kChunkQ * kLevels];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt = (1u << lane) - 1u;
     for (int k = tid; k < (int)(sizeof(PairGeom) / 16); k += kPairThreads)
@@ -708,8 +710,6 @@ __global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
     const int64_t q_off = L.inl.q_off;
     const int nlev = snlev;
     const bool haslev = lane < nlev;
-    const int lvl = haslev ? slv[lane] : 0;
-    const uint32_t *T = L.tab + L.inl.t_off + sg.tab[lvl];
     const float4 *recb = L.rec + L.inl.r_off;
     uint32_t *rg = ring[warp];
     const int sub = lane % G, grp = lane / G;
@@ -722,34 +722,51 @@ __global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
     const int64_t rnum = L.ratio_num, rden = L.ratio_den;
     uint32_t nwin = 0, ncand = 0, nexact = 0;
     const int64_t nwarps = (int64_t)gridDim.x * kPairWarps;
-    int64_t q = (int64_t)blockIdx.x * kPairWarps + warp;
-    // copies of a query's record (3 lanes) and descriptor row (G lanes) into buffer b
-    auto fetch = [&](int64_t qq, int b) {
-        if (lane < 3)
-            cp_async16(reinterpret_cast<uint4 *>(&qbuf[warp][b]) + lane, reinterpret_cast<const uint4 *>(L.qrec + qq) + lane);
-        if (kDesc && lane >= 8 && lane < 8 + G) cp_async16(&dbuf[warp][b][lane - 8], d1 + (qq - q_off) * G + (lane - 8));
-    };
-    if (q < L.nq) fetch(q, 0);
-    for (int it = 0; q < L.nq; q += nwarps, it++) {
+    // The warp's queries come in chunks of up to kChunkQ (q = c0 + k nwarps):
+    // their records and descriptor rows are copied at once, and the windows
+    // of every (query, level) slot of the chunk are computed in one pass over
+    // the lanes, with their table loads issued together.
+    for (int64_t c0 = (int64_t)blockIdx.x * kPairWarps + warp; c0 < L.nq; c0 += (int64_t)kChunkQ * nwarps) {
+    const int nk = (int)min((int64_t)kChunkQ, (L.nq - c0 + nwarps - 1) / nwarps);
+    for (int t = lane; t < 3 * nk; t += 32)
+        cp_async16(reinterpret_cast<uint4 *>(&qchunk[warp][t / 3]) + t % 3,
+                   reinterpret_cast<const uint4 *>(L.qrec + c0 + (int64_t)(t / 3) * nwarps) + t % 3);
+    if (kDesc)
+        for (int t = lane; t < G * nk; t += 32)
+            cp_async16(&dchunk[warp][t / G][t % G], d1 + (c0 + (int64_t)(t / G) * nwarps - q_off) * G + t % G);
+    cp_async_wait();
+    __syncwarp();
+    for (int s0 = 0; s0 < nk * nlev; s0 += 32) {
+        const int sl = s0 + lane;
+        if (sl < nk * nlev) {
+            const int k = sl / nlev, l = sl - k * nlev;
+            const WinKeys wk = level_window(sg, slc[l], qchunk[warp][k]);
+            uint32_t a = 0, b = 0;
+            if (wk.kind >= 2) {
+                const uint32_t *Tl = L.tab + L.inl.t_off + sg.tab[slv[l]];
+                a = __ldg(Tl + wk.ta);
+                b = __ldg(Tl + wk.tb);
+            }
+            const Window wl = window_ranges(wk, a, b);
+            wrng[warp][k * kLevels + l] = make_uint4(wl.b0, wl.len0, wl.b1, wl.len1);
+        }
+    }
+    __syncwarp();
+    for (int k = 0; k < nk; k++) {
+        const int64_t q = c0 + (int64_t)k * nwarps;
         const int64_t qi = q - q_off;
-        cp_async_wait();
-        __syncwarp();
-        const QueryRec rq = qbuf[warp][it & 1];
+        const QueryRec rq = qchunk[warp][k];
         uint4 qdq = make_uint4(0u, 0u, 0u, 0u);
-        if (kDesc) qdq = dbuf[warp][it & 1][sub];
-        __syncwarp();
-        if (q + nwarps < L.nq) fetch(q + nwarps, (it + 1) & 1);
+        if (kDesc) qdq = dchunk[warp][k][sub];
         // the window of this lane's level as (at most) two ranges of sorted positions
         Window w;
         w.b0 = w.len0 = w.b1 = w.len1 = 0u;
         if (haslev) {
-            const WinKeys wk = level_window(sg, slc[lane], rq);
-            uint32_t a = 0, b = 0;
-            if (wk.kind >= 2) {
-                a = __ldg(T + wk.ta);
-                b = __ldg(T + wk.tb);
-            }
-            w = window_ranges(wk, a, b);
+            const uint4 v = wrng[warp][k * kLevels + lane];
+            w.b0 = v.x;
+            w.len0 = v.y;
+            w.b1 = v.z;
+            w.len1 = v.w;
         }
         const uint32_t tl = w.len0 + w.len1;
         uint32_t incl = tl;
@@ -886,6 +903,8 @@ __global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
             if (lane < 4) static_cast<uint32_t *>(outp)[q] = word;
             else static_cast<uint8_t *>(outp)[q] = (uint8_t)fl;
         }
+    }
+    __syncwarp();  // the chunk's buffers are read before the next chunk's copies
     }
     if (L.counters) {
         const uint32_t a = __reduce_add_sync(0xffffffffu, nwin);
