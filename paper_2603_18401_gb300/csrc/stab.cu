@@ -674,10 +674,12 @@ static __device__ __noinline__ bool exact_pair_p(const double *F, const double *
     return exact_member(a, b, c, N, xy2[2 * (int64_t)j], xy2[2 * (int64_t)j + 1], eps);
 }
 
-template <int KIND, int G, int MODE>
+// G lanes read a descriptor row, C 16-byte chunks each (a row is G C 16 bytes).
+template <int KIND, int G, int C, int MODE>
 __global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
     static_assert(G >= 1 && G <= 16 && (G & (G - 1)) == 0, "lanes per descriptor row");
     constexpr int kPerRound = 32 / G;  // candidates per round of loads
+    constexpr int kRow16 = G * C;      // 16-byte chunks per row
     constexpr bool kDesc = MODE != 1;  // descriptor distances (the launcher checks that rows exist)
     pdl_begin();
     __shared__ __align__(16) PairGeom sg;
@@ -687,7 +689,7 @@ __global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
     __shared__ LevelWin slc[kLevels];
     // a warp's chunk of queries: their records, descriptor rows and window ranges
     __shared__ __align__(16) QueryRec qchunk[kPairWarps][kChunkQ];
-    __shared__ __align__(16) uint4 dchunk[kPairWarps][kChunkQ][G];
+    __shared__ __align__(16) uint4 dchunk[kPairWarps][kChunkQ][kRow16];
     __shared__ __align__(16) uint4 wrng[kPairWarps][kChunkQ * kLevels];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -732,8 +734,9 @@ __global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
         cp_async16(reinterpret_cast<uint4 *>(&qchunk[warp][t / 3]) + t % 3,
                    reinterpret_cast<const uint4 *>(L.qrec + c0 + (int64_t)(t / 3) * nwarps) + t % 3);
     if (kDesc)
-        for (int t = lane; t < G * nk; t += 32)
-            cp_async16(&dchunk[warp][t / G][t % G], d1 + (c0 + (int64_t)(t / G) * nwarps - q_off) * G + t % G);
+        for (int t = lane; t < kRow16 * nk; t += 32)
+            cp_async16(&dchunk[warp][t / kRow16][t % kRow16],
+                       d1 + (c0 + (int64_t)(t / kRow16) * nwarps - q_off) * kRow16 + t % kRow16);
     cp_async_wait();
     __syncwarp();
     for (int s0 = 0; s0 < nk * nlev; s0 += 32) {
@@ -756,8 +759,9 @@ __global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
         const int64_t q = c0 + (int64_t)k * nwarps;
         const int64_t qi = q - q_off;
         const QueryRec rq = qchunk[warp][k];
-        uint4 qdq = make_uint4(0u, 0u, 0u, 0u);
-        if (kDesc) qdq = dchunk[warp][k][sub];
+        uint4 qdq[C];
+#pragma unroll
+        for (int c = 0; c < C; c++) qdq[c] = kDesc ? dchunk[warp][k][sub * C + c] : make_uint4(0u, 0u, 0u, 0u);
         // the window of this lane's level as (at most) two ranges of sorted positions
         Window w;
         w.b0 = w.len0 = w.b1 = w.len1 = 0u;
@@ -793,9 +797,13 @@ __global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
                 const uint32_t c = (uint32_t)(u * kPerRound + grp);
                 if (c < nb) {
                     const uint32_t jj = rg[(start + c) % kRing];
-                    const uint4 rv = __ldg(d2 + (int64_t)jj * G + sub);
+                    const uint4 *row = d2 + (int64_t)jj * kRow16 + sub * C;
+                    uint4 rv[C];
+#pragma unroll
+                    for (int cc = 0; cc < C; cc++) rv[cc] = __ldg(row + cc);
                     float unused = 0.0f;
-                    chunk_dist<KIND>(KIND, qdq, rv, acc[u], unused);
+#pragma unroll
+                    for (int cc = 0; cc < C; cc++) chunk_dist<KIND>(KIND, qdq[cc], rv[cc], acc[u], unused);
                 }
             }
             // transposed butterfly: after the step over lane bit h a lane keeps
@@ -918,28 +926,26 @@ __global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
     }
 }
 
-template <int KIND, int G, int MODE>
+template <int KIND, int G, int C, int MODE>
 cudaError_t launch_pair_mode(const Launch &L, int sms, cudaStream_t s) {
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stab_pair_kernel<KIND, G, MODE>,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stab_pair_kernel<KIND, G, C, MODE>,
                                                                       kPairThreads, 0);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
     int64_t blocks = (L.nq + kPairWarps - 1) / kPairWarps;
     blocks = std::min<int64_t>(blocks, (int64_t)per_sm * sms);
-    return launch_pdl(stab_pair_kernel<KIND, G, MODE>, dim3((unsigned)blocks), dim3(kPairThreads), 0, s, L);
+    return launch_pdl(stab_pair_kernel<KIND, G, C, MODE>, dim3((unsigned)blocks), dim3(kPairThreads), 0, s, L);
 }
 
-template <int KIND, int G>
+template <int KIND, int G, int C>
 cudaError_t launch_pair(const Launch &L, int mode, int sms, cudaStream_t s) {
-    // without descriptors only candidate lists are written (mode 2 then counts as mode 1 for
-    // the distances: the kernel's mode-2 path also needs rows)
     switch (mode) {
-        case 0: return launch_pair_mode<KIND, G, 0>(L, sms, s);
-        case 1: return launch_pair_mode<KIND, G, 1>(L, sms, s);
-        default: return launch_pair_mode<KIND, G, 2>(L, sms, s);
+        case 0: return launch_pair_mode<KIND, G, C, 0>(L, sms, s);
+        case 1: return launch_pair_mode<KIND, G, C, 1>(L, sms, s);
+        default: return launch_pair_mode<KIND, G, C, 2>(L, sms, s);
     }
 }
 
@@ -961,11 +967,12 @@ cudaError_t launch_stab(const Launch &L, int mode, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         const bool u8 = L.kind == EGM_DESC_U8_L2;
         switch (rb >> 4) {
-            case 1: return u8 ? launch_pair<EGM_DESC_U8_L2, 1>(L, mode, sms, s) : launch_pair<EGM_DESC_BIN, 1>(L, mode, sms, s);
-            case 2: return u8 ? launch_pair<EGM_DESC_U8_L2, 2>(L, mode, sms, s) : launch_pair<EGM_DESC_BIN, 2>(L, mode, sms, s);
-            case 4: return u8 ? launch_pair<EGM_DESC_U8_L2, 4>(L, mode, sms, s) : launch_pair<EGM_DESC_BIN, 4>(L, mode, sms, s);
-            case 8: return u8 ? launch_pair<EGM_DESC_U8_L2, 8>(L, mode, sms, s) : launch_pair<EGM_DESC_BIN, 8>(L, mode, sms, s);
-            default: return u8 ? launch_pair<EGM_DESC_U8_L2, 16>(L, mode, sms, s) : launch_pair<EGM_DESC_BIN, 16>(L, mode, sms, s);
+            // rows of 16 .. 256 bytes: a lane reads 32 bytes of a row (16 for 16-byte rows)
+            case 1: return u8 ? launch_pair<EGM_DESC_U8_L2, 1, 1>(L, mode, sms, s) : launch_pair<EGM_DESC_BIN, 1, 1>(L, mode, sms, s);
+            case 2: return u8 ? launch_pair<EGM_DESC_U8_L2, 1, 2>(L, mode, sms, s) : launch_pair<EGM_DESC_BIN, 1, 2>(L, mode, sms, s);
+            case 4: return u8 ? launch_pair<EGM_DESC_U8_L2, 2, 2>(L, mode, sms, s) : launch_pair<EGM_DESC_BIN, 2, 2>(L, mode, sms, s);
+            case 8: return u8 ? launch_pair<EGM_DESC_U8_L2, 4, 2>(L, mode, sms, s) : launch_pair<EGM_DESC_BIN, 4, 2>(L, mode, sms, s);
+            default: return u8 ? launch_pair<EGM_DESC_U8_L2, 8, 2>(L, mode, sms, s) : launch_pair<EGM_DESC_BIN, 8, 2>(L, mode, sms, s);
         }
     }
     switch (L.kind) {
