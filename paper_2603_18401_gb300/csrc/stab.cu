@@ -691,6 +691,7 @@ __global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
     __shared__ __align__(16) QueryRec qchunk[kPairWarps][kChunkQ];
     __shared__ __align__(16) uint4 dchunk[kPairWarps][kChunkQ][kRow16];
     __shared__ __align__(16) uint4 wrng[kPairWarps][kChunkQ * kLevels];
+    __shared__ __align__(16) uint4 res[kPairWarps][kChunkQ];   // best two (distance, index) of each query
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt = (1u << lane) - 1u;
     for (int k = tid; k < (int)(sizeof(PairGeom) / 16); k += kPairThreads)
@@ -718,9 +719,6 @@ __global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
     const uint4 *d1 = reinterpret_cast<const uint4 *>(L.inl.desc1);
     const uint4 *d2 = reinterpret_cast<const uint4 *>(L.inl.desc2);
     const bool write_rows = MODE == 2 && L.cand_offsets[L.nq] <= L.cand_capacity;
-    // result outputs of lanes 0-3 (32-bit words) and 4 (flags)
-    void *outp = lane == 0 ? (void *)L.best : lane == 1 ? (void *)L.second : lane == 2 ? (void *)L.best_d
-               : lane == 3 ? (void *)L.second_d : lane == 4 ? (void *)L.flags : nullptr;
     const int64_t rnum = L.ratio_num, rden = L.ratio_den;
     uint32_t nwin = 0, ncand = 0, nexact = 0;
     const int64_t nwarps = (int64_t)gridDim.x * kPairWarps;
@@ -885,9 +883,18 @@ __global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
         const uint32_t dk2 = (uint32_t)(c2 >> 32), jk2 = (uint32_t)c2;
         const uint32_t sd = __reduce_min_sync(0xffffffffu, dk2);
         const uint32_t sj = __reduce_min_sync(0xffffffffu, dk2 == sd ? jk2 : 0xffffffffu);
+        // the query's best two wait in shared memory; lane k writes query k's
+        // outputs after the chunk
+        if (lane == 0) res[warp][k] = make_uint4(md, mj, sd, sj);
+    }
+    __syncwarp();
+    if (MODE != 1 && lane < nk) {
         // outputs as store_match writes them (integer distances; Sec. 5.1 ratio
-        // test in exact integer form), one field per lane 0-4
-        uint32_t fl = rq.flags & EGM_FLAG_DEGENERATE_LINE;
+        // test in exact integer form)
+        const int64_t q = c0 + (int64_t)lane * nwarps;
+        const uint4 rr = res[warp][lane];
+        const uint32_t md = rr.x, mj = rr.y, sd = rr.z, sj = rr.w;
+        uint32_t fl = qchunk[warp][lane].flags & EGM_FLAG_DEGENERATE_LINE;
         const bool has1 = md != 0xffffffffu || mj != 0xffffffffu;
         const bool has2 = sd != 0xffffffffu || sj != 0xffffffffu;
         if (has1) {
@@ -903,14 +910,11 @@ __global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
             }
             if (pass) fl |= EGM_FLAG_RATIO_PASS;
         }
-        const uint32_t word = lane == 0 ? (has1 ? mj : 0xffffffffu)
-                            : lane == 1 ? (has2 ? sj : 0xffffffffu)
-                            : lane == 2 ? __float_as_uint(has1 ? (float)md : INFINITY)
-                                        : __float_as_uint(has2 ? (float)sd : INFINITY);
-        if (outp) {
-            if (lane < 4) static_cast<uint32_t *>(outp)[q] = word;
-            else static_cast<uint8_t *>(outp)[q] = (uint8_t)fl;
-        }
+        if (L.best) L.best[q] = has1 ? (int32_t)mj : -1;
+        if (L.second) L.second[q] = has2 ? (int32_t)sj : -1;
+        if (L.best_d) L.best_d[q] = has1 ? (float)md : INFINITY;
+        if (L.second_d) L.second_d[q] = has2 ? (float)sd : INFINITY;
+        if (L.flags) L.flags[q] = (uint8_t)fl;
     }
     __syncwarp();  // the chunk's buffers are read before the next chunk's copies
     }
