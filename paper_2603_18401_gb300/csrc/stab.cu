@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(kStabThreads, 4) stab_kernel(Launch L, int mod
 // a transposed butterfly (G - 1 shuffles for the G rounds), after which
 // each lane holds one candidate's distance.  Each lane keeps its best two
 // (distance, index) keys; four warp reductions give the query's best two.
-constexpr int kPairThreads = 128;
+constexpr int kPairThreads = 64;
 constexpr int kPairWarps = kPairThreads / 32;
 constexpr int kRing = 64;  // candidate ring per warp: 32 waiting + 32 new
 constexpr int kChunkQ = 8; // queries per warp whose windows are computed in one pass
@@ -676,7 +676,7 @@ static __device__ __noinline__ bool exact_pair_p(const double *F, const double *
 
 // G lanes read a descriptor row, C 16-byte chunks each (a row is G C 16 bytes).
 template <int KIND, int G, int C, int MODE>
-__global__ void __launch_bounds__(kPairThreads, 6) stab_pair_kernel(Launch L) {
+__global__ void __launch_bounds__(kPairThreads, 12) stab_pair_kernel(Launch L) {
     static_assert(G >= 1 && G <= 16 && (G & (G - 1)) == 0, "lanes per descriptor row");
     constexpr int kPerRound = 32 / G;  // candidates per round of loads
     constexpr int kRow16 = G * C;      // 16-byte chunks per row
