@@ -296,29 +296,32 @@ egm_status choose_band(const Plan &pl, const egm_params &prm, bool csr, int sms,
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Banded-form scratch: query permutation, packed operand rows, norms (padded
+// Banded-form scratch: query permutation and sorted query records; with
+// float pairs (`packed`) also the packed operand rows and their norms (padded
 // for the aligned 16-byte bulk copies that read past a pair's last row).
+// Without float pairs the operand buffers keep one tile of rows, which the
+// band kernel's (unused) tensor maps cover.
 struct BandLayout {
-    size_t qperm, descA, descB, qbkt, qsrt, qscale, rnorm, rbin, total;
-    BandLayout(int64_t nq, int64_t nr) {
+    size_t qperm, descA, descB, qbkt, qsrt, qscale, rnorm, total;
+    BandLayout(int64_t nq, int64_t nr, bool packed) {
         const size_t rb = (size_t)band_row_bytes();
+        const int64_t ta = packed ? nq : band_tile_queries(), tb = packed ? nr : band_tile_queries();
         qperm = 0;
         descA = qperm + align256(sizeof(uint32_t) * (size_t)std::max<int64_t>(nq, 1));
-        descB = descA + align256(rb * (size_t)std::max<int64_t>(nq, 1));
-        qbkt = descB + align256(rb * (size_t)std::max<int64_t>(nr, 1));
+        descB = descA + align256(rb * (size_t)std::max<int64_t>(ta, 1));
+        qbkt = descB + align256(rb * (size_t)std::max<int64_t>(tb, 1));
         qsrt = qbkt + align256(sizeof(uint16_t) * (size_t)std::max<int64_t>(nq, 1));
         qscale = qsrt + align256(sizeof(QueryRec) * (size_t)std::max<int64_t>(nq, 1));
-        rnorm = qscale + align256(sizeof(float) * (size_t)std::max<int64_t>(nq, 1));
-        rbin = rnorm + align256(sizeof(float4) * (size_t)(nr + 64));
-        // 32 rows of padding: bulk copies of a 32-row box may run past the last row
-        total = rbin + align256(32 * (size_t)(nr + 64));
+        rnorm = qscale + align256(sizeof(float) * (size_t)std::max<int64_t>(packed ? nq : 1, 1));
+        // 64 rows of padding: bulk copies of a 32-row box may run past the last row
+        total = rnorm + align256(sizeof(float4) * (size_t)((packed ? nr : 0) + 64));
     }
 };
 
-cudaError_t reserve(Scratch &c_, int64_t nq, int64_t nr, int64_t ntab, int npairs, bool band) {
+cudaError_t reserve(Scratch &c_, int64_t nq, int64_t nr, int64_t ntab, int npairs, bool band, bool packed) {
     Scratch *c = &c_;
     cudaError_t e;
-    if (band && (e = grow(c->band, BandLayout(nq, nr).total)) != cudaSuccess) return e;
+    if (band && (e = grow(c->band, BandLayout(nq, nr, packed).total)) != cudaSuccess) return e;
     if ((e = grow(c->pairs, 2 * sizeof(PairDesc) * (size_t)std::max(npairs, 1) + 512)) != cudaSuccess) return e;
     if ((e = grow(c->geom, 2 * sizeof(PairGeom) * (size_t)std::max(npairs, 1) + 512)) != cudaSuccess) return e;
     if ((e = grow(c->offs, 2 * sizeof(int64_t) * offs_entries(npairs, nq) + 512)) != cudaSuccess) return e;
@@ -387,7 +390,7 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
     }
     L.max_n = pl.max_n;
     if (band) {
-        const BandLayout bl(pl.nq, pl.nr);
+        const BandLayout bl(pl.nq, pl.nr, pl.has_float);
         unsigned char *b = static_cast<unsigned char *>(c->band.ptr);
         L.qperm = reinterpret_cast<uint32_t *>(b + bl.qperm);
         L.descA = b + bl.descA;
@@ -395,7 +398,6 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
         L.qbkt = reinterpret_cast<uint16_t *>(b + bl.qbkt);
         L.qsrt = reinterpret_cast<QueryRec *>(b + bl.qsrt);
         L.rnorm = reinterpret_cast<float4 *>(b + bl.rnorm);
-        L.rbin = b + bl.rbin;
         L.qscale = reinterpret_cast<float *>(b + bl.qscale);
         L.fp8 = prm.float_pass == EGM_FLOAT_PASS_FP8;
         L.probe = prm.timeout_check;
@@ -523,7 +525,7 @@ cudaError_t enqueue_pipeline(const Launch &L, Scratch &sc, bool csr, int max_n, 
     EGM_Q(launch_sort(L, st));
     if (band) EGM_Q(cudaStreamWaitEvent(st, sidec->join_ev, 0));
     if (tc) EGM_Q(mark(tc, tb, 3));
-    if (band) EGM_Q(launch_pack(L, st));
+    if (band) EGM_Q(launch_pack(L, st));  // float pairs only
     if (tc) EGM_Q(mark(tc, tb, 4));
     if (band) {
         if (shape >= 0) EGM_Q(launch_band(L, sms, shape, st, false));
@@ -679,7 +681,7 @@ egm_status run_batch(egm_ctx *c, const egm_pair *pairs, int npairs, const egm_ou
     if ((s = choose_config(c, pl, npairs, csr, band, shape, tune)) != EGM_OK) return s;
     EGM_TRY(cudaSetDevice(c->device));
     if (band || tune) EGM_TRY(ensure_side(c));
-    EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, npairs, band || tune));
+    EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, npairs, band || tune, pl.has_float));
     c->sc.parity ^= 1;
     if (npairs > 1) EGM_TRY(upload_plan(c, pl, npairs));  // one pair: the plan rides in the launch
     cudaStream_t st = c->stream;
@@ -802,7 +804,7 @@ egm_status egm_reserve(egm_ctx *c, int64_t queries, int64_t refs, int32_t pairs)
     if (!c || queries < 0 || refs < 0 || pairs < 0) return EGM_ERR_ARG;
     EGM_TRY(cudaSetDevice(c->device));
     const int64_t ntab = 4 * refs + (int64_t)std::max(pairs, 1) * (2 * kLevels + 32);
-    EGM_TRY(reserve(c->sc, queries, refs, ntab, std::max(pairs, 1), true));
+    EGM_TRY(reserve(c->sc, queries, refs, ntab, std::max(pairs, 1), true, true));
     return EGM_OK;
 }
 
@@ -1203,7 +1205,7 @@ egm_status egm_intervals(egm_ctx *c, const egm_pair *pair, double *theta, double
     egm_status s = make_plan(&p, 1, pl);
     if (s != EGM_OK) return s;
     EGM_TRY(cudaSetDevice(c->device));
-    EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, 1, false));
+    EGM_TRY(reserve(c->sc, pl.nq, pl.nr, pl.ntab, 1, false, false));
     c->sc.parity ^= 1;
     EGM_TRY(upload_plan(c, pl, 1));
     Launch L = make_launch(c->sc, false, c->params, pl, 1, nullptr);
@@ -1240,7 +1242,7 @@ egm_status egm_graph_create(egm_ctx *c, const egm_pair *pairs, int32_t npairs, c
     if (!g) return EGM_ERR_NOMEM;
     g->ctx = c;
     cudaError_t e = band || tune ? ensure_side(c) : cudaSuccess;
-    if (e == cudaSuccess) e = reserve(g->sc, pl.nq, pl.nr, pl.ntab, npairs, band || tune);
+    if (e == cudaSuccess) e = reserve(g->sc, pl.nq, pl.nr, pl.ntab, npairs, band || tune, pl.has_float);
     const size_t ob = sizeof(int64_t) * pl.offs.size();
     std::vector<unsigned char> h(sizeof(PairDesc) * npairs + ob);
     memcpy(h.data(), pl.pd.data(), sizeof(PairDesc) * npairs);

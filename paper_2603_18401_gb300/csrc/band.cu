@@ -11,26 +11,29 @@
 //   query_sort_kernel  one block per pair: counting sort of the queries by
 //                      the top bits of their quantised line angle; lines
 //                      without an FP32 view (FP64-only, degenerate) last.
-//   pack_kernel        descriptor rows of the sorted references and queries
-//                      as 256-byte tensor-core operands, with their norms:
-//                        u8 (128 values)  -> BF16, exact (integers < 2^8)
-//                        float (128 FP32) -> BF16 (nearest), with the norm of
-//                          the rounded row and the rounding error |x - bf16(x)|
-//                      binary (256-bit) reference rows are copied in sorted
-//                      order as they are (32 bytes): their Hamming distances
-//                      are popcounts on the CUDA cores
+//                      Writes the sorted query records (index in the padding).
+//   pack_kernel        float pairs only: descriptor rows of the sorted
+//                      references and queries as 256-byte BF16 (or E4M3)
+//                      operands, with the norm of the rounded row and the
+//                      rounding error |x - x~|
 //   band_kernel        persistent; one tile of 128 sorted queries at a time.
 //                      Warps 0-3 (one thread per query) build the tile's band
-//                      from the hull of their windows; warp 4 issues TMA loads
-//                      (128-byte swizzle) of the query tile and of 32-row
-//                      boxes of the band, and the tcgen05.mma chain
-//                      (M = 128, N = 32 per box, K = 128 BF16 or 256 E4M3)
-//                      into a double-buffered TMEM accumulator; warps 0-3 read
-//                      their lanes back, run the exact test on the columns in
-//                      their own windows, and keep the best two by
-//                      (distance, index):
+//                      from the hull of their windows; warp 4 issues the bulk
+//                      loads of the band's sorted records (32-row boxes) and
+//                      the tcgen05.mma chain (M = 128, N = 32 per box, K = 128)
+//                      into a double-buffered TMEM accumulator.  Operands:
+//                        u8 rows     gathered by warps 0-3 straight from the
+//                                    caller's descriptors (cp.async, 128 bytes
+//                                    a row) and widened in shared memory to
+//                                    FP16, exact (integers < 2^11)
+//                        float rows  the packed BF16 / E4M3 rows, by TMA
+//                        binary rows gathered as they are (32 bytes); no
+//                                    product: Hamming distances are popcounts
+//                      Warps 0-3 read their lanes back, run the exact test on
+//                      the columns in their own windows, and keep the best two
+//                      by (distance, index):
 //                        L2^2    = |q|^2 + |r|^2 - 2 q.r   (integers < 2^24: exact in FP32)
-//                        Hamming = |q| + |r| - 2 q.r
+//                        Hamming = popcount(q xor r)
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -54,6 +57,7 @@ __global__ void __launch_bounds__(kQSortThreads) query_sort_kernel(Launch L) {
     __shared__ uint32_t hist[kQBuckets];
     __shared__ uint32_t wsum[kQSortThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (blockIdx.x == 0 && tid == 0) *L.work = 0u;  // the band kernel's tile dispenser
     const PairDesc &P = L.pairs[blockIdx.x];
     const int m = P.m;
     if (m == 0) return;
@@ -118,7 +122,17 @@ __global__ void __launch_bounds__(kQSortThreads) query_sort_kernel(Launch L) {
 #pragma unroll
         for (int k = 0; k < kQSortPer; k++) {
             const int i = i0 + k * kQSortThreads + tid;
-            if (v[k] != 0xffffu) L.qperm[P.q_off + atomicAdd(&hist[v[k]], 1u)] = (uint32_t)i;
+            if (v[k] != 0xffffu) {
+                const int64_t slot = P.q_off + atomicAdd(&hist[v[k]], 1u);
+                L.qperm[slot] = (uint32_t)i;
+                // the sorted record: query index and (float pairs, set by the
+                // pack kernel) norm and rounding error in the padding
+                QueryRec rq = L.qrec[P.q_off + i];
+                rq.pair = 0;
+                rq.pad[0] = (uint32_t)i;
+                rq.pad[1] = 0u;
+                L.qsrt[slot] = rq;
+            }
         }
     }
 }
@@ -127,18 +141,13 @@ __global__ void __launch_bounds__(kQSortThreads) query_sort_kernel(Launch L) {
 constexpr int kRowB = 256;  // packed operand row: 128 BF16 or 256 E4M3 values
 constexpr int kBinRowB = 32;  // binary row (256 bits), kept as it is
 
-__device__ __forceinline__ uint32_t bf16_pair(uint32_t lo, uint32_t hi) {
-    // bytes 0..255 are exact in FP32 and their BF16 is the top half of the FP32 word
-    return (__float_as_uint((float)lo) >> 16) | (__float_as_uint((float)hi) & 0xffff0000u);
-}
-
+// Float rows only (u8 and binary rows go to the band kernel as they are).
 // 8 threads per row; thread part t writes output bytes [32 t, 32 t + 32).
 // F8: float rows packed for the FP8 pass (a separate variant: its staged
 // values would cost the common variant registers and occupancy).
 template <bool F8>
 __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
     pdl_begin();
-    if (blockIdx.x == 0 && threadIdx.x == 0) *L.work = 0u;  // the band kernel's tile dispenser
     const int64_t rows = L.nr + L.nq;
     const int part = threadIdx.x & 7;
     __shared__ int64_t s_roffs[kSmemPairs + 1], s_qoffs[kSmemPairs + 1];
@@ -146,21 +155,24 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
     __syncthreads();
     for (int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; g0 < ((rows + 3) / 4) * 4;
          g0 += ((int64_t)gridDim.x * blockDim.x) >> 3) {
-        const bool valid = g0 < rows;
+        bool use = g0 < rows;  // a float row (every thread of the row's group agrees)
         const bool is_ref = g0 < L.nr;
-        uint32_t nrm = 0, qi = 0;
-        float fnrm = 0.0f, ferr = 0.0f;  // float rows: squared norm of the rounded row, squared rounding error
-        bool isf = false, isf8 = false;
+        uint32_t qi = 0;
+        float fnrm = 0.0f, ferr = 0.0f;  // squared norm of the rounded row, squared rounding error
         float xs8[16];                   // FP8 pass: this thread's 16 values, kept for the second step
         float amax = 0.0f;               //   and their largest magnitude
         uint4 o0 = make_uint4(0, 0, 0, 0), o1 = o0, qr = o0;
         uint8_t *dst = nullptr;
-        int rowkind = 0;                 // 0: 256-byte operand row at dst; 1: binary row at dst; 2: none
-        if (valid) {
-            const int64_t g = is_ref ? g0 : g0 - L.nr;
+        const int64_t g = is_ref ? g0 : g0 - L.nr;
+        const PairDesc *PP = nullptr;
+        if (use) {
             const int p = cached ? pair_of_shared(is_ref ? s_roffs : s_qoffs, L.npairs, g)
                                  : pair_of(is_ref ? L.r_offs : L.q_offs, L.npairs, g);
-            const PairDesc &P = L.pairs[p];
+            PP = L.pairs + p;
+            use = PP->kind == EGM_DESC_F32_L2;
+        }
+        if (use) {
+            const PairDesc &P = *PP;
             const uint8_t *src;
             if (is_ref) {
                 const uint32_t j = __float_as_uint(L.rec[g].w);
@@ -172,24 +184,9 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
                 dst = L.descA + g * kRowB;
                 if (part < 3) qr = __ldg(reinterpret_cast<const uint4 *>(L.qrec + P.q_off + qi) + part);
             }
-            if (P.kind == EGM_DESC_U8_L2) {
-                const uint4 w = __ldg(reinterpret_cast<const uint4 *>(src) + part);
-                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-                uint32_t out[8];
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const uint32_t b0 = ws[k] & 0xffu, b1 = (ws[k] >> 8) & 0xffu, b2 = (ws[k] >> 16) & 0xffu,
-                                   b3 = ws[k] >> 24;
-                    out[2 * k] = bf16_pair(b0, b1);
-                    out[2 * k + 1] = bf16_pair(b2, b3);
-                    nrm += b0 * b0 + b1 * b1 + b2 * b2 + b3 * b3;
-                }
-                o0 = make_uint4(out[0], out[1], out[2], out[3]);
-                o1 = make_uint4(out[4], out[5], out[6], out[7]);
-            } else if (F8 && P.kind == EGM_DESC_F32_L2) {
+            if (F8) {
                 // FP8 pass, step 1: 16 values per thread and their largest magnitude
                 // (the row's scale needs the maximum over its 8 threads)
-                isf = isf8 = true;
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
                     const float4 v = __ldg(reinterpret_cast<const float4 *>(src) + 4 * part + c);
@@ -199,9 +196,8 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
                     xs8[4 * c + 3] = v.w;
                     amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
                 }
-            } else if (P.kind == EGM_DESC_F32_L2) {
+            } else {
                 // 16 values per thread: 64 bytes in, 32 bytes of BF16 out
-                isf = true;
                 uint32_t out[8];
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
@@ -220,14 +216,6 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
                 }
                 o0 = make_uint4(out[0], out[1], out[2], out[3]);
                 o1 = make_uint4(out[4], out[5], out[6], out[7]);
-            } else if (is_ref) {
-                // binary: the row itself (32 bytes) in sorted order; Hamming
-                // distances are popcounts in the band kernel, no operand row
-                if (part < 2) o0 = __ldg(reinterpret_cast<const uint4 *>(src) + part);
-                dst = L.rbin + g * kBinRowB;
-                rowkind = 1;
-            } else {
-                rowkind = 2;  // binary query: its sorted record only
             }
         }
         // FP8 pass, step 2: the row's scale s = max |x| / 448 (E4M3's largest
@@ -239,7 +227,7 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
 #pragma unroll
             for (int o = 4; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o, 8));
         }
-        if (F8 && isf8) {
+        if (F8 && use) {
             const float inv = amax > 0.0f ? 448.0f / amax : 1.0f;
             scale = amax > 0.0f ? amax / 448.0f : 1.0f;
             uint32_t w[4] = {0u, 0u, 0u, 0u};
@@ -256,18 +244,13 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
         }
 #pragma unroll
         for (int o = 4; o > 0; o >>= 1) {
-            nrm += __shfl_xor_sync(0xffffffffu, nrm, o, 8);
             fnrm += __shfl_xor_sync(0xffffffffu, fnrm, o, 8);
             ferr += __shfl_xor_sync(0xffffffffu, ferr, o, 8);
         }
-        // norm of the operand row; for float rows also |x - x~|, rounded up
-        const float norm = isf ? fnrm : (float)nrm;
-        const float err = isf ? sqrtf(ferr) * 1.0001f + 1e-30f : 0.0f;
-        if (valid) {
-            if (rowkind == 1) {
-                if (part < 2) reinterpret_cast<uint4 *>(dst)[part] = o0;
-            } else if (rowkind == 2) {
-            } else if (F8 && isf8) {
+        // norm of the operand row and |x - x~|, rounded up
+        const float err = sqrtf(ferr) * 1.0001f + 1e-30f;
+        if (use) {
+            if (F8) {
                 // 16 bytes per thread: bytes [16 part, 16 part + 16), zeros above 128
                 reinterpret_cast<uint4 *>(dst)[part] = o0;
                 reinterpret_cast<uint4 *>(dst)[8 + part] = make_uint4(0u, 0u, 0u, 0u);
@@ -276,7 +259,7 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
                 reinterpret_cast<uint4 *>(dst)[2 * part + 1] = o1;
             }
             if (is_ref) {
-                if (part == 0 && rowkind == 0) L.rnorm[g0] = make_float4(norm, err, scale, 0.0f);
+                if (part == 0) L.rnorm[g0] = make_float4(fnrm, err, scale, 0.0f);
             } else if (part < 3) {
                 if (part == 0) L.qscale[g0 - L.nr] = scale;
                 // sorted query record; the padding carries the query index and the
@@ -284,7 +267,7 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
                 if (part == 2) {
                     qr.y = __float_as_uint(err);
                     qr.z = qi;
-                    qr.w = __float_as_uint(norm);
+                    qr.w = __float_as_uint(fnrm);
                 }
                 reinterpret_cast<uint4 *>(L.qsrt + (g0 - L.nr))[part] = qr;
             }
@@ -308,33 +291,41 @@ struct __align__(16) Piece {
     int32_t li;
 };
 
+constexpr uint32_t kOperandArrivals = 5; // fullB / afull: the control thread and the four epilogue warps
+
 template <int CB>
 struct BandSmem {
     static constexpr int kCN = kBoxR * CB;  // columns per chunk
-    uint8_t A[2][kTM * 128];      // query tile, K halves (1024-byte aligned)
-    uint8_t B[2][2][kCN * 128];   // band chunk: stage, K half
+    // query tile, K halves (1024-byte aligned); u8 tiles stage each query's
+    // bytes in its own row of A[1] before widening them
+    uint8_t A[2][kTM * 128];
+    // band chunk: stage, K half.  u8 tiles stage a chunk's gathered bytes in
+    // K half 1 of its stage; binary tiles keep four chunks of 32-byte rows
+    // (chunk c in slot c mod 4) in B[0][0]
+    uint8_t B[2][2][kCN * 128];
     // The record stages are idle while a tile's windows are computed (every
     // load of the previous tile has landed and been read, and the next ones
     // are issued after), so the per-warp hulls share their memory.
     union {
         struct {
             float4 rec[2][kCN];       // (x - cx, y - cy, eps, index) of each column
-            float4 rn[2][CB][kBoxR];  // (norm, rounding error, row scale, 0) of each box's rows
+            float4 rn[2][CB][kBoxR];  // float rows: (norm, rounding error, row scale, 0) of each box's rows
+            float n8[4][kCN];         // u8 rows: squared norms, chunk c in slot c mod 4
         } io;
         struct {
             float wlo[4][kLevels], whi[4][kLevels];  // each epilogue warp's hull per level index
             int32_t wkind[4][kLevels];
         } hull;
     } u;
-    // fullB: a stage's operand rows landed; sfree: the MMA that read them is
-    // done; fullR: a stage's records and norms landed; done: an accumulator is
+    // fullB: a stage's operand rows are in place (TMA landed, or the epilogue
+    // warps wrote them); sfree: the MMA that read them is done; fullR: a
+    // stage's records (and float norms) landed; done: an accumulator is
     // ready; tfree: the epilogue has read it and the stage's records
     uint64_t fullB[2], sfree[2], fullR[2], done[2], tfree[2], afull;
     uint64_t probe;               // never arrived on: the wait of the timeout check (Launch::probe)
     PairGeom g;
     PairDesc pd;
     Piece pc[2 * kLevels];
-    uint2 wr[4][kLevels][2];      // each epilogue warp's window ranges per level index
     int32_t lv[kLevels];
     int32_t nlev, npc, nbox, gpair;
     int32_t tile;                 // the tile being processed, then the next one
@@ -496,6 +487,34 @@ __device__ __forceinline__ void top2(unsigned long long key, unsigned long long 
     }
 }
 
+// ---- u8 rows as FP16 tensor-core operands.  For a byte b, the halfword
+// 0x6400 | b is the FP16 number 1024 + b (spacing 1 in [1024, 2048)), so one
+// packed subtraction of 1024 gives b exactly; products of such integers and
+// their sums of 128 terms (below 2^24) are exact in the FP32 accumulator.
+__device__ __forceinline__ uint32_t h2_minus_1024(uint32_t x) {
+    uint32_t y;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(y) : "r"(x), "r"(0x64006400u));
+    return y;
+}
+
+// 16 bytes in, their FP16 values out (o0: bytes 0-7, o1: bytes 8-15); adds
+// the bytes' squared sum to nrm.
+__device__ __forceinline__ void widen16(const uint4 w, uint4 &o0, uint4 &o1, uint32_t &nrm) {
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+    uint32_t o[8];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        o[2 * k] = h2_minus_1024(__byte_perm(ws[k], 0x64u, 0x4140u));
+        o[2 * k + 1] = h2_minus_1024(__byte_perm(ws[k], 0x64u, 0x4342u));
+        nrm = __dp4a(ws[k], ws[k], nrm);
+    }
+    o0 = make_uint4(o[0], o[1], o[2], o[3]);
+    o1 = make_uint4(o[4], o[5], o[6], o[7]);
+}
+
+// Byte offset of 16-byte chunk c of row r in a 128-byte-swizzled operand tile.
+__device__ __forceinline__ uint32_t sw128(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
 // FLT: float descriptor pairs may occur (compiled out otherwise: the rerank
 // state costs registers).
 template <int CB, int CPS, bool FLT>
@@ -515,21 +534,23 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
     const bool ctl = tid == kTM;
     if (ctl) {
         for (int s = 0; s < 2; s++) {
-            tc::mbar_init(&S.fullB[s], 1);
+            tc::mbar_init(&S.fullB[s], kOperandArrivals);
             tc::mbar_init(&S.sfree[s], 1);
             tc::mbar_init(&S.fullR[s], 1);
             tc::mbar_init(&S.done[s], 1);
             tc::mbar_init(&S.tfree[s], 4);
         }
-        tc::mbar_init(&S.afull, 1);
+        tc::mbar_init(&S.afull, kOperandArrivals);
         tc::mbar_init(&S.probe, 1);
         tc::fence_mbar_init();
         S.err = 0;
         S.gpair = -1;
         const uint32_t k = atomicAdd(L.work, 1u);
         S.tile = k < (uint64_t)L.ntiles ? L.tile_seq[k] : -1;
-        tc::prefetch_tmap(&tmA);
-        tc::prefetch_tmap(&tmB);
+        if (FLT) {
+            tc::prefetch_tmap(&tmA);
+            tc::prefetch_tmap(&tmB);
+        }
     }
     if (warp == 4) {
         tc::tmem_alloc(&S.tmem, kTmemCols);
@@ -549,9 +570,11 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
     };
     uint32_t seq = 0;
     unsigned long long nwin = 0, ncand = 0, nexact = 0;
-    // phases the control thread armed on each barrier (copies and MMAs issued):
-    // after a failed wait, the CTA lets them complete before it leaves
+    // phases the control thread armed on each barrier (copies and MMAs issued)
+    // and whether the last one carries copies: after a failed wait, the CTA
+    // lets them complete before it leaves
     uint32_t armB[2] = {0u, 0u}, armR[2] = {0u, 0u}, armD[2] = {0u, 0u}, armA = 0u;
+    bool txB[2] = {false, false}, txA = false;
     if (L.probe) {
         // the timeout check: a short wait on a barrier that nothing arrives
         // on, before any copy or MMA is issued, takes the error path below
@@ -572,7 +595,8 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         const int64_t q_off = L.q_offs[p];
         const int64_t t0 = (tile - L.tile_offs[p]) * kTM;  // first sorted slot of the tile
         const int mt = (int)min((int64_t)kTM, L.q_offs[p + 1] - q_off - t0);
-        // ---- the tile's queries (sorted records: index and norm in the padding)
+        // ---- the tile's queries (sorted records: index, and for float rows
+        // norm and rounding error, in the padding)
         QueryRec r;
         const bool qv = warp < 4 && tid < mt;
         if (qv) {
@@ -584,16 +608,32 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             r.pad[0] = r.pad[1] = 0;
         }
         const uint32_t qi = r.pad[0];
-        const float qn = __uint_as_float(r.pad[1]);
+        float qn = __uint_as_float(r.pad[1]);
         const float qerr = __uint_as_float((uint32_t)r.pair);  // float rows: |q - q~|
-        const float qs = FLT && qv ? L.qscale[q_off + t0 + tid] : 1.0f;  // row scale of the FP8 pass
-        // binary pairs: Hamming distances by popcount, no operand rows
-        const bool pop = __ldg(&L.pairs[p].kind) == EGM_DESC_BIN;
+        const int kind = __ldg(&L.pairs[p].kind);
+        // binary pairs: Hamming distances by popcount, no operand rows; float
+        // pairs: packed rows by TMA; u8 pairs: rows widened here
+        const bool pop = kind == EGM_DESC_BIN;
+        const bool flt = FLT && kind == EGM_DESC_F32_L2;
+        const bool cvt = !pop && !flt;
+        const float qs = flt && qv ? L.qscale[q_off + t0 + tid] : 1.0f;  // row scale of the FP8 pass
         if (ctl && !pop) {
-            tc::mbar_arrive_expect_tx(&S.afull, 2 * kTM * 128);
+            if (flt) {
+                tc::mbar_arrive_expect_tx(&S.afull, 2 * kTM * 128);
+                tc::tma_load_2d(S.A[0], &tmA, 0, (int32_t)(q_off + t0), &S.afull);
+                tc::tma_load_2d(S.A[1], &tmA, 128, (int32_t)(q_off + t0), &S.afull);
+            } else {
+                tc::mbar_arrive(&S.afull);
+            }
             armA++;
-            tc::tma_load_2d(S.A[0], &tmA, 0, (int32_t)(q_off + t0), &S.afull);
-            tc::tma_load_2d(S.A[1], &tmA, 128, (int32_t)(q_off + t0), &S.afull);
+            txA = flt;
+        }
+        // a u8 query's bytes: staged in its thread's row of A[1], widened once
+        // the windows are known (the copy's latency hides behind them)
+        if (cvt && qv) {
+            const uint8_t *qrow = L.pairs[p].desc1 + (int64_t)qi * 128;
+#pragma unroll
+            for (int k = 0; k < 8; k++) tc::cp_async16(S.A[1] + tid * 128 + 16 * k, qrow + 16 * k);
         }
         // a binary query's row, in the idle query-tile buffer (its thread's slot)
         uint4 *qbrow = reinterpret_cast<uint4 *>(S.A[0] + tid * kBinRowB);
@@ -645,7 +685,9 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             }
         }
         __syncthreads();
-        // ---- windows as sorted positions: warps 0-3 their own, warp 4 the tile's (lane = level index)
+        // ---- windows as sorted positions: warps 0-3 their own (kept by the
+        // lane of the level index: wr0, wr1), warp 4 the tile's
+        uint2 wr0 = make_uint2(0u, 0u), wr1 = wr0;
         {
             const int li = lane;
             KeyWin w;
@@ -682,8 +724,8 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             const Window wn = window_ranges(wk, a, b);
             if (warp < 4) {
                 if (li < nlev) {
-                    S.wr[warp][li][0] = make_uint2(wn.b0, wn.len0);
-                    S.wr[warp][li][1] = make_uint2(wn.b1, wn.len1);
+                    wr0 = make_uint2(wn.b0, wn.len0);
+                    wr1 = make_uint2(wn.b1, wn.len1);
                 }
             } else {
                 const bool h0 = li < nlev && wn.len0 > 0, h1 = li < nlev && wn.len1 > 0;
@@ -729,24 +771,26 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         const int nchunk = (nbox + kCB - 1) / kCB;
 
         if (ctl) {
-            // ---- control.  Operand rows of chunk c + 2 load once the MMA of
-            // chunk c has read its stage; the records and norms of chunk c load
-            // once the epilogue has finished chunk c - 2 (it reads them too).
-            // At a tile start every stage and accumulator is free.
+            // ---- control.  The operand stage of chunk c + 2 opens once the
+            // MMA of chunk c has read it (TMA rows: loaded then; u8 and binary
+            // rows: written by the epilogue warps, which also arrive); the
+            // records and float norms of chunk c load once the epilogue has
+            // finished chunk c - 2.  At a tile start every stage and
+            // accumulator is free.
             BoxCursor curB, curR;
             auto issueB = [&](int c) {
                 const uint32_t sq = seq + (uint32_t)c, st = sq & 1u, use = sq >> 1;
-                if (c >= 2 && !wait(&S.sfree[st], (use - 1) & 1u)) return;
-                const int nb = min(kCB, nbox - c * kCB);
-                if (pop) {
-                    // no operand rows: the phase completes at once (every barrier
-                    // keeps one phase per use of its stage)
+                if (!flt) {
                     tc::mbar_arrive(&S.fullB[st]);
                     armB[st]++;
+                    txB[st] = false;
                     return;
                 }
+                if (c >= 2 && !wait(&S.sfree[st], (use - 1) & 1u)) return;
+                const int nb = min(kCB, nbox - c * kCB);
                 tc::mbar_arrive_expect_tx(&S.fullB[st], (uint32_t)nb * (2 * kBoxR * 128));
                 armB[st]++;
+                txB[st] = true;
                 for (int bb = 0; bb < nb; bb++) {
                     uint32_t pos, len;
                     int li;
@@ -759,10 +803,8 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             auto issueR = [&](int c) {
                 const uint32_t st = (seq + (uint32_t)c) & 1u;
                 const int nb = min(kCB, nbox - c * kCB);
-                // records, and the norms (operand tiles) or the binary rows, which
-                // take the idle operand stage (popcount tiles)
-                const uint32_t extra = pop ? kBoxR * kBinRowB : kBoxR * 16;
-                tc::mbar_arrive_expect_tx(&S.fullR[st], (uint32_t)nb * (kBoxR * 16 + extra));
+                // records, and the norms of float rows
+                tc::mbar_arrive_expect_tx(&S.fullR[st], (uint32_t)nb * (kBoxR * 16) * (flt ? 2u : 1u));
                 armR[st]++;
                 for (int bb = 0; bb < nb; bb++) {
                     uint32_t pos, len;
@@ -770,19 +812,16 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                     curR.next(S, pos, len, li);
                     const int64_t row = P.r_off + pos;
                     tc::bulk_load(&S.u.io.rec[st][bb * kBoxR], L.rec + row, kBoxR * 16, &S.fullR[st]);
-                    if (pop)
-                        tc::bulk_load(S.B[st][0] + bb * kBoxR * kBinRowB, L.rbin + row * kBinRowB, kBoxR * kBinRowB,
-                                      &S.fullR[st]);
-                    else
-                        tc::bulk_load(&S.u.io.rn[st][bb][0], L.rnorm + row, kBoxR * 16, &S.fullR[st]);
+                    if (flt) tc::bulk_load(&S.u.io.rn[st][bb][0], L.rnorm + row, kBoxR * 16, &S.fullR[st]);
                 }
             };
             for (int c = 0; c < nchunk && c < 2; c++) {
-                issueB(c);
                 issueR(c);
+                issueB(c);
             }
-            // E4M3 operands: float rows of the FP8 pass
-            const bool bin = FLT && L.fp8 && P.kind == EGM_DESC_F32_L2;
+            // operand types: E4M3 (float rows of the FP8 pass), BF16 (float
+            // rows), FP16 (u8 rows)
+            const bool e4m3 = flt && L.fp8;
             for (int c = 0; c < nchunk; c++) {
                 const uint32_t sq = seq + (uint32_t)c, st = sq & 1u, use = sq >> 1;
                 bool ok = true;
@@ -803,15 +842,17 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 }
                 tc::tc_fence_after();
                 const int nb = min(kCB, nbox - c * kCB);
-                const uint32_t idesc = bin ? tc::idesc_e4m3(kTM, nb * kBoxR) : tc::idesc_bf16(kTM, nb * kBoxR);
+                const uint32_t idesc = e4m3  ? tc::idesc_e4m3(kTM, nb * kBoxR)
+                                       : flt ? tc::idesc_bf16(kTM, nb * kBoxR)
+                                             : tc::idesc_f16(kTM, nb * kBoxR);
                 const uint32_t dcol = tmem + st * kCN;
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
                     const int h = k >> 2, kk = k & 3;
                     const uint64_t ad = tc::sdesc_sw128(tc::smem_addr(S.A[h]) + 32 * kk);
                     const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(S.B[st][h]) + 32 * kk);
-                    if (bin) tc::mma_e4m3(dcol, ad, bd, idesc, k > 0);
-                    else tc::mma_bf16(dcol, ad, bd, idesc, k > 0);
+                    if (e4m3) tc::mma_e4m3(dcol, ad, bd, idesc, k > 0);
+                    else tc::mma_f16(dcol, ad, bd, idesc, k > 0);
                 }
                 tc::mma_commit(&S.done[st]);
                 tc::mma_commit(&S.sfree[st]);
@@ -822,192 +863,338 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             if (nchunk == 0 && !pop) wait(&S.afull, (armA - 1u) & 1u);
         }
 
-        // ---- epilogue: tests and best two over this warp's columns
+        // ---- epilogue warps: operand rows, tests and best two over this warp's columns
         unsigned long long b1 = ~0ull, b2 = ~0ull;
-        const bool isf = FLT && P.kind == EGM_DESC_F32_L2;
+        const bool isf = flt;
         FBuf fb;
         fb.init();
-        if (warp < 4 && nchunk > 0) {
-            BoxCursor cur;
-            const bool exact_only = (r.flags & kQExactOnly) != 0;
-            const bool live = qv && !(r.flags & EGM_FLAG_DEGENERATE_LINE);
-            const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
-            // The pre-test bound of the plain kernel, 9.6e-7 S + 1.2e-7 eps + E1 (|x| + |y| + 2 eps)
-            // + E0 + 1e-9 with S = |A x| + |B y| + |C|, taken with |A|, |B| <= 1 (the line is
-            // normalised): bound = k1 (|x| + |y|) + ke eps + k0, never smaller.
-            const float k1 = 9.6e-7f * 1.00001f + r.E1;
-            const float ke = 1.2e-7f + 2.0f * r.E1;
-            const float k0 = fmaf(9.6e-7f, fabsf(r.C), r.E0 + 1e-9f);
-            for (int c = 0; c < nchunk; c++) {
-                const uint32_t sq = seq + (uint32_t)c, st = sq & 1u;
-                const bool ok = wait(&S.done[st], (sq >> 1) & 1u) && wait(&S.fullR[st], (sq >> 1) & 1u);
-                tc::tc_fence_after();
-                const int nb = min(kCB, nbox - c * kCB);
-                for (int bb = 0; bb < nb; bb++) {
-                    uint32_t pos, len;
-                    int li;
-                    cur.next(S, pos, len, li);
-                    if (!ok) continue;
-                    // columns of this box inside the warp's own windows
-                    const uint2 w0 = S.wr[warp][li][0], w1 = S.wr[warp][li][1];
-                    const int x0 = (int)max(pos, w0.x) - (int)pos;
-                    const int x1 = (int)min(pos + len, w0.x + w0.y) - (int)pos;
-                    const int y0 = (int)max(pos, w1.x) - (int)pos;
-                    const int y1 = (int)min(pos + len, w1.x + w1.y) - (int)pos;
-                    if (x1 <= x0 && y1 <= y0) continue;
-                    const float4 *rnb = &S.u.io.rn[st][bb][0];
-                    const float4 *recb = &S.u.io.rec[st][bb * kBoxR];
-                    const uint32_t tb = tmem + lanebase + st * kCN + bb * kBoxR;
-                    // the box's columns inside the warp's windows, as a bit mask
-                    auto span = [](int a, int b) {
-                        a = max(a, 0);
-                        b = min(b, kBoxR);
-                        return b <= a ? 0u : (b - a >= 32 ? ~0u : ((1u << (b - a)) - 1u) << a);
-                    };
-                    const uint32_t inbox = live ? (span(x0, x1) | span(y0, y1)) : 0u;
-#pragma unroll 1
-                    for (int g = 0; g < kBoxR; g += kGroup) {
-                        if (!__any_sync(0xffffffffu, (inbox >> g) & 0xffu)) continue;
-                        // the group's records, loaded together with its accumulators
-                        float4 rcs[kGroup];
+        if (warp < 4) {
+            // Rows of chunk c + 2, fetched while chunk c is tested: the row
+            // indices (loaded one chunk earlier) pick the rows; u8 bytes go to
+            // K half 1 of the operand stage of chunk c (its MMA is done) and
+            // are widened to FP16 in place (4 threads a row, 32 bytes each),
+            // their norms to slot c + 2 mod 4; binary rows go to slot c + 2
+            // mod 4 (2 threads a row).  The epilogue of chunk c - 2, the last
+            // reader of those slots, has ended in every warp: the MMA of chunk
+            // c waited for it.
+            const int grow = cvt ? (tid >> 2) : (tid >> 1);  // the row this thread copies in each box
+            const int gpart = cvt ? (tid & 3) : (tid & 1);
+            const bool gthr = cvt || (pop && tid < 2 * kBoxR);
+            BoxCursor curJ;
+            // row indices of chunk c (all ones: no row)
+            auto jload = [&](int c, uint32_t (&jj)[kCB]) {
+                const int nb = c < nchunk ? min(kCB, nbox - c * kCB) : 0;
 #pragma unroll
-                        for (int k = 0; k < kGroup; k++) rcs[k] = recb[g + k];
-                        uint32_t v[kGroup];
-                        if (!pop) {
-                            tc::tmem_ld8(tb + g, v);
-                            tc::tmem_wait_ld();
-                        }
-                        // membership of all columns first, branch-free (independent
-                        // work for the scheduler); then the few candidates
-                        const uint32_t gm = (inbox >> g) & 0xffu;
-                        uint32_t cm = 0, um = 0;  // FP32 sure members; members or inconclusive
-#pragma unroll
-                        for (int k = 0; k < kGroup; k++) {
-                            const float x = rcs[k].x, y = rcs[k].y, e = rcs[k].z;
-                            const float d = fabsf(fmaf(r.A, x, fmaf(r.B, y, r.C)));
-                            const float bound = fmaf(k1, fabsf(x) + fabsf(y), fmaf(ke, e, k0));
-                            cm |= (uint32_t)(d <= e - bound) << k;
-                            um |= (uint32_t)(d <= e + bound) << k;
-                        }
-                        if (exact_only) {
-                            cm = 0u;
-                            um = 0xffu;
-                        }
-                        cm &= gm;
-                        uint32_t exm = um & ~cm & gm;  // left to the FP64 expression
-                        nwin += __popc(gm);
-                        // FP32 inconclusive: the brute-force FP64 expression decides
-                        for (uint32_t m = exm; m; m &= m - 1u) {
-                            const int k = __ffs(m) - 1;
-                            nexact++;
-                            if (exact_pair(P, qi, __float_as_uint(recb[g + k].w))) cm |= 1u << k;
-                        }
-                        if (pop) {
-                            // Hamming distance of the binary rows by popcount
-                            for (; cm; cm &= cm - 1u) {
-                                const int k = __ffs(cm) - 1;
-                                const uint4 *rb = reinterpret_cast<const uint4 *>(
-                                    S.B[st][0] + (bb * kBoxR + g + k) * kBinRowB);
-                                const uint4 r0 = rb[0], r1 = rb[1], q0 = qbrow[0], q1 = qbrow[1];
-                                const uint32_t h = __popc(q0.x ^ r0.x) + __popc(q0.y ^ r0.y) + __popc(q0.z ^ r0.z) +
-                                                   __popc(q0.w ^ r0.w) + __popc(q1.x ^ r1.x) + __popc(q1.y ^ r1.y) +
-                                                   __popc(q1.z ^ r1.z) + __popc(q1.w ^ r1.w);
-                                ncand++;
-                                top2(((unsigned long long)h << 32) | __float_as_uint(recb[g + k].w), b1, b2);
-                            }
-                        }
-                        for (; cm; cm &= cm - 1u) {
-                            const int k = __ffs(cm) - 1;
-                            uint32_t vk = v[0], jk = __float_as_uint(rcs[0].w);
-#pragma unroll
-                            for (int t = 1; t < kGroup; t++)
-                                if (k == t) {
-                                    vk = v[t];
-                                    jk = __float_as_uint(rcs[t].w);
-                                }
-                            const float4 rk = rnb[g + k];
-                            ncand++;
-                            // the accumulator holds the product of the scaled rows (scales 1
-                            // except in the FP8 pass)
-                            const float dist = qn + rk.x - 2.0f * ((qs * rk.z) * __uint_as_float(vk));
-                            if (!isf) {
-                                // integer distances: exact
-                                top2(((unsigned long long)(uint32_t)dist << 32) | jk, b1, b2);
-                            } else {
-                                // distance of the BF16-rounded rows, bracketed around the FP32
-                                // distance the rerank will compute
-                                float lo, hi;
-                                float_bounds(dist, qn, rk.x, qerr, rk.y, lo, hi);
-                                fb.insert(lo, hi, jk);
-                            }
-                        }
+                for (int bb = 0; bb < kCB; bb++) {
+                    jj[bb] = ~0u;
+                    if (bb < nb) {
+                        uint32_t pos, len;
+                        int li;
+                        curJ.next(S, pos, len, li);
+                        if (gthr && (uint32_t)grow < len)
+                            jj[bb] = __float_as_uint(__ldg(&L.rec[P.r_off + pos + grow].w));
                     }
                 }
-                tc::tc_fence_before();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&S.tfree[st]);
-            }
-            if (isf) {
-                // FP32 rerank, one query of the warp at a time, the lanes over the
-                // dimensions: the candidates that can be among the best two, or
-                // (buffer overflow) every reference in the warp's windows
-                const bool live = qv && !(r.flags & EGM_FLAG_DEGENERATE_LINE);
-                const bool complete = fb.complete();
-                const bool exact_only = (r.flags & kQExactOnly) != 0;
-                for (int q = 0; q < 32; q++) {
-                    if (!__shfl_sync(0xffffffffu, (int)live, q)) continue;
-                    const uint32_t qiq = __shfl_sync(0xffffffffu, qi, q);
-                    const float4 qv4 = __ldg(reinterpret_cast<const float4 *>(P.desc1 + (int64_t)qiq * 512) + lane);
-                    unsigned long long k1 = ~0ull, k2 = ~0ull;
-                    if (__shfl_sync(0xffffffffu, (int)complete, q)) {
-                        const float U2q = __shfl_sync(0xffffffffu, fb.U2, q);
+            };
+            // copies of chunk c's rows; returns the boxes whose row this thread copied
+            auto gather_issue = [&](int c, const uint32_t (&jj)[kCB]) {
+                const uint32_t gs = seq + (uint32_t)c;
+                uint32_t gv = 0;
 #pragma unroll
-                        for (int t = 0; t < kFBuf; t++) {
-                            const float Lt = __shfl_sync(0xffffffffu, fb.L[t], q);
-                            const uint32_t jt = __shfl_sync(0xffffffffu, fb.J[t], q);
-                            if (Lt <= U2q) {
-                                const float d = coop_dist(qv4, P.desc2 + (int64_t)jt * 512, lane);
-                                top2(((unsigned long long)__float_as_uint(d) << 32) | jt, k1, k2);
-                            }
+                for (int bb = 0; bb < kCB; bb++) {
+                    const uint32_t j = jj[bb];
+                    if (j >= (uint32_t)P.n) continue;  // no row (or out of range: never copied)
+                    if (cvt) {
+                        const uint8_t *src = P.desc2 + (int64_t)j * 128 + gpart * 32;
+                        uint8_t *dst = S.B[gs & 1u][1] + (bb * kBoxR + grow) * 128 + gpart * 32;
+                        tc::cp_async16(dst, src);
+                        tc::cp_async16(dst + 16, src + 16);
+                        gv |= 1u << bb;
+                    } else if (pop) {
+                        tc::cp_async16(S.B[0][0] + ((c & 3) * kCN + bb * kBoxR + grow) * kBinRowB + gpart * 16,
+                                       P.desc2 + (int64_t)j * kBinRowB + gpart * 16);
+                    }
+                }
+                return gv;
+            };
+            // chunk c's rows in place (u8: widened, norms) and the warp's arrival
+            auto gather_finish = [&](int c, uint32_t gv) {
+                const uint32_t gs = seq + (uint32_t)c;
+                tc::cp_async_wait_all();
+                if (cvt) {
+                    const int nb = min(kCB, nbox - c * kCB);
+#pragma unroll
+                    for (int bb = 0; bb < kCB; bb++) {
+                        if (bb >= nb) break;
+                        const int R = bb * kBoxR + grow;
+                        uint4 x0 = make_uint4(0u, 0u, 0u, 0u), x1 = x0;
+                        const uint8_t *stg = S.B[gs & 1u][1] + R * 128 + gpart * 32;
+                        if ((gv >> bb) & 1u) {
+                            x0 = *reinterpret_cast<const uint4 *>(stg);
+                            x1 = *reinterpret_cast<const uint4 *>(stg + 16);
                         }
-                    } else {
-                        const float qA = __shfl_sync(0xffffffffu, r.A, q), qB = __shfl_sync(0xffffffffu, r.B, q);
-                        const float qC = __shfl_sync(0xffffffffu, r.C, q);
-                        const float qE0 = __shfl_sync(0xffffffffu, r.E0, q), qE1 = __shfl_sync(0xffffffffu, r.E1, q);
-                        const bool qex = __shfl_sync(0xffffffffu, (int)exact_only, q) != 0;
-                        for (int li = 0; li < nlev; li++)
-                            for (int h = 0; h < 2; h++) {
-                                const uint2 w = S.wr[warp][li][h];
-                                for (uint32_t b0 = 0; b0 < w.y; b0 += 32) {
-                                    const bool valid = b0 + (uint32_t)lane < w.y;
-                                    uint32_t j = 0;
-                                    int m = 0;
-                                    if (valid) {
-                                        const float4 rc = L.rec[P.r_off + w.x + b0 + lane];
-                                        j = __float_as_uint(rc.w);
-                                        m = qex ? 2 : member32(qA, qB, qC, qE0, qE1, rc);
-                                        if (m == 2) m = exact_pair(P, qiq, j) ? 1 : 0;
-                                    }
-                                    for (uint32_t bal = __ballot_sync(0xffffffffu, m == 1); bal; bal &= bal - 1u) {
-                                        const uint32_t jt = __shfl_sync(0xffffffffu, j, __ffs(bal) - 1);
-                                        const float d = coop_dist(qv4, P.desc2 + (int64_t)jt * 512, lane);
-                                        top2(((unsigned long long)__float_as_uint(d) << 32) | jt, k1, k2);
-                                    }
+                        // the row's four threads (lanes of this warp) have read its
+                        // staged bytes before K half 1 overwrites them
+                        __syncwarp();
+                        uint32_t nrm = 0;
+                        uint4 o0, o1, o2, o3;
+                        widen16(x0, o0, o1, nrm);
+                        widen16(x1, o2, o3, nrm);
+                        // bytes [32 part, 32 part + 32) are values of K half part / 2,
+                        // chunks 4 (part mod 2) .. + 3 of the row
+                        uint8_t *dh = S.B[gs & 1u][gpart >> 1];
+                        const int c0 = 4 * (gpart & 1);
+                        *reinterpret_cast<uint4 *>(dh + sw128(R, c0)) = o0;
+                        *reinterpret_cast<uint4 *>(dh + sw128(R, c0 + 1)) = o1;
+                        *reinterpret_cast<uint4 *>(dh + sw128(R, c0 + 2)) = o2;
+                        *reinterpret_cast<uint4 *>(dh + sw128(R, c0 + 3)) = o3;
+                        nrm += __shfl_xor_sync(0xffffffffu, nrm, 1);
+                        nrm += __shfl_xor_sync(0xffffffffu, nrm, 2);
+                        if (gpart == 0) S.u.io.n8[c & 3][R] = (float)nrm;
+                    }
+                    tc::fence_proxy_async();
+                }
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&S.fullB[gs & 1u]);
+            };
+            // the row indices of chunks 0 and 1 load while the query rows are widened
+            uint32_t jc[kCB], jn[kCB];
+            jload(0, jc);
+            jload(1, jn);
+            if (!pop) {
+                if (cvt) {
+                    tc::cp_async_wait_all();
+                    // own row only: K half 0 from staged chunks 0-3, then half 1
+                    // (over the staged bytes) from chunks 4-7
+                    uint32_t nq = 0;
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        uint4 w[4];
+#pragma unroll
+                        for (int k = 0; k < 4; k++)
+                            w[k] = qv ? *reinterpret_cast<const uint4 *>(S.A[1] + tid * 128 + 16 * (4 * h + k))
+                                      : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            uint4 o0, o1;
+                            widen16(w[k], o0, o1, nq);
+                            *reinterpret_cast<uint4 *>(S.A[h] + sw128(tid, 2 * k)) = o0;
+                            *reinterpret_cast<uint4 *>(S.A[h] + sw128(tid, 2 * k + 1)) = o1;
+                        }
+                    }
+                    qn = (float)nq;
+                    tc::fence_proxy_async();
+                }
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&S.afull);
+            }
+            if (nchunk > 0) {
+                // chunks 0 and 1 before the loop (both stages are free at a tile start)
+                const uint32_t gv0 = gather_issue(0, jc);
+                const uint32_t gv1 = nchunk > 1 ? gather_issue(1, jn) : 0u;
+                jload(2, jc);
+                gather_finish(0, gv0);
+                if (nchunk > 1) gather_finish(1, gv1);
+                BoxCursor cur;
+                const bool exact_only = (r.flags & kQExactOnly) != 0;
+                const bool live = qv && !(r.flags & EGM_FLAG_DEGENERATE_LINE);
+                const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
+                // The pre-test bound of the plain kernel, 9.6e-7 S + 1.2e-7 eps + E1 (|x| + |y| + 2 eps)
+                // + E0 + 1e-9 with S = |A x| + |B y| + |C|, taken with |A|, |B| <= 1 (the line is
+                // normalised): bound = k1 (|x| + |y|) + ke eps + k0, never smaller.
+                const float k1 = 9.6e-7f * 1.00001f + r.E1;
+                const float ke = 1.2e-7f + 2.0f * r.E1;
+                const float k0 = fmaf(9.6e-7f, fabsf(r.C), r.E0 + 1e-9f);
+                for (int c = 0; c < nchunk; c++) {
+                    const uint32_t sq = seq + (uint32_t)c, st = sq & 1u;
+                    const bool more = c + 2 < nchunk;
+                    // row indices of chunk c + 3 (jc holds those of chunk c + 2)
+                    jload(c + 3, jn);
+                    // the accumulator, the other warps' rows and norms, the records
+                    const bool ok = wait(&S.done[st], (sq >> 1) & 1u) && wait(&S.fullB[st], (sq >> 1) & 1u) &&
+                                    wait(&S.fullR[st], (sq >> 1) & 1u);
+                    tc::tc_fence_after();
+                    const uint32_t gv = more && ok ? gather_issue(c + 2, jc) : 0u;
+                    const int nb = min(kCB, nbox - c * kCB);
+                    for (int bb = 0; bb < nb; bb++) {
+                        uint32_t pos, len;
+                        int li;
+                        cur.next(S, pos, len, li);
+                        if (!ok) continue;
+                        // columns of this box inside the warp's own windows
+                        const uint2 w0 = make_uint2(__shfl_sync(0xffffffffu, wr0.x, li),
+                                                    __shfl_sync(0xffffffffu, wr0.y, li));
+                        const uint2 w1 = make_uint2(__shfl_sync(0xffffffffu, wr1.x, li),
+                                                    __shfl_sync(0xffffffffu, wr1.y, li));
+                        const int x0 = (int)max(pos, w0.x) - (int)pos;
+                        const int x1 = (int)min(pos + len, w0.x + w0.y) - (int)pos;
+                        const int y0 = (int)max(pos, w1.x) - (int)pos;
+                        const int y1 = (int)min(pos + len, w1.x + w1.y) - (int)pos;
+                        if (x1 <= x0 && y1 <= y0) continue;
+                        const float4 *rnb = &S.u.io.rn[st][bb][0];
+                        const float *n8b = &S.u.io.n8[c & 3][bb * kBoxR];
+                        const float4 *recb = &S.u.io.rec[st][bb * kBoxR];
+                        const uint8_t *binb = S.B[0][0] + ((c & 3) * kCN + bb * kBoxR) * kBinRowB;
+                        const uint32_t tb = tmem + lanebase + st * kCN + bb * kBoxR;
+                        // the box's columns inside the warp's windows, as a bit mask
+                        auto span = [](int a, int b) {
+                            a = max(a, 0);
+                            b = min(b, kBoxR);
+                            return b <= a ? 0u : (b - a >= 32 ? ~0u : ((1u << (b - a)) - 1u) << a);
+                        };
+                        const uint32_t inbox = live ? (span(x0, x1) | span(y0, y1)) : 0u;
+    #pragma unroll 1
+                        for (int g = 0; g < kBoxR; g += kGroup) {
+                            if (!__any_sync(0xffffffffu, (inbox >> g) & 0xffu)) continue;
+                            // the group's records, loaded together with its accumulators
+                            float4 rcs[kGroup];
+#pragma unroll
+                            for (int k = 0; k < kGroup; k++) rcs[k] = recb[g + k];
+                            uint32_t v[kGroup];
+                            if (!pop) {
+                                tc::tmem_ld8(tb + g, v);
+                                tc::tmem_wait_ld();
+                            }
+                            // membership of all columns first, branch-free (independent
+                            // work for the scheduler); then the few candidates
+                            const uint32_t gm = (inbox >> g) & 0xffu;
+                            uint32_t cm = 0, um = 0;  // FP32 sure members; members or inconclusive
+#pragma unroll
+                            for (int k = 0; k < kGroup; k++) {
+                                const float x = rcs[k].x, y = rcs[k].y, e = rcs[k].z;
+                                const float d = fabsf(fmaf(r.A, x, fmaf(r.B, y, r.C)));
+                                const float bound = fmaf(k1, fabsf(x) + fabsf(y), fmaf(ke, e, k0));
+                                cm |= (uint32_t)(d <= e - bound) << k;
+                                um |= (uint32_t)(d <= e + bound) << k;
+                            }
+                            if (exact_only) {
+                                cm = 0u;
+                                um = 0xffu;
+                            }
+                            cm &= gm;
+                            uint32_t exm = um & ~cm & gm;  // left to the FP64 expression
+                            nwin += __popc(gm);
+                            // FP32 inconclusive: the brute-force FP64 expression decides
+                            for (uint32_t m = exm; m; m &= m - 1u) {
+                                const int k = __ffs(m) - 1;
+                                nexact++;
+                                if (exact_pair(P, qi, __float_as_uint(recb[g + k].w))) cm |= 1u << k;
+                            }
+                            if (pop) {
+                                // Hamming distance of the binary rows by popcount
+                                for (; cm; cm &= cm - 1u) {
+                                    const int k = __ffs(cm) - 1;
+                                    const uint4 *rb = reinterpret_cast<const uint4 *>(binb + (g + k) * kBinRowB);
+                                    const uint4 r0 = rb[0], r1 = rb[1], q0 = qbrow[0], q1 = qbrow[1];
+                                    const uint32_t h = __popc(q0.x ^ r0.x) + __popc(q0.y ^ r0.y) + __popc(q0.z ^ r0.z) +
+                                                       __popc(q0.w ^ r0.w) + __popc(q1.x ^ r1.x) + __popc(q1.y ^ r1.y) +
+                                                       __popc(q1.z ^ r1.z) + __popc(q1.w ^ r1.w);
+                                    ncand++;
+                                    top2(((unsigned long long)h << 32) | __float_as_uint(recb[g + k].w), b1, b2);
                                 }
                             }
+                            for (; cm; cm &= cm - 1u) {
+                                const int k = __ffs(cm) - 1;
+                                uint32_t vk = v[0], jk = __float_as_uint(rcs[0].w);
+#pragma unroll
+                                for (int t = 1; t < kGroup; t++)
+                                    if (k == t) {
+                                        vk = v[t];
+                                        jk = __float_as_uint(rcs[t].w);
+                                    }
+                                ncand++;
+                                if (!isf) {
+                                    // integer distances: exact
+                                    const float dist = qn + n8b[g + k] - 2.0f * __uint_as_float(vk);
+                                    top2(((unsigned long long)(uint32_t)dist << 32) | jk, b1, b2);
+                                } else {
+                                    // the accumulator holds the product of the scaled rows (scales 1
+                                    // except in the FP8 pass)
+                                    const float4 rk = rnb[g + k];
+                                    const float dist = qn + rk.x - 2.0f * ((qs * rk.z) * __uint_as_float(vk));
+                                    // distance of the BF16-rounded rows, bracketed around the FP32
+                                    // distance the rerank will compute
+                                    float lo, hi;
+                                    float_bounds(dist, qn, rk.x, qerr, rk.y, lo, hi);
+                                    fb.insert(lo, hi, jk);
+                                }
+                            }
+                        }
                     }
-                    if (lane == q) {
-                        b1 = k1;
-                        b2 = k2;
+                    if (more) gather_finish(c + 2, gv);
+#pragma unroll
+                    for (int bb = 0; bb < kCB; bb++) jc[bb] = jn[bb];
+                    tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&S.tfree[st]);
+                }
+                if (isf) {
+                    // FP32 rerank, one query of the warp at a time, the lanes over the
+                    // dimensions: the candidates that can be among the best two, or
+                    // (buffer overflow) every reference in the warp's windows
+                    const bool live = qv && !(r.flags & EGM_FLAG_DEGENERATE_LINE);
+                    const bool complete = fb.complete();
+                    const bool exact_only = (r.flags & kQExactOnly) != 0;
+                    for (int q = 0; q < 32; q++) {
+                        if (!__shfl_sync(0xffffffffu, (int)live, q)) continue;
+                        const uint32_t qiq = __shfl_sync(0xffffffffu, qi, q);
+                        const float4 qv4 = __ldg(reinterpret_cast<const float4 *>(P.desc1 + (int64_t)qiq * 512) + lane);
+                        unsigned long long k1 = ~0ull, k2 = ~0ull;
+                        if (__shfl_sync(0xffffffffu, (int)complete, q)) {
+                            const float U2q = __shfl_sync(0xffffffffu, fb.U2, q);
+#pragma unroll
+                            for (int t = 0; t < kFBuf; t++) {
+                                const float Lt = __shfl_sync(0xffffffffu, fb.L[t], q);
+                                const uint32_t jt = __shfl_sync(0xffffffffu, fb.J[t], q);
+                                if (Lt <= U2q) {
+                                    const float d = coop_dist(qv4, P.desc2 + (int64_t)jt * 512, lane);
+                                    top2(((unsigned long long)__float_as_uint(d) << 32) | jt, k1, k2);
+                                }
+                            }
+                        } else {
+                            const float qA = __shfl_sync(0xffffffffu, r.A, q), qB = __shfl_sync(0xffffffffu, r.B, q);
+                            const float qC = __shfl_sync(0xffffffffu, r.C, q);
+                            const float qE0 = __shfl_sync(0xffffffffu, r.E0, q);
+                            const float qE1 = __shfl_sync(0xffffffffu, r.E1, q);
+                            const bool qex = __shfl_sync(0xffffffffu, (int)exact_only, q) != 0;
+                            for (int li = 0; li < nlev; li++)
+                                for (int h = 0; h < 2; h++) {
+                                    const uint2 wh = h ? wr1 : wr0;
+                                    const uint2 w = make_uint2(__shfl_sync(0xffffffffu, wh.x, li),
+                                                               __shfl_sync(0xffffffffu, wh.y, li));
+                                    for (uint32_t b0 = 0; b0 < w.y; b0 += 32) {
+                                        const bool valid = b0 + (uint32_t)lane < w.y;
+                                        uint32_t j = 0;
+                                        int m = 0;
+                                        if (valid) {
+                                            const float4 rc = L.rec[P.r_off + w.x + b0 + lane];
+                                            j = __float_as_uint(rc.w);
+                                            m = qex ? 2 : member32(qA, qB, qC, qE0, qE1, rc);
+                                            if (m == 2) m = exact_pair(P, qiq, j) ? 1 : 0;
+                                        }
+                                        for (uint32_t bal = __ballot_sync(0xffffffffu, m == 1); bal; bal &= bal - 1u) {
+                                            const uint32_t jt = __shfl_sync(0xffffffffu, j, __ffs(bal) - 1);
+                                            const float d = coop_dist(qv4, P.desc2 + (int64_t)jt * 512, lane);
+                                            top2(((unsigned long long)__float_as_uint(d) << 32) | jt, k1, k2);
+                                        }
+                                    }
+                                }
+                        }
+                        if (lane == q) {
+                            b1 = k1;
+                            b2 = k2;
+                        }
                     }
                 }
             }
         }
+        // no gathered copy may still be landing when the tile's memory is reused
+        tc::cp_async_wait_all();
         seq += (uint32_t)nchunk;
         if (qv) store_match(L, q_off + qi, P, r.flags, b1, b2);
-        // the query-tile buffer's generic accesses (binary rows) before the
-        // next tile's copies into it
-        if (pop) tc::fence_proxy_async();
+        // generic accesses of this tile (query rows, binary rows, widened
+        // rows) before the next tile's copies into the same memory
+        tc::fence_proxy_async();
         if (ctl) S.tile = knext < (uint64_t)L.ntiles ? L.tile_seq[knext] : -1;
         __syncthreads();
     }
@@ -1024,19 +1211,20 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
     if (ctl && S.err) {
         // A wait gave up.  Before the CTA's shared memory and TMEM are
         // released, every copy and MMA it issued must have landed: wait
-        // (bounded) for the last phase armed on each barrier.  The pipeline
-        // re-arms a barrier only after the previous phase was waited for, so
-        // at most that last phase is outstanding; an MMA commit also covers
-        // every earlier MMA of the thread.
+        // (bounded) for the last phase armed on each barrier that carries
+        // copies.  The pipeline re-arms a barrier only after the previous
+        // phase was waited for, so at most that last phase is outstanding;
+        // an MMA commit also covers every earlier MMA of the thread.
         for (int st = 0; st < 2; st++) {
-            if (armB[st]) tc::mbar_wait(&S.fullB[st], (armB[st] - 1u) & 1u);
-            if (armR[st]) tc::mbar_wait(&S.fullR[st], (armR[st] - 1u) & 1u);
+            if (armB[st] && txB[st]) tc::mbar_wait(&S.fullB[st], (armB[st] - 1u) & 1u);
             if (armD[st]) {
                 tc::mbar_wait(&S.done[st], (armD[st] - 1u) & 1u);
                 tc::mbar_wait(&S.sfree[st], (armD[st] - 1u) & 1u);
             }
         }
-        if (armA) tc::mbar_wait(&S.afull, (armA - 1u) & 1u);
+        for (int st = 0; st < 2; st++)
+            if (armR[st]) tc::mbar_wait(&S.fullR[st], (armR[st] - 1u) & 1u);
+        if (armA && txA) tc::mbar_wait(&S.afull, (armA - 1u) & 1u);
     }
     tc::tc_fence_before();
     __syncthreads();
@@ -1090,7 +1278,7 @@ cudaError_t launch_query_sort(const Launch &L, cudaStream_t s) {
 
 cudaError_t launch_pack(const Launch &L, cudaStream_t s) {
     const int64_t rows = L.nr + L.nq;
-    if (rows == 0) return cudaSuccess;
+    if (rows == 0 || !(L.kinds & (1u << EGM_DESC_F32_L2))) return cudaSuccess;
     int64_t blocks = (rows * 8 + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (L.fp8 && (L.kinds & (1u << EGM_DESC_F32_L2))) pack_kernel<true><<<(int)blocks, 256, 0, s>>>(L);
@@ -1100,7 +1288,7 @@ cudaError_t launch_pack(const Launch &L, cudaStream_t s) {
 
 template <int CB, int CPS, bool FLT>
 cudaError_t launch_band_shape(const Launch &L, int sms, const CUtensorMap &tA, const CUtensorMap &tB,
-                              bool zero_work, cudaStream_t s) {
+                              bool zero_work, bool pdl, cudaStream_t s) {
     const int smem = (int)sizeof(BandSmem<CB>) + 1024;
     int64_t grid = L.ntiles;
     if (grid > CPS * (int64_t)sms) grid = CPS * (int64_t)sms;
@@ -1108,23 +1296,32 @@ cudaError_t launch_band_shape(const Launch &L, int sms, const CUtensorMap &tA, c
     if (zero_work && (e = cudaMemsetAsync(L.work, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
     e = cudaFuncSetAttribute(band_kernel<CB, CPS, FLT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return launch_pdl(band_kernel<CB, CPS, FLT>, dim3((unsigned)grid), dim3(kBandThreads), (size_t)smem, s, tA, tB,
-                      L);
+    if (pdl)
+        return launch_pdl(band_kernel<CB, CPS, FLT>, dim3((unsigned)grid), dim3(kBandThreads), (size_t)smem, s, tA,
+                          tB, L);
+    band_kernel<CB, CPS, FLT><<<(unsigned)grid, kBandThreads, (size_t)smem, s>>>(tA, tB, L);
+    return cudaGetLastError();
 }
 
 int band_shapes() { return 3; }
 
 cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s, bool zero_work) {
     if (L.ntiles == 0) return cudaSuccess;
+    // Packed operand rows (and the tensor maps over them) exist for float
+    // pairs only; otherwise the maps cover the minimal buffers and are never
+    // used.  The pack kernel runs for float pairs only, so the band kernel
+    // follows it as a dependent launch, or else follows the join of the
+    // query-sort stream in full.
+    const bool flt = (L.kinds & (1u << EGM_DESC_F32_L2)) != 0;
     CUtensorMap tA, tB;
-    cudaError_t e = make_tmap(&tA, L.descA, L.nq, kTM);
+    cudaError_t e = make_tmap(&tA, L.descA, flt ? L.nq : kTM, kTM);
     if (e != cudaSuccess) return e;
-    if ((e = make_tmap(&tB, L.descB, L.nr, kBoxR)) != cudaSuccess) return e;
-    if (L.kinds & (1u << EGM_DESC_F32_L2)) return launch_band_shape<4, 2, true>(L, sms, tA, tB, zero_work, s);
+    if ((e = make_tmap(&tB, L.descB, flt ? L.nr : kTM, kBoxR)) != cudaSuccess) return e;
+    if (flt) return launch_band_shape<4, 2, true>(L, sms, tA, tB, zero_work, true, s);
     switch (shape) {
-        case 0: return launch_band_shape<4, 2, false>(L, sms, tA, tB, zero_work, s);
-        case 1: return launch_band_shape<2, 3, false>(L, sms, tA, tB, zero_work, s);
-        case 2: return launch_band_shape<1, 4, false>(L, sms, tA, tB, zero_work, s);
+        case 0: return launch_band_shape<4, 2, false>(L, sms, tA, tB, zero_work, zero_work, s);
+        case 1: return launch_band_shape<2, 3, false>(L, sms, tA, tB, zero_work, zero_work, s);
+        case 2: return launch_band_shape<1, 4, false>(L, sms, tA, tB, zero_work, zero_work, s);
         default: return cudaErrorInvalidValue;
     }
 }

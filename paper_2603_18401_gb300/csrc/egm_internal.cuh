@@ -9,7 +9,8 @@
 //     rec              float4 (x - cx, y - cy, eps, index bits) in bucket order
 //   tab                per (pair, level) bucket -> first sorted position
 //   curs               bucket fill cursors while the records are placed
-//   banded form: query order, packed operand rows, sorted query records
+//   banded form: query order, sorted query records, packed operand rows
+//                (float pairs)
 //   per query (sum of m, pair p at q_off):
 //     QueryRec         FP32 line in the pair frame, window centre, pad terms
 //     qcount           candidates per query (CSR path)
@@ -176,13 +177,11 @@ struct Launch {
     // banded form (tiles of 128 queries sorted by angle)
     uint32_t *qperm;              // sorted query slot -> pair-local query index
     uint16_t *qbkt;               // per query: its bucket of the angle order (written by the prep kernel)
-    uint8_t *descA, *descB;       // 256-byte operand rows of the sorted queries / references
-    uint8_t *rbin;                // binary pairs: 32-byte rows of the sorted references (popcount tiles)
+    uint8_t *descA, *descB;       // float pairs: 256-byte operand rows of the sorted queries / references
     QueryRec *qsrt;               // query records in sorted order, pad = (query index, norm bits)
-    float4 *rnorm;                // sorted references: (squared norm of the operand row, or popcount;
-                                  //   rounding error |r - r~| of float rows, else 0; row scale, 1
-                                  //   unless FP8; 0)
-    float *qscale;                // sorted queries: row scale of the operand row (1 unless FP8)
+    float4 *rnorm;                // float pairs, sorted references: (squared norm of the operand
+                                  //   row; rounding error |r - r~|; row scale, 1 unless FP8; 0)
+    float *qscale;                // float pairs, sorted queries: row scale of the operand row (1 unless FP8)
     int32_t fp8;                  // float rows packed as FP8 E4M3 with per-row scales
     const int64_t *tile_offs;     // npairs + 1: first tile of each pair
     const int32_t *tile_seq;      // ntiles: tiles in the order they are handed out (costliest pairs first)
@@ -568,8 +567,8 @@ cudaError_t launch_gms(void *scratch, const GmsLayout &l, int npairs, int64_t ro
 int64_t compact_tiles(int64_t m);
 cudaError_t launch_compact(const uint8_t *flags, const int32_t *best, int64_t m, uint32_t require,
                            uint32_t *tile_count, int32_t *qi, int32_t *rj, int64_t *count, cudaStream_t s);
-// zero_work: reset the tile dispenser first (the pipeline's pack kernel
-// resets it otherwise, keeping the launches back to back)
+// zero_work: reset the tile dispenser first (the pipeline's query-sort
+// kernel resets it otherwise)
 cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s, bool zero_work = true);
 cudaError_t launch_prep(const Launch &L, cudaStream_t s);
 cudaError_t launch_sort(const Launch &L, cudaStream_t s);

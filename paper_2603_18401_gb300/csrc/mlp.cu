@@ -258,11 +258,11 @@ __global__ void __launch_bounds__(kTT, 4) mlp_forward_tc_kernel(const float *par
                     const uint8_t *W = l == 0 ? S.W2 : S.W3;
 #pragma unroll
                     for (int kk = 0; kk < 4; kk++)
-                        tc::mma_bf16(tmem, tc::sdesc_sw128(tc::smem_addr(S.Ahi) + 32 * kk),
+                        tc::mma_f16(tmem, tc::sdesc_sw128(tc::smem_addr(S.Ahi) + 32 * kk),
                                      tc::sdesc_sw128(tc::smem_addr(W) + 32 * kk), idesc, kk > 0);
 #pragma unroll
                     for (int kk = 0; kk < 4; kk++)
-                        tc::mma_bf16(tmem, tc::sdesc_sw128(tc::smem_addr(S.Alo) + 32 * kk),
+                        tc::mma_f16(tmem, tc::sdesc_sw128(tc::smem_addr(S.Alo) + 32 * kk),
                                      tc::sdesc_sw128(tc::smem_addr(W) + 32 * kk), idesc, 1);
                     tc::mma_commit(&S.bar);
                 }

@@ -3,8 +3,9 @@
 // (TMEM) allocation and loads, and tcgen05.mma with shared-memory operand
 // descriptors.  Everything is inline PTX; no library headers.
 //
-// Operand layout: K-major rows of 128 bytes per K block, written by TMA with
-// the 128-byte swizzle, so an 8-row group is one 1024-byte atom.  The MMA
+// Operand layout: K-major rows of 128 bytes per K block with the 128-byte
+// swizzle (16-byte chunk c of row r stored at chunk position c ^ (r mod 8)),
+// written by TMA or by threads, so an 8-row group is one 1024-byte atom.  The MMA
 // descriptor of such a tile has stride-byte-offset 1024, swizzle mode
 // "128B", and moves along K inside the atom by advancing the start address
 // 32 bytes per MMA step (16 BF16 or 32 FP8 elements).
@@ -91,6 +92,13 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared by one thread (both addresses
+// 16-byte aligned); cp_async_wait_all() before the issuing thread reads it.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ void prefetch_tmap(const void *tmap) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
 }
@@ -157,15 +165,20 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
 
 // Instruction descriptors, D in FP32, A and B K-major.
 //   kind::f16 with BF16 operands (K = 16 per instruction)
+//   kind::f16 with FP16 operands (K = 16 per instruction)
 //   kind::f8f6f4 with E4M3 operands (K = 32 per instruction)
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 __host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
     return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+// kind::f16: BF16 or FP16 operands, as the instruction descriptor says.
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
