@@ -263,19 +263,19 @@ egm_status make_plan(const egm_pair *pairs, int npairs, Plan &pl) {
     for (int p = 0; p < npairs; p++) order[p] = p;
     auto cost = [&](int p) { return (double)tm * pairs[p].n / std::max(pairs[p].m, 1) + 64.0; };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    // one int64 entry per tile: the tile (low 32 bits) and its pair (high)
     const size_t base = pl.offs.size();
-    pl.offs.resize(base + (size_t)(pl.ntiles + 1) / 2, 0);
-    int32_t *seq = reinterpret_cast<int32_t *>(pl.offs.data() + base);
+    pl.offs.resize(base + (size_t)pl.ntiles, 0);
     int64_t k = 0;
     for (int p : order)
         for (int64_t t = pl.offs[2 * (npairs + 1) + p]; t < pl.offs[2 * (npairs + 1) + p + 1]; t++)
-            seq[k++] = (int32_t)t;
+            pl.offs[base + k++] = (int64_t)(uint32_t)t | ((int64_t)p << 32);
     return EGM_OK;
 }
 
 // int64 entries of the offsets upload for a batch of npairs pairs and nq queries.
 size_t offs_entries(int npairs, int64_t nq) {
-    return 3 * (size_t)(npairs + 1) + (size_t)(nq / band_tile_queries() + npairs + 2) / 2 + 1;
+    return 3 * (size_t)(npairs + 1) + (size_t)(nq / band_tile_queries() + npairs + 2) + 1;
 }
 
 // The banded form runs when every pair fits it, no candidate lists are asked
@@ -296,9 +296,10 @@ egm_status choose_band(const Plan &pl, const egm_params &prm, bool csr, int sms,
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Banded-form scratch: query permutation and sorted query records; with
-// float pairs (`packed`) also the packed operand rows and their norms (padded
-// for the aligned 16-byte bulk copies that read past a pair's last row).
+// Banded-form scratch: query permutation and buckets; with float pairs
+// (`packed`) also the sorted query records, the packed operand rows and
+// their norms (padded for the aligned 16-byte bulk copies that read past a
+// pair's last row).
 // Without float pairs the operand buffers keep one tile of rows, which the
 // band kernel's (unused) tensor maps cover.
 struct BandLayout {
@@ -311,7 +312,7 @@ struct BandLayout {
         descB = descA + align256(rb * (size_t)std::max<int64_t>(ta, 1));
         qbkt = descB + align256(rb * (size_t)std::max<int64_t>(tb, 1));
         qsrt = qbkt + align256(sizeof(uint16_t) * (size_t)std::max<int64_t>(nq, 1));
-        qscale = qsrt + align256(sizeof(QueryRec) * (size_t)std::max<int64_t>(nq, 1));
+        qscale = qsrt + align256(sizeof(QueryRec) * (size_t)std::max<int64_t>(packed ? nq : 1, 1));
         rnorm = qscale + align256(sizeof(float) * (size_t)std::max<int64_t>(packed ? nq : 1, 1));
         // 64 rows of padding: bulk copies of a 32-row box may run past the last row
         total = rnorm + align256(sizeof(float4) * (size_t)((packed ? nr : 0) + 64));
@@ -402,7 +403,7 @@ Launch make_launch(Scratch &sc, bool counters_on, const egm_params &prm, const P
         L.fp8 = prm.float_pass == EGM_FLOAT_PASS_FP8;
         L.probe = prm.timeout_check;
         L.tile_offs = offs + 2 * (npairs + 1);
-        L.tile_seq = reinterpret_cast<const int32_t *>(offs + 3 * (npairs + 1));
+        L.tile_seq = reinterpret_cast<const int2 *>(offs + 3 * (npairs + 1));
         L.work = as<uint32_t>(c->small) + 32;
         L.ntiles = pl.ntiles;
     }

@@ -11,11 +11,10 @@
 //   query_sort_kernel  one block per pair: counting sort of the queries by
 //                      the top bits of their quantised line angle; lines
 //                      without an FP32 view (FP64-only, degenerate) last.
-//                      Writes the sorted query records (index in the padding).
 //   pack_kernel        float pairs only: descriptor rows of the sorted
 //                      references and queries as 256-byte BF16 (or E4M3)
 //                      operands, with the norm of the rounded row and the
-//                      rounding error |x - x~|
+//                      rounding error |x - x~|, and the sorted query records
 //   band_kernel        persistent; one tile of 128 sorted queries at a time.
 //                      Warps 0-3 (one thread per query) build the tile's band
 //                      from the hull of their windows; warp 4 issues the bulk
@@ -122,17 +121,7 @@ __global__ void __launch_bounds__(kQSortThreads) query_sort_kernel(Launch L) {
 #pragma unroll
         for (int k = 0; k < kQSortPer; k++) {
             const int i = i0 + k * kQSortThreads + tid;
-            if (v[k] != 0xffffu) {
-                const int64_t slot = P.q_off + atomicAdd(&hist[v[k]], 1u);
-                L.qperm[slot] = (uint32_t)i;
-                // the sorted record: query index and (float pairs, set by the
-                // pack kernel) norm and rounding error in the padding
-                QueryRec rq = L.qrec[P.q_off + i];
-                rq.pair = 0;
-                rq.pad[0] = (uint32_t)i;
-                rq.pad[1] = 0u;
-                L.qsrt[slot] = rq;
-            }
+            if (v[k] != 0xffffu) L.qperm[P.q_off + atomicAdd(&hist[v[k]], 1u)] = (uint32_t)i;
         }
     }
 }
@@ -291,6 +280,13 @@ struct __align__(16) Piece {
     int32_t li;
 };
 
+// A tile as the control thread hands it out: its pair, the pair's first
+// query slot, the tile's first sorted slot and its query count.
+struct TileDesc {
+    int64_t q_off, q_first;
+    int32_t pair, mt, kind;  // pair -1: no tile left
+};
+
 constexpr uint32_t kOperandArrivals = 5; // fullB / afull: the control thread and the four epilogue warps
 
 template <int CB>
@@ -328,7 +324,7 @@ struct BandSmem {
     Piece pc[2 * kLevels];
     int32_t lv[kLevels];
     int32_t nlev, npc, nbox, gpair;
-    int32_t tile;                 // the tile being processed, then the next one
+    TileDesc td, tdn;             // the tile being processed; the next one
     uint32_t tmem;
     volatile uint32_t err;
 };
@@ -512,6 +508,23 @@ __device__ __forceinline__ void widen16(const uint4 w, uint4 &o0, uint4 &o1, uin
     o1 = make_uint4(o[4], o[5], o[6], o[7]);
 }
 
+// The k-th tile handed out (tile_seq holds each tile's index and pair).
+__device__ __forceinline__ TileDesc fetch_tile(const Launch &L, uint32_t k) {
+    TileDesc d;
+    d.pair = -1;
+    d.q_off = d.q_first = 0;
+    d.mt = d.kind = 0;
+    if (k >= (uint64_t)L.ntiles) return d;
+    const int2 ts = L.tile_seq[k];
+    const int p = ts.y;
+    d.pair = p;
+    d.q_off = L.q_offs[p];
+    d.q_first = d.q_off + ((int64_t)ts.x - L.tile_offs[p]) * kTM;
+    d.mt = (int)min((int64_t)kTM, L.q_offs[p + 1] - d.q_first);
+    d.kind = L.pairs[p].kind;
+    return d;
+}
+
 // Byte offset of 16-byte chunk c of row r in a 128-byte-swizzled operand tile.
 __device__ __forceinline__ uint32_t sw128(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
 
@@ -545,8 +558,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         tc::fence_mbar_init();
         S.err = 0;
         S.gpair = -1;
-        const uint32_t k = atomicAdd(L.work, 1u);
-        S.tile = k < (uint64_t)L.ntiles ? L.tile_seq[k] : -1;
+        S.td = fetch_tile(L, atomicAdd(L.work, 1u));
         if (FLT) {
             tc::prefetch_tmap(&tmA);
             tc::prefetch_tmap(&tmB);
@@ -569,7 +581,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         return false;
     };
     uint32_t seq = 0;
-    unsigned long long nwin = 0, ncand = 0, nexact = 0;
+    uint32_t nwin = 0, ncand = 0, nexact = 0;  // per-thread counts (counters on)
     // phases the control thread armed on each barrier (copies and MMAs issued)
     // and whether the last one carries copies: after a failed wait, the CTA
     // lets them complete before it leaves
@@ -586,42 +598,46 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
     }
 
     for (;;) {
-        const int64_t tile = S.tile;
-        if (tile < 0 || S.err) break;
+        const TileDesc td = S.td;
+        if (td.pair < 0 || S.err) break;
         // the next tile, fetched while this one is processed
-        uint32_t knext = 0;
-        if (ctl) knext = atomicAdd(L.work, 1u);
-        const int p = pair_of(L.tile_offs, L.npairs, tile);
-        const int64_t q_off = L.q_offs[p];
-        const int64_t t0 = (tile - L.tile_offs[p]) * kTM;  // first sorted slot of the tile
-        const int mt = (int)min((int64_t)kTM, L.q_offs[p + 1] - q_off - t0);
-        // ---- the tile's queries (sorted records: index, and for float rows
-        // norm and rounding error, in the padding)
+        TileDesc tnext;
+        if (ctl) tnext = fetch_tile(L, atomicAdd(L.work, 1u));
+        const int p = td.pair, mt = td.mt, kind = td.kind;
+        const int64_t q_off = td.q_off, q_first = td.q_first;
+        // binary pairs: Hamming distances by popcount, no operand rows; float
+        // pairs: packed rows by TMA; u8 pairs: rows widened here
+        const bool pop = kind == EGM_DESC_BIN;
+        const bool flt = FLT && kind == EGM_DESC_F32_L2;
+        const bool cvt = !pop && !flt;
+        // ---- the tile's queries: records in sorted order (float pairs: with
+        // norm and rounding error in the padding), else through the order
         QueryRec r;
         const bool qv = warp < 4 && tid < mt;
+        uint32_t qi = 0;
+        float qn = 0.0f, qerr = 0.0f;
         if (qv) {
-            r = L.qsrt[q_off + t0 + tid];
+            if (flt) {
+                r = L.qsrt[q_first + tid];
+                qi = r.pad[0];
+                qn = __uint_as_float(r.pad[1]);
+                qerr = __uint_as_float((uint32_t)r.pair);  // |q - q~|
+            } else {
+                qi = L.qperm[q_first + tid];
+                r = L.qrec[q_off + qi];
+            }
         } else {
             r.A = r.B = r.C = r.key = r.aux0 = r.aux1 = r.E0 = r.E1 = 0.0f;
             r.flags = EGM_FLAG_DEGENERATE_LINE;
             r.pair = p;
             r.pad[0] = r.pad[1] = 0;
         }
-        const uint32_t qi = r.pad[0];
-        float qn = __uint_as_float(r.pad[1]);
-        const float qerr = __uint_as_float((uint32_t)r.pair);  // float rows: |q - q~|
-        const int kind = __ldg(&L.pairs[p].kind);
-        // binary pairs: Hamming distances by popcount, no operand rows; float
-        // pairs: packed rows by TMA; u8 pairs: rows widened here
-        const bool pop = kind == EGM_DESC_BIN;
-        const bool flt = FLT && kind == EGM_DESC_F32_L2;
-        const bool cvt = !pop && !flt;
-        const float qs = flt && qv ? L.qscale[q_off + t0 + tid] : 1.0f;  // row scale of the FP8 pass
+        const float qs = flt && qv ? L.qscale[q_first + tid] : 1.0f;  // row scale of the FP8 pass
         if (ctl && !pop) {
             if (flt) {
                 tc::mbar_arrive_expect_tx(&S.afull, 2 * kTM * 128);
-                tc::tma_load_2d(S.A[0], &tmA, 0, (int32_t)(q_off + t0), &S.afull);
-                tc::tma_load_2d(S.A[1], &tmA, 128, (int32_t)(q_off + t0), &S.afull);
+                tc::tma_load_2d(S.A[0], &tmA, 0, (int32_t)q_first, &S.afull);
+                tc::tma_load_2d(S.A[1], &tmA, 128, (int32_t)q_first, &S.afull);
             } else {
                 tc::mbar_arrive(&S.afull);
             }
@@ -771,6 +787,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         const int nchunk = (nbox + kCB - 1) / kCB;
 
         if (ctl) {
+            S.tdn = tnext;  // landed by now (its loads were issued at the tile start)
             // ---- control.  The operand stage of chunk c + 2 opens once the
             // MMA of chunk c has read it (TMA rows: loaded then; u8 and binary
             // rows: written by the epilogue warps, which also arrive); the
@@ -1195,13 +1212,13 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         // generic accesses of this tile (query rows, binary rows, widened
         // rows) before the next tile's copies into the same memory
         tc::fence_proxy_async();
-        if (ctl) S.tile = knext < (uint64_t)L.ntiles ? L.tile_seq[knext] : -1;
+        if (ctl) S.td = S.tdn;
         __syncthreads();
     }
     if (L.counters && warp < 4) {
-        const uint32_t a = __reduce_add_sync(0xffffffffu, (uint32_t)nwin);
-        const uint32_t b = __reduce_add_sync(0xffffffffu, (uint32_t)ncand);
-        const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)nexact);
+        const uint32_t a = __reduce_add_sync(0xffffffffu, nwin);
+        const uint32_t b = __reduce_add_sync(0xffffffffu, ncand);
+        const uint32_t c = __reduce_add_sync(0xffffffffu, nexact);
         if (lane == 0) {
             atomicAdd(L.counters + 2, (unsigned long long)a);
             atomicAdd(L.counters + 3, (unsigned long long)b);

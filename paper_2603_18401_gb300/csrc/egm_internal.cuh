@@ -9,8 +9,8 @@
 //     rec              float4 (x - cx, y - cy, eps, index bits) in bucket order
 //   tab                per (pair, level) bucket -> first sorted position
 //   curs               bucket fill cursors while the records are placed
-//   banded form: query order, sorted query records, packed operand rows
-//                (float pairs)
+//   banded form: query order; for float pairs sorted query records and
+//                packed operand rows
 //   per query (sum of m, pair p at q_off):
 //     QueryRec         FP32 line in the pair frame, window centre, pad terms
 //     qcount           candidates per query (CSR path)
@@ -178,13 +178,14 @@ struct Launch {
     uint32_t *qperm;              // sorted query slot -> pair-local query index
     uint16_t *qbkt;               // per query: its bucket of the angle order (written by the prep kernel)
     uint8_t *descA, *descB;       // float pairs: 256-byte operand rows of the sorted queries / references
-    QueryRec *qsrt;               // query records in sorted order, pad = (query index, norm bits)
+    QueryRec *qsrt;               // float pairs: query records in sorted order, pad = (query index, norm
+                                  //   bits), pair field = rounding error bits
     float4 *rnorm;                // float pairs, sorted references: (squared norm of the operand
                                   //   row; rounding error |r - r~|; row scale, 1 unless FP8; 0)
     float *qscale;                // float pairs, sorted queries: row scale of the operand row (1 unless FP8)
     int32_t fp8;                  // float rows packed as FP8 E4M3 with per-row scales
     const int64_t *tile_offs;     // npairs + 1: first tile of each pair
-    const int32_t *tile_seq;      // ntiles: tiles in the order they are handed out (costliest pairs first)
+    const int2 *tile_seq;         // ntiles: (tile, pair) in the order tiles are handed out (costliest pairs first)
     uint32_t *work;               // tile dispenser (zeroed before the band kernel)
     int64_t ntiles;
     int32_t probe;                // timeout check: band CTAs first wait on a barrier nothing completes

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(32) geometry_kernel(Launch L) {
             }
         }
         if (L.tile_seq)
-            for (int64_t t = lane; t < L.ntiles; t += 32) const_cast<int32_t *>(L.tile_seq)[t] = (int32_t)t;
+            for (int64_t t = lane; t < L.ntiles; t += 32) const_cast<int2 *>(L.tile_seq)[t] = make_int2((int)t, 0);
     }
     const PairDesc &P = L.inl_use ? L.inl : L.pairs[p];
     PairGeom &G = L.geom[p];
