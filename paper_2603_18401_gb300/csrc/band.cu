@@ -335,6 +335,7 @@ struct BandShape {
     static constexpr uint32_t kTmemCols = 2 * kCN;  // double-buffered accumulator (a power of two)
     using Smem = BandSmem<CB>;
     static_assert(offsetof(Smem, B) % 1024 == 0, "operand tiles need 1024-byte alignment");
+    static_assert(kTM * sizeof(QueryRec) <= sizeof(Smem::B[1]), "a tile's query records fit operand stage 1");
     static_assert(offsetof(Smem, u) % 16 == 0, "bulk copy destinations need 16-byte alignment");
     // CPS CTAs per SM share the 512 TMEM columns; shared memory keeps one more
     // from becoming resident (its allocation would wait for another CTA to end)
@@ -525,6 +526,14 @@ __device__ __forceinline__ TileDesc fetch_tile(const Launch &L, uint32_t k) {
     return d;
 }
 
+// a[k] for a lane-dependent k in [0, 8), by a tree of selects (no local memory).
+__device__ __forceinline__ uint32_t pick8(const uint32_t (&a)[8], int k) {
+    const bool b0 = k & 1, b1 = k & 2, b2 = k & 4;
+    const uint32_t a01 = b0 ? a[1] : a[0], a23 = b0 ? a[3] : a[2], a45 = b0 ? a[5] : a[4], a67 = b0 ? a[7] : a[6];
+    const uint32_t a03 = b1 ? a23 : a01, a47 = b1 ? a67 : a45;
+    return b2 ? a47 : a03;
+}
+
 // Byte offset of 16-byte chunk c of row r in a 128-byte-swizzled operand tile.
 __device__ __forceinline__ uint32_t sw128(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
 
@@ -597,6 +606,10 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         __syncthreads();
     }
 
+    // the next tile's query record (u8 and binary pairs), copied at the end of
+    // a tile into the operand stage 1 (idle by then) while the tile ends
+    bool staged = false;
+    uint32_t qi_next = 0;
     for (;;) {
         const TileDesc td = S.td;
         if (td.pair < 0 || S.err) break;
@@ -622,6 +635,12 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 qi = r.pad[0];
                 qn = __uint_as_float(r.pad[1]);
                 qerr = __uint_as_float((uint32_t)r.pair);  // |q - q~|
+            } else if (staged) {
+                tc::cp_async_wait_all();
+                qi = qi_next;
+                const uint4 *sr = reinterpret_cast<const uint4 *>(S.B[1][0] + tid * sizeof(QueryRec));
+                uint4 w[3] = {sr[0], sr[1], sr[2]};
+                memcpy(&r, w, sizeof(QueryRec));
             } else {
                 qi = L.qperm[q_first + tid];
                 r = L.qrec[q_off + qi];
@@ -779,15 +798,24 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 }
             }
         }
+        if (ctl) S.tdn = tnext;  // landed by now (its loads were issued at the tile start)
         // the hull arrays' last generic accesses before the record stages they
         // share are written by bulk copies again
         tc::fence_proxy_async();
         __syncthreads();
         const int nbox = S.nbox;
         const int nchunk = (nbox + kCB - 1) / kCB;
+        // the next tile's query order entries, loaded while this tile runs
+        staged = false;
+        {
+            const TileDesc &tn = S.tdn;
+            if (warp < 4 && tn.pair >= 0 && !(FLT && tn.kind == EGM_DESC_F32_L2) && tid < tn.mt) {
+                qi_next = L.qperm[tn.q_first + tid];
+                staged = true;
+            }
+        }
 
         if (ctl) {
-            S.tdn = tnext;  // landed by now (its loads were issued at the tile start)
             // ---- control.  The operand stage of chunk c + 2 opens once the
             // MMA of chunk c has read it (TMA rows: loaded then; u8 and binary
             // rows: written by the epilogue warps, which also arrive); the
@@ -1110,31 +1138,42 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                                     top2(((unsigned long long)h << 32) | __float_as_uint(recb[g + k].w), b1, b2);
                                 }
                             }
-                            for (; cm; cm &= cm - 1u) {
-                                const int k = __ffs(cm) - 1;
-                                uint32_t vk = v[0], jk = __float_as_uint(rcs[0].w);
+                            if (cvt && __any_sync(0xffffffffu, cm)) {
+                                // the group's distances first, branch-free (integers below
+                                // 2^24: exact in FP32, compared by their bit patterns);
+                                // then the candidates pick theirs by a select tree
+                                const float4 na = *reinterpret_cast<const float4 *>(n8b + g);
+                                const float4 nb4 = *reinterpret_cast<const float4 *>(n8b + g + 4);
+                                const float nk[kGroup] = {na.x, na.y, na.z, na.w, nb4.x, nb4.y, nb4.z, nb4.w};
+                                uint32_t dk[kGroup], jv[kGroup];
 #pragma unroll
-                                for (int t = 1; t < kGroup; t++)
-                                    if (k == t) {
-                                        vk = v[t];
-                                        jk = __float_as_uint(rcs[t].w);
-                                    }
-                                ncand++;
-                                if (!isf) {
-                                    // integer distances: exact
-                                    const float dist = qn + n8b[g + k] - 2.0f * __uint_as_float(vk);
-                                    top2(((unsigned long long)(uint32_t)dist << 32) | jk, b1, b2);
-                                } else {
-                                    // the accumulator holds the product of the scaled rows (scales 1
-                                    // except in the FP8 pass)
-                                    const float4 rk = rnb[g + k];
-                                    const float dist = qn + rk.x - 2.0f * ((qs * rk.z) * __uint_as_float(vk));
-                                    // distance of the BF16-rounded rows, bracketed around the FP32
-                                    // distance the rerank will compute
-                                    float lo, hi;
-                                    float_bounds(dist, qn, rk.x, qerr, rk.y, lo, hi);
-                                    fb.insert(lo, hi, jk);
+                                for (int k = 0; k < kGroup; k++) {
+                                    dk[k] = __float_as_uint(fmaf(-2.0f, __uint_as_float(v[k]), qn + nk[k]));
+                                    jv[k] = __float_as_uint(rcs[k].w);
                                 }
+                                for (; cm; cm &= cm - 1u) {
+                                    const int k = __ffs(cm) - 1;
+                                    ncand++;
+                                    top2(((unsigned long long)pick8(dk, k) << 32) | pick8(jv, k), b1, b2);
+                                }
+                            }
+                            for (; cm; cm &= cm - 1u) {
+                                // float rows
+                                const int k = __ffs(cm) - 1;
+                                uint32_t jv[kGroup];
+#pragma unroll
+                                for (int t = 0; t < kGroup; t++) jv[t] = __float_as_uint(rcs[t].w);
+                                const uint32_t vk = pick8(v, k), jk = pick8(jv, k);
+                                ncand++;
+                                // the accumulator holds the product of the scaled rows (scales 1
+                                // except in the FP8 pass)
+                                const float4 rk = rnb[g + k];
+                                const float dist = qn + rk.x - 2.0f * ((qs * rk.z) * __uint_as_float(vk));
+                                // distance of the BF16-rounded rows, bracketed around the FP32
+                                // distance the rerank will compute
+                                float lo, hi;
+                                float_bounds(dist, qn, rk.x, qerr, rk.y, lo, hi);
+                                fb.insert(lo, hi, jk);
                             }
                         }
                     }
@@ -1208,13 +1247,32 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         // no gathered copy may still be landing when the tile's memory is reused
         tc::cp_async_wait_all();
         seq += (uint32_t)nchunk;
+        if (cvt) {
+            // u8 keys hold the distance's FP32 bits: the integer distance, as elsewhere
+            auto as_int = [](unsigned long long b) {
+                return b == ~0ull ? b
+                                  : ((unsigned long long)(uint32_t)__uint_as_float((uint32_t)(b >> 32)) << 32) |
+                                        (b & 0xffffffffull);
+            };
+            b1 = as_int(b1);
+            b2 = as_int(b2);
+        }
         if (qv) store_match(L, q_off + qi, P, r.flags, b1, b2);
+        if (staged) {
+            // every MMA of this tile is done and stage 1 holds no binary rows
+            const uint8_t *src = reinterpret_cast<const uint8_t *>(L.qrec + S.tdn.q_off + qi_next);
+            uint8_t *dst = S.B[1][0] + tid * sizeof(QueryRec);
+            tc::cp_async16(dst, src);
+            tc::cp_async16(dst + 16, src + 16);
+            tc::cp_async16(dst + 32, src + 32);
+        }
         // generic accesses of this tile (query rows, binary rows, widened
         // rows) before the next tile's copies into the same memory
         tc::fence_proxy_async();
         if (ctl) S.td = S.tdn;
         __syncthreads();
     }
+    tc::cp_async_wait_all();
     if (L.counters && warp < 4) {
         const uint32_t a = __reduce_add_sync(0xffffffffu, nwin);
         const uint32_t b = __reduce_add_sync(0xffffffffu, ncand);

@@ -491,14 +491,37 @@ __device__ __forceinline__ Window window_ranges(const WinKeys &k, uint32_t pa, u
     return w;
 }
 
+// exact_member(a, b, c, exact_norm(a, b), x, y, eps), mostly without the
+// square root and the division.  With num = |a x + b y + c| and S = a a + b b
+// evaluated as the definition evaluates them, the definition's quotient is
+// Q = RN(num / N), N = RN(sqrt(S)).  Let lhs = RN(num num), rhs = RN(RN(eps
+// eps) S), all normal (u = 2^-53 the unit roundoff), so N^2 is within
+// (1 +- 3u) of S.  If lhs <= RN(rhs (1 - 2^-48)) then num^2 < eps^2 S (1 -
+// 2^-49) < eps^2 N^2: num / N < eps and Q <= eps.  If lhs >= RN(rhs (1 +
+// 2^-48)) then num^2 > eps^2 N^2 (1 + 2^-50): num / N > eps (1 + 2^-52) >=
+// eps + ulp(eps), and Q > eps.  Otherwise (and outside the normal range)
+// the definition itself decides.
+__device__ __forceinline__ bool exact_within(double a, double b, double c, double x, double y, double eps) {
+    const double num = fabs(__dadd_rn(__dadd_rn(__dmul_rn(a, x), __dmul_rn(b, y)), c));
+    const double S = __dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b));
+    if (eps >= 1e-140 && eps <= 1e140 && num <= 1e145) {
+        const double lhs = __dmul_rn(num, num);
+        const double rhs = __dmul_rn(__dmul_rn(eps, eps), S);
+        if (rhs >= 1e-290 && rhs <= 1e290) {
+            if (lhs <= __dmul_rn(rhs, 1.0 - 0x1p-48)) return true;
+            if (lhs >= __dmul_rn(rhs, 1.0 + 0x1p-48)) return false;
+        }
+    }
+    return exact_member(a, b, c, exact_norm(a, b), x, y, eps);
+}
+
 // The brute-force FP64 decision for one (query, reference) pair, kept out of
 // line: it runs only when the FP32 test is inconclusive.
 static __device__ __noinline__ bool exact_pair(const PairDesc &P, int64_t i, uint32_t j) {
     double a, b, c;
     exact_line(P.F, P.xy1[2 * i], P.xy1[2 * i + 1], a, b, c);
-    const double N = exact_norm(a, b);
     const double eps = P.eps2 ? P.eps2[j] : P.eps_scalar;
-    return exact_member(a, b, c, N, P.xy2[2 * (int64_t)j], P.xy2[2 * (int64_t)j + 1], eps);
+    return exact_within(a, b, c, P.xy2[2 * (int64_t)j], P.xy2[2 * (int64_t)j + 1], eps);
 }
 
 // Outputs of query gq from its best two (distance << 32 | index) keys:

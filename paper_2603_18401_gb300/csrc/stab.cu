@@ -669,9 +669,8 @@ static __device__ __noinline__ bool exact_pair_p(const double *F, const double *
                                                  const double *eps2, double eps_scalar, int64_t i, uint32_t j) {
     double a, b, c;
     exact_line(F, xy1[2 * i], xy1[2 * i + 1], a, b, c);
-    const double N = exact_norm(a, b);
     const double eps = eps2 ? eps2[j] : eps_scalar;
-    return exact_member(a, b, c, N, xy2[2 * (int64_t)j], xy2[2 * (int64_t)j + 1], eps);
+    return exact_within(a, b, c, xy2[2 * (int64_t)j], xy2[2 * (int64_t)j + 1], eps);
 }
 
 // G lanes read a descriptor row, C 16-byte chunks each (a row is G C 16 bytes).
