@@ -168,8 +168,9 @@ typedef struct egm_params {
     int32_t sync;          /* 1 (default): calls wait and return the device status */
     int32_t form;          /* EGM_FORM_* */
     int32_t band_tile;     /* banded form tile shape: 0 (default) chosen by the tuner (see tune);
-                              k = 1, 2, 3: shape k - 1 (4, 2 or 1 boxes of 32 references per
-                              tensor-core chunk, with 2, 3 or 4 resident CTAs per SM) */
+                              k = 1..7: shape k - 1, (boxes of 32 references per tensor-core
+                              chunk, resident CTAs per SM) = (4, 2), (2, 3), (1, 4), (1, 3),
+                              (2, 2), (4, 1), (1, 2) */
     int32_t float_pass;    /* banded form, float descriptors: the tensor-core pass that brackets
                               the distances before the exact FP32 rerank (results are the same):
                               EGM_FLOAT_PASS_BF16 (default) or EGM_FLOAT_PASS_FP8 */
@@ -186,7 +187,7 @@ typedef struct egm_params {
                               tiles (log2), one or several pairs, the descriptor kinds, the expected
                               candidates per query (log2) -- by timing the plain form and every band
                               tile shape on the first call of a regime (that call waits for the
-                              device and runs the pipeline 16 times; results are the same in every
+                              device and runs the pipeline 32 times; results are the same in every
                               configuration) and caching the fastest in the context
                               (egm_tuner_export / egm_tuner_import); 0: no timing, a fixed rule */
     int32_t reserved[8];   /* zero */

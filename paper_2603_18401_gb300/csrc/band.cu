@@ -268,11 +268,14 @@ __global__ void __launch_bounds__(256) pack_kernel(Launch L) {
 constexpr int kTM = 128;                 // queries per tile (MMA M, TMEM lanes)
 constexpr int kBoxR = 32;                // reference rows per TMA box (N per box)
 constexpr int kBandThreads = kTM + 32;   // four epilogue warps and the control warp
-// Tile shapes (chosen per workload by the tuner): CB boxes per MMA chunk
+// Tile shapes (chosen per call regime by the tuner): CB boxes per MMA chunk
 // (N = 32 CB) and CPS resident CTAs per SM, which size shared memory and TMEM.
 //   0: CB 4, CPS 2   few tiles per SM (single pairs): fewer, larger chunks
 //   1: CB 2, CPS 3   many tiles (batches): more CTAs in flight per SM
 //   2: CB 1, CPS 4   many tiles: more CTAs still, more synchronisation per box
+//   3: CB 1, CPS 3   4: CB 2, CPS 2   5: CB 4, CPS 1   6: CB 1, CPS 2
+// Every shape whose CPS CTAs fit the SM's shared memory (CB 1: up to 4,
+// CB 2: up to 3, CB 4: up to 2) except CPS 1 with CB 1 or 2.
 constexpr int kGroup = 8;                // columns per TMEM load in the epilogue
 
 struct __align__(16) Piece {
@@ -320,11 +323,12 @@ struct BandSmem {
     uint64_t fullB[2], sfree[2], fullR[2], done[2], tfree[2], afull;
     uint64_t probe;               // never arrived on: the wait of the timeout check (Launch::probe)
     PairGeom g;
-    PairDesc pd;
+    PairDesc pd[2];               // the pair of the tile (pd[pdi]); the next tile's, prefetched
     Piece pc[2 * kLevels];
     int32_t lv[kLevels];
-    int32_t nlev, npc, nbox, gpair;
-    TileDesc td, tdn;             // the tile being processed; the next one
+    int32_t nlev, npc, nbox;
+    int32_t gpair, pdi, pref;     // pair in g and pd[pdi]; pair prefetched into g and pd[pdi ^ 1] (-1: none)
+    TileDesc td, tdn, tdnn;       // the tile being processed; the next two
     uint32_t tmem;
     volatile uint32_t err;
 };
@@ -337,10 +341,15 @@ struct BandShape {
     static_assert(offsetof(Smem, B) % 1024 == 0, "operand tiles need 1024-byte alignment");
     static_assert(kTM * sizeof(QueryRec) <= sizeof(Smem::B[1]), "a tile's query records fit operand stage 1");
     static_assert(offsetof(Smem, u) % 16 == 0, "bulk copy destinations need 16-byte alignment");
-    // CPS CTAs per SM share the 512 TMEM columns; shared memory keeps one more
-    // from becoming resident (its allocation would wait for another CTA to end)
-    static constexpr size_t kSmPerSm = 228 * 1024, kSmPerCta = sizeof(Smem) + 1024 + 1024;
-    static_assert(CPS * kSmPerCta <= kSmPerSm && (CPS + 1) * kSmPerCta > kSmPerSm,
+    // CPS CTAs per SM share the 512 TMEM columns; the shared memory a CTA asks
+    // for (its layout, 1 KB of alignment slack, the 1 KB the SM reserves per
+    // CTA) keeps one more from becoming resident (its TMEM allocation would
+    // wait for another CTA to end)
+    static constexpr size_t kSmPerSm = 228 * 1024;
+    static constexpr size_t kDynSmem = sizeof(Smem) + 1024 > kSmPerSm / (CPS + 1) + 1 - 1024
+                                           ? sizeof(Smem) + 1024
+                                           : kSmPerSm / (CPS + 1) + 1 - 1024;
+    static_assert(CPS * (kDynSmem + 1024) <= kSmPerSm && (CPS + 1) * (kDynSmem + 1024) > kSmPerSm,
                   "shared memory admits exactly CPS CTAs per SM");
     static_assert(CPS * kTmemCols <= 512 && (kTmemCols & (kTmemCols - 1)) == 0, "TMEM columns");
 };
@@ -567,7 +576,10 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         tc::fence_mbar_init();
         S.err = 0;
         S.gpair = -1;
+        S.pdi = 0;
+        S.pref = -1;
         S.td = fetch_tile(L, atomicAdd(L.work, 1u));
+        S.tdn = fetch_tile(L, atomicAdd(L.work, 1u));
         if (FLT) {
             tc::prefetch_tmap(&tmA);
             tc::prefetch_tmap(&tmB);
@@ -613,9 +625,6 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
     for (;;) {
         const TileDesc td = S.td;
         if (td.pair < 0 || S.err) break;
-        // the next tile, fetched while this one is processed
-        TileDesc tnext;
-        if (ctl) tnext = fetch_tile(L, atomicAdd(L.work, 1u));
         const int p = td.pair, mt = td.mt, kind = td.kind;
         const int64_t q_off = td.q_off, q_first = td.q_first;
         // binary pairs: Hamming distances by popcount, no operand rows; float
@@ -677,15 +686,28 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             qbrow[0] = __ldg(qrow);
             qbrow[1] = __ldg(qrow + 1);
         }
-        const bool newpair = p != S.gpair;
-        __syncthreads();
-        if (warp == 4 && newpair) {
-            copy16(&S.g, L.geom + p, (int)sizeof(PairGeom), lane);
-            copy16(&S.pd, L.pairs + p, (int)sizeof(PairDesc), lane);
-            if (lane == 0) S.gpair = p;
+        // the pair's geometry and table entry: kept from the last tile, or
+        // prefetched during it, or copied now
+        if (warp == 4) {
+            tc::cp_async_wait_all();  // the prefetch copies
+            if (p != S.gpair) {
+                if (p == S.pref) {
+                    __syncwarp();
+                    if (lane == 0) {
+                        S.pdi ^= 1;
+                        S.gpair = p;
+                    }
+                } else {
+                    const int pdi = S.pdi;
+                    __syncwarp();
+                    copy16(&S.g, L.geom + p, (int)sizeof(PairGeom), lane);
+                    copy16(&S.pd[pdi], L.pairs + p, (int)sizeof(PairDesc), lane);
+                    if (lane == 0) S.gpair = p;
+                }
+            }
         }
         __syncthreads();
-        const PairDesc &P = S.pd;
+        const PairDesc &P = S.pd[S.pdi];
         const PairGeom &G = S.g;
         if (warp == 4) {
             const uint32_t nz = __ballot_sync(0xffffffffu, G.cnt[lane] > 0);
@@ -798,20 +820,37 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 }
             }
         }
-        if (ctl) S.tdn = tnext;  // landed by now (its loads were issued at the tile start)
         // the hull arrays' last generic accesses before the record stages they
         // share are written by bulk copies again
         tc::fence_proxy_async();
         __syncthreads();
         const int nbox = S.nbox;
         const int nchunk = (nbox + kCB - 1) / kCB;
-        // the next tile's query order entries, loaded while this tile runs
+        // the next tile's query order entries, loaded while this tile runs,
+        // and (warp 4) its pair's geometry and table entry: the geometry is not
+        // read after the windows
         staged = false;
+        int64_t qoff_next = 0;
         {
             const TileDesc &tn = S.tdn;
             if (warp < 4 && tn.pair >= 0 && !(FLT && tn.kind == EGM_DESC_F32_L2) && tid < tn.mt) {
                 qi_next = L.qperm[tn.q_first + tid];
+                qoff_next = tn.q_off;
                 staged = true;
+            }
+            if (warp == 4) {
+                const int pn = tn.pair;
+                const bool pre = pn >= 0 && pn != p;
+                if (pre) {
+                    const uint4 *gs = reinterpret_cast<const uint4 *>(L.geom + pn);
+                    uint4 *gd = reinterpret_cast<uint4 *>(&S.g);
+                    for (int k = lane; k < (int)(sizeof(PairGeom) / 16); k += 32) tc::cp_async16(gd + k, gs + k);
+                    const uint4 *ps = reinterpret_cast<const uint4 *>(L.pairs + pn);
+                    uint4 *pdst = reinterpret_cast<uint4 *>(&S.pd[S.pdi ^ 1]);
+                    for (int k = lane; k < (int)(sizeof(PairDesc) / 16); k += 32) tc::cp_async16(pdst + k, ps + k);
+                }
+                __syncwarp();
+                if (lane == 0) S.pref = pre ? pn : -1;
             }
         }
 
@@ -906,6 +945,8 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             }
             // the query tile's load completes before its buffer is reused
             if (nchunk == 0 && !pop) wait(&S.afull, (armA - 1u) & 1u);
+            // the tile after the next one, while the epilogue runs
+            S.tdnn = fetch_tile(L, atomicAdd(L.work, 1u));
         }
 
         // ---- epilogue warps: operand rows, tests and best two over this warp's columns
@@ -1260,7 +1301,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         if (qv) store_match(L, q_off + qi, P, r.flags, b1, b2);
         if (staged) {
             // every MMA of this tile is done and stage 1 holds no binary rows
-            const uint8_t *src = reinterpret_cast<const uint8_t *>(L.qrec + S.tdn.q_off + qi_next);
+            const uint8_t *src = reinterpret_cast<const uint8_t *>(L.qrec + qoff_next + qi_next);
             uint8_t *dst = S.B[1][0] + tid * sizeof(QueryRec);
             tc::cp_async16(dst, src);
             tc::cp_async16(dst + 16, src + 16);
@@ -1269,7 +1310,10 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         // generic accesses of this tile (query rows, binary rows, widened
         // rows) before the next tile's copies into the same memory
         tc::fence_proxy_async();
-        if (ctl) S.td = S.tdn;
+        if (ctl) {
+            S.td = S.tdn;
+            S.tdn = S.tdnn;
+        }
         __syncthreads();
     }
     tc::cp_async_wait_all();
@@ -1364,7 +1408,7 @@ cudaError_t launch_pack(const Launch &L, cudaStream_t s) {
 template <int CB, int CPS, bool FLT>
 cudaError_t launch_band_shape(const Launch &L, int sms, const CUtensorMap &tA, const CUtensorMap &tB,
                               bool zero_work, bool pdl, cudaStream_t s) {
-    const int smem = (int)sizeof(BandSmem<CB>) + 1024;
+    const int smem = (int)BandShape<CB, CPS>::kDynSmem;
     int64_t grid = L.ntiles;
     if (grid > CPS * (int64_t)sms) grid = CPS * (int64_t)sms;
     cudaError_t e;
@@ -1378,7 +1422,7 @@ cudaError_t launch_band_shape(const Launch &L, int sms, const CUtensorMap &tA, c
     return cudaGetLastError();
 }
 
-int band_shapes() { return 3; }
+int band_shapes() { return 7; }
 
 cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s, bool zero_work) {
     if (L.ntiles == 0) return cudaSuccess;
@@ -1397,6 +1441,10 @@ cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s, boo
         case 0: return launch_band_shape<4, 2, false>(L, sms, tA, tB, zero_work, zero_work, s);
         case 1: return launch_band_shape<2, 3, false>(L, sms, tA, tB, zero_work, zero_work, s);
         case 2: return launch_band_shape<1, 4, false>(L, sms, tA, tB, zero_work, zero_work, s);
+        case 3: return launch_band_shape<1, 3, false>(L, sms, tA, tB, zero_work, zero_work, s);
+        case 4: return launch_band_shape<2, 2, false>(L, sms, tA, tB, zero_work, zero_work, s);
+        case 5: return launch_band_shape<4, 1, false>(L, sms, tA, tB, zero_work, zero_work, s);
+        case 6: return launch_band_shape<1, 2, false>(L, sms, tA, tB, zero_work, zero_work, s);
         default: return cudaErrorInvalidValue;
     }
 }

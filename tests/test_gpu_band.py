@@ -263,7 +263,7 @@ def test_every_tile_shape_and_the_tuner(mt):
     mt.set_params(form=FORM_PLAIN)
     ref = {k: v.cpu().numpy() for k, v in mt.match_batch(items).items()}
     try:
-        for tile in (1, 2, 3, 0, 0):
+        for tile in (1, 2, 3, 4, 5, 6, 7, 0, 0):
             mt.set_params(form=FORM_BANDED, band_tile=tile)
             got = {k: v.cpu().numpy() for k, v in mt.match_batch(items).items()}
             for k in KEYS:
@@ -275,7 +275,7 @@ def test_every_tile_shape_and_the_tuner(mt):
         mt.set_params(form=FORM_AUTO, band_tile=0)
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7])
 def test_each_tile_shape_on_ragged_and_full_size_pairs(mt, tile):
     """Each forced tile shape (boxes per chunk, CTAs per SM) on ragged tiles
     and boxes and on a full-size pair: outputs equal the plain form's."""
@@ -438,7 +438,7 @@ def test_regime_tuner_cache_export_import(mt):
     entries = mt.tuner_entries()
     assert len(entries) >= 1
     e = [x for x in entries if not x["one_pair"]][0]
-    assert e["form"] in ("plain", "banded") and 0 <= e["band_tile"] < 3
+    assert e["form"] in ("plain", "banded") and 0 <= e["band_tile"] < 7
     assert e["ms_plain"] > 0 and e["ms_band"] > 0
     assert (e["form"] == "banded") == (e["ms_band"] < e["ms_plain"])
     blob = mt.tuner_export()
