@@ -779,11 +779,14 @@ def batched_leg(mt, torch, stream, args, world, local):
                "tuned_regimes": mt.tuner_entries()}
     if bform != 1:
         # the band kernel over the batch, on the method's algorithmic bytes
-        # (each pair's inputs read once, its results written once); the
-        # kernel's own layout (packed 256-byte operand rows, sorted records,
-        # norms) beside them
+        # (each pair's inputs read once, its results written once); beside
+        # them the kernel's own layout read once: per query its order entry,
+        # FP32 record, descriptor row and outputs, per reference its sorted
+        # record and descriptor row (re-reads of a row by neighbouring tiles
+        # not counted)
         kb = sum(algorithmic_bytes(s) for s in bsc)
-        lb = bM * (256 + 48 + 17) + sum(s.n for s in bsc) * (256 + 16 + 16)
+        lb = sum(s.m * (4 + 48 + desc_row_bytes(s.kind, s.dim) + 17) + s.n * (16 + desc_row_bytes(s.kind, s.dim))
+                 for s in bsc)
         ks = bstage["stab"] * 1e-3
         peak, peak_kind = measured_peaks()
         prof = kernel_profile("band_kernel", "batch")
@@ -931,14 +934,14 @@ def run_ours(args):
 
     def layout_bytes(sc, band):
         """The kernel's own layout: what it reads and writes per launch."""
+        row = sc.desc1.shape[1]
         if band:
-            # every query's packed operand row (256 B), sorted record (48 B) and
-            # result (17 B) once; every reference's packed row (256 B), record
-            # (16 B) and norms (16 B) once
-            return sc.m * (256 + 48 + 17) + sc.n * (256 + 16 + 16)
+            # every query's order entry (4 B), line record (48 B), descriptor
+            # and result (17 B) once; every reference's record (16 B) and
+            # descriptor once
+            return sc.m * (4 + 48 + row + 17) + sc.n * (16 + row)
         # every query's line record (48 B), descriptor and result (17 B) once;
         # every reference's record (16 B) and descriptor once
-        row = sc.desc1.shape[1]
         return sc.m * (48 + row + 17) + sc.n * (16 + row)
 
     kt = {False: 0.0, True: 0.0}
