@@ -291,6 +291,7 @@ struct TileDesc {
 };
 
 constexpr uint32_t kOperandArrivals = 5; // fullB / afull: the control thread and the four epilogue warps
+constexpr int kDeferCap = 16;            // FP64 tests a warp defers per tile (more: decided at once)
 
 template <int CB>
 struct BandSmem {
@@ -328,6 +329,10 @@ struct BandSmem {
     int32_t lv[kLevels];
     int32_t nlev, npc, nbox;
     int32_t gpair, pdi, pref;     // pair in g and pd[pdi]; pair prefetched into g and pd[pdi ^ 1] (-1: none)
+    // u8 and binary tiles: each epilogue warp's pairs left to the FP64 test,
+    // (distance key, reference, owner lane), decided together at the tile end
+    uint4 xq[4][kDeferCap];
+    uint32_t xn[4];
     TileDesc td, tdn, tdnn;       // the tile being processed; the next two
     uint32_t tmem;
     volatile uint32_t err;
@@ -578,6 +583,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         S.gpair = -1;
         S.pdi = 0;
         S.pref = -1;
+        for (int w = 0; w < 4; w++) S.xn[w] = 0u;
         S.td = fetch_tile(L, atomicAdd(L.work, 1u));
         S.tdn = fetch_tile(L, atomicAdd(L.work, 1u));
         if (FLT) {
@@ -1160,11 +1166,36 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                             cm &= gm;
                             uint32_t exm = um & ~cm & gm;  // left to the FP64 expression
                             nwin += __popc(gm);
-                            // FP32 inconclusive: the brute-force FP64 expression decides
+                            // FP32 inconclusive: the brute-force FP64 expression decides.
+                            // Float rows at once; u8 and binary rows with their
+                            // distance key formed now (the accumulator and the rows
+                            // are gone by then) and the test deferred to the tile end,
+                            // where the warp's lanes run the deferred tests together
                             for (uint32_t m = exm; m; m &= m - 1u) {
                                 const int k = __ffs(m) - 1;
                                 nexact++;
-                                if (exact_pair(P, qi, __float_as_uint(recb[g + k].w))) cm |= 1u << k;
+                                const uint32_t jk = __float_as_uint(recb[g + k].w);
+                                if (isf) {
+                                    if (exact_pair(P, qi, jk)) cm |= 1u << k;
+                                    continue;
+                                }
+                                uint32_t dh;
+                                if (pop) {
+                                    const uint4 *rb = reinterpret_cast<const uint4 *>(binb + (g + k) * kBinRowB);
+                                    const uint4 r0 = rb[0], r1 = rb[1], q0 = qbrow[0], q1 = qbrow[1];
+                                    dh = __popc(q0.x ^ r0.x) + __popc(q0.y ^ r0.y) + __popc(q0.z ^ r0.z) +
+                                         __popc(q0.w ^ r0.w) + __popc(q1.x ^ r1.x) + __popc(q1.y ^ r1.y) +
+                                         __popc(q1.z ^ r1.z) + __popc(q1.w ^ r1.w);
+                                } else {
+                                    dh = __float_as_uint(fmaf(-2.0f, __uint_as_float(pick8(v, k)), qn + n8b[g + k]));
+                                }
+                                const uint32_t slot = atomicAdd(&S.xn[warp], 1u);
+                                if (slot < (uint32_t)kDeferCap) {
+                                    S.xq[warp][slot] = make_uint4(dh, jk, (uint32_t)lane, 0u);
+                                } else if (exact_pair(P, qi, jk)) {
+                                    ncand++;
+                                    top2(((unsigned long long)dh << 32) | jk, b1, b2);
+                                }
                             }
                             if (pop) {
                                 // Hamming distance of the binary rows by popcount
@@ -1192,9 +1223,14 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                                     dk[k] = __float_as_uint(fmaf(-2.0f, __uint_as_float(v[k]), qn + nk[k]));
                                     jv[k] = __float_as_uint(rcs[k].w);
                                 }
-                                for (; cm; cm &= cm - 1u) {
+                                // a candidate farther than the second best so far cannot enter
+                                ncand += __popc(cm);
+                                const uint32_t d2 = (uint32_t)(b2 >> 32);
+                                uint32_t near = 0u;
+#pragma unroll
+                                for (int k = 0; k < kGroup; k++) near |= (uint32_t)(dk[k] <= d2) << k;
+                                for (cm &= near; cm; cm &= cm - 1u) {
                                     const int k = __ffs(cm) - 1;
-                                    ncand++;
                                     top2(((unsigned long long)pick8(dk, k) << 32) | pick8(jv, k), b1, b2);
                                 }
                             }
@@ -1224,6 +1260,31 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                     tc::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&S.tfree[st]);
+                }
+                if (!isf) {
+                    // the deferred FP64 tests of the warp, one per lane, then the
+                    // members into their owners' best two
+                    __syncwarp();
+                    const uint32_t n = min(S.xn[warp], (uint32_t)kDeferCap);
+                    if (n > 0) {
+                        uint4 e = make_uint4(0u, 0u, (uint32_t)lane, 0u);
+                        if ((uint32_t)lane < n) e = S.xq[warp][lane];
+                        const uint32_t qo = __shfl_sync(0xffffffffu, qi, (int)e.z);
+                        const bool mem = (uint32_t)lane < n && exact_pair(P, qo, e.y);
+                        for (uint32_t bal = __ballot_sync(0xffffffffu, mem); bal; bal &= bal - 1u) {
+                            const int src = __ffs(bal) - 1;
+                            const uint32_t owner = __shfl_sync(0xffffffffu, e.z, src);
+                            const uint32_t kh = __shfl_sync(0xffffffffu, e.x, src);
+                            const uint32_t kj = __shfl_sync(0xffffffffu, e.y, src);
+                            if ((uint32_t)lane == owner) {
+                                ncand++;
+                                top2(((unsigned long long)kh << 32) | kj, b1, b2);
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) S.xn[warp] = 0u;
+                    __syncwarp();
                 }
                 if (isf) {
                     // FP32 rerank, one query of the warp at a time, the lanes over the
