@@ -1270,7 +1270,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                         uint4 e = make_uint4(0u, 0u, (uint32_t)lane, 0u);
                         if ((uint32_t)lane < n) e = S.xq[warp][lane];
                         const uint32_t qo = __shfl_sync(0xffffffffu, qi, (int)e.z);
-                        const bool mem = (uint32_t)lane < n && exact_pair(P, qo, e.y);
+                        const bool mem = (uint32_t)lane < n && exact_pair_inline(P, qo, e.y);
                         for (uint32_t bal = __ballot_sync(0xffffffffu, mem); bal; bal &= bal - 1u) {
                             const int src = __ffs(bal) - 1;
                             const uint32_t owner = __shfl_sync(0xffffffffu, e.z, src);

@@ -515,13 +515,18 @@ __device__ __forceinline__ bool exact_within(double a, double b, double c, doubl
     return exact_member(a, b, c, exact_norm(a, b), x, y, eps);
 }
 
-// The brute-force FP64 decision for one (query, reference) pair, kept out of
-// line: it runs only when the FP32 test is inconclusive.
-static __device__ __noinline__ bool exact_pair(const PairDesc &P, int64_t i, uint32_t j) {
+// The brute-force FP64 decision for one (query, reference) pair.
+__device__ __forceinline__ bool exact_pair_inline(const PairDesc &P, int64_t i, uint32_t j) {
     double a, b, c;
     exact_line(P.F, P.xy1[2 * i], P.xy1[2 * i + 1], a, b, c);
     const double eps = P.eps2 ? P.eps2[j] : P.eps_scalar;
     return exact_within(a, b, c, P.xy2[2 * (int64_t)j], P.xy2[2 * (int64_t)j + 1], eps);
+}
+
+// The same, kept out of line for the loops where it runs only when the FP32
+// test is inconclusive.
+static __device__ __noinline__ bool exact_pair(const PairDesc &P, int64_t i, uint32_t j) {
+    return exact_pair_inline(P, i, j);
 }
 
 // Outputs of query gq from its best two (distance << 32 | index) keys:
