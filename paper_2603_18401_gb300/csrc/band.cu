@@ -290,62 +290,66 @@ struct TileDesc {
     int32_t pair, mt, kind;  // pair -1: no tile left
 };
 
-constexpr uint32_t kOperandArrivals = 5; // fullB / afull: the control thread and the four epilogue warps
+constexpr uint32_t kOperandArrivals = 5; // afull: the control thread and the four consumer warps
 constexpr int kDeferCap = 16;            // FP64 tests a warp defers per tile (more: decided at once)
+constexpr int kRS = 4;                   // record / norm / binary-row slots (chunk g in slot g mod kRS)
 
-template <int CB>
+template <int CB, bool FLT>
 struct BandSmem {
     static constexpr int kCN = kBoxR * CB;  // columns per chunk
     // query tile, K halves (1024-byte aligned); u8 tiles stage each query's
     // bytes in its own row of A[1] before widening them
     uint8_t A[2][kTM * 128];
-    // band chunk: stage, K half.  u8 tiles stage a chunk's gathered bytes in
-    // K half 1 of its stage; binary tiles keep four chunks of 32-byte rows
-    // (chunk c in slot c mod 4) in B[0][0]
+    // band chunk: operand stage, K half.  u8 tiles stage a chunk's gathered
+    // bytes in K half 1 of its stage; binary tiles keep kRS chunks of 32-byte
+    // rows (chunk g in slot g mod kRS) in B[0][0]
     uint8_t B[2][2][kCN * 128];
-    // The record stages are idle while a tile's windows are computed (every
-    // load of the previous tile has landed and been read, and the next ones
-    // are issued after), so the per-warp hulls share their memory.
+    // The record slots are idle while a tile's windows are computed (every
+    // chunk of the previous tile has been tested, and the next records are
+    // copied after), so the per-warp hulls share their memory.
     union {
         struct {
-            float4 rec[2][kCN];       // (x - cx, y - cy, eps, index) of each column
-            float4 rn[2][CB][kBoxR];  // float rows: (norm, rounding error, row scale, 0) of each box's rows
-            float n8[4][kCN];         // u8 rows: squared norms, chunk c in slot c mod 4
+            float4 rec[kRS][kCN];                  // (x - cx, y - cy, eps, index) of each column
+            float4 rn[FLT ? kRS : 1][CB][kBoxR];   // float rows: (norm, rounding error, row scale, 0)
+            float n8[kRS][kCN];                    // u8 rows: squared norms
         } io;
         struct {
-            float wlo[4][kLevels], whi[4][kLevels];  // each epilogue warp's hull per level index
+            float wlo[4][kLevels], whi[4][kLevels];  // each consumer warp's hull per level index
             int32_t wkind[4][kLevels];
         } hull;
     } u;
-    // fullB: a stage's operand rows are in place (TMA landed, or the epilogue
-    // warps wrote them); sfree: the MMA that read them is done; fullR: a
-    // stage's records (and float norms) landed; done: an accumulator is
-    // ready; tfree: the epilogue has read it and the stage's records
-    uint64_t fullB[2], sfree[2], fullR[2], done[2], tfree[2], afull;
+    // fullR: a slot's records (and float norms) landed; rows: the producer has
+    // written a chunk's rows (u8 norms, binary rows); rfree: the consumers have
+    // finished a slot's chunk; sfree: the MMA that read an operand stage is
+    // done; fullB: a stage's float rows landed (TMA); done: an accumulator is
+    // ready; tfree: the consumers have read it
+    uint64_t fullR[kRS], rows[kRS], rfree[kRS], sfree[2], fullB[2], done[4], tfree[4], afull;
     uint64_t probe;               // never arrived on: the wait of the timeout check (Launch::probe)
     PairGeom g;
-    PairDesc pd[2];               // the pair of the tile (pd[pdi]); the next tile's, prefetched
+    PairDesc pd;
     Piece pc[2 * kLevels];
     int32_t lv[kLevels];
-    int32_t nlev, npc, nbox;
-    int32_t gpair, pdi, pref;     // pair in g and pd[pdi]; pair prefetched into g and pd[pdi ^ 1] (-1: none)
-    // u8 and binary tiles: each epilogue warp's pairs left to the FP64 test,
+    int32_t nlev, npc, nbox, gpair;
+    TileDesc td, tdn, tdnn;       // the tile being processed; the next two
+    // u8 and binary tiles: each consumer warp's pairs left to the FP64 test,
     // (distance key, reference, owner lane), decided together at the tile end
     uint4 xq[4][kDeferCap];
     uint32_t xn[4];
-    TileDesc td, tdn, tdnn;       // the tile being processed; the next two
     uint32_t tmem;
     volatile uint32_t err;
 };
 
-template <int CB, int CPS>
+template <int CB, int CPS, bool FLT>
 struct BandShape {
     static constexpr int kCB = CB, kCN = kBoxR * CB;
-    static constexpr uint32_t kTmemCols = 2 * kCN;  // double-buffered accumulator (a power of two)
-    using Smem = BandSmem<CB>;
+    // accumulators: four where TMEM holds them for CPS CTAs, else two
+    static constexpr int kNA = 512 / (CPS * kCN) >= 4 ? 4 : 2;
+    static constexpr uint32_t kTmemCols = kNA * kCN;  // a power of two
+    using Smem = BandSmem<CB, FLT>;
     static_assert(offsetof(Smem, B) % 1024 == 0, "operand tiles need 1024-byte alignment");
     static_assert(kTM * sizeof(QueryRec) <= sizeof(Smem::B[1]), "a tile's query records fit operand stage 1");
     static_assert(offsetof(Smem, u) % 16 == 0, "bulk copy destinations need 16-byte alignment");
+    static_assert(kRS * kCN * kBinRowB <= sizeof(Smem::B[0][0]), "binary rows fit their slots");
     // CPS CTAs per SM share the 512 TMEM columns; the shared memory a CTA asks
     // for (its layout, 1 KB of alignment slack, the 1 KB the SM reserves per
     // CTA) keeps one more from becoming resident (its TMEM allocation would
@@ -553,13 +557,30 @@ __device__ __forceinline__ uint32_t sw128(int r, int c) { return (uint32_t)(r * 
 
 // FLT: float descriptor pairs may occur (compiled out otherwise: the rerank
 // state costs registers).
+//
+// Roles.  Warps 0-3 (the consumers, one thread per query of the tile): the
+// query records, their windows' hulls, the u8 query rows widened to FP16,
+// and per chunk the exact tests and the best two over their own columns.
+// Warp 4 (the producer): the tile's windows as runs of boxes; per chunk the
+// band's rows -- u8 rows gathered by the sorted records' indices (one row
+// per lane per box) and widened to FP16 in place, binary rows gathered into
+// a slot -- then (lane 0, the control thread) the records' bulk copies, the
+// tcgen05.mma chain and its commits.  Rings, indexed by the running chunk
+// number g of the CTA:
+//   records, u8 norms, binary rows   kRS slots (g mod kRS); a slot is reused
+//                                    once the consumers have finished its chunk
+//   operand stages                   2 (g mod 2); reused once the chunk's MMA is done
+//   accumulators                     kNA (g mod kNA); reused once the consumers
+//                                    have read them
+// so the producer runs up to kNA - 1 chunks ahead of the consumers and the
+// consumers do not wait for each other's rows.
 template <int CB, int CPS, bool FLT>
 __global__ void __launch_bounds__(kBandThreads, CPS)
     band_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Launch L) {
     pdl_begin();
-    using Shape = BandShape<CB, CPS>;
+    using Shape = BandShape<CB, CPS, FLT>;
     using BandSmem = typename Shape::Smem;
-    constexpr int kCB = Shape::kCB, kCN = Shape::kCN;
+    constexpr int kCB = Shape::kCB, kCN = Shape::kCN, kNA = Shape::kNA;
     constexpr uint32_t kTmemCols = Shape::kTmemCols;
     extern __shared__ uint8_t smraw[];
     // 1024-byte alignment by pointer arithmetic on the shared array, so that
@@ -569,10 +590,16 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
     const uint32_t lt = (1u << lane) - 1u;
     const bool ctl = tid == kTM;
     if (ctl) {
-        for (int s = 0; s < 2; s++) {
-            tc::mbar_init(&S.fullB[s], kOperandArrivals);
-            tc::mbar_init(&S.sfree[s], 1);
+        for (int s = 0; s < kRS; s++) {
             tc::mbar_init(&S.fullR[s], 1);
+            tc::mbar_init(&S.rows[s], 1);
+            tc::mbar_init(&S.rfree[s], 4);
+        }
+        for (int s = 0; s < 2; s++) {
+            tc::mbar_init(&S.sfree[s], 1);
+            tc::mbar_init(&S.fullB[s], 1);
+        }
+        for (int s = 0; s < kNA; s++) {
             tc::mbar_init(&S.done[s], 1);
             tc::mbar_init(&S.tfree[s], 4);
         }
@@ -581,8 +608,6 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         tc::fence_mbar_init();
         S.err = 0;
         S.gpair = -1;
-        S.pdi = 0;
-        S.pref = -1;
         for (int w = 0; w < 4; w++) S.xn[w] = 0u;
         S.td = fetch_tile(L, atomicAdd(L.work, 1u));
         S.tdn = fetch_tile(L, atomicAdd(L.work, 1u));
@@ -607,13 +632,13 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         atomicOr(L.status, kStTimeout);
         return false;
     };
-    uint32_t seq = 0;
+    uint32_t seq = 0;                           // chunks of earlier tiles (the rings' running count)
     uint32_t nwin = 0, ncand = 0, nexact = 0;  // per-thread counts (counters on)
-    // phases the control thread armed on each barrier (copies and MMAs issued)
-    // and whether the last one carries copies: after a failed wait, the CTA
-    // lets them complete before it leaves
-    uint32_t armB[2] = {0u, 0u}, armR[2] = {0u, 0u}, armD[2] = {0u, 0u}, armA = 0u;
-    bool txB[2] = {false, false}, txA = false;
+    // phases the control thread armed with copies or MMAs (records per slot,
+    // float operand loads per stage, the query tile, the MMA chain): after a
+    // failed wait, the CTA lets the last of each complete before it leaves
+    uint32_t armR[kRS] = {}, armB[2] = {0u, 0u}, armA = 0u, lastD = 0u;
+    bool anyD = false, txA = false;
     if (L.probe) {
         // the timeout check: a short wait on a barrier that nothing arrives
         // on, before any copy or MMA is issued, takes the error path below
@@ -628,6 +653,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
     // a tile into the operand stage 1 (idle by then) while the tile ends
     bool staged = false;
     uint32_t qi_next = 0;
+    int64_t qoff_next = 0;
     for (;;) {
         const TileDesc td = S.td;
         if (td.pair < 0 || S.err) break;
@@ -678,12 +704,13 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             armA++;
             txA = flt;
         }
-        // a u8 query's bytes: staged in its thread's row of A[1], widened once
-        // the windows are known (the copy's latency hides behind them)
+        // a u8 query's bytes: staged in its thread's row of A[1] (128-byte
+        // swizzle, so that the 32 rows of a warp spread over the banks),
+        // widened once the windows are known (the copy's latency hides behind them)
         if (cvt && qv) {
             const uint8_t *qrow = L.pairs[p].desc1 + (int64_t)qi * 128;
 #pragma unroll
-            for (int k = 0; k < 8; k++) tc::cp_async16(S.A[1] + tid * 128 + 16 * k, qrow + 16 * k);
+            for (int k = 0; k < 8; k++) tc::cp_async16(S.A[1] + sw128(tid, k), qrow + 16 * k);
         }
         // a binary query's row, in the idle query-tile buffer (its thread's slot)
         uint4 *qbrow = reinterpret_cast<uint4 *>(S.A[0] + tid * kBinRowB);
@@ -692,28 +719,15 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             qbrow[0] = __ldg(qrow);
             qbrow[1] = __ldg(qrow + 1);
         }
-        // the pair's geometry and table entry: kept from the last tile, or
-        // prefetched during it, or copied now
-        if (warp == 4) {
-            tc::cp_async_wait_all();  // the prefetch copies
-            if (p != S.gpair) {
-                if (p == S.pref) {
-                    __syncwarp();
-                    if (lane == 0) {
-                        S.pdi ^= 1;
-                        S.gpair = p;
-                    }
-                } else {
-                    const int pdi = S.pdi;
-                    __syncwarp();
-                    copy16(&S.g, L.geom + p, (int)sizeof(PairGeom), lane);
-                    copy16(&S.pd[pdi], L.pairs + p, (int)sizeof(PairDesc), lane);
-                    if (lane == 0) S.gpair = p;
-                }
-            }
+        // the pair's geometry and table entry (kept from the last tile of the pair)
+        if (warp == 4 && p != S.gpair) {
+            __syncwarp();
+            copy16(&S.g, L.geom + p, (int)sizeof(PairGeom), lane);
+            copy16(&S.pd, L.pairs + p, (int)sizeof(PairDesc), lane);
+            if (lane == 0) S.gpair = p;
         }
         __syncthreads();
-        const PairDesc &P = S.pd[S.pdi];
+        const PairDesc &P = S.pd;
         const PairGeom &G = S.g;
         if (warp == 4) {
             const uint32_t nz = __ballot_sync(0xffffffffu, G.cnt[lane] > 0);
@@ -832,11 +846,8 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         __syncthreads();
         const int nbox = S.nbox;
         const int nchunk = (nbox + kCB - 1) / kCB;
-        // the next tile's query order entries, loaded while this tile runs,
-        // and (warp 4) its pair's geometry and table entry: the geometry is not
-        // read after the windows
+        // the next tile's query order entries, loaded while this tile runs
         staged = false;
-        int64_t qoff_next = 0;
         {
             const TileDesc &tn = S.tdn;
             if (warp < 4 && tn.pair >= 0 && !(FLT && tn.kind == EGM_DESC_F32_L2) && tid < tn.mt) {
@@ -844,43 +855,35 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 qoff_next = tn.q_off;
                 staged = true;
             }
-            if (warp == 4) {
-                const int pn = tn.pair;
-                const bool pre = pn >= 0 && pn != p;
-                if (pre) {
-                    const uint4 *gs = reinterpret_cast<const uint4 *>(L.geom + pn);
-                    uint4 *gd = reinterpret_cast<uint4 *>(&S.g);
-                    for (int k = lane; k < (int)(sizeof(PairGeom) / 16); k += 32) tc::cp_async16(gd + k, gs + k);
-                    const uint4 *ps = reinterpret_cast<const uint4 *>(L.pairs + pn);
-                    uint4 *pdst = reinterpret_cast<uint4 *>(&S.pd[S.pdi ^ 1]);
-                    for (int k = lane; k < (int)(sizeof(PairDesc) / 16); k += 32) tc::cp_async16(pdst + k, ps + k);
-                }
-                __syncwarp();
-                if (lane == 0) S.pref = pre ? pn : -1;
-            }
         }
 
-        if (ctl) {
-            // ---- control.  The operand stage of chunk c + 2 opens once the
-            // MMA of chunk c has read it (TMA rows: loaded then; u8 and binary
-            // rows: written by the epilogue warps, which also arrive); the
-            // records and float norms of chunk c load once the epilogue has
-            // finished chunk c - 2.  At a tile start every stage and
-            // accumulator is free.
-            BoxCursor curB, curR;
-            auto issueB = [&](int c) {
-                const uint32_t sq = seq + (uint32_t)c, st = sq & 1u, use = sq >> 1;
-                if (!flt) {
-                    tc::mbar_arrive(&S.fullB[st]);
-                    armB[st]++;
-                    txB[st] = false;
-                    return;
+        if (warp == 4) {
+            // ---- producer
+            BoxCursor curR, curB;
+            // records (and float norms) of chunk c into slot g mod kRS (control
+            // thread; the slot's previous chunk is finished)
+            auto issueR = [&](int c) {
+                const uint32_t g = seq + (uint32_t)c, s = g % kRS;
+                const int nb = min(kCB, nbox - c * kCB);
+                tc::mbar_arrive_expect_tx(&S.fullR[s], (uint32_t)nb * (kBoxR * 16) * (flt ? 2u : 1u));
+                armR[s]++;
+                for (int bb = 0; bb < nb; bb++) {
+                    uint32_t pos, len;
+                    int li;
+                    curR.next(S, pos, len, li);
+                    const int64_t row = P.r_off + pos;
+                    tc::bulk_load(&S.u.io.rec[s][bb * kBoxR], L.rec + row, kBoxR * 16, &S.fullR[s]);
+                    if (flt) tc::bulk_load(&S.u.io.rn[FLT ? s : 0][bb][0], L.rnorm + row, kBoxR * 16, &S.fullR[s]);
                 }
-                if (c >= 2 && !wait(&S.sfree[st], (use - 1) & 1u)) return;
+            };
+            // float rows of chunk c by TMA into operand stage g mod 2, once the
+            // MMA of chunk g - 2 is done (control thread)
+            auto issueB = [&](int c) {
+                const uint32_t g = seq + (uint32_t)c, st = g & 1u;
+                if (g >= 2u && !wait(&S.sfree[st], ((g - 2u) >> 1) & 1u)) return;
                 const int nb = min(kCB, nbox - c * kCB);
                 tc::mbar_arrive_expect_tx(&S.fullB[st], (uint32_t)nb * (2 * kBoxR * 128));
                 armB[st]++;
-                txB[st] = true;
                 for (int bb = 0; bb < nb; bb++) {
                     uint32_t pos, len;
                     int li;
@@ -890,90 +893,27 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                     tc::tma_load_2d(S.B[st][1] + bb * kBoxR * 128, &tmB, 128, row, &S.fullB[st]);
                 }
             };
-            auto issueR = [&](int c) {
-                const uint32_t st = (seq + (uint32_t)c) & 1u;
-                const int nb = min(kCB, nbox - c * kCB);
-                // records, and the norms of float rows
-                tc::mbar_arrive_expect_tx(&S.fullR[st], (uint32_t)nb * (kBoxR * 16) * (flt ? 2u : 1u));
-                armR[st]++;
-                for (int bb = 0; bb < nb; bb++) {
-                    uint32_t pos, len;
-                    int li;
-                    curR.next(S, pos, len, li);
-                    const int64_t row = P.r_off + pos;
-                    tc::bulk_load(&S.u.io.rec[st][bb * kBoxR], L.rec + row, kBoxR * 16, &S.fullR[st]);
-                    if (flt) tc::bulk_load(&S.u.io.rn[st][bb][0], L.rnorm + row, kBoxR * 16, &S.fullR[st]);
+            // u8 and binary rows of chunk c, one row per lane and box, by the
+            // indices in its records: u8 bytes into K half 1 of operand stage
+            // g mod 2 (128-byte swizzle), once the MMA of chunk g - 2 is done;
+            // binary rows into slot g mod kRS of B[0][0] (free: its records'
+            // slot was).  Returns the boxes whose row this lane copied.
+            // Records are copied in chunk order as far ahead as their slots allow,
+            // without waiting (try_wait), and waited for only at the tile end
+            // (the consumers wait for them anyway).
+            int nextR = 0;
+            auto pollR = [&](int upto, bool block) {
+                while (nextR < nchunk && nextR <= upto) {
+                    const uint32_t g = seq + (uint32_t)nextR, s = g % kRS;
+                    if (g >= (uint32_t)kRS) {
+                        const uint32_t par = ((g - kRS) / kRS) & 1u;
+                        if (block ? !wait(&S.rfree[s], par) : !tc::mbar_try_wait(&S.rfree[s], par)) break;
+                    }
+                    issueR(nextR++);
                 }
             };
-            for (int c = 0; c < nchunk && c < 2; c++) {
-                issueR(c);
-                issueB(c);
-            }
-            // operand types: E4M3 (float rows of the FP8 pass), BF16 (float
-            // rows), FP16 (u8 rows)
-            const bool e4m3 = flt && L.fp8;
-            for (int c = 0; c < nchunk; c++) {
-                const uint32_t sq = seq + (uint32_t)c, st = sq & 1u, use = sq >> 1;
-                bool ok = true;
-                if (c >= 2) {
-                    ok = wait(&S.tfree[st], (use - 1) & 1u);
-                    if (ok) issueR(c);
-                }
-                ok = wait(&S.fullB[st], use & 1u) && ok;
-                if (c == 0 && !pop) ok = wait(&S.afull, (armA - 1u) & 1u) && ok;
-                if (!ok) continue;
-                if (pop) {
-                    // no product: the accumulator and the stage are free at once
-                    tc::mbar_arrive(&S.done[st]);
-                    tc::mbar_arrive(&S.sfree[st]);
-                    armD[st]++;
-                    if (c + 2 < nchunk) issueB(c + 2);
-                    continue;
-                }
-                tc::tc_fence_after();
-                const int nb = min(kCB, nbox - c * kCB);
-                const uint32_t idesc = e4m3  ? tc::idesc_e4m3(kTM, nb * kBoxR)
-                                       : flt ? tc::idesc_bf16(kTM, nb * kBoxR)
-                                             : tc::idesc_f16(kTM, nb * kBoxR);
-                const uint32_t dcol = tmem + st * kCN;
-#pragma unroll
-                for (int k = 0; k < 8; k++) {
-                    const int h = k >> 2, kk = k & 3;
-                    const uint64_t ad = tc::sdesc_sw128(tc::smem_addr(S.A[h]) + 32 * kk);
-                    const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(S.B[st][h]) + 32 * kk);
-                    if (e4m3) tc::mma_e4m3(dcol, ad, bd, idesc, k > 0);
-                    else tc::mma_f16(dcol, ad, bd, idesc, k > 0);
-                }
-                tc::mma_commit(&S.done[st]);
-                tc::mma_commit(&S.sfree[st]);
-                armD[st]++;
-                if (c + 2 < nchunk) issueB(c + 2);
-            }
-            // the query tile's load completes before its buffer is reused
-            if (nchunk == 0 && !pop) wait(&S.afull, (armA - 1u) & 1u);
-            // the tile after the next one, while the epilogue runs
-            S.tdnn = fetch_tile(L, atomicAdd(L.work, 1u));
-        }
-
-        // ---- epilogue warps: operand rows, tests and best two over this warp's columns
-        unsigned long long b1 = ~0ull, b2 = ~0ull;
-        const bool isf = flt;
-        FBuf fb;
-        fb.init();
-        if (warp < 4) {
-            // Rows of chunk c + 2, fetched while chunk c is tested: the row
-            // indices (loaded one chunk earlier) pick the rows; u8 bytes go to
-            // K half 1 of the operand stage of chunk c (its MMA is done) and
-            // are widened to FP16 in place (4 threads a row, 32 bytes each),
-            // their norms to slot c + 2 mod 4; binary rows go to slot c + 2
-            // mod 4 (2 threads a row).  The epilogue of chunk c - 2, the last
-            // reader of those slots, has ended in every warp: the MMA of chunk
-            // c waited for it.
-            const int grow = cvt ? (tid >> 2) : (tid >> 1);  // the row this thread copies in each box
-            const int gpart = cvt ? (tid & 3) : (tid & 1);
-            const bool gthr = cvt || (pop && tid < 2 * kBoxR);
+            // the row indices of chunk c, lane = row of each box (all ones: none)
             BoxCursor curJ;
-            // row indices of chunk c (all ones: no row)
             auto jload = [&](int c, uint32_t (&jj)[kCB]) {
                 const int nb = c < nchunk ? min(kCB, nbox - c * kCB) : 0;
 #pragma unroll
@@ -983,76 +923,160 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                         uint32_t pos, len;
                         int li;
                         curJ.next(S, pos, len, li);
-                        if (gthr && (uint32_t)grow < len)
-                            jj[bb] = __float_as_uint(__ldg(&L.rec[P.r_off + pos + grow].w));
+                        if ((uint32_t)lane < len) jj[bb] = __float_as_uint(__ldg(&L.rec[P.r_off + pos + lane].w));
                     }
                 }
             };
-            // copies of chunk c's rows; returns the boxes whose row this thread copied
-            auto gather_issue = [&](int c, const uint32_t (&jj)[kCB]) {
-                const uint32_t gs = seq + (uint32_t)c;
-                uint32_t gv = 0;
+            auto gather = [&](int c, const uint32_t (&jj)[kCB]) -> uint32_t {
+                const uint32_t g = seq + (uint32_t)c, s = g % kRS, st = g & 1u;
+                // the slot's previous chunk tested (binary rows, u8 norms) and the
+                // operand stage's previous MMA done (u8 bytes)
+                bool ok = g < (uint32_t)kRS || wait(&S.rfree[s], ((g - kRS) / kRS) & 1u);
+                if (cvt && g >= 2u) ok = wait(&S.sfree[st], ((g - 2u) >> 1) & 1u) && ok;
+                const int nb = min(kCB, nbox - c * kCB);
+                uint32_t gv = 0u;
 #pragma unroll
                 for (int bb = 0; bb < kCB; bb++) {
+                    if (bb >= nb) break;
                     const uint32_t j = jj[bb];
-                    if (j >= (uint32_t)P.n) continue;  // no row (or out of range: never copied)
+                    if (!ok || j >= (uint32_t)P.n) continue;  // no row (j never exceeds n otherwise)
+                    const int R = bb * kBoxR + lane;
                     if (cvt) {
-                        const uint8_t *src = P.desc2 + (int64_t)j * 128 + gpart * 32;
-                        uint8_t *dst = S.B[gs & 1u][1] + (bb * kBoxR + grow) * 128 + gpart * 32;
-                        tc::cp_async16(dst, src);
-                        tc::cp_async16(dst + 16, src + 16);
+                        const uint8_t *src = P.desc2 + (int64_t)j * 128;
+#pragma unroll
+                        for (int k = 0; k < 8; k++) tc::cp_async16(S.B[st][1] + sw128(R, k), src + 16 * k);
                         gv |= 1u << bb;
-                    } else if (pop) {
-                        tc::cp_async16(S.B[0][0] + ((c & 3) * kCN + bb * kBoxR + grow) * kBinRowB + gpart * 16,
-                                       P.desc2 + (int64_t)j * kBinRowB + gpart * 16);
+                    } else {
+                        uint8_t *dst = S.B[0][0] + ((int)s * kCN + R) * kBinRowB;
+                        tc::cp_async16(dst, P.desc2 + (int64_t)j * kBinRowB);
+                        tc::cp_async16(dst + 16, P.desc2 + (int64_t)j * kBinRowB + 16);
                     }
                 }
+                tc::cp_async_commit();
                 return gv;
             };
-            // chunk c's rows in place (u8: widened, norms) and the warp's arrival
-            auto gather_finish = [&](int c, uint32_t gv) {
-                const uint32_t gs = seq + (uint32_t)c;
-                tc::cp_async_wait_all();
-                if (cvt) {
-                    const int nb = min(kCB, nbox - c * kCB);
+            // u8 rows of chunk c widened in place (each lane its own rows:
+            // K half 0 from staged chunks 0-3, then half 1 over the staged
+            // bytes from chunks 4-7) and their norms into slot g mod kRS
+            auto widen_rows = [&](int c, uint32_t gv) {
+                const uint32_t g = seq + (uint32_t)c, s = g % kRS, st = g & 1u;
+                const int nb = min(kCB, nbox - c * kCB);
 #pragma unroll
-                    for (int bb = 0; bb < kCB; bb++) {
-                        if (bb >= nb) break;
-                        const int R = bb * kBoxR + grow;
-                        uint4 x0 = make_uint4(0u, 0u, 0u, 0u), x1 = x0;
-                        const uint8_t *stg = S.B[gs & 1u][1] + R * 128 + gpart * 32;
-                        if ((gv >> bb) & 1u) {
-                            x0 = *reinterpret_cast<const uint4 *>(stg);
-                            x1 = *reinterpret_cast<const uint4 *>(stg + 16);
+                for (int bb = 0; bb < kCB; bb++) {
+                    if (bb >= nb) break;
+                    const int R = bb * kBoxR + lane;
+                    const bool have = (gv >> bb) & 1u;
+                    uint32_t nrm = 0;
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        uint4 w[4];
+#pragma unroll
+                        for (int k = 0; k < 4; k++)
+                            w[k] = have ? *reinterpret_cast<const uint4 *>(S.B[st][1] + sw128(R, 4 * h + k))
+                                        : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            uint4 o0, o1;
+                            widen16(w[k], o0, o1, nrm);
+                            *reinterpret_cast<uint4 *>(S.B[st][h] + sw128(R, 2 * k)) = o0;
+                            *reinterpret_cast<uint4 *>(S.B[st][h] + sw128(R, 2 * k + 1)) = o1;
                         }
-                        // the row's four threads (lanes of this warp) have read its
-                        // staged bytes before K half 1 overwrites them
-                        __syncwarp();
-                        uint32_t nrm = 0;
-                        uint4 o0, o1, o2, o3;
-                        widen16(x0, o0, o1, nrm);
-                        widen16(x1, o2, o3, nrm);
-                        // bytes [32 part, 32 part + 32) are values of K half part / 2,
-                        // chunks 4 (part mod 2) .. + 3 of the row
-                        uint8_t *dh = S.B[gs & 1u][gpart >> 1];
-                        const int c0 = 4 * (gpart & 1);
-                        *reinterpret_cast<uint4 *>(dh + sw128(R, c0)) = o0;
-                        *reinterpret_cast<uint4 *>(dh + sw128(R, c0 + 1)) = o1;
-                        *reinterpret_cast<uint4 *>(dh + sw128(R, c0 + 2)) = o2;
-                        *reinterpret_cast<uint4 *>(dh + sw128(R, c0 + 3)) = o3;
-                        nrm += __shfl_xor_sync(0xffffffffu, nrm, 1);
-                        nrm += __shfl_xor_sync(0xffffffffu, nrm, 2);
-                        if (gpart == 0) S.u.io.n8[c & 3][R] = (float)nrm;
                     }
+                    S.u.io.n8[s][R] = (float)nrm;
+                }
+            };
+            // E4M3 operands: float rows of the FP8 pass
+            const bool e4m3 = flt && L.fp8;
+            uint32_t j1[kCB], j2[kCB];
+            if (!flt) {
+                jload(0, j1);
+                jload(1, j2);
+            }
+            if (ctl) {
+                pollR(1, true);
+                if (flt && nchunk > 0) issueB(0);
+            }
+            __syncwarp();
+            uint32_t gv = (nchunk > 0 && !flt) ? gather(0, j1) : 0u;
+            if (!flt) {
+#pragma unroll
+                for (int bb = 0; bb < kCB; bb++) j1[bb] = j2[bb];
+                jload(2, j2);
+            }
+            for (int c = 0; c < nchunk; c++) {
+                const uint32_t g = seq + (uint32_t)c, s = g % kRS, st = g & 1u, as = g % kNA;
+                const bool more = c + 1 < nchunk;
+                // the next chunk's rows in flight while this one is widened
+                uint32_t gvn = 0u;
+                if (!flt && more) {
+                    gvn = gather(c + 1, j1);
+#pragma unroll
+                    for (int bb = 0; bb < kCB; bb++) j1[bb] = j2[bb];
+                    jload(c + 3, j2);
+                }
+                if (!flt) {
+                    if (more) tc::cp_async_wait_group<1>();
+                    else tc::cp_async_wait_group<0>();
+                    if (cvt) widen_rows(c, gv);
                     tc::fence_proxy_async();
                 }
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&S.fullB[gs & 1u]);
-            };
-            // the row indices of chunks 0 and 1 load while the query rows are widened
-            uint32_t jc[kCB], jn[kCB];
-            jload(0, jc);
-            jload(1, jn);
+                gv = gvn;
+                if (ctl) {
+                    // the chunk's norms and binary rows are visible to the consumers
+                    tc::mbar_arrive(&S.rows[s]);
+                    if (flt && more) issueB(c + 1);
+                    bool ok = true;
+                    if (g >= (uint32_t)kNA) ok = wait(&S.tfree[as], ((g - kNA) / kNA) & 1u);
+                    if (flt) ok = wait(&S.fullB[st], (armB[st] - 1u) & 1u) && ok;
+                    if (c == 0 && !pop) ok = wait(&S.afull, (armA - 1u) & 1u) && ok;
+                    if (ok) {
+                        if (pop) {
+                            // no product: the accumulator and the stage are free at once
+                            tc::mbar_arrive(&S.done[as]);
+                            tc::mbar_arrive(&S.sfree[st]);
+                        } else {
+                            tc::tc_fence_after();
+                            const int nb = min(kCB, nbox - c * kCB);
+                            const uint32_t idesc = e4m3  ? tc::idesc_e4m3(kTM, nb * kBoxR)
+                                                   : flt ? tc::idesc_bf16(kTM, nb * kBoxR)
+                                                         : tc::idesc_f16(kTM, nb * kBoxR);
+                            const uint32_t dcol = tmem + as * kCN;
+#pragma unroll
+                            for (int k = 0; k < 8; k++) {
+                                const int h = k >> 2, kk = k & 3;
+                                const uint64_t ad = tc::sdesc_sw128(tc::smem_addr(S.A[h]) + 32 * kk);
+                                const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(S.B[st][h]) + 32 * kk);
+                                if (e4m3) tc::mma_e4m3(dcol, ad, bd, idesc, k > 0);
+                                else tc::mma_f16(dcol, ad, bd, idesc, k > 0);
+                            }
+                            tc::mma_commit(&S.done[as]);
+                            tc::mma_commit(&S.sfree[st]);
+                            anyD = true;
+                            lastD = g;
+                        }
+                    }
+                    // records ahead, after the MMA, as far as their slots are free
+                    pollR(c + 3, false);
+                }
+                __syncwarp();
+            }
+            if (ctl) {
+                pollR(nchunk, true);
+                // the query tile's load completes before its buffer is reused
+                if (nchunk == 0 && !pop) wait(&S.afull, (armA - 1u) & 1u);
+                // the tile after the next one, while the consumers finish
+                S.tdnn = fetch_tile(L, atomicAdd(L.work, 1u));
+            }
+        }
+
+        // ---- consumers: the query tile's operand rows (u8: widened here), then
+        // the tests and best two over each warp's own columns
+        unsigned long long b1 = ~0ull, b2 = ~0ull;
+        const bool isf = flt;
+        FBuf fb;
+        fb.init();
+        if (warp < 4) {
             if (!pop) {
                 if (cvt) {
                     tc::cp_async_wait_all();
@@ -1064,7 +1088,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                         uint4 w[4];
 #pragma unroll
                         for (int k = 0; k < 4; k++)
-                            w[k] = qv ? *reinterpret_cast<const uint4 *>(S.A[1] + tid * 128 + 16 * (4 * h + k))
+                            w[k] = qv ? *reinterpret_cast<const uint4 *>(S.A[1] + sw128(tid, 4 * h + k))
                                       : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
                         for (int k = 0; k < 4; k++) {
@@ -1081,12 +1105,6 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 if (lane == 0) tc::mbar_arrive(&S.afull);
             }
             if (nchunk > 0) {
-                // chunks 0 and 1 before the loop (both stages are free at a tile start)
-                const uint32_t gv0 = gather_issue(0, jc);
-                const uint32_t gv1 = nchunk > 1 ? gather_issue(1, jn) : 0u;
-                jload(2, jc);
-                gather_finish(0, gv0);
-                if (nchunk > 1) gather_finish(1, gv1);
                 BoxCursor cur;
                 const bool exact_only = (r.flags & kQExactOnly) != 0;
                 const bool live = qv && !(r.flags & EGM_FLAG_DEGENERATE_LINE);
@@ -1098,15 +1116,11 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 const float ke = 1.2e-7f + 2.0f * r.E1;
                 const float k0 = fmaf(9.6e-7f, fabsf(r.C), r.E0 + 1e-9f);
                 for (int c = 0; c < nchunk; c++) {
-                    const uint32_t sq = seq + (uint32_t)c, st = sq & 1u;
-                    const bool more = c + 2 < nchunk;
-                    // row indices of chunk c + 3 (jc holds those of chunk c + 2)
-                    jload(c + 3, jn);
-                    // the accumulator, the other warps' rows and norms, the records
-                    const bool ok = wait(&S.done[st], (sq >> 1) & 1u) && wait(&S.fullB[st], (sq >> 1) & 1u) &&
-                                    wait(&S.fullR[st], (sq >> 1) & 1u);
+                    const uint32_t g = seq + (uint32_t)c, rs = g % kRS, as = g % kNA;
+                    // the accumulator, the chunk's norms and binary rows, its records
+                    const bool ok = wait(&S.done[as], (g / kNA) & 1u) && wait(&S.rows[rs], (g / kRS) & 1u) &&
+                                    wait(&S.fullR[rs], (g / kRS) & 1u);
                     tc::tc_fence_after();
-                    const uint32_t gv = more && ok ? gather_issue(c + 2, jc) : 0u;
                     const int nb = min(kCB, nbox - c * kCB);
                     for (int bb = 0; bb < nb; bb++) {
                         uint32_t pos, len;
@@ -1123,11 +1137,11 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                         const int y0 = (int)max(pos, w1.x) - (int)pos;
                         const int y1 = (int)min(pos + len, w1.x + w1.y) - (int)pos;
                         if (x1 <= x0 && y1 <= y0) continue;
-                        const float4 *rnb = &S.u.io.rn[st][bb][0];
-                        const float *n8b = &S.u.io.n8[c & 3][bb * kBoxR];
-                        const float4 *recb = &S.u.io.rec[st][bb * kBoxR];
-                        const uint8_t *binb = S.B[0][0] + ((c & 3) * kCN + bb * kBoxR) * kBinRowB;
-                        const uint32_t tb = tmem + lanebase + st * kCN + bb * kBoxR;
+                        const float4 *rnb = &S.u.io.rn[FLT ? rs : 0][bb][0];
+                        const float *n8b = &S.u.io.n8[rs][bb * kBoxR];
+                        const float4 *recb = &S.u.io.rec[rs][bb * kBoxR];
+                        const uint8_t *binb = S.B[0][0] + ((int)rs * kCN + bb * kBoxR) * kBinRowB;
+                        const uint32_t tb = tmem + lanebase + as * kCN + bb * kBoxR;
                         // the box's columns inside the warp's windows, as a bit mask
                         auto span = [](int a, int b) {
                             a = max(a, 0);
@@ -1254,12 +1268,12 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                             }
                         }
                     }
-                    if (more) gather_finish(c + 2, gv);
-#pragma unroll
-                    for (int bb = 0; bb < kCB; bb++) jc[bb] = jn[bb];
                     tc::tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&S.tfree[st]);
+                    if (lane == 0) {
+                        tc::mbar_arrive(&S.tfree[as]);
+                        tc::mbar_arrive(&S.rfree[rs]);
+                    }
                 }
                 if (!isf) {
                     // the deferred FP64 tests of the warp, one per lane, then the
@@ -1392,18 +1406,15 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         // A wait gave up.  Before the CTA's shared memory and TMEM are
         // released, every copy and MMA it issued must have landed: wait
         // (bounded) for the last phase armed on each barrier that carries
-        // copies.  The pipeline re-arms a barrier only after the previous
-        // phase was waited for, so at most that last phase is outstanding;
-        // an MMA commit also covers every earlier MMA of the thread.
-        for (int st = 0; st < 2; st++) {
-            if (armB[st] && txB[st]) tc::mbar_wait(&S.fullB[st], (armB[st] - 1u) & 1u);
-            if (armD[st]) {
-                tc::mbar_wait(&S.done[st], (armD[st] - 1u) & 1u);
-                tc::mbar_wait(&S.sfree[st], (armD[st] - 1u) & 1u);
-            }
-        }
+        // copies, and for the commit of the last MMA chain (a commit covers
+        // every earlier MMA of the thread).  A barrier is re-armed only
+        // after its previous phase was waited for, so at most that last
+        // phase is outstanding.
+        for (int s = 0; s < kRS; s++)
+            if (armR[s]) tc::mbar_wait(&S.fullR[s], (armR[s] - 1u) & 1u);
         for (int st = 0; st < 2; st++)
-            if (armR[st]) tc::mbar_wait(&S.fullR[st], (armR[st] - 1u) & 1u);
+            if (armB[st]) tc::mbar_wait(&S.fullB[st], (armB[st] - 1u) & 1u);
+        if (anyD) tc::mbar_wait(&S.done[lastD % kNA], (lastD / kNA) & 1u);
         if (armA && txA) tc::mbar_wait(&S.afull, (armA - 1u) & 1u);
     }
     tc::tc_fence_before();
@@ -1469,7 +1480,7 @@ cudaError_t launch_pack(const Launch &L, cudaStream_t s) {
 template <int CB, int CPS, bool FLT>
 cudaError_t launch_band_shape(const Launch &L, int sms, const CUtensorMap &tA, const CUtensorMap &tB,
                               bool zero_work, bool pdl, cudaStream_t s) {
-    const int smem = (int)BandShape<CB, CPS>::kDynSmem;
+    const int smem = (int)BandShape<CB, CPS, FLT>::kDynSmem;
     int64_t grid = L.ntiles;
     if (grid > CPS * (int64_t)sms) grid = CPS * (int64_t)sms;
     cudaError_t e;
@@ -1497,7 +1508,7 @@ cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s, boo
     cudaError_t e = make_tmap(&tA, L.descA, flt ? L.nq : kTM, kTM);
     if (e != cudaSuccess) return e;
     if ((e = make_tmap(&tB, L.descB, flt ? L.nr : kTM, kBoxR)) != cudaSuccess) return e;
-    if (flt) return launch_band_shape<4, 2, true>(L, sms, tA, tB, zero_work, true, s);
+    if (flt) return launch_band_shape<2, 2, true>(L, sms, tA, tB, zero_work, true, s);
     switch (shape) {
         case 0: return launch_band_shape<4, 2, false>(L, sms, tA, tB, zero_work, zero_work, s);
         case 1: return launch_band_shape<2, 3, false>(L, sms, tA, tB, zero_work, zero_work, s);
