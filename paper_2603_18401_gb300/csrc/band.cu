@@ -899,7 +899,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             // binary rows into slot g mod kRS of B[0][0] (free: its records'
             // slot was).  Returns the boxes whose row this lane copied.
             // Records are copied in chunk order as far ahead as their slots allow,
-            // without waiting (try_wait), and waited for only at the tile end
+            // without waiting (test_wait), and waited for only at the tile end
             // (the consumers wait for them anyway).
             int nextR = 0;
             auto pollR = [&](int upto, bool block) {
@@ -907,7 +907,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                     const uint32_t g = seq + (uint32_t)nextR, s = g % kRS;
                     if (g >= (uint32_t)kRS) {
                         const uint32_t par = ((g - kRS) / kRS) & 1u;
-                        if (block ? !wait(&S.rfree[s], par) : !tc::mbar_try_wait(&S.rfree[s], par)) break;
+                        if (block ? !wait(&S.rfree[s], par) : !tc::mbar_test_wait(&S.rfree[s], par)) break;
                     }
                     issueR(nextR++);
                 }
