@@ -294,16 +294,16 @@ constexpr uint32_t kOperandArrivals = 5; // afull: the control thread and the fo
 constexpr int kDeferCap = 16;            // FP64 tests a warp defers per tile (more: decided at once)
 constexpr int kRS = 4;                   // record / norm / binary-row slots (chunk g in slot g mod kRS)
 
-template <int CB, bool FLT>
+template <int CB, bool FLT, int NB>
 struct BandSmem {
     static constexpr int kCN = kBoxR * CB;  // columns per chunk
     // query tile, K halves (1024-byte aligned); u8 tiles stage each query's
     // bytes in its own row of A[1] before widening them
     uint8_t A[2][kTM * 128];
-    // band chunk: operand stage, K half.  u8 tiles stage a chunk's gathered
-    // bytes in K half 1 of its stage; binary tiles keep kRS chunks of 32-byte
-    // rows (chunk g in slot g mod kRS) in B[0][0]
-    uint8_t B[2][2][kCN * 128];
+    // band chunk: operand stage (NB of them), K half.  u8 tiles stage a chunk's
+    // gathered bytes in K half 1 of its stage; binary tiles keep kRS chunks of
+    // 32-byte rows (chunk g in slot g mod kRS) in B[0][0]
+    uint8_t B[NB][2][kCN * 128];
     // The record slots are idle while a tile's windows are computed (every
     // chunk of the previous tile has been tested, and the next records are
     // copied after), so the per-warp hulls share their memory.
@@ -323,7 +323,7 @@ struct BandSmem {
     // finished a slot's chunk; sfree: the MMA that read an operand stage is
     // done; fullB: a stage's float rows landed (TMA); done: an accumulator is
     // ready; tfree: the consumers have read it
-    uint64_t fullR[kRS], rows[kRS], rfree[kRS], sfree[2], fullB[2], done[4], tfree[4], afull;
+    uint64_t fullR[kRS], rows[kRS], rfree[kRS], sfree[NB], fullB[NB], done[4], tfree[4], afull;
     uint64_t probe;               // never arrived on: the wait of the timeout check (Launch::probe)
     PairGeom g;
     PairDesc pd;
@@ -345,7 +345,10 @@ struct BandShape {
     // accumulators: four where TMEM holds them for CPS CTAs, else two
     static constexpr int kNA = 512 / (CPS * kCN) >= 4 ? 4 : 2;
     static constexpr uint32_t kTmemCols = kNA * kCN;  // a power of two
-    using Smem = BandSmem<CB, FLT>;
+    static constexpr size_t kSmPerSm = 228 * 1024;
+    // operand stages: three where the shared memory holds them for CPS CTAs
+    static constexpr int kNB = CPS * (sizeof(BandSmem<CB, FLT, 3>) + 2048) <= kSmPerSm ? 3 : 2;
+    using Smem = BandSmem<CB, FLT, kNB>;
     static_assert(offsetof(Smem, B) % 1024 == 0, "operand tiles need 1024-byte alignment");
     static_assert(kTM * sizeof(QueryRec) <= sizeof(Smem::B[1]), "a tile's query records fit operand stage 1");
     static_assert(offsetof(Smem, u) % 16 == 0, "bulk copy destinations need 16-byte alignment");
@@ -354,7 +357,6 @@ struct BandShape {
     // for (its layout, 1 KB of alignment slack, the 1 KB the SM reserves per
     // CTA) keeps one more from becoming resident (its TMEM allocation would
     // wait for another CTA to end)
-    static constexpr size_t kSmPerSm = 228 * 1024;
     static constexpr size_t kDynSmem = sizeof(Smem) + 1024 > kSmPerSm / (CPS + 1) + 1 - 1024
                                            ? sizeof(Smem) + 1024
                                            : kSmPerSm / (CPS + 1) + 1 - 1024;
@@ -580,7 +582,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
     pdl_begin();
     using Shape = BandShape<CB, CPS, FLT>;
     using BandSmem = typename Shape::Smem;
-    constexpr int kCB = Shape::kCB, kCN = Shape::kCN, kNA = Shape::kNA;
+    constexpr int kCB = Shape::kCB, kCN = Shape::kCN, kNA = Shape::kNA, kNB = Shape::kNB;
     constexpr uint32_t kTmemCols = Shape::kTmemCols;
     extern __shared__ uint8_t smraw[];
     // 1024-byte alignment by pointer arithmetic on the shared array, so that
@@ -595,7 +597,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             tc::mbar_init(&S.rows[s], 1);
             tc::mbar_init(&S.rfree[s], 4);
         }
-        for (int s = 0; s < 2; s++) {
+        for (int s = 0; s < kNB; s++) {
             tc::mbar_init(&S.sfree[s], 1);
             tc::mbar_init(&S.fullB[s], 1);
         }
@@ -637,7 +639,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
     // phases the control thread armed with copies or MMAs (records per slot,
     // float operand loads per stage, the query tile, the MMA chain): after a
     // failed wait, the CTA lets the last of each complete before it leaves
-    uint32_t armR[kRS] = {}, armB[2] = {0u, 0u}, armA = 0u, lastD = 0u;
+    uint32_t armR[kRS] = {}, armB[3] = {0u, 0u, 0u}, armA = 0u, lastD = 0u;
     bool anyD = false, txA = false;
     if (L.probe) {
         // the timeout check: a short wait on a barrier that nothing arrives
@@ -879,8 +881,8 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             // float rows of chunk c by TMA into operand stage g mod 2, once the
             // MMA of chunk g - 2 is done (control thread)
             auto issueB = [&](int c) {
-                const uint32_t g = seq + (uint32_t)c, st = g & 1u;
-                if (g >= 2u && !wait(&S.sfree[st], ((g - 2u) >> 1) & 1u)) return;
+                const uint32_t g = seq + (uint32_t)c, st = g % kNB;
+                if (g >= (uint32_t)kNB && !wait(&S.sfree[st], ((g - kNB) / kNB) & 1u)) return;
                 const int nb = min(kCB, nbox - c * kCB);
                 tc::mbar_arrive_expect_tx(&S.fullB[st], (uint32_t)nb * (2 * kBoxR * 128));
                 armB[st]++;
@@ -928,11 +930,11 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 }
             };
             auto gather = [&](int c, const uint32_t (&jj)[kCB]) -> uint32_t {
-                const uint32_t g = seq + (uint32_t)c, s = g % kRS, st = g & 1u;
+                const uint32_t g = seq + (uint32_t)c, s = g % kRS, st = g % kNB;
                 // the slot's previous chunk tested (binary rows, u8 norms) and the
                 // operand stage's previous MMA done (u8 bytes)
                 bool ok = g < (uint32_t)kRS || wait(&S.rfree[s], ((g - kRS) / kRS) & 1u);
-                if (cvt && g >= 2u) ok = wait(&S.sfree[st], ((g - 2u) >> 1) & 1u) && ok;
+                if (cvt && g >= (uint32_t)kNB) ok = wait(&S.sfree[st], ((g - kNB) / kNB) & 1u) && ok;
                 const int nb = min(kCB, nbox - c * kCB);
                 uint32_t gv = 0u;
 #pragma unroll
@@ -959,7 +961,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             // K half 0 from staged chunks 0-3, then half 1 over the staged
             // bytes from chunks 4-7) and their norms into slot g mod kRS
             auto widen_rows = [&](int c, uint32_t gv) {
-                const uint32_t g = seq + (uint32_t)c, s = g % kRS, st = g & 1u;
+                const uint32_t g = seq + (uint32_t)c, s = g % kRS, st = g % kNB;
                 const int nb = min(kCB, nbox - c * kCB);
 #pragma unroll
                 for (int bb = 0; bb < kCB; bb++) {
@@ -987,7 +989,18 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
             };
             // E4M3 operands: float rows of the FP8 pass
             const bool e4m3 = flt && L.fp8;
+            // the gathers in chunk order: chunk k's row indices load two gathers
+            // ahead.  Two operand stages: chunk c + 1's rows are gathered before
+            // chunk c is widened; three: chunk c + 2's after chunk c's MMA (its
+            // stage is chunk c - 1's, whose MMA is an iteration old by then)
             uint32_t j1[kCB], j2[kCB];
+            auto next_gather = [&](int k) -> uint32_t {
+                const uint32_t gvk = gather(k, j1);
+#pragma unroll
+                for (int bb = 0; bb < kCB; bb++) j1[bb] = j2[bb];
+                jload(k + 2, j2);
+                return gvk;
+            };
             if (!flt) {
                 jload(0, j1);
                 jload(1, j2);
@@ -997,31 +1010,24 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                 if (flt && nchunk > 0) issueB(0);
             }
             __syncwarp();
-            uint32_t gv = (nchunk > 0 && !flt) ? gather(0, j1) : 0u;
-            if (!flt) {
-#pragma unroll
-                for (int bb = 0; bb < kCB; bb++) j1[bb] = j2[bb];
-                jload(2, j2);
+            uint32_t gv = 0u, gvn = 0u;  // boxes copied by this lane: chunk c, chunk c + 1
+            if (nchunk > 0 && !flt) {
+                gv = next_gather(0);
+                if (kNB == 3 && nchunk > 1) gvn = next_gather(1);
             }
             for (int c = 0; c < nchunk; c++) {
-                const uint32_t g = seq + (uint32_t)c, s = g % kRS, st = g & 1u, as = g % kNA;
+                const uint32_t g = seq + (uint32_t)c, s = g % kRS, st = g % kNB, as = g % kNA;
                 const bool more = c + 1 < nchunk;
-                // the next chunk's rows in flight while this one is widened
-                uint32_t gvn = 0u;
-                if (!flt && more) {
-                    gvn = gather(c + 1, j1);
-#pragma unroll
-                    for (int bb = 0; bb < kCB; bb++) j1[bb] = j2[bb];
-                    jload(c + 3, j2);
-                }
+                // two stages: the next chunk's rows in flight while this one is widened
+                if (kNB == 2 && !flt && more) gvn = next_gather(c + 1);
                 if (!flt) {
+                    // this chunk's copies landed (chunk c + 1's may still be in flight)
                     if (more) tc::cp_async_wait_group<1>();
                     else tc::cp_async_wait_group<0>();
                     if (cvt) widen_rows(c, gv);
                     tc::fence_proxy_async();
                 }
                 __syncwarp();
-                gv = gvn;
                 if (ctl) {
                     // the chunk's norms and binary rows are visible to the consumers
                     tc::mbar_arrive(&S.rows[s]);
@@ -1060,6 +1066,10 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
                     pollR(c + 3, false);
                 }
                 __syncwarp();
+                uint32_t gvnn = 0u;
+                if (kNB == 3 && !flt && c + 2 < nchunk) gvnn = next_gather(c + 2);
+                gv = gvn;
+                gvn = gvnn;
             }
             if (ctl) {
                 pollR(nchunk, true);
@@ -1412,7 +1422,7 @@ __global__ void __launch_bounds__(kBandThreads, CPS)
         // phase is outstanding.
         for (int s = 0; s < kRS; s++)
             if (armR[s]) tc::mbar_wait(&S.fullR[s], (armR[s] - 1u) & 1u);
-        for (int st = 0; st < 2; st++)
+        for (int st = 0; st < kNB; st++)
             if (armB[st]) tc::mbar_wait(&S.fullB[st], (armB[st] - 1u) & 1u);
         if (anyD) tc::mbar_wait(&S.done[lastD % kNA], (lastD / kNA) & 1u);
         if (armA && txA) tc::mbar_wait(&S.afull, (armA - 1u) & 1u);
