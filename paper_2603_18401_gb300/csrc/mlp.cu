@@ -305,15 +305,18 @@ __global__ void __launch_bounds__(kTT, 4) mlp_forward_tc_kernel(const float *par
 constexpr int kBB = 64;        // backward samples per block
 constexpr int kRS = kH + 4;    // padded row stride of the [sample][unit] buffers (16-byte rows)
 
-// One block of 256 threads per kBB samples; activations, their GELU slopes
-// and deltas are stored sample-major in shared memory, so that
+// Persistent blocks of 256 threads, each taking tiles of kBB samples in turn;
+// per tile the activations, their GELU slopes and the deltas are stored
+// sample-major in shared memory, so that
 //   weight gradients  dW[k][j] = sum_c D[c][k] H[c][j]: a thread accumulates a
 //                     4 x 4 tile from two float4 loads per sample;
 //   deltas below      E[c][j] = (sum_k W[k][j] D[c][k]) gelu'(a[c][j]): a
 //                     thread accumulates a 4 x 4 (sample x unit) tile from
 //                     eight float4 loads per four k.
-// Every sum runs over samples, or over k, in ascending order.  The block's
-// gradients are added to the global gradient with atomics.
+// A thread keeps its gradient tiles in registers over all of its block's
+// tiles; the block adds them to the global gradient with atomics once, at
+// the end.  Every sum within a tile runs over samples, or over k, in
+// ascending order.
 __global__ void __launch_bounds__(256, 2) mlp_backward_kernel(const float *params, const float *feat,
                                                               const float *resid, int64_t n, float q,
                                                               const float *pre, const float *zin, float *grad,
@@ -322,88 +325,81 @@ __global__ void __launch_bounds__(256, 2) mlp_backward_kernel(const float *param
     float *w = sm;                   // kP
     float *Hs = w + kWPad;           // activations of the layer below  [sample][unit]
     float *Gs = Hs + kBB * kRS;      // their GELU slopes               [sample][unit]
-    float *Ds = Gs + kBB * kRS;      // deltas of the current layer     [sample][unit]
-    float *Es = Ds + kBB * kRS;      // deltas of the layer below       [sample][unit]
-    float *dz = Es + kBB * kRS;      // [sample]
+    float *D0 = Gs + kBB * kRS;      // deltas of the current layer     [sample][unit]
+    float *E0 = D0 + kBB * kRS;      // deltas of the layer below       [sample][unit]
+    float *dz = E0 + kBB * kRS;      // [sample]
     float *red = dz + kBB;           // loss partials of the warps
     load_weights(w, params);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int64_t s0 = (int64_t)blockIdx.x * kBB;
-    const int nb = (int)min((int64_t)kBB, n - s0);
-    __syncthreads();
-    // output layer: dL/dz and the loss
+    const int kt = t >> 4, jt = t & 15;  // this thread's 4 x 4 tile of a 64 x 64 gradient
+    float acc3[4][4], acc2[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc3[i][j] = acc2[i][j] = 0.0f;
+    float gw4 = 0.0f, gb3 = 0.0f, gb2 = 0.0f, gb1 = 0.0f, gw1a = 0.0f, gw1b = 0.0f;  // the rest
     float lsum = 0.0f;
-    if (t < kBB) {
-        float d = 0.0f;
-        if (t < nb) {
-            const int64_t s = s0 + t;
-            const float z = zin[s];
-            const float e = softplus(z) + kEpsFloor;
-            const float r = resid[s];
-            const float diff = r - e;
-            lsum = fmaxf(q * diff, (q - 1.0f) * diff);
-            const float de = r > e ? -q : (r < e ? 1.0f - q : 0.0f);
-            d = de / (float)n * sigmoid(z);
-        }
-        dz[t] = d;
-    }
-    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-    if (lane == 0) red[warp] = lsum;
     __syncthreads();
-    if (t == 0 && loss) {
-        float v = 0.0f;
-        for (int k = 0; k < 8; k++) v += red[k];
-        atomicAdd(loss, v / (float)n);
-    }
-    // h3 and delta3 = dz W4 gelu'(a3)
-    for (int i = t; i < kH * kBB; i += blockDim.x) {
-        const int k = i / kBB, c = i % kBB;
-        float h = 0.0f, d = 0.0f;
-        if (c < nb) {
-            const float a = pre[(2 * kH + k) * n + s0 + c];
-            h = gelu(a);
-            d = dz[c] * w[oW4 + k] * gelu_grad(a);
-        }
-        Hs[c * kRS + k] = h;
-        Ds[c * kRS + k] = d;
-    }
-    __syncthreads();
-    // W4, b4
-    if (t < kH) {
-        float g = 0.0f;
-        for (int c = 0; c < nb; c++) g = fmaf(dz[c], Hs[c * kRS + t], g);
-        atomicAdd(grad + oW4 + t, g);
-    } else if (t == kH) {
-        float g = 0.0f;
-        for (int c = 0; c < nb; c++) g += dz[c];
-        atomicAdd(grad + ob4, g);
-    }
-    __syncthreads();
-    // layers 3 and 2: weights of layer L map H (below) to D (current)
-    for (int L = 3; L >= 2; L--) {
-        const float *W = w + (L == 3 ? oW3 : oW2);
-        const int oW = L == 3 ? oW3 : oW2, ob = L == 3 ? ob3 : ob2;
-        // activations of the layer below and their slopes
-        for (int i = t; i < kH * kBB; i += blockDim.x) {
-            const int k = i / kBB, c = i % kBB;
-            float h = 0.0f, gg = 0.0f;
-            if (c < nb) {
-                const float a = pre[((L - 2) * kH + k) * n + s0 + c];
-                h = gelu(a);
-                gg = gelu_grad(a);
+    const int64_t ntiles = (n + kBB - 1) / kBB;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t s0 = tile * kBB;
+        const int nb = (int)min((int64_t)kBB, n - s0);
+        float *Ds = D0, *Es = E0;
+        // output layer: dL/dz and the loss
+        if (t < kBB) {
+            float d = 0.0f;
+            if (t < nb) {
+                const int64_t s = s0 + t;
+                const float z = zin[s];
+                const float e = softplus(z) + kEpsFloor;
+                const float r = resid[s];
+                const float diff = r - e;
+                lsum += fmaxf(q * diff, (q - 1.0f) * diff);
+                const float de = r > e ? -q : (r < e ? 1.0f - q : 0.0f);
+                d = de / (float)n * sigmoid(z);
             }
-            Hs[c * kRS + k] = h;
-            Gs[c * kRS + k] = gg;
+            dz[t] = d;
         }
         __syncthreads();
-        // weight gradients of layer L: a 4 x 4 tile (rows 4 kt.., columns 4 jt..) per thread
-        {
-            const int kt = t >> 4, jt = t & 15;
-            float acc[4][4];
+        // h3 and delta3 = dz W4 gelu'(a3)
+        for (int i = t; i < kH * kBB; i += blockDim.x) {
+            const int k = i / kBB, c = i % kBB;
+            float h = 0.0f, d = 0.0f;
+            if (c < nb) {
+                const float a = pre[(2 * kH + k) * n + s0 + c];
+                h = gelu(a);
+                d = dz[c] * w[oW4 + k] * gelu_grad(a);
+            }
+            Hs[c * kRS + k] = h;
+            Ds[c * kRS + k] = d;
+        }
+        __syncthreads();
+        // W4, b4
+        if (t < kH) {
+            for (int c = 0; c < nb; c++) gw4 = fmaf(dz[c], Hs[c * kRS + t], gw4);
+        } else if (t == kH) {
+            for (int c = 0; c < nb; c++) gw4 += dz[c];
+        }
+        __syncthreads();
+        // layers 3 and 2: weights of layer L map H (below) to D (current)
 #pragma unroll
-            for (int i = 0; i < 4; i++)
-#pragma unroll
-                for (int j = 0; j < 4; j++) acc[i][j] = 0.0f;
+        for (int L = 3; L >= 2; L--) {
+            const float *W = w + (L == 3 ? oW3 : oW2);
+            float (&acc)[4][4] = L == 3 ? acc3 : acc2;
+            // activations of the layer below and their slopes
+            for (int i = t; i < kH * kBB; i += blockDim.x) {
+                const int k = i / kBB, c = i % kBB;
+                float h = 0.0f, gg = 0.0f;
+                if (c < nb) {
+                    const float a = pre[((L - 2) * kH + k) * n + s0 + c];
+                    h = gelu(a);
+                    gg = gelu_grad(a);
+                }
+                Hs[c * kRS + k] = h;
+                Gs[c * kRS + k] = gg;
+            }
+            __syncthreads();
+            // weight gradients of layer L: the thread's 4 x 4 tile (rows 4 kt.., columns 4 jt..)
             for (int c = 0; c < nb; c++) {
                 const float4 d4 = *reinterpret_cast<const float4 *>(Ds + c * kRS + 4 * kt);
                 const float4 h4 = *reinterpret_cast<const float4 *>(Hs + c * kRS + 4 * jt);
@@ -413,77 +409,103 @@ __global__ void __launch_bounds__(256, 2) mlp_backward_kernel(const float *param
 #pragma unroll
                     for (int j = 0; j < 4; j++) acc[i][j] = fmaf(dv[i], hv[j], acc[i][j]);
             }
+            if (t < kH) {
+                float g = 0.0f;
+                for (int c = 0; c < nb; c++) g += Ds[c * kRS + t];
+                if (L == 3) gb3 += g;
+                else gb2 += g;
+            }
+            // deltas of the layer below: E[c][j] = (sum_k W[k][j] D[c][k]) gelu'(a[c][j]),
+            // a 4 x 4 tile (samples 4 ct.., units 4 jt..) per thread and step
+            for (int tl = t; tl < (kH / 4) * (kBB / 4); tl += blockDim.x) {
+                const int jt2 = tl & 15, ct = tl >> 4;
+                float e[4][4];
 #pragma unroll
-            for (int i = 0; i < 4; i++)
+                for (int i = 0; i < 4; i++)
 #pragma unroll
-                for (int j = 0; j < 4; j++) atomicAdd(grad + oW + (4 * kt + i) * kH + 4 * jt + j, acc[i][j]);
+                    for (int j = 0; j < 4; j++) e[i][j] = 0.0f;
+                for (int k = 0; k < kH; k += 4) {
+                    float4 wr[4], dr[4];
+#pragma unroll
+                    for (int i = 0; i < 4; i++) wr[i] = *reinterpret_cast<const float4 *>(W + (k + i) * kH + 4 * jt2);
+#pragma unroll
+                    for (int cc = 0; cc < 4; cc++)
+                        dr[cc] = *reinterpret_cast<const float4 *>(Ds + (4 * ct + cc) * kRS + k);
+#pragma unroll
+                    for (int cc = 0; cc < 4; cc++) {
+                        const float dv[4] = {dr[cc].x, dr[cc].y, dr[cc].z, dr[cc].w};
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            const float wv[4] = {j == 0 ? wr[0].x : j == 1 ? wr[0].y : j == 2 ? wr[0].z : wr[0].w,
+                                                 j == 0 ? wr[1].x : j == 1 ? wr[1].y : j == 2 ? wr[1].z : wr[1].w,
+                                                 j == 0 ? wr[2].x : j == 1 ? wr[2].y : j == 2 ? wr[2].z : wr[2].w,
+                                                 j == 0 ? wr[3].x : j == 1 ? wr[3].y : j == 2 ? wr[3].z : wr[3].w};
+#pragma unroll
+                            for (int i = 0; i < 4; i++) e[cc][j] = fmaf(wv[i], dv[i], e[cc][j]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int cc = 0; cc < 4; cc++) {
+                    const int c = 4 * ct + cc;
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+                        Es[c * kRS + 4 * jt2 + j] = c < nb ? e[cc][j] * Gs[c * kRS + 4 * jt2 + j] : 0.0f;
+                }
+            }
+            __syncthreads();
+            float *tmp = Ds;
+            Ds = Es;
+            Es = tmp;
+        }
+        // layer 1: inputs are the features (sample-major in Hs, kIn columns)
+        for (int c = t; c < kBB; c += blockDim.x) {
+            float u[kIn] = {0, 0, 0, 0, 0};
+            if (c < nb) features(feat, s0 + c, u);
+#pragma unroll
+            for (int j = 0; j < kIn; j++) Hs[c * kRS + j] = u[j];
+        }
+        __syncthreads();
+        // W1: entries t and t + 256 of its kH x kIn gradient
+        {
+            const int i0 = t, i1 = t + (int)blockDim.x;
+            for (int c = 0; c < nb; c++) {
+                gw1a = fmaf(Ds[c * kRS + i0 / kIn], Hs[c * kRS + i0 % kIn], gw1a);
+                if (i1 < kH * kIn) gw1b = fmaf(Ds[c * kRS + i1 / kIn], Hs[c * kRS + i1 % kIn], gw1b);
+            }
         }
         if (t < kH) {
             float g = 0.0f;
             for (int c = 0; c < nb; c++) g += Ds[c * kRS + t];
-            atomicAdd(grad + ob + t, g);
+            gb1 += g;
         }
-        // deltas of the layer below: E[c][j] = (sum_k W[k][j] D[c][k]) gelu'(a[c][j]),
-        // a 4 x 4 tile (samples 4 ct.., units 4 jt..) per thread and step
-        for (int tile = t; tile < (kH / 4) * (kBB / 4); tile += blockDim.x) {
-            const int jt = tile & 15, ct = tile >> 4;
-            float e[4][4];
+        __syncthreads();  // the tile's buffers are read before the next tile writes them
+    }
+    // the block's gradients and loss, once
 #pragma unroll
-            for (int i = 0; i < 4; i++)
+    for (int i = 0; i < 4; i++)
 #pragma unroll
-                for (int j = 0; j < 4; j++) e[i][j] = 0.0f;
-            for (int k = 0; k < kH; k += 4) {
-                float4 wr[4], dr[4];
-#pragma unroll
-                for (int i = 0; i < 4; i++) wr[i] = *reinterpret_cast<const float4 *>(W + (k + i) * kH + 4 * jt);
-#pragma unroll
-                for (int cc = 0; cc < 4; cc++)
-                    dr[cc] = *reinterpret_cast<const float4 *>(Ds + (4 * ct + cc) * kRS + k);
-#pragma unroll
-                for (int cc = 0; cc < 4; cc++) {
-                    const float dv[4] = {dr[cc].x, dr[cc].y, dr[cc].z, dr[cc].w};
-#pragma unroll
-                    for (int j = 0; j < 4; j++) {
-                        const float wv[4] = {j == 0 ? wr[0].x : j == 1 ? wr[0].y : j == 2 ? wr[0].z : wr[0].w,
-                                             j == 0 ? wr[1].x : j == 1 ? wr[1].y : j == 2 ? wr[1].z : wr[1].w,
-                                             j == 0 ? wr[2].x : j == 1 ? wr[2].y : j == 2 ? wr[2].z : wr[2].w,
-                                             j == 0 ? wr[3].x : j == 1 ? wr[3].y : j == 2 ? wr[3].z : wr[3].w};
-#pragma unroll
-                        for (int i = 0; i < 4; i++) e[cc][j] = fmaf(wv[i], dv[i], e[cc][j]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int cc = 0; cc < 4; cc++) {
-                const int c = 4 * ct + cc;
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    Es[c * kRS + 4 * jt + j] = c < nb ? e[cc][j] * Gs[c * kRS + 4 * jt + j] : 0.0f;
-            }
+        for (int j = 0; j < 4; j++) {
+            atomicAdd(grad + oW3 + (4 * kt + i) * kH + 4 * jt + j, acc3[i][j]);
+            atomicAdd(grad + oW2 + (4 * kt + i) * kH + 4 * jt + j, acc2[i][j]);
         }
-        __syncthreads();
-        float *tmp = Ds;
-        Ds = Es;
-        Es = tmp;
-    }
-    // layer 1: inputs are the features (sample-major in Hs, kIn columns)
-    for (int c = t; c < kBB; c += blockDim.x) {
-        float u[kIn] = {0, 0, 0, 0, 0};
-        if (c < nb) features(feat, s0 + c, u);
-#pragma unroll
-        for (int j = 0; j < kIn; j++) Hs[c * kRS + j] = u[j];
-    }
-    __syncthreads();
-    for (int i = t; i < kH * kIn; i += blockDim.x) {
-        const int k = i / kIn, j = i % kIn;
-        float g = 0.0f;
-        for (int c = 0; c < nb; c++) g = fmaf(Ds[c * kRS + k], Hs[c * kRS + j], g);
-        atomicAdd(grad + oW1 + i, g);
-    }
     if (t < kH) {
-        float g = 0.0f;
-        for (int c = 0; c < nb; c++) g += Ds[c * kRS + t];
-        atomicAdd(grad + ob1 + t, g);
+        atomicAdd(grad + oW4 + t, gw4);
+        atomicAdd(grad + ob3 + t, gb3);
+        atomicAdd(grad + ob2 + t, gb2);
+        atomicAdd(grad + ob1 + t, gb1);
+    } else if (t == kH) {
+        atomicAdd(grad + ob4, gw4);
+    }
+    atomicAdd(grad + oW1 + t, gw1a);
+    if (t + (int)blockDim.x < kH * kIn) atomicAdd(grad + oW1 + t + blockDim.x, gw1b);
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0) red[warp] = lsum;
+    __syncthreads();
+    if (t == 0 && loss) {
+        float v = 0.0f;
+        for (int k = 0; k < 8; k++) v += red[k];
+        atomicAdd(loss, v / (float)n);
     }
 }
 
@@ -551,7 +573,13 @@ cudaError_t launch_mlp_backward(const float *params, const float *feat, const fl
     const int smem = (int)mlp_backward_smem();
     cudaError_t e = cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    mlp_backward_kernel<<<(int)((n + kBB - 1) / kBB), 256, smem, s>>>(params, feat, resid, n, q, pre, z, grad, loss);
+    // two persistent blocks per SM (the kernel's bound), at most one per tile
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int64_t tiles = (n + kBB - 1) / kBB;
+    const int grid = (int)std::min<int64_t>(tiles, 2 * (int64_t)sms);
+    mlp_backward_kernel<<<grid, 256, smem, s>>>(params, feat, resid, n, q, pre, z, grad, loss);
     return cudaGetLastError();
 }
 
