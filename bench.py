@@ -180,6 +180,20 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+def max_sm_mhz(device):
+    """The device's largest SM clock as nvidia-smi reports it (a query only),
+    else GB300's 2070 MHz."""
+    try:
+        import torch
+
+        idx = torch.device(device).index or 0
+        r = subprocess.run(["nvidia-smi", "-i", str(idx), "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                           capture_output=True, text=True, timeout=10)
+        return float(r.stdout.strip().splitlines()[0])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return 2070.0
+
+
 # ------------------------------------------------------------------ distributed
 # One process per GPU, replicas of the same workload (the pairs are
 # independent: no data-path collective).  The process group only carries the
@@ -509,7 +523,9 @@ def mlp_leg(mt, torch, stream):
     backward pass, twice the forward products.  Inference runs layers 2 and 3
     on the tensor cores (two BF16 products per layer: activations split into
     hi and lo parts), the rest on the FP32 CUDA cores; training runs on the
-    CUDA cores, whose peak is 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz."""
+    CUDA cores.  Both are bound by CUDA-core issue: the peak is the device's
+    SMs x 128 FP32 lanes x 2 FLOP x its largest SM clock (nvidia-smi's
+    clocks.max.sm, else 2070 MHz)."""
     import numpy as np
     import synth
 
@@ -551,11 +567,17 @@ def mlp_leg(mt, torch, stream):
         out[name] = {"samples_per_s": samples / (ms * 1e-3), "ms": ms, "samples": samples,
                      "tflops": samples * flop / (ms * 1e-3) / 1e12}
     net.close()
-    peak = 152 * 128 * 2 * 2.07e9 / 1e12
-    out["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
-                       "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+    sms = torch.cuda.get_device_properties(mt.device).multi_processor_count
+    mhz = max_sm_mhz(mt.device)
+    peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    src = f"derived: {sms} SMs x 128 FP32 lanes x 2 FLOP x {mhz:g} MHz"
+    out["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak, "peak_source": src,
                        "achieved": out["train_step"]["tflops"], "frac": out["train_step"]["tflops"] / peak,
                        "kernel": "mlp_forward_kernel + mlp_backward_kernel + adam_kernel (one training step)"}
+    out["roofline_inference"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak, "peak_source": src,
+                                 "achieved": out["inference"]["tflops"],
+                                 "frac": out["inference"]["tflops"] / peak,
+                                 "kernel": "mlp_forward_tc_kernel (FLOPs of the FP32 network, each product once)"}
     out["network"] = "5-64-64-64-1 GELU, softplus + 0.25 px, BF16-rounded weights, FP32 arithmetic"
     out["inference"]["kernel"] = ("mlp_forward_tc_kernel: layers 2 and 3 as tcgen05.mma (M 128, N 64, K 64, BF16 "
                                   "hi + lo activations, FP32 in TMEM); layers 1 and 4, GELU on CUDA cores")

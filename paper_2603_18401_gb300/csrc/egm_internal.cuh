@@ -118,6 +118,11 @@ struct __align__(16) PairGeom {
     // cos phi and |sin phi|), the largest |key|
     uint32_t qa0max, qa0min, qa1max, qkabs;
     float cxf, cyf, xef, yef;     // cx, cy, xe, ye rounded to FP32 (for error terms)
+    // angular: upper bounds of |v_k|, v = F^T (xe, ye, 1), the residual of the
+    // computed epipole; p . v is the exact line of p = (x1, y1, 1) evaluated
+    // at (xe, ye)
+    float vb[3];
+    int32_t pad1;
 };
 
 static_assert(sizeof(PairGeom) % 16 == 0, "PairGeom is copied in 16-byte units");

@@ -31,6 +31,65 @@ namespace {
 
 __device__ __forceinline__ void set_status(uint32_t *st, uint32_t bit) { atomicOr(st, bit); }
 
+// The hardware conversion for the values d2f leaves to it (kept out of line,
+// so that the common case issues no FP64-pipe instruction).
+__device__ __noinline__ float d2f_other(double d) { return __double2float_rn(d); }
+
+// double -> float rounded to nearest, ties to even, on the integer pipes (the
+// IEEE 754 conversion: keep the sign, rebias the exponent, keep the top 23
+// fraction bits and round on the 29 dropped ones; a carry out of the
+// fraction moves into the exponent, and from the largest finite float to
+// infinity, as rounding to nearest requires).  Only results that are normal
+// floats before rounding take this path: zeros, subnormals, values above the
+// float range and non-finite values take the hardware conversion.  GB300
+// issues FP64-pipe instructions, conversions included, at a small fraction of
+// its integer rate.
+__device__ __forceinline__ float d2f(double d) {
+    const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+    const uint32_t e = (hi >> 20) & 0x7ffu;
+    if (e - 897u > 253u) return d2f_other(d);  // float exponent field (e - 896) outside 1..254
+    uint32_t f = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t rem = lo & 0x1fffffffu;
+    f += (rem > 0x10000000u || (rem == 0x10000000u && (f & 1u))) ? 1u : 0u;
+    return __uint_as_float(f);
+}
+
+// |(x, y)| within a few ulps: the square root of the FMA sum of squares
+// where that sum is a normal float far from overflow (a component lost to
+// underflow then changes the norm by far less than an ulp), hypotf elsewhere.
+__device__ __forceinline__ float norm2f(float x, float y) {
+    const float s = fmaf(x, x, y * y);
+    if (s >= 1e-30f && s <= 1e30f) return sqrtf(s);
+    return hypotf(x, y);
+}
+
+// The pair of row g (references first, then queries) for every lane of a
+// converged warp whose rows ascend with the lane, from offsets cached in
+// shared memory (at most kSmemPairs pairs): the warp finds the pair of its
+// first row in two rounds of the 32 lanes comparing offsets with it (the
+// largest k with offs[k] <= row, as the binary search finds it); a lane
+// whose row lies beyond that pair, or on the other side of the split,
+// searches alone.
+__device__ __forceinline__ int warp_pair(const int64_t *s_roffs, const int64_t *s_qoffs, int npairs, int64_t nr,
+                                         int64_t g) {
+    const int lane = threadIdx.x & 31;
+    const bool isr = g < nr;
+    const int64_t key = isr ? g : g - nr;
+    const int64_t *own = isr ? s_roffs : s_qoffs;
+    const bool r0 = __shfl_sync(0xffffffffu, isr, 0);
+    const int64_t k0 = __shfl_sync(0xffffffffu, key, 0);
+    const int64_t *o0 = r0 ? s_roffs : s_qoffs;
+    const int c1 = lane * 16;
+    const uint32_t b1 = __ballot_sync(0xffffffffu, c1 < npairs && o0[c1 < npairs ? c1 : 0] <= k0);
+    const int seg = (__popc(b1) - 1) * 16;
+    const int c2 = seg + lane;
+    const bool in2 = lane < 16 && c2 < npairs;
+    const uint32_t b2 = __ballot_sync(0xffffffffu, in2 && o0[in2 ? c2 : 0] <= k0);
+    const int p0 = seg + __popc(b2) - 1;
+    if (isr == r0 && (p0 + 1 >= npairs || key < own[p0 + 1])) return p0;
+    return pair_of_shared(own, npairs, key);
+}
+
 __device__ __forceinline__ float fold_atan2(float px, float py) {
     if (px < 0.0f || (px == 0.0f && py > 0.0f)) { px = -px; py = -py; }
     return atan2f(py, px);
@@ -160,6 +219,19 @@ __global__ void __launch_bounds__(32) geometry_kernel(Launch L) {
         hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
     if (lane < 9) G.Ff[lane] = (float)fv;
+    // lanes 0..2: v_k = F_k xe + F_{3+k} ye + F_{6+k} (two roundings, each at
+    // most 2^-53 of the terms' magnitudes), bounded above in FP32
+    {
+        const double f0 = __shfl_sync(0xffffffffu, fv, lane % 3), f1 = __shfl_sync(0xffffffffu, fv, lane % 3 + 3),
+                     f2 = __shfl_sync(0xffffffffu, fv, lane % 3 + 6);
+        float vb = 0.0f;
+        if (!parallel) {
+            const double v = fma(f0, xe, fma(f1, ye, f2));
+            const double T = fabs(f0 * xe) + fabs(f1 * ye) + fabs(f2);
+            vb = (float)(fabs(v) + 4.5e-16 * T) * 1.000001f;
+        }
+        if (lane < 3) G.vb[lane] = vb;
+    }
     if (lane != 0) {
         pdl_wait();
         return;
@@ -226,11 +298,20 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
         const int64_t g = g0 + threadIdx.x;
         const bool valid = g < total;
         const bool is_ref = g < L.nr;
+        // the row's pair (the warp is converged here; a warp with no valid
+        // row skips the lookup as a whole)
+        int p = 0;
+        if (!one) {
+            if (cached) {
+                if (g0 + (threadIdx.x & ~31) < total) p = warp_pair(s_roffs, s_qoffs, L.npairs, L.nr, g);
+            } else if (valid) {
+                p = is_ref ? pair_of(L.r_offs, L.npairs, g) : pair_of(L.q_offs, L.npairs, g - L.nr);
+            }
+        }
         uint32_t group = 0xffffffffu;
         uint32_t s_bits = 0, d_bits = 0x7f800000u, t_bits = 0;
         uint32_t qgroup = 0xffffffffu, qa0 = 0u, qa1 = 0u, qk = 0u;
         if (valid && is_ref) {
-            const int p = one ? 0 : cached ? pair_of_shared(s_roffs, L.npairs, g) : pair_of(L.r_offs, L.npairs, g);
             const PairView P = pair_view(L, p);
             const PairGeom &G = L.geom[p];
             const int64_t j = g - P.r_off;
@@ -238,19 +319,21 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
             const double eps = P.eps2 ? P.eps2[j] : P.eps_scalar;
             if (!(finite64(x) && finite64(y) && finite64(eps))) set_status(L.status, kStNan);
             else if (!positive64(eps)) set_status(L.status, kStArg);
-            const float epsf = (float)eps;
-            const float xf = (float)(x - G.cx), yf = (float)(y - G.cy);
+            const float epsf = d2f(eps);
+            const float xf = d2f(x - G.cx), yf = d2f(y - G.cy);
             // the reference's FP32 record, placed in its bucket by the sort
             L.rtmp[g] = make_float4(xf, yf, epsf, __uint_as_float((uint32_t)j));
-            const float rr = hypotf(xf, yf);
+            const float rr = norm2f(xf, yf);
             int level;
             float key;
             if (G.mode == kModeAngular) {
                 const float px = G.de + (G.ux * xf + G.uy * yf);
                 const float py = (G.ux * yf - G.uy * xf) + G.kappa;
                 key = fold_atan2(px, py);
-                const float d = hypotf(px, py);
-                const float ratio = d / epsf;
+                const float d = norm2f(px, py);
+                // the level only groups references (its statistics come from
+                // its members): an approximate quotient serves
+                const float ratio = __fdividef(d, epsf);
                 if (!(ratio >= 2.0f)) {
                     level = 0;
                 } else {
@@ -273,7 +356,6 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
             group = (uint32_t)p * kLevels + (uint32_t)level;
         } else if (valid) {
             const int64_t gq = g - L.nr;
-            const int p = one ? 0 : cached ? pair_of_shared(s_qoffs, L.npairs, gq) : pair_of(L.q_offs, L.npairs, gq);
             const PairView P = pair_view(L, p);
             const PairGeom &G = L.geom[p];
             const int64_t i = gq - P.q_off;
@@ -290,11 +372,11 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
             const double a = fma(F[0], x1, fma(F[1], y1, F[2]));
             const double b = fma(F[3], x1, fma(F[4], y1, F[5]));
             const double c = fma(F[6], x1, fma(F[7], y1, F[8]));
-            const float x1f = fabsf((float)x1), y1f = fabsf((float)y1);
+            const float x1f = fabsf(d2f(x1)), y1f = fabsf(d2f(y1));
             const float ta = fabsf(G.Ff[0]) * x1f + fabsf(G.Ff[1]) * y1f + fabsf(G.Ff[2]);
             const float tb = fabsf(G.Ff[3]) * x1f + fabsf(G.Ff[4]) * y1f + fabsf(G.Ff[5]);
             const float tc = fabsf(G.Ff[6]) * x1f + fabsf(G.Ff[7]) * y1f + fabsf(G.Ff[8]);
-            const float af = (float)a, bf = (float)b;
+            const float af = d2f(a), bf = d2f(b);
             const float N = sqrtf(af * af + bf * bf);
             const bool usable = isfinite(N) && finite64(c) && N > 1e-6f * (ta + tb) && N > 1e-30f;
             if (!usable) {
@@ -307,17 +389,20 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
             } else {
                 const float invN = 1.0f / N;
                 const double Cn = fma(a, G.cx, fma(b, G.cy, c));
-                float A = af * invN, B = bf * invN, C = (float)Cn * invN;
+                float A = af * invN, B = bf * invN, C = d2f(Cn) * invN;
                 // the oracle's line differs from (a, b, c) by at most ~2 ulps of the terms
                 const float da = 8.9e-16f * ta, db = 8.9e-16f * tb, dc = 8.9e-16f * tc;
                 r.E0 = (da * G.cxf + db * G.cyf + dc) * invN * 1.001f;
                 r.E1 = (da + db) * invN * 1.001f;
                 if (G.mode == kModeAngular) {
-                    // distance of the computed epipole from the line, rounded up
-                    const double rn = fma(a, G.xe, fma(b, G.ye, c));
+                    // distance of the computed epipole from the line, bounded
+                    // above: the exact line there is p . v (|v_k| <= vb_k), and
+                    // the brute force's line is within a few ulps of its terms
+                    // of the exact one
                     const float xe = fabsf(G.xef), ye = fabsf(G.yef);
                     const float rerr = 2.0e-15f * (ta * xe + tb * ye + tc);
-                    r.aux0 = (fabsf((float)rn) + rerr) * invN * 1.00001f + 1e-12f;
+                    const float rv = G.vb[0] * x1f + G.vb[1] * y1f + G.vb[2];
+                    r.aux0 = (rv + rerr) * invN * 1.00001f + 1e-12f;
                     // line direction (B, -A) in the frame of u, reduced mod pi
                     r.key = fold_atan2(B * G.ux - A * G.uy, -(G.ux * A + G.uy * B));
                 } else {
@@ -344,7 +429,7 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
         }
         // warp-aggregated query extremes of each pair (the single-pair
         // stabbing kernel's per-level windows cover every query with them)
-        {
+        if (__any_sync(0xffffffffu, qgroup != 0xffffffffu)) {
             const uint32_t qpeers = __match_any_sync(0xffffffffu, qgroup);
             const uint32_t a0x = __reduce_max_sync(qpeers, qa0);
             const uint32_t a0n = __reduce_min_sync(qpeers, qgroup == 0xffffffffu ? 0x7f800000u : qa0);
@@ -359,17 +444,19 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
             }
         }
         // warp-aggregated level statistics
-        const uint32_t peers = __match_any_sync(0xffffffffu, group);
-        const uint32_t smax = __reduce_max_sync(peers, s_bits);
-        const uint32_t dmin = __reduce_min_sync(peers, d_bits);
-        const uint32_t tmax = __reduce_max_sync(peers, t_bits);
-        if (group != 0xffffffffu && lane == __ffs(peers) - 1) {
-            const int pp = (int)(group / kLevels), lv = (int)(group % kLevels);
-            PairGeom &G = L.geom[pp];
-            atomicAdd(&G.cnt[lv], (uint32_t)__popc(peers));
-            atomicMax(&G.smax[lv], smax);
-            atomicMin(&G.dmin[lv], dmin);
-            atomicMax(&G.tmax[lv], tmax);
+        if (__any_sync(0xffffffffu, group != 0xffffffffu)) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, group);
+            const uint32_t smax = __reduce_max_sync(peers, s_bits);
+            const uint32_t dmin = __reduce_min_sync(peers, d_bits);
+            const uint32_t tmax = __reduce_max_sync(peers, t_bits);
+            if (group != 0xffffffffu && lane == __ffs(peers) - 1) {
+                const int pp = (int)(group / kLevels), lv = (int)(group % kLevels);
+                PairGeom &G = L.geom[pp];
+                atomicAdd(&G.cnt[lv], (uint32_t)__popc(peers));
+                atomicMax(&G.smax[lv], smax);
+                atomicMin(&G.dmin[lv], dmin);
+                atomicMax(&G.tmax[lv], tmax);
+            }
         }
     }
     // The last block to finish derives every pair's level layout (first sorted
@@ -378,10 +465,14 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
     // (each of its blocks from the counts), which keeps this step -- a fence
     // and an atomic round trip -- off the single-pair chain.
     if (one) return;
+    // the block's writes are ordered before thread 0's fence by the barrier
+    // (fences are cumulative), so one thread fences and counts the block
     __shared__ bool s_last;
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(L.prep_done, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(L.prep_done, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
     if (s_last) {
         __threadfence();
