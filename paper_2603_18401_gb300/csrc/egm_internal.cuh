@@ -275,6 +275,33 @@ __device__ __forceinline__ bool load_offsets(int64_t *s_offs, const int64_t *off
     return true;
 }
 
+// The pair of row g (references first, then queries) for every lane of a
+// converged warp whose rows ascend with the lane, from offsets cached in
+// shared memory (at most kSmemPairs pairs): the warp finds the pair of its
+// first row in two rounds of the 32 lanes comparing offsets with it (the
+// largest k with offs[k] <= row, as the binary search finds it); a lane
+// whose row lies beyond that pair, or on the other side of the split,
+// searches alone.
+__device__ __forceinline__ int warp_pair(const int64_t *s_roffs, const int64_t *s_qoffs, int npairs, int64_t nr,
+                                         int64_t g) {
+    const int lane = threadIdx.x & 31;
+    const bool isr = g < nr;
+    const int64_t key = isr ? g : g - nr;
+    const int64_t *own = isr ? s_roffs : s_qoffs;
+    const bool r0 = __shfl_sync(0xffffffffu, isr, 0);
+    const int64_t k0 = __shfl_sync(0xffffffffu, key, 0);
+    const int64_t *o0 = r0 ? s_roffs : s_qoffs;
+    const int c1 = lane * 16;
+    const uint32_t b1 = __ballot_sync(0xffffffffu, c1 < npairs && o0[c1 < npairs ? c1 : 0] <= k0);
+    const int seg = (__popc(b1) - 1) * 16;
+    const int c2 = seg + lane;
+    const bool in2 = lane < 16 && c2 < npairs;
+    const uint32_t b2 = __ballot_sync(0xffffffffu, in2 && o0[in2 ? c2 : 0] <= k0);
+    const int p0 = seg + __popc(b2) - 1;
+    if (isr == r0 && (p0 + 1 >= npairs || key < own[p0 + 1])) return p0;
+    return pair_of_shared(own, npairs, key);
+}
+
 // Index of the pair that owns flattened element g, given offs[0..npairs] in
 // global memory.
 __device__ __forceinline__ int pair_of(const int64_t *offs, int npairs, int64_t g) {

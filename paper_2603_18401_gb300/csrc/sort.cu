@@ -252,15 +252,24 @@ __global__ void __launch_bounds__(256) bucket_count_kernel(Launch L) {
         }
     }
     __syncthreads();
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L.nr; g += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < L.nr; g0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = g0 + threadIdx.x;
         if (one) {
-            const uint32_t key = L.key_a[g];
-            const int lv = (int)(key >> kQBits);
-            atomicAdd(L.tab + L.inl.t_off + s_tab[lv] + ((key & kQMax) >> (kQBits - s_bits[lv])), 1u);
+            if (g < L.nr) {
+                const uint32_t key = L.key_a[g];
+                const int lv = (int)(key >> kQBits);
+                atomicAdd(L.tab + L.inl.t_off + s_tab[lv] + ((key & kQMax) >> (kQBits - s_bits[lv])), 1u);
+            }
             continue;
         }
-        const int p = cached ? pair_of_shared(offs, L.npairs, g) : pair_of(L.r_offs, L.npairs, g);
-        atomicAdd(L.tab + L.pairs[p].t_off + bucket_slot(L.geom[p], L.key_a[g]), 1u);
+        // the reference's pair (the warp is converged here; every row is a reference)
+        int p = 0;
+        if (cached) {
+            if (g0 + (threadIdx.x & ~31) < L.nr) p = warp_pair(offs, offs, L.npairs, L.nr, g);
+        } else if (g < L.nr) {
+            p = pair_of(L.r_offs, L.npairs, g);
+        }
+        if (g < L.nr) atomicAdd(L.tab + L.pairs[p].t_off + bucket_slot(L.geom[p], L.key_a[g]), 1u);
     }
 }
 
@@ -271,11 +280,13 @@ __global__ void __launch_bounds__(256) bucket_count_kernel(Launch L) {
 // of one pair takes a cluster of 16 blocks of 512 threads (the placement's
 // atomics and stores spread over more SMs: the nine-pair config-2 step runs
 // 0.377 instead of 0.397 ms); a batch 8 blocks of 256 per pair (the larger
-// clusters took its sort stage from 0.118 to 0.262 ms).
-constexpr int kScanRound = 8;  // rows a warp keeps in registers per round
-
-template <int kScanCtas, int kScanThreads>
-__global__ void __cluster_dims__(kScanCtas, 1, 1) __launch_bounds__(kScanThreads) bucket_scan_kernel(Launch L) {
+// clusters took its sort stage from 0.118 to 0.262 ms).  kScanRound: rows a
+// warp keeps in registers per round; kPre: references a thread loads ahead;
+// kMinCtas: resident blocks per SM the register budget is held to (a batch
+// runs its pairs' clusters in waves, which more resident clusters shorten).
+template <int kScanCtas, int kScanThreads, int kScanRound, int kPre, int kMinCtas>
+__global__ void __cluster_dims__(kScanCtas, 1, 1) __launch_bounds__(kScanThreads, kMinCtas)
+    bucket_scan_kernel(Launch L) {
     constexpr int kScanWarps = kScanThreads / 32;
     pdl_begin();
     __shared__ __align__(16) PairGeom G;
@@ -302,7 +313,6 @@ __global__ void __cluster_dims__(kScanCtas, 1, 1) __launch_bounds__(kScanThreads
         return i * 4u < used4 ? T4[i] : make_uint4(0, 0, 0, 0);
     };
     // this thread's first references, loaded now so that the loads overlap the scan
-    constexpr int kPre = 8;
     const int64_t b = P.r_off;
     const int stride = kScanCtas * kScanThreads;
     uint32_t key[kPre];
@@ -382,7 +392,6 @@ __global__ void __cluster_dims__(kScanCtas, 1, 1) __launch_bounds__(kScanThreads
 #pragma unroll
         for (int k = 0; k < kPre; k++) {
             if (key[k] == 0xffffffffu) continue;
-            const int e = e0 + k * stride;
             const uint32_t pos = atomicAdd(L.curs + P.t_off + bucket_slot(G, key[k]), 1u);
             L.rec[b + pos] = rv[k];
         }
@@ -417,11 +426,11 @@ cudaError_t launch_sort(const Launch &L, cudaStream_t s) {
     cudaError_t e = launch_pdl(bucket_count_kernel, dim3((unsigned)blocks), dim3(256), 0, s, L);
     if (e != cudaSuccess) return e;
     if (L.npairs == 1) {
-        e = cudaFuncSetAttribute(bucket_scan_kernel<16, 512>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(bucket_scan_kernel<16, 512, 8, 8, 1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
-        return launch_pdl(bucket_scan_kernel<16, 512>, dim3(16), dim3(512), 0, s, L);
+        return launch_pdl(bucket_scan_kernel<16, 512, 8, 8, 1>, dim3(16), dim3(512), 0, s, L);
     }
-    return launch_pdl(bucket_scan_kernel<8, 256>, dim3(L.npairs * 8), dim3(256), 0, s, L);
+    return launch_pdl(bucket_scan_kernel<8, 256, 4, 4, 4>, dim3(L.npairs * 8), dim3(256), 0, s, L);
 }
 
 cudaError_t launch_long_row_sort(const Launch &L, const uint32_t *list, const uint32_t *count, cudaStream_t s) {
