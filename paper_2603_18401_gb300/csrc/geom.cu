@@ -489,9 +489,13 @@ cudaError_t launch_geometry(const Launch &L, cudaStream_t s) {
 cudaError_t launch_prep(const Launch &L, cudaStream_t s) {
     const int64_t total = L.nr + L.nq;
     if (total == 0) return cudaSuccess;
-    int64_t blocks = (total + 255) / 256;
+    // one pair: blocks of 128 rows spread a pair's rows over more SMs (each
+    // row is one pass of a latency-bound chain); a batch: blocks of 256 in
+    // two resident waves
+    const int T = L.npairs == 1 ? 128 : 256;
+    int64_t blocks = (total + T - 1) / T;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    return launch_pdl(prep_kernel, dim3((unsigned)blocks), dim3(256), 0, s, L);
+    return launch_pdl(prep_kernel, dim3((unsigned)blocks), dim3(T), 0, s, L);
 }
 
 cudaError_t launch_intervals(const Launch &L, double *theta, double *delta, double *e3, int32_t *mode,
