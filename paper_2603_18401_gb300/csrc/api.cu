@@ -514,15 +514,20 @@ cudaError_t enqueue_pipeline(const Launch &L, Scratch &sc, bool csr, int max_n, 
     if (tc) EGM_Q(mark(tc, tb, 0));
     EGM_Q(launch_geometry(L, st));
     if (tc) EGM_Q(mark(tc, tb, 1));
-    EGM_Q(launch_prep(L, st));
-    if (tc) EGM_Q(mark(tc, tb, 2));
     if (band) {
-        // the query order runs beside the reference sort
+        // the queries' preparation and order run beside the references'
+        // preparation and sort (the band kernel reads no per-pair query
+        // statistics)
         EGM_Q(cudaEventRecord(sidec->fork_ev, st));
         EGM_Q(cudaStreamWaitEvent(sidec->side, sidec->fork_ev, 0));
+        EGM_Q(launch_prep(L, sidec->side, 2));
         EGM_Q(launch_query_sort(L, sidec->side));
         EGM_Q(cudaEventRecord(sidec->join_ev, sidec->side));
+        EGM_Q(launch_prep(L, st, 1));
+    } else {
+        EGM_Q(launch_prep(L, st, 0));
     }
+    if (tc) EGM_Q(mark(tc, tb, 2));
     EGM_Q(launch_sort(L, st));
     if (band) EGM_Q(cudaStreamWaitEvent(st, sidec->join_ev, 0));
     if (tc) EGM_Q(mark(tc, tb, 3));

@@ -631,7 +631,8 @@ cudaError_t launch_compact(const uint8_t *flags, const int32_t *best, int64_t m,
 // zero_work: reset the tile dispenser first (the pipeline's query-sort
 // kernel resets it otherwise)
 cudaError_t launch_band(const Launch &L, int sms, int shape, cudaStream_t s, bool zero_work = true);
-cudaError_t launch_prep(const Launch &L, cudaStream_t s);
+// part: 0 every row, 1 the references, 2 the queries (prep_kernel)
+cudaError_t launch_prep(const Launch &L, cudaStream_t s, int part = 0);
 cudaError_t launch_sort(const Launch &L, cudaStream_t s);
 cudaError_t launch_stab(const Launch &L, int mode, cudaStream_t s);  // 0 fused match, 1 count, 2 fill+match
 cudaError_t launch_csr_offsets(const Launch &L, uint32_t *long_count, cudaStream_t s);

@@ -255,9 +255,13 @@ __global__ void __launch_bounds__(32) geometry_kernel(Launch L) {
 }
 
 
-__global__ void __launch_bounds__(256) prep_kernel(Launch L) {
+// part: 0 every row; 1 the references (with the tables' zeroing and the
+// level layout); 2 the queries (the banded form runs them beside part 1:
+// nothing of either part reads the other's output)
+__global__ void __launch_bounds__(256) prep_kernel(Launch L, int part) {
     pdl_begin();
     const int64_t total = L.nr + L.nq;
+    const int64_t lo = part == 2 ? L.nr : 0, hi = part == 1 ? L.nr : total;
     const int lane = threadIdx.x & 31;
     __shared__ int64_t s_roffs[kSmemPairs + 1], s_qoffs[kSmemPairs + 1];
     // one pair (plan in the parameters): every row is pair 0, no offsets to load
@@ -265,18 +269,20 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
     const bool cached = one || (load_offsets(s_roffs, L.r_offs, L.npairs) && load_offsets(s_qoffs, L.q_offs, L.npairs));
     __syncthreads();
     // the bucket tables start from zero (the counting sort after this kernel fills them)
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.ntab / 4; i += (int64_t)gridDim.x * blockDim.x)
-        reinterpret_cast<uint4 *>(L.tab)[i] = make_uint4(0, 0, 0, 0);
-    for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < total; g0 += (int64_t)gridDim.x * blockDim.x) {
+    if (part != 2)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.ntab / 4;
+             i += (int64_t)gridDim.x * blockDim.x)
+            reinterpret_cast<uint4 *>(L.tab)[i] = make_uint4(0, 0, 0, 0);
+    for (int64_t g0 = lo + (int64_t)blockIdx.x * blockDim.x; g0 < hi; g0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t g = g0 + threadIdx.x;
-        const bool valid = g < total;
+        const bool valid = g < hi;
         const bool is_ref = g < L.nr;
         // the row's pair (the warp is converged here; a warp with no valid
         // row skips the lookup as a whole)
         int p = 0;
         if (!one) {
             if (cached) {
-                if (g0 + (threadIdx.x & ~31) < total) p = warp_pair(s_roffs, s_qoffs, L.npairs, L.nr, g);
+                if (g0 + (threadIdx.x & ~31) < hi) p = warp_pair(s_roffs, s_qoffs, L.npairs, L.nr, g);
             } else if (valid) {
                 p = is_ref ? pair_of(L.r_offs, L.npairs, g) : pair_of(L.q_offs, L.npairs, g - L.nr);
             }
@@ -437,7 +443,7 @@ __global__ void __launch_bounds__(256) prep_kernel(Launch L) {
     // single pair's layout is derived by the bucket-count kernel instead
     // (each of its blocks from the counts), which keeps this step -- a fence
     // and an atomic round trip -- off the single-pair chain.
-    if (one) return;
+    if (one || part == 2) return;
     // the block's writes are ordered before thread 0's fence by the barrier
     // (fences are cumulative), so one thread fences and counts the block
     __shared__ bool s_last;
@@ -486,16 +492,17 @@ cudaError_t launch_geometry(const Launch &L, cudaStream_t s) {
     return launch_pdl(geometry_kernel, dim3(L.npairs), dim3(32), 0, s, L);
 }
 
-cudaError_t launch_prep(const Launch &L, cudaStream_t s) {
-    const int64_t total = L.nr + L.nq;
-    if (total == 0) return cudaSuccess;
+cudaError_t launch_prep(const Launch &L, cudaStream_t s, int part) {
+    const int64_t total = part == 1 ? L.nr : part == 2 ? L.nq : L.nr + L.nq;
+    if (total == 0 && part != 1) return cudaSuccess;
     // one pair: blocks of 128 rows spread a pair's rows over more SMs (each
     // row is one pass of a latency-bound chain); a batch: blocks of 256 in
     // two resident waves
     const int T = L.npairs == 1 ? 128 : 256;
     int64_t blocks = (total + T - 1) / T;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    return launch_pdl(prep_kernel, dim3((unsigned)blocks), dim3(T), 0, s, L);
+    if (blocks < 1) blocks = 1;  // part 1 of a call without references: the tables and the layout
+    return launch_pdl(prep_kernel, dim3((unsigned)blocks), dim3(T), 0, s, L, part);
 }
 
 cudaError_t launch_intervals(const Launch &L, double *theta, double *delta, double *e3, int32_t *mode,
