@@ -17,9 +17,11 @@
 //   mlp_forward_tc_kernel  inference: layers 2 and 3 on the tensor cores
 //                        (tcgen05.mma, M = 128 samples, N = 64 units, K = 64),
 //                        the rest as in mlp_forward_kernel
-//   mlp_backward_kernel  64 samples per block: deltas layer by layer and the
-//                        block's weight gradients in 4 x 4 register tiles,
-//                        added to the global gradient with atomics
+//   mlp_backward_kernel  persistent blocks taking tiles of 64 samples: deltas
+//                        layer by layer, the weight gradients in 4 x 4 register
+//                        tiles and the other sums split over all threads, kept
+//                        over the block's tiles and added to the global
+//                        gradient with atomics once
 //   adam_kernel          the Adam update, one thread per parameter
 //   residual_kernel      FP64 distances of given (query, reference) pairs,
 //                        in the brute force's exact evaluation order
@@ -332,12 +334,22 @@ __global__ void __launch_bounds__(256, 2) mlp_backward_kernel(const float *param
     load_weights(w, params);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int kt = t >> 4, jt = t & 15;  // this thread's 4 x 4 tile of a 64 x 64 gradient
+    // the sums over a tile's samples of the other gradients: unit u, samples
+    // [16 sq, 16 sq + 16) (every thread; the four quarters meet in the atomics)
+    const int u = t & (kH - 1), sq = t >> 6, c0 = 16 * sq;
+    static_assert(kH == 64 && kBB == 64, "four sample quarters of 16 per unit");
     float acc3[4][4], acc2[4][4];
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++) acc3[i][j] = acc2[i][j] = 0.0f;
-    float gw4 = 0.0f, gb3 = 0.0f, gb2 = 0.0f, gb1 = 0.0f, gw1a = 0.0f, gw1b = 0.0f;  // the rest
+    // W4 and the biases (unit u), b4 (threads 0-3), and five (W1 entry, quarter)
+    // pairs: pair k = t + 256 k is entry k % 320 over quarter k / 320
+    constexpr int kW1 = kH * kIn, kW1Per = 4 * kW1 / 256;
+    static_assert(4 * kW1 % 256 == 0, "W1's (entry, quarter) pairs fill the threads");
+    float gw4 = 0.0f, gb4 = 0.0f, gb3 = 0.0f, gb2 = 0.0f, gb1 = 0.0f, gw1[kW1Per];
+#pragma unroll
+    for (int k = 0; k < kW1Per; k++) gw1[k] = 0.0f;
     float lsum = 0.0f;
     __syncthreads();
     const int64_t ntiles = (n + kBB - 1) / kBB;
@@ -361,42 +373,56 @@ __global__ void __launch_bounds__(256, 2) mlp_backward_kernel(const float *param
             dz[t] = d;
         }
         __syncthreads();
-        // h3 and delta3 = dz W4 gelu'(a3)
-        for (int i = t; i < kH * kBB; i += blockDim.x) {
-            const int k = i / kBB, c = i % kBB;
-            float h = 0.0f, d = 0.0f;
-            if (c < nb) {
-                const float a = pre[(2 * kH + k) * n + s0 + c];
-                h = gelu(a);
-                d = dz[c] * w[oW4 + k] * gelu_grad(a);
+        // h3 and delta3 = dz W4 gelu'(a3): sample c = t mod 64, units 4 r + t / 64
+        // (the 16 pre-activations loaded together, then used)
+        {
+            const int c = t & (kBB - 1), k0 = t >> 6;
+            float a[16];
+#pragma unroll
+            for (int r = 0; r < 16; r++) a[r] = c < nb ? pre[(2 * kH + k0 + 4 * r) * n + s0 + c] : 0.0f;
+#pragma unroll
+            for (int r = 0; r < 16; r++) {
+                const int k = k0 + 4 * r;
+                float h = 0.0f, d = 0.0f;
+                if (c < nb) {
+                    h = gelu(a[r]);
+                    d = dz[c] * w[oW4 + k] * gelu_grad(a[r]);
+                }
+                Hs[c * kRS + k] = h;
+                Ds[c * kRS + k] = d;
             }
-            Hs[c * kRS + k] = h;
-            Ds[c * kRS + k] = d;
         }
         __syncthreads();
-        // W4, b4
-        if (t < kH) {
-            for (int c = 0; c < nb; c++) gw4 = fmaf(dz[c], Hs[c * kRS + t], gw4);
-        } else if (t == kH) {
-            for (int c = 0; c < nb; c++) gw4 += dz[c];
-        }
+        // W4, b4 (rows past the tile's samples are zero)
+#pragma unroll 4
+        for (int c = c0; c < c0 + 16; c++) gw4 = fmaf(dz[c], Hs[c * kRS + u], gw4);
+        if (t < 4)
+#pragma unroll 4
+            for (int c = 16 * t; c < 16 * t + 16; c++) gb4 += dz[c];
         __syncthreads();
         // layers 3 and 2: weights of layer L map H (below) to D (current)
 #pragma unroll
         for (int L = 3; L >= 2; L--) {
             const float *W = w + (L == 3 ? oW3 : oW2);
             float (&acc)[4][4] = L == 3 ? acc3 : acc2;
-            // activations of the layer below and their slopes
-            for (int i = t; i < kH * kBB; i += blockDim.x) {
-                const int k = i / kBB, c = i % kBB;
-                float h = 0.0f, gg = 0.0f;
-                if (c < nb) {
-                    const float a = pre[((L - 2) * kH + k) * n + s0 + c];
-                    h = gelu(a);
-                    gg = gelu_grad(a);
+            // activations of the layer below and their slopes (as above)
+            {
+                const int c = t & (kBB - 1), k0 = t >> 6;
+                float a[16];
+#pragma unroll
+                for (int r = 0; r < 16; r++)
+                    a[r] = c < nb ? pre[((L - 2) * kH + k0 + 4 * r) * n + s0 + c] : 0.0f;
+#pragma unroll
+                for (int r = 0; r < 16; r++) {
+                    const int k = k0 + 4 * r;
+                    float h = 0.0f, gg = 0.0f;
+                    if (c < nb) {
+                        h = gelu(a[r]);
+                        gg = gelu_grad(a[r]);
+                    }
+                    Hs[c * kRS + k] = h;
+                    Gs[c * kRS + k] = gg;
                 }
-                Hs[c * kRS + k] = h;
-                Gs[c * kRS + k] = gg;
             }
             __syncthreads();
             // weight gradients of layer L: the thread's 4 x 4 tile (rows 4 kt.., columns 4 jt..)
@@ -409,9 +435,10 @@ __global__ void __launch_bounds__(256, 2) mlp_backward_kernel(const float *param
 #pragma unroll
                     for (int j = 0; j < 4; j++) acc[i][j] = fmaf(dv[i], hv[j], acc[i][j]);
             }
-            if (t < kH) {
+            {
                 float g = 0.0f;
-                for (int c = 0; c < nb; c++) g += Ds[c * kRS + t];
+#pragma unroll 4
+                for (int c = c0; c < c0 + 16; c++) g += Ds[c * kRS + u];
                 if (L == 3) gb3 += g;
                 else gb2 += g;
             }
@@ -466,17 +493,20 @@ __global__ void __launch_bounds__(256, 2) mlp_backward_kernel(const float *param
             for (int j = 0; j < kIn; j++) Hs[c * kRS + j] = u[j];
         }
         __syncthreads();
-        // W1: entries t and t + 256 of its kH x kIn gradient
-        {
-            const int i0 = t, i1 = t + (int)blockDim.x;
-            for (int c = 0; c < nb; c++) {
-                gw1a = fmaf(Ds[c * kRS + i0 / kIn], Hs[c * kRS + i0 % kIn], gw1a);
-                if (i1 < kH * kIn) gw1b = fmaf(Ds[c * kRS + i1 / kIn], Hs[c * kRS + i1 % kIn], gw1b);
-            }
-        }
-        if (t < kH) {
+        // W1: the thread's (entry, quarter) pairs; b1
+#pragma unroll
+        for (int k = 0; k < kW1Per; k++) {
+            const int pk = t + 256 * k, e = pk % kW1, cq = 16 * (pk / kW1);
+            const float *dr = Ds + e / kIn, *hr = Hs + e % kIn;
             float g = 0.0f;
-            for (int c = 0; c < nb; c++) g += Ds[c * kRS + t];
+#pragma unroll 4
+            for (int c = cq; c < cq + 16; c++) g = fmaf(dr[c * kRS], hr[c * kRS], g);
+            gw1[k] += g;
+        }
+        {
+            float g = 0.0f;
+#pragma unroll 4
+            for (int c = c0; c < c0 + 16; c++) g += Ds[c * kRS + u];
             gb1 += g;
         }
         __syncthreads();  // the tile's buffers are read before the next tile writes them
@@ -489,16 +519,13 @@ __global__ void __launch_bounds__(256, 2) mlp_backward_kernel(const float *param
             atomicAdd(grad + oW3 + (4 * kt + i) * kH + 4 * jt + j, acc3[i][j]);
             atomicAdd(grad + oW2 + (4 * kt + i) * kH + 4 * jt + j, acc2[i][j]);
         }
-    if (t < kH) {
-        atomicAdd(grad + oW4 + t, gw4);
-        atomicAdd(grad + ob3 + t, gb3);
-        atomicAdd(grad + ob2 + t, gb2);
-        atomicAdd(grad + ob1 + t, gb1);
-    } else if (t == kH) {
-        atomicAdd(grad + ob4, gw4);
-    }
-    atomicAdd(grad + oW1 + t, gw1a);
-    if (t + (int)blockDim.x < kH * kIn) atomicAdd(grad + oW1 + t + blockDim.x, gw1b);
+    atomicAdd(grad + oW4 + u, gw4);
+    atomicAdd(grad + ob3 + u, gb3);
+    atomicAdd(grad + ob2 + u, gb2);
+    atomicAdd(grad + ob1 + u, gb1);
+    if (t < 4) atomicAdd(grad + ob4, gb4);
+#pragma unroll
+    for (int k = 0; k < kW1Per; k++) atomicAdd(grad + oW1 + (t + 256 * k) % kW1, gw1[k]);
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
     if (lane == 0) red[warp] = lsum;
     __syncthreads();
