@@ -434,7 +434,12 @@ egm_status egm_mlp_infer(egm_mlp *mlp, const float *feat, int64_t n, double *eps
  * tolerance the learned one is compared with).  EGM_ERR_ARG unless finite
  * and > 0. */
 egm_status egm_mlp_set_fallback(egm_mlp *mlp, double eps_px);
-/* Gradient of the mean pinball loss (device outputs: grad [EGM_MLP_PARAMS], loss [1]). */
+/* Gradient of the mean pinball loss (device outputs: grad [EGM_MLP_PARAMS], loss [1]).
+ * The forward pass of training runs as egm_mlp_infer's (layers 2 and 3 on
+ * the tensor cores) and also keeps the pre-activations for the backward
+ * pass (CUDA cores, FP32).  EGM_ERR_TIMEOUT if a tensor-core wait gave up in
+ * this call or in an egm_mlp_train_step since the last report (the steps
+ * concerned used stale activations); egm_mlp_get_state reports it too. */
 egm_status egm_mlp_grad(egm_mlp *mlp, const float *feat, const float *resid, int64_t n, float quantile, float *grad,
                         float *loss);
 /* One Adam step on a batch; loss [1] (device, may be NULL) receives the batch loss. */

@@ -10,11 +10,13 @@
 #include "egm_internal.cuh"
 
 namespace egm {
-// Learned-tolerance inference with layers 2 and 3 on the tensor cores
-// (mlp.cu); a timed-out MMA wait sets kStTimeout in *err (device); samples
-// without a finite output get `fallback`.
+// The learned-tolerance network's forward pass with layers 2 and 3 on the
+// tensor cores (mlp.cu); a timed-out MMA wait sets kStTimeout in *err
+// (device); samples without a finite output get `fallback` in eps.  Any of
+// eps, pre (the pre-activations a1..a3, [layer][unit][sample]) and z (the
+// output before the softplus) may be null.
 cudaError_t launch_mlp_forward_tc(const float *params, const float *feat, int64_t n, double *eps, uint32_t *err,
-                                  double fallback, int sms, cudaStream_t s);
+                                  double fallback, int sms, cudaStream_t s, float *pre = nullptr, float *z = nullptr);
 }  // namespace egm
 
 using namespace egm;
@@ -1321,6 +1323,21 @@ struct egm_mlp {
     double fallback = 2.0;   // tolerance (px) of samples without a finite network output
 };
 
+namespace {
+// Waits for the stream and reports (and clears) a tensor-core wait that gave
+// up in a training forward pass since the last report.
+egm_status take_training_error(egm_mlp *m) {
+    cudaStream_t st = m->ctx->stream;
+    uint32_t bits = 0;
+    EGM_TRY(cudaMemcpyAsync(&bits, as<uint32_t>(m->err) + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    EGM_TRY(cudaStreamSynchronize(st));
+    if (bits == 0) return EGM_OK;
+    EGM_TRY(cudaMemsetAsync(as<uint32_t>(m->err) + 1, 0, sizeof(uint32_t), st));
+    EGM_TRY(cudaStreamSynchronize(st));
+    return from_bits(bits);
+}
+}  // namespace
+
 extern "C" {
 
 egm_status egm_mlp_create(egm_ctx *c, const float *params, egm_mlp **out) {
@@ -1337,7 +1354,8 @@ egm_status egm_mlp_create(egm_ctx *c, const float *params, egm_mlp **out) {
     if (e == cudaSuccess) e = grow(m->v, pb);
     if (e == cudaSuccess) e = grow(m->grad, pb);
     if (e == cudaSuccess) e = grow(m->loss, 64);
-    if (e == cudaSuccess) e = grow(m->err, 16);
+    if (e == cudaSuccess) e = grow(m->err, 16);  // word 0: inference; word 1: training
+    if (e == cudaSuccess) e = cudaMemset(m->err.ptr, 0, 16);
     if (e == cudaSuccess) e = cudaMemcpy(m->params.ptr, params, pb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->m.ptr, 0, pb);
     if (e == cudaSuccess) e = cudaMemset(m->v.ptr, 0, pb);
@@ -1370,7 +1388,7 @@ egm_status egm_mlp_get_state(egm_mlp *m, float *params, float *am, float *av, in
     if (am) EGM_TRY(cudaMemcpy(am, m->m.ptr, pb, cudaMemcpyDeviceToHost));
     if (av) EGM_TRY(cudaMemcpy(av, m->v.ptr, pb, cudaMemcpyDeviceToHost));
     if (step) *step = m->step;
-    return EGM_OK;
+    return take_training_error(m);
 }
 
 egm_status egm_mlp_set_state(egm_mlp *m, const float *params, const float *am, const float *av, int64_t step) {
@@ -1412,7 +1430,11 @@ egm_status mlp_backprop(egm_mlp *m, const float *feat, const float *resid, int64
     EGM_TRY(grow(m->z, sizeof(float) * (size_t)n));
     EGM_TRY(cudaMemsetAsync(m->grad.ptr, 0, sizeof(float) * EGM_MLP_PARAMS, st));
     EGM_TRY(cudaMemsetAsync(m->loss.ptr, 0, sizeof(float), st));
-    EGM_TRY(launch_mlp_forward(as<float>(m->params), feat, n, nullptr, as<float>(m->pre), as<float>(m->z), st));
+    // the forward pass on the tensor cores; a timed-out wait is recorded in
+    // the training word of the error flags (reported by egm_mlp_grad and
+    // egm_mlp_get_state)
+    EGM_TRY(launch_mlp_forward_tc(as<float>(m->params), feat, n, nullptr, as<uint32_t>(m->err) + 1, m->fallback,
+                                  m->ctx->sms, st, as<float>(m->pre), as<float>(m->z)));
     EGM_TRY(launch_mlp_backward(as<float>(m->params), feat, resid, n, q, as<float>(m->pre), as<float>(m->z),
                                 as<float>(m->grad), as<float>(m->loss), st));
     return EGM_OK;
@@ -1428,8 +1450,7 @@ egm_status egm_mlp_grad(egm_mlp *m, const float *feat, const float *resid, int64
     cudaStream_t st = m->ctx->stream;
     if (grad) EGM_TRY(cudaMemcpyAsync(grad, m->grad.ptr, sizeof(float) * EGM_MLP_PARAMS, cudaMemcpyDeviceToDevice, st));
     if (loss) EGM_TRY(cudaMemcpyAsync(loss, m->loss.ptr, sizeof(float), cudaMemcpyDeviceToDevice, st));
-    EGM_TRY(cudaStreamSynchronize(st));
-    return EGM_OK;
+    return take_training_error(m);
 }
 
 egm_status egm_mlp_train_step(egm_mlp *m, const float *feat, const float *resid, int64_t n, float lr, float q,

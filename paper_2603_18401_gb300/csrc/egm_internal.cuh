@@ -641,8 +641,6 @@ cudaError_t launch_long_row_sort(const Launch &L, const uint32_t *list, const ui
 cudaError_t launch_intervals(const Launch &L, double *theta, double *delta, double *e3, int32_t *mode,
                              cudaStream_t s);
 int mlp_param_count();
-cudaError_t launch_mlp_forward(const float *params, const float *feat, int64_t n, double *eps, float *pre, float *z,
-                               cudaStream_t s);
 cudaError_t launch_mlp_backward(const float *params, const float *feat, const float *resid, int64_t n, float q,
                                 const float *pre, const float *z, float *grad, float *loss, cudaStream_t s);
 cudaError_t launch_adam(float *p, float *g, float *m, float *v, float lr, int64_t step, cudaStream_t s);

@@ -9,14 +9,14 @@
 //   loss: pinball loss at quantile q of the residual r (the distance of the
 //   true match from its epipolar line, Eq. 3) against eps.
 // Weights are kept in FP32 (the Adam master copy) and rounded to BF16 when a
-// kernel loads them; every product and sum is FP32.
+// kernel loads them; every sum is FP32 (the tensor-core layers take each FP32
+// activation as the sum of two BF16 parts, the rest is FP32 arithmetic).
 //
-//   mlp_forward_kernel   one thread per sample, 128 samples per block, the
-//                        sample's activations in registers, the weights in
-//                        shared memory read as broadcast float4
-//   mlp_forward_tc_kernel  inference: layers 2 and 3 on the tensor cores
-//                        (tcgen05.mma, M = 128 samples, N = 64 units, K = 64),
-//                        the rest as in mlp_forward_kernel
+//   mlp_forward_tc_kernel  inference and the training forward pass (which
+//                        also writes the pre-activations and the output):
+//                        one thread per sample, layer 1 and GELU on the CUDA
+//                        cores, layers 2 and 3 on the tensor cores
+//                        (tcgen05.mma, M = 128 samples, N = 64 units, K = 64)
 //   mlp_backward_kernel  persistent blocks taking tiles of 64 samples: deltas
 //                        layer by layer, the weight gradients in 4 x 4 register
 //                        tiles and the other sums split over all threads, kept
@@ -65,78 +65,8 @@ __device__ __forceinline__ void features(const float *feat, int64_t s, float *u)
     u[4] = f[4];
 }
 
-constexpr int kFB = 128;  // forward samples per block
 constexpr int kWPad = (kP + 3) & ~3;  // weights, then the activation buffer (16-byte aligned)
 static_assert(oW2 % 4 == 0 && oW3 % 4 == 0 && oW4 % 4 == 0, "float4 weight rows");
-
-// eps (double) and, for training, pre-activations a1..a3 stored [layer][unit][sample].
-// One thread per sample with its activations in registers; the weights are
-// read from shared memory as broadcast float4 (one load feeds four products)
-// for four output units at a time.  Every dot product runs over the inputs in
-// ascending order, one FMA at a time.
-__global__ void __launch_bounds__(kFB, 3) mlp_forward_kernel(const float *params, const float *feat, int64_t n,
-                                                             double *eps, float *pre, float *zout) {
-    extern __shared__ float sm[];
-    float *w = sm;                  // kP
-    float *hs = w + kWPad;          // kH x kFB: a layer's outputs, [unit][sample]
-    load_weights(w, params);
-    __syncthreads();
-    const int t = threadIdx.x;
-    const int64_t s = (int64_t)blockIdx.x * kFB + t;
-    const bool valid = s < n;
-    float u[kIn] = {0, 0, 0, 0, 0};
-    if (valid) features(feat, s, u);
-    float h[kH];
-    // layer 1
-#pragma unroll
-    for (int k = 0; k < kH; k++) {
-        float a = w[ob1 + k];
-#pragma unroll
-        for (int j = 0; j < kIn; j++) a = fmaf(w[oW1 + k * kIn + j], u[j], a);
-        if (valid && pre) pre[(0 * kH + k) * n + s] = a;
-        h[k] = gelu(a);
-    }
-    // layers 2 and 3
-    for (int l = 0; l < 2; l++) {
-        const float4 *W = reinterpret_cast<const float4 *>(w + (l == 0 ? oW2 : oW3));
-        const float *b = w + (l == 0 ? ob2 : ob3);
-#pragma unroll 1
-        for (int k = 0; k < kH; k += 4) {
-            float a0 = b[k], a1 = b[k + 1], a2 = b[k + 2], a3 = b[k + 3];
-#pragma unroll
-            for (int j4 = 0; j4 < kH / 4; j4++) {
-                const float4 w0 = W[(k + 0) * (kH / 4) + j4], w1 = W[(k + 1) * (kH / 4) + j4];
-                const float4 w2 = W[(k + 2) * (kH / 4) + j4], w3 = W[(k + 3) * (kH / 4) + j4];
-                const float x0 = h[4 * j4], x1 = h[4 * j4 + 1], x2 = h[4 * j4 + 2], x3 = h[4 * j4 + 3];
-                a0 = fmaf(w0.x, x0, a0); a0 = fmaf(w0.y, x1, a0); a0 = fmaf(w0.z, x2, a0); a0 = fmaf(w0.w, x3, a0);
-                a1 = fmaf(w1.x, x0, a1); a1 = fmaf(w1.y, x1, a1); a1 = fmaf(w1.z, x2, a1); a1 = fmaf(w1.w, x3, a1);
-                a2 = fmaf(w2.x, x0, a2); a2 = fmaf(w2.y, x1, a2); a2 = fmaf(w2.z, x2, a2); a2 = fmaf(w2.w, x3, a2);
-                a3 = fmaf(w3.x, x0, a3); a3 = fmaf(w3.y, x1, a3); a3 = fmaf(w3.z, x2, a3); a3 = fmaf(w3.w, x3, a3);
-            }
-            if (valid && pre) {
-                float *pl = pre + ((1 + l) * kH + k) * n + s;
-                pl[0] = a0;
-                pl[n] = a1;
-                pl[2 * n] = a2;
-                pl[3 * n] = a3;
-            }
-            // this thread's own column: no other thread reads it
-            hs[(k + 0) * kFB + t] = gelu(a0);
-            hs[(k + 1) * kFB + t] = gelu(a1);
-            hs[(k + 2) * kFB + t] = gelu(a2);
-            hs[(k + 3) * kFB + t] = gelu(a3);
-        }
-#pragma unroll
-        for (int k = 0; k < kH; k++) h[k] = hs[k * kFB + t];
-    }
-    float z = w[ob4];
-#pragma unroll
-    for (int j = 0; j < kH; j++) z = fmaf(w[oW4 + j], h[j], z);
-    if (valid) {
-        if (eps) eps[s] = (double)(softplus(z) + kEpsFloor);
-        if (zout) zout[s] = z;
-    }
-}
 
 // ------------------------------------------------------------ tensor-core forward
 // Layers 2 and 3 (the two 64 x 64 products, 96 % of the network's multiply-adds) as
@@ -194,7 +124,8 @@ __device__ __forceinline__ void store_split(MlpTcSmem &S, int r, const float (&h
 // tolerance (non-finite features, or a block whose MMA wait gave up) gets the
 // fixed tolerance `fallback` instead.
 __global__ void __launch_bounds__(kTT, 4) mlp_forward_tc_kernel(const float *params, const float *feat, int64_t n,
-                                                                double *eps, uint32_t *err, double fallback) {
+                                                                double *eps, uint32_t *err, double fallback,
+                                                                float *pre, float *zout) {
     extern __shared__ uint8_t smraw[];
     MlpTcSmem &S = *reinterpret_cast<MlpTcSmem *>(smraw + ((1024u - (tc::smem_addr(smraw) & 1023u)) & 1023u));
     const int t = threadIdx.x, warp = t >> 5;
@@ -245,6 +176,7 @@ __global__ void __launch_bounds__(kTT, 4) mlp_forward_tc_kernel(const float *par
             float a = S.b1[k];
 #pragma unroll
             for (int j = 0; j < kIn; j++) a = fmaf(S.w1[k * kIn + j], u[j], a);
+            if (pre && valid) pre[k * n + s] = a;
             h[k] = gelu(a);
         }
         store_split(S, t, h);
@@ -283,7 +215,11 @@ __global__ void __launch_bounds__(kTT, 4) mlp_forward_tc_kernel(const float *par
                     tc::tmem_ld32(tmem + lane_base + 32 * half, v);
                     tc::tmem_wait_ld();
 #pragma unroll
-                    for (int k = 0; k < 32; k++) h[32 * half + k] = gelu(__uint_as_float(v[k]) + b[32 * half + k]);
+                    for (int k = 0; k < 32; k++) {
+                        const float a = __uint_as_float(v[k]) + b[32 * half + k];
+                        if (pre && valid) pre[((1 + l) * kH + 32 * half + k) * n + s] = a;
+                        h[32 * half + k] = gelu(a);
+                    }
                 }
                 if (l == 0) store_split(S, t, h);
             }
@@ -291,10 +227,11 @@ __global__ void __launch_bounds__(kTT, 4) mlp_forward_tc_kernel(const float *par
         float z = S.b4;
 #pragma unroll
         for (int j = 0; j < kH; j++) z = fmaf(S.w4[j], h[j], z);
-        if (valid) {
+        if (valid && eps) {
             const float e = softplus(z) + kEpsFloor;
             eps[s] = (failed || !isfinite(e)) ? fallback : (double)e;
         }
+        if (valid && zout) zout[s] = z;
     }
     // after a failed wait the MMAs of the last commit may still run: wait for
     // that commit's phase (bounded) before the TMEM is released
@@ -569,28 +506,17 @@ __global__ void residual_kernel(const double *xy1, const double *xy2, const doub
 
 int mlp_param_count() { return kP; }
 
-size_t mlp_forward_smem() { return sizeof(float) * (kWPad + kH * kFB); }
 size_t mlp_backward_smem() { return sizeof(float) * (kWPad + 4 * kBB * kRS + kBB + 8); }
 
-cudaError_t launch_mlp_forward(const float *params, const float *feat, int64_t n, double *eps, float *pre, float *z,
-                               cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    const int smem = (int)mlp_forward_smem();
-    cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    mlp_forward_kernel<<<(int)((n + kFB - 1) / kFB), kFB, smem, s>>>(params, feat, n, eps, pre, z);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_mlp_forward_tc(const float *params, const float *feat, int64_t n, double *eps, uint32_t *err,
-                                  double fallback, int sms, cudaStream_t s) {
+                                  double fallback, int sms, cudaStream_t s, float *pre, float *z) {
     if (n <= 0) return cudaSuccess;
     const int smem = (int)sizeof(MlpTcSmem) + 1024;
     cudaError_t e = cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (n + kTT - 1) / kTT;
     const int grid = (int)std::min<int64_t>(tiles, 4 * (int64_t)sms);
-    mlp_forward_tc_kernel<<<grid, kTT, smem, s>>>(params, feat, n, eps, err, fallback);
+    mlp_forward_tc_kernel<<<grid, kTT, smem, s>>>(params, feat, n, eps, err, fallback, pre, z);
     return cudaGetLastError();
 }
 
