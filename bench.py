@@ -520,12 +520,13 @@ def mlp_leg(mt, torch, stream):
 
     FLOPs per sample: forward 2 (5*64 + 2*64*64 + 64) = 17 152 in the layer
     products plus ~25 per unit for GELU / softplus; training adds the
-    backward pass, twice the forward products.  Inference runs layers 2 and 3
-    on the tensor cores (two BF16 products per layer: activations split into
-    hi and lo parts), the rest on the FP32 CUDA cores; training runs on the
-    CUDA cores.  Both are bound by CUDA-core issue: the peak is the device's
-    SMs x 128 FP32 lanes x 2 FLOP x its largest SM clock (nvidia-smi's
-    clocks.max.sm, else 2070 MHz)."""
+    backward pass, twice the forward products.  The forward pass (inference
+    and training) runs layers 2 and 3 on the tensor cores (two BF16 products
+    per layer: activations split into hi and lo parts), the rest on the FP32
+    CUDA cores; the backward pass and Adam run on the CUDA cores.  Both legs
+    are bound by CUDA-core issue: the peak is the device's SMs x 128 FP32
+    lanes x 2 FLOP x its largest SM clock (nvidia-smi's clocks.max.sm, else
+    2070 MHz), each product of the FP32 network counted once."""
     import numpy as np
     import synth
 
@@ -573,7 +574,7 @@ def mlp_leg(mt, torch, stream):
     src = f"derived: {sms} SMs x 128 FP32 lanes x 2 FLOP x {mhz:g} MHz"
     out["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak, "peak_source": src,
                        "achieved": out["train_step"]["tflops"], "frac": out["train_step"]["tflops"] / peak,
-                       "kernel": "mlp_forward_kernel + mlp_backward_kernel + adam_kernel (one training step)"}
+                       "kernel": "mlp_forward_tc_kernel + mlp_backward_kernel + adam_kernel (one training step)"}
     out["roofline_inference"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak, "peak_source": src,
                                  "achieved": out["inference"]["tflops"],
                                  "frac": out["inference"]["tflops"] / peak,

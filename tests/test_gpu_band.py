@@ -103,6 +103,34 @@ def test_config3_mixed_batch(mt):
         q0 += s.m
 
 
+@pytest.mark.parametrize("sizes", [[(300, 0), (0, 200), (129, 33), (1, 1), (5, 3000), (128, 32)],
+                                   [(40, 0), (17, 0)]])
+def test_ragged_and_empty_pairs_in_one_batch(mt, sizes):
+    """A banded batch whose pairs are ragged or empty on either side (the
+    queries' and the references' preparation run on two streams; a batch
+    without any reference still lays out its levels): equal to the plain
+    form and to the oracle, pair by pair."""
+    rng = np.random.default_rng(len(sizes))
+    scenes = []
+    for i, (m, n) in enumerate(sizes):
+        kind, dim = ((0, 128), (2, 256))[i % 2]
+        scenes.append(_scene(rng.uniform([0, 0], [640, 480], (m, 2)), rng.uniform([0, 0], [640, 480], (n, 2)), _F(),
+                             6.0, kind=kind, dim=dim, seed=100 + i))
+    items = [mt.to_device(s) for s in scenes]
+    res = {}
+    for form in (FORM_BANDED, FORM_PLAIN):
+        mt.set_params(form=form)
+        res[form] = {k: v.cpu().numpy() for k, v in mt.match_batch(items).items()}
+    mt.set_params(form=FORM_AUTO)
+    for k in KEYS:
+        assert np.array_equal(res[FORM_BANDED][k], res[FORM_PLAIN][k]), k
+    q0 = 0
+    for s in scenes:
+        if s.m:
+            check_matches({k: res[FORM_BANDED][k][q0:q0 + s.m] for k in KEYS}, s)
+        q0 += s.m
+
+
 def test_full_size_batch_exact(mt):
     """The bench's batch (256 pairs of 6048x4032, counts log-uniform in [1k,
     32k], half binary) at full size, every query: banded matches equal plain
