@@ -310,23 +310,31 @@ __global__ void __launch_bounds__(256, 2) mlp_backward_kernel(const float *param
             dz[t] = d;
         }
         __syncthreads();
-        // h3 and delta3 = dz W4 gelu'(a3): sample c = t mod 64, units 4 r + t / 64
-        // (the 16 pre-activations loaded together, then used)
+        // h3 and delta3 = dz W4 gelu'(a3): sample c = t mod 64, the four runs of
+        // four units 4 (t / 64 + 4 r) ..; the 16 pre-activations loaded together,
+        // each run stored as one float4 (a warp's 32 samples then fall on
+        // distinct banks)
         {
-            const int c = t & (kBB - 1), k0 = t >> 6;
+            const int c = t & (kBB - 1), gq = t >> 6;
             float a[16];
 #pragma unroll
-            for (int r = 0; r < 16; r++) a[r] = c < nb ? pre[(2 * kH + k0 + 4 * r) * n + s0 + c] : 0.0f;
+            for (int r = 0; r < 4; r++)
 #pragma unroll
-            for (int r = 0; r < 16; r++) {
-                const int k = k0 + 4 * r;
-                float h = 0.0f, d = 0.0f;
+                for (int j = 0; j < 4; j++)
+                    a[4 * r + j] = c < nb ? pre[(2 * kH + 4 * (gq + 4 * r) + j) * n + s0 + c] : 0.0f;
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const int k0 = 4 * (gq + 4 * r);
+                float h[4] = {0.0f, 0.0f, 0.0f, 0.0f}, d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                 if (c < nb) {
-                    h = gelu(a[r]);
-                    d = dz[c] * w[oW4 + k] * gelu_grad(a[r]);
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        h[j] = gelu(a[4 * r + j]);
+                        d[j] = dz[c] * w[oW4 + k0 + j] * gelu_grad(a[4 * r + j]);
+                    }
                 }
-                Hs[c * kRS + k] = h;
-                Ds[c * kRS + k] = d;
+                *reinterpret_cast<float4 *>(Hs + c * kRS + k0) = make_float4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<float4 *>(Ds + c * kRS + k0) = make_float4(d[0], d[1], d[2], d[3]);
             }
         }
         __syncthreads();
@@ -344,21 +352,26 @@ __global__ void __launch_bounds__(256, 2) mlp_backward_kernel(const float *param
             float (&acc)[4][4] = L == 3 ? acc3 : acc2;
             // activations of the layer below and their slopes (as above)
             {
-                const int c = t & (kBB - 1), k0 = t >> 6;
+                const int c = t & (kBB - 1), gq = t >> 6;
                 float a[16];
 #pragma unroll
-                for (int r = 0; r < 16; r++)
-                    a[r] = c < nb ? pre[((L - 2) * kH + k0 + 4 * r) * n + s0 + c] : 0.0f;
+                for (int r = 0; r < 4; r++)
 #pragma unroll
-                for (int r = 0; r < 16; r++) {
-                    const int k = k0 + 4 * r;
-                    float h = 0.0f, gg = 0.0f;
+                    for (int j = 0; j < 4; j++)
+                        a[4 * r + j] = c < nb ? pre[((L - 2) * kH + 4 * (gq + 4 * r) + j) * n + s0 + c] : 0.0f;
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const int k0 = 4 * (gq + 4 * r);
+                    float h[4] = {0.0f, 0.0f, 0.0f, 0.0f}, gg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                     if (c < nb) {
-                        h = gelu(a[r]);
-                        gg = gelu_grad(a[r]);
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            h[j] = gelu(a[4 * r + j]);
+                            gg[j] = gelu_grad(a[4 * r + j]);
+                        }
                     }
-                    Hs[c * kRS + k] = h;
-                    Gs[c * kRS + k] = gg;
+                    *reinterpret_cast<float4 *>(Hs + c * kRS + k0) = make_float4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<float4 *>(Gs + c * kRS + k0) = make_float4(gg[0], gg[1], gg[2], gg[3]);
                 }
             }
             __syncthreads();
