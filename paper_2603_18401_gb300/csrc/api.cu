@@ -12,9 +12,10 @@
 namespace egm {
 // The learned-tolerance network's forward pass with layers 2 and 3 on the
 // tensor cores (mlp.cu); a timed-out MMA wait sets kStTimeout in *err
-// (device); samples without a finite output get `fallback` in eps.  Any of
-// eps, pre (the pre-activations a1..a3, [layer][unit][sample]) and z (the
-// output before the softplus) may be null.
+// (device); samples without a finite output get `fallback` in eps.  With pre
+// (the pre-activations a1..a3, [layer][unit][sample]) the training pass runs
+// instead: pre and z (the output before the softplus) are written, eps is
+// not.
 cudaError_t launch_mlp_forward_tc(const float *params, const float *feat, int64_t n, double *eps, uint32_t *err,
                                   double fallback, int sms, cudaStream_t s, float *pre = nullptr, float *z = nullptr);
 }  // namespace egm

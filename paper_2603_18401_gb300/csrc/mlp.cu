@@ -122,7 +122,10 @@ __device__ __forceinline__ void store_split(MlpTcSmem &S, int r, const float (&h
 // the MMA barrier is bounded; a timeout sets the timeout bit in *err and the
 // block issues no more MMAs.  A sample whose output is not a finite
 // tolerance (non-finite features, or a block whose MMA wait gave up) gets the
-// fixed tolerance `fallback` instead.
+// fixed tolerance `fallback` instead.  kTrain: the training forward pass,
+// which writes the pre-activations and outputs instead of eps (a separate
+// instance: the stores cost the inference instance registers).
+template <bool kTrain>
 __global__ void __launch_bounds__(kTT, 4) mlp_forward_tc_kernel(const float *params, const float *feat, int64_t n,
                                                                 double *eps, uint32_t *err, double fallback,
                                                                 float *pre, float *zout) {
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(kTT, 4) mlp_forward_tc_kernel(const float *par
             float a = S.b1[k];
 #pragma unroll
             for (int j = 0; j < kIn; j++) a = fmaf(S.w1[k * kIn + j], u[j], a);
-            if (pre && valid) pre[k * n + s] = a;
+            if (kTrain && valid) pre[k * n + s] = a;
             h[k] = gelu(a);
         }
         store_split(S, t, h);
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(kTT, 4) mlp_forward_tc_kernel(const float *par
 #pragma unroll
                     for (int k = 0; k < 32; k++) {
                         const float a = __uint_as_float(v[k]) + b[32 * half + k];
-                        if (pre && valid) pre[((1 + l) * kH + 32 * half + k) * n + s] = a;
+                        if (kTrain && valid) pre[((1 + l) * kH + 32 * half + k) * n + s] = a;
                         h[32 * half + k] = gelu(a);
                     }
                 }
@@ -227,11 +230,11 @@ __global__ void __launch_bounds__(kTT, 4) mlp_forward_tc_kernel(const float *par
         float z = S.b4;
 #pragma unroll
         for (int j = 0; j < kH; j++) z = fmaf(S.w4[j], h[j], z);
-        if (valid && eps) {
+        if (valid && !kTrain) {
             const float e = softplus(z) + kEpsFloor;
             eps[s] = (failed || !isfinite(e)) ? fallback : (double)e;
         }
-        if (valid && zout) zout[s] = z;
+        if (valid && kTrain) zout[s] = z;
     }
     // after a failed wait the MMAs of the last commit may still run: wait for
     // that commit's phase (bounded) before the TMEM is released
@@ -525,11 +528,16 @@ cudaError_t launch_mlp_forward_tc(const float *params, const float *feat, int64_
                                   double fallback, int sms, cudaStream_t s, float *pre, float *z) {
     if (n <= 0) return cudaSuccess;
     const int smem = (int)sizeof(MlpTcSmem) + 1024;
-    cudaError_t e = cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const bool train = pre != nullptr;
+    cudaError_t e = train ? cudaFuncSetAttribute(mlp_forward_tc_kernel<true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                          : cudaFuncSetAttribute(mlp_forward_tc_kernel<false>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (n + kTT - 1) / kTT;
     const int grid = (int)std::min<int64_t>(tiles, 4 * (int64_t)sms);
-    mlp_forward_tc_kernel<<<grid, kTT, smem, s>>>(params, feat, n, eps, err, fallback, pre, z);
+    if (train) mlp_forward_tc_kernel<true><<<grid, kTT, smem, s>>>(params, feat, n, eps, err, fallback, pre, z);
+    else mlp_forward_tc_kernel<false><<<grid, kTT, smem, s>>>(params, feat, n, eps, err, fallback, pre, z);
     return cudaGetLastError();
 }
 
